@@ -1,0 +1,227 @@
+"""Pins for the oracle's SP, SP-RK-RGS and SP-SCD methods (CPU only).
+
+Each check comes from a statement of the paper that does not restate the
+oracle's own formula: Theorem 2.1 (energy-norm contraction by rho, obtained
+here from a generalized eigenvalue solve), Theorem 3.1 (the inner fixed point of
+RK-RGS is the SP iterate), the Pythagorean step of Theorem 3.2's proof, the
+reduction of RK-RGS with j1 = j2 to coordinate descent (Sec. 4), the exact energy
+decrease of Theorem 4.1's proof, the alpha = n (Motzkin) special case, and the
+iteration counts printed in Tables 2-3.
+"""
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import oracle as O
+import workloads as W
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")
+
+
+@pytest.fixture(scope="module")
+def c1():
+    inst = W.config1()
+    xs = O.qr_cholesky_solve(inst.A, inst.b, inst.p)
+    return inst, xs
+
+
+def relerr(x, xs):
+    return np.linalg.norm(x - xs) / np.linalg.norm(xs)
+
+
+def test_sp_converges_to_direct_solution(c1):
+    inst, xs = c1
+    x, info = O.sp_solve(inst.A, inst.b, inst.p, tol=1e-12)
+    assert info.converged and relerr(x, xs) <= 1e-10
+    assert 3 <= info.outer_iters <= 20
+
+
+def test_sp_energy_contraction_theorem21(c1):
+    """||x_{k+1} - x*||_{Abar1} <= rho ||x_k - x*||_{Abar1}; the ratio tends to rho."""
+    inst, xs = c1
+    A1 = inst.A[: inst.p]
+    G1 = A1.T @ A1
+    rho = O.sp_spectral_radius(inst.A, inst.p)
+    x0 = np.random.default_rng(1).standard_normal(inst.n)
+    _, info = O.sp_solve(inst.A, inst.b, inst.p, x0=x0, tol=1e-14, max_outer=6, record=True)
+    errs = [O.energy_norm(x - xs, G1) for x in info.iterates]
+    ratios = [errs[k + 1] / errs[k] for k in range(len(errs) - 1)]
+    assert all(r <= rho * (1 + 1e-6) for r in ratios), (ratios, rho)
+    assert ratios[-1] >= 0.5 * rho  # the bound is attained asymptotically
+
+
+def test_sp_q_zero_one_step():
+    """q = 0: B = 0, so one SP step gives the least-squares solution (Sec. 1)."""
+    inst = W.dense_gaussian(80, 0, 12, 0.0, 4)
+    x, info = O.sp_solve(inst.A, inst.b, inst.p, tol=1e-13)
+    x_ls = np.linalg.lstsq(inst.A, inst.b, rcond=None)[0]
+    assert info.outer_iters == 1 and relerr(x, x_ls) < 1e-12
+
+
+def test_sp_multi_rhs_columns_independent():
+    inst = W.dense_gaussian(90, 20, 10, 0.3, 8, k=3)
+    X, info = O.sp_solve(inst.A, inst.b, inst.p, tol=1e-12)
+    for j in range(3):
+        xj, _ = O.sp_solve(inst.A, inst.b[:, j], inst.p, tol=1e-12)
+        assert np.allclose(X[:, j], xj, rtol=0, atol=1e-12 * np.linalg.norm(xj))
+
+
+def test_paper_table_iteration_counts():
+    """Tables 2-3 print SP IT = 1 at RR < 1e-6 from x0 = 0 on the rand / 7*eye workload.
+
+    Replayed at p = 4000, n = q = 1300 (the p/n ratio of Table 3's first column).
+    lambda_min(Abar1) grows like p while the 7*eye block does not, so the replay
+    scales the diagonal to keep rho(Abar1^{-1} Abar2) at the paper-size value
+    (about 0.17 for p = 30000, n = 13000).
+    """
+    gold = json.load(open(GOLD))
+    assert all(v == 1 for row in gold["printed"] for v in row["SP_IT"])
+    p, n = 4000, 1300
+    lam = lambda pp, nn: pp / 12.0 * (1.0 - math.sqrt(nn / pp)) ** 2  # U[0,1) Marchenko-Pastur edge
+    diag = 7.0 * math.sqrt(lam(p, n) / lam(30000, 13000))
+    inst = W.paper_table_workload(p, n, n, seed=0, diag=diag)
+    assert O.is_spd(O.normal_matrix(inst.A, p))
+    assert abs(O.sp_spectral_radius(inst.A, p) - 49.0 / lam(30000, 13000)) < 0.02
+    tol = math.sqrt(gold["stop_rr"])
+    x, info = O.sp_solve(inst.A, inst.b, p, tol=tol, max_outer=gold["max_outer"])
+    assert info.outer_iters == 1
+    assert O.paper_rr(inst.A, inst.b, p, x) < gold["stop_rr"]
+    # SP-SCD: the printed IT is between 1 and 2 on average (Tables 2-5).
+    _, info2 = O.sp_scd_solve(inst.A, inst.b, p, tol=tol, max_outer=3, max_inner=5 * n, theta=1e-3)
+    assert 1 <= info2.outer_iters <= 2 and info2.converged
+
+
+def test_rk_rgs_inner_fixed_point_theorem31(c1):
+    """With a tight inner solve the outer iterates of SP-RK-RGS equal SP's (Theorem 3.1)."""
+    inst, xs = c1
+    small = W.dense_gaussian(60, 15, 6, 0.2, 21)
+    _, sp = O.sp_solve(small.A, small.b, small.p, tol=1e-30, max_outer=3, record=True)
+    _, rk = O.sp_rk_rgs_solve(small.A, small.b, small.p, tol=1e-30, max_outer=3, theta=1e-9,
+                              max_inner=200000, check_every=6, record=True)
+    for a, b in zip(sp.iterates, rk.iterates):
+        assert np.linalg.norm(a - b) <= 1e-7 * np.linalg.norm(sp.iterates[-1])
+
+
+def test_rgs_pythagorean_step_theorem32():
+    """With w = w* = A_1 z*, an RGS step satisfies
+    ||A_1(z~ - z*)||^2 = ||A_1(z - z*)||^2 - ||A_1(z~ - z)||^2 (proof of Theorem 3.2)."""
+    rng = np.random.default_rng(3)
+    A1 = rng.standard_normal((25, 7))
+    norms2, _ = O.column_cumsum(A1)
+    zs = rng.standard_normal(7)
+    ws = A1 @ zs
+    z = rng.standard_normal(7)
+    for j in range(7):
+        zt = O.rgs_step(A1, z, ws, j, norms2)
+        lhs = np.sum((A1 @ (zt - zs)) ** 2)
+        rhs = np.sum((A1 @ (z - zs)) ** 2) - np.sum((A1 @ (zt - z)) ** 2)
+        assert abs(lhs - rhs) <= 1e-10 * np.sum((A1 @ (z - zs)) ** 2)
+        # orthogonality of A_1(z~ - z*) to column j
+        assert abs(A1[:, j] @ (A1 @ (zt - zs))) <= 1e-10 * np.linalg.norm(A1[:, j]) * np.linalg.norm(A1 @ (z - zs))
+
+
+def test_rk_projection_satisfies_row():
+    """After the RK step, the chosen equation A_1(:,j)^T w = bhat_j holds exactly (Sec. 3.1)."""
+    rng = np.random.default_rng(4)
+    A1 = rng.standard_normal((20, 5))
+    norms2, _ = O.column_cumsum(A1)
+    w = rng.standard_normal(20)
+    bhat = rng.standard_normal(5)
+    for j in range(5):
+        w2 = O.rk_step(A1, w, bhat, j, norms2)
+        assert abs(A1[:, j] @ w2 - bhat[j]) < 1e-12 * (1 + abs(bhat[j]))
+        d = w2 - w  # the change is along column j
+        assert np.linalg.matrix_rank(np.c_[d, A1[:, j]], tol=1e-10) == 1
+
+
+def test_rk_rgs_same_index_is_coordinate_descent():
+    """j1 = j2 = j turns the RK-RGS step into z_j += (bhat_j - Abar1(j,:) z) / Abar1_jj (Sec. 4)."""
+    rng = np.random.default_rng(6)
+    A1 = rng.standard_normal((30, 6))
+    G1 = A1.T @ A1
+    norms2, _ = O.column_cumsum(A1)
+    bhat = rng.standard_normal(6)
+    w = np.zeros(30)
+    z = np.zeros(6)
+    for t in range(40):
+        j = int(rng.integers(6))
+        w = O.rk_step(A1, w, bhat, j, norms2)
+        z_new = O.rgs_step(A1, z, w, j, norms2)
+        cd = z.copy()
+        cd[j] += (bhat[j] - G1[j] @ z) / G1[j, j]
+        assert np.allclose(z_new, cd, atol=1e-12 * (1 + np.abs(cd).max()))
+        z = z_new
+
+
+def test_scd_energy_decrease_theorem41():
+    """||beta_t - beta*||^2_{Abar1} = ||beta_{t-1} - beta*||^2_{Abar1} - r_j^2 / Abar1_jj, exactly."""
+    rng = np.random.default_rng(7)
+    A1 = rng.standard_normal((40, 8))
+    G1 = A1.T @ A1
+    bhat = rng.standard_normal(8)
+    bs = np.linalg.solve(G1, bhat)
+    beta = np.zeros(8)
+    r = bhat.copy()
+    e = lambda v: float((v - bs) @ G1 @ (v - bs))
+    for t in range(30):
+        j = int(rng.integers(8))
+        rj = r[j]
+        before = e(beta)
+        beta, r = O.scd_step(G1, beta, r, j)
+        assert abs(e(beta) - (before - rj * rj / G1[j, j])) <= 1e-9 * before
+        assert np.allclose(r, bhat - G1 @ beta, atol=1e-10)
+
+
+def test_scd_rank_law_equals_literal_law():
+    """The rank sampler has exactly the law of alpha ~ U{1..n} + uniform alpha-subset + argmax."""
+    rng = np.random.default_rng(8)
+    for n in range(1, 8):
+        absr = rng.permutation(n) + rng.random(n) * 0.1 + 0.5
+        assert np.allclose(O.scd_rank_law(absr), O.scd_literal_law(absr), atol=1e-14)
+
+
+def test_scd_rank_sampler_inverse_cdf():
+    n = 9
+    probs = np.array([(n + 1) / (n * i * (i + 1)) for i in range(1, n + 1)])
+    assert abs(probs.sum() - 1) < 1e-14
+    counts = np.zeros(n)
+    rng = np.random.default_rng(9)
+    for u in rng.random(20000):
+        counts[O.scd_rank_from_uniform(u, n) - 1] += 1
+    assert stats.chisquare(counts, 20000 * probs).pvalue > 1e-3
+    assert O.scd_rank_from_uniform(0.0, n) == 1
+    assert O.scd_rank_from_uniform(1.0 - 1e-16, n) == n
+
+
+def test_scd_literal_sampler_empirical_law():
+    rng = np.random.default_rng(10)
+    r = np.array([0.3, -2.0, 1.1, 0.05, -0.7])
+    counts = np.zeros(5)
+    for _ in range(20000):
+        a = int(rng.integers(1, 6))
+        counts[O.scd_pick_literal(r, a, rng.choice(5, size=a, replace=False))] += 1
+    expect = 20000 * O.scd_literal_law(np.abs(r))
+    assert stats.chisquare(counts, expect).pvalue > 1e-3
+
+
+def test_scd_greedy_is_argmax():
+    r = np.array([0.5, -3.0, 3.0, 1.0])
+    assert O.scd_pick_literal(r, 4, range(4)) == 1  # tie |r|=3: lowest index
+
+
+@pytest.mark.parametrize("sampler", ["rank", "literal", "greedy"])
+def test_scd_converges(c1, sampler):
+    inst, xs = c1
+    x, info = O.sp_scd_solve(inst.A, inst.b, inst.p, tol=1e-12, sampler=sampler)
+    assert info.converged and relerr(x, xs) <= 1e-10
+
+
+def test_rk_rgs_converges(c1):
+    inst, xs = c1
+    x, info = O.sp_rk_rgs_solve(inst.A, inst.b, inst.p, tol=1e-12)
+    assert info.converged and relerr(x, xs) <= 1e-10
