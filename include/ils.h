@@ -1,0 +1,163 @@
+/*
+ * ils.h -- C ABI of a GB300 (sm_103a) solver for the indefinite least squares
+ * (ILS) problem
+ *
+ *     min_x (b - A x)^T J (b - A x),   J = diag(I_p, -I_q),  p + q = m,
+ *
+ * (Zhang & Li, "Splitting-based randomized iterative methods for solving
+ * indefinite least squares problem", Sec. 1, eq. (1.1)).  A = [A_1; A_2] with
+ * A_1 p x n and A_2 q x n (Sec. 1.4, eq. (1.4)); the solution is unique and
+ * equals (A^T J A)^{-1} A^T J b exactly when A^T J A is symmetric positive
+ * definite (eq. (1.2)-(1.3)).  Three methods are provided: SP (Alg. 1),
+ * SP-RK-RGS (Alg. 2) and SP-SCD (Alg. 5).
+ *
+ * Conventions for every entry point:
+ *   - Matrices are column-major.  "lda" is the distance in elements between
+ *     consecutive columns and must be >= the number of rows.
+ *   - Pointers are DEVICE pointers unless the comment says "host".
+ *   - Work is ordered on the caller's stream (NULL = the legacy default
+ *     stream).  Calls that return an ils_info synchronize that stream before
+ *     returning; the others only enqueue work.
+ *   - Errors are returned as ils_status; nothing aborts, traps or prints.  A
+ *     CUDA error inside a call is returned as ILS_ERR_CUDA.
+ *   - A handle is not thread-safe; calls on one handle must not overlap.
+ */
+#ifndef ILS_H
+#define ILS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same object as cudaStream_t / CUstream. */
+typedef struct CUstream_st* ils_stream_t;
+
+typedef struct ils_handle_s* ils_handle;
+
+typedef enum {
+  ILS_OK = 0,
+  ILS_ERR_INVALID_ARG = 1,    /* bad size, stride, pointer or option */
+  ILS_ERR_NOT_SPD = 2,        /* A_1^T A_1 (hence A^T J A) failed its Cholesky pivot test, eq. (1.3) */
+  ILS_ERR_NO_CONVERGENCE = 3, /* max_outer reached; x holds the last iterate */
+  ILS_ERR_NONFINITE = 4,      /* a NaN/Inf appeared in the input or the iteration */
+  ILS_ERR_TIMEOUT = 5,        /* a bounded device-side wait ran out */
+  ILS_ERR_CUDA = 6,           /* a CUDA runtime call failed */
+  ILS_ERR_OOM = 7             /* device allocation failed */
+} ils_status;
+
+typedef enum {
+  ILS_SP = 0,        /* Alg. 1: x_{k+1} = B x_k + c, B = (A_1^T A_1)^{-1} A_2^T A_2 */
+  ILS_SP_RK_RGS = 1, /* Alg. 2: inner RK step on A_1^T w = bhat, RGS step on A_1 z = w */
+  ILS_SP_SCD = 2     /* Alg. 5: inner sampling coordinate descent on (A_1^T A_1) beta = bhat */
+} ils_method;
+
+typedef enum {
+  ILS_FP64 = 0,        /* every product in FP64 */
+  ILS_FP32_REFINE = 1, /* FP32 sweeps, FP64 residual refinement */
+  ILS_BF16_REFINE = 2  /* BF16 tensor-core products (FP32 accumulate), FP64 refinement */
+} ils_precision;
+
+typedef enum {
+  ILS_GRAM_FP64 = 0, /* A_1^T A_1 with FP64 fused multiply-adds */
+  ILS_GRAM_SPLIT = 1 /* A_1^T A_1 to FP64 accuracy from exact integer slice products on tensor cores */
+} ils_gram_mode;
+
+typedef struct {
+  int32_t method;      /* ils_method */
+  int32_t precision;   /* ils_precision */
+  int32_t gram;        /* ils_gram_mode */
+  int32_t timing;      /* != 0: time the setup phases with CUDA events (see ils_get_timings) */
+  int64_t max_outer;   /* outer-iteration cap; default 20000 (Sec. 5) */
+  int64_t max_inner;   /* inner-step cap per outer iteration (randomized methods); 0 = 200 n */
+  double theta;        /* inner stop: ||bhat - Abar1 z|| <= theta ||bbar - H x_k||; default 0.1 */
+  int64_t check_every; /* RK-RGS inner residual test period in steps; 0 = n */
+  int32_t scd_sampler; /* 0 = rank sampler equal in law to Alg. 5 steps 7-9; 1 = greedy (alpha = n) */
+  int32_t reserved1;
+  uint64_t seed;       /* Philox4x32-10 key for the randomized methods */
+} ils_options;
+
+typedef struct {
+  int64_t outer_iters;  /* IT in the paper's tables */
+  int64_t inner_iters;  /* IT-inner: total inner steps over all outer iterations */
+  int64_t refinements;  /* FP64 refinement passes (mixed precision) */
+  double relres;        /* ||A^T J (b - A x)|| / ||A^T J b|| of the returned x (FP64) */
+  int32_t status;       /* ils_status of this solve */
+  int32_t reserved;
+} ils_info;
+
+/* Fill *o with the defaults above (method SP, FP64, FP64 Gram, max_outer 20000,
+ * theta 0.1, seed 0).  Host only.  Returns ILS_ERR_INVALID_ARG if o is NULL. */
+ils_status ils_options_default(ils_options* o);
+
+/* Build a handle for one ILS instance (Alg. 1 steps 2-4; Alg. 2 steps 2-3;
+ * Alg. 5 step 2).
+ *   h    [host, out] receives the new handle (NULL on failure).
+ *   m,n,p,q          A is m x n with m = p + q, p >= n >= 1, q >= 0.
+ *   A    m x n, column-major, leading dimension lda >= m, FP64.  Read only; the
+ *        handle copies what it needs, so A may be freed once the stream has
+ *        passed this call.
+ *   o    [host] options, or NULL for the defaults.
+ * Work: copies A, forms Abar1 = A_1^T A_1 and Abar2 = A_2^T A_2, factors Abar1
+ * by Cholesky and forms P = Abar1^{-1}, B = P Abar2 and H = Abar1 - Abar2.
+ * Synchronizes the stream once to read the Cholesky pivot status.
+ * Errors: INVALID_ARG, OOM, CUDA, NOT_SPD (handle not created), NONFINITE. */
+ils_status ils_setup(ils_handle* h, int64_t m, int64_t n, int64_t p, int64_t q,
+                     const double* A, int64_t lda, const ils_options* o, ils_stream_t stream);
+
+/* Recompute every setup product of h for new matrix values of the same shape
+ * (same m, n, p, q), allocating nothing.  Same errors as ils_setup; on
+ * NOT_SPD the handle stays valid but must not be used to solve. */
+ils_status ils_refactor(ils_handle h, const double* A, int64_t lda, ils_stream_t stream);
+
+/* Solve for one right-hand side with the handle's method.
+ *   b    length m, FP64.
+ *   x    length n, FP64.  In: x0 unless x0_zero != 0.  Out: the solution.
+ *   tol  stop once ||A^T J (b - A x_k)|| <= tol ||A^T J b|| (checked before each
+ *        outer update, as in Sec. 5) or after max_outer updates.
+ *   info [host, out, may be NULL] iteration counts and the final relres.
+ * Synchronizes the stream.  Errors: INVALID_ARG, NO_CONVERGENCE (x = last
+ * iterate), NONFINITE, TIMEOUT, CUDA. */
+ils_status ils_solve(ils_handle h, const double* b, double* x, int x0_zero, double tol,
+                     ils_info* info, ils_stream_t stream);
+
+/* Solve for k right-hand sides at once (columns of B, m x k, leading dimension
+ * ldb >= m; X n x k, ldx >= n).  Each column stops on its own tolerance test.
+ * info [host, may be NULL] receives the worst column (largest relres; the
+ * largest iteration counts).  Synchronizes the stream. */
+ils_status ils_solve_many(ils_handle h, int64_t k, const double* B, int64_t ldb, double* X,
+                          int64_t ldx, int x0_zero, double tol, ils_info* info,
+                          ils_stream_t stream);
+
+/* Copy an internal n x n FP64 product of the handle into dst (device, column-major,
+ * leading dimension ldd >= n): which = 0 Abar1, 1 Abar2, 2 Cholesky factor L of
+ * Abar1 (lower triangle; the strict upper triangle of dst is set to 0), 3 P = Abar1^{-1},
+ * 4 B = P Abar2.  For tests and diagnostics.  Errors: INVALID_ARG, CUDA. */
+ils_status ils_get_matrix(ils_handle h, int which, double* dst, int64_t ldd, ils_stream_t stream);
+
+/* Setup phase times of the last ils_setup / ils_refactor on h, in milliseconds,
+ * measured with CUDA events on the handle's stream when options.timing != 0
+ * (zeros otherwise).  out [host] receives min(count, 6) values:
+ *   0 Abar1 Gram, 1 Abar2 Gram, 2 the two Cholesky factorizations,
+ *   3 P = Abar1^{-1} and B = P Abar2, 4 the whole setup, 5 the copy of A.
+ * Returns the number of values written, or -1 on a bad argument. */
+int ils_get_timings(ils_handle h, double* out, int count);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (all handles, all threads).  Host only. */
+int64_t ils_kernel_launches(void);
+
+/* Release everything the handle owns (stream-ordered on the stream it was
+ * created with).  NULL is ignored. */
+void ils_destroy(ils_handle h);
+
+/* Static, human-readable name of a status code.  Host only. */
+const char* ils_status_string(ils_status st);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ILS_H */

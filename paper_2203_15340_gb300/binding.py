@@ -1,0 +1,231 @@
+"""ctypes binding of libils.so: argument marshalling only.
+
+The functions keep the C names of ``include/ils.h``.  Device pointers, leading
+dimensions and the stream are passed as plain integers; the small ``Solver``
+wrapper takes torch CUDA tensors and reads their pointers.  Every numerical step
+runs inside the CUDA library; if ``libils.so`` is missing this module raises
+instead of computing anything itself.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libils.so")
+
+ILS_OK = 0
+ILS_ERR_INVALID_ARG = 1
+ILS_ERR_NOT_SPD = 2
+ILS_ERR_NO_CONVERGENCE = 3
+ILS_ERR_NONFINITE = 4
+ILS_ERR_TIMEOUT = 5
+ILS_ERR_CUDA = 6
+ILS_ERR_OOM = 7
+
+ILS_SP = 0
+ILS_SP_RK_RGS = 1
+ILS_SP_SCD = 2
+
+ILS_FP64 = 0
+ILS_FP32_REFINE = 1
+ILS_BF16_REFINE = 2
+
+ILS_GRAM_FP64 = 0
+ILS_GRAM_SPLIT = 1
+
+MAT_GRAM1, MAT_GRAM2, MAT_CHOL, MAT_P, MAT_B = range(5)
+
+
+class ils_options(ctypes.Structure):
+    _fields_ = [
+        ("method", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("gram", ctypes.c_int32),
+        ("timing", ctypes.c_int32),
+        ("max_outer", ctypes.c_int64),
+        ("max_inner", ctypes.c_int64),
+        ("theta", ctypes.c_double),
+        ("check_every", ctypes.c_int64),
+        ("scd_sampler", ctypes.c_int32),
+        ("reserved1", ctypes.c_int32),
+        ("seed", ctypes.c_uint64),
+    ]
+
+
+class ils_info(ctypes.Structure):
+    _fields_ = [
+        ("outer_iters", ctypes.c_int64),
+        ("inner_iters", ctypes.c_int64),
+        ("refinements", ctypes.c_int64),
+        ("relres", ctypes.c_double),
+        ("status", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+    def as_dict(self):
+        return {f[0]: getattr(self, f[0]) for f in self._fields_ if not f[0].startswith("reserved")}
+
+
+# Exported symbols and their ctypes signatures, in the order of include/ils.h.
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+SIGNATURES = {
+    "ils_options_default": (ctypes.c_int, [ctypes.POINTER(ils_options)]),
+    "ils_setup": (ctypes.c_int, [ctypes.POINTER(_P), _I64, _I64, _I64, _I64, _P, _I64,
+                                 ctypes.POINTER(ils_options), _P]),
+    "ils_refactor": (ctypes.c_int, [_P, _P, _I64, _P]),
+    "ils_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ils_info), _P]),
+    "ils_solve_many": (ctypes.c_int, [_P, _I64, _P, _I64, _P, _I64, ctypes.c_int, ctypes.c_double,
+                                      ctypes.POINTER(ils_info), _P]),
+    "ils_get_matrix": (ctypes.c_int, [_P, ctypes.c_int, _P, _I64, _P]),
+    "ils_get_timings": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
+    "ils_kernel_launches": (ctypes.c_int64, []),
+    "ils_destroy": (None, [_P]),
+    "ils_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libils.so (built by ``__graft_entry__.build()``); raise if it is absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is missing: build the CUDA library first (python -c "
+                "'import __graft_entry__ as g; g.build()'). There is no CPU fallback.")
+        handle = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(handle, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = handle
+    return _lib
+
+
+def kernel_launches() -> int:
+    """Kernels launched by libils.so in this process so far."""
+    return int(lib().ils_kernel_launches())
+
+
+def status_string(code: int) -> str:
+    return lib().ils_status_string(int(code)).decode()
+
+
+class ILSError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {status_string(code)} (status {code})")
+        self.code = code
+
+
+def _check(code: int, where: str, allow=(ILS_OK,)):
+    if code not in allow:
+        raise ILSError(code, where)
+    return code
+
+
+def options(**kw) -> ils_options:
+    o = ils_options()
+    _check(lib().ils_options_default(ctypes.byref(o)), "ils_options_default")
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        import torch
+        return int(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def _colmajor_ptr(t, rows: int, cols: int) -> tuple:
+    """Device pointer and leading dimension of a column-major rows x cols matrix.
+
+    A torch tensor of shape (cols, rows) with unit stride along its last axis is
+    the column-major layout the C ABI expects (it is the transpose view of a
+    row-major tensor).
+    """
+    if not t.is_cuda:
+        raise ValueError("tensor must live on the GPU")
+    if t.dtype.itemsize != 8:
+        raise ValueError("FP64 tensor expected")
+    if t.dim() == 1:
+        if t.shape[0] != rows or t.stride(0) != 1:
+            raise ValueError("vector shape/stride mismatch")
+        return t.data_ptr(), rows
+    if tuple(t.shape) != (cols, rows) or t.stride(1) != 1:
+        raise ValueError(f"expected a ({cols}, {rows}) tensor with unit inner stride, got "
+                         f"{tuple(t.shape)} strides {t.stride()}")
+    return t.data_ptr(), t.stride(0)
+
+
+class Solver:
+    """One ILS instance on the GPU (wraps an ils_handle).
+
+    ``At`` holds A column-major: a CUDA float64 tensor of shape (n, m).
+    """
+
+    def __init__(self, At, p: int, opts: ils_options | None = None, stream=None):
+        n, m = At.shape
+        self.m, self.n, self.p, self.q = m, n, p, m - p
+        ptr, lda = _colmajor_ptr(At, m, n)
+        self.opts = opts if opts is not None else options()
+        h = ctypes.c_void_p()
+        code = lib().ils_setup(ctypes.byref(h), m, n, p, m - p, ptr, lda, ctypes.byref(self.opts),
+                               _stream_ptr(stream))
+        _check(code, "ils_setup")
+        self.h = h
+
+    def refactor(self, At, stream=None):
+        ptr, lda = _colmajor_ptr(At, self.m, self.n)
+        return _check(lib().ils_refactor(self.h, ptr, lda, _stream_ptr(stream)), "ils_refactor")
+
+    def solve(self, b, x, x0_zero=True, tol=1e-12, stream=None, allow=(ILS_OK,)):
+        """Solve into the CUDA tensor ``x`` (length n) for ``b`` (length m)."""
+        bp, _ = _colmajor_ptr(b, self.m, 1)
+        xp, _ = _colmajor_ptr(x, self.n, 1)
+        info = ils_info()
+        code = lib().ils_solve(self.h, bp, xp, int(bool(x0_zero)), float(tol), ctypes.byref(info),
+                               _stream_ptr(stream))
+        _check(code, "ils_solve", allow)
+        return info
+
+    def solve_many(self, Bt, Xt, x0_zero=True, tol=1e-12, stream=None, allow=(ILS_OK,)):
+        """k right-hand sides: ``Bt`` (k, m) and ``Xt`` (k, n), both column-major views."""
+        k = Bt.shape[0]
+        bp, ldb = _colmajor_ptr(Bt, self.m, k)
+        xp, ldx = _colmajor_ptr(Xt, self.n, k)
+        info = ils_info()
+        code = lib().ils_solve_many(self.h, k, bp, ldb, xp, ldx, int(bool(x0_zero)), float(tol),
+                                    ctypes.byref(info), _stream_ptr(stream))
+        _check(code, "ils_solve_many", allow)
+        return info
+
+    def get_matrix(self, which: int, out, stream=None):
+        ptr, ld = _colmajor_ptr(out, self.n, self.n)
+        return _check(lib().ils_get_matrix(self.h, which, ptr, ld, _stream_ptr(stream)), "ils_get_matrix")
+
+    def timings(self):
+        """Setup phase times (ms) of the last setup/refactor when options.timing was set."""
+        buf = (ctypes.c_double * 6)()
+        n = lib().ils_get_timings(self.h, buf, 6)
+        keys = ["gram1", "gram2", "cholesky", "inverse_and_B", "setup", "copy_A"]
+        return {k: buf[i] for i, k in enumerate(keys[:max(n, 0)])}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ils_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,436 @@
+// C ABI of the ILS solver: handle life cycle, setup (Alg. 1 steps 2-4) and the
+// outer-iteration driver.  All device memory of a handle is one stream-ordered
+// allocation carved into aligned pieces.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "ils_internal.h"
+
+using namespace ils;
+
+struct ils_handle_s {
+  int64_t m = 0, n = 0, p = 0, q = 0;
+  ils_options opt{};
+  cudaStream_t stream = nullptr;
+  void* block = nullptr;  // the single device allocation
+  size_t block_bytes = 0;
+  // setup products
+  double* A = nullptr;  // m x n copy, ld m
+  double* G1 = nullptr; // Abar1 = A_1^T A_1
+  double* G2 = nullptr; // Abar2 = A_2^T A_2
+  double* L = nullptr;  // Cholesky factor of Abar1 (lower)
+  double* P = nullptr;  // Abar1^{-1}
+  double* Bt = nullptr; // B^T = (P Abar2)^T
+  double* H = nullptr;  // Abar1 - Abar2
+  double* work = nullptr;
+  // per-solve workspace (one pass of up to kMaxRhsPerPass columns)
+  double* bbar = nullptr;
+  double* cvec = nullptr;
+  double* bnorm2 = nullptr;
+  double* X0 = nullptr;
+  double* X1 = nullptr;
+  int32_t* col_done = nullptr;
+  double* col_rr = nullptr;
+  int64_t* col_iters = nullptr;
+  double* partials = nullptr;
+  SolveState* st = nullptr;
+  int32_t* dstatus = nullptr;
+  // pinned host mirrors
+  SolveState* h_st = nullptr;
+  int32_t* h_status = nullptr;
+  double* h_rr = nullptr;     // kMaxRhsPerPass
+  double* h_bn = nullptr;     // kMaxRhsPerPass
+  int64_t* h_iters = nullptr; // kMaxRhsPerPass
+  // setup phase timing (options.timing != 0)
+  cudaEvent_t ev[7] = {};
+  double t_ms[6] = {};
+};
+
+namespace ils {
+static std::atomic<int64_t> g_launches{0};
+void note_launch(int64_t count) { g_launches.fetch_add(count, std::memory_order_relaxed); }
+}  // namespace ils
+
+namespace {
+
+#define ILS_CK(expr)                          \
+  do {                                        \
+    cudaError_t e_ = (expr);                  \
+    if (e_ != cudaSuccess) return ILS_ERR_CUDA; \
+  } while (0)
+
+__global__ void init_state_kernel(SolveState* st, int64_t max_outer, int32_t* col_done, int k) {
+  if (threadIdx.x == 0) {
+    st->done = 0;
+    st->cur = 0;
+    st->status = 0;
+    st->pad0 = 0;
+    st->iters = 0;
+    st->max_outer = max_outer;
+    st->inner_total = 0;
+    st->counter = 0u;
+    st->pad1 = 0u;
+  }
+  if (threadIdx.x < kMaxRhsPerPass) col_done[threadIdx.x] = (threadIdx.x < k) ? 0 : 1;
+}
+
+__global__ void transpose_kernel(int64_t n, const double* src, double* dst, int64_t ldd) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % n, j = e / n;
+    dst[j + i * ldd] = src[i + j * n];
+  }
+}
+
+size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
+
+struct Carver {
+  char* base;
+  size_t off = 0;
+  bool dry;
+  template <class T>
+  T* take(size_t count) {
+    T* p = dry ? nullptr : reinterpret_cast<T*>(base + off);
+    off = align_up(off + sizeof(T) * count);
+    return p;
+  }
+};
+
+void carve(ils_handle h, Carver& c, size_t work_elems) {
+  const size_t nn = (size_t)h->n * (size_t)h->n;
+  const size_t nk = (size_t)h->n * kMaxRhsPerPass;
+  h->A = c.take<double>((size_t)h->m * (size_t)h->n);
+  h->G1 = c.take<double>(nn);
+  h->G2 = c.take<double>(nn);
+  h->L = c.take<double>(nn);
+  h->P = c.take<double>(nn);
+  h->Bt = c.take<double>(nn);
+  h->H = c.take<double>(nn);
+  h->work = c.take<double>(std::max<size_t>(work_elems, 1));
+  h->bbar = c.take<double>(nk);
+  h->cvec = c.take<double>(nk);
+  h->bnorm2 = c.take<double>(kMaxRhsPerPass);
+  h->X0 = c.take<double>(nk);
+  h->X1 = c.take<double>(nk);
+  h->col_done = c.take<int32_t>(kMaxRhsPerPass);
+  h->col_rr = c.take<double>(kMaxRhsPerPass);
+  h->col_iters = c.take<int64_t>(kMaxRhsPerPass);
+  h->partials = c.take<double>((size_t)sp_iterate_blocks(h->n) * kMaxRhsPerPass);
+  h->st = c.take<SolveState>(1);
+  h->dstatus = c.take<int32_t>(1);
+}
+
+size_t setup_work_elems(int64_t m, int64_t n, int64_t p, int64_t q) {
+  (void)m;
+  size_t w = 0;
+  w = std::max(w, gemm_tn_work_elems(p, n, n, true, nullptr));
+  w = std::max(w, gemm_tn_work_elems(q, n, n, true, nullptr));
+  w = std::max(w, gemm_tn_work_elems(n, n, n, false, nullptr));
+  return w;
+}
+
+ils_status validate_options(const ils_options* o) {
+  if (o->method < ILS_SP || o->method > ILS_SP_SCD) return ILS_ERR_INVALID_ARG;
+  if (o->precision < ILS_FP64 || o->precision > ILS_BF16_REFINE) return ILS_ERR_INVALID_ARG;
+  if (o->max_outer < 0 || o->max_inner < 0 || o->check_every < 0) return ILS_ERR_INVALID_ARG;
+  if (!(o->theta > 0.0)) return ILS_ERR_INVALID_ARG;
+  return ILS_OK;
+}
+
+cudaError_t mark(ils_handle h, int i) {
+  if (!h->opt.timing) return cudaSuccess;
+  if (!h->ev[i]) {
+    cudaError_t e = cudaEventCreate(&h->ev[i]);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaEventRecord(h->ev[i], h->stream);
+}
+
+void collect_timings(ils_handle h) {
+  for (double& t : h->t_ms) t = 0.0;
+  if (!h->opt.timing) return;
+  float ms = 0.f;
+  // events: 0 start(copy) 1 after copy 2 after gram1 3 after gram2 4 after cholesky 5 end
+  auto el = [&](int a, int b) {
+    if (h->ev[a] && h->ev[b] && cudaEventElapsedTime(&ms, h->ev[a], h->ev[b]) == cudaSuccess) return (double)ms;
+    cudaGetLastError();
+    return 0.0;
+  };
+  h->t_ms[0] = el(1, 2);
+  h->t_ms[1] = el(2, 3);
+  h->t_ms[2] = el(3, 4);
+  h->t_ms[3] = el(4, 5);
+  h->t_ms[4] = el(0, 5);
+  h->t_ms[5] = el(0, 1);
+}
+
+// All setup products for the current contents of h->A.
+ils_status compute_setup(ils_handle h) {
+  cudaStream_t s = h->stream;
+  const int64_t m = h->m, n = h->n, p = h->p, q = h->q;
+  ILS_CK(mark(h, 1));
+  // Abar1 = A_1^T A_1, Abar2 = A_2^T A_2 (Alg. 1 steps 2-3; Alg. 2 step 2; Alg. 5 step 2).
+  ILS_CK(gemm_tn_f64(p, n, n, h->A, m, h->A, m, p, h->G1, n, true, false, h->work, s));
+  ILS_CK(mark(h, 2));
+  ILS_CK(gemm_tn_f64(q, n, n, h->A + p, m, h->A + p, m, q, h->G2, n, true, false, h->work, s));
+  ILS_CK(mark(h, 3));
+  ILS_CK(axpby_mat_f64(n, 1.0, h->G1, -1.0, h->G2, h->H, s));
+  // Cholesky of Abar1; the explicit inverse of Alg. 1 step 2 is formed from it.
+  ILS_CK(cudaMemcpyAsync(h->L, h->G1, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, s));
+  ILS_CK(cudaMemsetAsync(h->dstatus, 0, sizeof(int32_t), s));
+  ILS_CK(cholesky_f64(n, h->L, h->dstatus, s));
+  // Condition (1.3): H = A^T J A must be SPD as well (Abar1 SPD alone does not give
+  // rho(B) < 1).  Its Cholesky runs in the P buffer, which is overwritten below.
+  ILS_CK(cudaMemcpyAsync(h->P, h->H, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, s));
+  ILS_CK(cholesky_f64(n, h->P, h->dstatus, s));
+  ILS_CK(mark(h, 4));
+  ILS_CK(cudaMemcpyAsync(h->h_status, h->dstatus, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  ILS_CK(cudaStreamSynchronize(s));
+  if (*h->h_status != 0) return (ils_status)*h->h_status;
+  // P = L^{-T} L^{-1} (Alg. 1 step 2), B^T = (P Abar2)^T = Abar2 P (Alg. 1 step 3).
+  ILS_CK(set_identity_f64(n, h->P, n, s));
+  ILS_CK(trsm_lower_f64(n, n, h->L, h->P, n, true, true, s));
+  ILS_CK(gemm_tn_f64(n, n, n, h->G2, n, h->P, n, n, h->Bt, n, false, false, h->work, s));
+  ILS_CK(mark(h, 5));
+  return ILS_OK;
+}
+
+void free_handle(ils_handle h) {
+  if (!h) return;
+  if (h->block) cudaFreeAsync(h->block, h->stream);
+  if (h->h_st) cudaFreeHost(h->h_st);
+  for (cudaEvent_t e : h->ev)
+    if (e) cudaEventDestroy(e);
+  delete h;
+}
+
+// One pass of SP over kk <= kMaxRhsPerPass right-hand sides.
+ils_status sp_pass(ils_handle h, int64_t kk, const double* B, int64_t ldb, double* X, int64_t ldx,
+                   int x0_zero, double tol, ils_info* agg) {
+  cudaStream_t s = h->stream;
+  const int64_t m = h->m, n = h->n, p = h->p;
+  // bbar = A^T J b (Alg. 1 step 4), c = P bbar.
+  ILS_CK(rhs_bar_f64(m, n, p, kk, h->A, m, B, ldb, h->bbar, n, s));
+  ILS_CK(sq_norms_cols_f64(n, kk, h->bbar, n, h->bnorm2, s));
+  ILS_CK(gemv_cols_f64(n, kk, h->P, n, h->bbar, n, h->cvec, n, s));
+  if (x0_zero) {
+    ILS_CK(cudaMemsetAsync(h->X0, 0, sizeof(double) * n * kk, s));
+  } else {
+    ILS_CK(cudaMemcpy2DAsync(h->X0, sizeof(double) * n, X, sizeof(double) * ldx, sizeof(double) * n, kk,
+                             cudaMemcpyDeviceToDevice, s));
+  }
+  init_state_kernel<<<1, 32, 0, s>>>(h->st, h->opt.max_outer, h->col_done, (int)kk);
+  note_launch();
+  ILS_CK(cudaGetLastError());
+  SpIterArgs a;
+  a.n = n;
+  a.k = kk;
+  a.Bt = h->Bt;
+  a.H = h->H;
+  a.cvec = h->cvec;
+  a.bbar = h->bbar;
+  a.bnorm2 = h->bnorm2;
+  a.X0 = h->X0;
+  a.X1 = h->X1;
+  a.tol2 = tol * tol;
+  a.col_done = h->col_done;
+  a.col_rr = h->col_rr;
+  a.col_iters = h->col_iters;
+  a.partials = h->partials;
+  a.st = h->st;
+  // Launch the outer step in growing chunks; launches after convergence return at once.
+  int64_t launched = 0, chunk = 16;
+  const int64_t cap = h->opt.max_outer + 1;
+  for (;;) {
+    const int64_t todo = std::min(chunk, cap - launched);
+    for (int64_t i = 0; i < todo; ++i) ILS_CK(sp_iterate_f64(a, s));
+    launched += todo;
+    ILS_CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+    ILS_CK(cudaStreamSynchronize(s));
+    if (h->h_st->done || launched >= cap) break;
+    chunk = std::min<int64_t>(chunk * 2, 1024);
+  }
+  if (!h->h_st->done) return ILS_ERR_TIMEOUT;  // cannot happen: the cap launch always finishes
+  ILS_CK(copy_final_f64(n, kk, h->X0, h->X1, h->st, X, ldx, s));
+  ILS_CK(cudaMemcpyAsync(h->h_rr, h->col_rr, sizeof(double) * kk, cudaMemcpyDeviceToHost, s));
+  ILS_CK(cudaMemcpyAsync(h->h_bn, h->bnorm2, sizeof(double) * kk, cudaMemcpyDeviceToHost, s));
+  ILS_CK(cudaMemcpyAsync(h->h_iters, h->col_iters, sizeof(int64_t) * kk, cudaMemcpyDeviceToHost, s));
+  ILS_CK(cudaStreamSynchronize(s));
+  for (int64_t c = 0; c < kk; ++c) {
+    const double bn = h->h_bn[c];
+    const double rel = bn > 0.0 ? std::sqrt(h->h_rr[c] / bn) : std::sqrt(h->h_rr[c]);
+    agg->relres = std::max(agg->relres, rel);
+    if (rel != rel) agg->relres = rel;
+    agg->outer_iters = std::max<int64_t>(agg->outer_iters, h->h_iters[c]);
+  }
+  const int32_t st = h->h_st->status;
+  if (st != 0 && agg->status == 0) agg->status = st;
+  return ILS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ils_status_string(ils_status st) {
+  switch (st) {
+    case ILS_OK: return "ok";
+    case ILS_ERR_INVALID_ARG: return "invalid argument";
+    case ILS_ERR_NOT_SPD: return "A^T J A (or A_1^T A_1) is not symmetric positive definite";
+    case ILS_ERR_NO_CONVERGENCE: return "outer-iteration cap reached before the tolerance";
+    case ILS_ERR_NONFINITE: return "non-finite value in the input or the iteration";
+    case ILS_ERR_TIMEOUT: return "a bounded device-side wait ran out";
+    case ILS_ERR_CUDA: return "CUDA runtime error";
+    case ILS_ERR_OOM: return "device memory allocation failed";
+  }
+  return "unknown status";
+}
+
+ils_status ils_options_default(ils_options* o) {
+  if (!o) return ILS_ERR_INVALID_ARG;
+  std::memset(o, 0, sizeof(*o));
+  o->method = ILS_SP;
+  o->precision = ILS_FP64;
+  o->gram = ILS_GRAM_FP64;
+  o->max_outer = 20000;
+  o->max_inner = 0;
+  o->theta = 0.1;
+  o->check_every = 0;
+  o->scd_sampler = 0;
+  o->seed = 0;
+  return ILS_OK;
+}
+
+ils_status ils_setup(ils_handle* out, int64_t m, int64_t n, int64_t p, int64_t q, const double* A, int64_t lda,
+                     const ils_options* o, ils_stream_t stream) {
+  if (!out) return ILS_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (n < 1 || p < n || q < 0 || m != p + q || lda < m || !A) return ILS_ERR_INVALID_ARG;
+  ils_options opt;
+  if (o) opt = *o;
+  else ils_options_default(&opt);
+  if (validate_options(&opt) != ILS_OK) return ILS_ERR_INVALID_ARG;
+  ils_handle h = new (std::nothrow) ils_handle_s();
+  if (!h) return ILS_ERR_OOM;
+  h->m = m;
+  h->n = n;
+  h->p = p;
+  h->q = q;
+  h->opt = opt;
+  h->stream = (cudaStream_t)stream;
+  const size_t work = setup_work_elems(m, n, p, q);
+  Carver dry{nullptr, 0, true};
+  carve(h, dry, work);
+  h->block_bytes = dry.off;
+  if (cudaMallocAsync(&h->block, h->block_bytes, h->stream) != cudaSuccess) {
+    cudaGetLastError();
+    h->block = nullptr;
+    free_handle(h);
+    return ILS_ERR_OOM;
+  }
+  Carver real{(char*)h->block, 0, false};
+  carve(h, real, work);
+  const size_t host_bytes = align_up(sizeof(SolveState)) + align_up(sizeof(int32_t)) +
+                            3 * align_up(sizeof(double) * kMaxRhsPerPass);
+  char* hb = nullptr;
+  if (cudaMallocHost((void**)&hb, host_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    free_handle(h);
+    return ILS_ERR_OOM;
+  }
+  h->h_st = (SolveState*)hb;
+  hb += align_up(sizeof(SolveState));
+  h->h_status = (int32_t*)hb;
+  hb += align_up(sizeof(int32_t));
+  h->h_rr = (double*)hb;
+  hb += align_up(sizeof(double) * kMaxRhsPerPass);
+  h->h_bn = (double*)hb;
+  hb += align_up(sizeof(double) * kMaxRhsPerPass);
+  h->h_iters = (int64_t*)hb;
+  ils_status st = ils_refactor(h, A, lda, stream);
+  if (st != ILS_OK) {
+    free_handle(h);
+    return st;
+  }
+  *out = h;
+  return ILS_OK;
+}
+
+ils_status ils_refactor(ils_handle h, const double* A, int64_t lda, ils_stream_t stream) {
+  if (!h || !A || lda < h->m) return ILS_ERR_INVALID_ARG;
+  h->stream = (cudaStream_t)stream;
+  cudaStream_t s = h->stream;
+  ILS_CK(mark(h, 0));
+  ILS_CK(cudaMemcpy2DAsync(h->A, sizeof(double) * h->m, A, sizeof(double) * lda, sizeof(double) * h->m, h->n,
+                           cudaMemcpyDeviceToDevice, s));
+  ils_status st = compute_setup(h);
+  if (st == ILS_OK && h->opt.timing) {
+    if (cudaStreamSynchronize(s) != cudaSuccess) return ILS_ERR_CUDA;
+    collect_timings(h);
+  }
+  return st;
+}
+
+int ils_get_timings(ils_handle h, double* out, int count) {
+  if (!h || !out || count < 0) return -1;
+  const int c = count < 6 ? count : 6;
+  for (int i = 0; i < c; ++i) out[i] = h->t_ms[i];
+  return c;
+}
+
+int64_t ils_kernel_launches(void) { return ils::g_launches.load(std::memory_order_relaxed); }
+
+ils_status ils_solve_many(ils_handle h, int64_t k, const double* B, int64_t ldb, double* X, int64_t ldx,
+                          int x0_zero, double tol, ils_info* info, ils_stream_t stream) {
+  if (!h || k < 0 || (k > 0 && (!B || !X)) || ldb < h->m || ldx < h->n || !(tol >= 0.0))
+    return ILS_ERR_INVALID_ARG;
+  h->stream = (cudaStream_t)stream;
+  ils_info agg;
+  std::memset(&agg, 0, sizeof(agg));
+  for (int64_t c0 = 0; c0 < k; c0 += kMaxRhsPerPass) {
+    const int64_t kk = std::min<int64_t>(kMaxRhsPerPass, k - c0);
+    ils_status st = sp_pass(h, kk, B + c0 * ldb, ldb, X + c0 * ldx, ldx, x0_zero, tol, &agg);
+    if (st != ILS_OK) {
+      agg.status = st;
+      if (info) *info = agg;
+      return st;
+    }
+  }
+  if (info) *info = agg;
+  return (ils_status)agg.status;
+}
+
+ils_status ils_solve(ils_handle h, const double* b, double* x, int x0_zero, double tol, ils_info* info,
+                     ils_stream_t stream) {
+  if (!h) return ILS_ERR_INVALID_ARG;
+  return ils_solve_many(h, 1, b, h->m, x, h->n, x0_zero, tol, info, stream);
+}
+
+ils_status ils_get_matrix(ils_handle h, int which, double* dst, int64_t ldd, ils_stream_t stream) {
+  if (!h || !dst || ldd < h->n || which < 0 || which > 4) return ILS_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = h->n;
+  const double* src = nullptr;
+  switch (which) {
+    case 0: src = h->G1; break;
+    case 1: src = h->G2; break;
+    case 2: ILS_CK(copy_lower_zero_upper_f64(n, h->L, dst, ldd, s)); return ILS_OK;
+    case 3: src = h->P; break;
+    case 4: {
+      transpose_kernel<<<256, 256, 0, s>>>(n, h->Bt, dst, ldd);
+      note_launch();
+      ILS_CK(cudaGetLastError());
+      return ILS_OK;
+    }
+  }
+  ILS_CK(cudaMemcpy2DAsync(dst, sizeof(double) * ldd, src, sizeof(double) * n, sizeof(double) * n, n,
+                           cudaMemcpyDeviceToDevice, s));
+  return ILS_OK;
+}
+
+void ils_destroy(ils_handle h) { free_handle(h); }
+
+}  // extern "C"

@@ -1,0 +1,58 @@
+"""The C-ABI library builds, loads and exports every function include/ils.h declares (CPU only)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?\w+\**\s+\**(ils_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    import __graft_entry__ as g
+    from paper_2203_15340_gb300 import _build
+    return _build.build()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("ils_setup", "ils_solve", "ils_solve_many", "ils_destroy", "ils_options_default",
+                     "ils_status_string", "ils_refactor"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_signatures_cover_header(libpath):
+    from paper_2203_15340_gb300 import binding
+    assert set(declared_functions()) <= set(binding.SIGNATURES)
+
+
+def test_host_only_calls_without_gpu(libpath):
+    from paper_2203_15340_gb300 import binding
+    o = binding.options()
+    assert o.max_outer == 20000 and abs(o.theta - 0.1) < 1e-15 and o.method == 0
+    assert binding.status_string(2).startswith("A^T J A")
+    lib = binding.lib()
+    h = ctypes.c_void_p()
+    # Invalid sizes are rejected on the host before any CUDA call.
+    assert lib.ils_setup(ctypes.byref(h), 10, 5, 3, 7, 1, 10, None, None) == binding.ILS_ERR_INVALID_ARG
+    assert lib.ils_setup(ctypes.byref(h), 10, 5, 8, 2, 0, 10, None, None) == binding.ILS_ERR_INVALID_ARG
+    assert lib.ils_setup(ctypes.byref(h), 10, 5, 8, 2, 1, 9, None, None) == binding.ILS_ERR_INVALID_ARG
+    assert lib.ils_options_default(None) == binding.ILS_ERR_INVALID_ARG
