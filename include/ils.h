@@ -74,7 +74,8 @@ typedef struct {
   int64_t max_inner;   /* inner-step cap per outer iteration (randomized methods); 0 = 200 n */
   double theta;        /* inner stop: ||bhat - Abar1 z|| <= theta ||bbar - H x_k||; default 0.1 */
   int64_t check_every; /* RK-RGS inner residual test period in steps; 0 = n */
-  int32_t scd_sampler; /* 0 = rank sampler equal in law to Alg. 5 steps 7-9; 1 = greedy (alpha = n) */
+  int32_t scd_sampler; /* SP-SCD: 0 = rank sampler equal in law to Alg. 5 steps 7-9, 1 = greedy
+                          (alpha = n, the Motzkin rule).  SP-RK-RGS: 2 = draw j2 = j1 (SP-RCD) */
   int32_t reserved1;
   uint64_t seed;       /* Philox4x32-10 key for the randomized methods */
 } ils_options;

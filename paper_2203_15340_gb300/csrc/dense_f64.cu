@@ -420,7 +420,8 @@ __global__ void __launch_bounds__(32 * kIterWarps) sp_iter_kernel(SpIterArgs a) 
         if (done_c[c]) {
           xn[i + c * n] = x[i + c * n];
         } else {
-          xn[i + c * n] = sb + a.cvec[i + c * n];
+          if (a.mode == 0) xn[i + c * n] = sb + a.cvec[i + c * n];
+          else a.bhat_out[i + c * n] = sb + a.cvec[i + c * n];
           const double r = a.bbar[i + c * n] - sh;
           rpart[c] = fma(r, r, rpart[c]);
         }
@@ -466,6 +467,7 @@ __global__ void __launch_bounds__(32 * kIterWarps) sp_iter_kernel(SpIterArgs a) 
         else if (!conv) atomicCAS(&st->status, 0, ILS_ERR_NO_CONVERGENCE);
       } else {
         all = 0;
+        if (a.mode == 1) a.col_target2[c] = a.theta2 * rr;
       }
     }
     all_done = all;

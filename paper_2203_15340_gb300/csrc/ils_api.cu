@@ -36,6 +36,13 @@ struct ils_handle_s {
   double* col_rr = nullptr;
   int64_t* col_iters = nullptr;
   double* partials = nullptr;
+  double* bhat = nullptr;        // n x kMaxRhsPerPass (randomized methods)
+  double* col_target2 = nullptr; // kMaxRhsPerPass
+  int64_t* col_inner = nullptr;  // kMaxRhsPerPass
+  double* norms2 = nullptr;      // n: ||A_1(:,j)||^2
+  double* cum = nullptr;         // n: running sum of norms2
+  double* vec_scratch = nullptr; // RK-RGS w and e when they do not fit in shared memory
+  bool vec_in_smem = true;
   SolveState* st = nullptr;
   int32_t* dstatus = nullptr;
   // pinned host mirrors
@@ -44,6 +51,7 @@ struct ils_handle_s {
   double* h_rr = nullptr;     // kMaxRhsPerPass
   double* h_bn = nullptr;     // kMaxRhsPerPass
   int64_t* h_iters = nullptr; // kMaxRhsPerPass
+  int64_t* h_inner = nullptr; // kMaxRhsPerPass
   // setup phase timing (options.timing != 0)
   cudaEvent_t ev[7] = {};
   double t_ms[6] = {};
@@ -62,7 +70,8 @@ namespace {
     if (e_ != cudaSuccess) return ILS_ERR_CUDA; \
   } while (0)
 
-__global__ void init_state_kernel(SolveState* st, int64_t max_outer, int32_t* col_done, int k) {
+__global__ void init_state_kernel(SolveState* st, int64_t max_outer, int32_t* col_done, int64_t* col_inner,
+                                  int k) {
   if (threadIdx.x == 0) {
     st->done = 0;
     st->cur = 0;
@@ -74,7 +83,10 @@ __global__ void init_state_kernel(SolveState* st, int64_t max_outer, int32_t* co
     st->counter = 0u;
     st->pad1 = 0u;
   }
-  if (threadIdx.x < kMaxRhsPerPass) col_done[threadIdx.x] = (threadIdx.x < k) ? 0 : 1;
+  if (threadIdx.x < kMaxRhsPerPass) {
+    col_done[threadIdx.x] = (threadIdx.x < k) ? 0 : 1;
+    col_inner[threadIdx.x] = 0;
+  }
 }
 
 __global__ void transpose_kernel(int64_t n, const double* src, double* dst, int64_t ldd) {
@@ -119,6 +131,14 @@ void carve(ils_handle h, Carver& c, size_t work_elems) {
   h->col_rr = c.take<double>(kMaxRhsPerPass);
   h->col_iters = c.take<int64_t>(kMaxRhsPerPass);
   h->partials = c.take<double>((size_t)sp_iterate_blocks(h->n) * kMaxRhsPerPass);
+  h->bhat = c.take<double>(nk);
+  h->col_target2 = c.take<double>(kMaxRhsPerPass);
+  h->col_inner = c.take<int64_t>(kMaxRhsPerPass);
+  h->norms2 = c.take<double>((size_t)h->n);
+  h->cum = c.take<double>((size_t)h->n);
+  h->vec_in_smem = rkrgs_vec_fits(h->n, h->p);
+  const bool need_scratch = h->opt.method == ILS_SP_RK_RGS && !h->vec_in_smem;
+  h->vec_scratch = c.take<double>(need_scratch ? (size_t)kMaxRhsPerPass * 2 * (size_t)h->p : 1);
   h->st = c.take<SolveState>(1);
   h->dstatus = c.take<int32_t>(1);
 }
@@ -175,6 +195,7 @@ ils_status compute_setup(ils_handle h) {
   // Abar1 = A_1^T A_1, Abar2 = A_2^T A_2 (Alg. 1 steps 2-3; Alg. 2 step 2; Alg. 5 step 2).
   ILS_CK(gemm_tn_f64(p, n, n, h->A, m, h->A, m, p, h->G1, n, true, false, h->work, s));
   ILS_CK(mark(h, 2));
+  ILS_CK(column_cumsum_f64(n, h->G1, h->norms2, h->cum, s));
   ILS_CK(gemm_tn_f64(q, n, n, h->A + p, m, h->A + p, m, q, h->G2, n, true, false, h->work, s));
   ILS_CK(mark(h, 3));
   ILS_CK(axpby_mat_f64(n, 1.0, h->G1, -1.0, h->G2, h->H, s));
@@ -208,8 +229,9 @@ void free_handle(ils_handle h) {
 }
 
 // One pass of SP over kk <= kMaxRhsPerPass right-hand sides.
-ils_status sp_pass(ils_handle h, int64_t kk, const double* B, int64_t ldb, double* X, int64_t ldx,
+ils_status sp_pass(ils_handle h, int64_t c0, int64_t kk, const double* B, int64_t ldb, double* X, int64_t ldx,
                    int x0_zero, double tol, ils_info* agg) {
+  const int method = h->opt.method;
   cudaStream_t s = h->stream;
   const int64_t m = h->m, n = h->n, p = h->p;
   // bbar = A^T J b (Alg. 1 step 4), c = P bbar.
@@ -222,15 +244,20 @@ ils_status sp_pass(ils_handle h, int64_t kk, const double* B, int64_t ldb, doubl
     ILS_CK(cudaMemcpy2DAsync(h->X0, sizeof(double) * n, X, sizeof(double) * ldx, sizeof(double) * n, kk,
                              cudaMemcpyDeviceToDevice, s));
   }
-  init_state_kernel<<<1, 32, 0, s>>>(h->st, h->opt.max_outer, h->col_done, (int)kk);
+  init_state_kernel<<<1, 32, 0, s>>>(h->st, h->opt.max_outer, h->col_done, h->col_inner, (int)kk);
   note_launch();
   ILS_CK(cudaGetLastError());
   SpIterArgs a;
   a.n = n;
   a.k = kk;
-  a.Bt = h->Bt;
+  a.mode = method == ILS_SP ? 0 : 1;
+  a.pad = 0;
+  a.Bt = method == ILS_SP ? h->Bt : h->G2;
   a.H = h->H;
-  a.cvec = h->cvec;
+  a.cvec = method == ILS_SP ? h->cvec : h->bbar;
+  a.bhat_out = h->bhat;
+  a.theta2 = h->opt.theta * h->opt.theta;
+  a.col_target2 = h->col_target2;
   a.bbar = h->bbar;
   a.bnorm2 = h->bnorm2;
   a.X0 = h->X0;
@@ -241,12 +268,40 @@ ils_status sp_pass(ils_handle h, int64_t kk, const double* B, int64_t ldb, doubl
   a.col_iters = h->col_iters;
   a.partials = h->partials;
   a.st = h->st;
+  RandArgs ra;
+  ra.n = n;
+  ra.k = kk;
+  ra.m = m;
+  ra.p = p;
+  ra.A = h->A;
+  ra.G1 = h->G1;
+  ra.norms2 = h->norms2;
+  ra.cum = h->cum;
+  ra.bhat = h->bhat;
+  ra.X0 = h->X0;
+  ra.X1 = h->X1;
+  ra.col_done = h->col_done;
+  ra.col_target2 = h->col_target2;
+  ra.col_inner = h->col_inner;
+  ra.st = h->st;
+  ra.seed = h->opt.seed;
+  ra.chain0 = c0;
+  ra.max_inner = h->opt.max_inner > 0 ? h->opt.max_inner : 200 * n;
+  ra.check_every = h->opt.check_every > 0 ? h->opt.check_every : n;
+  ra.greedy = h->opt.scd_sampler == 1 ? 1 : 0;
+  ra.same_index = h->opt.scd_sampler == 2 ? 1 : 0;
+  ra.vec_in_smem = h->vec_in_smem ? 1 : 0;
+  ra.pad = 0;
+  ra.vec_scratch = h->vec_scratch;
   // Launch the outer step in growing chunks; launches after convergence return at once.
-  int64_t launched = 0, chunk = 16;
+  int64_t launched = 0, chunk = method == ILS_SP ? 16 : 4;
   const int64_t cap = h->opt.max_outer + 1;
   for (;;) {
     const int64_t todo = std::min(chunk, cap - launched);
-    for (int64_t i = 0; i < todo; ++i) ILS_CK(sp_iterate_f64(a, s));
+    for (int64_t i = 0; i < todo; ++i) {
+      ILS_CK(sp_iterate_f64(a, s));
+      if (method != ILS_SP) ILS_CK(rand_chain_f64(ra, method, s));
+    }
     launched += todo;
     ILS_CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
     ILS_CK(cudaStreamSynchronize(s));
@@ -258,6 +313,7 @@ ils_status sp_pass(ils_handle h, int64_t kk, const double* B, int64_t ldb, doubl
   ILS_CK(cudaMemcpyAsync(h->h_rr, h->col_rr, sizeof(double) * kk, cudaMemcpyDeviceToHost, s));
   ILS_CK(cudaMemcpyAsync(h->h_bn, h->bnorm2, sizeof(double) * kk, cudaMemcpyDeviceToHost, s));
   ILS_CK(cudaMemcpyAsync(h->h_iters, h->col_iters, sizeof(int64_t) * kk, cudaMemcpyDeviceToHost, s));
+  ILS_CK(cudaMemcpyAsync(h->h_inner, h->col_inner, sizeof(int64_t) * kk, cudaMemcpyDeviceToHost, s));
   ILS_CK(cudaStreamSynchronize(s));
   for (int64_t c = 0; c < kk; ++c) {
     const double bn = h->h_bn[c];
@@ -265,6 +321,7 @@ ils_status sp_pass(ils_handle h, int64_t kk, const double* B, int64_t ldb, doubl
     agg->relres = std::max(agg->relres, rel);
     if (rel != rel) agg->relres = rel;
     agg->outer_iters = std::max<int64_t>(agg->outer_iters, h->h_iters[c]);
+    agg->inner_iters = std::max<int64_t>(agg->inner_iters, h->h_inner[c]);
   }
   const int32_t st = h->h_st->status;
   if (st != 0 && agg->status == 0) agg->status = st;
@@ -334,7 +391,7 @@ ils_status ils_setup(ils_handle* out, int64_t m, int64_t n, int64_t p, int64_t q
   Carver real{(char*)h->block, 0, false};
   carve(h, real, work);
   const size_t host_bytes = align_up(sizeof(SolveState)) + align_up(sizeof(int32_t)) +
-                            3 * align_up(sizeof(double) * kMaxRhsPerPass);
+                            4 * align_up(sizeof(double) * kMaxRhsPerPass);
   char* hb = nullptr;
   if (cudaMallocHost((void**)&hb, host_bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -350,6 +407,8 @@ ils_status ils_setup(ils_handle* out, int64_t m, int64_t n, int64_t p, int64_t q
   h->h_bn = (double*)hb;
   hb += align_up(sizeof(double) * kMaxRhsPerPass);
   h->h_iters = (int64_t*)hb;
+  hb += align_up(sizeof(double) * kMaxRhsPerPass);
+  h->h_inner = (int64_t*)hb;
   ils_status st = ils_refactor(h, A, lda, stream);
   if (st != ILS_OK) {
     free_handle(h);
@@ -392,7 +451,7 @@ ils_status ils_solve_many(ils_handle h, int64_t k, const double* B, int64_t ldb,
   std::memset(&agg, 0, sizeof(agg));
   for (int64_t c0 = 0; c0 < k; c0 += kMaxRhsPerPass) {
     const int64_t kk = std::min<int64_t>(kMaxRhsPerPass, k - c0);
-    ils_status st = sp_pass(h, kk, B + c0 * ldb, ldb, X + c0 * ldx, ldx, x0_zero, tol, &agg);
+    ils_status st = sp_pass(h, c0, kk, B + c0 * ldb, ldb, X + c0 * ldx, ldx, x0_zero, tol, &agg);
     if (st != ILS_OK) {
       agg.status = st;
       if (info) *info = agg;

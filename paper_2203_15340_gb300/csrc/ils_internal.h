@@ -65,18 +65,27 @@ cudaError_t copy_lower_zero_upper_f64(int64_t n, const double* L, double* dst, i
 cudaError_t sq_norms_cols_f64(int64_t n, int64_t k, const double* X, int64_t ldx, double* out,
                               cudaStream_t s);
 
-// One SP outer step for up to kMaxRhsPerPass columns (Alg. 1 step 6 with the residual
-// test of Sec. 5 on x_k).  See dense_f64.cu for the protocol.
+// One outer step for up to kMaxRhsPerPass columns.  For every unfinished column it
+// forms the residual r_k = bbar - H x_k of Sec. 5's stopping test and either
+//   mode 0 (SP, Alg. 1 step 6):        x_{k+1} = B x_k + c  (M = B^T, addv = c), or
+//   mode 1 (randomized, Alg. 2 step 5 / Alg. 5 step 4): bhat = Abar2 x_k + bbar
+//          (M = Abar2, addv = bbar), written to bhat_out for the inner chain.
+// See dense_f64.cu for the completion protocol.
 struct SpIterArgs {
   int64_t n, k;
-  const double* Bt;    // B^T, column-major n x n: column i = row i of B
+  int32_t mode;
+  int32_t pad;
+  const double* Bt;    // M, column-major n x n: column i = row i of the operator
   const double* H;     // A^T J A (symmetric)
-  const double* cvec;  // n x k
+  const double* cvec;  // addv, n x k
   const double* bbar;  // n x k
   const double* bnorm2;  // k
   double* X0;          // n x k iterate buffers
   double* X1;
+  double* bhat_out;    // n x k (mode 1)
   double tol2;         // tol^2
+  double theta2;       // theta^2 (mode 1): inner target = theta^2 ||r_k||^2
+  double* col_target2; // k (mode 1)
   int32_t* col_done;   // k flags
   double* col_rr;      // k: ||r||^2 of each column's returned iterate
   int64_t* col_iters;  // k
@@ -89,5 +98,33 @@ int sp_iterate_blocks(int64_t n);
 // Copy the final iterate buffer (chosen on the device) into the user's X.
 cudaError_t copy_final_f64(int64_t n, int64_t k, const double* X0, const double* X1,
                            const SolveState* st, double* X, int64_t ldx, cudaStream_t s);
+
+// ---- randomized inner chains (randomized.cu) ----------------------------------------------
+struct RandArgs {
+  int64_t n, k, m, p;
+  const double* A;        // the handle's copy of A, m x n, ld m (A_1 = rows 0..p-1)
+  const double* G1;       // Abar1
+  const double* norms2;   // ||A_1(:,j)||^2
+  const double* cum;      // running sum of norms2, left to right
+  const double* bhat;     // n x k
+  double* X0;
+  double* X1;
+  const int32_t* col_done;
+  const double* col_target2;
+  int64_t* col_inner;
+  SolveState* st;
+  uint64_t seed;
+  int64_t chain0;         // chain id of column 0 of this pass
+  int64_t max_inner;
+  int64_t check_every;
+  int32_t greedy;         // SCD: alpha = n
+  int32_t same_index;     // RK-RGS: j2 = j1 (the SP-RCD special case)
+  int32_t vec_in_smem;    // RK-RGS: w, e in shared memory
+  int32_t pad;
+  double* vec_scratch;    // RK-RGS: k x 2p when not in shared memory
+};
+cudaError_t column_cumsum_f64(int64_t n, const double* G1, double* norms2, double* cum, cudaStream_t s);
+cudaError_t rand_chain_f64(const RandArgs& a, int method, cudaStream_t s);
+bool rkrgs_vec_fits(int64_t n, int64_t p);
 
 }  // namespace ils
