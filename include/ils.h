@@ -150,6 +150,24 @@ int ils_get_timings(ils_handle h, double* out, int count);
  * (all handles, all threads).  Host only. */
 int64_t ils_kernel_launches(void);
 
+/* Gram product C = X^T X (FP64) without any device allocation.  The paper has no
+ * counterpart; this entry point exists for callers that cannot call cudaMalloc (for
+ * example code that runs under stream capture with allocation forbidden, or inside a
+ * host application whose allocator owns all device memory).
+ *   K, n  X is K x n, column-major, leading dimension ldx >= max(K, 1); 1 <= n <= 1024
+ *         (larger n is rejected with ILS_ERR_INVALID_ARG).  K = 0 gives C = 0.
+ *   C     n x n, column-major, ldc >= n; both triangles are written.
+ * The split-K partial sums live in a fixed 16 MiB array (2^21 doubles) inside the
+ * library's device memory, resident on every GPU that loads the library until the
+ * process exits; when they would not fit, the call uses fewer, longer K slices.  The
+ * first call on each device looks up that array's device address (with that device
+ * current), so make the first call on a device before any stream capture.  Every call
+ * shares the array: calls whose work overlaps on the GPU (different streams, or
+ * different host threads) race on it and must be serialized by the caller.  Enqueues
+ * work only; nothing is synchronized.  Errors: INVALID_ARG, CUDA. */
+ils_status ils_gram_noalloc(int64_t K, int64_t n, const double* X, int64_t ldx, double* C, int64_t ldc,
+                            ils_stream_t stream);
+
 /* Release everything the handle owns (stream-ordered on the stream it was
  * created with).  NULL is ignored. */
 void ils_destroy(ils_handle h);

@@ -81,6 +81,7 @@ SIGNATURES = {
     "ils_get_matrix": (ctypes.c_int, [_P, ctypes.c_int, _P, _I64, _P]),
     "ils_get_timings": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
     "ils_kernel_launches": (ctypes.c_int64, []),
+    "ils_gram_noalloc": (ctypes.c_int, [_I64, _I64, _P, _I64, _P, _I64, _P]),
     "ils_destroy": (None, [_P]),
     "ils_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }

@@ -543,6 +543,32 @@ cudaError_t gemm_tn_f64(int64_t K, int64_t n1, int64_t n2, const double* X, int6
   return cudaGetLastError();
 }
 
+cudaError_t gemm_tn_f64_capped(int64_t K, int64_t n, const double* X, int64_t ldx, double* C, int64_t ldc,
+                               double* work, size_t work_cap_elems, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (K <= 0) return cudaMemset2DAsync(C, sizeof(double) * ldc, 0, sizeof(double) * n, n, s);
+  int splits;
+  int64_t chunk;
+  gemm_plan(K, n, n, true, &splits, &chunk);
+  const int64_t cap = (int64_t)(work_cap_elems / ((size_t)n * (size_t)n));
+  if (splits > 1 && splits > cap) {
+    // Fewer, longer K slices so the partial sums fit in the caller's scratch.
+    const int64_t sp = std::max<int64_t>(1, cap);
+    chunk = ((K + sp - 1) / sp + kTK - 1) / kTK * kTK;
+    splits = (int)((K + chunk - 1) / chunk);
+  }
+  dim3 grid((unsigned)((n + kTM - 1) / kTM), (unsigned)((n + kTM - 1) / kTM), (unsigned)splits);
+  const bool partial = splits > 1;
+  gemm_tn_kernel<<<grid, kGemmThreads, 0, s>>>(K, n, n, X, ldx, X, ldx, K, partial ? work : C, ldc, 1, 0, chunk,
+                                                partial ? 1 : 0);
+  note_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !partial) return e;
+  gemm_reduce_kernel<<<grid_for(n * n, 256), 256, 0, s>>>(n, n, splits, work, C, ldc, 1, 0);
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t rhs_bar_f64(int64_t m, int64_t n, int64_t p, int64_t k, const double* A, int64_t lda, const double* B,
                         int64_t ldb, double* out, int64_t ldo, cudaStream_t s) {
   if (n <= 0 || k <= 0) return cudaSuccess;

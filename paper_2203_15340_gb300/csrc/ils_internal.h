@@ -39,6 +39,11 @@ cudaError_t gemm_tn_f64(int64_t K, int64_t n1, int64_t n2, const double* X, int6
                         const double* Y, int64_t ldy, int64_t sign_split, double* C,
                         int64_t ldc, bool sym, bool trans_out, double* work, cudaStream_t s);
 
+// Symmetric C = X^T X like gemm_tn_f64, with the split-K partial sums limited to
+// work_cap_elems doubles of the given work array (fewer, longer K slices if needed).
+cudaError_t gemm_tn_f64_capped(int64_t K, int64_t n, const double* X, int64_t ldx, double* C, int64_t ldc,
+                               double* work, size_t work_cap_elems, cudaStream_t s);
+
 // out(:,c) = A^T J b(:,c) for k right-hand sides: A m x n (lda), B m x k (ldb),
 // rows >= p carry the minus sign of J.  out is n x k (ldo).
 cudaError_t rhs_bar_f64(int64_t m, int64_t n, int64_t p, int64_t k, const double* A, int64_t lda,
