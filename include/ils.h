@@ -55,9 +55,12 @@ typedef enum {
 } ils_method;
 
 typedef enum {
-  ILS_FP64 = 0,        /* every product in FP64 */
-  ILS_FP32_REFINE = 1, /* FP32 sweeps, FP64 residual refinement */
-  ILS_BF16_REFINE = 2  /* BF16 tensor-core products (FP32 accumulate), FP64 refinement */
+  ILS_FP64 = 0,        /* every product in FP64 (the paper's arithmetic) */
+  ILS_FP32_REFINE = 1, /* SP method only: FP64-accurate Grams and Cholesky factor; the
+                          correction sweeps use P = Abar1^{-1} and B = P Abar2 in FP32 with FP32
+                          accumulation; each step's residual bbar - H x is FP64 (iterative
+                          refinement), so the FP64 stopping test still decides. */
+  ILS_BF16_REFINE = 2  /* as ILS_FP32_REFINE with B held in BF16 (FP32 accumulation) */
 } ils_precision;
 
 typedef enum {
@@ -76,14 +79,14 @@ typedef struct {
   int64_t check_every; /* RK-RGS inner residual test period in steps; 0 = n */
   int32_t scd_sampler; /* SP-SCD: 0 = rank sampler equal in law to Alg. 5 steps 7-9, 1 = greedy
                           (alpha = n, the Motzkin rule).  SP-RK-RGS: 2 = draw j2 = j1 (SP-RCD) */
-  int32_t reserved1;
+  int32_t sweeps;      /* mixed precision: SP sweeps per FP64 refinement step; 0 = 3 */
   uint64_t seed;       /* Philox4x32-10 key for the randomized methods */
 } ils_options;
 
 typedef struct {
-  int64_t outer_iters;  /* IT in the paper's tables */
+  int64_t outer_iters;  /* IT in the paper's tables (mixed precision: total SP sweeps) */
   int64_t inner_iters;  /* IT-inner: total inner steps over all outer iterations */
-  int64_t refinements;  /* FP64 refinement passes (mixed precision) */
+  int64_t refinements;  /* FP64 refinement steps (mixed precision), 0 otherwise */
   double relres;        /* ||A^T J (b - A x)|| / ||A^T J b|| of the returned x (FP64) */
   int32_t status;       /* ils_status of this solve */
   int32_t reserved;
@@ -101,8 +104,10 @@ ils_status ils_options_default(ils_options* o);
  *        handle copies what it needs, so A may be freed once the stream has
  *        passed this call.
  *   o    [host] options, or NULL for the defaults.
- * Work: copies A, forms Abar1 = A_1^T A_1 and Abar2 = A_2^T A_2, factors Abar1
- * by Cholesky and forms P = Abar1^{-1}, B = P Abar2 and H = Abar1 - Abar2.
+ * Work: copies A, forms Abar1 = A_1^T A_1 and Abar2 = A_2^T A_2 (FP64, or FP64-accurate
+ * split tensor-core products when options.gram = ILS_GRAM_SPLIT or precision is mixed),
+ * factors Abar1 and H = Abar1 - Abar2 by Cholesky (the SPD test of eq. (1.3)) and forms
+ * P = Abar1^{-1}, B = P Abar2 (FP64, or FP32/BF16 for the mixed precisions).
  * Synchronizes the stream once to read the Cholesky pivot status.
  * Errors: INVALID_ARG, OOM, CUDA, NOT_SPD (handle not created), NONFINITE. */
 ils_status ils_setup(ils_handle* h, int64_t m, int64_t n, int64_t p, int64_t q,

@@ -48,7 +48,7 @@ class ils_options(ctypes.Structure):
         ("theta", ctypes.c_double),
         ("check_every", ctypes.c_int64),
         ("scd_sampler", ctypes.c_int32),
-        ("reserved1", ctypes.c_int32),
+        ("sweeps", ctypes.c_int32),
         ("seed", ctypes.c_uint64),
     ]
 

@@ -4,6 +4,7 @@
 // shaped to spread its multiply-adds evenly over all 152 SMs rather than to save
 // bandwidth.
 #include <algorithm>
+#include <cmath>
 
 #include "ils_internal.h"
 
@@ -113,20 +114,33 @@ __global__ void gemm_reduce_kernel(int64_t n1, int64_t n2, int splits, const dou
   }
 }
 
+// K-split of the GEMM grid.  The kernel is FP64-issue bound, so the split is chosen to
+// give every one of the SMs the same number of CTAs (ties: fewer slices), with at least
+// two CTAs per SM and at least 64 K rows per slice.
 void gemm_plan(int64_t K, int64_t n1, int64_t n2, bool sym, int* splits, int64_t* chunk) {
   const int64_t nb1 = (n1 + kTM - 1) / kTM, nb2 = (n2 + kTM - 1) / kTM;
   const int64_t tiles = sym ? nb1 * (nb1 + 1) / 2 : nb1 * nb2;
-  const int64_t target = 2 * (int64_t)num_sms();
-  int64_t s = (target + tiles - 1) / tiles;
-  const int64_t max_s = std::max<int64_t>(1, K / 256);
-  s = std::max<int64_t>(1, std::min(s, max_s));
-  int64_t ch = (K + s - 1) / s;
-  ch = ((ch + kTK - 1) / kTK) * kTK;
-  if (ch <= 0) ch = kTK;
-  s = (K + ch - 1) / ch;
-  if (s < 1) s = 1;
-  *splits = (int)s;
-  *chunk = ch;
+  const int64_t sms = num_sms();
+  const int64_t s_min = std::max<int64_t>(1, (2 * sms + tiles - 1) / tiles);
+  const int64_t s_max = std::max<int64_t>(1, std::min<int64_t>(32, K / 64));
+  int64_t best_s = 1, best_ch = ((K + kTK - 1) / kTK) * kTK;
+  double best_eff = -1.0;
+  for (int64_t s = std::min(s_min, s_max); s <= s_max; ++s) {
+    int64_t ch = ((K + s - 1) / s + kTK - 1) / kTK * kTK;
+    if (ch <= 0) ch = kTK;
+    const int64_t se = (K + ch - 1) / ch;
+    const int64_t ctas = tiles * se;
+    const double waves = (double)ctas / (double)sms;
+    const double eff = waves / std::ceil(waves);
+    if (eff > best_eff + 1e-9) {
+      best_eff = eff;
+      best_s = se;
+      best_ch = ch;
+    }
+    if (eff >= 0.98) break;
+  }
+  *splits = (int)best_s;
+  *chunk = best_ch;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -195,47 +209,67 @@ gemv_cols_kernel(int64_t n, int64_t k, const double* __restrict__ M, int64_t ldm
 }
 
 // ---------------------------------------------------------------------------------------
-// Blocked right-looking Cholesky, 32-wide panels.
+// Blocked right-looking Cholesky, 32-wide panels, for a batch of matrices at once
+// (blockIdx.z selects the matrix).  FP64 latency, not throughput, limits these kernels
+// at n ~ 500, so the diagonal block lives in one warp's registers (lane i holds row i)
+// and every division by a pivot becomes a multiplication by its reciprocal.
 // ---------------------------------------------------------------------------------------
 constexpr int kNB = 32;
 
+struct CholBatch {
+  double* M[2];       // matrices (ld n), lower triangles factored in place
+  double* inv_diag[2];  // 1 / L_ii, filled panel by panel
+  int32_t* status;
+};
+
 __device__ void set_status(int32_t* status, int32_t code) { atomicCAS(status, 0, code); }
 
-__global__ void __launch_bounds__(1024)
-potrf_diag_kernel(int64_t n, double* __restrict__ L, int64_t k0, int nb, int32_t* status) {
-  __shared__ double s[kNB][kNB + 1];
-  const int i = threadIdx.y, j = threadIdx.x;
-  s[i][j] = (i < nb && j < nb) ? L[(k0 + i) + (k0 + j) * n] : (i == j ? 1.0 : 0.0);
-  for (int c = 0; c < nb; ++c) {
-    __syncthreads();
-    if (i == c && j == c) {
-      double d = s[c][c];
-      if (!isfinite(d)) {
-        set_status(status, ILS_ERR_NONFINITE);
-        d = 1.0;
-      } else if (!(d > 0.0)) {
-        set_status(status, ILS_ERR_NOT_SPD);
-        d = 1.0;
-      }
-      s[c][c] = sqrt(d);
+__global__ void __launch_bounds__(32)
+potrf_diag_kernel(int64_t n, CholBatch cb, int64_t k0, int nb) {
+  double* L = cb.M[blockIdx.z];
+  double* inv = cb.inv_diag[blockIdx.z];
+  const int i = threadIdx.x;
+  double a[kNB];
+#pragma unroll
+  for (int j = 0; j < kNB; ++j)
+    a[j] = (i < nb && j < nb) ? L[(k0 + i) + (k0 + j) * n] : (i == j ? 1.0 : 0.0);
+#pragma unroll
+  for (int c = 0; c < kNB; ++c) {
+    double d = __shfl_sync(0xffffffffu, a[c], c);
+    if (!isfinite(d)) {
+      if (i == 0) set_status(cb.status, ILS_ERR_NONFINITE);
+      d = 1.0;
+    } else if (!(d > 0.0)) {
+      if (i == 0) set_status(cb.status, ILS_ERR_NOT_SPD);
+      d = 1.0;
     }
-    __syncthreads();
-    if (j == c && i > c) s[i][c] /= s[c][c];
-    __syncthreads();
-    if (j > c && i >= j) s[i][j] = fma(-s[i][c], s[j][c], s[i][j]);
+    const double sd = sqrt(d);
+    const double rs = 1.0 / sd;
+    a[c] = (i == c) ? sd : (i > c ? a[c] * rs : a[c]);
+    if (i == c && c < nb) inv[k0 + c] = rs;
+#pragma unroll
+    for (int j = c + 1; j < kNB; ++j) {
+      const double ljc = __shfl_sync(0xffffffffu, a[c], j);
+      if (i >= j) a[j] = fma(-a[c], ljc, a[j]);
+    }
   }
-  __syncthreads();
-  if (i < nb && j < nb && i >= j) L[(k0 + i) + (k0 + j) * n] = s[i][j];
+#pragma unroll
+  for (int j = 0; j < kNB; ++j)
+    if (i < nb && j < nb && i >= j) L[(k0 + i) + (k0 + j) * n] = a[j];
 }
 
 // Rows below the diagonal block: L21 = A21 L11^{-T}, one thread per row.
-__global__ void __launch_bounds__(128)
-trsm_panel_kernel(int64_t n, double* __restrict__ L, int64_t k0, int nb) {
+__global__ void __launch_bounds__(32)
+trsm_panel_kernel(int64_t n, CholBatch cb, int64_t k0, int nb) {
+  double* L = cb.M[blockIdx.z];
+  const double* inv = cb.inv_diag[blockIdx.z];
   __shared__ double l11[kNB][kNB + 1];
+  __shared__ double rinv[kNB];
   for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x) {
     const int a = e % kNB, b = e / kNB;
     l11[a][b] = (a < nb && b < nb && a >= b) ? L[(k0 + a) + (k0 + b) * n] : 0.0;
   }
+  if (threadIdx.x < kNB) rinv[threadIdx.x] = (threadIdx.x < nb) ? inv[k0 + threadIdx.x] : 0.0;
   __syncthreads();
   const int64_t i = k0 + nb + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -244,13 +278,10 @@ trsm_panel_kernel(int64_t n, double* __restrict__ L, int64_t k0, int nb) {
   for (int c = 0; c < kNB; ++c) x[c] = (c < nb) ? L[i + (k0 + c) * n] : 0.0;
 #pragma unroll
   for (int c = 0; c < kNB; ++c) {
-    if (c < nb) {
-      double v = x[c];
+    double v = x[c];
 #pragma unroll
-      for (int d = 0; d < kNB; ++d)
-        if (d < c) v = fma(-x[d], l11[c][d], v);
-      x[c] = v / l11[c][c];
-    }
+    for (int d = 0; d < c; ++d) v = fma(-x[d], l11[c][d], v);
+    x[c] = v * rinv[c];
   }
 #pragma unroll
   for (int c = 0; c < kNB; ++c)
@@ -259,7 +290,8 @@ trsm_panel_kernel(int64_t n, double* __restrict__ L, int64_t k0, int nb) {
 
 // Trailing update A22 -= L21 L21^T on lower 32 x 32 tiles.
 __global__ void __launch_bounds__(256)
-syrk_trailing_kernel(int64_t n, double* __restrict__ L, int64_t k0, int nb) {
+syrk_trailing_kernel(int64_t n, CholBatch cb, int64_t k0, int nb) {
+  double* L = cb.M[blockIdx.z];
   const int bi = blockIdx.x, bj = blockIdx.y;
   if (bi < bj) return;
   const int64_t k1 = k0 + nb;
@@ -288,43 +320,117 @@ syrk_trailing_kernel(int64_t n, double* __restrict__ L, int64_t k0, int nb) {
 }
 
 // ---------------------------------------------------------------------------------------
-// Triangular solves with many right-hand sides: one warp per right-hand side,
-// the vector kept in shared memory.
+// Triangular solves with many right-hand sides: one warp per right-hand side, the vector
+// kept in shared memory.  The blocked kernel stages each 32-column panel of L (rows i0..n-1)
+// in shared memory once per 32 substitution steps, so a step reads L from shared memory
+// instead of paying an L2 round trip; the simple kernel is the fallback when the panel does
+// not fit.
 // ---------------------------------------------------------------------------------------
 constexpr int kTrsmWarps = 4;
 
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T>
 __global__ void __launch_bounds__(32 * kTrsmWarps)
-trsm_kernel(int64_t n, int64_t k, const double* __restrict__ L, double* __restrict__ X, int64_t ldx,
-            int fwd, int bwd) {
-  extern __shared__ double smem_y[];
+trsm_kernel(int64_t n, int64_t k, const T* __restrict__ L, T* __restrict__ X, int64_t ldx, int fwd, int bwd) {
+  extern __shared__ __align__(16) unsigned char smem_raw_t[];
+  T* smem_y = reinterpret_cast<T*>(smem_raw_t);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t col = (int64_t)blockIdx.x * kTrsmWarps + w;
   if (col >= k) return;
-  double* y = smem_y + (size_t)w * n;
-  double* xc = X + col * ldx;
+  T* y = smem_y + (size_t)w * n;
+  T* xc = X + col * ldx;
   for (int64_t r = lane; r < n; r += 32) y[r] = xc[r];
   __syncwarp();
   if (fwd) {
     for (int64_t i = 0; i < n; ++i) {
-      const double yi = y[i] / L[i + i * n];
+      const T yi = y[i] / L[i + i * n];
       __syncwarp();
       if (lane == 0) y[i] = yi;
-      const double* li = L + i * n;
+      const T* li = L + i * n;
       for (int64_t r = i + 1 + lane; r < n; r += 32) y[r] = fma(-li[r], yi, y[r]);
       __syncwarp();
     }
   }
   if (bwd) {
     for (int64_t i = n - 1; i >= 0; --i) {
-      const double* li = L + i * n;
-      double s = 0.0;
+      const T* li = L + i * n;
+      T s = T(0);
       for (int64_t r = i + 1 + lane; r < n; r += 32) s = fma(li[r], y[r], s);
-      s = warp_sum(s);
+      s = warp_sum_t(s);
       if (lane == 0) y[i] = (y[i] - s) / li[i];
       __syncwarp();
     }
   }
   for (int64_t r = lane; r < n; r += 32) xc[r] = y[r];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32 * kTrsmWarps)
+trsm_blocked_kernel(int64_t n, int64_t k, const T* __restrict__ L, T* __restrict__ X, int64_t ldx, int fwd, int bwd) {
+  extern __shared__ __align__(16) unsigned char smem_raw_t[];
+  T* panel = reinterpret_cast<T*>(smem_raw_t);  // 32 columns x n rows (rows i0..n-1 used)
+  T* ys = panel + (size_t)32 * n;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t col = (int64_t)blockIdx.x * kTrsmWarps + w;
+  const bool valid = col < k;
+  T* y = ys + (size_t)w * n;
+  if (valid)
+    for (int64_t r = lane; r < n; r += 32) y[r] = X[r + col * ldx];
+  const int nblk = (int)((n + 31) / 32);
+  auto load_panel = [&](int64_t i0, int nb) {
+    __syncthreads();
+    const int64_t rows = n - i0;
+    for (int64_t e = threadIdx.x; e < rows * nb; e += blockDim.x) {
+      const int64_t r = i0 + e % rows;
+      const int c = (int)(e / rows);
+      panel[(size_t)c * n + r] = L[r + (i0 + c) * n];
+    }
+    __syncthreads();
+  };
+  if (fwd) {
+    for (int b = 0; b < nblk; ++b) {
+      const int64_t i0 = (int64_t)b * 32;
+      const int nb = (int)((n - i0) < 32 ? (n - i0) : 32);
+      load_panel(i0, nb);
+      if (valid) {
+        for (int c = 0; c < nb; ++c) {
+          const int64_t i = i0 + c;
+          const T* pc = panel + (size_t)c * n;
+          const T yi = y[i] / pc[i];
+          __syncwarp();
+          if (lane == 0) y[i] = yi;
+          for (int64_t r = i + 1 + lane; r < n; r += 32) y[r] = fma(-pc[r], yi, y[r]);
+          __syncwarp();
+        }
+      }
+    }
+  }
+  if (bwd) {
+    for (int b = nblk - 1; b >= 0; --b) {
+      const int64_t i0 = (int64_t)b * 32;
+      const int nb = (int)((n - i0) < 32 ? (n - i0) : 32);
+      load_panel(i0, nb);
+      if (valid) {
+        for (int c = nb - 1; c >= 0; --c) {
+          const int64_t i = i0 + c;
+          const T* pc = panel + (size_t)c * n;
+          T s = T(0);
+          for (int64_t r = i + 1 + lane; r < n; r += 32) s = fma(pc[r], y[r], s);
+          s = warp_sum_t(s);
+          if (lane == 0) y[i] = (y[i] - s) / pc[i];
+          __syncwarp();
+        }
+      }
+    }
+  }
+  if (valid)
+    for (int64_t r = lane; r < n; r += 32) X[r + col * ldx] = y[r];
 }
 
 __global__ void set_identity_kernel(int64_t n, double* M, int64_t ld) {
@@ -401,15 +507,24 @@ __global__ void __launch_bounds__(32 * kIterWarps) sp_iter_kernel(SpIterArgs a) 
     double ab[kMaxRhsPerPass], ah[kMaxRhsPerPass];
 #pragma unroll
     for (int c = 0; c < kMaxRhsPerPass; ++c) ab[c] = ah[c] = 0.0;
-    for (int64_t j = lane; j < n; j += 32) {
-      const double bv = brow[j], hv = hrow[j];
+    if (a.mode != 2) {
+      for (int64_t j = lane; j < n; j += 32) {
+        const double bv = brow[j], hv = hrow[j];
 #pragma unroll
-      for (int c = 0; c < kMaxRhsPerPass; ++c) {
-        if (c < k) {
-          const double xv = x[j + c * n];
-          ab[c] = fma(bv, xv, ab[c]);
-          ah[c] = fma(hv, xv, ah[c]);
+        for (int c = 0; c < kMaxRhsPerPass; ++c) {
+          if (c < k) {
+            const double xv = x[j + c * n];
+            ab[c] = fma(bv, xv, ab[c]);
+            ah[c] = fma(hv, xv, ah[c]);
+          }
         }
+      }
+    } else {
+      for (int64_t j = lane; j < n; j += 32) {
+        const double hv = hrow[j];
+#pragma unroll
+        for (int c = 0; c < kMaxRhsPerPass; ++c)
+          if (c < k) ah[c] = fma(hv, x[j + c * n], ah[c]);
       }
     }
 #pragma unroll
@@ -418,11 +533,12 @@ __global__ void __launch_bounds__(32 * kIterWarps) sp_iter_kernel(SpIterArgs a) 
       const double sh = warp_sum(ah[c]);
       if (lane == 0 && c < k) {
         if (done_c[c]) {
-          xn[i + c * n] = x[i + c * n];
+          if (a.mode != 2) xn[i + c * n] = x[i + c * n];
         } else {
-          if (a.mode == 0) xn[i + c * n] = sb + a.cvec[i + c * n];
-          else a.bhat_out[i + c * n] = sb + a.cvec[i + c * n];
           const double r = a.bbar[i + c * n] - sh;
+          if (a.mode == 0) xn[i + c * n] = sb + a.cvec[i + c * n];
+          else if (a.mode == 1) a.bhat_out[i + c * n] = sb + a.cvec[i + c * n];
+          else a.bhat_out[i + c * n] = r;
           rpart[c] = fma(r, r, rpart[c]);
         }
       }
@@ -474,13 +590,13 @@ __global__ void __launch_bounds__(32 * kIterWarps) sp_iter_kernel(SpIterArgs a) 
     if (all) {
       st->done = 1;  // the answer of every column is in buffer `cur`
     } else {
-      st->cur = cur ^ 1;
+      if (a.mode != 2) st->cur = cur ^ 1;  // mode 2 updates x in place
       st->iters = it + 1;
     }
     st->counter = 0u;
   }
   __syncthreads();
-  if (!all_done) {
+  if (!all_done && a.mode != 2) {
     // Columns that finished now keep x_k: copy it over the x_{k+1} just written.
     for (int c = 0; c < k; ++c) {
       if (!newly_done[c]) continue;
@@ -587,21 +703,29 @@ cudaError_t gemv_cols_f64(int64_t n, int64_t k, const double* M, int64_t ldm, co
   return cudaGetLastError();
 }
 
-cudaError_t cholesky_f64(int64_t n, double* L, int32_t* status, cudaStream_t s) {
+cudaError_t cholesky_f64_batch(int64_t n, int count, double* const* mats, double* const* inv_diag, int32_t* status,
+                               cudaStream_t s) {
+  if (count < 1 || count > 2) return cudaErrorInvalidValue;
+  CholBatch cb;
+  for (int i = 0; i < 2; ++i) {
+    cb.M[i] = mats[i < count ? i : 0];
+    cb.inv_diag[i] = inv_diag[i < count ? i : 0];
+  }
+  cb.status = status;
   for (int64_t k0 = 0; k0 < n; k0 += kNB) {
     const int nb = (int)std::min<int64_t>(kNB, n - k0);
-    potrf_diag_kernel<<<1, dim3(kNB, kNB), 0, s>>>(n, L, k0, nb, status);
+    potrf_diag_kernel<<<dim3(1, 1, count), 32, 0, s>>>(n, cb, k0, nb);
     note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int64_t rest = n - k0 - nb;
     if (rest <= 0) break;
-    trsm_panel_kernel<<<(unsigned)((rest + 127) / 128), 128, 0, s>>>(n, L, k0, nb);
+    trsm_panel_kernel<<<dim3((unsigned)((rest + 31) / 32), 1, count), 32, 0, s>>>(n, cb, k0, nb);
     note_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const unsigned nt = (unsigned)((rest + kNB - 1) / kNB);
-    syrk_trailing_kernel<<<dim3(nt, nt), 256, 0, s>>>(n, L, k0, nb);
+    syrk_trailing_kernel<<<dim3(nt, nt, count), 256, 0, s>>>(n, cb, k0, nb);
     note_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -609,18 +733,39 @@ cudaError_t cholesky_f64(int64_t n, double* L, int32_t* status, cudaStream_t s) 
   return cudaSuccess;
 }
 
-cudaError_t trsm_lower_f64(int64_t n, int64_t k, const double* L, double* X, int64_t ldx, bool forward,
-                           bool backward, cudaStream_t s) {
+template <typename T>
+cudaError_t trsm_lower_t(int64_t n, int64_t k, const T* L, T* X, int64_t ldx, bool forward, bool backward,
+                         cudaStream_t s) {
   if (n <= 0 || k <= 0) return cudaSuccess;
-  const size_t smem = sizeof(double) * (size_t)n * kTrsmWarps;
+  const unsigned grid = (unsigned)((k + kTrsmWarps - 1) / kTrsmWarps);
+  const size_t blocked = sizeof(T) * (size_t)n * (32 + kTrsmWarps);
+  if (blocked <= 200 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(trsm_blocked_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)std::max<size_t>(blocked, 48 * 1024));
+    if (e != cudaSuccess) return e;
+    trsm_blocked_kernel<T><<<grid, 32 * kTrsmWarps, blocked, s>>>(n, k, L, X, ldx, forward ? 1 : 0,
+                                                                  backward ? 1 : 0);
+    note_launch();
+    return cudaGetLastError();
+  }
+  const size_t smem = sizeof(T) * (size_t)n * kTrsmWarps;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(trsm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(trsm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  trsm_kernel<<<(unsigned)((k + kTrsmWarps - 1) / kTrsmWarps), 32 * kTrsmWarps, smem, s>>>(
-      n, k, L, X, ldx, forward ? 1 : 0, backward ? 1 : 0);
+  trsm_kernel<T><<<grid, 32 * kTrsmWarps, smem, s>>>(n, k, L, X, ldx, forward ? 1 : 0, backward ? 1 : 0);
   note_launch();
   return cudaGetLastError();
+}
+
+cudaError_t trsm_lower_f64(int64_t n, int64_t k, const double* L, double* X, int64_t ldx, bool forward,
+                           bool backward, cudaStream_t s) {
+  return trsm_lower_t<double>(n, k, L, X, ldx, forward, backward, s);
+}
+
+cudaError_t trsm_lower_f32(int64_t n, int64_t k, const float* L, float* X, int64_t ldx, bool forward,
+                           bool backward, cudaStream_t s) {
+  return trsm_lower_t<float>(n, k, L, X, ldx, forward, backward, s);
 }
 
 cudaError_t set_identity_f64(int64_t n, double* M, int64_t ld, cudaStream_t s) {

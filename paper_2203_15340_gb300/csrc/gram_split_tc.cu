@@ -1,0 +1,479 @@
+// FP64-accurate Gram matrix A^T A on the tcgen05 tensor cores.
+//
+// GB300 issues FP64 fused multiply-adds at about 2 per clock per SM, while its BF16
+// tensor cores are three orders of magnitude faster.  The Gram products of Alg. 1 step 2
+// (Abar1 = A_1^T A_1) and step 3 (Abar2 = A_2^T A_2) are therefore formed from exact
+// integer slice products:
+//
+//   1. Column j of A is scaled by 2^-e_j so that its entries lie in (-1, 1).
+//   2. Each scaled entry is split into S signed digits of beta bits by repeated rounding
+//      to nearest, a = sum_{t=1..S} 2^{-beta t} d_t with integers |d_1| <= 2^beta and
+//      |d_t| <= 2^(beta-1) after; every digit is exact in BF16.  Rounding (not
+//      truncation) leaves the digits' signs independent of the entry's sign, so the split
+//      and the omitted pairs add unbiased errors, and the error of the split is at most
+//      2^{-beta S - 1} times the column scale.
+//   3. For every ordered pair (t, u) with t + u <= S + 1 the tensor cores form
+//      D_t^T D_u with FP32 accumulation.  All partial sums are integers below
+//      K_chunk 2^(2 beta) < 2^24, so the FP32 accumulation is exact.
+//   4. The epilogue scales each exact product by 2^{e_i + e_j - beta (t + u)} (an exponent
+//      shift on the bit pattern) and a reduction adds the products of a tile in FP64 in a
+//      fixed order (deterministic).
+//
+// The tcgen05 kernel is warp-specialised: warp 0 issues TMA loads of 128 x 64 BF16 tiles
+// (128B swizzle) into a 6-stage shared-memory ring, warp 1 issues 128x128x16 MMAs into a
+// TMEM accumulator, warps 2-5 drain TMEM.  Every mbarrier wait is bounded; on a timeout
+// the kernel records an error flag, stops issuing work, frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "ils_internal.h"
+
+namespace ils {
+namespace {
+
+constexpr int kBeta = 5;        // bits per slice
+constexpr int kSlices = 10;     // 50 bits below each column's scale
+constexpr int kBM = 128;        // output tile rows (columns of D_t)
+constexpr int kBN = 128;        // output tile cols (columns of D_u)
+constexpr int kBK = 64;         // K per stage: 64 BF16 = one 128-byte swizzle row
+constexpr int kStages = 6;
+constexpr int kKChunk = 16384;  // K rows per work item: 16384 * 32^2 = 2^24 (exact FP32 sums)
+constexpr int kThreads = 192;   // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr uint32_t kTileBytes = kBM * kBK * 2;  // 16 KB per operand tile
+constexpr uint64_t kWaitNs = 4000000000ull;  // bound on any mbarrier wait (4 s)
+
+// ------------------------------- device helpers ----------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// Poll an mbarrier phase for at most kWaitNs of wall time.  Returns false on timeout.
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t addr = smem_u32(bar);
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (global_ns() - t0 > kWaitNs) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
+                                            int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand tile in the 128-byte swizzle
+// layout: 8-row x 128-byte atoms stacked every 1024 bytes (stride byte offset), version 1.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);      // start address
+  d |= (uint64_t)1 << 16;                        // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;              // stride byte offset
+  d |= (uint64_t)1 << 46;                        // descriptor version
+  d |= (uint64_t)2 << 61;                        // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: kind::f16 with BF16 A/B, FP32 D, both K-major, M = 128, N = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBN >> 3) << 17) |
+                            ((uint32_t)(kBM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+        "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// (double)x * 2^sc for an FP32 x holding an exact integer, built from x's bit pattern with
+// integer operations (sign, rebased exponent, widened significand).
+__device__ __forceinline__ double scaled_f32_to_f64(uint32_t xb, int sc) {
+  if ((xb & 0x7FFFFFFFu) == 0u) return 0.0;
+  const unsigned long long sign = (unsigned long long)(xb >> 31) << 63;
+  const int ef = (int)((xb >> 23) & 0xFF);  // integers >= 1 are normal floats
+  const unsigned long long exp64 = (unsigned long long)(ef - 127 + 1023 + sc) << 52;
+  const unsigned long long man = (unsigned long long)(xb & 0x7FFFFFu) << 29;
+  return __longlong_as_double((long long)(sign | exp64 | man));
+}
+
+struct SplitParams {
+  int n;            // Gram order
+  int K;            // rows of A (reduction length)
+  int n_tiles;      // ceil(n / 128)
+  int n_pairs;      // ordered slice pairs (t, u) with t + u <= S + 1
+  int n_kchunks;
+  const int* exps;  // per-column exponents e_j (device)
+  double* partial;  // [item][128][128] FP64 scaled products
+  int32_t* err;     // device error flag
+};
+
+// Work item -> (K chunk, upper tile pair, slice pair).  Items of one K chunk run together
+// so the chunk's slices stay in L2; the partial-product slot keeps the items of a tile
+// contiguous for the reduction: slot = (tile * n_pairs + pair) * n_kchunks + kc.
+__device__ __forceinline__ void decode_item(int item, const SplitParams& P, int* bi, int* bj, int* t, int* u,
+                                            int* kc, int* slot) {
+  const int n_upper = P.n_tiles * (P.n_tiles + 1) / 2;
+  const int per_chunk = n_upper * P.n_pairs;
+  *kc = item / per_chunk;
+  const int rest = item % per_chunk;
+  int tile = rest / P.n_pairs;
+  const int pair = rest % P.n_pairs;
+  *slot = (tile * P.n_pairs + pair) * P.n_kchunks + *kc;
+  // upper tile pairs (bi <= bj) in row-major order
+  int r = 0;
+  while (tile >= P.n_tiles - r) {
+    tile -= P.n_tiles - r;
+    ++r;
+  }
+  *bi = r;
+  *bj = r + tile;
+  // ordered pairs with t + u <= S + 1 (1-based), enumerated by t then u
+  int p = pair, tt = 1;
+  while (p >= kSlices + 1 - tt) {
+    p -= kSlices + 1 - tt;
+    ++tt;
+  }
+  *t = tt;
+  *u = 1 + p;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+gram_split_mma_kernel(const __grid_constant__ CUtensorMap tmap, SplitParams P) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* tiles = smem;  // kStages x (A tile, B tile)
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * 2 * kTileBytes);
+  uint64_t* empty = full + kStages;
+  uint64_t* acc_full = empty + kStages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_full + 1);
+  __shared__ int s_abort;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int bi, bj, t, u, kc, slot;
+  decode_item(blockIdx.x, P, &bi, &bj, &t, &u, &kc, &slot);
+  const int k_begin = kc * kKChunk;
+  const int k_end = min(P.K, k_begin + kKChunk);
+  const int nk = (k_end - k_begin + kBK - 1) / kBK;
+
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(acc_full, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(kBN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem_acc = *tmem_slot;
+
+  int issued = 0;  // stages handed to TMA by the producer
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer ----------------
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % kStages;
+      const uint32_t ph = (uint32_t)(kb / kStages) & 1u;
+      if (!mbar_wait(&empty[s], ph ^ 1u)) {
+        atomicExch(P.err, 1);
+        s_abort = 1;
+        break;
+      }
+      if (*((volatile int*)&s_abort)) break;
+      uint8_t* a_tile = tiles + (size_t)s * 2 * kTileBytes;
+      uint8_t* b_tile = a_tile + kTileBytes;
+      mbar_expect_tx(&full[s], 2 * kTileBytes);
+      const int k = k_begin + kb * kBK;
+      tma_load_3d(a_tile, &tmap, &full[s], k, bi * kBM, t - 1);
+      tma_load_3d(b_tile, &tmap, &full[s], k, bj * kBN, u - 1);
+      ++issued;
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer ----------------
+    bool ok = true;
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % kStages;
+      const uint32_t ph = (uint32_t)(kb / kStages) & 1u;
+      if (!mbar_wait(&full[s], ph)) {
+        atomicExch(P.err, 1);
+        s_abort = 1;
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a_addr = smem_u32(tiles + (size_t)s * 2 * kTileBytes);
+      const uint32_t b_addr = a_addr + kTileBytes;
+#pragma unroll
+      for (int kk = 0; kk < kBK / 16; ++kk) {
+        mma_bf16(tmem_acc, smem_desc_sw128(a_addr + kk * 32), smem_desc_sw128(b_addr + kk * 32),
+                 (kb > 0 || kk > 0) ? 1u : 0u);
+      }
+      mma_commit(&empty[s]);  // frees the stage once these MMAs have read it
+    }
+    (void)ok;
+    mma_commit(acc_full);  // arrives when every MMA issued above has completed
+  } else if (warp >= 2) {
+    // ---------------- epilogue: TMEM -> scaled FP64 partial ----------------
+    const bool ok = mbar_wait(acc_full, 0);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int q = warp & 3;  // this warp may read TMEM lanes 32q .. 32q+31
+    const int row = q * 32 + lane;
+    const int gi = bi * kBM + row;
+    double* out = P.partial + (size_t)slot * kBM * kBN;  // column-major 128 x 128 tile
+    if (!ok) {
+      atomicExch(P.err, 1);
+    } else if (!*((volatile int*)&s_abort)) {
+      const int ei = gi < P.n ? P.exps[gi] : 0;
+#pragma unroll 1
+      for (int c0 = 0; c0 < kBN; c0 += 32) {
+        uint32_t v[32];
+        tmem_ld_32x32b_x32(tmem_acc + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          const int gj = bj * kBN + c0 + c;
+          const int ej = gj < P.n ? P.exps[gj] : 0;
+          out[(size_t)(c0 + c) * kBM + row] = scaled_f32_to_f64(v[c], ei + ej - kBeta * (t + u));
+        }
+      }
+    }
+  }
+  // Producer: on an abort, wait (bounded) for the copies it issued before leaving.
+  if (warp == 0 && lane == 0 && *((volatile int*)&s_abort)) {
+    for (int kb = 0; kb < issued; ++kb) mbar_wait(&full[kb % kStages], (uint32_t)(kb / kStages) & 1u);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_acc), "r"(kBN));
+  }
+}
+
+// Per-column exponent e_j with max_r |A(r,j)| < 2^e_j (0 for a zero column), read from the
+// exponent fields of the FP64 bit patterns (integer work only).
+__global__ void column_exponent_kernel(int K, int n, const double* __restrict__ A, int64_t lda, int* __restrict__ exps) {
+  const int j = blockIdx.x;
+  int mx = 0;
+  for (int r = threadIdx.x; r < K; r += blockDim.x) {
+    const long long bits = __double_as_longlong(A[r + (int64_t)j * lda]);
+    mx = max(mx, (int)((bits >> 52) & 0x7FF));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  __shared__ int red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int m = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = max(m, red[w]);
+    // A normal value with exponent field f lies in [2^(f-1023), 2^(f-1022)).
+    exps[j] = (m == 0 || m == 0x7FF) ? 0 : m - 1022;
+  }
+}
+
+// Digits of column j: D[t][j][r] (K-contiguous, leading dimension ldk).  The scaled entry
+// a 2^-e_j is rounded to the 50-bit fixed-point integer V = rint(a 2^(50 - e_j)) straight
+// from its bit pattern, and V is written in balanced base 32: five-bit digits in
+// [-16, 15] from the least significant end, the top digit taking the rest (|d_1| <= 32).
+// This equals the digit expansion by repeated rounding to nearest, using integer work
+// only (GB300's FP64 pipe is the scarce unit).
+__global__ void split_kernel(int K, int n, const double* __restrict__ A, int64_t lda, const int* __restrict__ exps,
+                             __nv_bfloat16* __restrict__ D, int64_t ldk, int32_t* err) {
+  const int64_t total = (int64_t)K * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e % K), j = (int)(e / K);
+    const long long bits = __double_as_longlong(A[r + (int64_t)j * lda]);
+    const int f = (int)((bits >> 52) & 0x7FF);
+    long long V = 0;
+    if (f == 0x7FF) {
+      atomicExch(err, 2);
+    } else if (f != 0) {  // subnormals are below 2^-1022 and round to 0 at 50 bits
+      const unsigned long long mant = (unsigned long long)(bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+      // value = mant 2^(f - 1075); V = mant 2^(f - 1075 + kBeta*kSlices - e_j) with a right shift > 0
+      const int sh = 1075 - f - kBeta * kSlices + exps[j];
+      if (sh < 64) {
+        const unsigned long long half = (sh > 0) ? (1ull << (sh - 1)) : 0ull;
+        const unsigned long long mag = (sh > 0) ? ((mant + half) >> sh) : (mant << (-sh));
+        V = (bits < 0) ? -(long long)mag : (long long)mag;
+      }
+    }
+#pragma unroll
+    for (int t = kSlices - 1; t >= 1; --t) {
+      int d = (int)(V & 31);
+      if (d >= 16) d -= 32;
+      V = (V - d) >> kBeta;
+      D[((int64_t)t * n + j) * ldk + r] = __int2bfloat16_rn(d);
+    }
+    D[(int64_t)j * ldk + r] = __int2bfloat16_rn((int)V);  // top digit, |V| <= 32
+  }
+}
+
+// C(i,j) for the upper tiles: sum of the tile's items in a fixed order, mirrored.
+__global__ void split_reduce_kernel(SplitParams P, double* __restrict__ C, int64_t ldc) {
+  const int items_per_tile = P.n_pairs * P.n_kchunks;
+  const int n_upper = P.n_tiles * (P.n_tiles + 1) / 2;
+  const int64_t total = (int64_t)n_upper * kBM * kBN;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int tile = (int)(e / (kBM * kBN));
+    const int local = (int)(e % (kBM * kBN));
+    const int row = local % kBM, col = local / kBM;
+    int r = 0;
+    int tt = tile;
+    while (tt >= P.n_tiles - r) {
+      tt -= P.n_tiles - r;
+      ++r;
+    }
+    const int bi = r, bj = r + tt;
+    const int gi = bi * kBM + row, gj = bj * kBN + col;
+    if (gi >= P.n || gj >= P.n || (bi == bj && gi > gj)) continue;
+    const double* base = P.partial + (size_t)tile * items_per_tile * kBM * kBN + local;
+    double s = 0.0;
+    for (int it = 0; it < items_per_tile; ++it) s += base[(size_t)it * kBM * kBN];
+    C[gi + (int64_t)gj * ldc] = s;
+    C[gj + (int64_t)gi * ldc] = s;
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+int num_pairs() {
+  int c = 0;
+  for (int t = 1; t <= kSlices; ++t) c += kSlices + 1 - t;
+  return c;
+}
+
+size_t smem_bytes() { return 1024 + (size_t)kStages * 2 * kTileBytes + (2 * kStages + 2) * sizeof(uint64_t) + 16; }
+
+}  // namespace
+
+GramSplitWork gram_split_work(int64_t K, int64_t n) {
+  GramSplitWork w;
+  const int64_t ldk = ((K + 7) / 8) * 8;
+  const int64_t n_tiles = (n + kBM - 1) / kBM;
+  const int64_t n_upper = n_tiles * (n_tiles + 1) / 2;
+  const int64_t n_kchunks = std::max<int64_t>(1, (K + kKChunk - 1) / kKChunk);
+  w.slice_elems = (size_t)kSlices * (size_t)n * (size_t)ldk;
+  w.partial_elems = (size_t)n_upper * num_pairs() * n_kchunks * kBM * kBN;
+  w.exps = (size_t)n;
+  return w;
+}
+
+cudaError_t gram_split_tc(int64_t K, int64_t n, const double* A, int64_t lda, double* C, int64_t ldc, void* slices,
+                          double* partial, int* exps, int32_t* err, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (K <= 0) return cudaMemset2DAsync(C, sizeof(double) * ldc, 0, sizeof(double) * n, n, s);
+  if (K > (int64_t)1 << 30 || n > (int64_t)1 << 20) return cudaErrorInvalidValue;
+  PFN_cuTensorMapEncodeTiled_v12000 encode = get_encode_fn();
+  if (!encode) return cudaErrorNotSupported;
+  const int64_t ldk = ((K + 7) / 8) * 8;
+  __nv_bfloat16* D = static_cast<__nv_bfloat16*>(slices);
+  column_exponent_kernel<<<(unsigned)n, 256, 0, s>>>((int)K, (int)n, A, lda, exps);
+  note_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (ldk != K) {  // zero the padding rows so TMA never reads stale values inside ldk
+    e = cudaMemsetAsync(D, 0, sizeof(__nv_bfloat16) * (size_t)kSlices * n * ldk, s);
+    if (e != cudaSuccess) return e;
+  }
+  split_kernel<<<1024, 256, 0, s>>>((int)K, (int)n, A, lda, exps, D, ldk, err);
+  note_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+
+  CUtensorMap map;
+  const cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)n, (cuuint64_t)kSlices};
+  const cuuint64_t strides[2] = {(cuuint64_t)ldk * 2, (cuuint64_t)ldk * 2 * (cuuint64_t)n};
+  const cuuint32_t box[3] = {kBK, kBM, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, D, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+      CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+
+  SplitParams P;
+  P.n = (int)n;
+  P.K = (int)K;
+  P.n_tiles = (int)((n + kBM - 1) / kBM);
+  P.n_pairs = num_pairs();
+  P.n_kchunks = (int)std::max<int64_t>(1, (K + kKChunk - 1) / kKChunk);
+  P.exps = exps;
+  P.partial = partial;
+  P.err = err;
+  const int n_upper = P.n_tiles * (P.n_tiles + 1) / 2;
+  const int items = n_upper * P.n_pairs * P.n_kchunks;
+  const size_t smem = smem_bytes();
+  e = cudaFuncSetAttribute(gram_split_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  gram_split_mma_kernel<<<items, kThreads, smem, s>>>(map, P);
+  note_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  split_reduce_kernel<<<1024, 256, 0, s>>>(P, C, ldc);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace ils

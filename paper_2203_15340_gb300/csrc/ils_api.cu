@@ -39,10 +39,26 @@ struct ils_handle_s {
   double* bhat = nullptr;        // n x kMaxRhsPerPass (randomized methods)
   double* col_target2 = nullptr; // kMaxRhsPerPass
   int64_t* col_inner = nullptr;  // kMaxRhsPerPass
+  double* inv_diag = nullptr;    // 2n: reciprocal Cholesky pivots (Abar1, H)
   double* norms2 = nullptr;      // n: ||A_1(:,j)||^2
   double* cum = nullptr;         // n: running sum of norms2
   double* vec_scratch = nullptr; // RK-RGS w and e when they do not fit in shared memory
   bool vec_in_smem = true;
+  // mixed precision (options.precision != ILS_FP64)
+  float* L32 = nullptr;
+  float* P32 = nullptr;
+  float* G2_32 = nullptr;
+  float* Bt32 = nullptr;
+  void* Bt16 = nullptr;
+  float* r32 = nullptr;
+  float* c32 = nullptr;
+  float* d32a = nullptr;
+  float* d32b = nullptr;
+  // split tensor-core Gram (options.gram == ILS_GRAM_SPLIT)
+  void* gs_slices = nullptr;
+  double* gs_partial = nullptr;
+  int* gs_exps = nullptr;
+  int32_t* gs_err = nullptr;
   SolveState* st = nullptr;
   int32_t* dstatus = nullptr;
   // pinned host mirrors
@@ -134,11 +150,31 @@ void carve(ils_handle h, Carver& c, size_t work_elems) {
   h->bhat = c.take<double>(nk);
   h->col_target2 = c.take<double>(kMaxRhsPerPass);
   h->col_inner = c.take<int64_t>(kMaxRhsPerPass);
+  h->inv_diag = c.take<double>(2 * (size_t)h->n);
   h->norms2 = c.take<double>((size_t)h->n);
   h->cum = c.take<double>((size_t)h->n);
   h->vec_in_smem = rkrgs_vec_fits(h->n, h->p);
   const bool need_scratch = h->opt.method == ILS_SP_RK_RGS && !h->vec_in_smem;
   h->vec_scratch = c.take<double>(need_scratch ? (size_t)kMaxRhsPerPass * 2 * (size_t)h->p : 1);
+  if (h->opt.precision != ILS_FP64) {
+    const size_t nn = (size_t)h->n * (size_t)h->n;
+    h->L32 = c.take<float>(nn);
+    h->P32 = c.take<float>(nn);
+    h->G2_32 = c.take<float>(nn);
+    h->Bt32 = c.take<float>(nn);
+    h->Bt16 = c.take<uint16_t>(h->opt.precision == ILS_BF16_REFINE ? nn : 1);
+    h->r32 = c.take<float>(nk);
+    h->c32 = c.take<float>(nk);
+    h->d32a = c.take<float>(nk);
+    h->d32b = c.take<float>(nk);
+  }
+  if (h->opt.gram == ILS_GRAM_SPLIT) {
+    GramSplitWork w1 = gram_split_work(h->p, h->n), w2 = gram_split_work(h->q, h->n);
+    h->gs_slices = c.take<uint16_t>(std::max(w1.slice_elems, w2.slice_elems));
+    h->gs_partial = c.take<double>(std::max(w1.partial_elems, w2.partial_elems));
+    h->gs_exps = c.take<int>((size_t)h->n);
+    h->gs_err = c.take<int32_t>(1);
+  }
   h->st = c.take<SolveState>(1);
   h->dstatus = c.take<int32_t>(1);
 }
@@ -156,6 +192,7 @@ ils_status validate_options(const ils_options* o) {
   if (o->method < ILS_SP || o->method > ILS_SP_SCD) return ILS_ERR_INVALID_ARG;
   if (o->precision < ILS_FP64 || o->precision > ILS_BF16_REFINE) return ILS_ERR_INVALID_ARG;
   if (o->max_outer < 0 || o->max_inner < 0 || o->check_every < 0) return ILS_ERR_INVALID_ARG;
+  if (o->gram != ILS_GRAM_FP64 && o->gram != ILS_GRAM_SPLIT) return ILS_ERR_INVALID_ARG;
   if (!(o->theta > 0.0)) return ILS_ERR_INVALID_ARG;
   return ILS_OK;
 }
@@ -193,28 +230,50 @@ ils_status compute_setup(ils_handle h) {
   const int64_t m = h->m, n = h->n, p = h->p, q = h->q;
   ILS_CK(mark(h, 1));
   // Abar1 = A_1^T A_1, Abar2 = A_2^T A_2 (Alg. 1 steps 2-3; Alg. 2 step 2; Alg. 5 step 2).
-  ILS_CK(gemm_tn_f64(p, n, n, h->A, m, h->A, m, p, h->G1, n, true, false, h->work, s));
+  if (h->opt.gram == ILS_GRAM_SPLIT) {
+    ILS_CK(cudaMemsetAsync(h->gs_err, 0, sizeof(int32_t), s));
+    ILS_CK(gram_split_tc(p, n, h->A, m, h->G1, n, h->gs_slices, h->gs_partial, h->gs_exps, h->gs_err, s));
+  } else {
+    ILS_CK(gemm_tn_f64(p, n, n, h->A, m, h->A, m, p, h->G1, n, true, false, h->work, s));
+  }
   ILS_CK(mark(h, 2));
   ILS_CK(column_cumsum_f64(n, h->G1, h->norms2, h->cum, s));
-  ILS_CK(gemm_tn_f64(q, n, n, h->A + p, m, h->A + p, m, q, h->G2, n, true, false, h->work, s));
+  if (h->opt.gram == ILS_GRAM_SPLIT) {
+    ILS_CK(gram_split_tc(q, n, h->A + p, m, h->G2, n, h->gs_slices, h->gs_partial, h->gs_exps, h->gs_err, s));
+  } else {
+    ILS_CK(gemm_tn_f64(q, n, n, h->A + p, m, h->A + p, m, q, h->G2, n, true, false, h->work, s));
+  }
   ILS_CK(mark(h, 3));
   ILS_CK(axpby_mat_f64(n, 1.0, h->G1, -1.0, h->G2, h->H, s));
   // Cholesky of Abar1; the explicit inverse of Alg. 1 step 2 is formed from it.
   ILS_CK(cudaMemcpyAsync(h->L, h->G1, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, s));
   ILS_CK(cudaMemsetAsync(h->dstatus, 0, sizeof(int32_t), s));
-  ILS_CK(cholesky_f64(n, h->L, h->dstatus, s));
   // Condition (1.3): H = A^T J A must be SPD as well (Abar1 SPD alone does not give
-  // rho(B) < 1).  Its Cholesky runs in the P buffer, which is overwritten below.
+  // rho(B) < 1).  Its Cholesky runs in the P buffer, which is overwritten below; both
+  // factorizations share each panel's launches.
   ILS_CK(cudaMemcpyAsync(h->P, h->H, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, s));
-  ILS_CK(cholesky_f64(n, h->P, h->dstatus, s));
+  {
+    double* mats[2] = {h->L, h->P};
+    double* invd[2] = {h->inv_diag, h->inv_diag + n};
+    ILS_CK(cholesky_f64_batch(n, 2, mats, invd, h->dstatus, s));
+  }
   ILS_CK(mark(h, 4));
   ILS_CK(cudaMemcpyAsync(h->h_status, h->dstatus, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  if (h->opt.gram == ILS_GRAM_SPLIT)
+    ILS_CK(cudaMemcpyAsync(h->h_status + 1, h->gs_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   ILS_CK(cudaStreamSynchronize(s));
+  if (h->opt.gram == ILS_GRAM_SPLIT && h->h_status[1] != 0)
+    return h->h_status[1] == 2 ? ILS_ERR_NONFINITE : ILS_ERR_TIMEOUT;
   if (*h->h_status != 0) return (ils_status)*h->h_status;
-  // P = L^{-T} L^{-1} (Alg. 1 step 2), B^T = (P Abar2)^T = Abar2 P (Alg. 1 step 3).
-  ILS_CK(set_identity_f64(n, h->P, n, s));
-  ILS_CK(trsm_lower_f64(n, n, h->L, h->P, n, true, true, s));
-  ILS_CK(gemm_tn_f64(n, n, n, h->G2, n, h->P, n, n, h->Bt, n, false, false, h->work, s));
+  if (h->opt.precision != ILS_FP64) {
+    // Mixed precision: P and B for the correction sweeps in FP32 (B also in BF16).
+    ILS_CK(mixed_setup(n, h->L, h->G2, h->opt.precision, h->L32, h->P32, h->G2_32, h->Bt32, h->Bt16, s));
+  } else {
+    // P = L^{-T} L^{-1} (Alg. 1 step 2), B^T = (P Abar2)^T = Abar2 P (Alg. 1 step 3).
+    ILS_CK(set_identity_f64(n, h->P, n, s));
+    ILS_CK(trsm_lower_f64(n, n, h->L, h->P, n, true, true, s));
+    ILS_CK(gemm_tn_f64(n, n, n, h->G2, n, h->P, n, n, h->Bt, n, false, false, h->work, s));
+  }
   ILS_CK(mark(h, 5));
   return ILS_OK;
 }
@@ -237,7 +296,7 @@ ils_status sp_pass(ils_handle h, int64_t c0, int64_t kk, const double* B, int64_
   // bbar = A^T J b (Alg. 1 step 4), c = P bbar.
   ILS_CK(rhs_bar_f64(m, n, p, kk, h->A, m, B, ldb, h->bbar, n, s));
   ILS_CK(sq_norms_cols_f64(n, kk, h->bbar, n, h->bnorm2, s));
-  ILS_CK(gemv_cols_f64(n, kk, h->P, n, h->bbar, n, h->cvec, n, s));
+  if (h->opt.precision == ILS_FP64) ILS_CK(gemv_cols_f64(n, kk, h->P, n, h->bbar, n, h->cvec, n, s));
   if (x0_zero) {
     ILS_CK(cudaMemsetAsync(h->X0, 0, sizeof(double) * n * kk, s));
   } else {
@@ -250,7 +309,8 @@ ils_status sp_pass(ils_handle h, int64_t c0, int64_t kk, const double* B, int64_
   SpIterArgs a;
   a.n = n;
   a.k = kk;
-  a.mode = method == ILS_SP ? 0 : 1;
+  const bool mixed = h->opt.precision != ILS_FP64;
+  a.mode = mixed ? 2 : (method == ILS_SP ? 0 : 1);
   a.pad = 0;
   a.Bt = method == ILS_SP ? h->Bt : h->G2;
   a.H = h->H;
@@ -293,14 +353,32 @@ ils_status sp_pass(ils_handle h, int64_t c0, int64_t kk, const double* B, int64_
   ra.vec_in_smem = h->vec_in_smem ? 1 : 0;
   ra.pad = 0;
   ra.vec_scratch = h->vec_scratch;
+  MixedArgs ma;
+  ma.n = n;
+  ma.k = kk;
+  ma.sweeps = h->opt.sweeps > 0 ? h->opt.sweeps : 3;
+  ma.pad = 0;
+  ma.r = h->bhat;
+  ma.r32 = h->r32;
+  ma.c32 = h->c32;
+  ma.d32[0] = h->d32a;
+  ma.d32[1] = h->d32b;
+  ma.P32 = h->P32;
+  ma.Bt32 = h->Bt32;
+  ma.Bt16 = h->Bt16;
+  ma.X0 = h->X0;
+  ma.X1 = h->X1;
+  ma.col_done = h->col_done;
+  ma.st = h->st;
   // Launch the outer step in growing chunks; launches after convergence return at once.
-  int64_t launched = 0, chunk = method == ILS_SP ? 16 : 4;
+  int64_t launched = 0, chunk = (method == ILS_SP && !mixed) ? 16 : 4;
   const int64_t cap = h->opt.max_outer + 1;
   for (;;) {
     const int64_t todo = std::min(chunk, cap - launched);
     for (int64_t i = 0; i < todo; ++i) {
       ILS_CK(sp_iterate_f64(a, s));
-      if (method != ILS_SP) ILS_CK(rand_chain_f64(ra, method, s));
+      if (mixed) ILS_CK(mixed_correct(ma, h->opt.precision, s));
+      else if (method != ILS_SP) ILS_CK(rand_chain_f64(ra, method, s));
     }
     launched += todo;
     ILS_CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
@@ -320,7 +398,12 @@ ils_status sp_pass(ils_handle h, int64_t c0, int64_t kk, const double* B, int64_
     const double rel = bn > 0.0 ? std::sqrt(h->h_rr[c] / bn) : std::sqrt(h->h_rr[c]);
     agg->relres = std::max(agg->relres, rel);
     if (rel != rel) agg->relres = rel;
-    agg->outer_iters = std::max<int64_t>(agg->outer_iters, h->h_iters[c]);
+    if (mixed) {
+      agg->refinements = std::max<int64_t>(agg->refinements, h->h_iters[c]);
+      agg->outer_iters = std::max<int64_t>(agg->outer_iters, h->h_iters[c] * ma.sweeps);
+    } else {
+      agg->outer_iters = std::max<int64_t>(agg->outer_iters, h->h_iters[c]);
+    }
     agg->inner_iters = std::max<int64_t>(agg->inner_iters, h->h_inner[c]);
   }
   const int32_t st = h->h_st->status;
@@ -370,6 +453,11 @@ ils_status ils_setup(ils_handle* out, int64_t m, int64_t n, int64_t p, int64_t q
   if (o) opt = *o;
   else ils_options_default(&opt);
   if (validate_options(&opt) != ILS_OK) return ILS_ERR_INVALID_ARG;
+  if (opt.precision != ILS_FP64) {
+    if (opt.method != ILS_SP) return ILS_ERR_INVALID_ARG;  // mixed precision refines the SP method
+    opt.gram = ILS_GRAM_SPLIT;  // the FP64 refinement needs FP64-accurate Grams; these are the fast ones
+  }
+  if (opt.sweeps < 0) return ILS_ERR_INVALID_ARG;
   ils_handle h = new (std::nothrow) ils_handle_s();
   if (!h) return ILS_ERR_OOM;
   h->m = m;

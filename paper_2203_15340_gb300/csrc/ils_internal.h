@@ -53,12 +53,16 @@ cudaError_t rhs_bar_f64(int64_t m, int64_t n, int64_t p, int64_t k, const double
 cudaError_t gemv_cols_f64(int64_t n, int64_t k, const double* M, int64_t ldm, const double* X,
                           int64_t ldx, double* Y, int64_t ldy, cudaStream_t s);
 
-// In-place blocked Cholesky of the lower triangle of the n x n matrix L (ld n).
-// status (device int) is set to ILS_ERR_NOT_SPD or ILS_ERR_NONFINITE on a bad pivot.
-cudaError_t cholesky_f64(int64_t n, double* L, int32_t* status, cudaStream_t s);
+// In-place blocked Cholesky of the lower triangles of `count` (1 or 2) n x n matrices
+// (ld n), factored together.  inv_diag[i] (length n) receives 1 / L_jj.  status (device
+// int) is set to ILS_ERR_NOT_SPD or ILS_ERR_NONFINITE on a bad pivot of any matrix.
+cudaError_t cholesky_f64_batch(int64_t n, int count, double* const* mats, double* const* inv_diag,
+                               int32_t* status, cudaStream_t s);
 
 // X := L^{-1} X (lower = forward) then, if both, X := L^{-T} X.  X n x k (ldx).
 cudaError_t trsm_lower_f64(int64_t n, int64_t k, const double* L, double* X, int64_t ldx,
+                           bool forward, bool backward, cudaStream_t s);
+cudaError_t trsm_lower_f32(int64_t n, int64_t k, const float* L, float* X, int64_t ldx,
                            bool forward, bool backward, cudaStream_t s);
 
 // Elementwise helpers.
@@ -74,7 +78,9 @@ cudaError_t sq_norms_cols_f64(int64_t n, int64_t k, const double* X, int64_t ldx
 // forms the residual r_k = bbar - H x_k of Sec. 5's stopping test and either
 //   mode 0 (SP, Alg. 1 step 6):        x_{k+1} = B x_k + c  (M = B^T, addv = c), or
 //   mode 1 (randomized, Alg. 2 step 5 / Alg. 5 step 4): bhat = Abar2 x_k + bbar
-//          (M = Abar2, addv = bbar), written to bhat_out for the inner chain.
+//          (M = Abar2, addv = bbar), written to bhat_out for the inner chain, or
+//   mode 2 (mixed-precision refinement): r_k itself is written to bhat_out and x_k stays
+//          in place (the correction kernels update it).
 // See dense_f64.cu for the completion protocol.
 struct SpIterArgs {
   int64_t n, k;
@@ -103,6 +109,40 @@ int sp_iterate_blocks(int64_t n);
 // Copy the final iterate buffer (chosen on the device) into the user's X.
 cudaError_t copy_final_f64(int64_t n, int64_t k, const double* X0, const double* X1,
                            const SolveState* st, double* X, int64_t ldx, cudaStream_t s);
+
+// ---- FP64-accurate Gram from exact integer slice products on tcgen05 (gram_split_tc.cu) ----
+struct GramSplitWork {
+  size_t slice_elems = 0;    // BF16 slices
+  size_t partial_elems = 0;  // FP64 partial products
+  size_t exps = 0;           // int exponents
+};
+GramSplitWork gram_split_work(int64_t K, int64_t n);
+// C = A^T A for the K x n column-major A (lda), both triangles written.  err (device int)
+// is set to 1 on a tensor-pipeline timeout and 2 on a non-finite input.
+cudaError_t gram_split_tc(int64_t K, int64_t n, const double* A, int64_t lda, double* C, int64_t ldc,
+                          void* slices, double* partial, int* exps, int32_t* err, cudaStream_t s);
+
+// ---- mixed precision with FP64 refinement (mixed.cu) ----------------------------------------
+struct MixedArgs {
+  int64_t n, k;
+  int32_t sweeps;         // SP sweeps per correction (>= 1)
+  int32_t pad;
+  const double* r;        // n x k FP64 residuals (from the mode-2 outer step)
+  float* r32;             // n x k
+  float* c32;             // n x k: P r
+  float* d32[2];          // n x k ping-pong sweep iterates
+  const float* P32;       // Abar1^{-1}
+  const float* Bt32;      // (P Abar2)^T
+  const void* Bt16;       // BF16 copy of Bt32 (ILS_BF16_REFINE)
+  double* X0;
+  double* X1;
+  const int32_t* col_done;
+  SolveState* st;
+};
+// L32/P32/G2_32/Bt32 are n x n FP32 buffers, Bt16 an n x n BF16 buffer (BF16 mode only).
+cudaError_t mixed_setup(int64_t n, const double* L, const double* G2, int precision, float* L32, float* P32,
+                        float* G2_32, float* Bt32, void* Bt16, cudaStream_t s);
+cudaError_t mixed_correct(const MixedArgs& a, int precision, cudaStream_t s);
 
 // ---- randomized inner chains (randomized.cu) ----------------------------------------------
 struct RandArgs {

@@ -1,0 +1,79 @@
+"""GPU parity of mixed-precision SP with FP64 residual refinement.
+
+Stated bounds: after refinement the FP32 and BF16 variants meet the same
+||x - x*|| / ||x*|| <= 1e-10 as FP64 SP.  One correction step (three sweeps) must
+contract the FP64 residual to at most 1e-3 (FP32 P and B) or 5e-2 (B in BF16) of its
+start: rho(B)^3 plus the low-precision error of P and B times kappa(A^T J A).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from tests.helpers import colmajor, relerr, to_np_colmajor, vec
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ils():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2203_15340_gb300 as pkg
+    return pkg
+
+
+def run(ils, inst, precision, tol=1e-12, **opt):
+    import torch
+    s = ils.Solver(colmajor(inst.A), inst.p, ils.options(precision=precision, **opt))
+    x = vec(np.zeros(inst.n))
+    info = s.solve(vec(inst.b), x, tol=tol, allow=(ils.ILS_OK, ils.ILS_ERR_NO_CONVERGENCE))
+    torch.cuda.synchronize()
+    out = x.cpu().numpy()
+    s.close()
+    return out, info
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("cfg", ["c1", "c2"])
+def test_mixed_reaches_fp64_accuracy(ils, prec, cfg):
+    inst = W.config1() if cfg == "c1" else W.config2()
+    precision = ils.ILS_FP32_REFINE if prec == "fp32" else ils.ILS_BF16_REFINE
+    xs = O.qr_cholesky_solve(inst.A, inst.b, inst.p)
+    x, info = run(ils, inst, precision, tol=1e-12)
+    assert info.status == ils.ILS_OK
+    assert relerr(x, xs) <= 1e-10
+    assert 1 <= info.refinements <= (6 if prec == "fp32" else 12)
+    assert info.relres <= 1e-12
+
+
+@pytest.mark.parametrize("prec,bound", [("fp32", 1e-3), ("bf16", 5e-2)])
+def test_one_correction_contracts_residual(ils, prec, bound):
+    inst = W.config1()
+    precision = ils.ILS_FP32_REFINE if prec == "fp32" else ils.ILS_BF16_REFINE
+    x, info = run(ils, inst, precision, tol=0.0, max_outer=1)
+    assert info.refinements == 1
+    assert O.relres(inst.A, inst.b, inst.p, x) <= bound
+
+
+def test_mixed_many_rhs(ils):
+    import torch
+    inst = W.dense_gaussian(900, 200, 70, 0.3, 17, k=11)
+    s = ils.Solver(colmajor(inst.A), inst.p, ils.options(precision=ils.ILS_FP32_REFINE))
+    X = torch.zeros((11, 70), dtype=torch.float64, device="cuda")
+    info = s.solve_many(colmajor(inst.b), X, tol=1e-12)
+    Xg = to_np_colmajor(X)
+    Xs = O.normal_equation_solve(inst.A, inst.b, inst.p)
+    for j in range(11):
+        assert relerr(Xg[:, j], Xs[:, j]) <= 1e-10
+    s.close()
+
+
+def test_mixed_precision_needs_sp(ils):
+    inst = W.config1()
+    with pytest.raises(ils.ILSError) as e:
+        ils.Solver(colmajor(inst.A), inst.p, ils.options(precision=ils.ILS_FP32_REFINE, method=ils.ILS_SP_SCD))
+    assert e.value.code == ils.ILS_ERR_INVALID_ARG
