@@ -28,6 +28,21 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// dst[e] = src(e) for e in [tid, total) stepping by nthr, with 8 loads in flight per thread
+// (a plain load-store loop would wait one L2 round trip per element).
+template <typename T, typename F>
+__device__ __forceinline__ void batched_copy(T* dst, int64_t total, int tid, int nthr, F src) {
+  int64_t e = tid;
+  for (; e + 7 * (int64_t)nthr < total; e += 8 * (int64_t)nthr) {
+    T v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = src(e + u * (int64_t)nthr);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) dst[e + u * (int64_t)nthr] = v[u];
+  }
+  for (; e < total; e += nthr) dst[e] = src(e);
+}
+
 // ---------------------------------------------------------------------------------------
 // C = X^T Y (Gram / GEMM-TN), 64 x 64 output tiles, 16-row k-steps, optional split over K.
 // ---------------------------------------------------------------------------------------
@@ -104,7 +119,7 @@ __global__ void gemm_reduce_kernel(int64_t n1, int64_t n2, int splits, const dou
   const int64_t total = n1 * n2;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t gi = e % n1, gj = e / n1;
+    const int64_t gi = (uint32_t)e % (uint32_t)n1, gj = (uint32_t)e / (uint32_t)n1;  // n1 * n2 < 2^31
     if (sym && gi > gj) continue;
     double v = 0.0;
     for (int s = 0; s < splits; ++s) v += work[(size_t)s * total + e];
@@ -148,31 +163,50 @@ void gemm_plan(int64_t K, int64_t n1, int64_t n2, bool sym, int* splits, int64_t
 // ---------------------------------------------------------------------------------------
 constexpr int kRhsThreads = 256;
 
+template <int KR>
 __global__ void __launch_bounds__(kRhsThreads)
 rhs_bar_kernel(int64_t m, int64_t n, int64_t p, int64_t k, const double* __restrict__ A, int64_t lda,
                const double* __restrict__ B, int64_t ldb, double* __restrict__ out, int64_t ldo) {
   const int64_t j = blockIdx.x;
   const int64_t c0 = (int64_t)blockIdx.y * kMaxRhsPerPass;
-  const int kk = (int)((k - c0) < kMaxRhsPerPass ? (k - c0) : kMaxRhsPerPass);
-  double acc[kMaxRhsPerPass];
+  // Four interleaved partial sums per right-hand side keep FP64 latency (64 cycles per
+  // dependent FMA) and the loads overlapped.
+  double acc[KR][4];
 #pragma unroll
-  for (int c = 0; c < kMaxRhsPerPass; ++c) acc[c] = 0.0;
+  for (int c = 0; c < KR; ++c)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[c][u] = 0.0;
   const double* col = A + j * lda;
-  for (int64_t r = threadIdx.x; r < m; r += blockDim.x) {
+  const int64_t stride = blockDim.x;
+  int64_t r = threadIdx.x;
+  for (; r + 3 * stride < m; r += 4 * stride) {
+    double av[4], bv[KR][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t rr = r + u * stride;
+      av[u] = (rr < p) ? col[rr] : -col[rr];
+#pragma unroll
+      for (int c = 0; c < KR; ++c) bv[c][u] = B[rr + c * ldb];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int c = 0; c < KR; ++c) acc[c][u] = fma(av[u], bv[c][u], acc[c][u]);
+  }
+  for (; r < m; r += stride) {
     const double a = (r < p) ? col[r] : -col[r];
 #pragma unroll
-    for (int c = 0; c < kMaxRhsPerPass; ++c)
-      if (c < kk) acc[c] = fma(a, B[r + (c0 + c) * ldb], acc[c]);
+    for (int c = 0; c < KR; ++c) acc[c][0] = fma(a, B[r + c * ldb], acc[c][0]);
   }
   __shared__ double red[kRhsThreads / 32][kMaxRhsPerPass];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
-  for (int c = 0; c < kMaxRhsPerPass; ++c) {
-    const double v = warp_sum(acc[c]);
+  for (int c = 0; c < KR; ++c) {
+    const double v = warp_sum((acc[c][0] + acc[c][1]) + (acc[c][2] + acc[c][3]));
     if (lane == 0) red[w][c] = v;
   }
   __syncthreads();
-  if (threadIdx.x < kk) {
+  if (threadIdx.x < KR) {
     double v = 0.0;
     for (int ww = 0; ww < kRhsThreads / 32; ++ww) v += red[ww][threadIdx.x];
     out[j + (c0 + threadIdx.x) * ldo] = v;
@@ -182,28 +216,25 @@ rhs_bar_kernel(int64_t m, int64_t n, int64_t p, int64_t k, const double* __restr
 // Y(:,c) = M^T X(:,c): warp i reduces column i of M against each right-hand side.
 constexpr int kGemvWarps = 2;
 
+template <int KR>
 __global__ void __launch_bounds__(32 * kGemvWarps)
-gemv_cols_kernel(int64_t n, int64_t k, const double* __restrict__ M, int64_t ldm,
-                 const double* __restrict__ X, int64_t ldx, double* __restrict__ Y, int64_t ldy) {
+gemv_cols_kernel(int64_t n, const double* __restrict__ M, int64_t ldm, const double* __restrict__ X, int64_t ldx,
+                 double* __restrict__ Y, int64_t ldy) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int64_t i = (int64_t)blockIdx.x * kGemvWarps + w; i < n; i += (int64_t)gridDim.x * kGemvWarps) {
     const double* col = M + i * ldm;
-    for (int64_t c0 = 0; c0 < k; c0 += kMaxRhsPerPass) {
-      const int kk = (int)((k - c0) < kMaxRhsPerPass ? (k - c0) : kMaxRhsPerPass);
-      double acc[kMaxRhsPerPass];
+    double acc[KR];
 #pragma unroll
-      for (int c = 0; c < kMaxRhsPerPass; ++c) acc[c] = 0.0;
-      for (int64_t j = lane; j < n; j += 32) {
-        const double mv = col[j];
+    for (int c = 0; c < KR; ++c) acc[c] = 0.0;
+    for (int64_t j = lane; j < n; j += 32) {
+      const double mv = col[j];
 #pragma unroll
-        for (int c = 0; c < kMaxRhsPerPass; ++c)
-          if (c < kk) acc[c] = fma(mv, X[j + (c0 + c) * ldx], acc[c]);
-      }
+      for (int c = 0; c < KR; ++c) acc[c] = fma(mv, X[j + c * ldx], acc[c]);
+    }
 #pragma unroll
-      for (int c = 0; c < kMaxRhsPerPass; ++c) {
-        const double v = warp_sum(acc[c]);
-        if (lane == 0 && c < kk) Y[i + (c0 + c) * ldy] = v;
-      }
+    for (int c = 0; c < KR; ++c) {
+      const double v = warp_sum(acc[c]);
+      if (lane == 0) Y[i + c * ldy] = v;
     }
   }
 }
@@ -243,8 +274,8 @@ potrf_diag_kernel(int64_t n, CholBatch cb, int64_t k0, int nb) {
       if (i == 0) set_status(cb.status, ILS_ERR_NOT_SPD);
       d = 1.0;
     }
-    const double sd = sqrt(d);
-    const double rs = 1.0 / sd;
+    const double rs = rsqrt(d);
+    const double sd = d * rs;
     a[c] = (i == c) ? sd : (i > c ? a[c] * rs : a[c]);
     if (i == c && c < nb) inv[k0 + c] = rs;
 #pragma unroll
@@ -265,9 +296,14 @@ trsm_panel_kernel(int64_t n, CholBatch cb, int64_t k0, int nb) {
   const double* inv = cb.inv_diag[blockIdx.z];
   __shared__ double l11[kNB][kNB + 1];
   __shared__ double rinv[kNB];
-  for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x) {
-    const int a = e % kNB, b = e / kNB;
-    l11[a][b] = (a < nb && b < nb && a >= b) ? L[(k0 + a) + (k0 + b) * n] : 0.0;
+  {
+    // One row of L11 per thread, all 32 loads in flight before the stores.
+    const int a = threadIdx.x;
+    double v[kNB];
+#pragma unroll
+    for (int b = 0; b < kNB; ++b) v[b] = (a < nb && b < nb && a >= b) ? L[(k0 + a) + (k0 + b) * n] : 0.0;
+#pragma unroll
+    for (int b = 0; b < kNB; ++b) l11[a][b] = v[b];
   }
   if (threadIdx.x < kNB) rinv[threadIdx.x] = (threadIdx.x < nb) ? inv[k0 + threadIdx.x] : 0.0;
   __syncthreads();
@@ -276,12 +312,13 @@ trsm_panel_kernel(int64_t n, CholBatch cb, int64_t k0, int nb) {
   double x[kNB];
 #pragma unroll
   for (int c = 0; c < kNB; ++c) x[c] = (c < nb) ? L[i + (k0 + c) * n] : 0.0;
+  // Right-looking: once x_c is final, its contribution leaves every later x_d at once,
+  // so the dependent chain is 32 steps long instead of 528.
 #pragma unroll
   for (int c = 0; c < kNB; ++c) {
-    double v = x[c];
+    x[c] *= rinv[c];
 #pragma unroll
-    for (int d = 0; d < c; ++d) v = fma(-x[d], l11[c][d], v);
-    x[c] = v * rinv[c];
+    for (int d = c + 1; d < kNB; ++d) x[d] = fma(-x[c], l11[d][c], x[d]);
   }
 #pragma unroll
   for (int c = 0; c < kNB; ++c)
@@ -385,11 +422,10 @@ trsm_blocked_kernel(int64_t n, int64_t k, const T* __restrict__ L, T* __restrict
   const int nblk = (int)((n + 31) / 32);
   auto load_panel = [&](int64_t i0, int nb) {
     __syncthreads();
-    const int64_t rows = n - i0;
-    for (int64_t e = threadIdx.x; e < rows * nb; e += blockDim.x) {
-      const int64_t r = i0 + e % rows;
-      const int c = (int)(e / rows);
-      panel[(size_t)c * n + r] = L[r + (i0 + c) * n];
+    for (int c = 0; c < nb; ++c) {
+      const T* src = L + (i0 + c) * n;
+      T* dst = panel + (size_t)c * n;
+      for (int64_t r = i0 + threadIdx.x; r < n; r += blockDim.x) dst[r] = src[r];
     }
     __syncthreads();
   };
@@ -433,10 +469,114 @@ trsm_blocked_kernel(int64_t n, int64_t k, const T* __restrict__ L, T* __restrict
     for (int64_t r = lane; r < n; r += 32) X[r + col * ldx] = y[r];
 }
 
+// Inverses of the 32 x 32 diagonal blocks of a lower-triangular L (ld n): block b is stored
+// column-major at Dinv + b * 1024.  Thread j forms column j of the inverse by forward
+// substitution, X_jj = 1 / L_jj and X_ij = -(sum_{j <= k < i} L_ik X_kj) / L_ii.
+template <typename T>
+__global__ void __launch_bounds__(32) diag_block_inverse_kernel(int64_t n, const T* __restrict__ L, T* __restrict__ Dinv) {
+  __shared__ T Lb[32][33];
+  __shared__ T X[32][33];
+  const int64_t i0 = (int64_t)blockIdx.x * 32;
+  const int nb = (int)((n - i0) < 32 ? (n - i0) : 32);
+  const int j = threadIdx.x;
+  for (int a = 0; a < 32; ++a) Lb[a][j] = (a < nb && j < nb && a >= j) ? L[(i0 + a) + (i0 + j) * n] : (a == j ? T(1) : T(0));
+  __syncthreads();
+  // Right-looking: x = e_j; for k = j..31: x_k /= L_kk, then x_{k+1..} -= L(k+1..,k) x_k.
+  T x[32];
+#pragma unroll
+  for (int a = 0; a < 32; ++a) x[a] = (a == j) ? T(1) : T(0);
+#pragma unroll
+  for (int kk = 0; kk < 32; ++kk) {
+    if (kk >= j) {
+      x[kk] = x[kk] / Lb[kk][kk];
+#pragma unroll
+      for (int a = kk + 1; a < 32; ++a) x[a] = fma(-Lb[a][kk], x[kk], x[a]);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 32; ++a) X[a][j] = x[a];
+  for (int a = 0; a < 32; ++a) Dinv[(size_t)blockIdx.x * 1024 + a + j * 32] = X[a][j];
+}
+
+// X := L^{-1} X and/or L^{-T} X by 32-row block substitution with the diagonal-block
+// inverses: T = X_I - sum_{J<I} L_IJ X_J, X_I = Dinv_I T (and the transposed sweep
+// backwards).  Each CTA owns CT right-hand sides, kept in shared memory; one thread per
+// (row of the block, right-hand side).
+template <typename T, int CT>
+__global__ void __launch_bounds__(32 * CT)
+trsm_binv_kernel(int64_t n, int64_t k, const T* __restrict__ L, const T* __restrict__ Dinv, T* __restrict__ X,
+                 int64_t ldx, int fwd, int bwd) {
+  extern __shared__ __align__(16) unsigned char smem_raw_b[];
+  T* Xs = reinterpret_cast<T*>(smem_raw_b);      // CT columns of length n
+  T* Pn = Xs + (size_t)CT * n;                   // one block row / block column of L: 32 x n
+  __shared__ T Db[32][33];
+  __shared__ T Tm[32][CT];
+  const int r = threadIdx.x & 31, c = threadIdx.x >> 5;
+  const int nthr = 32 * CT;
+  const int64_t col = (int64_t)blockIdx.x * CT + c;
+  const bool cvalid = col < k;
+  for (int64_t e = r; e < n; e += 32) Xs[(size_t)c * n + e] = cvalid ? X[e + col * ldx] : T(0);
+  const int nblk = (int)((n + 31) / 32);
+  auto load_dinv = [&](int64_t ib) {
+    for (int e = threadIdx.x; e < 1024; e += nthr) Db[e & 31][e >> 5] = Dinv[(size_t)ib * 1024 + e];
+  };
+  if (fwd) {
+    for (int I = 0; I < nblk; ++I) {
+      const int64_t i0 = (int64_t)I * 32, cols = i0;  // L(i0..i0+31, 0..i0-1), stored Pn[col * 32 + row]
+      __syncthreads();
+      batched_copy(Pn, cols * 32, threadIdx.x, nthr, [&](int64_t e) {
+        const int64_t cc = e >> 5, rr = e & 31;
+        return (i0 + rr < n) ? L[(i0 + rr) + cc * n] : T(0);
+      });
+      load_dinv(I);
+      __syncthreads();
+      const int64_t gi = i0 + r;
+      T acc = (gi < n) ? Xs[(size_t)c * n + gi] : T(0);
+      const T* xc = Xs + (size_t)c * n;
+#pragma unroll 8
+      for (int64_t cc = 0; cc < cols; ++cc) acc = fma(-Pn[cc * 32 + r], xc[cc], acc);
+      Tm[r][c] = acc;
+      __syncthreads();
+      T out = T(0);
+#pragma unroll 8
+      for (int b = 0; b < 32; ++b) out = fma(Db[r][b], Tm[b][c], out);
+      if (gi < n) Xs[(size_t)c * n + gi] = out;
+    }
+  }
+  if (bwd) {
+    for (int I = nblk - 1; I >= 0; --I) {
+      const int64_t i0 = (int64_t)I * 32, j0 = i0 + 32;
+      const int64_t rows = n > j0 ? n - j0 : 0;  // L(j0..n-1, i0..i0+31), stored Pn[b * rows + row]
+      __syncthreads();
+      batched_copy(Pn, rows * 32, threadIdx.x, nthr, [&](int64_t e) {
+        const int64_t b = e / rows, rr = e - b * rows;
+        return (i0 + b < n) ? L[(j0 + rr) + (i0 + b) * n] : T(0);
+      });
+      load_dinv(I);
+      __syncthreads();
+      const int64_t gi = i0 + r;
+      T acc = (gi < n) ? Xs[(size_t)c * n + gi] : T(0);
+      const T* xc = Xs + (size_t)c * n + j0;
+      const T* pr = Pn + (size_t)r * rows;
+#pragma unroll 8
+      for (int64_t e = 0; e < rows; ++e) acc = fma(-pr[e], xc[e], acc);
+      Tm[r][c] = acc;
+      __syncthreads();
+      T out = T(0);
+#pragma unroll 8
+      for (int b = 0; b < 32; ++b) out = fma(Db[b][r], Tm[b][c], out);
+      if (gi < n) Xs[(size_t)c * n + gi] = out;
+    }
+  }
+  __syncthreads();
+  if (cvalid)
+    for (int64_t e = r; e < n; e += 32) X[e + col * ldx] = Xs[(size_t)c * n + e];
+}
+
 __global__ void set_identity_kernel(int64_t n, double* M, int64_t ld) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * n;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e % n, j = e / n;
+    const int64_t i = (uint32_t)e % (uint32_t)n, j = (uint32_t)e / (uint32_t)n;  // n * n < 2^31
     M[i + j * ld] = (i == j) ? 1.0 : 0.0;
   }
 }
@@ -451,7 +591,7 @@ __global__ void axpby_kernel(int64_t total, double alpha, const double* X, doubl
 __global__ void copy_lower_kernel(int64_t n, const double* L, double* D, int64_t ldd) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * n;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e % n, j = e / n;
+    const int64_t i = (uint32_t)e % (uint32_t)n, j = (uint32_t)e / (uint32_t)n;  // n * n < 2^31
     D[i + j * ldd] = (i >= j) ? L[i + j * n] : 0.0;
   }
 }
@@ -485,6 +625,7 @@ __global__ void sq_norms_kernel(int64_t n, int64_t k, const double* X, int64_t l
 // ---------------------------------------------------------------------------------------
 constexpr int kIterWarps = 2;
 
+template <int KR>
 __global__ void __launch_bounds__(32 * kIterWarps) sp_iter_kernel(SpIterArgs a) {
   SolveState* st = a.st;
   if (*((volatile int32_t*)&st->done)) return;
@@ -492,46 +633,71 @@ __global__ void __launch_bounds__(32 * kIterWarps) sp_iter_kernel(SpIterArgs a) 
   const double* __restrict__ x = cur ? a.X1 : a.X0;
   double* __restrict__ xn = cur ? a.X0 : a.X1;
   const int64_t n = a.n;
-  const int k = (int)a.k;
+  constexpr int k = KR;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   __shared__ int32_t done_c[kMaxRhsPerPass];
   if (threadIdx.x < kMaxRhsPerPass) done_c[threadIdx.x] = (threadIdx.x < k) ? a.col_done[threadIdx.x] : 1;
   __syncthreads();
-  double rpart[kMaxRhsPerPass];
+  double rpart[KR];
 #pragma unroll
-  for (int c = 0; c < kMaxRhsPerPass; ++c) rpart[c] = 0.0;
+  for (int c = 0; c < KR; ++c) rpart[c] = 0.0;
 
   for (int64_t i = (int64_t)blockIdx.x * kIterWarps + w; i < n; i += (int64_t)gridDim.x * kIterWarps) {
     const double* brow = a.Bt + i * n;
     const double* hrow = a.H + i * n;
-    double ab[kMaxRhsPerPass], ah[kMaxRhsPerPass];
+    double ab[KR], ah[KR];
 #pragma unroll
-    for (int c = 0; c < kMaxRhsPerPass; ++c) ab[c] = ah[c] = 0.0;
+    for (int c = 0; c < KR; ++c) ab[c] = ah[c] = 0.0;
+    double ab2[KR], ah2[KR];
+#pragma unroll
+    for (int c = 0; c < KR; ++c) ab2[c] = ah2[c] = 0.0;
+    int64_t j = lane;
     if (a.mode != 2) {
-      for (int64_t j = lane; j < n; j += 32) {
+      for (; j + 32 < n; j += 64) {
+        const double bv = brow[j], hv = hrow[j], bv2 = brow[j + 32], hv2 = hrow[j + 32];
+#pragma unroll
+        for (int c = 0; c < KR; ++c) {
+          const double xv = x[j + c * n], xv2 = x[j + 32 + c * n];
+          ab[c] = fma(bv, xv, ab[c]);
+          ah[c] = fma(hv, xv, ah[c]);
+          ab2[c] = fma(bv2, xv2, ab2[c]);
+          ah2[c] = fma(hv2, xv2, ah2[c]);
+        }
+      }
+      for (; j < n; j += 32) {
         const double bv = brow[j], hv = hrow[j];
 #pragma unroll
-        for (int c = 0; c < kMaxRhsPerPass; ++c) {
-          if (c < k) {
-            const double xv = x[j + c * n];
-            ab[c] = fma(bv, xv, ab[c]);
-            ah[c] = fma(hv, xv, ah[c]);
-          }
+        for (int c = 0; c < KR; ++c) {
+          const double xv = x[j + c * n];
+          ab[c] = fma(bv, xv, ab[c]);
+          ah[c] = fma(hv, xv, ah[c]);
         }
       }
     } else {
-      for (int64_t j = lane; j < n; j += 32) {
+      for (; j + 32 < n; j += 64) {
+        const double hv = hrow[j], hv2 = hrow[j + 32];
+#pragma unroll
+        for (int c = 0; c < KR; ++c) {
+          ah[c] = fma(hv, x[j + c * n], ah[c]);
+          ah2[c] = fma(hv2, x[j + 32 + c * n], ah2[c]);
+        }
+      }
+      for (; j < n; j += 32) {
         const double hv = hrow[j];
 #pragma unroll
-        for (int c = 0; c < kMaxRhsPerPass; ++c)
-          if (c < k) ah[c] = fma(hv, x[j + c * n], ah[c]);
+        for (int c = 0; c < KR; ++c) ah[c] = fma(hv, x[j + c * n], ah[c]);
       }
     }
 #pragma unroll
-    for (int c = 0; c < kMaxRhsPerPass; ++c) {
-      const double sb = warp_sum(ab[c]);
+    for (int c = 0; c < KR; ++c) {
+      ab[c] += ab2[c];
+      ah[c] += ah2[c];
+    }
+#pragma unroll
+    for (int c = 0; c < KR; ++c) {
+      const double sb = a.mode != 2 ? warp_sum(ab[c]) : 0.0;
       const double sh = warp_sum(ah[c]);
-      if (lane == 0 && c < k) {
+      if (lane == 0) {
         if (done_c[c]) {
           if (a.mode != 2) xn[i + c * n] = x[i + c * n];
         } else {
@@ -544,10 +710,10 @@ __global__ void __launch_bounds__(32 * kIterWarps) sp_iter_kernel(SpIterArgs a) 
       }
     }
   }
-  __shared__ double red[kIterWarps][kMaxRhsPerPass];
+  __shared__ double red[kIterWarps][KR];
   if (lane == 0) {
 #pragma unroll
-    for (int c = 0; c < kMaxRhsPerPass; ++c) red[w][c] = rpart[c];
+    for (int c = 0; c < KR; ++c) red[w][c] = rpart[c];
   }
   __syncthreads();
   if (threadIdx.x < k) {
@@ -610,7 +776,7 @@ __global__ void copy_final_kernel(int64_t n, int64_t k, const double* X0, const 
   const double* src = st->cur ? X1 : X0;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * k;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e % n, c = e / n;
+    const int64_t i = (uint32_t)e % (uint32_t)n, c = (uint32_t)e / (uint32_t)n;
     X[i + c * ldx] = src[i + c * n];
   }
 }
@@ -688,19 +854,51 @@ cudaError_t gemm_tn_f64_capped(int64_t K, int64_t n, const double* X, int64_t ld
 cudaError_t rhs_bar_f64(int64_t m, int64_t n, int64_t p, int64_t k, const double* A, int64_t lda, const double* B,
                         int64_t ldb, double* out, int64_t ldo, cudaStream_t s) {
   if (n <= 0 || k <= 0) return cudaSuccess;
-  dim3 grid((unsigned)n, (unsigned)((k + kMaxRhsPerPass - 1) / kMaxRhsPerPass));
-  rhs_bar_kernel<<<grid, kRhsThreads, 0, s>>>(m, n, p, k, A, lda, B, ldb, out, ldo);
-  note_launch();
-  return cudaGetLastError();
+  for (int64_t c0 = 0; c0 < k; c0 += kMaxRhsPerPass) {
+    const int kk = (int)std::min<int64_t>(kMaxRhsPerPass, k - c0);
+    const double* Bc = B + c0 * ldb;  // the kernel indexes columns from 0
+    double* Oc = out + c0 * ldo;
+    const dim3 grid((unsigned)n, 1);
+    switch (kk) {
+      case 1: rhs_bar_kernel<1><<<grid, kRhsThreads, 0, s>>>(m, n, p, kk, A, lda, Bc, ldb, Oc, ldo); break;
+      case 2: rhs_bar_kernel<2><<<grid, kRhsThreads, 0, s>>>(m, n, p, kk, A, lda, Bc, ldb, Oc, ldo); break;
+      case 3: rhs_bar_kernel<3><<<grid, kRhsThreads, 0, s>>>(m, n, p, kk, A, lda, Bc, ldb, Oc, ldo); break;
+      case 4: rhs_bar_kernel<4><<<grid, kRhsThreads, 0, s>>>(m, n, p, kk, A, lda, Bc, ldb, Oc, ldo); break;
+      case 5: rhs_bar_kernel<5><<<grid, kRhsThreads, 0, s>>>(m, n, p, kk, A, lda, Bc, ldb, Oc, ldo); break;
+      case 6: rhs_bar_kernel<6><<<grid, kRhsThreads, 0, s>>>(m, n, p, kk, A, lda, Bc, ldb, Oc, ldo); break;
+      case 7: rhs_bar_kernel<7><<<grid, kRhsThreads, 0, s>>>(m, n, p, kk, A, lda, Bc, ldb, Oc, ldo); break;
+      default: rhs_bar_kernel<8><<<grid, kRhsThreads, 0, s>>>(m, n, p, kk, A, lda, Bc, ldb, Oc, ldo); break;
+    }
+    note_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t gemv_cols_f64(int64_t n, int64_t k, const double* M, int64_t ldm, const double* X, int64_t ldx,
                           double* Y, int64_t ldy, cudaStream_t s) {
   if (n <= 0 || k <= 0) return cudaSuccess;
   const int blocks = (int)std::min<int64_t>((n + kGemvWarps - 1) / kGemvWarps, 16 * (int64_t)num_sms());
-  gemv_cols_kernel<<<blocks, 32 * kGemvWarps, 0, s>>>(n, k, M, ldm, X, ldx, Y, ldy);
-  note_launch();
-  return cudaGetLastError();
+  for (int64_t c0 = 0; c0 < k; c0 += kMaxRhsPerPass) {
+    const int kk = (int)std::min<int64_t>(kMaxRhsPerPass, k - c0);
+    const double* Xc = X + c0 * ldx;
+    double* Yc = Y + c0 * ldy;
+    switch (kk) {
+      case 1: gemv_cols_kernel<1><<<blocks, 32 * kGemvWarps, 0, s>>>(n, M, ldm, Xc, ldx, Yc, ldy); break;
+      case 2: gemv_cols_kernel<2><<<blocks, 32 * kGemvWarps, 0, s>>>(n, M, ldm, Xc, ldx, Yc, ldy); break;
+      case 3: gemv_cols_kernel<3><<<blocks, 32 * kGemvWarps, 0, s>>>(n, M, ldm, Xc, ldx, Yc, ldy); break;
+      case 4: gemv_cols_kernel<4><<<blocks, 32 * kGemvWarps, 0, s>>>(n, M, ldm, Xc, ldx, Yc, ldy); break;
+      case 5: gemv_cols_kernel<5><<<blocks, 32 * kGemvWarps, 0, s>>>(n, M, ldm, Xc, ldx, Yc, ldy); break;
+      case 6: gemv_cols_kernel<6><<<blocks, 32 * kGemvWarps, 0, s>>>(n, M, ldm, Xc, ldx, Yc, ldy); break;
+      case 7: gemv_cols_kernel<7><<<blocks, 32 * kGemvWarps, 0, s>>>(n, M, ldm, Xc, ldx, Yc, ldy); break;
+      default: gemv_cols_kernel<8><<<blocks, 32 * kGemvWarps, 0, s>>>(n, M, ldm, Xc, ldx, Yc, ldy); break;
+    }
+    note_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t cholesky_f64_batch(int64_t n, int count, double* const* mats, double* const* inv_diag, int32_t* status,
@@ -731,6 +929,36 @@ cudaError_t cholesky_f64_batch(int64_t n, int count, double* const* mats, double
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t trsm_lower_t(int64_t n, int64_t k, const T* L, T* X, int64_t ldx, bool forward, bool backward,
+                         cudaStream_t s);
+
+template <typename T>
+cudaError_t trsm_binv_t(int64_t n, int64_t k, const T* L, T* Dinv, T* X, int64_t ldx, bool forward, bool backward,
+                        cudaStream_t s) {
+  if (n <= 0 || k <= 0) return cudaSuccess;
+  constexpr int CT0 = sizeof(T) == 8 ? 4 : 8;
+  if (sizeof(T) * (size_t)n * (CT0 + 32) > 200 * 1024)  // panel does not fit: per-step solver
+    return trsm_lower_t<T>(n, k, L, X, ldx, forward, backward, s);
+  const int nblk = (int)((n + 31) / 32);
+  diag_block_inverse_kernel<T><<<nblk, 32, 0, s>>>(n, L, Dinv);
+  note_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // FP64 is issue-bound: 4 right-hand sides per CTA spread the work over more SMs.
+  constexpr int CT = sizeof(T) == 8 ? 4 : 8;
+  const size_t smem = sizeof(T) * (size_t)n * (CT + 32);
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  if (smem > 48 * 1024) {
+    e = cudaFuncSetAttribute(trsm_binv_kernel<T, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  trsm_binv_kernel<T, CT><<<(unsigned)((k + CT - 1) / CT), 32 * CT, smem, s>>>(n, k, L, Dinv, X, ldx,
+                                                                             forward ? 1 : 0, backward ? 1 : 0);
+  note_launch();
+  return cudaGetLastError();
 }
 
 template <typename T>
@@ -768,6 +996,16 @@ cudaError_t trsm_lower_f32(int64_t n, int64_t k, const float* L, float* X, int64
   return trsm_lower_t<float>(n, k, L, X, ldx, forward, backward, s);
 }
 
+cudaError_t trsm_binv_f64(int64_t n, int64_t k, const double* L, double* Dinv, double* X, int64_t ldx, bool forward,
+                          bool backward, cudaStream_t s) {
+  return trsm_binv_t<double>(n, k, L, Dinv, X, ldx, forward, backward, s);
+}
+
+cudaError_t trsm_binv_f32(int64_t n, int64_t k, const float* L, float* Dinv, float* X, int64_t ldx, bool forward,
+                          bool backward, cudaStream_t s) {
+  return trsm_binv_t<float>(n, k, L, Dinv, X, ldx, forward, backward, s);
+}
+
 cudaError_t set_identity_f64(int64_t n, double* M, int64_t ld, cudaStream_t s) {
   set_identity_kernel<<<grid_for(n * n, 256), 256, 0, s>>>(n, M, ld);
   note_launch();
@@ -800,7 +1038,17 @@ int sp_iterate_blocks(int64_t n) {
 }
 
 cudaError_t sp_iterate_f64(const SpIterArgs& a, cudaStream_t s) {
-  sp_iter_kernel<<<sp_iterate_blocks(a.n), 32 * kIterWarps, 0, s>>>(a);
+  const int blocks = sp_iterate_blocks(a.n);
+  switch ((int)a.k) {
+    case 1: sp_iter_kernel<1><<<blocks, 32 * kIterWarps, 0, s>>>(a); break;
+    case 2: sp_iter_kernel<2><<<blocks, 32 * kIterWarps, 0, s>>>(a); break;
+    case 3: sp_iter_kernel<3><<<blocks, 32 * kIterWarps, 0, s>>>(a); break;
+    case 4: sp_iter_kernel<4><<<blocks, 32 * kIterWarps, 0, s>>>(a); break;
+    case 5: sp_iter_kernel<5><<<blocks, 32 * kIterWarps, 0, s>>>(a); break;
+    case 6: sp_iter_kernel<6><<<blocks, 32 * kIterWarps, 0, s>>>(a); break;
+    case 7: sp_iter_kernel<7><<<blocks, 32 * kIterWarps, 0, s>>>(a); break;
+    default: sp_iter_kernel<8><<<blocks, 32 * kIterWarps, 0, s>>>(a); break;
+  }
   note_launch();
   return cudaGetLastError();
 }

@@ -331,9 +331,8 @@ __global__ void column_exponent_kernel(int K, int n, const double* __restrict__ 
 // only (GB300's FP64 pipe is the scarce unit).
 __global__ void split_kernel(int K, int n, const double* __restrict__ A, int64_t lda, const int* __restrict__ exps,
                              __nv_bfloat16* __restrict__ D, int64_t ldk, int32_t* err) {
-  const int64_t total = (int64_t)K * n;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int r = (int)(e % K), j = (int)(e / K);
+  const int j = blockIdx.y;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < K; r += gridDim.x * blockDim.x) {
     const long long bits = __double_as_longlong(A[r + (int64_t)j * lda]);
     const int f = (int)((bits >> 52) & 0x7FF);
     long long V = 0;
@@ -427,7 +426,7 @@ cudaError_t gram_split_tc(int64_t K, int64_t n, const double* A, int64_t lda, do
                           double* partial, int* exps, int32_t* err, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   if (K <= 0) return cudaMemset2DAsync(C, sizeof(double) * ldc, 0, sizeof(double) * n, n, s);
-  if (K > (int64_t)1 << 30 || n > (int64_t)1 << 20) return cudaErrorInvalidValue;
+  if (K > (int64_t)1 << 30 || n > 65535) return cudaErrorInvalidValue;
   PFN_cuTensorMapEncodeTiled_v12000 encode = get_encode_fn();
   if (!encode) return cudaErrorNotSupported;
   const int64_t ldk = ((K + 7) / 8) * 8;
@@ -440,7 +439,8 @@ cudaError_t gram_split_tc(int64_t K, int64_t n, const double* A, int64_t lda, do
     e = cudaMemsetAsync(D, 0, sizeof(__nv_bfloat16) * (size_t)kSlices * n * ldk, s);
     if (e != cudaSuccess) return e;
   }
-  split_kernel<<<1024, 256, 0, s>>>((int)K, (int)n, A, lda, exps, D, ldk, err);
+  split_kernel<<<dim3((unsigned)std::min<int64_t>((K + 255) / 256, 64), (unsigned)n), 256, 0, s>>>(
+      (int)K, (int)n, A, lda, exps, D, ldk, err);
   note_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
 

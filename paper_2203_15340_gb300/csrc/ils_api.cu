@@ -40,6 +40,7 @@ struct ils_handle_s {
   double* col_target2 = nullptr; // kMaxRhsPerPass
   int64_t* col_inner = nullptr;  // kMaxRhsPerPass
   double* inv_diag = nullptr;    // 2n: reciprocal Cholesky pivots (Abar1, H)
+  double* Dinv = nullptr;        // inverses of L's 32 x 32 diagonal blocks
   double* norms2 = nullptr;      // n: ||A_1(:,j)||^2
   double* cum = nullptr;         // n: running sum of norms2
   double* vec_scratch = nullptr; // RK-RGS w and e when they do not fit in shared memory
@@ -108,12 +109,14 @@ __global__ void init_state_kernel(SolveState* st, int64_t max_outer, int32_t* co
 __global__ void transpose_kernel(int64_t n, const double* src, double* dst, int64_t ldd) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * n;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e % n, j = e / n;
+    const int64_t i = (uint32_t)e % (uint32_t)n, j = (uint32_t)e / (uint32_t)n;  // n * n < 2^31
     dst[j + i * ldd] = src[i + j * n];
   }
 }
 
 size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
+
+constexpr int64_t kMaxN = 16384;  // n x n FP64 products stay below 2^31 elements
 
 struct Carver {
   char* base;
@@ -151,6 +154,7 @@ void carve(ils_handle h, Carver& c, size_t work_elems) {
   h->col_target2 = c.take<double>(kMaxRhsPerPass);
   h->col_inner = c.take<int64_t>(kMaxRhsPerPass);
   h->inv_diag = c.take<double>(2 * (size_t)h->n);
+  h->Dinv = c.take<double>((size_t)((h->n + 31) / 32) * 1024);
   h->norms2 = c.take<double>((size_t)h->n);
   h->cum = c.take<double>((size_t)h->n);
   h->vec_in_smem = rkrgs_vec_fits(h->n, h->p);
@@ -237,7 +241,7 @@ ils_status compute_setup(ils_handle h) {
     ILS_CK(gemm_tn_f64(p, n, n, h->A, m, h->A, m, p, h->G1, n, true, false, h->work, s));
   }
   ILS_CK(mark(h, 2));
-  ILS_CK(column_cumsum_f64(n, h->G1, h->norms2, h->cum, s));
+  if (h->opt.method != ILS_SP) ILS_CK(column_cumsum_f64(n, h->G1, h->norms2, h->cum, s));
   if (h->opt.gram == ILS_GRAM_SPLIT) {
     ILS_CK(gram_split_tc(q, n, h->A + p, m, h->G2, n, h->gs_slices, h->gs_partial, h->gs_exps, h->gs_err, s));
   } else {
@@ -267,11 +271,12 @@ ils_status compute_setup(ils_handle h) {
   if (*h->h_status != 0) return (ils_status)*h->h_status;
   if (h->opt.precision != ILS_FP64) {
     // Mixed precision: P and B for the correction sweeps in FP32 (B also in BF16).
-    ILS_CK(mixed_setup(n, h->L, h->G2, h->opt.precision, h->L32, h->P32, h->G2_32, h->Bt32, h->Bt16, s));
+    ILS_CK(mixed_setup(n, h->L, h->G2, h->opt.precision, h->L32, h->P32, h->G2_32, h->Bt32, h->Bt16,
+                       reinterpret_cast<float*>(h->Dinv), s));
   } else {
     // P = L^{-T} L^{-1} (Alg. 1 step 2), B^T = (P Abar2)^T = Abar2 P (Alg. 1 step 3).
     ILS_CK(set_identity_f64(n, h->P, n, s));
-    ILS_CK(trsm_lower_f64(n, n, h->L, h->P, n, true, true, s));
+    ILS_CK(trsm_binv_f64(n, n, h->L, h->Dinv, h->P, n, true, true, s));
     ILS_CK(gemm_tn_f64(n, n, n, h->G2, n, h->P, n, n, h->Bt, n, false, false, h->work, s));
   }
   ILS_CK(mark(h, 5));
@@ -448,7 +453,8 @@ ils_status ils_setup(ils_handle* out, int64_t m, int64_t n, int64_t p, int64_t q
                      const ils_options* o, ils_stream_t stream) {
   if (!out) return ILS_ERR_INVALID_ARG;
   *out = nullptr;
-  if (n < 1 || p < n || q < 0 || m != p + q || lda < m || !A) return ILS_ERR_INVALID_ARG;
+  if (n < 1 || n > kMaxN || p < n || q < 0 || m != p + q || lda < m || !A || m > ((int64_t)1 << 31))
+    return ILS_ERR_INVALID_ARG;
   ils_options opt;
   if (o) opt = *o;
   else ils_options_default(&opt);

@@ -64,6 +64,13 @@ cudaError_t trsm_lower_f64(int64_t n, int64_t k, const double* L, double* X, int
                            bool forward, bool backward, cudaStream_t s);
 cudaError_t trsm_lower_f32(int64_t n, int64_t k, const float* L, float* X, int64_t ldx,
                            bool forward, bool backward, cudaStream_t s);
+// Same solves by 32-row blocks with explicit inverses of L's 32 x 32 diagonal blocks
+// (written to Dinv, ceil(n/32) * 1024 elements); the right-hand sides of a CTA stay in
+// shared memory with one 32 x n panel of L (n <= 708 in FP64, 1422 in FP32).
+cudaError_t trsm_binv_f64(int64_t n, int64_t k, const double* L, double* Dinv, double* X, int64_t ldx,
+                          bool forward, bool backward, cudaStream_t s);
+cudaError_t trsm_binv_f32(int64_t n, int64_t k, const float* L, float* Dinv, float* X, int64_t ldx,
+                          bool forward, bool backward, cudaStream_t s);
 
 // Elementwise helpers.
 cudaError_t set_identity_f64(int64_t n, double* M, int64_t ld, cudaStream_t s);
@@ -141,7 +148,7 @@ struct MixedArgs {
 };
 // L32/P32/G2_32/Bt32 are n x n FP32 buffers, Bt16 an n x n BF16 buffer (BF16 mode only).
 cudaError_t mixed_setup(int64_t n, const double* L, const double* G2, int precision, float* L32, float* P32,
-                        float* G2_32, float* Bt32, void* Bt16, cudaStream_t s);
+                        float* G2_32, float* Bt32, void* Bt16, float* Dinv32, cudaStream_t s);
 cudaError_t mixed_correct(const MixedArgs& a, int precision, cudaStream_t s);
 
 // ---- randomized inner chains (randomized.cu) ----------------------------------------------

@@ -36,7 +36,7 @@ __global__ void f32_to_bf16_kernel(int64_t count, const float* __restrict__ src,
 
 __global__ void identity_f32_kernel(int64_t n, float* M) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * n; e += (int64_t)gridDim.x * blockDim.x)
-    M[e] = (e % n == e / n) ? 1.f : 0.f;
+    M[e] = ((uint32_t)e % (uint32_t)n == (uint32_t)e / (uint32_t)n) ? 1.f : 0.f;
 }
 
 // C = X^T Y in FP32 (X, Y n x n column-major): 32 x 32 tiles, one output per thread.
@@ -75,41 +75,55 @@ __device__ __forceinline__ float ld_op(const __nv_bfloat16* p, int64_t i) { retu
 
 constexpr int kSweepWarps = 2;
 
-// out(:,c) = M^T v(:,c) (+ add(:,c)) for the unfinished columns; column i of M is row i of
-// the operator.  `first` marks the step that starts from v = P r: it also converts r.
-template <typename TM>
+// out(:,c) = M^T v(:,c) (+ add(:,c)); column i of M is row i of the operator.  KR is the
+// number of right-hand sides, fixed at compile time so no predicated work is issued.
+template <typename TM, int KR>
 __global__ void __launch_bounds__(32 * kSweepWarps) sweep_kernel(MixedArgs a, const TM* __restrict__ M,
                                                                  const float* __restrict__ v,
                                                                  const float* __restrict__ add,
                                                                  float* __restrict__ out) {
   if (*((volatile int32_t*)&a.st->done)) return;
   const int64_t n = a.n;
-  const int k = (int)a.k;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int64_t i = (int64_t)blockIdx.x * kSweepWarps + w; i < n; i += (int64_t)gridDim.x * kSweepWarps) {
     const TM* col = M + i * n;
-    float acc[kMaxRhsPerPass];
+    float acc[KR];
 #pragma unroll
-    for (int c = 0; c < kMaxRhsPerPass; ++c) acc[c] = 0.f;
+    for (int c = 0; c < KR; ++c) acc[c] = 0.f;
     for (int64_t j = lane; j < n; j += 32) {
       const float mv = ld_op(col, j);
 #pragma unroll
-      for (int c = 0; c < kMaxRhsPerPass; ++c)
-        if (c < k) acc[c] = fmaf(mv, v[j + c * n], acc[c]);
+      for (int c = 0; c < KR; ++c) acc[c] = fmaf(mv, v[j + c * n], acc[c]);
     }
 #pragma unroll
-    for (int c = 0; c < kMaxRhsPerPass; ++c) {
+    for (int c = 0; c < KR; ++c) {
       const float sv = warp_sum_f(acc[c]);
-      if (lane == 0 && c < k) out[i + c * n] = sv + (add ? add[i + c * n] : 0.f);
+      if (lane == 0) out[i + c * n] = sv + (add ? add[i + c * n] : 0.f);
     }
   }
+}
+
+template <typename TM>
+void launch_sweep(const MixedArgs& a, int blocks, const TM* M, const float* v, const float* add, float* out,
+                  cudaStream_t s) {
+  switch ((int)a.k) {
+    case 1: sweep_kernel<TM, 1><<<blocks, 32 * kSweepWarps, 0, s>>>(a, M, v, add, out); break;
+    case 2: sweep_kernel<TM, 2><<<blocks, 32 * kSweepWarps, 0, s>>>(a, M, v, add, out); break;
+    case 3: sweep_kernel<TM, 3><<<blocks, 32 * kSweepWarps, 0, s>>>(a, M, v, add, out); break;
+    case 4: sweep_kernel<TM, 4><<<blocks, 32 * kSweepWarps, 0, s>>>(a, M, v, add, out); break;
+    case 5: sweep_kernel<TM, 5><<<blocks, 32 * kSweepWarps, 0, s>>>(a, M, v, add, out); break;
+    case 6: sweep_kernel<TM, 6><<<blocks, 32 * kSweepWarps, 0, s>>>(a, M, v, add, out); break;
+    case 7: sweep_kernel<TM, 7><<<blocks, 32 * kSweepWarps, 0, s>>>(a, M, v, add, out); break;
+    default: sweep_kernel<TM, 8><<<blocks, 32 * kSweepWarps, 0, s>>>(a, M, v, add, out); break;
+  }
+  note_launch();
 }
 
 __global__ void residual_to_f32_kernel(MixedArgs a) {
   if (*((volatile int32_t*)&a.st->done)) return;
   const int64_t total = a.n * a.k;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(e / a.n);
+    const int c = (int)((uint32_t)e / (uint32_t)a.n);
     a.r32[e] = a.col_done[c] ? 0.f : (float)a.r[e];
   }
 }
@@ -120,7 +134,7 @@ __global__ void refine_update_kernel(MixedArgs a, const float* __restrict__ d) {
   double* x = *((volatile int32_t*)&a.st->cur) ? a.X1 : a.X0;
   const int64_t total = a.n * a.k;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(e / a.n);
+    const int c = (int)((uint32_t)e / (uint32_t)a.n);
     if (!a.col_done[c]) x[e] += (double)d[e];
   }
 }
@@ -130,7 +144,7 @@ int grid_small(int64_t total) { return (int)std::max<int64_t>(1, std::min<int64_
 }  // namespace
 
 cudaError_t mixed_setup(int64_t n, const double* L, const double* G2, int precision, float* L32, float* P32,
-                        float* G2_32, float* Bt32, void* Bt16, cudaStream_t s) {
+                        float* G2_32, float* Bt32, void* Bt16, float* Dinv32, cudaStream_t s) {
   const int64_t nn = n * n;
   f64_to_f32_kernel<<<grid_small(nn), 256, 0, s>>>(nn, L, L32);
   note_launch();
@@ -141,7 +155,7 @@ cudaError_t mixed_setup(int64_t n, const double* L, const double* G2, int precis
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // P = L^{-T} L^{-1} in FP32 from the FP64 Cholesky factor.
-  if ((e = trsm_lower_f32(n, n, L32, P32, n, true, true, s)) != cudaSuccess) return e;
+  if ((e = trsm_binv_f32(n, n, L32, Dinv32, P32, n, true, true, s)) != cudaSuccess) return e;
   // B^T = Abar2 P (both symmetric), so column i of B^T is row i of B = P Abar2.
   const unsigned nt = (unsigned)((n + 31) / 32);
   gemm_tn_f32_kernel<<<dim3(nt, nt), 256, 0, s>>>(n, G2_32, P32, Bt32);
@@ -165,18 +179,15 @@ cudaError_t mixed_correct(const MixedArgs& a, int precision, cudaStream_t s) {
   note_launch();
   const int blocks = mixed_sweep_blocks(a.n);
   // c = P r  (kept in a.c32; also the first iterate d_1)
-  sweep_kernel<float><<<blocks, 32 * kSweepWarps, 0, s>>>(a, a.P32, a.r32, nullptr, a.c32);
-  note_launch();
+  launch_sweep<float>(a, blocks, a.P32, a.r32, nullptr, a.c32, s);
   const float* dcur = a.c32;
   float* bufs[2] = {a.d32[0], a.d32[1]};
   for (int sw = 1; sw < a.sweeps; ++sw) {
     float* dn = bufs[sw & 1];
     if (precision == ILS_BF16_REFINE)
-      sweep_kernel<__nv_bfloat16><<<blocks, 32 * kSweepWarps, 0, s>>>(
-          a, static_cast<const __nv_bfloat16*>(a.Bt16), dcur, a.c32, dn);
+      launch_sweep<__nv_bfloat16>(a, blocks, static_cast<const __nv_bfloat16*>(a.Bt16), dcur, a.c32, dn, s);
     else
-      sweep_kernel<float><<<blocks, 32 * kSweepWarps, 0, s>>>(a, a.Bt32, dcur, a.c32, dn);
-    note_launch();
+      launch_sweep<float>(a, blocks, a.Bt32, dcur, a.c32, dn, s);
     dcur = dn;
   }
   refine_update_kernel<<<grid_small(a.n * a.k), 256, 0, s>>>(a, dcur);

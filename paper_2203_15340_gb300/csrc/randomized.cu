@@ -295,22 +295,31 @@ __global__ void __launch_bounds__(kChainThreads) rkrgs_chain_kernel(RandArgs a) 
   if (threadIdx.x == 0) a.col_inner[c] += t;
 }
 
-// cum[j] = sum_{i <= j} norms2[i], added left to right; norms2 = diag(Abar1).
+// cum[j] = sum_{i <= j} norms2[i], added left to right; norms2 = diag(Abar1).  The
+// diagonal is gathered in parallel; one thread then adds it in order, 32 loads at a time.
 __global__ void column_cumsum_kernel(int64_t n, const double* G1, double* norms2, double* cum) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) norms2[j] = G1[j + j * n];
+  __syncthreads();
+  if (threadIdx.x != 0) return;
   double s = 0.0;
-  for (int64_t j = 0; j < n; ++j) {
-    const double v = G1[j + j * n];
-    norms2[j] = v;
-    s += v;
-    cum[j] = s;
+  for (int64_t j0 = 0; j0 < n; j0 += 32) {
+    double v[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) v[t] = (j0 + t < n) ? norms2[j0 + t] : 0.0;
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+      if (j0 + t < n) {
+        s += v[t];
+        cum[j0 + t] = s;
+      }
+    }
   }
 }
 
 }  // namespace
 
 cudaError_t column_cumsum_f64(int64_t n, const double* G1, double* norms2, double* cum, cudaStream_t s) {
-  column_cumsum_kernel<<<1, 32, 0, s>>>(n, G1, norms2, cum);
+  column_cumsum_kernel<<<1, 256, 0, s>>>(n, G1, norms2, cum);
   note_launch();
   return cudaGetLastError();
 }
