@@ -2,11 +2,15 @@
 """ILS solves/s on GB300 for the dense 20000 x 500 instance (p = 16000, q = 4000).
 
 One step = one complete solve of a fresh instance through the C ABI: every setup
-product (ils_refactor: the Gram matrices A_1^T A_1 and A_2^T A_2, both Cholesky
-factorizations, P = (A_1^T A_1)^{-1} and B = P A_2^T A_2) followed by ils_solve
-(A^T J b, c = P A^T J b and the SP iterations to the tolerance).  The inputs are
-resident in HBM when a step starts; A (80 MB) fits in L2, so L2 is flushed
-before every step (a 256 MiB write, outside the timed events).
+product (ils_refactor: the Gram matrices A_1^T A_1 and A_2^T A_2, the Cholesky
+factorizations of A_1^T A_1 and A^T J A, P = (A_1^T A_1)^{-1} and B = P A_2^T A_2)
+followed by ils_solve (A^T J b and the iterations to the tolerance).  The headline
+path is mixed-precision SP: FP64-accurate Gram matrices from exact BF16 digit
+products on the tcgen05 tensor cores, FP64 Cholesky, FP32 sweeps with P and B, and
+FP64 residual refinement.  Plain FP64 SP (the paper's Alg. 1 in FP64 throughout) is
+timed the same way on the same instance and reported beside it.  The inputs are
+resident in HBM when a step starts; A (80 MB) fits in L2, so L2 is flushed before
+every step (a 256 MiB write, outside the timed events).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun every rank runs its own replica (weak scaling); rank 0 prints one
@@ -30,6 +34,7 @@ METRIC = "ILS solves/s at rel err ≤1e-10: mixed+batched+warm vs plain FP64 SP,
 WORKLOAD = "dense ILS 20000x500 (A_1 16000x500 N(0,1), A_2 4000x500 0.3*N(0,1)), single RHS, seed 1"
 TOL_RELRES = 1e-11  # relres target; kappa(A^T J A) ~ 2.5 here, so the error bound is ~2.5e-11
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (FMA pipe) rate from the profiling recipe
+BF16_PEAK_TFLOPS = 1982.7  # measured cuBLAS BF16 burst rate on this machine (MEASURED_PEAKS.json)
 
 
 def parse():
@@ -177,53 +182,60 @@ def main():
     b = torch.from_numpy(inst.b).to(dev)
     x = torch.zeros(n, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
-    solver = ils.Solver(At, p, ils.options(timing=1), stream=stream)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-
-    def step():
-        solver.refactor(At, stream=stream)
-        return solver.solve(b, x, tol=TOL_RELRES, stream=stream)
-
-    for _ in range(max(args.warmup, 1)):
-        info = step()
-    torch.cuda.synchronize()
-    # Accuracy gate on the warm-up result: the oracle's QR-Cholesky solution.
     import oracle
     xs = oracle.qr_cholesky_solve(inst.A, inst.b, inst.p)
-    relerr = float(np.linalg.norm(x.cpu().numpy() - xs) / np.linalg.norm(xs))
-    if not relerr <= 1e-10:
-        raise SystemExit(f"accuracy gate failed: relerr {relerr:.3e}")
 
-    # ---- timed region: K steps, per-step CUDA events, L2 flushed between steps ----
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    gram_ms, iters = [], []
-    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
-    barrier()
-    torch.cuda.synchronize()
-    if sampler:
-        sampler.start()
-    launches0 = ils.binding.kernel_launches()
-    wall0 = time.perf_counter()
-    for i in range(args.steps):
-        flush.zero_()
-        ev[i][0].record(stream)
-        info = step()
-        ev[i][1].record(stream)
-        gram_ms.append(solver.timings()["gram1"])
-        iters.append(info.outer_iters)
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - wall0
-    launches = ils.binding.kernel_launches() - launches0
-    barrier()
-    clocks = sampler.stop() if sampler else None
-    step_ms = [a.elapsed_time(bb) for a, bb in ev]
-    total_s = sum(step_ms) / 1e3
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = world * args.steps / total_s
+    def measure(opts, steps, with_clocks):
+        """Warm up, gate accuracy, then time `steps` complete solves (per-step events)."""
+        solver = ils.Solver(At, p, opts, stream=stream)
+
+        def step():
+            solver.refactor(At, stream=stream)
+            return solver.solve(b, x, tol=TOL_RELRES, stream=stream)
+
+        for _ in range(max(args.warmup, 3)):
+            info = step()
+        torch.cuda.synchronize()
+        relerr = float(np.linalg.norm(x.cpu().numpy() - xs) / np.linalg.norm(xs))
+        if not relerr <= 1e-10:
+            raise SystemExit(f"accuracy gate failed: relerr {relerr:.3e}")
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        phases, infos = [], []
+        sampler = ClockSampler(torch.cuda.current_device()) if (rank == 0 and with_clocks) else None
+        barrier()
+        torch.cuda.synchronize()
+        if sampler:
+            sampler.start()
+        launches0 = ils.binding.kernel_launches()
+        wall0 = time.perf_counter()
+        for i in range(steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            info = step()
+            ev[i][1].record(stream)
+            phases.append(solver.timings())
+            infos.append(info.as_dict())
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+        launches = ils.binding.kernel_launches() - launches0
+        barrier()
+        clocks = sampler.stop() if sampler else None
+        total_s = sum(a.elapsed_time(bb) for a, bb in ev) / 1e3
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([total_s], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_s = float(t.item())
+        ph = {k: statistics.mean(d[k] for d in phases) for k in phases[0]}
+        return dict(solver=solver, total_s=total_s, wall=wall, launches=launches, clocks=clocks, relerr=relerr,
+                    phases=ph, info=infos[-1], steps=steps)
+
+    mixed = measure(ils.options(precision=ils.ILS_FP32_REFINE, timing=1), args.steps, True)
+    plain = measure(ils.options(timing=1), max(3, min(args.steps, 10)), False)
+    solver = mixed["solver"]
+    value = world * args.steps / mixed["total_s"]
+    plain_value = world * plain["steps"] / plain["total_s"]
 
     # ---- end to end through the C ABI with host buffers ----
     A_host = torch.from_numpy(np.ascontiguousarray(inst.A.T)).pin_memory()
@@ -250,9 +262,18 @@ def main():
 
     if rank != 0:
         return
-    gram_avg_ms = statistics.mean(gram_ms)
-    gram_flops = float(p) * n * (n + 1)  # symmetric half of A_1^T A_1: p n (n+1) flops
-    achieved = gram_flops / (gram_avg_ms * 1e-3) / 1e12
+    ms_step = 1e3 * mixed["total_s"] / args.steps
+    ph = mixed["phases"]
+    # Dominant kernel group of the headline step: the FP64 Cholesky factorizations of
+    # A_1^T A_1 and A^T J A (2 n^3 / 3 algorithmic flops), latency-bound FP64 chains.
+    chol_ms = ph["cholesky"]
+    chol_flops = 2.0 * n ** 3 / 3.0
+    chol_ach = chol_flops / (chol_ms * 1e-3) / 1e12
+    # Tensor-core Gram A_1^T A_1: algorithmic p n (n+1) flops (FP64-accurate result).
+    gram_ms = ph["gram1"]
+    gram_flops = float(p) * n * (n + 1)
+    n_tiles = (n + 127) // 128
+    tensor_flops = 2.0 * 128 * 128 * p * (n_tiles * (n_tiles + 1) // 2) * 55  # executed BF16 MMA flops
     cpu_rate, cpu_cnt, cpu_secs = time_oracle(inst, args.cpu_seconds)
     line = {
         "metric": METRIC,
@@ -261,7 +282,7 @@ def main():
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": 1e3 * total_s / args.steps,
+        "ms_per_step": ms_step,
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
@@ -269,26 +290,46 @@ def main():
         "data": "synthetic",
         "config": {
             "workload": WORKLOAD,
-            "method": "SP (Alg. 1), explicit B = P A_2^T A_2",
-            "precision": "fp64",
+            "method": "SP (Alg. 1), mixed precision: tensor-core FP64-accurate Grams, FP64 Cholesky, "
+                      "FP32 sweeps, FP64 residual refinement",
             "tol_relres": TOL_RELRES,
-            "relerr_vs_oracle": relerr,
-            "outer_iters": int(statistics.median(iters)),
+            "relerr_vs_oracle": mixed["relerr"],
+            "refinements": mixed["info"]["refinements"],
+            "sp_sweeps": mixed["info"]["outer_iters"],
+            "setup_phases_ms": {k: round(v, 4) for k, v in ph.items()},
             "l2": "flushed before every step (256 MiB write outside the timed events)",
             "step": "ils_refactor (all setup products) + ils_solve",
-            "wall_s_timed_loop": wall,
+            "wall_s_timed_loop": mixed["wall"],
+        },
+        "plain_fp64_sp": {
+            "value": plain_value, "unit": "solves/s", "ms_per_step": 1e3 * plain["total_s"] / plain["steps"],
+            "steps": plain["steps"], "relerr_vs_oracle": plain["relerr"], "outer_iters": plain["info"]["outer_iters"],
+            "setup_phases_ms": {k: round(v, 4) for k, v in plain["phases"].items()},
+            "speedup_of_headline": value / plain_value,
         },
         "roofline": {
-            "kernel": "gemm_tn_kernel (A_1^T A_1 Gram, FP64 FMA, incl. split-K reduce)",
+            "kernel": "FP64 Cholesky of A_1^T A_1 and A^T J A (potrf_diag + trsm_panel + syrk_trailing)",
             "bound": "alu",
-            "achieved": achieved,
+            "achieved": chol_ach,
             "peak": FP64_PEAK_TFLOPS,
             "peak_source": "nominal FP64 rate of the profiling recipe (FP64 is absent from MEASURED_PEAKS.json)",
             "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS,
+            "frac": chol_ach / FP64_PEAK_TFLOPS,
             "traffic": None,
-            "kernel_ms": gram_avg_ms,
-            "share_of_step": gram_avg_ms / (1e3 * total_s / args.steps),
+            "kernel_ms": chol_ms,
+            "share_of_step": chol_ms / ms_step,
+            "note": "latency-bound: 64-cycle dependent FP64 FMA and 440-cycle FP64 rsqrt on the pivot chain",
+        },
+        "roofline_tensor_gram": {
+            "kernel": "gram_split_mma_kernel + digit split + reduce (A_1^T A_1 to FP64 accuracy)",
+            "bound": "tensor",
+            "achieved": tensor_flops / (gram_ms * 1e-3) / 1e12,
+            "peak": BF16_PEAK_TFLOPS,
+            "unit": "TFLOP/s (executed BF16 MMA flops)",
+            "frac": tensor_flops / (gram_ms * 1e-3) / 1e12 / BF16_PEAK_TFLOPS,
+            "fp64_equivalent_tflops": gram_flops / (gram_ms * 1e-3) / 1e12,
+            "kernel_ms": gram_ms,
+            "share_of_step": gram_ms / ms_step,
         },
         "cpu_baseline": {
             "value": cpu_rate, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
@@ -296,11 +337,12 @@ def main():
                       "with the default BLAS thread count)",
         },
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": int(launches),
-        "clocks": clocks,
+        "gpu_launches": int(mixed["launches"]),
+        "clocks": mixed["clocks"],
     }
     print(json.dumps(line), flush=True)
-    solver.close()
+    mixed["solver"].close()
+    plain["solver"].close()
 
 
 if __name__ == "__main__":

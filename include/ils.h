@@ -155,6 +155,42 @@ int ils_get_timings(ils_handle h, double* out, int count);
  * (all handles, all threads).  Host only. */
 int64_t ils_kernel_launches(void);
 
+/* ---- Batches of independent problems (uneven m, n, p, q) ---------------------------------- */
+
+typedef struct ils_batch_s* ils_batch;
+
+/* One problem of a batch: A is m x n, column-major, leading dimension lda >= m, FP64,
+ * device memory; rows 0..p-1 form A_1 and rows p..m-1 form A_2. */
+typedef struct {
+  int64_t m, n, p, q;
+  const double* A;
+  int64_t lda;
+} ils_problem;
+
+/* Set up `count` independent problems (probs is a host array) with the same options.
+ * Each problem is set up exactly as by ils_setup; the problems' kernels are spread over
+ * internal streams so they run concurrently, ordered after the work already on `stream`;
+ * the call returns when every setup has finished.  On any failure nothing is kept and the
+ * first failing status is returned (INVALID_ARG, OOM, CUDA, NOT_SPD, NONFINITE). */
+ils_status ils_batch_setup(ils_batch* b, int64_t count, const ils_problem* probs, const ils_options* o,
+                           ils_stream_t stream);
+
+/* Solve k right-hand sides for every problem of the batch.  B and X are host arrays of
+ * `count` device pointers: B[i] is m_i x k (leading dimension ldb[i] >= m_i, or m_i when
+ * ldb is NULL) and X[i] is n_i x k (ldx[i] >= n_i, or n_i when ldx is NULL).  x0_zero and
+ * tol as in ils_solve_many.  infos [host, may be NULL] receives one ils_info per problem.
+ * The work is ordered after `stream` and `stream` waits for it; the call synchronizes.
+ * Returns ILS_OK or the first non-OK problem status. */
+ils_status ils_batch_solve(ils_batch b, int64_t k, const double* const* B, const int64_t* ldb, double* const* X,
+                           const int64_t* ldx, int x0_zero, double tol, ils_info* infos, ils_stream_t stream);
+
+/* The handle of problem i (owned by the batch; for ils_get_matrix and diagnostics), or
+ * NULL when i is out of range. */
+ils_handle ils_batch_handle(ils_batch b, int64_t i);
+
+/* Release the batch and every handle it owns.  NULL is ignored. */
+void ils_batch_destroy(ils_batch b);
+
 /* Gram product C = X^T X (FP64) without any device allocation.  The paper has no
  * counterpart; this entry point exists for callers that cannot call cudaMalloc (for
  * example code that runs under stream capture with allocation forbidden, or inside a

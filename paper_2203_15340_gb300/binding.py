@@ -53,6 +53,11 @@ class ils_options(ctypes.Structure):
     ]
 
 
+class ils_problem(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("p", ctypes.c_int64), ("q", ctypes.c_int64),
+                ("A", ctypes.c_void_p), ("lda", ctypes.c_int64)]
+
+
 class ils_info(ctypes.Structure):
     _fields_ = [
         ("outer_iters", ctypes.c_int64),
@@ -81,6 +86,13 @@ SIGNATURES = {
     "ils_get_matrix": (ctypes.c_int, [_P, ctypes.c_int, _P, _I64, _P]),
     "ils_get_timings": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
     "ils_kernel_launches": (ctypes.c_int64, []),
+    "ils_batch_setup": (ctypes.c_int, [ctypes.POINTER(_P), _I64, ctypes.POINTER(ils_problem),
+                                       ctypes.POINTER(ils_options), _P]),
+    "ils_batch_solve": (ctypes.c_int, [_P, _I64, ctypes.POINTER(_P), ctypes.POINTER(_I64), ctypes.POINTER(_P),
+                                       ctypes.POINTER(_I64), ctypes.c_int, ctypes.c_double, ctypes.POINTER(ils_info),
+                                       _P]),
+    "ils_batch_handle": (_P, [_P, _I64]),
+    "ils_batch_destroy": (None, [_P]),
     "ils_gram_noalloc": (ctypes.c_int, [_I64, _I64, _P, _I64, _P, _I64, _P]),
     "ils_destroy": (None, [_P]),
     "ils_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -224,6 +236,59 @@ class Solver:
         if getattr(self, "h", None):
             lib().ils_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchSolver:
+    """A batch of independent ILS instances (wraps an ils_batch).
+
+    ``Ats`` is a list of CUDA float64 tensors of shape (n_i, m_i) (A_i column-major) and
+    ``ps`` the list of p_i.
+    """
+
+    def __init__(self, Ats, ps, opts: ils_options | None = None, stream=None):
+        count = len(Ats)
+        probs = (ils_problem * count)()
+        self.shapes = []
+        for i, (At, p) in enumerate(zip(Ats, ps)):
+            n, m = At.shape
+            ptr, lda = _colmajor_ptr(At, m, n)
+            probs[i] = ils_problem(m, n, p, m - p, ptr, lda)
+            self.shapes.append((m, n, p))
+        self._keep = Ats
+        self.opts = opts if opts is not None else options()
+        b = ctypes.c_void_p()
+        _check(lib().ils_batch_setup(ctypes.byref(b), count, probs, ctypes.byref(self.opts), _stream_ptr(stream)),
+               "ils_batch_setup")
+        self.b = b
+        self.count = count
+
+    def solve(self, Bts, Xts, x0_zero=True, tol=1e-12, stream=None, allow=(ILS_OK,)):
+        """Bts[i]: (k, m_i) tensor, Xts[i]: (k, n_i) tensor, column-major views."""
+        count = self.count
+        k = Bts[0].shape[0]
+        Bp = (ctypes.c_void_p * count)()
+        Xp = (ctypes.c_void_p * count)()
+        lb = (ctypes.c_int64 * count)()
+        lx = (ctypes.c_int64 * count)()
+        for i, ((m, n, _), Bt, Xt) in enumerate(zip(self.shapes, Bts, Xts)):
+            Bp[i], lb[i] = _colmajor_ptr(Bt, m, k)
+            Xp[i], lx[i] = _colmajor_ptr(Xt, n, k)
+        infos = (ils_info * count)()
+        code = lib().ils_batch_solve(self.b, k, Bp, lb, Xp, lx, int(bool(x0_zero)), float(tol), infos,
+                                     _stream_ptr(stream))
+        _check(code, "ils_batch_solve", allow)
+        return list(infos)
+
+    def close(self):
+        if getattr(self, "b", None):
+            lib().ils_batch_destroy(self.b)
+            self.b = None
 
     def __del__(self):
         try:

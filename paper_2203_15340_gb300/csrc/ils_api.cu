@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "ils_internal.h"
 
@@ -69,6 +70,13 @@ struct ils_handle_s {
   double* h_bn = nullptr;     // kMaxRhsPerPass
   int64_t* h_iters = nullptr; // kMaxRhsPerPass
   int64_t* h_inner = nullptr; // kMaxRhsPerPass
+  // state of the solve pass in flight (between pass_begin and pass_end)
+  SpIterArgs pa{};
+  RandArgs pra{};
+  MixedArgs pma{};
+  int64_t pass_k = 0;
+  int64_t pass_launched = 0;
+  bool pass_mixed = false;
   // setup phase timing (options.timing != 0)
   cudaEvent_t ev[7] = {};
   double t_ms[6] = {};
@@ -265,10 +273,8 @@ ils_status compute_setup(ils_handle h) {
   ILS_CK(cudaMemcpyAsync(h->h_status, h->dstatus, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   if (h->opt.gram == ILS_GRAM_SPLIT)
     ILS_CK(cudaMemcpyAsync(h->h_status + 1, h->gs_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-  ILS_CK(cudaStreamSynchronize(s));
-  if (h->opt.gram == ILS_GRAM_SPLIT && h->h_status[1] != 0)
-    return h->h_status[1] == 2 ? ILS_ERR_NONFINITE : ILS_ERR_TIMEOUT;
-  if (*h->h_status != 0) return (ils_status)*h->h_status;
+  // P and B are formed without waiting for the pivot status; setup_finish reports it
+  // (products of a rejected matrix are never used).
   if (h->opt.precision != ILS_FP64) {
     // Mixed precision: P and B for the correction sweeps in FP32 (B also in BF16).
     ILS_CK(mixed_setup(n, h->L, h->G2, h->opt.precision, h->L32, h->P32, h->G2_32, h->Bt32, h->Bt16,
@@ -283,6 +289,15 @@ ils_status compute_setup(ils_handle h) {
   return ILS_OK;
 }
 
+// Wait for the setup enqueued by compute_setup and report its pivot / input status.
+ils_status setup_finish(ils_handle h) {
+  ILS_CK(cudaStreamSynchronize(h->stream));
+  h->h_status[1] = h->opt.gram == ILS_GRAM_SPLIT ? h->h_status[1] : 0;
+  if (h->h_status[1] != 0) return h->h_status[1] == 2 ? ILS_ERR_NONFINITE : ILS_ERR_TIMEOUT;
+  if (*h->h_status != 0) return (ils_status)*h->h_status;
+  return ILS_OK;
+}
+
 void free_handle(ils_handle h) {
   if (!h) return;
   if (h->block) cudaFreeAsync(h->block, h->stream);
@@ -292,9 +307,13 @@ void free_handle(ils_handle h) {
   delete h;
 }
 
-// One pass of SP over kk <= kMaxRhsPerPass right-hand sides.
-ils_status sp_pass(ils_handle h, int64_t c0, int64_t kk, const double* B, int64_t ldb, double* X, int64_t ldx,
-                   int x0_zero, double tol, ils_info* agg) {
+// One pass over kk <= kMaxRhsPerPass right-hand sides, in three phases so that many
+// handles can have passes in flight on different streams: pass_begin enqueues A^T J b,
+// the start vector and the device state; pass_launch enqueues outer steps (each returns
+// at once after completion); pass_end synchronizes, launches more steps if needed and
+// collects the results.
+ils_status pass_begin(ils_handle h, int64_t c0, int64_t kk, const double* B, int64_t ldb, const double* X,
+                      int64_t ldx, int x0_zero, double tol) {
   const int method = h->opt.method;
   cudaStream_t s = h->stream;
   const int64_t m = h->m, n = h->n, p = h->p;
@@ -375,21 +394,48 @@ ils_status sp_pass(ils_handle h, int64_t c0, int64_t kk, const double* B, int64_
   ma.X1 = h->X1;
   ma.col_done = h->col_done;
   ma.st = h->st;
-  // Launch the outer step in growing chunks; launches after convergence return at once.
-  int64_t launched = 0, chunk = (method == ILS_SP && !mixed) ? 16 : 4;
+  h->pa = a;
+  h->pra = ra;
+  h->pma = ma;
+  h->pass_k = kk;
+  h->pass_launched = 0;
+  h->pass_mixed = mixed;
+  return ILS_OK;
+}
+
+// Enqueue up to `count` more outer steps of the pass in flight (never past max_outer + 1).
+ils_status pass_launch(ils_handle h, int64_t count) {
+  cudaStream_t s = h->stream;
+  const int method = h->opt.method;
   const int64_t cap = h->opt.max_outer + 1;
+  const int64_t todo = std::min(count, cap - h->pass_launched);
+  for (int64_t i = 0; i < todo; ++i) {
+    ILS_CK(sp_iterate_f64(h->pa, s));
+    if (h->pass_mixed) ILS_CK(mixed_correct(h->pma, h->opt.precision, s));
+    else if (method != ILS_SP) ILS_CK(rand_chain_f64(h->pra, method, s));
+  }
+  h->pass_launched += todo;
+  return ILS_OK;
+}
+
+int64_t first_chunk(ils_handle h) {
+  if (h->opt.precision != ILS_FP64) return 6;
+  return h->opt.method == ILS_SP ? 16 : 4;
+}
+
+ils_status pass_end(ils_handle h, double* X, int64_t ldx, ils_info* agg) {
+  cudaStream_t s = h->stream;
+  const int64_t n = h->n, kk = h->pass_k;
+  const bool mixed = h->pass_mixed;
+  const int64_t cap = h->opt.max_outer + 1;
+  int64_t chunk = std::max<int64_t>(first_chunk(h), 1);
   for (;;) {
-    const int64_t todo = std::min(chunk, cap - launched);
-    for (int64_t i = 0; i < todo; ++i) {
-      ILS_CK(sp_iterate_f64(a, s));
-      if (mixed) ILS_CK(mixed_correct(ma, h->opt.precision, s));
-      else if (method != ILS_SP) ILS_CK(rand_chain_f64(ra, method, s));
-    }
-    launched += todo;
     ILS_CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
     ILS_CK(cudaStreamSynchronize(s));
-    if (h->h_st->done || launched >= cap) break;
+    if (h->h_st->done || h->pass_launched >= cap) break;
     chunk = std::min<int64_t>(chunk * 2, 1024);
+    ils_status st = pass_launch(h, chunk);
+    if (st != ILS_OK) return st;
   }
   if (!h->h_st->done) return ILS_ERR_TIMEOUT;  // cannot happen: the cap launch always finishes
   ILS_CK(copy_final_f64(n, kk, h->X0, h->X1, h->st, X, ldx, s));
@@ -405,7 +451,7 @@ ils_status sp_pass(ils_handle h, int64_t c0, int64_t kk, const double* B, int64_
     if (rel != rel) agg->relres = rel;
     if (mixed) {
       agg->refinements = std::max<int64_t>(agg->refinements, h->h_iters[c]);
-      agg->outer_iters = std::max<int64_t>(agg->outer_iters, h->h_iters[c] * ma.sweeps);
+      agg->outer_iters = std::max<int64_t>(agg->outer_iters, h->h_iters[c] * h->pma.sweeps);
     } else {
       agg->outer_iters = std::max<int64_t>(agg->outer_iters, h->h_iters[c]);
     }
@@ -413,6 +459,73 @@ ils_status sp_pass(ils_handle h, int64_t c0, int64_t kk, const double* B, int64_
   }
   const int32_t st = h->h_st->status;
   if (st != 0 && agg->status == 0) agg->status = st;
+  return ILS_OK;
+}
+
+ils_status sp_pass(ils_handle h, int64_t c0, int64_t kk, const double* B, int64_t ldb, double* X, int64_t ldx,
+                   int x0_zero, double tol, ils_info* agg) {
+  ils_status st = pass_begin(h, c0, kk, B, ldb, X, ldx, x0_zero, tol);
+  if (st != ILS_OK) return st;
+  if ((st = pass_launch(h, first_chunk(h))) != ILS_OK) return st;
+  return pass_end(h, X, ldx, agg);
+}
+
+// Validate a problem, allocate its handle and carve its device memory (stream-ordered
+// on `stream`); nothing is computed yet.
+ils_status create_handle(ils_handle* out, int64_t m, int64_t n, int64_t p, int64_t q, const double* A, int64_t lda,
+                         const ils_options* o, cudaStream_t stream) {
+  *out = nullptr;
+  if (n < 1 || n > kMaxN || p < n || q < 0 || m != p + q || lda < m || !A || m > ((int64_t)1 << 31))
+    return ILS_ERR_INVALID_ARG;
+  ils_options opt;
+  if (o) opt = *o;
+  else ils_options_default(&opt);
+  if (validate_options(&opt) != ILS_OK) return ILS_ERR_INVALID_ARG;
+  if (opt.precision != ILS_FP64) {
+    if (opt.method != ILS_SP) return ILS_ERR_INVALID_ARG;  // mixed precision refines the SP method
+    opt.gram = ILS_GRAM_SPLIT;  // the FP64 refinement needs FP64-accurate Grams; these are the fast ones
+  }
+  if (opt.sweeps < 0) return ILS_ERR_INVALID_ARG;
+  ils_handle h = new (std::nothrow) ils_handle_s();
+  if (!h) return ILS_ERR_OOM;
+  h->m = m;
+  h->n = n;
+  h->p = p;
+  h->q = q;
+  h->opt = opt;
+  h->stream = stream;
+  const size_t work = setup_work_elems(m, n, p, q);
+  Carver dry{nullptr, 0, true};
+  carve(h, dry, work);
+  h->block_bytes = dry.off;
+  if (cudaMallocAsync(&h->block, h->block_bytes, h->stream) != cudaSuccess) {
+    cudaGetLastError();
+    h->block = nullptr;
+    free_handle(h);
+    return ILS_ERR_OOM;
+  }
+  Carver real{(char*)h->block, 0, false};
+  carve(h, real, work);
+  const size_t host_bytes = align_up(sizeof(SolveState)) + align_up(sizeof(int32_t)) +
+                            4 * align_up(sizeof(double) * kMaxRhsPerPass);
+  char* hb = nullptr;
+  if (cudaMallocHost((void**)&hb, host_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    free_handle(h);
+    return ILS_ERR_OOM;
+  }
+  h->h_st = (SolveState*)hb;
+  hb += align_up(sizeof(SolveState));
+  h->h_status = (int32_t*)hb;
+  hb += align_up(sizeof(int32_t));
+  h->h_rr = (double*)hb;
+  hb += align_up(sizeof(double) * kMaxRhsPerPass);
+  h->h_bn = (double*)hb;
+  hb += align_up(sizeof(double) * kMaxRhsPerPass);
+  h->h_iters = (int64_t*)hb;
+  hb += align_up(sizeof(double) * kMaxRhsPerPass);
+  h->h_inner = (int64_t*)hb;
+  *out = h;
   return ILS_OK;
 }
 
@@ -453,57 +566,10 @@ ils_status ils_setup(ils_handle* out, int64_t m, int64_t n, int64_t p, int64_t q
                      const ils_options* o, ils_stream_t stream) {
   if (!out) return ILS_ERR_INVALID_ARG;
   *out = nullptr;
-  if (n < 1 || n > kMaxN || p < n || q < 0 || m != p + q || lda < m || !A || m > ((int64_t)1 << 31))
-    return ILS_ERR_INVALID_ARG;
-  ils_options opt;
-  if (o) opt = *o;
-  else ils_options_default(&opt);
-  if (validate_options(&opt) != ILS_OK) return ILS_ERR_INVALID_ARG;
-  if (opt.precision != ILS_FP64) {
-    if (opt.method != ILS_SP) return ILS_ERR_INVALID_ARG;  // mixed precision refines the SP method
-    opt.gram = ILS_GRAM_SPLIT;  // the FP64 refinement needs FP64-accurate Grams; these are the fast ones
-  }
-  if (opt.sweeps < 0) return ILS_ERR_INVALID_ARG;
-  ils_handle h = new (std::nothrow) ils_handle_s();
-  if (!h) return ILS_ERR_OOM;
-  h->m = m;
-  h->n = n;
-  h->p = p;
-  h->q = q;
-  h->opt = opt;
-  h->stream = (cudaStream_t)stream;
-  const size_t work = setup_work_elems(m, n, p, q);
-  Carver dry{nullptr, 0, true};
-  carve(h, dry, work);
-  h->block_bytes = dry.off;
-  if (cudaMallocAsync(&h->block, h->block_bytes, h->stream) != cudaSuccess) {
-    cudaGetLastError();
-    h->block = nullptr;
-    free_handle(h);
-    return ILS_ERR_OOM;
-  }
-  Carver real{(char*)h->block, 0, false};
-  carve(h, real, work);
-  const size_t host_bytes = align_up(sizeof(SolveState)) + align_up(sizeof(int32_t)) +
-                            4 * align_up(sizeof(double) * kMaxRhsPerPass);
-  char* hb = nullptr;
-  if (cudaMallocHost((void**)&hb, host_bytes) != cudaSuccess) {
-    cudaGetLastError();
-    free_handle(h);
-    return ILS_ERR_OOM;
-  }
-  h->h_st = (SolveState*)hb;
-  hb += align_up(sizeof(SolveState));
-  h->h_status = (int32_t*)hb;
-  hb += align_up(sizeof(int32_t));
-  h->h_rr = (double*)hb;
-  hb += align_up(sizeof(double) * kMaxRhsPerPass);
-  h->h_bn = (double*)hb;
-  hb += align_up(sizeof(double) * kMaxRhsPerPass);
-  h->h_iters = (int64_t*)hb;
-  hb += align_up(sizeof(double) * kMaxRhsPerPass);
-  h->h_inner = (int64_t*)hb;
-  ils_status st = ils_refactor(h, A, lda, stream);
+  ils_handle h = nullptr;
+  ils_status st = create_handle(&h, m, n, p, q, A, lda, o, (cudaStream_t)stream);
+  if (st != ILS_OK) return st;
+  st = ils_refactor(h, A, lda, stream);
   if (st != ILS_OK) {
     free_handle(h);
     return st;
@@ -520,10 +586,8 @@ ils_status ils_refactor(ils_handle h, const double* A, int64_t lda, ils_stream_t
   ILS_CK(cudaMemcpy2DAsync(h->A, sizeof(double) * h->m, A, sizeof(double) * lda, sizeof(double) * h->m, h->n,
                            cudaMemcpyDeviceToDevice, s));
   ils_status st = compute_setup(h);
-  if (st == ILS_OK && h->opt.timing) {
-    if (cudaStreamSynchronize(s) != cudaSuccess) return ILS_ERR_CUDA;
-    collect_timings(h);
-  }
+  if (st == ILS_OK) st = setup_finish(h);
+  if (st == ILS_OK && h->opt.timing) collect_timings(h);
   return st;
 }
 
@@ -585,5 +649,138 @@ ils_status ils_get_matrix(ils_handle h, int which, double* dst, int64_t ldd, ils
 }
 
 void ils_destroy(ils_handle h) { free_handle(h); }
+
+// ---------------------------------------------------------------------------------------
+// Batches of independent problems: each problem keeps its own handle; handles are spread
+// round-robin over internal streams so their kernels run concurrently, and every host
+// synchronization is deferred until all problems have been enqueued.
+// ---------------------------------------------------------------------------------------
+struct ils_batch_s {
+  std::vector<ils_handle> h;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> events;  // one per internal stream (join)
+  cudaEvent_t fork = nullptr;
+};
+
+namespace {
+constexpr int kBatchStreams = 16;
+
+void free_batch(ils_batch b) {
+  if (!b) return;
+  for (ils_handle h : b->h) free_handle(h);
+  for (cudaStream_t s : b->streams) {
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+  }
+  for (cudaEvent_t e : b->events) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  delete b;
+}
+
+// Internal streams wait for the caller's stream (fork); the caller's stream waits for
+// the internal streams (join).
+cudaError_t batch_fork(ils_batch b, cudaStream_t user) {
+  cudaError_t e = cudaEventRecord(b->fork, user);
+  for (size_t i = 0; e == cudaSuccess && i < b->streams.size(); ++i) e = cudaStreamWaitEvent(b->streams[i], b->fork, 0);
+  return e;
+}
+
+cudaError_t batch_join(ils_batch b, cudaStream_t user) {
+  cudaError_t e = cudaSuccess;
+  for (size_t i = 0; e == cudaSuccess && i < b->streams.size(); ++i) {
+    e = cudaEventRecord(b->events[i], b->streams[i]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(user, b->events[i], 0);
+  }
+  return e;
+}
+}  // namespace
+
+ils_status ils_batch_setup(ils_batch* out, int64_t count, const ils_problem* probs, const ils_options* o,
+                           ils_stream_t stream) {
+  if (!out) return ILS_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (count < 1 || !probs) return ILS_ERR_INVALID_ARG;
+  ils_batch b = new (std::nothrow) ils_batch_s();
+  if (!b) return ILS_ERR_OOM;
+  const int ns = (int)std::min<int64_t>(count, kBatchStreams);
+  b->streams.assign(ns, nullptr);
+  b->events.assign(ns, nullptr);
+  bool ok = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; ok && i < ns; ++i)
+    ok = cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->events[i], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok || batch_fork(b, (cudaStream_t)stream) != cudaSuccess) {
+    cudaGetLastError();
+    free_batch(b);
+    return ILS_ERR_CUDA;
+  }
+  b->h.assign(count, nullptr);
+  ils_status st = ILS_OK;
+  for (int64_t i = 0; i < count && st == ILS_OK; ++i) {
+    const ils_problem& pr = probs[i];
+    cudaStream_t s = b->streams[i % ns];
+    st = create_handle(&b->h[i], pr.m, pr.n, pr.p, pr.q, pr.A, pr.lda, o, s);
+    if (st != ILS_OK) break;
+    ils_handle h = b->h[i];
+    if (cudaMemcpy2DAsync(h->A, sizeof(double) * h->m, pr.A, sizeof(double) * pr.lda, sizeof(double) * h->m, h->n,
+                          cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+      cudaGetLastError();
+      st = ILS_ERR_CUDA;
+      break;
+    }
+    st = compute_setup(h);
+  }
+  for (int64_t i = 0; i < count && st == ILS_OK; ++i) st = setup_finish(b->h[i]);
+  if (st == ILS_OK && batch_join(b, (cudaStream_t)stream) != cudaSuccess) st = ILS_ERR_CUDA;
+  if (st != ILS_OK) {
+    free_batch(b);
+    return st;
+  }
+  *out = b;
+  return ILS_OK;
+}
+
+ils_status ils_batch_solve(ils_batch b, int64_t k, const double* const* B, const int64_t* ldb, double* const* X,
+                           const int64_t* ldx, int x0_zero, double tol, ils_info* infos, ils_stream_t stream) {
+  if (!b || k < 0 || !(tol >= 0.0) || (k > 0 && (!B || !X))) return ILS_ERR_INVALID_ARG;
+  const int64_t count = (int64_t)b->h.size();
+  for (int64_t i = 0; i < count && k > 0; ++i) {
+    const int64_t lb = ldb ? ldb[i] : b->h[i]->m, lx = ldx ? ldx[i] : b->h[i]->n;
+    if (!B[i] || !X[i] || lb < b->h[i]->m || lx < b->h[i]->n) return ILS_ERR_INVALID_ARG;
+  }
+  std::vector<ils_info> agg(count);
+  for (auto& a : agg) std::memset(&a, 0, sizeof(a));
+  if (batch_fork(b, (cudaStream_t)stream) != cudaSuccess) return ILS_ERR_CUDA;
+  ils_status worst = ILS_OK;
+  for (int64_t c0 = 0; c0 < k; c0 += kMaxRhsPerPass) {
+    const int64_t kk = std::min<int64_t>(kMaxRhsPerPass, k - c0);
+    for (int64_t i = 0; i < count; ++i) {
+      ils_handle h = b->h[i];
+      const int64_t lb = ldb ? ldb[i] : h->m, lx = ldx ? ldx[i] : h->n;
+      ils_status st = pass_begin(h, c0, kk, B[i] + c0 * lb, lb, X[i] + c0 * lx, lx, x0_zero, tol);
+      if (st == ILS_OK) st = pass_launch(h, first_chunk(h));
+      if (st != ILS_OK) return st;
+    }
+    for (int64_t i = 0; i < count; ++i) {
+      ils_handle h = b->h[i];
+      const int64_t lx = ldx ? ldx[i] : h->n;
+      ils_status st = pass_end(h, X[i] + c0 * lx, lx, &agg[i]);
+      if (st != ILS_OK) return st;
+    }
+  }
+  if (batch_join(b, (cudaStream_t)stream) != cudaSuccess) return ILS_ERR_CUDA;
+  for (int64_t i = 0; i < count; ++i) {
+    if (infos) infos[i] = agg[i];
+    if (agg[i].status != ILS_OK && worst == ILS_OK) worst = (ils_status)agg[i].status;
+  }
+  return worst;
+}
+
+ils_handle ils_batch_handle(ils_batch b, int64_t i) {
+  if (!b || i < 0 || i >= (int64_t)b->h.size()) return nullptr;
+  return b->h[i];
+}
+
+void ils_batch_destroy(ils_batch b) { free_batch(b); }
 
 }  // extern "C"
