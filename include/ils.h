@@ -191,6 +191,49 @@ ils_handle ils_batch_handle(ils_batch b, int64_t i);
 /* Release the batch and every handle it owns.  NULL is ignored. */
 void ils_batch_destroy(ils_batch b);
 
+/* ---- Learned warm start ---------------------------------------------------------------------
+ * A three-layer perceptron x0 = net(theta) for parametric right-hand sides b(theta):
+ *   z1 = W1 theta + b1, h1 = gelu(z1), z2 = W2 h1 + b2, h2 = gelu(z2), y = W3 h2 + b3,
+ *   x0 = mu + sigma * y  (mu, sigma: per-coordinate mean and deviation of the training
+ *   targets), gelu(z) = z Phi(z).  The paper has no counterpart.  Weights are FP32 and
+ *   trained on the GPU by this library's kernels (mean-squared error on standardized
+ *   targets, Adam); inference runs in BF16 or FP32.  Parameters are stored flat: W1
+ *   (d_hidden x d_in, row-major), b1, W2 (d_hidden x d_hidden), b2, W3 (d_out x d_hidden),
+ *   b3.  Samples are contiguous: theta is d_in x count and targets/outputs d_out x count,
+ *   column-major. */
+typedef struct ils_mlp_s* ils_mlp;
+
+/* New network with weights and biases ~ U(-1/sqrt(fan_in), 1/sqrt(fan_in)) drawn from
+ * Philox4x32-10 keyed by `seed`; mu = 0, sigma = 1.  Errors: INVALID_ARG, OOM, CUDA. */
+ils_status ils_mlp_create(ils_mlp* net, int64_t d_in, int64_t d_hidden, int64_t d_out, uint64_t seed,
+                          ils_stream_t stream);
+/* Number of FP32 parameters (-1 for NULL). */
+int64_t ils_mlp_num_params(ils_mlp net);
+/* Copy the flat FP32 parameters to / from device memory. */
+ils_status ils_mlp_get_params(ils_mlp net, float* dst, ils_stream_t stream);
+ils_status ils_mlp_set_params(ils_mlp net, const float* src, ils_stream_t stream);
+/* Mean over count x d_out entries of (y - (T - mu)/sigma)^2 for 1 <= count <= 1024 samples
+ * (loss, host, FP64) and its gradient with respect to the flat parameters (grad, device,
+ * FP32).  Synchronizes the stream. */
+ils_status ils_mlp_loss_grad(ils_mlp net, int64_t count, const float* theta, const double* T, double* loss,
+                             float* grad, ils_stream_t stream);
+/* Set mu, sigma from the targets T (d_out x count, FP64) and run `epochs` passes of Adam
+ * (lr; beta1 0.9, beta2 0.999, eps 1e-8) over minibatches of `batch` <= 1024 consecutive
+ * samples.  final_loss [host, may be NULL]: loss of the last minibatch seen.  Synchronizes. */
+ils_status ils_mlp_train(ils_mlp net, int64_t count, const float* theta, const double* T, int64_t epochs,
+                         int64_t batch, double lr, double* final_loss, ils_stream_t stream);
+/* X(:, i) = net(theta(:, i)) for count samples (X d_out x count, ldx >= d_out, FP64);
+ * bf16 != 0 runs the layers in BF16 with FP32 accumulation.  Non-finite outputs are 0. */
+ils_status ils_mlp_forward(ils_mlp net, int64_t count, const float* theta, double* X, int64_t ldx, int bf16,
+                           ils_stream_t stream);
+/* Solve for k parametric right-hand sides B(:, i) = b(theta(:, i)) starting from the
+ * network's prediction (BF16 inference), as ils_solve_many with x0 = net(theta).  Since the
+ * iteration converges from any start, the prediction only changes the iteration count.
+ * Requires d_in of the net = rows of theta and d_out = n. */
+ils_status ils_solve_param(ils_handle h, ils_mlp net, int64_t k, const float* theta, const double* B, int64_t ldb,
+                           double* X, int64_t ldx, double tol, ils_info* info, ils_stream_t stream);
+void ils_mlp_destroy(ils_mlp net);
+
 /* Gram product C = X^T X (FP64) without any device allocation.  The paper has no
  * counterpart; this entry point exists for callers that cannot call cudaMalloc (for
  * example code that runs under stream capture with allocation forbidden, or inside a

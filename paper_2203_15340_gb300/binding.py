@@ -93,6 +93,17 @@ SIGNATURES = {
                                        _P]),
     "ils_batch_handle": (_P, [_P, _I64]),
     "ils_batch_destroy": (None, [_P]),
+    "ils_mlp_create": (ctypes.c_int, [ctypes.POINTER(_P), _I64, _I64, _I64, ctypes.c_uint64, _P]),
+    "ils_mlp_num_params": (_I64, [_P]),
+    "ils_mlp_get_params": (ctypes.c_int, [_P, _P, _P]),
+    "ils_mlp_set_params": (ctypes.c_int, [_P, _P, _P]),
+    "ils_mlp_loss_grad": (ctypes.c_int, [_P, _I64, _P, _P, ctypes.POINTER(ctypes.c_double), _P, _P]),
+    "ils_mlp_train": (ctypes.c_int, [_P, _I64, _P, _P, _I64, _I64, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                                     _P]),
+    "ils_mlp_forward": (ctypes.c_int, [_P, _I64, _P, _P, _I64, ctypes.c_int, _P]),
+    "ils_solve_param": (ctypes.c_int, [_P, _P, _I64, _P, _P, _I64, _P, _I64, ctypes.c_double,
+                                       ctypes.POINTER(ils_info), _P]),
+    "ils_mlp_destroy": (None, [_P]),
     "ils_gram_noalloc": (ctypes.c_int, [_I64, _I64, _P, _I64, _P, _I64, _P]),
     "ils_destroy": (None, [_P]),
     "ils_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -289,6 +300,66 @@ class BatchSolver:
         if getattr(self, "b", None):
             lib().ils_batch_destroy(self.b)
             self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class WarmStartNet:
+    """The warm-start perceptron (wraps an ils_mlp).  Tensors are CUDA tensors: theta
+    (count, d_in) float32, targets/outputs (count, d_out) float64 (sample-major rows)."""
+
+    def __init__(self, d_in, d_hidden, d_out, seed=0, stream=None):
+        h = ctypes.c_void_p()
+        _check(lib().ils_mlp_create(ctypes.byref(h), d_in, d_hidden, d_out, seed, _stream_ptr(stream)),
+               "ils_mlp_create")
+        self.h = h
+        self.d_in, self.d_hidden, self.d_out = d_in, d_hidden, d_out
+
+    @property
+    def num_params(self):
+        return int(lib().ils_mlp_num_params(self.h))
+
+    def get_params(self, out, stream=None):
+        return _check(lib().ils_mlp_get_params(self.h, out.data_ptr(), _stream_ptr(stream)), "ils_mlp_get_params")
+
+    def set_params(self, src, stream=None):
+        return _check(lib().ils_mlp_set_params(self.h, src.data_ptr(), _stream_ptr(stream)), "ils_mlp_set_params")
+
+    def loss_grad(self, theta, T, grad, stream=None):
+        loss = ctypes.c_double()
+        _check(lib().ils_mlp_loss_grad(self.h, theta.shape[0], theta.data_ptr(), T.data_ptr(), ctypes.byref(loss),
+                                       grad.data_ptr(), _stream_ptr(stream)), "ils_mlp_loss_grad")
+        return loss.value
+
+    def train(self, theta, T, epochs, batch=256, lr=1e-3, stream=None):
+        loss = ctypes.c_double()
+        _check(lib().ils_mlp_train(self.h, theta.shape[0], theta.data_ptr(), T.data_ptr(), epochs, batch, lr,
+                                   ctypes.byref(loss), _stream_ptr(stream)), "ils_mlp_train")
+        return loss.value
+
+    def forward(self, theta, X, bf16=True, stream=None):
+        return _check(lib().ils_mlp_forward(self.h, theta.shape[0], theta.data_ptr(), X.data_ptr(), X.stride(0),
+                                            int(bool(bf16)), _stream_ptr(stream)), "ils_mlp_forward")
+
+    def solve(self, solver, theta, Bt, Xt, tol=1e-12, stream=None, allow=(ILS_OK,)):
+        """ils_solve_param: x0 = net(theta), then the solver's iteration."""
+        k = Bt.shape[0]
+        bp, ldb = _colmajor_ptr(Bt, solver.m, k)
+        xp, ldx = _colmajor_ptr(Xt, solver.n, k)
+        info = ils_info()
+        code = lib().ils_solve_param(solver.h, self.h, k, theta.data_ptr(), bp, ldb, xp, ldx, float(tol),
+                                     ctypes.byref(info), _stream_ptr(stream))
+        _check(code, "ils_solve_param", allow)
+        return info
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ils_mlp_destroy(self.h)
+            self.h = None
 
     def __del__(self):
         try:
