@@ -81,7 +81,12 @@ typedef struct {
                           (alpha = n, the Motzkin rule).  SP-RK-RGS: 2 = draw j2 = j1 (SP-RCD) */
   int32_t sweeps;      /* mixed precision: SP sweeps per FP64 refinement step; 0 = 3 */
   uint64_t seed;       /* Philox4x32-10 key for the randomized methods */
+  int32_t route;       /* SP only: 0 auto, 1 explicit B = P Abar2, 2 matrix-free (stream A_2 every
+                          step, never form Abar2; n <= 512).  Auto picks matrix-free when q > 32 n. */
+  int32_t reserved2;
 } ils_options;
+
+typedef enum { ILS_ROUTE_AUTO = 0, ILS_ROUTE_EXPLICIT = 1, ILS_ROUTE_MATRIX_FREE = 2 } ils_route;
 
 typedef struct {
   int64_t outer_iters;  /* IT in the paper's tables (mixed precision: total SP sweeps) */
@@ -252,9 +257,20 @@ void ils_mlp_destroy(ils_mlp net);
 ils_status ils_gram_noalloc(int64_t K, int64_t n, const double* X, int64_t ldx, double* C, int64_t ldc,
                             ils_stream_t stream);
 
+/* v = A_2^T (A_2 x) for one vector (length n in, length n out, FP64, device) by the
+ * handle's one-pass stream over its row-major copy of A_2: prec 0 streams the FP64 copy,
+ * 1 the FP32 copy, 2 the BF16 copy (FP32 accumulation); the copy must exist (matrix-free
+ * route; the low-precision copy in the matching mixed precision).  For tests and
+ * bandwidth measurements.  Errors: INVALID_ARG, CUDA. */
+ils_status ils_aq_product(ils_handle h, const double* x, double* v, int prec, ils_stream_t stream);
+
 /* Release everything the handle owns (stream-ordered on the stream it was
  * created with).  NULL is ignored. */
 void ils_destroy(ils_handle h);
+
+/* Description of the last CUDA failure that made a call of this thread return
+ * ILS_ERR_CUDA (the failing call and the CUDA error string); "" if none.  Host only. */
+const char* ils_last_error(void);
 
 /* Static, human-readable name of a status code.  Host only. */
 const char* ils_status_string(ils_status st);

@@ -31,6 +31,10 @@ ILS_FP64 = 0
 ILS_FP32_REFINE = 1
 ILS_BF16_REFINE = 2
 
+ILS_ROUTE_AUTO = 0
+ILS_ROUTE_EXPLICIT = 1
+ILS_ROUTE_MATRIX_FREE = 2
+
 ILS_GRAM_FP64 = 0
 ILS_GRAM_SPLIT = 1
 
@@ -50,6 +54,8 @@ class ils_options(ctypes.Structure):
         ("scd_sampler", ctypes.c_int32),
         ("sweeps", ctypes.c_int32),
         ("seed", ctypes.c_uint64),
+        ("route", ctypes.c_int32),
+        ("reserved2", ctypes.c_int32),
     ]
 
 
@@ -84,6 +90,7 @@ SIGNATURES = {
     "ils_solve_many": (ctypes.c_int, [_P, _I64, _P, _I64, _P, _I64, ctypes.c_int, ctypes.c_double,
                                       ctypes.POINTER(ils_info), _P]),
     "ils_get_matrix": (ctypes.c_int, [_P, ctypes.c_int, _P, _I64, _P]),
+    "ils_aq_product": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
     "ils_get_timings": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
     "ils_kernel_launches": (ctypes.c_int64, []),
     "ils_batch_setup": (ctypes.c_int, [ctypes.POINTER(_P), _I64, ctypes.POINTER(ils_problem),
@@ -107,6 +114,7 @@ SIGNATURES = {
     "ils_gram_noalloc": (ctypes.c_int, [_I64, _I64, _P, _I64, _P, _I64, _P]),
     "ils_destroy": (None, [_P]),
     "ils_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "ils_last_error": (ctypes.c_char_p, []),
 }
 
 _lib = None
@@ -140,7 +148,10 @@ def status_string(code: int) -> str:
 
 class ILSError(RuntimeError):
     def __init__(self, code: int, where: str):
-        super().__init__(f"{where}: {status_string(code)} (status {code})")
+        detail = ""
+        if code == ILS_ERR_CUDA:
+            detail = " [" + lib().ils_last_error().decode(errors="replace") + "]"
+        super().__init__(f"{where}: {status_string(code)} (status {code}){detail}")
         self.code = code
 
 
@@ -231,6 +242,11 @@ class Solver:
                                     ctypes.byref(info), _stream_ptr(stream))
         _check(code, "ils_solve_many", allow)
         return info
+
+    def aq_product(self, x, v, prec=0, stream=None):
+        """v = A_2^T (A_2 x) by the one-pass stream (prec 0 FP64, 1 FP32, 2 BF16 copy)."""
+        return _check(lib().ils_aq_product(self.h, x.data_ptr(), v.data_ptr(), prec, _stream_ptr(stream)),
+                      "ils_aq_product")
 
     def get_matrix(self, which: int, out, stream=None):
         ptr, ld = _colmajor_ptr(out, self.n, self.n)

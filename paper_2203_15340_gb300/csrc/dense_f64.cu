@@ -652,7 +652,17 @@ __global__ void __launch_bounds__(32 * kIterWarps) sp_iter_kernel(SpIterArgs a) 
 #pragma unroll
     for (int c = 0; c < KR; ++c) ab2[c] = ah2[c] = 0.0;
     int64_t j = lane;
-    if (a.mode != 2) {
+    if (a.mode == 3) {
+      // matrix-free SP: ab = P (v + bbar), ah = Abar1 x
+      for (; j < n; j += 32) {
+        const double bv = brow[j], hv = hrow[j];
+#pragma unroll
+        for (int c = 0; c < KR; ++c) {
+          ab[c] = fma(bv, a.vvec[j + c * n] + a.bbar[j + c * n], ab[c]);
+          ah[c] = fma(hv, x[j + c * n], ah[c]);
+        }
+      }
+    } else if (a.mode != 2 && a.mode != 4) {
       for (; j + 32 < n; j += 64) {
         const double bv = brow[j], hv = hrow[j], bv2 = brow[j + 32], hv2 = hrow[j + 32];
 #pragma unroll
@@ -695,15 +705,17 @@ __global__ void __launch_bounds__(32 * kIterWarps) sp_iter_kernel(SpIterArgs a) 
     }
 #pragma unroll
     for (int c = 0; c < KR; ++c) {
-      const double sb = a.mode != 2 ? warp_sum(ab[c]) : 0.0;
+      const double sb = (a.mode != 2 && a.mode != 4) ? warp_sum(ab[c]) : 0.0;
       const double sh = warp_sum(ah[c]);
       if (lane == 0) {
+        const bool inplace = a.mode == 2 || a.mode == 4;
         if (done_c[c]) {
-          if (a.mode != 2) xn[i + c * n] = x[i + c * n];
+          if (!inplace) xn[i + c * n] = x[i + c * n];
         } else {
-          const double r = a.bbar[i + c * n] - sh;
+          const double r = a.bbar[i + c * n] - sh + ((a.mode >= 3) ? a.vvec[i + c * n] : 0.0);
           if (a.mode == 0) xn[i + c * n] = sb + a.cvec[i + c * n];
           else if (a.mode == 1) a.bhat_out[i + c * n] = sb + a.cvec[i + c * n];
+          else if (a.mode == 3) xn[i + c * n] = sb;
           else a.bhat_out[i + c * n] = r;
           rpart[c] = fma(r, r, rpart[c]);
         }
@@ -756,13 +768,13 @@ __global__ void __launch_bounds__(32 * kIterWarps) sp_iter_kernel(SpIterArgs a) 
     if (all) {
       st->done = 1;  // the answer of every column is in buffer `cur`
     } else {
-      if (a.mode != 2) st->cur = cur ^ 1;  // mode 2 updates x in place
+      if (a.mode != 2 && a.mode != 4) st->cur = cur ^ 1;  // modes 2 and 4 update x in place
       st->iters = it + 1;
     }
     st->counter = 0u;
   }
   __syncthreads();
-  if (!all_done && a.mode != 2) {
+  if (!all_done && a.mode != 2 && a.mode != 4) {
     // Columns that finished now keep x_k: copy it over the x_{k+1} just written.
     for (int c = 0; c < k; ++c) {
       if (!newly_done[c]) continue;
@@ -951,7 +963,7 @@ cudaError_t trsm_binv_t(int64_t n, int64_t k, const T* L, T* Dinv, T* X, int64_t
   constexpr int CT = sizeof(T) == 8 ? 4 : 8;
   const size_t smem = sizeof(T) * (size_t)n * (CT + 32);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
-  if (smem > 48 * 1024) {
+  if (smem > 0) {  // static shared arrays count against the same limit
     e = cudaFuncSetAttribute(trsm_binv_kernel<T, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
@@ -977,7 +989,7 @@ cudaError_t trsm_lower_t(int64_t n, int64_t k, const T* L, T* X, int64_t ldx, bo
     return cudaGetLastError();
   }
   const size_t smem = sizeof(T) * (size_t)n * kTrsmWarps;
-  if (smem > 48 * 1024) {
+  if (smem > 0) {  // static shared arrays count against the same limit
     cudaError_t e = cudaFuncSetAttribute(trsm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }

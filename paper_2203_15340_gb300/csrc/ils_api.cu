@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -56,6 +57,14 @@ struct ils_handle_s {
   float* c32 = nullptr;
   float* d32a = nullptr;
   float* d32b = nullptr;
+  // matrix-free route: row-major copies of A_2 streamed every step
+  bool mf = false;
+  void* Aq64r = nullptr;    // FP64 copy (residuals; plain SP products)
+  void* Aq_lo = nullptr;    // FP32 or BF16 copy (mixed-precision sweeps)
+  void* sp_part = nullptr;  // per-CTA partial products
+  double* vbuf = nullptr;   // n x kMaxRhsPerPass
+  double* d64 = nullptr;    // n x kMaxRhsPerPass
+  float* t32 = nullptr;     // n x kMaxRhsPerPass
   // split tensor-core Gram (options.gram == ILS_GRAM_SPLIT)
   void* gs_slices = nullptr;
   double* gs_partial = nullptr;
@@ -89,10 +98,18 @@ void note_launch(int64_t count) { g_launches.fetch_add(count, std::memory_order_
 
 namespace {
 
-#define ILS_CK(expr)                          \
-  do {                                        \
-    cudaError_t e_ = (expr);                  \
-    if (e_ != cudaSuccess) return ILS_ERR_CUDA; \
+thread_local char g_last_error[256] = "";
+
+ils_status record_cuda_error(cudaError_t e, const char* what, int line) {
+  snprintf(g_last_error, sizeof(g_last_error), "%s (line %d): %s", what, line, cudaGetErrorString(e));
+  cudaGetLastError();
+  return ILS_ERR_CUDA;
+}
+
+#define ILS_CK(expr)                                                     \
+  do {                                                                   \
+    cudaError_t e_ = (expr);                                             \
+    if (e_ != cudaSuccess) return record_cuda_error(e_, #expr, __LINE__); \
   } while (0)
 
 __global__ void init_state_kernel(SolveState* st, int64_t max_outer, int32_t* col_done, int64_t* col_inner,
@@ -168,6 +185,16 @@ void carve(ils_handle h, Carver& c, size_t work_elems) {
   h->vec_in_smem = rkrgs_vec_fits(h->n, h->p);
   const bool need_scratch = h->opt.method == ILS_SP_RK_RGS && !h->vec_in_smem;
   h->vec_scratch = c.take<double>(need_scratch ? (size_t)kMaxRhsPerPass * 2 * (size_t)h->p : 1);
+  if (h->mf) {
+    const size_t rows = (size_t)h->q * (size_t)aq_row_stride(h->n);
+    h->Aq64r = c.take<double>(rows);
+    h->Aq_lo = h->opt.precision == ILS_FP64 ? c.take<uint16_t>(1)
+               : (h->opt.precision == ILS_FP32_REFINE ? (void*)c.take<float>(rows) : (void*)c.take<uint16_t>(rows));
+    h->sp_part = c.take<double>((size_t)aq_stream_blocks() * (size_t)h->n);
+    h->vbuf = c.take<double>(nk);
+    h->d64 = c.take<double>(nk);
+    h->t32 = c.take<float>(nk);
+  }
   if (h->opt.precision != ILS_FP64) {
     const size_t nn = (size_t)h->n * (size_t)h->n;
     h->L32 = c.take<float>(nn);
@@ -236,6 +263,38 @@ void collect_timings(ils_handle h) {
   h->t_ms[5] = el(0, 1);
 }
 
+// Matrix-free route after Abar1: Cholesky of Abar1, P (FP64, or FP32 for the mixed
+// precisions) and the row-major copies of A_2 that every step streams.  Abar2 and H are
+// never formed, so the SPD test of (1.3) reduces to Abar1's pivots; a matrix with
+// rho(B) >= 1 shows up as a residual that does not decrease (NO_CONVERGENCE).
+ils_status compute_setup_mf(ils_handle h) {
+  cudaStream_t s = h->stream;
+  const int64_t m = h->m, n = h->n, p = h->p, q = h->q;
+  ILS_CK(mark(h, 3));
+  ILS_CK(cudaMemcpyAsync(h->L, h->G1, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, s));
+  ILS_CK(cudaMemsetAsync(h->dstatus, 0, sizeof(int32_t), s));
+  {
+    double* mats[2] = {h->L, h->L};
+    double* invd[2] = {h->inv_diag, h->inv_diag};
+    ILS_CK(cholesky_f64_batch(n, 1, mats, invd, h->dstatus, s));
+  }
+  ILS_CK(mark(h, 4));
+  ILS_CK(cudaMemcpyAsync(h->h_status, h->dstatus, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  if (h->opt.gram == ILS_GRAM_SPLIT)
+    ILS_CK(cudaMemcpyAsync(h->h_status + 1, h->gs_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  ILS_CK(aq_copy_rows(q, n, h->A + p, m, h->Aq64r, 0, s));
+  if (h->opt.precision != ILS_FP64) {
+    ILS_CK(aq_copy_rows(q, n, h->A + p, m, h->Aq_lo, h->opt.precision == ILS_FP32_REFINE ? 1 : 2, s));
+    ILS_CK(mixed_setup(n, h->L, nullptr, h->opt.precision, h->L32, h->P32, nullptr, nullptr, nullptr,
+                       reinterpret_cast<float*>(h->Dinv), s));
+  } else {
+    ILS_CK(set_identity_f64(n, h->P, n, s));
+    ILS_CK(trsm_binv_f64(n, n, h->L, h->Dinv, h->P, n, true, true, s));
+  }
+  ILS_CK(mark(h, 5));
+  return ILS_OK;
+}
+
 // All setup products for the current contents of h->A.
 ils_status compute_setup(ils_handle h) {
   cudaStream_t s = h->stream;
@@ -250,6 +309,7 @@ ils_status compute_setup(ils_handle h) {
   }
   ILS_CK(mark(h, 2));
   if (h->opt.method != ILS_SP) ILS_CK(column_cumsum_f64(n, h->G1, h->norms2, h->cum, s));
+  if (h->mf) return compute_setup_mf(h);
   if (h->opt.gram == ILS_GRAM_SPLIT) {
     ILS_CK(gram_split_tc(q, n, h->A + p, m, h->G2, n, h->gs_slices, h->gs_partial, h->gs_exps, h->gs_err, s));
   } else {
@@ -320,7 +380,7 @@ ils_status pass_begin(ils_handle h, int64_t c0, int64_t kk, const double* B, int
   // bbar = A^T J b (Alg. 1 step 4), c = P bbar.
   ILS_CK(rhs_bar_f64(m, n, p, kk, h->A, m, B, ldb, h->bbar, n, s));
   ILS_CK(sq_norms_cols_f64(n, kk, h->bbar, n, h->bnorm2, s));
-  if (h->opt.precision == ILS_FP64) ILS_CK(gemv_cols_f64(n, kk, h->P, n, h->bbar, n, h->cvec, n, s));
+  if (h->opt.precision == ILS_FP64 && !h->mf) ILS_CK(gemv_cols_f64(n, kk, h->P, n, h->bbar, n, h->cvec, n, s));
   if (x0_zero) {
     ILS_CK(cudaMemsetAsync(h->X0, 0, sizeof(double) * n * kk, s));
   } else {
@@ -334,10 +394,11 @@ ils_status pass_begin(ils_handle h, int64_t c0, int64_t kk, const double* B, int
   a.n = n;
   a.k = kk;
   const bool mixed = h->opt.precision != ILS_FP64;
-  a.mode = mixed ? 2 : (method == ILS_SP ? 0 : 1);
+  a.mode = h->mf ? (mixed ? 4 : 3) : (mixed ? 2 : (method == ILS_SP ? 0 : 1));
+  a.vvec = h->vbuf;
   a.pad = 0;
-  a.Bt = method == ILS_SP ? h->Bt : h->G2;
-  a.H = h->H;
+  a.Bt = h->mf ? h->P : (method == ILS_SP ? h->Bt : h->G2);
+  a.H = h->mf ? h->G1 : h->H;
   a.cvec = method == ILS_SP ? h->cvec : h->bbar;
   a.bhat_out = h->bhat;
   a.theta2 = h->opt.theta * h->opt.theta;
@@ -410,8 +471,15 @@ ils_status pass_launch(ils_handle h, int64_t count) {
   const int64_t cap = h->opt.max_outer + 1;
   const int64_t todo = std::min(count, cap - h->pass_launched);
   for (int64_t i = 0; i < todo; ++i) {
+    if (h->mf) {
+      for (int c = 0; c < (int)h->pass_k; ++c)
+        ILS_CK(aq_product_iterate(h->q, h->n, h->Aq64r, 0, h->X0, h->X1, h->st, h->col_done, c, h->sp_part,
+                                  h->vbuf + c * h->n, s));
+    }
     ILS_CK(sp_iterate_f64(h->pa, s));
-    if (h->pass_mixed) ILS_CK(mixed_correct(h->pma, h->opt.precision, s));
+    if (h->pass_mixed && h->mf)
+      ILS_CK(mixed_correct_mf(h->pma, h->opt.precision, h->q, h->Aq_lo, h->sp_part, h->vbuf, h->d64, h->t32, s));
+    else if (h->pass_mixed) ILS_CK(mixed_correct(h->pma, h->opt.precision, s));
     else if (method != ILS_SP) ILS_CK(rand_chain_f64(h->pra, method, s));
   }
   h->pass_launched += todo;
@@ -486,6 +554,14 @@ ils_status create_handle(ils_handle* out, int64_t m, int64_t n, int64_t p, int64
     opt.gram = ILS_GRAM_SPLIT;  // the FP64 refinement needs FP64-accurate Grams; these are the fast ones
   }
   if (opt.sweeps < 0) return ILS_ERR_INVALID_ARG;
+  if (opt.route < ILS_ROUTE_AUTO || opt.route > ILS_ROUTE_MATRIX_FREE) return ILS_ERR_INVALID_ARG;
+  bool mf = false;
+  if (opt.route == ILS_ROUTE_MATRIX_FREE) {
+    if (opt.method != ILS_SP || n > 512 || q < 1) return ILS_ERR_INVALID_ARG;
+    mf = true;
+  } else if (opt.route == ILS_ROUTE_AUTO) {
+    mf = opt.method == ILS_SP && n <= 512 && q > 32 * n;
+  }
   ils_handle h = new (std::nothrow) ils_handle_s();
   if (!h) return ILS_ERR_OOM;
   h->m = m;
@@ -493,6 +569,7 @@ ils_status create_handle(ils_handle* out, int64_t m, int64_t n, int64_t p, int64
   h->p = p;
   h->q = q;
   h->opt = opt;
+  h->mf = mf;
   h->stream = stream;
   const size_t work = setup_work_elems(m, n, p, q);
   Carver dry{nullptr, 0, true};
@@ -532,6 +609,8 @@ ils_status create_handle(ils_handle* out, int64_t m, int64_t n, int64_t p, int64
 }  // namespace
 
 extern "C" {
+
+const char* ils_last_error(void) { return g_last_error; }
 
 const char* ils_status_string(ils_status st) {
   switch (st) {
@@ -589,6 +668,15 @@ ils_status ils_refactor(ils_handle h, const double* A, int64_t lda, ils_stream_t
   if (st == ILS_OK) st = setup_finish(h);
   if (st == ILS_OK && h->opt.timing) collect_timings(h);
   return st;
+}
+
+ils_status ils_aq_product(ils_handle h, const double* x, double* v, int prec, ils_stream_t stream) {
+  if (!h || !x || !v || prec < 0 || prec > 2 || !h->mf) return ILS_ERR_INVALID_ARG;
+  const void* Ar = prec == 0 ? h->Aq64r : h->Aq_lo;
+  if (prec != 0 && (h->opt.precision == ILS_FP64 || (prec == 1) != (h->opt.precision == ILS_FP32_REFINE)))
+    return ILS_ERR_INVALID_ARG;
+  ILS_CK(aq_product(h->q, h->n, Ar, prec, x, h->sp_part, v, (cudaStream_t)stream));
+  return ILS_OK;
 }
 
 int ils_get_timings(ils_handle h, double* out, int count) {

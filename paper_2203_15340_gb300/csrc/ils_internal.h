@@ -87,7 +87,11 @@ cudaError_t sq_norms_cols_f64(int64_t n, int64_t k, const double* X, int64_t ldx
 //   mode 1 (randomized, Alg. 2 step 5 / Alg. 5 step 4): bhat = Abar2 x_k + bbar
 //          (M = Abar2, addv = bbar), written to bhat_out for the inner chain, or
 //   mode 2 (mixed-precision refinement): r_k itself is written to bhat_out and x_k stays
-//          in place (the correction kernels update it).
+//          in place (the correction kernels update it);
+//   mode 3 (matrix-free SP): with v = A_2^T (A_2 x_k) given in vvec, r_k = bbar + v - Abar1 x_k
+//          (H = Abar1) and x_{k+1} = P (v + bbar) (M = P);
+//   mode 4 (matrix-free refinement): r_k = bbar + v - Abar1 x_k written to bhat_out, x_k in
+//          place.
 // See dense_f64.cu for the completion protocol.
 struct SpIterArgs {
   int64_t n, k;
@@ -100,7 +104,8 @@ struct SpIterArgs {
   const double* bnorm2;  // k
   double* X0;          // n x k iterate buffers
   double* X1;
-  double* bhat_out;    // n x k (mode 1)
+  double* bhat_out;    // n x k (modes 1, 2, 4)
+  const double* vvec;  // n x k: A_2^T (A_2 x_k) (modes 3, 4)
   double tol2;         // tol^2
   double theta2;       // theta^2 (mode 1): inner target = theta^2 ||r_k||^2
   double* col_target2; // k (mode 1)
@@ -129,6 +134,22 @@ GramSplitWork gram_split_work(int64_t K, int64_t n);
 cudaError_t gram_split_tc(int64_t K, int64_t n, const double* A, int64_t lda, double* C, int64_t ldc,
                           void* slices, double* partial, int* exps, int32_t* err, cudaStream_t s);
 
+// ---- matrix-free A_2 products (stream.cu) ---------------------------------------------------
+// Row-major copy of A_2 (q x n, column-major source with leading dimension lda) with rows
+// padded to aq_row_stride(n) elements; prec 0 FP64, 1 FP32, 2 BF16.
+int64_t aq_row_stride(int64_t n);
+int aq_stream_blocks();
+cudaError_t aq_copy_rows(int64_t q, int64_t n, const double* Ac, int64_t lda, void* Ar, int prec, cudaStream_t s);
+// v = A_2^T (A_2 x) in one pass; part: aq_stream_blocks() * n accumulators (double for
+// prec 0, float otherwise).  n <= 512 in FP64, n <= 1024 otherwise.
+cudaError_t aq_product(int64_t q, int64_t n, const void* Ar, int prec, const double* x, void* part, double* v,
+                       cudaStream_t s);
+// Same product for column c of the current iterate buffer (chosen on the device from st):
+// returns at once when the solve is done or column c is finished.
+cudaError_t aq_product_iterate(int64_t q, int64_t n, const void* Ar, int prec, const double* X0, const double* X1,
+                               const SolveState* st, const int32_t* col_done, int c, void* part, double* v,
+                               cudaStream_t s);
+
 // ---- mixed precision with FP64 refinement (mixed.cu) ----------------------------------------
 struct MixedArgs {
   int64_t n, k;
@@ -147,9 +168,12 @@ struct MixedArgs {
   SolveState* st;
 };
 // L32/P32/G2_32/Bt32 are n x n FP32 buffers, Bt16 an n x n BF16 buffer (BF16 mode only).
+// G2 == nullptr (matrix-free route) forms only P32.
 cudaError_t mixed_setup(int64_t n, const double* L, const double* G2, int precision, float* L32, float* P32,
                         float* G2_32, float* Bt32, void* Bt16, float* Dinv32, cudaStream_t s);
 cudaError_t mixed_correct(const MixedArgs& a, int precision, cudaStream_t s);
+cudaError_t mixed_correct_mf(const MixedArgs& a, int precision, int64_t q, const void* Aq_lo, void* part, double* v,
+                             double* d64, float* t32, cudaStream_t s);
 
 // ---- randomized inner chains (randomized.cu) ----------------------------------------------
 struct RandArgs {

@@ -139,6 +139,22 @@ __global__ void refine_update_kernel(MixedArgs a, const float* __restrict__ d) {
   }
 }
 
+// d64 = (double) d32 for the unfinished columns (the stream reads FP64 vectors).
+__global__ void widen_kernel(MixedArgs a, const float* __restrict__ d, double* __restrict__ d64) {
+  if (*((volatile int32_t*)&a.st->done)) return;
+  const int64_t total = a.n * a.k;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+    d64[e] = (double)d[e];
+}
+
+// t32 = (float) v + r32 (the right-hand side P is applied to in a matrix-free sweep).
+__global__ void sweep_rhs_kernel(MixedArgs a, const double* __restrict__ v, float* __restrict__ t32) {
+  if (*((volatile int32_t*)&a.st->done)) return;
+  const int64_t total = a.n * a.k;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+    t32[e] = (float)v[e] + a.r32[e];
+}
+
 int grid_small(int64_t total) { return (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 1024)); }
 
 }  // namespace
@@ -148,14 +164,17 @@ cudaError_t mixed_setup(int64_t n, const double* L, const double* G2, int precis
   const int64_t nn = n * n;
   f64_to_f32_kernel<<<grid_small(nn), 256, 0, s>>>(nn, L, L32);
   note_launch();
-  f64_to_f32_kernel<<<grid_small(nn), 256, 0, s>>>(nn, G2, G2_32);
-  note_launch();
+  if (G2) {
+    f64_to_f32_kernel<<<grid_small(nn), 256, 0, s>>>(nn, G2, G2_32);
+    note_launch();
+  }
   identity_f32_kernel<<<grid_small(nn), 256, 0, s>>>(n, P32);
   note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // P = L^{-T} L^{-1} in FP32 from the FP64 Cholesky factor.
   if ((e = trsm_binv_f32(n, n, L32, Dinv32, P32, n, true, true, s)) != cudaSuccess) return e;
+  if (!G2) return cudaSuccess;  // matrix-free route: B is never formed
   // B^T = Abar2 P (both symmetric), so column i of B^T is row i of B = P Abar2.
   const unsigned nt = (unsigned)((n + 31) / 32);
   gemm_tn_f32_kernel<<<dim3(nt, nt), 256, 0, s>>>(n, G2_32, P32, Bt32);
@@ -188,6 +207,39 @@ cudaError_t mixed_correct(const MixedArgs& a, int precision, cudaStream_t s) {
       launch_sweep<__nv_bfloat16>(a, blocks, static_cast<const __nv_bfloat16*>(a.Bt16), dcur, a.c32, dn, s);
     else
       launch_sweep<float>(a, blocks, a.Bt32, dcur, a.c32, dn, s);
+    dcur = dn;
+  }
+  refine_update_kernel<<<grid_small(a.n * a.k), 256, 0, s>>>(a, dcur);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace ils
+
+namespace ils {
+
+// Matrix-free refinement step: d_1 = P r, d_{s+1} = P (A_2^T A_2 d_s + r) with the product
+// streamed from the FP32/BF16 copy of A_2, then x += d.
+cudaError_t mixed_correct_mf(const MixedArgs& a, int precision, int64_t q, const void* Aq_lo, void* part, double* v,
+                             double* d64, float* t32, cudaStream_t s) {
+  residual_to_f32_kernel<<<grid_small(a.n * a.k), 256, 0, s>>>(a);
+  note_launch();
+  const int blocks = mixed_sweep_blocks(a.n);
+  launch_sweep<float>(a, blocks, a.P32, a.r32, nullptr, a.c32, s);
+  const float* dcur = a.c32;
+  float* bufs[2] = {a.d32[0], a.d32[1]};
+  const int prec = precision == ILS_BF16_REFINE ? 2 : 1;
+  for (int sw = 1; sw < a.sweeps; ++sw) {
+    widen_kernel<<<grid_small(a.n * a.k), 256, 0, s>>>(a, dcur, d64);
+    note_launch();
+    for (int c = 0; c < (int)a.k; ++c) {
+      cudaError_t e = aq_product_iterate(q, a.n, Aq_lo, prec, d64, d64, a.st, a.col_done, c, part, v + c * a.n, s);
+      if (e != cudaSuccess) return e;
+    }
+    sweep_rhs_kernel<<<grid_small(a.n * a.k), 256, 0, s>>>(a, v, t32);
+    note_launch();
+    float* dn = bufs[sw & 1];
+    launch_sweep<float>(a, blocks, a.P32, t32, nullptr, dn, s);
     dcur = dn;
   }
   refine_update_kernel<<<grid_small(a.n * a.k), 256, 0, s>>>(a, dcur);

@@ -303,7 +303,7 @@ bool rkrgs_vec_fits(int64_t n, int64_t p) { return rkrgs_smem_bytes(n, p, true) 
 cudaError_t rand_chain_f64(const RandArgs& a, int method, cudaStream_t s) {
   if (method == ILS_SP_SCD) {
     const size_t smem = sizeof(double) * 2 * (size_t)a.n;
-    if (smem > 48 * 1024) {
+    if (smem > 0) {  // static shared arrays count against the same limit
       cudaError_t e = cudaFuncSetAttribute(scd_chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
     }
@@ -312,7 +312,7 @@ cudaError_t rand_chain_f64(const RandArgs& a, int method, cudaStream_t s) {
     return cudaGetLastError();
   }
   const size_t smem = rkrgs_smem_bytes(a.n, a.p, a.vec_in_smem != 0);
-  if (smem > 48 * 1024) {
+  if (smem > 0) {  // static shared arrays count against the same limit
     cudaError_t e = cudaFuncSetAttribute(rkrgs_chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }

@@ -1,0 +1,283 @@
+// Matrix-free A_2 products v = A_2^T (A_2 x) in one pass over A_2 (the Abar2 x of Alg. 1
+// step 6 / Alg. 2 step 5 without forming Abar2).
+//
+// A_2 is kept as a row-major copy whose rows are padded to a multiple of 128 elements, in
+// FP64, FP32 or BF16.  One warp streams one row at a time: every lane loads four
+// consecutive elements per 128-wide chunk (16-byte loads for FP32), forms its part of
+// u_r = A_2(r,:) x against x in shared memory, the warp reduces u_r with shuffles, and the
+// same registers then accumulate v += u_r A_2(r,:).  Each element of A_2 is read from HBM
+// exactly once and the next row is loaded before the current one is reduced.  Per-CTA
+// partial v's are summed by a second small kernel in a fixed order (deterministic).
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "ils_internal.h"
+
+namespace ils {
+namespace {
+
+constexpr int kStreamWarps = 8;
+
+template <typename T>
+struct Acc;
+template <>
+struct Acc<double> {
+  using type = double;
+};
+template <>
+struct Acc<float> {
+  using type = float;
+};
+template <>
+struct Acc<__nv_bfloat16> {
+  using type = float;
+};
+
+// Four consecutive elements as accumulator-type values.
+template <typename T, typename A>
+__device__ __forceinline__ void load4(const T* p, A (&o)[4]);
+template <>
+__device__ __forceinline__ void load4<double, double>(const double* p, double (&o)[4]) {
+  const double2 a = *reinterpret_cast<const double2*>(p);
+  const double2 b = *reinterpret_cast<const double2*>(p + 2);
+  o[0] = a.x;
+  o[1] = a.y;
+  o[2] = b.x;
+  o[3] = b.y;
+}
+template <>
+__device__ __forceinline__ void load4<float, float>(const float* p, float (&o)[4]) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  o[0] = a.x;
+  o[1] = a.y;
+  o[2] = a.z;
+  o[3] = a.w;
+}
+template <>
+__device__ __forceinline__ void load4<__nv_bfloat16, float>(const __nv_bfloat16* p, float (&o)[4]) {
+  const uint2 a = *reinterpret_cast<const uint2*>(p);
+  o[0] = __uint_as_float(a.x << 16);
+  o[1] = __uint_as_float(a.x & 0xFFFF0000u);
+  o[2] = __uint_as_float(a.y << 16);
+  o[3] = __uint_as_float(a.y & 0xFFFF0000u);
+}
+
+template <typename A>
+__device__ __forceinline__ A warp_sum_a(A v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// NT = chunks of 128 columns per row (ldr = 128 NT >= n).
+// Where the vector comes from: a plain pointer, or column c of the current iterate buffer
+// of a solve in flight (nothing to do once the solve or the column is finished).
+struct XSrc {
+  const double* x;
+  const double* x1;
+  const SolveState* st;
+  const int32_t* col_done;
+  int c;
+};
+
+__device__ __forceinline__ const double* resolve_x(const XSrc& src, int64_t n, bool* skip) {
+  if (!src.st) {
+    *skip = false;
+    return src.x;
+  }
+  *skip = *((volatile const int32_t*)&src.st->done) || src.col_done[src.c];
+  const int cur = *((volatile const int32_t*)&src.st->cur);
+  return (cur ? src.x1 : src.x) + (int64_t)src.c * n;
+}
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(32 * kStreamWarps)
+aq_stream_kernel(int64_t q, int64_t n, const T* __restrict__ Ar, int64_t ldr, XSrc src,
+                 typename Acc<T>::type* __restrict__ part) {
+  using A = typename Acc<T>::type;
+  bool skip;
+  const double* __restrict__ x = resolve_x(src, n, &skip);
+  if (skip) return;
+  __shared__ A xs[128 * NT];
+  __shared__ A red[128 * NT];
+  for (int64_t j = threadIdx.x; j < 128 * NT; j += blockDim.x) xs[j] = j < n ? (A)x[j] : A(0);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  A xv[NT][4];
+#pragma unroll
+  for (int t = 0; t < NT; ++t)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) xv[t][e] = xs[t * 128 + lane * 4 + e];
+  A vacc[NT][4];
+#pragma unroll
+  for (int t = 0; t < NT; ++t)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) vacc[t][e] = A(0);
+  const int64_t gw = (int64_t)blockIdx.x * kStreamWarps + w, nw = (int64_t)gridDim.x * kStreamWarps;
+  A cur[NT][4], nxt[NT][4];
+  int64_t r = gw;
+  if (r < q) {
+#pragma unroll
+    for (int t = 0; t < NT; ++t) load4<T, A>(Ar + r * ldr + t * 128 + lane * 4, cur[t]);
+  }
+  for (; r < q; r += nw) {
+    const int64_t rn = r + nw;
+    if (rn < q) {
+#pragma unroll
+      for (int t = 0; t < NT; ++t) load4<T, A>(Ar + rn * ldr + t * 128 + lane * 4, nxt[t]);
+    }
+    A d = A(0);
+#pragma unroll
+    for (int t = 0; t < NT; ++t)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) d = fma(cur[t][e], xv[t][e], d);
+    const A u = warp_sum_a(d);
+#pragma unroll
+    for (int t = 0; t < NT; ++t)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) vacc[t][e] = fma(u, cur[t][e], vacc[t][e]);
+#pragma unroll
+    for (int t = 0; t < NT; ++t)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) cur[t][e] = nxt[t][e];
+  }
+  // Warps add their partial v into shared memory one after another (fixed order).
+  for (int j = threadIdx.x; j < 128 * NT; j += blockDim.x) red[j] = A(0);
+  for (int ww = 0; ww < kStreamWarps; ++ww) {
+    __syncthreads();
+    if (w == ww) {
+#pragma unroll
+      for (int t = 0; t < NT; ++t)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) red[t * 128 + lane * 4 + e] += vacc[t][e];
+    }
+  }
+  __syncthreads();
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) part[(int64_t)blockIdx.x * n + j] = red[j];
+}
+
+// v[j] = sum over CTAs of part[b][j] (fixed order).
+template <typename A>
+__global__ void aq_reduce_kernel(int64_t n, int blocks, const A* __restrict__ part, double* __restrict__ v, XSrc src) {
+  bool skip;
+  resolve_x(src, n, &skip);
+  if (skip) return;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    A s = A(0);
+    for (int b = 0; b < blocks; ++b) s += part[(int64_t)b * n + j];
+    v[j] = (double)s;
+  }
+}
+
+template <typename T>
+__global__ void rowmajor_copy_kernel(int64_t q, int64_t n, const double* __restrict__ Ac, int64_t lda, T* __restrict__ Ar,
+                                     int64_t ldr) {
+  // Tiles of 32 x 32 through shared memory: column-major reads, row-major writes.
+  __shared__ double tile[32][33];
+  const int64_t r0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t r = r0 + threadIdx.x, c = c0 + k;
+    tile[k][threadIdx.x] = (r < q && c < n) ? Ac[r + c * lda] : 0.0;
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t r = r0 + k, c = c0 + threadIdx.x;
+    if (r < q && c < ldr) Ar[r * ldr + c] = (T)tile[threadIdx.x][k];
+  }
+}
+
+}  // namespace
+
+// Rows are padded to the chunk count of the kernel instantiation that streams them
+// (1, 2, 4 or 8 chunks of 128), so the kernel's row stride is always 128 * NT.
+static int64_t chunk_bucket(int64_t n) {
+  const int64_t nt = (n + 127) / 128;
+  return nt <= 1 ? 1 : nt <= 2 ? 2 : nt <= 4 ? 4 : 8 * ((nt + 7) / 8);
+}
+
+int64_t aq_row_stride(int64_t n) { return 128 * chunk_bucket(n); }
+
+// Upper bound of the stream grid (sizes the partial-sum buffer): 4 CTAs per SM.
+int aq_stream_blocks() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
+  }
+  return 4 * sms;
+}
+
+template <typename T>
+static cudaError_t copy_rows(int64_t q, int64_t n, const double* Ac, int64_t lda, T* Ar, cudaStream_t s) {
+  const int64_t ldr = aq_row_stride(n);
+  if (q <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)((q + 31) / 32), (unsigned)((ldr + 31) / 32));
+  rowmajor_copy_kernel<T><<<grid, dim3(32, 8), 0, s>>>(q, n, Ac, lda, Ar, ldr);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t aq_copy_rows(int64_t q, int64_t n, const double* Ac, int64_t lda, void* Ar, int prec, cudaStream_t s) {
+  if (prec == 0) return copy_rows<double>(q, n, Ac, lda, static_cast<double*>(Ar), s);
+  if (prec == 1) return copy_rows<float>(q, n, Ac, lda, static_cast<float*>(Ar), s);
+  return copy_rows<__nv_bfloat16>(q, n, Ac, lda, static_cast<__nv_bfloat16*>(Ar), s);
+}
+
+template <typename T, int NT>
+static cudaError_t launch_stream(int64_t q, int64_t n, const T* Ar, XSrc x, void* part, double* v, cudaStream_t s) {
+  using A = typename Acc<T>::type;
+  // One wave of resident CTAs: every warp streams rows until A_2 is exhausted.
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, aq_stream_kernel<T, NT>, 32 * kStreamWarps, 0) !=
+            cudaSuccess ||
+        per_sm <= 0)
+      per_sm = 1;
+    per_sm = std::min(per_sm, 4);
+  }
+  const int blocks = (aq_stream_blocks() / 4) * per_sm;
+  aq_stream_kernel<T, NT><<<blocks, 32 * kStreamWarps, 0, s>>>(q, n, Ar, 128 * NT, x, static_cast<A*>(part));
+  note_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  aq_reduce_kernel<A><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, blocks, static_cast<const A*>(part), v, x);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t dispatch_stream(int64_t q, int64_t n, const T* Ar, XSrc x, void* part, double* v, cudaStream_t s) {
+  const int64_t nt = chunk_bucket(n);  // equals aq_row_stride(n) / 128, the copy's row stride
+  if (q <= 0 && !x.st) return cudaMemsetAsync(v, 0, sizeof(double) * n, s);
+  if (q <= 0) return cudaErrorInvalidValue;
+  if (nt == 1) return launch_stream<T, 1>(q, n, Ar, x, part, v, s);
+  if (nt == 2) return launch_stream<T, 2>(q, n, Ar, x, part, v, s);
+  if (nt == 4) return launch_stream<T, 4>(q, n, Ar, x, part, v, s);
+  if (nt == 8 && sizeof(T) < 8) return launch_stream<T, 8>(q, n, Ar, x, part, v, s);
+  return cudaErrorInvalidValue;  // wider rows: the explicit route handles them
+}
+
+template <typename... R>
+static cudaError_t by_prec(int prec, int64_t q, int64_t n, const void* Ar, XSrc x, void* part, double* v,
+                           cudaStream_t s) {
+  if (prec == 0) return dispatch_stream<double>(q, n, static_cast<const double*>(Ar), x, part, v, s);
+  if (prec == 1) return dispatch_stream<float>(q, n, static_cast<const float*>(Ar), x, part, v, s);
+  return dispatch_stream<__nv_bfloat16>(q, n, static_cast<const __nv_bfloat16*>(Ar), x, part, v, s);
+}
+
+// v = A_2^T (A_2 x) from the row-major copy Ar (prec 0 FP64, 1 FP32, 2 BF16).  part holds
+// aq_stream_blocks() * n accumulator values.
+cudaError_t aq_product(int64_t q, int64_t n, const void* Ar, int prec, const double* x, void* part, double* v,
+                       cudaStream_t s) {
+  return by_prec(prec, q, n, Ar, XSrc{x, nullptr, nullptr, nullptr, 0}, part, v, s);
+}
+
+cudaError_t aq_product_iterate(int64_t q, int64_t n, const void* Ar, int prec, const double* X0, const double* X1,
+                               const SolveState* st, const int32_t* col_done, int c, void* part, double* v,
+                               cudaStream_t s) {
+  return by_prec(prec, q, n, Ar, XSrc{X0, X1, st, col_done, c}, part, v, s);
+}
+
+}  // namespace ils

@@ -1,0 +1,91 @@
+"""GPU parity of the matrix-free route: v = A_2^T (A_2 x) streamed in one pass over A_2,
+and SP driven by it (x_{k+1} = P (A_2^T A_2 x_k + bbar), Alg. 1 step 6 without Abar2).
+
+Bounds: the FP64 stream meets 4 q u |A_2|^T |A_2| |x| elementwise; the FP32 copy 1e-5 and the
+BF16 copy 2e-2 in relative 2-norm; every solve reaches ||x - x*|| / ||x*|| <= 1e-10.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from tests.helpers import colmajor, relerr, vec
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ils():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2203_15340_gb300 as pkg
+    return pkg
+
+
+@pytest.mark.parametrize("n", [100, 300, 500])
+def test_stream_product_parity(ils, n):
+    import torch
+    p, q = 4 * n, 40 * n + 17
+    inst = W.dense_gaussian(p, q, n, W.mp_scale(p, q, n), 60 + n)
+    A2 = inst.A[p:]
+    x = np.random.default_rng(n).standard_normal(n)
+    vo = A2.T @ (A2 @ x)
+    for prec, name in ((0, "fp64"), (1, "fp32"), (2, "bf16")):
+        precision = {0: ils.ILS_FP64, 1: ils.ILS_FP32_REFINE, 2: ils.ILS_BF16_REFINE}[prec]
+        s = ils.Solver(colmajor(inst.A), p, ils.options(precision=precision, route=ils.ILS_ROUTE_MATRIX_FREE))
+        v = torch.empty(n, dtype=torch.float64, device="cuda")
+        s.aq_product(vec(x), v, prec=0)
+        vg = v.cpu().numpy()
+        bound = 4 * q * 2.0 ** -53 * (np.abs(A2).T @ (np.abs(A2) @ np.abs(x)))
+        assert np.all(np.abs(vg - vo) <= bound), name
+        if prec:
+            s.aq_product(vec(x), v, prec=prec)
+            tol = 1e-5 if prec == 1 else 2e-2
+            assert np.linalg.norm(v.cpu().numpy() - vo) <= tol * np.linalg.norm(vo), name
+        s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_matrix_free_solves(ils, precision):
+    p, q, n = 2000, 40000, 120
+    inst = W.dense_gaussian(p, q, n, W.mp_scale(p, q, n), 77)
+    xs = O.normal_equation_solve(inst.A, inst.b, p)
+    s = ils.Solver(colmajor(inst.A), p, ils.options(precision=precision, route=ils.ILS_ROUTE_MATRIX_FREE))
+    x = vec(np.zeros(n))
+    info = s.solve(vec(inst.b), x, tol=1e-12)
+    assert info.status == ils.ILS_OK and relerr(x.cpu().numpy(), xs) <= 1e-10
+    if precision == 0:
+        s2 = ils.Solver(colmajor(inst.A), p, ils.options(route=ils.ILS_ROUTE_EXPLICIT))
+        x2 = vec(np.zeros(n))
+        info2 = s2.solve(vec(inst.b), x2, tol=1e-12)
+        assert abs(info.outer_iters - info2.outer_iters) <= 1
+        s2.close()
+    s.close()
+
+
+def test_auto_route_choice(ils):
+    import torch
+    tall = W.dense_gaussian(400, 40 * 12 + 1, 12, 0.05, 5)
+    s = ils.Solver(colmajor(tall.A), tall.p)  # q > 32 n: matrix-free
+    v = torch.empty(12, dtype=torch.float64, device="cuda")
+    s.aq_product(vec(np.ones(12)), v)
+    s.close()
+    short = W.config1()  # q = 2 n: explicit
+    s = ils.Solver(colmajor(short.A), short.p)
+    with pytest.raises(ils.ILSError):
+        s.aq_product(vec(np.ones(short.n)), torch.empty(short.n, dtype=torch.float64, device="cuda"))
+    s.close()
+
+
+def test_tall_bandwidth_configuration(ils):
+    """A_1 16000 x 500, A_2 262144 x 500 (A_2 alone 1.05 GB in FP64): mixed precision, BF16 stream."""
+    inst = W.config2_roofline()
+    xs = O.normal_equation_solve(inst.A, inst.b, inst.p)
+    s = ils.Solver(colmajor(inst.A), inst.p, ils.options(precision=ils.ILS_BF16_REFINE))
+    x = vec(np.zeros(inst.n))
+    info = s.solve(vec(inst.b), x, tol=1e-12)
+    assert info.status == ils.ILS_OK and relerr(x.cpu().numpy(), xs) <= 1e-10
+    s.close()
