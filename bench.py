@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="bound on the CPU oracle sample")
+    ap.add_argument("--stream-only", action="store_true",
+                    help="only time the matrix-free A_2 stream on the tall 278144 x 500 instance")
     return ap.parse_args()
 
 
@@ -125,6 +127,59 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+HBM_PEAK_GBS = 6691.8  # measured STREAM-style copy bandwidth on this machine (MEASURED_PEAKS.json)
+
+
+def measure_stream(ils, torch, np, dev, reps=20):
+    """Time v = A_2^T (A_2 x) streamed from the FP64, FP32 and BF16 row-major copies of A_2 on
+    the tall bandwidth instance (A_2 262144 x 500: 1.05 GB in FP64, far above L2), and one
+    complete mixed-precision solve of that instance (matrix-free route, BF16 sweeps)."""
+    import workloads
+    inst = workloads.config2_roofline()
+    q, n, p = inst.q, inst.n, inst.p
+    At = torch.from_numpy(np.ascontiguousarray(inst.A.T)).to(dev)
+    x = torch.from_numpy(np.random.default_rng(0).standard_normal(n)).to(dev)
+    v = torch.empty(n, dtype=torch.float64, device=dev)
+    out = {}
+    for prec, name, elem in ((1, "fp32", 4), (2, "bf16", 2), (0, "fp64", 8)):
+        precision = {0: ils.ILS_BF16_REFINE, 1: ils.ILS_FP32_REFINE, 2: ils.ILS_BF16_REFINE}[prec]
+        s = ils.Solver(At, p, ils.options(precision=precision, route=ils.ILS_ROUTE_MATRIX_FREE))
+        for _ in range(3):
+            s.aq_product(x, v, prec=prec)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            s.aq_product(x, v, prec=prec)
+        e1.record()
+        torch.cuda.synchronize()
+        us = e0.elapsed_time(e1) * 1e3 / reps
+        gbs = q * n * elem / (us * 1e-6) / 1e9
+        out[name] = {"us_per_product": us, "achieved_GBps": gbs, "frac": gbs / HBM_PEAK_GBS,
+                     "algorithmic_bytes": q * n * elem}
+        if prec == 2:
+            import oracle
+            b = torch.from_numpy(inst.b).to(dev)
+            xs_dev = torch.zeros(n, dtype=torch.float64, device=dev)
+            for _ in range(2):
+                s.refactor(At)
+                info = s.solve(b, xs_dev, tol=TOL_RELRES)
+            torch.cuda.synchronize()
+            ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            ev[0].record()
+            s.refactor(At)
+            info = s.solve(b, xs_dev, tol=TOL_RELRES)
+            ev[1].record()
+            torch.cuda.synchronize()
+            xs = oracle.normal_equation_solve(inst.A, inst.b, p)
+            out["tall_mixed_solve"] = {
+                "ms_per_solve": ev[0].elapsed_time(ev[1]), "refinements": info.refinements,
+                "relerr_vs_oracle": float(np.linalg.norm(xs_dev.cpu().numpy() - xs) / np.linalg.norm(xs)),
+                "workload": "dense 278144x500 (p=16000, q=262144), matrix-free route, BF16 stream sweeps"}
+        s.close()
+    return out
+
+
 def run_reference(args, rank, world):
     """Reference arm: the CPU oracle on the host cores (rank 0 only)."""
     if rank != 0:
@@ -167,6 +222,9 @@ def main():
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.stream_only:
+        print(json.dumps(measure_stream(ils, torch, np, dev, reps=5)), flush=True)
+        return
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
@@ -274,6 +332,7 @@ def main():
     gram_flops = float(p) * n * (n + 1)
     n_tiles = (n + 127) // 128
     tensor_flops = 2.0 * 128 * 128 * p * (n_tiles * (n_tiles + 1) // 2) * 55  # executed BF16 MMA flops
+    stream = measure_stream(ils, torch, np, dev)
     cpu_rate, cpu_cnt, cpu_secs = time_oracle(inst, args.cpu_seconds)
     line = {
         "metric": METRIC,
@@ -331,6 +390,18 @@ def main():
             "kernel_ms": gram_ms,
             "share_of_step": gram_ms / ms_step,
         },
+        "roofline_stream": {
+            "kernel": "aq_stream_kernel (one-pass A_2^T (A_2 x), matrix-free route), tall instance A_2 262144x500",
+            "bound": "hbm",
+            "achieved": stream["fp32"]["achieved_GBps"],
+            "peak": HBM_PEAK_GBS,
+            "unit": "GB/s",
+            "frac": stream["fp32"]["frac"],
+            "traffic": None,
+            "by_precision": {k: v for k, v in stream.items() if k in ("fp32", "bf16", "fp64")},
+            "note": "FP64 copy is FP64-issue bound (2 FMA per 8 bytes); FP32/BF16 copies stream at HBM speed",
+        },
+        "tall_config": stream.get("tall_mixed_solve"),
         "cpu_baseline": {
             "value": cpu_rate, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
             "sample": f"{cpu_cnt} complete oracle SP solves of the same instance ({cpu_secs:.1f} s, numpy/LAPACK "

@@ -70,7 +70,6 @@ __device__ __forceinline__ A warp_sum_a(A v) {
   return v;
 }
 
-// NT = chunks of 128 columns per row (ldr = 128 NT >= n).
 // Where the vector comes from: a plain pointer, or column c of the current iterate buffer
 // of a solve in flight (nothing to do once the solve or the column is finished).
 struct XSrc {
@@ -91,7 +90,42 @@ __device__ __forceinline__ const double* resolve_x(const XSrc& src, int64_t n, b
   return (cur ? src.x1 : src.x) + (int64_t)src.c * n;
 }
 
+// Asynchronous global -> shared copies (16 or 8 bytes per lane) that keep several rows
+// in flight per warp without holding them in registers.
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(sdst)),
+               "l"(gsrc)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(sdst)), "l"(gsrc)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Lane `lane`'s four elements of every 128-wide chunk of row r: global -> its own slot bytes.
 template <typename T, int NT>
+__device__ __forceinline__ void issue_row(T* slot, const T* row, int lane) {
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    const int off = t * 128 + lane * 4;
+    if (sizeof(T) == 8) {
+      cp_async16(slot + off, row + off);
+      cp_async16(slot + off + 2, row + off + 2);
+    } else if (sizeof(T) == 4) {
+      cp_async16(slot + off, row + off);
+    } else {
+      cp_async8(slot + off, row + off);
+    }
+  }
+}
+
+// NT = chunks of 128 columns per row (ldr = 128 NT >= n); R rows in flight per warp.
+template <typename T, int NT, int R>
 __global__ void __launch_bounds__(32 * kStreamWarps)
 aq_stream_kernel(int64_t q, int64_t n, const T* __restrict__ Ar, int64_t ldr, XSrc src,
                  typename Acc<T>::type* __restrict__ part) {
@@ -99,11 +133,13 @@ aq_stream_kernel(int64_t q, int64_t n, const T* __restrict__ Ar, int64_t ldr, XS
   bool skip;
   const double* __restrict__ x = resolve_x(src, n, &skip);
   if (skip) return;
+  extern __shared__ __align__(16) unsigned char stream_smem[];
   __shared__ A xs[128 * NT];
   __shared__ A red[128 * NT];
   for (int64_t j = threadIdx.x; j < 128 * NT; j += blockDim.x) xs[j] = j < n ? (A)x[j] : A(0);
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  T* ring = reinterpret_cast<T*>(stream_smem) + (size_t)w * R * (128 * NT);
   A xv[NT][4];
 #pragma unroll
   for (int t = 0; t < NT; ++t)
@@ -115,33 +151,37 @@ aq_stream_kernel(int64_t q, int64_t n, const T* __restrict__ Ar, int64_t ldr, XS
 #pragma unroll
     for (int e = 0; e < 4; ++e) vacc[t][e] = A(0);
   const int64_t gw = (int64_t)blockIdx.x * kStreamWarps + w, nw = (int64_t)gridDim.x * kStreamWarps;
-  A cur[NT][4], nxt[NT][4];
-  int64_t r = gw;
-  if (r < q) {
+  // Prologue: rows gw, gw + nw, ..., one commit group per row (empty groups past q).
 #pragma unroll
-    for (int t = 0; t < NT; ++t) load4<T, A>(Ar + r * ldr + t * 128 + lane * 4, cur[t]);
+  for (int i = 0; i < R; ++i) {
+    const int64_t r = gw + i * nw;
+    if (r < q) issue_row<T, NT>(ring + i * (128 * NT), Ar + r * ldr, lane);
+    cp_async_commit();
   }
-  for (; r < q; r += nw) {
-    const int64_t rn = r + nw;
-    if (rn < q) {
+  int slot = 0;
+  for (int64_t r = gw; r < q; r += nw) {
+    cp_async_wait<R - 1>();  // the oldest group, this row, has landed (each lane reads its own bytes)
+    const T* srow = ring + slot * (128 * NT);
+    A cur[NT][4];
 #pragma unroll
-      for (int t = 0; t < NT; ++t) load4<T, A>(Ar + rn * ldr + t * 128 + lane * 4, nxt[t]);
-    }
+    for (int t = 0; t < NT; ++t) load4<T, A>(srow + t * 128 + lane * 4, cur[t]);
     A d = A(0);
 #pragma unroll
     for (int t = 0; t < NT; ++t)
 #pragma unroll
       for (int e = 0; e < 4; ++e) d = fma(cur[t][e], xv[t][e], d);
+    // The slot's values are in registers (consumed above): refill it with row r + R nw.
+    const int64_t rn = r + (int64_t)R * nw;
+    if (rn < q) issue_row<T, NT>(ring + slot * (128 * NT), Ar + rn * ldr, lane);
+    cp_async_commit();
     const A u = warp_sum_a(d);
 #pragma unroll
     for (int t = 0; t < NT; ++t)
 #pragma unroll
       for (int e = 0; e < 4; ++e) vacc[t][e] = fma(u, cur[t][e], vacc[t][e]);
-#pragma unroll
-    for (int t = 0; t < NT; ++t)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) cur[t][e] = nxt[t][e];
+    slot = (slot + 1 == R) ? 0 : slot + 1;
   }
+  cp_async_wait<0>();
   // Warps add their partial v into shared memory one after another (fixed order).
   for (int j = threadIdx.x; j < 128 * NT; j += blockDim.x) red[j] = A(0);
   for (int ww = 0; ww < kStreamWarps; ++ww) {
@@ -157,16 +197,35 @@ aq_stream_kernel(int64_t q, int64_t n, const T* __restrict__ Ar, int64_t ldr, XS
   for (int64_t j = threadIdx.x; j < n; j += blockDim.x) part[(int64_t)blockIdx.x * n + j] = red[j];
 }
 
-// v[j] = sum over CTAs of part[b][j] (fixed order).
+// v[j] = sum over CTAs of part[b][j]: 32 columns per CTA, its 8 warps split the partials
+// (4 loads in flight per thread) and add their sums in warp order (deterministic).
 template <typename A>
-__global__ void aq_reduce_kernel(int64_t n, int blocks, const A* __restrict__ part, double* __restrict__ v, XSrc src) {
+__global__ void __launch_bounds__(256) aq_reduce_kernel(int64_t n, int blocks, const A* __restrict__ part,
+                                                        double* __restrict__ v, XSrc src) {
   bool skip;
   resolve_x(src, n, &skip);
   if (skip) return;
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
-    A s = A(0);
-    for (int b = 0; b < blocks; ++b) s += part[(int64_t)b * n + j];
-    v[j] = (double)s;
+  __shared__ A red[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t j = (int64_t)blockIdx.x * 32 + lane;
+  A s0 = A(0), s1 = A(0), s2 = A(0), s3 = A(0);
+  if (j < n) {
+    int b = w;
+    for (; b + 24 < blocks; b += 32) {
+      s0 += part[(int64_t)b * n + j];
+      s1 += part[(int64_t)(b + 8) * n + j];
+      s2 += part[(int64_t)(b + 16) * n + j];
+      s3 += part[(int64_t)(b + 24) * n + j];
+    }
+    for (; b < blocks; b += 8) s0 += part[(int64_t)b * n + j];
+  }
+  red[w][lane] = (s0 + s1) + (s2 + s3);
+  __syncthreads();
+  if (w == 0 && j < n) {
+    A t = A(0);
+#pragma unroll
+    for (int ww = 0; ww < 8; ++ww) t += red[ww][lane];
+    v[j] = (double)t;
   }
 }
 
@@ -228,21 +287,26 @@ cudaError_t aq_copy_rows(int64_t q, int64_t n, const double* Ac, int64_t lda, vo
 template <typename T, int NT>
 static cudaError_t launch_stream(int64_t q, int64_t n, const T* Ar, XSrc x, void* part, double* v, cudaStream_t s) {
   using A = typename Acc<T>::type;
-  // One wave of resident CTAs: every warp streams rows until A_2 is exhausted.
+  constexpr int R = sizeof(T) == 8 ? 2 : 4;  // rows in flight per warp
+  const size_t smem = sizeof(T) * (size_t)kStreamWarps * R * 128 * NT;
   static int per_sm = 0;
   if (per_sm == 0) {
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, aq_stream_kernel<T, NT>, 32 * kStreamWarps, 0) !=
+    if (cudaFuncSetAttribute(aq_stream_kernel<T, NT, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return cudaErrorInvalidValue;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, aq_stream_kernel<T, NT, R>, 32 * kStreamWarps, smem) !=
             cudaSuccess ||
         per_sm <= 0)
       per_sm = 1;
     per_sm = std::min(per_sm, 4);
   }
+  // One wave of resident CTAs: every warp streams rows until A_2 is exhausted.
   const int blocks = (aq_stream_blocks() / 4) * per_sm;
-  aq_stream_kernel<T, NT><<<blocks, 32 * kStreamWarps, 0, s>>>(q, n, Ar, 128 * NT, x, static_cast<A*>(part));
+  aq_stream_kernel<T, NT, R><<<blocks, 32 * kStreamWarps, smem, s>>>(q, n, Ar, 128 * NT, x, static_cast<A*>(part));
   note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  aq_reduce_kernel<A><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, blocks, static_cast<const A*>(part), v, x);
+  aq_reduce_kernel<A><<<(unsigned)((n + 31) / 32), 256, 0, s>>>(n, blocks, static_cast<const A*>(part), v, x);
   note_launch();
   return cudaGetLastError();
 }
