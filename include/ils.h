@@ -56,10 +56,11 @@ typedef enum {
 
 typedef enum {
   ILS_FP64 = 0,        /* every product in FP64 (the paper's arithmetic) */
-  ILS_FP32_REFINE = 1, /* SP method only: FP64-accurate Grams and Cholesky factor; the
-                          correction sweeps use P = Abar1^{-1} and B = P Abar2 in FP32 with FP32
+  ILS_FP32_REFINE = 1, /* SP method: FP64-accurate Grams and Cholesky factor; the correction
+                          sweeps use P = Abar1^{-1} and B = P Abar2 in FP32 with FP32
                           accumulation; each step's residual bbar - H x is FP64 (iterative
-                          refinement), so the FP64 stopping test still decides. */
+                          refinement), so the FP64 stopping test still decides.  Also
+                          SP-RK-RGS on a sparse A (see ils_setup_csr). */
   ILS_BF16_REFINE = 2  /* as ILS_FP32_REFINE with B held in BF16 (FP32 accumulation) */
 } ils_precision;
 
@@ -117,6 +118,32 @@ ils_status ils_options_default(ils_options* o);
  * Errors: INVALID_ARG, OOM, CUDA, NOT_SPD (handle not created), NONFINITE. */
 ils_status ils_setup(ils_handle* h, int64_t m, int64_t n, int64_t p, int64_t q,
                      const double* A, int64_t lda, const ils_options* o, ils_stream_t stream);
+
+/* Build a handle for an instance whose A is sparse, given in CSR (Sec. 5 runs its
+ * methods on sparse test matrices; the randomized steps of Alg. 2 read single
+ * columns of A_1, which a column-sorted copy serves).
+ *   h       [host, out] receives the new handle (NULL on failure).
+ *   m,n,p,q as for ils_setup; rows 0..p-1 of A form A_1.
+ *   nnz     number of stored entries, 0 <= nnz < 2^31.
+ *   rowptr  m + 1 int32: row r holds entries rowptr[r] .. rowptr[r+1]-1; rowptr[0] = 0,
+ *           rowptr[m] = nnz, nondecreasing.
+ *   colind  nnz int32 column indices in [0, n), no (row, column) pair twice; any order
+ *           within a row.
+ *   val     nnz FP64 values.
+ *   o       [host] options or NULL.  Every method runs in FP64.  precision =
+ *           ILS_FP32_REFINE is accepted for ILS_SP (as for dense A) and for
+ *           ILS_SP_RK_RGS, whose inner chain then runs in FP32 on the FP64 residual
+ *           (x_k += d with Abar1 d = bbar - H x_k approximately); gram and route are ignored.
+ * All three arrays are read only during this call's stream work: the handle keeps a
+ * column-sorted CSC copy (entries of A_1 first in each column), Abar1 and Abar2 (formed
+ * from the rows' outer products in FP64) and the same n x n products as ils_setup.
+ * A column may hold at most 4096 entries.  Synchronizes the stream once.
+ * Errors: INVALID_ARG (sizes, malformed CSR, a duplicate entry, a column over 4096
+ * entries), NONFINITE, NOT_SPD, OOM, CUDA.  ils_refactor does not apply to such a
+ * handle (INVALID_ARG). */
+ils_status ils_setup_csr(ils_handle* h, int64_t m, int64_t n, int64_t p, int64_t q, int64_t nnz,
+                         const int32_t* rowptr, const int32_t* colind, const double* val,
+                         const ils_options* o, ils_stream_t stream);
 
 /* Recompute every setup product of h for new matrix values of the same shape
  * (same m, n, p, q), allocating nothing.  Same errors as ils_setup; on

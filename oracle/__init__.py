@@ -24,6 +24,9 @@ Parity status (what pins each function, see ``tests/test_oracle_*.py``):
     alpha/subset sampler (exact enumeration for small n).
   * philox4x32_10: the published known-answer vectors.
   * mlp_*: central finite differences.
+  * sparse.*: hand-computed products of a literal 4 x 3 CSR matrix; the dense
+    oracle on the densified matrix; the generator's pattern statistics.
 """
 from .ils_oracle import *  # noqa: F401,F403
 from .philox import philox4x32_10, step_uniforms, words_to_uniform  # noqa: F401
+from . import sparse  # noqa: F401

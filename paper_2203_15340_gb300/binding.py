@@ -85,6 +85,8 @@ SIGNATURES = {
     "ils_options_default": (ctypes.c_int, [ctypes.POINTER(ils_options)]),
     "ils_setup": (ctypes.c_int, [ctypes.POINTER(_P), _I64, _I64, _I64, _I64, _P, _I64,
                                  ctypes.POINTER(ils_options), _P]),
+    "ils_setup_csr": (ctypes.c_int, [ctypes.POINTER(_P), _I64, _I64, _I64, _I64, _I64, _P, _P, _P,
+                                     ctypes.POINTER(ils_options), _P]),
     "ils_refactor": (ctypes.c_int, [_P, _P, _I64, _P]),
     "ils_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ils_info), _P]),
     "ils_solve_many": (ctypes.c_int, [_P, _I64, _P, _I64, _P, _I64, ctypes.c_int, ctypes.c_double,
@@ -217,6 +219,26 @@ class Solver:
                                _stream_ptr(stream))
         _check(code, "ils_setup")
         self.h = h
+
+    @classmethod
+    def from_csr(cls, m: int, n: int, p: int, rowptr, colind, val, opts: ils_options | None = None,
+                 stream=None):
+        """Instance with a sparse A given in CSR: CUDA tensors rowptr (int32, m + 1),
+        colind (int32, nnz) and val (float64, nnz); rows 0..p-1 form A_1."""
+        for t, dt in ((rowptr, 4), (colind, 4), (val, 8)):
+            if not t.is_cuda or t.dtype.itemsize != dt or t.dim() != 1 or (t.numel() > 1 and t.stride(0) != 1):
+                raise ValueError("rowptr/colind must be contiguous int32 and val contiguous float64 CUDA vectors")
+        if rowptr.numel() != m + 1 or colind.numel() != val.numel():
+            raise ValueError("CSR array lengths do not match")
+        self = cls.__new__(cls)
+        self.m, self.n, self.p, self.q = m, n, p, m - p
+        self.opts = opts if opts is not None else options()
+        h = ctypes.c_void_p()
+        code = lib().ils_setup_csr(ctypes.byref(h), m, n, p, m - p, int(val.numel()), rowptr.data_ptr(),
+                                   colind.data_ptr(), val.data_ptr(), ctypes.byref(self.opts), _stream_ptr(stream))
+        _check(code, "ils_setup_csr")
+        self.h = h
+        return self
 
     def refactor(self, At, stream=None):
         ptr, lda = _colmajor_ptr(At, self.m, self.n)

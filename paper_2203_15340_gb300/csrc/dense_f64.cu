@@ -761,7 +761,7 @@ __global__ void __launch_bounds__(32 * kIterWarps) sp_iter_kernel(SpIterArgs a) 
         else if (!conv) atomicCAS(&st->status, 0, ILS_ERR_NO_CONVERGENCE);
       } else {
         all = 0;
-        if (a.mode == 1) a.col_target2[c] = a.theta2 * rr;
+        if (a.mode == 1 || a.mode == 2) a.col_target2[c] = a.theta2 * rr;
       }
     }
     all_done = all;

@@ -70,6 +70,12 @@ struct ils_handle_s {
   double* gs_partial = nullptr;
   int* gs_exps = nullptr;
   int32_t* gs_err = nullptr;
+  // sparse A (ils_setup_csr): column-sorted CSC copy; no dense copy of A is kept
+  bool sparse = false;
+  int64_t nnz = 0;
+  SparseCols sc{};
+  int32_t* cnt_fill = nullptr;  // 2n
+  int32_t* sp_err = nullptr;
   SolveState* st = nullptr;
   int32_t* dstatus = nullptr;
   // pinned host mirrors
@@ -158,7 +164,7 @@ struct Carver {
 void carve(ils_handle h, Carver& c, size_t work_elems) {
   const size_t nn = (size_t)h->n * (size_t)h->n;
   const size_t nk = (size_t)h->n * kMaxRhsPerPass;
-  h->A = c.take<double>((size_t)h->m * (size_t)h->n);
+  h->A = c.take<double>(h->sparse ? 1 : (size_t)h->m * (size_t)h->n);
   h->G1 = c.take<double>(nn);
   h->G2 = c.take<double>(nn);
   h->L = c.take<double>(nn);
@@ -183,6 +189,7 @@ void carve(ils_handle h, Carver& c, size_t work_elems) {
   h->norms2 = c.take<double>((size_t)h->n);
   h->cum = c.take<double>((size_t)h->n);
   h->vec_in_smem = rkrgs_vec_fits(h->n, h->p);
+  if (h->sparse) h->vec_in_smem = false;
   const bool need_scratch = h->opt.method == ILS_SP_RK_RGS && !h->vec_in_smem;
   h->vec_scratch = c.take<double>(need_scratch ? (size_t)kMaxRhsPerPass * 2 * (size_t)h->p : 1);
   if (h->mf) {
@@ -213,6 +220,16 @@ void carve(ils_handle h, Carver& c, size_t work_elems) {
     h->gs_partial = c.take<double>(std::max(w1.partial_elems, w2.partial_elems));
     h->gs_exps = c.take<int>((size_t)h->n);
     h->gs_err = c.take<int32_t>(1);
+  }
+  if (h->sparse) {
+    const size_t nnz = (size_t)std::max<int64_t>(h->nnz, 1);
+    h->sc.colptr = c.take<int32_t>((size_t)h->n + 1);
+    h->sc.rowind = c.take<int32_t>(nnz);
+    h->sc.val = c.take<double>(nnz);
+    h->sc.val32 = h->opt.precision == ILS_FP32_REFINE && h->opt.method == ILS_SP_RK_RGS ? c.take<float>(nnz) : nullptr;
+    h->sc.split = c.take<int32_t>((size_t)h->n);
+    h->cnt_fill = c.take<int32_t>(2 * (size_t)h->n);
+    h->sp_err = c.take<int32_t>(1);
   }
   h->st = c.take<SolveState>(1);
   h->dstatus = c.take<int32_t>(1);
@@ -295,6 +312,22 @@ ils_status compute_setup_mf(ils_handle h) {
   return ILS_OK;
 }
 
+ils_status compute_products(ils_handle h);
+
+// Sparse A: CSC copy and both Grams from the CSR input, then the dense n x n products.
+ils_status compute_setup_sparse(ils_handle h, const int32_t* rowptr, const int32_t* colind, const double* val) {
+  cudaStream_t s = h->stream;
+  ILS_CK(mark(h, 0));
+  ILS_CK(mark(h, 1));
+  ILS_CK(cudaMemsetAsync(h->sp_err, 0, sizeof(int32_t), s));
+  ILS_CK(sparse_setup(h->m, h->n, h->p, h->nnz, rowptr, colind, val, h->sc, h->cnt_fill, h->G1, h->G2, h->sp_err, s));
+  ILS_CK(cudaMemcpyAsync(h->h_status + 2, h->sp_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  ILS_CK(mark(h, 2));
+  if (h->opt.method != ILS_SP) ILS_CK(column_cumsum_f64(h->n, h->G1, h->norms2, h->cum, s));
+  ILS_CK(mark(h, 3));
+  return compute_products(h);
+}
+
 // All setup products for the current contents of h->A.
 ils_status compute_setup(ils_handle h) {
   cudaStream_t s = h->stream;
@@ -316,6 +349,14 @@ ils_status compute_setup(ils_handle h) {
     ILS_CK(gemm_tn_f64(q, n, n, h->A + p, m, h->A + p, m, q, h->G2, n, true, false, h->work, s));
   }
   ILS_CK(mark(h, 3));
+  return compute_products(h);
+}
+
+// Everything after the Grams: H = Abar1 - Abar2, the Cholesky factors of Abar1 and H,
+// P and B (Alg. 1 steps 2-3).
+ils_status compute_products(ils_handle h) {
+  cudaStream_t s = h->stream;
+  const int64_t n = h->n;
   ILS_CK(axpby_mat_f64(n, 1.0, h->G1, -1.0, h->G2, h->H, s));
   // Cholesky of Abar1; the explicit inverse of Alg. 1 step 2 is formed from it.
   ILS_CK(cudaMemcpyAsync(h->L, h->G1, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, s));
@@ -352,6 +393,7 @@ ils_status compute_setup(ils_handle h) {
 // Wait for the setup enqueued by compute_setup and report its pivot / input status.
 ils_status setup_finish(ils_handle h) {
   ILS_CK(cudaStreamSynchronize(h->stream));
+  if (h->sparse && h->h_status[2] != 0) return (ils_status)h->h_status[2];
   h->h_status[1] = h->opt.gram == ILS_GRAM_SPLIT ? h->h_status[1] : 0;
   if (h->h_status[1] != 0) return h->h_status[1] == 2 ? ILS_ERR_NONFINITE : ILS_ERR_TIMEOUT;
   if (*h->h_status != 0) return (ils_status)*h->h_status;
@@ -378,7 +420,8 @@ ils_status pass_begin(ils_handle h, int64_t c0, int64_t kk, const double* B, int
   cudaStream_t s = h->stream;
   const int64_t m = h->m, n = h->n, p = h->p;
   // bbar = A^T J b (Alg. 1 step 4), c = P bbar.
-  ILS_CK(rhs_bar_f64(m, n, p, kk, h->A, m, B, ldb, h->bbar, n, s));
+  if (h->sparse) ILS_CK(sparse_rhs_bar(n, p, kk, h->sc, B, ldb, h->bbar, n, s));
+  else ILS_CK(rhs_bar_f64(m, n, p, kk, h->A, m, B, ldb, h->bbar, n, s));
   ILS_CK(sq_norms_cols_f64(n, kk, h->bbar, n, h->bnorm2, s));
   if (h->opt.precision == ILS_FP64 && !h->mf) ILS_CK(gemv_cols_f64(n, kk, h->P, n, h->bbar, n, h->cvec, n, s));
   if (x0_zero) {
@@ -436,7 +479,7 @@ ils_status pass_begin(ils_handle h, int64_t c0, int64_t kk, const double* B, int
   ra.greedy = h->opt.scd_sampler == 1 ? 1 : 0;
   ra.same_index = h->opt.scd_sampler == 2 ? 1 : 0;
   ra.vec_in_smem = h->vec_in_smem ? 1 : 0;
-  ra.pad = 0;
+  ra.correction = mixed && h->sparse && method == ILS_SP_RK_RGS ? 1 : 0;
   ra.vec_scratch = h->vec_scratch;
   MixedArgs ma;
   ma.n = n;
@@ -477,7 +520,9 @@ ils_status pass_launch(ils_handle h, int64_t count) {
                                   h->vbuf + c * h->n, s));
     }
     ILS_CK(sp_iterate_f64(h->pa, s));
-    if (h->pass_mixed && h->mf)
+    if (h->sparse && method == ILS_SP_RK_RGS)
+      ILS_CK(rkrgs_sparse_chain(h->pra, h->sc, h->pass_mixed, s));
+    else if (h->pass_mixed && h->mf)
       ILS_CK(mixed_correct_mf(h->pma, h->opt.precision, h->q, h->Aq_lo, h->sp_part, h->vbuf, h->d64, h->t32, s));
     else if (h->pass_mixed) ILS_CK(mixed_correct(h->pma, h->opt.precision, s));
     else if (method != ILS_SP) ILS_CK(rand_chain_f64(h->pra, method, s));
@@ -517,7 +562,10 @@ ils_status pass_end(ils_handle h, double* X, int64_t ldx, ils_info* agg) {
     const double rel = bn > 0.0 ? std::sqrt(h->h_rr[c] / bn) : std::sqrt(h->h_rr[c]);
     agg->relres = std::max(agg->relres, rel);
     if (rel != rel) agg->relres = rel;
-    if (mixed) {
+    if (mixed && h->pra.correction) {
+      agg->refinements = std::max<int64_t>(agg->refinements, h->h_iters[c]);
+      agg->outer_iters = std::max<int64_t>(agg->outer_iters, h->h_iters[c]);
+    } else if (mixed) {
       agg->refinements = std::max<int64_t>(agg->refinements, h->h_iters[c]);
       agg->outer_iters = std::max<int64_t>(agg->outer_iters, h->h_iters[c] * h->pma.sweeps);
     } else {
@@ -541,20 +589,29 @@ ils_status sp_pass(ils_handle h, int64_t c0, int64_t kk, const double* B, int64_
 // Validate a problem, allocate its handle and carve its device memory (stream-ordered
 // on `stream`); nothing is computed yet.
 ils_status create_handle(ils_handle* out, int64_t m, int64_t n, int64_t p, int64_t q, const double* A, int64_t lda,
-                         const ils_options* o, cudaStream_t stream) {
+                         const ils_options* o, cudaStream_t stream, int64_t sparse_nnz = -1) {
   *out = nullptr;
-  if (n < 1 || n > kMaxN || p < n || q < 0 || m != p + q || lda < m || !A || m > ((int64_t)1 << 31))
-    return ILS_ERR_INVALID_ARG;
+  const bool sparse = sparse_nnz >= 0;
+  if (n < 1 || n > kMaxN || p < n || q < 0 || m != p + q || m > ((int64_t)1 << 31)) return ILS_ERR_INVALID_ARG;
+  if (!sparse && (lda < m || !A)) return ILS_ERR_INVALID_ARG;
+  if (sparse && sparse_nnz >= ((int64_t)1 << 31)) return ILS_ERR_INVALID_ARG;
   ils_options opt;
   if (o) opt = *o;
   else ils_options_default(&opt);
   if (validate_options(&opt) != ILS_OK) return ILS_ERR_INVALID_ARG;
-  if (opt.precision != ILS_FP64) {
+  if (opt.route < ILS_ROUTE_AUTO || opt.route > ILS_ROUTE_MATRIX_FREE) return ILS_ERR_INVALID_ARG;
+  if (sparse) {
+    // The Grams of a sparse A come from its stored entries (FP64); the route is explicit.
+    if (opt.route == ILS_ROUTE_MATRIX_FREE) return ILS_ERR_INVALID_ARG;
+    const bool chain32 = opt.method == ILS_SP_RK_RGS && opt.precision == ILS_FP32_REFINE;
+    if (opt.precision != ILS_FP64 && opt.method != ILS_SP && !chain32) return ILS_ERR_INVALID_ARG;
+    opt.gram = ILS_GRAM_FP64;
+    opt.route = ILS_ROUTE_EXPLICIT;
+  } else if (opt.precision != ILS_FP64) {
     if (opt.method != ILS_SP) return ILS_ERR_INVALID_ARG;  // mixed precision refines the SP method
     opt.gram = ILS_GRAM_SPLIT;  // the FP64 refinement needs FP64-accurate Grams; these are the fast ones
   }
   if (opt.sweeps < 0) return ILS_ERR_INVALID_ARG;
-  if (opt.route < ILS_ROUTE_AUTO || opt.route > ILS_ROUTE_MATRIX_FREE) return ILS_ERR_INVALID_ARG;
   bool mf = false;
   if (opt.route == ILS_ROUTE_MATRIX_FREE) {
     if (opt.method != ILS_SP || n > 512 || q < 1) return ILS_ERR_INVALID_ARG;
@@ -570,8 +627,10 @@ ils_status create_handle(ils_handle* out, int64_t m, int64_t n, int64_t p, int64
   h->q = q;
   h->opt = opt;
   h->mf = mf;
+  h->sparse = sparse;
+  h->nnz = sparse ? sparse_nnz : 0;
   h->stream = stream;
-  const size_t work = setup_work_elems(m, n, p, q);
+  const size_t work = sparse ? gemm_tn_work_elems(n, n, n, false, nullptr) : setup_work_elems(m, n, p, q);
   Carver dry{nullptr, 0, true};
   carve(h, dry, work);
   h->block_bytes = dry.off;
@@ -657,8 +716,28 @@ ils_status ils_setup(ils_handle* out, int64_t m, int64_t n, int64_t p, int64_t q
   return ILS_OK;
 }
 
+ils_status ils_setup_csr(ils_handle* out, int64_t m, int64_t n, int64_t p, int64_t q, int64_t nnz,
+                         const int32_t* rowptr, const int32_t* colind, const double* val, const ils_options* o,
+                         ils_stream_t stream) {
+  if (!out) return ILS_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (nnz < 0 || !rowptr || (nnz > 0 && (!colind || !val))) return ILS_ERR_INVALID_ARG;
+  ils_handle h = nullptr;
+  ils_status st = create_handle(&h, m, n, p, q, nullptr, 0, o, (cudaStream_t)stream, nnz);
+  if (st != ILS_OK) return st;
+  st = compute_setup_sparse(h, rowptr, colind, val);
+  if (st == ILS_OK) st = setup_finish(h);
+  if (st == ILS_OK && h->opt.timing) collect_timings(h);
+  if (st != ILS_OK) {
+    free_handle(h);
+    return st;
+  }
+  *out = h;
+  return ILS_OK;
+}
+
 ils_status ils_refactor(ils_handle h, const double* A, int64_t lda, ils_stream_t stream) {
-  if (!h || !A || lda < h->m) return ILS_ERR_INVALID_ARG;
+  if (!h || !A || lda < h->m || h->sparse) return ILS_ERR_INVALID_ARG;
   h->stream = (cudaStream_t)stream;
   cudaStream_t s = h->stream;
   ILS_CK(mark(h, 0));

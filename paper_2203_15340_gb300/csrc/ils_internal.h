@@ -196,9 +196,25 @@ struct RandArgs {
   int32_t greedy;         // SCD: alpha = n
   int32_t same_index;     // RK-RGS: j2 = j1 (the SP-RCD special case)
   int32_t vec_in_smem;    // RK-RGS: w, e in shared memory
-  int32_t pad;
+  int32_t correction;     // sparse RK-RGS in FP32: bhat holds r = bbar - H x_k, the chain
+                          // solves Abar1 d = r and x_k += d in place
   double* vec_scratch;    // RK-RGS: k x 2p when not in shared memory
 };
+// Sparse A: column-sorted CSC of all of A; split[j] = entries of column j in rows < p.
+struct SparseCols {
+  int32_t* colptr;  // n + 1
+  int32_t* rowind;  // nnz
+  double* val;      // nnz
+  float* val32;     // nnz (FP32 copy, mixed precision only; else nullptr)
+  int32_t* split;   // n
+};
+cudaError_t sparse_setup(int64_t m, int64_t n, int64_t p, int64_t nnz, const int32_t* rowptr, const int32_t* colind,
+                         const double* val, SparseCols sc, int32_t* cnt_fill, double* G1, double* G2, int32_t* err,
+                         cudaStream_t s);
+cudaError_t sparse_rhs_bar(int64_t n, int64_t p, int64_t k, SparseCols sc, const double* B, int64_t ldb, double* out,
+                           int64_t ldo, cudaStream_t s);
+cudaError_t rkrgs_sparse_chain(const RandArgs& a, SparseCols sc, bool fp32, cudaStream_t s);
+
 cudaError_t column_cumsum_f64(int64_t n, const double* G1, double* norms2, double* cum, cudaStream_t s);
 cudaError_t rand_chain_f64(const RandArgs& a, int method, cudaStream_t s);
 bool rkrgs_vec_fits(int64_t n, int64_t p);

@@ -56,3 +56,22 @@ def test_host_only_calls_without_gpu(libpath):
     assert lib.ils_setup(ctypes.byref(h), 10, 5, 8, 2, 0, 10, None, None) == binding.ILS_ERR_INVALID_ARG
     assert lib.ils_setup(ctypes.byref(h), 10, 5, 8, 2, 1, 9, None, None) == binding.ILS_ERR_INVALID_ARG
     assert lib.ils_options_default(None) == binding.ILS_ERR_INVALID_ARG
+
+
+def test_csr_setup_rejections_without_gpu(libpath):
+    """ils_setup_csr refuses bad sizes and unsupported option mixes before any CUDA call."""
+    from paper_2203_15340_gb300 import binding
+    lib = binding.lib()
+    h = ctypes.c_void_p()
+    fake = 256  # never dereferenced: every case below fails host-side validation first
+    bad = binding.ILS_ERR_INVALID_ARG
+    assert lib.ils_setup_csr(ctypes.byref(h), 10, 5, 3, 7, 20, fake, fake, fake, None, None) == bad  # p < n
+    assert lib.ils_setup_csr(ctypes.byref(h), 10, 5, 8, 2, -1, fake, fake, fake, None, None) == bad  # nnz < 0
+    assert lib.ils_setup_csr(ctypes.byref(h), 10, 5, 8, 2, 20, None, fake, fake, None, None) == bad  # no rowptr
+    assert lib.ils_setup_csr(None, 10, 5, 8, 2, 20, fake, fake, fake, None, None) == bad
+    for kw in (dict(route=binding.ILS_ROUTE_MATRIX_FREE),
+               dict(method=binding.ILS_SP_RK_RGS, precision=binding.ILS_BF16_REFINE),
+               dict(method=binding.ILS_SP_SCD, precision=binding.ILS_FP32_REFINE)):
+        o = binding.options(**kw)
+        assert lib.ils_setup_csr(ctypes.byref(h), 10, 5, 8, 2, 20, fake, fake, fake, ctypes.byref(o), None) == bad
+    assert not h.value
