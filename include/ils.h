@@ -84,7 +84,10 @@ typedef struct {
   uint64_t seed;       /* Philox4x32-10 key for the randomized methods */
   int32_t route;       /* SP only: 0 auto, 1 explicit B = P Abar2, 2 matrix-free (stream A_2 every
                           step, never form Abar2; n <= 512).  Auto picks matrix-free when q > 32 n. */
-  int32_t reserved2;
+  int32_t chain_ctas;  /* SP-RK-RGS on a sparse A: CTAs per inner chain.  0 = auto (the smallest
+                          thread-block cluster of 1, 2, 4 or 8 CTAs whose shared memory holds
+                          w and e, else one CTA with w and e in global memory); 1, 2, 4, 8 =
+                          that cluster size; -1 = one CTA, vectors in global memory. */
 } ils_options;
 
 typedef enum { ILS_ROUTE_AUTO = 0, ILS_ROUTE_EXPLICIT = 1, ILS_ROUTE_MATRIX_FREE = 2 } ils_route;
@@ -172,7 +175,9 @@ ils_status ils_solve_many(ils_handle h, int64_t k, const double* B, int64_t ldb,
 /* Copy an internal n x n FP64 product of the handle into dst (device, column-major,
  * leading dimension ldd >= n): which = 0 Abar1, 1 Abar2, 2 Cholesky factor L of
  * Abar1 (lower triangle; the strict upper triangle of dst is set to 0), 3 P = Abar1^{-1},
- * 4 B = P Abar2.  For tests and diagnostics.  Errors: INVALID_ARG, CUDA. */
+ * 4 B = P Abar2.  P and B are formed only by FP64 SP handles (B only on the explicit
+ * route); asking another handle for them is INVALID_ARG.  For tests and diagnostics.
+ * Errors: INVALID_ARG, CUDA. */
 ils_status ils_get_matrix(ils_handle h, int which, double* dst, int64_t ldd, ils_stream_t stream);
 
 /* Setup phase times of the last ils_setup / ils_refactor on h, in milliseconds,

@@ -55,7 +55,7 @@ class ils_options(ctypes.Structure):
         ("sweeps", ctypes.c_int32),
         ("seed", ctypes.c_uint64),
         ("route", ctypes.c_int32),
-        ("reserved2", ctypes.c_int32),
+        ("chain_ctas", ctypes.c_int32),
     ]
 
 

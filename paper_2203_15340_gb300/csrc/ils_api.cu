@@ -228,6 +228,10 @@ void carve(ils_handle h, Carver& c, size_t work_elems) {
     h->sc.val = c.take<double>(nnz);
     h->sc.val32 = h->opt.precision == ILS_FP32_REFINE && h->opt.method == ILS_SP_RK_RGS ? c.take<float>(nnz) : nullptr;
     h->sc.split = c.take<int32_t>((size_t)h->n);
+    const bool chain = h->opt.method == ILS_SP_RK_RGS;
+    h->sc.seg = c.take<int32_t>(chain && h->sc.cs > 0 ? (size_t)h->n * (h->sc.cs + 1) : 1);
+    h->sc.inv_norms2 = c.take<double>(chain ? (size_t)h->n : 1);
+    h->sc.G1c = chain && h->sc.cs > 0 ? c.take<double>((size_t)h->n * h->sc.ldg) : nullptr;
     h->cnt_fill = c.take<int32_t>(2 * (size_t)h->n);
     h->sp_err = c.take<int32_t>(1);
   }
@@ -324,6 +328,8 @@ ils_status compute_setup_sparse(ils_handle h, const int32_t* rowptr, const int32
   ILS_CK(cudaMemcpyAsync(h->h_status + 2, h->sp_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   ILS_CK(mark(h, 2));
   if (h->opt.method != ILS_SP) ILS_CK(column_cumsum_f64(h->n, h->G1, h->norms2, h->cum, s));
+  if (h->opt.method == ILS_SP_RK_RGS)
+    ILS_CK(sparse_chain_prep(h->n, h->sc, h->G1, h->norms2, h->opt.precision == ILS_FP32_REFINE, s));
   ILS_CK(mark(h, 3));
   return compute_products(h);
 }
@@ -375,8 +381,10 @@ ils_status compute_products(ils_handle h) {
   if (h->opt.gram == ILS_GRAM_SPLIT)
     ILS_CK(cudaMemcpyAsync(h->h_status + 1, h->gs_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   // P and B are formed without waiting for the pivot status; setup_finish reports it
-  // (products of a rejected matrix are never used).
-  if (h->opt.precision != ILS_FP64) {
+  // (products of a rejected matrix are never used).  The randomized methods never apply
+  // P or B (Alg. 2 and 5 use Abar1, Abar2 and H only), so they skip both.
+  if (h->opt.method != ILS_SP) {
+  } else if (h->opt.precision != ILS_FP64) {
     // Mixed precision: P and B for the correction sweeps in FP32 (B also in BF16).
     ILS_CK(mixed_setup(n, h->L, h->G2, h->opt.precision, h->L32, h->P32, h->G2_32, h->Bt32, h->Bt16,
                        reinterpret_cast<float*>(h->Dinv), s));
@@ -612,6 +620,9 @@ ils_status create_handle(ils_handle* out, int64_t m, int64_t n, int64_t p, int64
     opt.gram = ILS_GRAM_SPLIT;  // the FP64 refinement needs FP64-accurate Grams; these are the fast ones
   }
   if (opt.sweeps < 0) return ILS_ERR_INVALID_ARG;
+  if (opt.chain_ctas != 0 && opt.chain_ctas != -1 && opt.chain_ctas != 1 && opt.chain_ctas != 2 &&
+      opt.chain_ctas != 4 && opt.chain_ctas != 8)
+    return ILS_ERR_INVALID_ARG;
   bool mf = false;
   if (opt.route == ILS_ROUTE_MATRIX_FREE) {
     if (opt.method != ILS_SP || n > 512 || q < 1) return ILS_ERR_INVALID_ARG;
@@ -630,6 +641,16 @@ ils_status create_handle(ils_handle* out, int64_t m, int64_t n, int64_t p, int64
   h->sparse = sparse;
   h->nnz = sparse ? sparse_nnz : 0;
   h->stream = stream;
+  if (sparse && opt.method == ILS_SP_RK_RGS && opt.chain_ctas >= 0) {
+    const double col_entries = (double)sparse_nnz * ((double)p / (double)m) / (double)n;  // A_1 entries per column
+    const bool fp32 = opt.precision == ILS_FP32_REFINE;
+    h->sc.cs = rkrgs_cluster_plan(n, p, fp32, opt.chain_ctas, col_entries, &h->sc.slice, &h->sc.nres);
+    h->sc.ldg = (int32_t)((n + (fp32 ? 3 : 1)) / (fp32 ? 4 : 2) * (fp32 ? 4 : 2));
+    if (opt.chain_ctas > 0 && h->sc.cs != opt.chain_ctas) {
+      free_handle(h);
+      return ILS_ERR_INVALID_ARG;  // the requested cluster does not fit
+    }
+  }
   const size_t work = sparse ? gemm_tn_work_elems(n, n, n, false, nullptr) : setup_work_elems(m, n, p, q);
   Carver dry{nullptr, 0, true};
   carve(h, dry, work);
@@ -795,6 +816,9 @@ ils_status ils_solve(ils_handle h, const double* b, double* x, int x0_zero, doub
 
 ils_status ils_get_matrix(ils_handle h, int which, double* dst, int64_t ldd, ils_stream_t stream) {
   if (!h || !dst || ldd < h->n || which < 0 || which > 4) return ILS_ERR_INVALID_ARG;
+  // P exists for FP64 SP handles, B for those on the explicit route
+  if (which >= 3 && (h->opt.method != ILS_SP || h->opt.precision != ILS_FP64)) return ILS_ERR_INVALID_ARG;
+  if (which == 4 && h->mf) return ILS_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t n = h->n;
   const double* src = nullptr;

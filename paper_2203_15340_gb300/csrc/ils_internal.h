@@ -207,6 +207,14 @@ struct SparseCols {
   double* val;      // nnz
   float* val32;     // nnz (FP32 copy, mixed precision only; else nullptr)
   int32_t* split;   // n
+  // SP-RK-RGS on a thread-block cluster of cs CTAs (cs = 0: one CTA, vectors in global memory)
+  int32_t* seg;         // n x (cs + 1): CTA r's entries of column j are seg[j(cs+1)+r] .. seg[j(cs+1)+r+1]-1
+  double* inv_norms2;   // n: 1 / ||A_1(:,j)||^2
+  void* G1c;            // Abar1 in the chain's precision, leading dimension ldg (16-byte columns)
+  int32_t cs;
+  int32_t slice;        // rows of A_1 per CTA
+  int32_t nres;         // entries of s = bhat - Abar1 z per CTA
+  int32_t ldg;
 };
 cudaError_t sparse_setup(int64_t m, int64_t n, int64_t p, int64_t nnz, const int32_t* rowptr, const int32_t* colind,
                          const double* val, SparseCols sc, int32_t* cnt_fill, double* G1, double* G2, int32_t* err,
@@ -214,6 +222,15 @@ cudaError_t sparse_setup(int64_t m, int64_t n, int64_t p, int64_t nnz, const int
 cudaError_t sparse_rhs_bar(int64_t n, int64_t p, int64_t k, SparseCols sc, const double* B, int64_t ldb, double* out,
                            int64_t ldo, cudaStream_t s);
 cudaError_t rkrgs_sparse_chain(const RandArgs& a, SparseCols sc, bool fp32, cudaStream_t s);
+// Cluster size for the sparse RK-RGS chain (0 when none fits); *slice = rows of A_1 per CTA.
+// want = 0: the smallest size that fits and leaves about col_entries / cs <= 112 entries
+// of a column per CTA; else only that size is tried.
+int rkrgs_cluster_plan(int64_t n, int64_t p, bool fp32, int want, double col_entries, int32_t* slice,
+                       int32_t* nres);
+// After the Grams and column norms: the per-CTA column segments, 1/||A_1(:,j)||^2 and the
+// padded copy of Abar1 the cluster chain reads.
+cudaError_t sparse_chain_prep(int64_t n, SparseCols sc, const double* G1, const double* norms2, bool fp32,
+                              cudaStream_t s);
 
 cudaError_t column_cumsum_f64(int64_t n, const double* G1, double* norms2, double* cum, cudaStream_t s);
 cudaError_t rand_chain_f64(const RandArgs& a, int method, cudaStream_t s);

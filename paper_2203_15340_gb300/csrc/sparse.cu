@@ -7,6 +7,8 @@
 // those dense n x n products exactly as for dense A.
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "ils_internal.h"
 #include "philox.cuh"
 
@@ -333,6 +335,367 @@ __global__ void __launch_bounds__(kChainThreads) rkrgs_sparse_chain_kernel(RandA
   if (threadIdx.x == 0) a.col_inner[c] += t;
 }
 
+// ---------------------------------------------------------------------------------------
+// The same chain on a thread-block cluster of CS CTAs of one warp each.
+//
+// Only e = w - A_1 z is stored, split by rows over the cluster's shared memory (CTA r
+// owns rows [r S, (r+1) S) of A_1), with the residual s = bhat - Abar1 z split by
+// entries (CTA r owns n/CS of them).  w itself is never formed: since w = e + A_1 z,
+//   A_1(:,j1)^T w = A_1(:,j1)^T e + (Abar1 z)_j1 = A_1(:,j1)^T e + bhat_j1 - s_j1,
+// so the RK step of Alg. 2 is delta = (s_j1 - A_1(:,j1)^T e) / ||A_1(:,j1)||^2, and the
+// RGS step that follows reads e after e += delta A_1(:,j1):
+//   A_1(:,j2)^T e' = A_1(:,j2)^T e + delta Abar1(j2, j1).
+// Both dot products therefore come from the same e, and one exchange per step (the two
+// partial dots and the owner's s_j1, through distributed shared memory and a cluster
+// barrier) gives every CTA delta and eps; then e += delta A_1(:,j1), e -= eps A_1(:,j2),
+// z_j2 += eps and s -= eps Abar1(:,j2) on the local rows.  In exact arithmetic these are
+// the steps of Alg. 2.  The index draws do not depend on the data, so the columns of a
+// step (segments, values, Abar1 entries, 1/||A_1(:,j)||^2) are fetched a step ahead.
+// Every CTA adds the same numbers in the same order, so all take the same branch at
+// every barrier.
+// ---------------------------------------------------------------------------------------
+constexpr int kMaxE = 4;  // column-segment entries per lane held in registers
+
+// 16-byte vectors of T for the residual update: VecT<float> = float4, VecT<double> = double2.
+template <class T>
+struct VecT;
+template <>
+struct VecT<float> {
+  using type = float4;
+  static constexpr int width = 4;
+};
+template <>
+struct VecT<double> {
+  using type = double2;
+  static constexpr int width = 2;
+};
+// Vectors of Abar1(:, j2) per lane: 512 entries of the CTA's share of s in registers.
+template <class T>
+constexpr int kVecPerLane = 512 / (32 * VecT<T>::width);
+
+// Columns of one step, as raw loads: nothing consumes a fetched value until the step
+// that uses it, so the warp never waits on these loads while it works on another step.
+template <class T>
+struct StepCols {
+  int32_t r1[kMaxE], r2[kMaxE];  // absolute row, or -1 past the segment
+  T v1[kMaxE], v2[kMaxE];
+  typename VecT<T>::type g[kVecPerLane<T>];  // Abar1(i0 + width (lane + 32 i) + 0.., j2)
+};
+
+// Per-step scalars of the next 64 steps (two blocks of 32), in shared memory.
+struct PickRing {
+  int32_t j1[64], j2[64], b1[64], e1[64], b2[64], e2[64];
+  double inv1[64], inv2[64], c12[64];
+};
+
+struct StepPick {
+  int j1, j2;
+  int32_t b1, e1, b2, e2;
+  double inv1, inv2, c12;
+};
+
+// Draws of steps 32 blk .. 32 blk + 31 (one per lane) and everything about them that does
+// not depend on the data: this CTA's segments of both columns, 1/||A_1(:,j)||^2 and
+// Abar1(j1, j2).  The warp waits for these loads once per 32 steps.
+template <int CS>
+__device__ __forceinline__ void draw_block(const RandArgs& a, const SparseCols& sc, const double* cum, int c,
+                                           uint32_t k, int rank, int64_t blk, PickRing& ring) {
+  double u0, u1;
+  const int64_t t = 32 * blk + threadIdx.x;
+  step_uniforms(a.seed, (uint32_t)(a.chain0 + c), k, (uint64_t)t, &u0, &u1);
+  const int n = (int)a.n;
+  const int j1 = invcdf_pick(cum, n, u0);
+  const int j2 = a.same_index ? j1 : invcdf_pick(cum, n, u1);
+  const int q = (int)(blk & 1) * 32 + threadIdx.x;
+  ring.j1[q] = j1;
+  ring.j2[q] = j2;
+  ring.b1[q] = sc.seg[j1 * (CS + 1) + rank];
+  ring.e1[q] = sc.seg[j1 * (CS + 1) + rank + 1];
+  ring.b2[q] = sc.seg[j2 * (CS + 1) + rank];
+  ring.e2[q] = sc.seg[j2 * (CS + 1) + rank + 1];
+  ring.inv1[q] = sc.inv_norms2[j1];
+  ring.inv2[q] = sc.inv_norms2[j2];
+  ring.c12[q] = a.G1[(int64_t)j2 * n + j1];
+}
+
+__device__ __forceinline__ StepPick read_pick(const PickRing& ring, int64_t t) {
+  const int q = (int)((t >> 5) & 1) * 32 + (int)(t & 31);
+  StepPick sp;
+  sp.j1 = ring.j1[q];
+  sp.j2 = ring.j2[q];
+  sp.b1 = ring.b1[q];
+  sp.e1 = ring.e1[q];
+  sp.b2 = ring.b2[q];
+  sp.e2 = ring.e2[q];
+  sp.inv1 = ring.inv1[q];
+  sp.inv2 = ring.inv2[q];
+  sp.c12 = ring.c12[q];
+  return sp;
+}
+
+template <class T>
+__device__ __forceinline__ void load_cols(StepCols<T>& out, const StepPick& sp, const SparseCols& sc, const T* val,
+                                          int i0, int ni) {
+  using V = typename VecT<T>::type;
+  constexpr int W = VecT<T>::width;
+  const int lane = threadIdx.x;
+#pragma unroll
+  for (int i = 0; i < kMaxE; ++i) {
+    const int32_t q1 = sp.b1 + lane + 32 * i, q2 = sp.b2 + lane + 32 * i;
+    out.r1[i] = -1;
+    out.v1[i] = T(0);
+    out.r2[i] = -1;
+    out.v2[i] = T(0);
+    if (q1 < sp.e1) {
+      out.r1[i] = __ldg(sc.rowind + q1);
+      out.v1[i] = __ldg(val + q1);
+    }
+    if (q2 < sp.e2) {
+      out.r2[i] = __ldg(sc.rowind + q2);
+      out.v2[i] = __ldg(val + q2);
+    }
+  }
+  const V* gcol = reinterpret_cast<const V*>(reinterpret_cast<const T*>(sc.G1c) + (int64_t)sp.j2 * sc.ldg + i0);
+#pragma unroll
+  for (int i = 0; i < kVecPerLane<T>; ++i) {
+    const int v = lane + 32 * i;
+    if (W * v < ni) out.g[i] = __ldg(gcol + v);
+  }
+}
+
+// Sum over the cluster of (v0, v1, v2): lane r stores this CTA's triple into CTA r's
+// slot (double-buffered by round), a cluster barrier publishes the stores, and every
+// CTA adds the CS triples in rank order.
+template <class T, int CS>
+__device__ __forceinline__ void cluster_sum3(T& v0, T& v1, T& v2, T* slots, int& round, int rank,
+                                             cooperative_groups::cluster_group& cl) {
+  T* buf = slots + (round & 1) * 4 * CS;
+  if (threadIdx.x < CS) {
+    T* dst = cl.map_shared_rank(buf + 4 * rank, threadIdx.x);
+    dst[0] = v0;
+    dst[1] = v1;
+    dst[2] = v2;
+  }
+  cl.sync();  // release our stores, acquire everyone's
+  T s0 = buf[0], s1 = buf[1], s2 = buf[2];
+#pragma unroll
+  for (int r = 1; r < CS; ++r) {
+    s0 += buf[4 * r];
+    s1 += buf[4 * r + 1];
+    s2 += buf[4 * r + 2];
+  }
+  v0 = s0;
+  v1 = s1;
+  v2 = s2;
+  ++round;
+}
+
+template <class T, int CS>
+struct ChainCtx {
+  RandArgs a;
+  SparseCols sc;
+  const T* val;
+  const double* cum;
+  T* z;
+  T* res;
+  T* slots;
+  T* e;
+  PickRing* ring;
+  int c, rank, n, i0, ni;
+  int32_t r0;
+  uint32_t k;
+  double target2;
+  int round;
+  int64_t next_check;
+  bool stop;
+};
+
+// One inner step t of the chain with the columns in cc; fetches step t+1's into cn.
+template <class T, int CS>
+__device__ __forceinline__ void chain_step(ChainCtx<T, CS>& x, int64_t t, const StepCols<T>& cc, StepCols<T>& cn,
+                                           cooperative_groups::cluster_group& cl) {
+  using V = typename VecT<T>::type;
+  constexpr int W = VecT<T>::width;
+  const int lane = threadIdx.x;
+  if ((t & 31) == 0 && t > 0) {  // the block after next (the next one is in place)
+    __syncwarp();
+    draw_block<CS>(x.a, x.sc, x.cum, x.c, x.k, x.rank, (t >> 5) + 1, *x.ring);
+    __syncwarp();
+  }
+  load_cols<T>(cn, read_pick(*x.ring, t + 1), x.sc, x.val, x.i0, x.ni);
+  const StepPick p0 = read_pick(*x.ring, t);
+  T* e = x.e;
+  const int32_t r0 = x.r0;
+  // local parts of A_1(:,j1)^T e and A_1(:,j2)^T e, and s_j1 from its owner
+  T d1 = T(0), d2 = T(0);
+#pragma unroll
+  for (int i = 0; i < kMaxE; ++i) {
+    d1 = fma(cc.v1[i], e[max(cc.r1[i] - r0, 0)], d1);
+    d2 = fma(cc.v2[i], e[max(cc.r2[i] - r0, 0)], d2);
+  }
+  for (int32_t q = p0.b1 + 32 * kMaxE + lane; q < p0.e1; q += 32) d1 = fma(x.val[q], e[x.sc.rowind[q] - r0], d1);
+  for (int32_t q = p0.b2 + 32 * kMaxE + lane; q < p0.e2; q += 32) d2 = fma(x.val[q], e[x.sc.rowind[q] - r0], d2);
+  d1 = warp_sum_t(d1);
+  d2 = warp_sum_t(d2);
+  const int own = p0.j1 - x.i0;
+  T s1 = (own >= 0 && own < x.ni) ? x.res[own] : T(0);
+  cluster_sum3<T, CS>(d1, d2, s1, x.slots, x.round, x.rank, cl);
+  // RK step on A_1^T w = bhat (step 9), RGS step on A_1 z = w (step 11)
+  const T delta = (s1 - d1) * T(p0.inv1);
+  const T eps = fma(delta, T(p0.c12), d2) * T(p0.inv2);
+#pragma unroll
+  for (int i = 0; i < kMaxE; ++i)
+    if (cc.r1[i] >= 0) e[cc.r1[i] - r0] = fma(delta, cc.v1[i], e[cc.r1[i] - r0]);
+  for (int32_t q = p0.b1 + 32 * kMaxE + lane; q < p0.e1; q += 32) {
+    const int32_t r = x.sc.rowind[q] - r0;
+    e[r] = fma(delta, x.val[q], e[r]);
+  }
+  __syncwarp();  // a row of both columns takes the RK update before the RGS update
+#pragma unroll
+  for (int i = 0; i < kMaxE; ++i)
+    if (cc.r2[i] >= 0) e[cc.r2[i] - r0] = fma(-eps, cc.v2[i], e[cc.r2[i] - r0]);
+  for (int32_t q = p0.b2 + 32 * kMaxE + lane; q < p0.e2; q += 32) {
+    const int32_t r = x.sc.rowind[q] - r0;
+    e[r] = fma(-eps, x.val[q], e[r]);
+  }
+  if (lane == 0) x.z[p0.j2] += eps;
+  // s -= eps Abar1(:, j2) on this CTA's entries
+  V* rv = reinterpret_cast<V*>(x.res);
+#pragma unroll
+  for (int i = 0; i < kVecPerLane<T>; ++i) {
+    const int v = lane + 32 * i;
+    if (W * v < x.ni) {
+      V r = rv[v];
+      const V g = cc.g[i];
+      if constexpr (W == 4) {
+        r.x = fma(-eps, g.x, r.x);
+        r.y = fma(-eps, g.y, r.y);
+        r.z = fma(-eps, g.z, r.z);
+        r.w = fma(-eps, g.w, r.w);
+      } else {
+        r.x = fma(-eps, g.x, r.x);
+        r.y = fma(-eps, g.y, r.y);
+      }
+      rv[v] = r;
+    }
+  }
+  const T* gcol = reinterpret_cast<const T*>(x.sc.G1c) + (int64_t)p0.j2 * x.sc.ldg + x.i0;
+  for (int ii = W * (lane + 32 * kVecPerLane<T>); ii < x.ni; ii += W * 32)
+    for (int u = 0; u < W; ++u) x.res[ii + u] = fma(-eps, gcol[ii + u], x.res[ii + u]);
+  __syncwarp();
+  if (t + 1 == x.next_check) {  // inner stop test: ||s||^2 <= target2
+    x.next_check += x.a.check_every;
+    T acc = T(0);
+    for (int i = lane; i < x.ni; i += 32) acc = fma(x.res[i], x.res[i], acc);
+    acc = warp_sum_t(acc);
+    T u1 = T(0), u2 = T(0);
+    cluster_sum3<T, CS>(acc, u1, u2, x.slots, x.round, x.rank, cl);
+    if ((double)acc <= x.target2) x.stop = true;
+  }
+}
+
+template <class T, int CS>
+__global__ void __launch_bounds__(32) rkrgs_cluster_kernel(RandArgs a, SparseCols sc) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  ChainCtx<T, CS> x;
+  x.a = a;
+  x.sc = sc;
+  x.rank = (int)cl.block_rank();
+  x.c = blockIdx.x / CS;
+  SolveState* st = a.st;
+  // the same c for every CTA of the cluster, so the whole cluster returns or none does
+  if (*((volatile int32_t*)&st->done) || a.col_done[x.c]) return;
+  const int n = (int)a.n, lane = threadIdx.x;
+  x.n = n;
+  const int32_t S = sc.slice;
+  x.r0 = x.rank * S;
+  const int nres = sc.nres;  // a multiple of the vector width
+  x.i0 = x.rank * nres;
+  x.ni = max(0, min(nres, n - x.i0));
+  const int cur = *((volatile int32_t*)&st->cur);
+  x.k = (uint32_t)(st->iters - 1);
+  const double* bhat = a.bhat + (size_t)x.c * n;
+  x.val = values<T>(sc);
+  extern __shared__ double smem[];
+  double* cum = smem;                                 // n
+  x.res = reinterpret_cast<T*>(cum + ((n + 1) & ~1));  // nres (16-byte aligned): s = bhat - Abar1 z
+  x.z = x.res + nres;                                 // n
+  x.slots = x.z + n;                                  // 2 x 4 CS
+  x.e = x.slots + 8 * CS;                             // S: e = w - A_1 z on rows r0 .. r0+S-1
+  x.cum = cum;
+  __shared__ PickRing ring;
+  x.ring = &ring;
+  for (int s = lane; s < n; s += 32) {
+    cum[s] = a.cum[s];
+    x.z[s] = T(0);
+  }
+  for (int i = lane; i < nres; i += 32) x.res[i] = i < x.ni ? T(bhat[x.i0 + i]) : T(0);
+  for (int32_t r = lane; r < S; r += 32) x.e[r] = T(0);  // the whole slice: padding lanes read e[0]
+  __syncwarp();
+  draw_block<CS>(a, sc, cum, x.c, x.k, x.rank, 0, ring);
+  draw_block<CS>(a, sc, cum, x.c, x.k, x.rank, 1, ring);
+  __syncwarp();
+  cl.sync();  // every CTA of the cluster is running and initialized before any remote store
+  x.target2 = a.col_target2[x.c];
+  x.round = 0;
+  x.next_check = a.check_every;
+  x.stop = false;
+  StepCols<T> ca, cb;
+  load_cols<T>(ca, read_pick(ring, 0), sc, x.val, x.i0, x.ni);
+  int64_t t = 0;
+  // two steps per trip so that the two column buffers swap roles without copies
+  for (;;) {
+    if (t >= a.max_inner || x.stop) break;
+    chain_step<T, CS>(x, t, ca, cb, cl);
+    ++t;
+    if (t >= a.max_inner || x.stop) break;
+    chain_step<T, CS>(x, t, cb, ca, cl);
+    ++t;
+  }
+  cl.sync();  // no CTA leaves while another may still address its shared memory
+  if (x.rank == 0) {
+    double* xout = (cur ? a.X1 : a.X0) + (size_t)x.c * n;
+    if (a.correction) {
+      for (int s = lane; s < n; s += 32) xout[s] += (double)x.z[s];
+    } else {
+      for (int s = lane; s < n; s += 32) xout[s] = (double)x.z[s];  // x_{k+1} = z (step 13)
+    }
+    if (lane == 0) a.col_inner[x.c] += t;
+  }
+}
+
+// G1c = Abar1 in T with leading dimension ldg (zero padding rows).
+template <class T>
+__global__ void pad_copy_kernel(int64_t n, int64_t ldg, const double* __restrict__ G1, T* __restrict__ G1c) {
+  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < n * ldg;
+       id += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = id / ldg, i = id - j * ldg;
+    G1c[id] = i < n ? T(G1[i + j * n]) : T(0);
+  }
+}
+
+// seg[j (CS+1) + r]: first entry of column j (A_1 part, rows sorted) with row >= r S;
+// seg[j (CS+1) + CS] = end of the A_1 part.
+__global__ void segment_kernel(int64_t n, int cs, int32_t S, const int32_t* __restrict__ colptr,
+                               const int32_t* __restrict__ rowind, const int32_t* __restrict__ split,
+                               int32_t* __restrict__ seg) {
+  const int64_t total = n * (cs + 1);
+  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total; id += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = id / (cs + 1);
+    const int r = (int)(id - j * (cs + 1));
+    const int32_t end = colptr[j] + split[j];
+    int32_t lo = colptr[j], hi = end;
+    const int64_t bound = (int64_t)r * S;
+    while (lo < hi) {  // first entry with row >= bound (rows are sorted)
+      const int32_t mid = lo + ((hi - lo) >> 1);
+      if (rowind[mid] < bound) lo = mid + 1;
+      else hi = mid;
+    }
+    seg[id] = r < cs ? lo : end;
+  }
+}
+
 __global__ void narrow_kernel(int64_t count, const double* __restrict__ src, float* __restrict__ dst) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
     dst[i] = (float)src[i];
@@ -399,7 +762,107 @@ cudaError_t sparse_rhs_bar(int64_t n, int64_t p, int64_t k, SparseCols sc, const
   return cudaSuccess;
 }
 
+namespace {
+
+int64_t cluster_nres(int64_t n, int cs, bool fp32) {
+  const int64_t w = fp32 ? 4 : 2;
+  return ((n + cs - 1) / cs + w - 1) / w * w;
+}
+
+size_t cluster_smem(int64_t n, int64_t p, int cs, bool fp32) {
+  const size_t ts = fp32 ? sizeof(float) : sizeof(double);
+  const int64_t S = (p + cs - 1) / cs;
+  return sizeof(double) * (size_t)((n + 1) & ~1) + ts * (size_t)(cluster_nres(n, cs, fp32) + n + 8 * cs + S);
+}
+
+template <class T, int CS>
+cudaError_t launch_cluster(const RandArgs* a, const SparseCols* sc, size_t smem, cudaStream_t s, int* max_clusters) {
+  auto kern = rkrgs_cluster_kernel<T, CS>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)((a ? a->k : 1) * CS));
+  cfg.blockDim = dim3(32);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (max_clusters) return cudaOccupancyMaxActiveClusters(max_clusters, (void*)kern, &cfg);
+  e = cudaLaunchKernelEx(&cfg, kern, *a, *sc);
+  note_launch();
+  return e;
+}
+
+template <class T>
+cudaError_t dispatch_cluster(int cs, const RandArgs* a, const SparseCols* sc, size_t smem, cudaStream_t s,
+                             int* max_clusters) {
+  switch (cs) {
+    case 1: return launch_cluster<T, 1>(a, sc, smem, s, max_clusters);
+    case 2: return launch_cluster<T, 2>(a, sc, smem, s, max_clusters);
+    case 4: return launch_cluster<T, 4>(a, sc, smem, s, max_clusters);
+    case 8: return launch_cluster<T, 8>(a, sc, smem, s, max_clusters);
+  }
+  return cudaErrorInvalidValue;
+}
+
+__global__ void reciprocal_kernel(int64_t n, const double* __restrict__ x, double* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = 1.0 / x[i];
+}
+
+}  // namespace
+
+int rkrgs_cluster_plan(int64_t n, int64_t p, bool fp32, int want, double col_entries, int32_t* slice,
+                       int32_t* nres) {
+  for (int cs = 1; cs <= 8; cs *= 2) {
+    if (want > 0 && cs != want) continue;
+    const size_t smem = cluster_smem(n, p, cs, fp32);
+    if (smem > 200 * 1024) continue;
+    // prefer segments that the lanes' registers hold (about 3.5 entries per lane)
+    if (want == 0 && cs < 8 && col_entries / cs > 3.5 * 32) continue;
+    int clusters = 0;
+    cudaError_t e = fp32 ? dispatch_cluster<float>(cs, nullptr, nullptr, smem, nullptr, &clusters)
+                         : dispatch_cluster<double>(cs, nullptr, nullptr, smem, nullptr, &clusters);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (clusters >= 1) {
+      *slice = (int32_t)((p + cs - 1) / cs);
+      *nres = (int32_t)cluster_nres(n, cs, fp32);
+      return cs;
+    }
+  }
+  *slice = 0;
+  *nres = 0;
+  return 0;
+}
+
+cudaError_t sparse_chain_prep(int64_t n, SparseCols sc, const double* G1, const double* norms2, bool fp32,
+                              cudaStream_t s) {
+  reciprocal_kernel<<<gs(n), 256, 0, s>>>(n, norms2, sc.inv_norms2);
+  note_launch();
+  if (sc.cs > 0) {
+    if (fp32) pad_copy_kernel<float><<<gs(n * sc.ldg), 256, 0, s>>>(n, sc.ldg, G1, (float*)sc.G1c);
+    else pad_copy_kernel<double><<<gs(n * sc.ldg), 256, 0, s>>>(n, sc.ldg, G1, (double*)sc.G1c);
+    note_launch();
+    segment_kernel<<<gs(n * (sc.cs + 1)), 256, 0, s>>>(n, sc.cs, sc.slice, sc.colptr, sc.rowind, sc.split, sc.seg);
+    note_launch();
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t rkrgs_sparse_chain(const RandArgs& a, SparseCols sc, bool fp32, cudaStream_t s) {
+  if (sc.cs > 0) {
+    const size_t smem = cluster_smem(a.n, a.p, sc.cs, fp32);
+    return fp32 ? dispatch_cluster<float>(sc.cs, &a, &sc, smem, s, nullptr)
+                : dispatch_cluster<double>(sc.cs, &a, &sc, smem, s, nullptr);
+  }
   const size_t smem = sizeof(double) * 2 * (size_t)a.n;
   cudaError_t e;
   if (fp32) {

@@ -85,17 +85,67 @@ def test_sparse_fp64_methods_converge(ils, small, method):
         assert abs(info.outer_iters - oinfo.outer_iters) <= 2
 
 
-def test_sparse_rk_rgs_trajectory_matches_oracle(ils, small):
-    """300 inner steps of the first outer iteration, no inner stop test: same picks, same z."""
-    inst, A, _ = small
-    steps = 300
-    s = make(ils, inst, method=ils.ILS_SP_RK_RGS, max_outer=1, max_inner=steps, check_every=10 ** 9, seed=9)
+@pytest.fixture(scope="module")
+def ragged():
+    """Sizes that divide by no cluster size: slices and residual shares end ragged."""
+    inst = W.config3_sparse(m=2003, n=61, p=1603, density=0.05, seed=34)
+    return inst, OS.csr_dense(inst.m, inst.n, inst.rowptr, inst.colind, inst.val)
+
+
+@pytest.fixture(scope="module")
+def long_columns():
+    """About 600 entries per column of A_1 (beyond what a lane holds in registers) and
+    n = 600 (beyond the residual share a lane holds in registers)."""
+    a = W.config3_sparse(m=3600, n=20, p=3000, density=0.2, seed=35)
+    b = W.config3_sparse(m=3600, n=600, p=3000, density=0.02, seed=36)
+    return [(x, OS.csr_dense(x.m, x.n, x.rowptr, x.colind, x.val)) for x in (a, b)]
+
+
+def trajectory(ils, inst, A, ctas, steps=300, seed=9):
+    s = make(ils, inst, method=ils.ILS_SP_RK_RGS, max_outer=1, max_inner=steps, check_every=10 ** 9, seed=seed,
+             chain_ctas=ctas)
     x, info = solve(ils, s, inst.b, tol=0.0)
     s.close()
     xo, oinfo = O.sp_rk_rgs_solve(A, inst.b, inst.p, tol=0.0, max_outer=1, max_inner=steps,
-                                  check_every=10 ** 9, seed=9)
+                                  check_every=10 ** 9, seed=seed)
     assert info.inner_iters == steps == oinfo.inner_iters[0]
-    assert np.linalg.norm(x - xo) <= 1e-11 * np.linalg.norm(xo)
+    assert np.linalg.norm(x - xo) <= 1e-11 * np.linalg.norm(xo), np.linalg.norm(x - xo) / np.linalg.norm(xo)
+
+
+@pytest.mark.parametrize("ctas", [-1, 1, 2, 4, 8])
+def test_sparse_rk_rgs_trajectory_matches_oracle(ils, ragged, ctas):
+    """300 inner steps of the first outer iteration, no inner stop test: same picks, same z,
+    for one CTA with global vectors and for every cluster size."""
+    inst, A = ragged
+    trajectory(ils, inst, A, ctas)
+
+
+@pytest.mark.parametrize("which,ctas", [(0, 1), (0, 2), (1, 1), (1, 8)])
+def test_sparse_rk_rgs_trajectory_long_columns(ils, long_columns, which, ctas):
+    inst, A = long_columns[which]
+    trajectory(ils, inst, A, ctas, steps=200)
+
+
+@pytest.mark.parametrize("which,ctas", [(0, 1), (1, 1), (1, 2)])
+def test_sparse_rk_rgs_fp32_long_columns_converge(ils, long_columns, which, ctas):
+    inst, A = long_columns[which]
+    xs = O.qr_cholesky_solve(A, inst.b, inst.p)
+    s = make(ils, inst, method=ils.ILS_SP_RK_RGS, precision=ils.ILS_FP32_REFINE, seed=8, chain_ctas=ctas)
+    x, info = solve(ils, s, inst.b)
+    s.close()
+    assert info.status == ils.ILS_OK and relerr(x, xs) <= 1e-10, (info.status, relerr(x, xs))
+
+
+@pytest.mark.parametrize("ctas", [-1, 2, 8])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_sparse_rk_rgs_cluster_sizes_converge(ils, ragged, ctas, precision):
+    inst, A = ragged
+    xs = O.qr_cholesky_solve(A, inst.b, inst.p)
+    prec = ils.ILS_FP32_REFINE if precision == "fp32" else ils.ILS_FP64
+    s = make(ils, inst, method=ils.ILS_SP_RK_RGS, precision=prec, seed=6, chain_ctas=ctas)
+    x, info = solve(ils, s, inst.b)
+    s.close()
+    assert info.status == ils.ILS_OK and relerr(x, xs) <= 1e-10, (info.status, relerr(x, xs))
 
 
 @pytest.mark.parametrize("method", ["sp", "rk_rgs"])
@@ -159,7 +209,8 @@ def full():
     return inst, xs
 
 
-@pytest.mark.parametrize("method,precision", [("rk_rgs", "fp32"), ("scd", "fp64"), ("sp", "fp64")])
+@pytest.mark.parametrize("method,precision", [("rk_rgs", "fp32"), ("rk_rgs", "fp64"), ("scd", "fp64"),
+                                              ("sp", "fp64")])
 def test_full_size_sparse_solve(ils, full, method, precision):
     """100000 x 2000 CSR at density 0.005: the solution matches x* to 1e-10."""
     inst, xs = full
