@@ -56,6 +56,22 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """The largest `value` over all ranks (the slowest replica's timed region)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(world: int, steps: int, max_seconds: float) -> float:
+    """Whole-job throughput of `world` independent replicas that each ran `steps` steps."""
+    return world * steps / max_seconds
+
+
 def cpu_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -279,12 +295,7 @@ def main():
         launches = ils.binding.kernel_launches() - launches0
         barrier()
         clocks = sampler.stop() if sampler else None
-        total_s = sum(a.elapsed_time(bb) for a, bb in ev) / 1e3
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([total_s], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_s = float(t.item())
+        total_s = max_over_ranks(sum(a.elapsed_time(bb) for a, bb in ev) / 1e3, world, dev)
         ph = {k: statistics.mean(d[k] for d in phases) for k in phases[0]}
         return dict(solver=solver, total_s=total_s, wall=wall, launches=launches, clocks=clocks, relerr=relerr,
                     phases=ph, info=infos[-1], steps=steps)
@@ -292,8 +303,8 @@ def main():
     mixed = measure(ils.options(precision=ils.ILS_FP32_REFINE, timing=1), args.steps, True)
     plain = measure(ils.options(timing=1), max(3, min(args.steps, 10)), False)
     solver = mixed["solver"]
-    value = world * args.steps / mixed["total_s"]
-    plain_value = world * plain["steps"] / plain["total_s"]
+    value = replica_rate(world, args.steps, mixed["total_s"])
+    plain_value = replica_rate(world, plain["steps"], plain["total_s"])
 
     # ---- end to end through the C ABI with host buffers ----
     A_host = torch.from_numpy(np.ascontiguousarray(inst.A.T)).pin_memory()
@@ -313,8 +324,8 @@ def main():
         x_host.copy_(x, non_blocking=True)
         e2e_ev[i][1].record(stream)
     torch.cuda.synchronize()
-    e2e_s = sum(a.elapsed_time(bb) for a, bb in e2e_ev) / 1e3
-    e2e_value = world * e2e_steps / e2e_s
+    e2e_s = max_over_ranks(sum(a.elapsed_time(bb) for a, bb in e2e_ev) / 1e3, world, dev)
+    e2e_value = replica_rate(world, e2e_steps, e2e_s)
     h2d = A_host.numel() * 8 + b_host.numel() * 8
     d2h = x_host.numel() * 8
 
