@@ -241,11 +241,19 @@ gemv_cols_kernel(int64_t n, const double* __restrict__ M, int64_t ldm, const dou
 
 // ---------------------------------------------------------------------------------------
 // Blocked right-looking Cholesky, 32-wide panels, for a batch of matrices at once
-// (blockIdx.z selects the matrix).  FP64 latency, not throughput, limits these kernels
-// at n ~ 500, so the diagonal block lives in one warp's registers (lane i holds row i)
-// and every division by a pivot becomes a multiplication by its reciprocal.
+// (blockIdx.z selects the matrix).  On GB300 one warp issues FP64 fused multiply-adds at
+// about one per 64 cycles (the SM's FP64 rate is about 2 lanes per clock over its four
+// sub-partitions), so no FP64 stage may rest on a single warp: every kernel spreads its
+// multiply-adds over several warps and CTAs.  Two launches per panel:
+//   chol_panel_kernel  every CTA factors the 32 x 32 diagonal block in shared memory
+//                      (4 warps; redundantly, so no CTA waits for another), CTA 0 stores
+//                      it, and each warp then solves one row of L21 = A21 L11^{-T} with
+//                      the 32 columns spread over its lanes;
+//   syrk16_kernel      A22 -= L21 L21^T on 16 x 16 lower tiles, 4 warps per tile.
+// Division by a pivot is multiplication by its reciprocal square root.
 // ---------------------------------------------------------------------------------------
 constexpr int kNB = 32;
+constexpr int kPanelWarps = 4;
 
 struct CholBatch {
   double* M[2];       // matrices (ld n), lower triangles factored in place
@@ -255,105 +263,91 @@ struct CholBatch {
 
 __device__ void set_status(int32_t* status, int32_t code) { atomicCAS(status, 0, code); }
 
-__global__ void __launch_bounds__(32)
-potrf_diag_kernel(int64_t n, CholBatch cb, int64_t k0, int nb) {
+__global__ void __launch_bounds__(32 * kPanelWarps)
+chol_panel_kernel(int64_t n, CholBatch cb, int64_t k0, int nb) {
   double* L = cb.M[blockIdx.z];
   double* inv = cb.inv_diag[blockIdx.z];
-  const int i = threadIdx.x;
-  double a[kNB];
-#pragma unroll
-  for (int j = 0; j < kNB; ++j)
-    a[j] = (i < nb && j < nb) ? L[(k0 + i) + (k0 + j) * n] : (i == j ? 1.0 : 0.0);
-#pragma unroll
+  __shared__ double a[kNB][kNB + 1];
+  __shared__ double rinv[kNB];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  for (int e = tid; e < kNB * kNB; e += blockDim.x) {
+    const int r = e & 31, c = e >> 5;
+    a[r][c] = (r < nb && c < nb && r >= c) ? L[(k0 + r) + (k0 + c) * n] : (r == c ? 1.0 : 0.0);
+  }
+  __syncthreads();
+  // Pivot c: every thread reads a[c][c] and forms rs = 1/sqrt(a_cc) itself, then
+  // a[i][j] -= a[i][c] a[j][c] rs^2 for c < j <= i (lane = column j, warps take rows in
+  // turn).  Column c is scaled by rs one pivot later, once nobody reads it unscaled.
   for (int c = 0; c < kNB; ++c) {
-    double d = __shfl_sync(0xffffffffu, a[c], c);
+    __syncthreads();
+    if (c > 0 && w == 0 && lane >= c - 1) a[lane][c - 1] *= rinv[c - 1];
+    double d = a[c][c];
     if (!isfinite(d)) {
-      if (i == 0) set_status(cb.status, ILS_ERR_NONFINITE);
+      if (tid == 0 && blockIdx.x == 0) set_status(cb.status, ILS_ERR_NONFINITE);
       d = 1.0;
     } else if (!(d > 0.0)) {
-      if (i == 0) set_status(cb.status, ILS_ERR_NOT_SPD);
+      if (tid == 0 && blockIdx.x == 0) set_status(cb.status, ILS_ERR_NOT_SPD);
       d = 1.0;
     }
     const double rs = rsqrt(d);
-    const double sd = d * rs;
-    a[c] = (i == c) ? sd : (i > c ? a[c] * rs : a[c]);
-    if (i == c && c < nb) inv[k0 + c] = rs;
-#pragma unroll
-    for (int j = c + 1; j < kNB; ++j) {
-      const double ljc = __shfl_sync(0xffffffffu, a[c], j);
-      if (i >= j) a[j] = fma(-a[c], ljc, a[j]);
+    if (tid == 0) rinv[c] = rs;
+    const int j = lane;
+    if (j > c) {
+      const double tj = a[j][c] * (rs * rs);
+      for (int i = j + ((w - j) % kPanelWarps + kPanelWarps) % kPanelWarps; i < kNB; i += kPanelWarps)
+        a[i][j] = fma(-a[i][c], tj, a[i][j]);
     }
   }
-#pragma unroll
-  for (int j = 0; j < kNB; ++j)
-    if (i < nb && j < nb && i >= j) L[(k0 + i) + (k0 + j) * n] = a[j];
-}
-
-// Rows below the diagonal block: L21 = A21 L11^{-T}, one thread per row.
-__global__ void __launch_bounds__(32)
-trsm_panel_kernel(int64_t n, CholBatch cb, int64_t k0, int nb) {
-  double* L = cb.M[blockIdx.z];
-  const double* inv = cb.inv_diag[blockIdx.z];
-  __shared__ double l11[kNB][kNB + 1];
-  __shared__ double rinv[kNB];
-  {
-    // One row of L11 per thread, all 32 loads in flight before the stores.
-    const int a = threadIdx.x;
-    double v[kNB];
-#pragma unroll
-    for (int b = 0; b < kNB; ++b) v[b] = (a < nb && b < nb && a >= b) ? L[(k0 + a) + (k0 + b) * n] : 0.0;
-#pragma unroll
-    for (int b = 0; b < kNB; ++b) l11[a][b] = v[b];
-  }
-  if (threadIdx.x < kNB) rinv[threadIdx.x] = (threadIdx.x < nb) ? inv[k0 + threadIdx.x] : 0.0;
   __syncthreads();
-  const int64_t i = k0 + nb + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  double x[kNB];
-#pragma unroll
-  for (int c = 0; c < kNB; ++c) x[c] = (c < nb) ? L[i + (k0 + c) * n] : 0.0;
-  // Right-looking: once x_c is final, its contribution leaves every later x_d at once,
-  // so the dependent chain is 32 steps long instead of 528.
-#pragma unroll
-  for (int c = 0; c < kNB; ++c) {
-    x[c] *= rinv[c];
-#pragma unroll
-    for (int d = c + 1; d < kNB; ++d) x[d] = fma(-x[c], l11[d][c], x[d]);
+  if (w == 0 && lane >= kNB - 1) a[lane][kNB - 1] *= rinv[kNB - 1];
+  __syncthreads();
+  if (blockIdx.x == 0) {
+    for (int e = tid; e < kNB * kNB; e += blockDim.x) {
+      const int r = e & 31, c = e >> 5;
+      if (r < nb && c < nb && r >= c) L[(k0 + r) + (k0 + c) * n] = a[r][c];
+    }
+    if (tid < nb) inv[k0 + tid] = rinv[tid];
   }
-#pragma unroll
-  for (int c = 0; c < kNB; ++c)
-    if (c < nb) L[i + (k0 + c) * n] = x[c];
+  // One row of L21 per warp: x_c = (a_c - sum_{d<c} x_d l_cd) / l_cc, lane = column.
+  const int64_t row = k0 + nb + (int64_t)blockIdx.x * kPanelWarps + w;
+  if (row >= n) return;
+  double x = lane < nb ? L[row + (k0 + lane) * n] : 0.0;
+  for (int c = 0; c < nb; ++c) {
+    const double xc = __shfl_sync(0xffffffffu, x, c) * rinv[c];
+    if (lane == c) x = xc;
+    else if (lane > c) x = fma(-xc, a[lane][c], x);
+  }
+  if (lane < nb) L[row + (k0 + lane) * n] = x;
 }
 
-// Trailing update A22 -= L21 L21^T on lower 32 x 32 tiles.
-__global__ void __launch_bounds__(256)
-syrk_trailing_kernel(int64_t n, CholBatch cb, int64_t k0, int nb) {
+// Trailing update A22 -= L21 L21^T on lower 16 x 16 tiles (two elements per thread).
+__global__ void __launch_bounds__(128)
+syrk16_kernel(int64_t n, CholBatch cb, int64_t k0, int nb) {
   double* L = cb.M[blockIdx.z];
   const int bi = blockIdx.x, bj = blockIdx.y;
   if (bi < bj) return;
   const int64_t k1 = k0 + nb;
-  const int64_t ri0 = k1 + (int64_t)bi * kNB, rj0 = k1 + (int64_t)bj * kNB;
-  __shared__ double Pi[kNB][kNB + 1];
-  __shared__ double Pj[kNB][kNB + 1];
-  for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x) {
-    const int r = e % kNB, c = e / kNB;
+  const int64_t ri0 = k1 + (int64_t)bi * 16, rj0 = k1 + (int64_t)bj * 16;
+  __shared__ double Pi[16][kNB + 1];
+  __shared__ double Pj[16][kNB + 1];
+  for (int e = threadIdx.x; e < 16 * kNB; e += blockDim.x) {
+    const int r = e & 15, c = e >> 4;
     Pi[r][c] = (ri0 + r < n && c < nb) ? L[(ri0 + r) + (k0 + c) * n] : 0.0;
     Pj[r][c] = (rj0 + r < n && c < nb) ? L[(rj0 + r) + (k0 + c) * n] : 0.0;
   }
   __syncthreads();
-  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int c = 0; c < nb; ++c) {
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // ty in 0..7
+  double acc0 = 0.0, acc1 = 0.0;
+#pragma unroll 8
+  for (int c = 0; c < kNB; ++c) {
     const double pj = Pj[tx][c];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) acc[a] = fma(Pi[ty + 8 * a][c], pj, acc[a]);
+    acc0 = fma(Pi[ty][c], pj, acc0);
+    acc1 = fma(Pi[ty + 8][c], pj, acc1);
   }
   const int64_t gj = rj0 + tx;
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const int64_t gi = ri0 + ty + 8 * a;
-    if (gi < n && gj < n && gi >= gj) L[gi + gj * n] -= acc[a];
-  }
+  const int64_t gi0 = ri0 + ty, gi1 = ri0 + ty + 8;
+  if (gi0 < n && gj < n && gi0 >= gj) L[gi0 + gj * n] -= acc0;
+  if (gi1 < n && gj < n && gi1 >= gj) L[gi1 + gj * n] -= acc1;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -924,18 +918,15 @@ cudaError_t cholesky_f64_batch(int64_t n, int count, double* const* mats, double
   cb.status = status;
   for (int64_t k0 = 0; k0 < n; k0 += kNB) {
     const int nb = (int)std::min<int64_t>(kNB, n - k0);
-    potrf_diag_kernel<<<dim3(1, 1, count), 32, 0, s>>>(n, cb, k0, nb);
+    const int64_t rest = n - k0 - nb;
+    const unsigned panel_ctas = (unsigned)std::max<int64_t>(1, (rest + kPanelWarps - 1) / kPanelWarps);
+    chol_panel_kernel<<<dim3(panel_ctas, 1, count), 32 * kPanelWarps, 0, s>>>(n, cb, k0, nb);
     note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int64_t rest = n - k0 - nb;
     if (rest <= 0) break;
-    trsm_panel_kernel<<<dim3((unsigned)((rest + 31) / 32), 1, count), 32, 0, s>>>(n, cb, k0, nb);
-    note_launch();
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    const unsigned nt = (unsigned)((rest + kNB - 1) / kNB);
-    syrk_trailing_kernel<<<dim3(nt, nt, count), 256, 0, s>>>(n, cb, k0, nb);
+    const unsigned nt = (unsigned)((rest + 15) / 16);
+    syrk16_kernel<<<dim3(nt, nt, count), 128, 0, s>>>(n, cb, k0, nb);
     note_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
