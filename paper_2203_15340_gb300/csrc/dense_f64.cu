@@ -282,10 +282,12 @@ chol_panel_kernel(int64_t n, CholBatch cb, int64_t k0, int nb) {
     __syncthreads();
     if (c > 0 && w == 0 && lane >= c - 1) a[lane][c - 1] *= rinv[c - 1];
     double d = a[c][c];
-    if (!isfinite(d)) {
+    // pivot tests on the bit pattern (integer pipe, not the scarce FP64 one)
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(d);
+    if (((bits >> 52) & 0x7ffull) == 0x7ffull) {
       if (tid == 0 && blockIdx.x == 0) set_status(cb.status, ILS_ERR_NONFINITE);
       d = 1.0;
-    } else if (!(d > 0.0)) {
+    } else if ((bits >> 63) != 0ull || bits == 0ull) {
       if (tid == 0 && blockIdx.x == 0) set_status(cb.status, ILS_ERR_NOT_SPD);
       d = 1.0;
     }
@@ -308,16 +310,32 @@ chol_panel_kernel(int64_t n, CholBatch cb, int64_t k0, int nb) {
     }
     if (tid < nb) inv[k0 + tid] = rinv[tid];
   }
-  // One row of L21 per warp: x_c = (a_c - sum_{d<c} x_d l_cd) / l_cc, lane = column.
-  const int64_t row = k0 + nb + (int64_t)blockIdx.x * kPanelWarps + w;
-  if (row >= n) return;
-  double x = lane < nb ? L[row + (k0 + lane) * n] : 0.0;
-  for (int c = 0; c < nb; ++c) {
-    const double xc = __shfl_sync(0xffffffffu, x, c) * rinv[c];
-    if (lane == c) x = xc;
-    else if (lane > c) x = fma(-xc, a[lane][c], x);
+  // Rows of L21, two per warp at a time: x_c = (a_c - sum_{d<c} x_d l_cd) / l_cc with the
+  // columns over the lanes.  The grid holds at most one CTA per SM, so the redundant
+  // factorizations above never share an SM's FP64 pipes.
+  const int64_t stride = (int64_t)gridDim.x * kPanelWarps;
+  for (int64_t row = k0 + nb + (int64_t)blockIdx.x * kPanelWarps + w; row < n; row += 2 * stride) {
+    const int64_t row2 = row + stride;
+    const bool two = row2 < n;
+    double x = lane < nb ? L[row + (k0 + lane) * n] : 0.0;
+    double y = (two && lane < nb) ? L[row2 + (k0 + lane) * n] : 0.0;
+    for (int c = 0; c < nb; ++c) {
+      const double xc = __shfl_sync(0xffffffffu, x, c) * rinv[c];
+      const double yc = __shfl_sync(0xffffffffu, y, c) * rinv[c];
+      if (lane == c) {
+        x = xc;
+        y = yc;
+      } else if (lane > c) {
+        const double l = a[lane][c];
+        x = fma(-xc, l, x);
+        y = fma(-yc, l, y);
+      }
+    }
+    if (lane < nb) {
+      L[row + (k0 + lane) * n] = x;
+      if (two) L[row2 + (k0 + lane) * n] = y;
+    }
   }
-  if (lane < nb) L[row + (k0 + lane) * n] = x;
 }
 
 // Trailing update A22 -= L21 L21^T on lower 16 x 16 tiles (two elements per thread).
@@ -919,7 +937,9 @@ cudaError_t cholesky_f64_batch(int64_t n, int count, double* const* mats, double
   for (int64_t k0 = 0; k0 < n; k0 += kNB) {
     const int nb = (int)std::min<int64_t>(kNB, n - k0);
     const int64_t rest = n - k0 - nb;
-    const unsigned panel_ctas = (unsigned)std::max<int64_t>(1, (rest + kPanelWarps - 1) / kPanelWarps);
+    const int64_t per_matrix = std::max<int64_t>(1, num_sms() / count);
+    const unsigned panel_ctas =
+        (unsigned)std::max<int64_t>(1, std::min<int64_t>((rest + kPanelWarps - 1) / kPanelWarps, per_matrix));
     chol_panel_kernel<<<dim3(panel_ctas, 1, count), 32 * kPanelWarps, 0, s>>>(n, cb, k0, nb);
     note_launch();
     cudaError_t e = cudaGetLastError();
@@ -997,6 +1017,12 @@ cudaError_t trsm_lower_f64(int64_t n, int64_t k, const double* L, double* X, int
 cudaError_t trsm_lower_f32(int64_t n, int64_t k, const float* L, float* X, int64_t ldx, bool forward,
                            bool backward, cudaStream_t s) {
   return trsm_lower_t<float>(n, k, L, X, ldx, forward, backward, s);
+}
+
+cudaError_t diag_block_inverse_f32(int64_t n, const float* L, float* Dinv, cudaStream_t s) {
+  diag_block_inverse_kernel<float><<<(unsigned)((n + 31) / 32), 32, 0, s>>>(n, L, Dinv);
+  note_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t trsm_binv_f64(int64_t n, int64_t k, const double* L, double* Dinv, double* X, int64_t ldx, bool forward,

@@ -69,6 +69,8 @@ cudaError_t trsm_lower_f32(int64_t n, int64_t k, const float* L, float* X, int64
 // shared memory with one 32 x n panel of L (n <= 708 in FP64, 1422 in FP32).
 cudaError_t trsm_binv_f64(int64_t n, int64_t k, const double* L, double* Dinv, double* X, int64_t ldx,
                           bool forward, bool backward, cudaStream_t s);
+// Dinv = inverses of the 32 x 32 diagonal blocks of the lower-triangular L (block after block).
+cudaError_t diag_block_inverse_f32(int64_t n, const float* L, float* Dinv, cudaStream_t s);
 cudaError_t trsm_binv_f32(int64_t n, int64_t k, const float* L, float* Dinv, float* X, int64_t ldx,
                           bool forward, bool backward, cudaStream_t s);
 

@@ -159,27 +159,188 @@ int grid_small(int64_t total) { return (int)std::max<int64_t>(1, std::min<int64_
 
 }  // namespace
 
+// ---------------------------------------------------------------------------------------
+// FP32 GEMM for the setup products: C = alpha op(A) op(B) + beta C, column-major, batched
+// over blockIdx.z with element strides.  64 x 64 tiles, 16-deep K slices in shared
+// memory, a 4 x 4 register tile per thread (two float4 shared-memory loads per 16 FMAs).
+// ---------------------------------------------------------------------------------------
+struct GemmF32 {
+  int64_t M, N, K, lda, ldb, ldc, sa, sb, sc;
+  const float* A;
+  const float* B;
+  float* C;
+  float alpha, beta;
+};
+
+// Shared-memory tiles are [k][64] with the 4-float groups of a row permuted by k (an XOR
+// swizzle): a warp's stores hit 32 different banks whichever operand layout it copies, and
+// a float4 read of 4 consecutive m (or n) stays contiguous.
+__device__ __forceinline__ int swz(int mn, int k) { return (((mn >> 2) ^ (k & 7)) << 2) | (mn & 3); }
+
+// Element e (0..2047) of a 64 x 32 operand slice: which (mn, k) it is.  kfast = the
+// operand's k index is contiguous in memory; then a warp covers 8 k x 4 mn (four 32-byte
+// sectors), otherwise 32 consecutive mn.
+template <bool kfast>
+__device__ __forceinline__ void slice_pos(int e, int& mn, int& k) {
+  if (kfast) {
+    const int rest = e >> 5;
+    k = (e & 7) + 8 * (rest & 3);
+    mn = ((e >> 3) & 3) + 4 * (rest >> 2);
+  } else {
+    mn = e & 63;
+    k = e >> 6;
+  }
+}
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256) gemm_f32_kernel(GemmF32 g) {
+  constexpr int BK = 32;
+  __shared__ __align__(16) float As[BK][64];
+  __shared__ __align__(16) float Bs[BK][64];
+  const float* A = g.A + (int64_t)blockIdx.z * g.sa;
+  const float* B = g.B + (int64_t)blockIdx.z * g.sb;
+  float* C = g.C + (int64_t)blockIdx.z * g.sc;
+  const int64_t m0 = (int64_t)blockIdx.x * 64, n0 = (int64_t)blockIdx.y * 64;
+  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+  float acc[4][4] = {};
+  float ra[8], rb[8];  // the next K slice, fetched while the current one is multiplied
+  auto fetch = [&](int64_t k0) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int e = t + 256 * r;
+      int mm, kk, nn, kb;
+      slice_pos<TA>(e, mm, kk);
+      slice_pos<!TB>(e, nn, kb);
+      const int64_t gm = m0 + mm, gk = k0 + kk, gn = n0 + nn, gkb = k0 + kb;
+      ra[r] = (gm < g.M && gk < g.K) ? (TA ? A[gk + gm * g.lda] : A[gm + gk * g.lda]) : 0.f;
+      rb[r] = (gn < g.N && gkb < g.K) ? (TB ? B[gn + gkb * g.ldb] : B[gkb + gn * g.ldb]) : 0.f;
+    }
+  };
+  auto stash = [&]() {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int e = t + 256 * r;
+      int mm, kk, nn, kb;
+      slice_pos<TA>(e, mm, kk);
+      slice_pos<!TB>(e, nn, kb);
+      As[kk][swz(mm, kk)] = ra[r];
+      Bs[kb][swz(nn, kb)] = rb[r];
+    }
+  };
+  fetch(0);
+  stash();
+  __syncthreads();
+  for (int64_t k0 = 0; k0 < g.K; k0 += BK) {
+    const bool more = k0 + BK < g.K;
+    if (more) fetch(k0 + BK);
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      const float4 a = *reinterpret_cast<const float4*>(&As[kk][swz(4 * ty, kk)]);
+      const float4 b = *reinterpret_cast<const float4*>(&Bs[kk][swz(4 * tx, kk)]);
+      const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+    if (more) {
+      stash();
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t gm = m0 + 4 * ty + i;
+    if (gm >= g.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t gn = n0 + 4 * tx + j;
+      if (gn >= g.N) continue;
+      float* c = C + gm + gn * g.ldc;
+      *c = g.beta == 0.f ? g.alpha * acc[i][j] : fmaf(g.alpha, acc[i][j], g.beta * *c);
+    }
+  }
+}
+
+cudaError_t gemm_f32(bool ta, bool tb, const GemmF32& g, int64_t batch, cudaStream_t s) {
+  if (g.M <= 0 || g.N <= 0 || batch <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)((g.M + 63) / 64), (unsigned)((g.N + 63) / 64), (unsigned)batch);
+  if (ta && !tb) gemm_f32_kernel<true, false><<<grid, 256, 0, s>>>(g);
+  else if (!ta && !tb) gemm_f32_kernel<false, false><<<grid, 256, 0, s>>>(g);
+  else if (!ta && tb) gemm_f32_kernel<false, true><<<grid, 256, 0, s>>>(g);
+  else gemm_f32_kernel<true, true><<<grid, 256, 0, s>>>(g);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// L32 = lower triangle of L (FP64 -> FP32), zeros above.
+__global__ void lower_f32_kernel(int64_t n, const double* __restrict__ L, float* __restrict__ L32) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = (uint32_t)e % (uint32_t)n, j = (uint32_t)e / (uint32_t)n;
+    L32[e] = i >= j ? (float)L[e] : 0.f;
+  }
+}
+
+// Diagonal 32 x 32 blocks of X := their inverses (Dinv, stored block after block).
+__global__ void place_diag_f32_kernel(int64_t n, const float* __restrict__ Dinv, float* __restrict__ X) {
+  const int64_t i0 = (int64_t)blockIdx.x * 32;
+  for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+    const int a = e & 31, b = e >> 5;
+    if (i0 + a < n && i0 + b < n) X[(i0 + a) + (i0 + b) * n] = Dinv[(size_t)blockIdx.x * 1024 + a + 32 * b];
+  }
+}
+
+// X := L^{-1} in place (X holds L, lower, zeros above; W is n x n scratch).  Starting
+// from inverted 32 x 32 diagonal blocks, adjacent s x s inverted blocks are merged into
+// 2s x 2s ones: [A 0; L21 C]^{-1} has off-diagonal block -C^{-1} L21 A^{-1}, two GEMMs
+// per merge, all merges of one size in one batched launch.
+cudaError_t tri_inverse_f32(int64_t n, float* X, float* W, float* Dinv, cudaStream_t s) {
+  const int nblk = (int)((n + 31) / 32);
+  cudaError_t e = diag_block_inverse_f32(n, X, Dinv, s);
+  if (e != cudaSuccess) return e;
+  place_diag_f32_kernel<<<nblk, 256, 0, s>>>(n, Dinv, X);
+  note_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  for (int64_t sz = 32; sz < n; sz *= 2) {
+    const int64_t full = n / (2 * sz);         // merges with two full sz blocks
+    const int64_t tail0 = full * 2 * sz;       // a last, shorter merge starts here
+    for (int part = 0; part < 2; ++part) {
+      const int64_t i0 = part == 0 ? 0 : tail0;
+      const int64_t batch = part == 0 ? full : (tail0 + sz < n ? 1 : 0);
+      if (batch == 0) continue;
+      const int64_t s2 = part == 0 ? sz : n - tail0 - sz;  // rows of the lower block
+      const int64_t stride = 2 * sz * (n + 1);
+      const int64_t a11 = i0 + i0 * n, a21 = (i0 + sz) + i0 * n, a22 = (i0 + sz) + (i0 + sz) * n;
+      GemmF32 g1{s2, sz, sz, n, n, n, stride, stride, stride, X + a21, X + a11, W + a21, 1.f, 0.f};
+      if ((e = gemm_f32(false, false, g1, batch, s)) != cudaSuccess) return e;   // W21 = L21 A^{-1}
+      GemmF32 g2{s2, sz, s2, n, n, n, stride, stride, stride, X + a22, W + a21, X + a21, -1.f, 0.f};
+      if ((e = gemm_f32(false, false, g2, batch, s)) != cudaSuccess) return e;   // X21 = -C^{-1} W21
+    }
+  }
+  return cudaSuccess;
+}
+
 cudaError_t mixed_setup(int64_t n, const double* L, const double* G2, int precision, float* L32, float* P32,
                         float* G2_32, float* Bt32, void* Bt16, float* Dinv32, cudaStream_t s) {
   const int64_t nn = n * n;
-  f64_to_f32_kernel<<<grid_small(nn), 256, 0, s>>>(nn, L, L32);
+  lower_f32_kernel<<<grid_small(nn), 256, 0, s>>>(n, L, L32);
   note_launch();
   if (G2) {
     f64_to_f32_kernel<<<grid_small(nn), 256, 0, s>>>(nn, G2, G2_32);
     note_launch();
   }
-  identity_f32_kernel<<<grid_small(nn), 256, 0, s>>>(n, P32);
-  note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  // P = L^{-T} L^{-1} in FP32 from the FP64 Cholesky factor.
-  if ((e = trsm_binv_f32(n, n, L32, Dinv32, P32, n, true, true, s)) != cudaSuccess) return e;
+  // P = L^{-T} L^{-1} in FP32 from the FP64 Cholesky factor: L32 := L^{-1} (P32 serves as
+  // the merge scratch), then P = (L^{-1})^T L^{-1}.
+  if ((e = tri_inverse_f32(n, L32, P32, Dinv32, s)) != cudaSuccess) return e;
+  GemmF32 gp{n, n, n, n, n, n, 0, 0, 0, L32, L32, P32, 1.f, 0.f};
+  if ((e = gemm_f32(true, false, gp, 1, s)) != cudaSuccess) return e;
   if (!G2) return cudaSuccess;  // matrix-free route: B is never formed
   // B^T = Abar2 P (both symmetric), so column i of B^T is row i of B = P Abar2.
-  const unsigned nt = (unsigned)((n + 31) / 32);
-  gemm_tn_f32_kernel<<<dim3(nt, nt), 256, 0, s>>>(n, G2_32, P32, Bt32);
-  note_launch();
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  GemmF32 gb{n, n, n, n, n, n, 0, 0, 0, G2_32, P32, Bt32, 1.f, 0.f};
+  if ((e = gemm_f32(false, false, gb, 1, s)) != cudaSuccess) return e;
   if (precision == ILS_BF16_REFINE) {
     f32_to_bf16_kernel<<<grid_small(nn), 256, 0, s>>>(nn, Bt32, static_cast<__nv_bfloat16*>(Bt16));
     note_launch();
