@@ -40,14 +40,15 @@ BF16_PEAK_TFLOPS = 1982.7  # measured cuBLAS BF16 burst rate on this machine (MEASU
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="bound on the CPU oracle sample")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the sparse, batched and warm-start measurements")
-    ap.add_argument("--stream-only", action="store_true",
-                    help="only time the matrix-free A_2 stream on the tall 278144 x 500 instance")
+    ap.add_argument("--only", choices=["stream", "sparse", "batched", "warm"],
+                    help="print only one secondary measurement (for profiling runs): the matrix-free stream on "
+                         "the tall 278144 x 500 instance, or the sparse, batched or warm-start configuration")
     return ap.parse_args()
 
 
@@ -428,8 +429,12 @@ def main():
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    if args.stream_only:
-        print(json.dumps(measure_stream(ils, torch, np, dev, reps=5)), flush=True)
+    if args.only:
+        fn = {"stream": lambda: measure_stream(ils, torch, np, dev, reps=5),
+              "sparse": lambda: measure_sparse(ils, torch, np, dev),
+              "batched": lambda: measure_batched(ils, torch, np, dev),
+              "warm": lambda: measure_warm(ils, torch, np, dev)}[args.only]
+        print(json.dumps(fn()), flush=True)
         return
     if world > 1:
         import torch.distributed as dist
@@ -457,19 +462,25 @@ def main():
             solver.refactor(At, stream=stream)
             return solver.solve(b, x, tol=TOL_RELRES, stream=stream)
 
-        for _ in range(max(args.warmup, 3)):
-            info = step()
-        torch.cuda.synchronize()
+        # nvidia-smi starts before the warm-up so that its start-up does not overlap the
+        # timed region; every sample it takes falls in the loaded warm-up or timed steps.
+        sampler = ClockSampler(torch.cuda.current_device()) if (rank == 0 and with_clocks) else None
+        if sampler:
+            sampler.start()
+        t_warm = time.perf_counter()
+        while True:
+            for _ in range(max(args.warmup, 3)):
+                info = step()
+            torch.cuda.synchronize()
+            if sampler is None or time.perf_counter() - t_warm > 0.5:
+                break
         relerr = float(np.linalg.norm(x.cpu().numpy() - xs) / np.linalg.norm(xs))
         if not relerr <= 1e-10:
             raise SystemExit(f"accuracy gate failed: relerr {relerr:.3e}")
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         phases, infos = [], []
-        sampler = ClockSampler(torch.cuda.current_device()) if (rank == 0 and with_clocks) else None
         barrier()
         torch.cuda.synchronize()
-        if sampler:
-            sampler.start()
         launches0 = ils.binding.kernel_launches()
         wall0 = time.perf_counter()
         for i in range(steps):

@@ -540,7 +540,7 @@ ils_status pass_launch(ils_handle h, int64_t count) {
 }
 
 int64_t first_chunk(ils_handle h) {
-  if (h->opt.precision != ILS_FP64) return 6;
+  if (h->opt.precision != ILS_FP64) return 4;  // three refinements and the final test, typically
   return h->opt.method == ILS_SP ? 16 : 4;
 }
 
