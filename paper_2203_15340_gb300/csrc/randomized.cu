@@ -58,32 +58,40 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return red[kChainWarps];
 }
 
-// Key order of the SCD selection: larger |r| first, then lower index.
-__device__ __forceinline__ bool key_greater(double a, int i, double b, int j) {
+// Key order of the SCD selection: larger |r| first, then lower index.  |r| is compared
+// through its bit pattern (for non-negative doubles the unsigned integer order is the
+// numeric order), so the selection uses the integer pipes, not the scarce FP64 one.
+__device__ __forceinline__ bool key_greater(unsigned long long a, int i, unsigned long long b, int j) {
   return a > b || (a == b && i < j);
+}
+
+__device__ __forceinline__ unsigned long long abs_key(double v) {
+  return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
 }
 
 // Index of the i-th largest |r_s| (ties to the lowest index) by i rounds of a block
 // argmax restricted to keys below the previous round's key.  The expected number of
-// rounds under the rank law is about ln(n).  Returns -1 if r holds no finite entries.
-__device__ int select_ith_largest(const double* r, int n, int i, double* red_a, int* red_i) {
-  double prev_a = INFINITY;
+// rounds under the rank law is about ln(n).  NaN entries are never picked; returns -1 if
+// r holds no entry that can be.
+__device__ int select_ith_largest(const double* r, int n, int i, unsigned long long* red_a, int* red_i) {
+  constexpr unsigned long long kNaN = 0x7ff0000000000000ull;  // keys above this are NaN
+  unsigned long long prev_a = ~0ull;
   int prev_i = -1;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int round = 0; round < i; ++round) {
-    double best_a = -1.0;
+    unsigned long long best_a = 0ull;
     int best_i = n;
     for (int s = threadIdx.x; s < n; s += blockDim.x) {
-      const double a = fabs(r[s]);
+      const unsigned long long a = abs_key(r[s]);
       const bool below = a < prev_a || (a == prev_a && s > prev_i);
-      if (below && key_greater(a, s, best_a, best_i)) {
+      if (a <= kNaN && below && key_greater(a, s, best_a, best_i)) {
         best_a = a;
         best_i = s;
       }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      const double oa = __shfl_xor_sync(0xffffffffu, best_a, o);
+      const unsigned long long oa = __shfl_xor_sync(0xffffffffu, best_a, o);
       const int oi = __shfl_xor_sync(0xffffffffu, best_i, o);
       if (key_greater(oa, oi, best_a, best_i)) {
         best_a = oa;
@@ -97,11 +105,11 @@ __device__ int select_ith_largest(const double* r, int n, int i, double* red_a, 
     }
     __syncthreads();
     if (w == 0) {
-      double a = lane < kChainWarps ? red_a[lane] : -1.0;
+      unsigned long long a = lane < kChainWarps ? red_a[lane] : 0ull;
       int ii = lane < kChainWarps ? red_i[lane] : n;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        const double oa = __shfl_xor_sync(0xffffffffu, a, o);
+        const unsigned long long oa = __shfl_xor_sync(0xffffffffu, a, o);
         const int oi = __shfl_xor_sync(0xffffffffu, ii, o);
         if (key_greater(oa, oi, a, ii)) {
           a = oa;
@@ -136,7 +144,7 @@ __global__ void __launch_bounds__(kChainThreads) scd_chain_kernel(RandArgs a) {
   double* r = smem;
   double* beta = smem + n;
   __shared__ double red[kChainWarps + 1];
-  __shared__ double red_a[kChainWarps + 1];
+  __shared__ unsigned long long red_a[kChainWarps + 1];
   __shared__ int red_i[kChainWarps + 1];
   const double* bhat = a.bhat + (size_t)c * n;
   double part = 0.0;
