@@ -221,6 +221,31 @@ ils_status ils_batch_setup(ils_batch* b, int64_t count, const ils_problem* probs
 ils_status ils_batch_solve(ils_batch b, int64_t k, const double* const* B, const int64_t* ldb, double* const* X,
                            const int64_t* ldx, int x0_zero, double tol, ils_info* infos, ils_stream_t stream);
 
+/* Record one batch solve as a CUDA graph, to be replayed by ils_batch_run with a single
+ * graph launch (the batched form of the spec design: every problem's kernels, on
+ * the batch's internal streams, in one launch).  Nothing is computed by this call.
+ *   refactor  != 0: each replay first recomputes every setup product from the A pointers
+ *             given to ils_batch_setup (their contents may change between replays, their
+ *             addresses and shapes may not); 0: the products of the last setup are used.
+ *   k         right-hand sides per problem, 1 <= k <= 8.
+ *   B, ldb, X, ldx, x0_zero, tol  as in ils_batch_solve; these device buffers are baked
+ *             into the graph, so every replay reads B and writes X at the same addresses.
+ *   steps     outer steps recorded per problem (each returns at once once its problem
+ *             has converged); a problem that needs more is finished by ils_batch_run on
+ *             the host-driven path.
+ *   stream    must not be the legacy default stream (it cannot be captured).
+ * Replaces any earlier capture of the batch.  Errors: INVALID_ARG, CUDA. */
+ils_status ils_batch_capture(ils_batch b, int refactor, int64_t k, const double* const* B, const int64_t* ldb,
+                             double* const* X, const int64_t* ldx, int x0_zero, double tol, int64_t steps,
+                             ils_stream_t stream);
+
+/* Replay the captured batch solve on `stream` and synchronize it; problems that had not
+ * converged within the captured steps continue on the host-driven path.  infos [host,
+ * may be NULL] receives one ils_info per problem (a refactor's NOT_SPD or NONFINITE is
+ * reported there).  Returns ILS_OK or the first non-OK problem status; INVALID_ARG when
+ * nothing was captured. */
+ils_status ils_batch_run(ils_batch b, ils_info* infos, ils_stream_t stream);
+
 /* The handle of problem i (owned by the batch; for ils_get_matrix and diagnostics), or
  * NULL when i is out of range. */
 ils_handle ils_batch_handle(ils_batch b, int64_t i);

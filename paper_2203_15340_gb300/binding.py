@@ -100,6 +100,10 @@ SIGNATURES = {
     "ils_batch_solve": (ctypes.c_int, [_P, _I64, ctypes.POINTER(_P), ctypes.POINTER(_I64), ctypes.POINTER(_P),
                                        ctypes.POINTER(_I64), ctypes.c_int, ctypes.c_double, ctypes.POINTER(ils_info),
                                        _P]),
+    "ils_batch_capture": (ctypes.c_int, [_P, ctypes.c_int, _I64, ctypes.POINTER(_P), ctypes.POINTER(_I64),
+                                         ctypes.POINTER(_P), ctypes.POINTER(_I64), ctypes.c_int, ctypes.c_double,
+                                         _I64, _P]),
+    "ils_batch_run": (ctypes.c_int, [_P, ctypes.POINTER(ils_info), _P]),
     "ils_batch_handle": (_P, [_P, _I64]),
     "ils_batch_destroy": (None, [_P]),
     "ils_mlp_create": (ctypes.c_int, [ctypes.POINTER(_P), _I64, _I64, _I64, ctypes.c_uint64, _P]),
@@ -332,6 +336,33 @@ class BatchSolver:
         code = lib().ils_batch_solve(self.b, k, Bp, lb, Xp, lx, int(bool(x0_zero)), float(tol), infos,
                                      _stream_ptr(stream))
         _check(code, "ils_batch_solve", allow)
+        return list(infos)
+
+    def _ptrs(self, Bts, Xts):
+        count = self.count
+        k = Bts[0].shape[0]
+        Bp = (ctypes.c_void_p * count)()
+        Xp = (ctypes.c_void_p * count)()
+        lb = (ctypes.c_int64 * count)()
+        lx = (ctypes.c_int64 * count)()
+        for i, ((m, n, _), Bt, Xt) in enumerate(zip(self.shapes, Bts, Xts)):
+            Bp[i], lb[i] = _colmajor_ptr(Bt, m, k)
+            Xp[i], lx[i] = _colmajor_ptr(Xt, n, k)
+        return k, Bp, lb, Xp, lx
+
+    def capture(self, Bts, Xts, refactor=False, steps=8, x0_zero=True, tol=1e-12, stream=None):
+        """Record the batch solve (and, with refactor, the setup) as one CUDA graph.  The
+        tensors must stay alive: the graph reads and writes them at their addresses.
+        ``stream`` must be a non-default torch stream."""
+        k, Bp, lb, Xp, lx = self._ptrs(Bts, Xts)
+        self._cap_keep = (Bts, Xts)
+        _check(lib().ils_batch_capture(self.b, int(bool(refactor)), k, Bp, lb, Xp, lx, int(bool(x0_zero)),
+                                       float(tol), int(steps), _stream_ptr(stream)), "ils_batch_capture")
+
+    def run(self, stream=None, allow=(ILS_OK,)):
+        """Replay the captured graph; one ils_info per problem."""
+        infos = (ils_info * self.count)()
+        _check(lib().ils_batch_run(self.b, infos, _stream_ptr(stream)), "ils_batch_run", allow)
         return list(infos)
 
     def close(self):

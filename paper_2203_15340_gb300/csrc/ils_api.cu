@@ -544,10 +544,11 @@ int64_t first_chunk(ils_handle h) {
   return h->opt.method == ILS_SP ? 16 : 4;
 }
 
+ils_status pass_finish_enqueue(ils_handle h, double* X, int64_t ldx);
+void pass_collect(ils_handle h, ils_info* agg);
+
 ils_status pass_end(ils_handle h, double* X, int64_t ldx, ils_info* agg) {
   cudaStream_t s = h->stream;
-  const int64_t n = h->n, kk = h->pass_k;
-  const bool mixed = h->pass_mixed;
   const int64_t cap = h->opt.max_outer + 1;
   int64_t chunk = std::max<int64_t>(first_chunk(h), 1);
   for (;;) {
@@ -559,12 +560,30 @@ ils_status pass_end(ils_handle h, double* X, int64_t ldx, ils_info* agg) {
     if (st != ILS_OK) return st;
   }
   if (!h->h_st->done) return ILS_ERR_TIMEOUT;  // cannot happen: the cap launch always finishes
+  ils_status st = pass_finish_enqueue(h, X, ldx);
+  if (st != ILS_OK) return st;
+  ILS_CK(cudaStreamSynchronize(s));
+  pass_collect(h, agg);
+  return ILS_OK;
+}
+
+// The answer of the pass to X and the per-column results to the pinned host mirrors
+// (enqueued only; nothing here waits, so it can be captured in a graph).
+ils_status pass_finish_enqueue(ils_handle h, double* X, int64_t ldx) {
+  cudaStream_t s = h->stream;
+  const int64_t n = h->n, kk = h->pass_k;
   ILS_CK(copy_final_f64(n, kk, h->X0, h->X1, h->st, X, ldx, s));
   ILS_CK(cudaMemcpyAsync(h->h_rr, h->col_rr, sizeof(double) * kk, cudaMemcpyDeviceToHost, s));
   ILS_CK(cudaMemcpyAsync(h->h_bn, h->bnorm2, sizeof(double) * kk, cudaMemcpyDeviceToHost, s));
   ILS_CK(cudaMemcpyAsync(h->h_iters, h->col_iters, sizeof(int64_t) * kk, cudaMemcpyDeviceToHost, s));
   ILS_CK(cudaMemcpyAsync(h->h_inner, h->col_inner, sizeof(int64_t) * kk, cudaMemcpyDeviceToHost, s));
-  ILS_CK(cudaStreamSynchronize(s));
+  return ILS_OK;
+}
+
+// Fold the host mirrors of a finished pass into *agg (after a synchronization).
+void pass_collect(ils_handle h, ils_info* agg) {
+  const int64_t kk = h->pass_k;
+  const bool mixed = h->pass_mixed;
   for (int64_t c = 0; c < kk; ++c) {
     const double bn = h->h_bn[c];
     const double rel = bn > 0.0 ? std::sqrt(h->h_rr[c] / bn) : std::sqrt(h->h_rr[c]);
@@ -583,7 +602,6 @@ ils_status pass_end(ils_handle h, double* X, int64_t ldx, ils_info* agg) {
   }
   const int32_t st = h->h_st->status;
   if (st != 0 && agg->status == 0) agg->status = st;
-  return ILS_OK;
 }
 
 ils_status sp_pass(ils_handle h, int64_t c0, int64_t kk, const double* B, int64_t ldb, double* X, int64_t ldx,
@@ -848,9 +866,17 @@ void ils_destroy(ils_handle h) { free_handle(h); }
 // ---------------------------------------------------------------------------------------
 struct ils_batch_s {
   std::vector<ils_handle> h;
+  std::vector<ils_problem> probs;   // the caller's A of every problem (re-read by a captured refactor)
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> events;  // one per internal stream (join)
   cudaEvent_t fork = nullptr;
+  // captured solve (ils_batch_capture / ils_batch_run)
+  cudaGraphExec_t exec = nullptr;
+  bool cap_refactor = false;
+  int64_t cap_steps = 0;
+  int64_t cap_launches = 0;  // kernels per replay
+  std::vector<double*> cap_X;
+  std::vector<int64_t> cap_ldx;
 };
 
 namespace {
@@ -865,6 +891,7 @@ void free_batch(ils_batch b) {
   }
   for (cudaEvent_t e : b->events) cudaEventDestroy(e);
   if (b->fork) cudaEventDestroy(b->fork);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
   delete b;
 }
 
@@ -906,6 +933,7 @@ ils_status ils_batch_setup(ils_batch* out, int64_t count, const ils_problem* pro
     return ILS_ERR_CUDA;
   }
   b->h.assign(count, nullptr);
+  b->probs.assign(probs, probs + count);
   ils_status st = ILS_OK;
   for (int64_t i = 0; i < count && st == ILS_OK; ++i) {
     const ils_problem& pr = probs[i];
@@ -963,6 +991,101 @@ ils_status ils_batch_solve(ils_batch b, int64_t k, const double* const* B, const
   for (int64_t i = 0; i < count; ++i) {
     if (infos) infos[i] = agg[i];
     if (agg[i].status != ILS_OK && worst == ILS_OK) worst = (ils_status)agg[i].status;
+  }
+  return worst;
+}
+
+ils_status ils_batch_capture(ils_batch b, int refactor, int64_t k, const double* const* B, const int64_t* ldb,
+                             double* const* X, const int64_t* ldx, int x0_zero, double tol, int64_t steps,
+                             ils_stream_t stream) {
+  if (!b || k < 1 || k > kMaxRhsPerPass || !B || !X || !(tol >= 0.0) || steps < 1) return ILS_ERR_INVALID_ARG;
+  const int64_t count = (int64_t)b->h.size();
+  for (int64_t i = 0; i < count; ++i) {
+    const int64_t lb = ldb ? ldb[i] : b->h[i]->m, lx = ldx ? ldx[i] : b->h[i]->n;
+    if (!B[i] || !X[i] || lb < b->h[i]->m || lx < b->h[i]->n) return ILS_ERR_INVALID_ARG;
+  }
+  cudaStream_t user = (cudaStream_t)stream;
+  if (user == nullptr) return ILS_ERR_INVALID_ARG;  // the legacy stream cannot be captured
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  const int64_t launches0 = ils_kernel_launches();
+  ILS_CK(cudaStreamBeginCapture(user, cudaStreamCaptureModeRelaxed));
+  ils_status st = batch_fork(b, user) == cudaSuccess ? ILS_OK : ILS_ERR_CUDA;
+  b->cap_X.assign(count, nullptr);
+  b->cap_ldx.assign(count, 0);
+  for (int64_t i = 0; i < count && st == ILS_OK; ++i) {
+    ils_handle h = b->h[i];
+    const int64_t lb = ldb ? ldb[i] : h->m, lx = ldx ? ldx[i] : h->n;
+    b->cap_X[i] = X[i];
+    b->cap_ldx[i] = lx;
+    if (refactor) {
+      const ils_problem& pr = b->probs[i];
+      if (cudaMemcpy2DAsync(h->A, sizeof(double) * h->m, pr.A, sizeof(double) * pr.lda, sizeof(double) * h->m,
+                            h->n, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+        st = ILS_ERR_CUDA;
+      if (st == ILS_OK) st = compute_setup(h);
+    }
+    if (st == ILS_OK) st = pass_begin(h, 0, k, B[i], lb, X[i], lx, x0_zero, tol);
+    if (st == ILS_OK) st = pass_launch(h, steps);
+    if (st == ILS_OK && cudaMemcpyAsync(h->h_st, h->st, sizeof(SolveState), cudaMemcpyDeviceToHost, h->stream) !=
+                            cudaSuccess)
+      st = ILS_ERR_CUDA;
+    if (st == ILS_OK) st = pass_finish_enqueue(h, X[i], lx);
+  }
+  if (st == ILS_OK && batch_join(b, user) != cudaSuccess) st = ILS_ERR_CUDA;
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(user, &graph);
+  if (st == ILS_OK && ec != cudaSuccess) st = record_cuda_error(ec, "cudaStreamEndCapture", __LINE__);
+  if (st == ILS_OK) {
+    const cudaError_t ei = cudaGraphInstantiate(&b->exec, graph, 0);
+    if (ei != cudaSuccess) st = record_cuda_error(ei, "cudaGraphInstantiate", __LINE__);
+  }
+  if (graph) cudaGraphDestroy(graph);
+  cudaGetLastError();
+  if (st != ILS_OK) {
+    b->exec = nullptr;
+    return st;
+  }
+  b->cap_refactor = refactor != 0;
+  b->cap_steps = steps;
+  b->cap_launches = ils_kernel_launches() - launches0;
+  return ILS_OK;
+}
+
+ils_status ils_batch_run(ils_batch b, ils_info* infos, ils_stream_t stream) {
+  if (!b || !b->exec) return ILS_ERR_INVALID_ARG;
+  cudaStream_t user = (cudaStream_t)stream;
+  ILS_CK(cudaGraphLaunch(b->exec, user));
+  note_launch(b->cap_launches);
+  ILS_CK(cudaStreamSynchronize(user));
+  const int64_t count = (int64_t)b->h.size();
+  ils_status worst = ILS_OK;
+  for (int64_t i = 0; i < count; ++i) {
+    ils_handle h = b->h[i];
+    ils_info agg;
+    std::memset(&agg, 0, sizeof(agg));
+    if (b->cap_refactor) {
+      h->h_status[1] = h->opt.gram == ILS_GRAM_SPLIT ? h->h_status[1] : 0;
+      ils_status sst = h->h_status[1] != 0 ? (h->h_status[1] == 2 ? ILS_ERR_NONFINITE : ILS_ERR_TIMEOUT)
+                                           : (ils_status)*h->h_status;
+      if (sst != ILS_OK) {
+        agg.status = sst;
+        if (infos) infos[i] = agg;
+        if (worst == ILS_OK) worst = sst;
+        continue;
+      }
+    }
+    h->pass_launched = b->cap_steps;
+    if (h->h_st->done) {
+      pass_collect(h, &agg);  // the graph already stored x and the per-column results
+    } else {
+      ils_status st = pass_end(h, b->cap_X[i], b->cap_ldx[i], &agg);  // more steps than captured
+      if (st != ILS_OK) return st;
+    }
+    if (infos) infos[i] = agg;
+    if (agg.status != ILS_OK && worst == ILS_OK) worst = (ils_status)agg.status;
   }
   return worst;
 }
