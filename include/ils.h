@@ -188,6 +188,15 @@ ils_status ils_get_matrix(ils_handle h, int which, double* dst, int64_t ldd, ils
  * Returns the number of values written, or -1 on a bad argument. */
 int ils_get_timings(ils_handle h, double* out, int count);
 
+/* The launch shape the autotuner picked for the mixed-precision sweep GEMV of an n x n
+ * operator with k right-hand sides (bf16 != 0: the BF16 copy of B): *warps per CTA and
+ * *blocks CTAs.  The first mixed-precision setup of a given n (rounded up to 32) times
+ * 1, 2, 4 and 8 warps per CTA with one, two or four rows per warp on its own operators
+ * and keeps the fastest for the rest of the process (k classes: k <= 2 and k > 2).
+ * Returns 1 when a tuned shape exists, else 0 (the default shape is then used).  Host
+ * only; warps and blocks may be NULL. */
+int ils_tuned_shape(int64_t n, int64_t k, int bf16, int* warps, int* blocks);
+
 /* Number of CUDA kernels this library has launched in this process so far
  * (all handles, all threads).  Host only. */
 int64_t ils_kernel_launches(void);

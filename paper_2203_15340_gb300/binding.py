@@ -95,6 +95,8 @@ SIGNATURES = {
     "ils_aq_product": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
     "ils_get_timings": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
     "ils_kernel_launches": (ctypes.c_int64, []),
+    "ils_tuned_shape": (ctypes.c_int, [_I64, _I64, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_int)]),
     "ils_batch_setup": (ctypes.c_int, [ctypes.POINTER(_P), _I64, ctypes.POINTER(ils_problem),
                                        ctypes.POINTER(ils_options), _P]),
     "ils_batch_solve": (ctypes.c_int, [_P, _I64, ctypes.POINTER(_P), ctypes.POINTER(_I64), ctypes.POINTER(_P),
@@ -146,6 +148,14 @@ def lib():
 def kernel_launches() -> int:
     """Kernels launched by libils.so in this process so far."""
     return int(lib().ils_kernel_launches())
+
+
+def tuned_shape(n: int, k: int, bf16: bool = False):
+    """(warps per CTA, CTAs) the autotuner picked for the sweep of an n x n operator, or None."""
+    w, b = ctypes.c_int(), ctypes.c_int()
+    if lib().ils_tuned_shape(n, k, int(bool(bf16)), ctypes.byref(w), ctypes.byref(b)):
+        return w.value, b.value
+    return None
 
 
 def status_string(code: int) -> str:

@@ -408,6 +408,14 @@ ils_status setup_finish(ils_handle h) {
   return ILS_OK;
 }
 
+// Autotune the sweep shapes for this handle's n once per process (mixed precision only).
+ils_status tune_handle(ils_handle h) {
+  if (h->opt.precision == ILS_FP64 || h->opt.method != ILS_SP) return ILS_OK;
+  ILS_CK(tune_sweeps(h->n, h->opt.precision, h->P32, h->mf ? nullptr : h->Bt32, h->Bt16, h->r32, h->d32a, h->st,
+                     h->stream));
+  return ILS_OK;
+}
+
 void free_handle(ils_handle h) {
   if (!h) return;
   if (h->block) cudaFreeAsync(h->block, h->stream);
@@ -767,6 +775,7 @@ ils_status ils_setup_csr(ils_handle* out, int64_t m, int64_t n, int64_t p, int64
   st = compute_setup_sparse(h, rowptr, colind, val);
   if (st == ILS_OK) st = setup_finish(h);
   if (st == ILS_OK && h->opt.timing) collect_timings(h);
+  if (st == ILS_OK) st = tune_handle(h);
   if (st != ILS_OK) {
     free_handle(h);
     return st;
@@ -785,6 +794,7 @@ ils_status ils_refactor(ils_handle h, const double* A, int64_t lda, ils_stream_t
   ils_status st = compute_setup(h);
   if (st == ILS_OK) st = setup_finish(h);
   if (st == ILS_OK && h->opt.timing) collect_timings(h);
+  if (st == ILS_OK) st = tune_handle(h);
   return st;
 }
 
@@ -805,6 +815,10 @@ int ils_get_timings(ils_handle h, double* out, int count) {
 }
 
 int64_t ils_kernel_launches(void) { return ils::g_launches.load(std::memory_order_relaxed); }
+
+int ils_tuned_shape(int64_t n, int64_t k, int bf16, int* warps, int* blocks) {
+  return ils::ils_tuned_shape_impl(n, k, bf16, warps, blocks);
+}
 
 ils_status ils_solve_many(ils_handle h, int64_t k, const double* B, int64_t ldb, double* X, int64_t ldx,
                           int x0_zero, double tol, ils_info* info, ils_stream_t stream) {
@@ -950,6 +964,7 @@ ils_status ils_batch_setup(ils_batch* out, int64_t count, const ils_problem* pro
     st = compute_setup(h);
   }
   for (int64_t i = 0; i < count && st == ILS_OK; ++i) st = setup_finish(b->h[i]);
+  for (int64_t i = 0; i < count && st == ILS_OK; ++i) st = tune_handle(b->h[i]);
   if (st == ILS_OK && batch_join(b, (cudaStream_t)stream) != cudaSuccess) st = ILS_ERR_CUDA;
   if (st != ILS_OK) {
     free_batch(b);

@@ -169,6 +169,19 @@ struct MixedArgs {
   const int32_t* col_done;
   SolveState* st;
 };
+// Launch shape of the sweep GEMV: warps per CTA and CTAs (each warp takes whole rows).
+struct SweepShape {
+  int32_t warps;
+  int32_t blocks;
+};
+// The shape for (n, k, operator type): tuned if ils_tune_sweeps ran for it, else a default.
+SweepShape sweep_shape(int64_t n, int64_t k, bool bf16);
+// Time the candidate shapes for (n, k) on the handle's operators (P32 and Bt32 or Bt16) and
+// cache the fastest, once per process.  Synchronizes `s`; not for use inside a capture.
+cudaError_t tune_sweeps(int64_t n, int precision, const float* P32, const float* Bt32, const void* Bt16,
+                        float* scratch_in, float* scratch_out, SolveState* st, cudaStream_t s);
+// 1 and the tuned shape of (n, k, operator type) if the autotuner has one, else 0.
+int ils_tuned_shape_impl(int64_t n, int64_t k, int bf16, int* warps, int* blocks);
 // L32/P32/G2_32/Bt32 are n x n FP32 buffers, Bt16 an n x n BF16 buffer (BF16 mode only).
 // G2 == nullptr (matrix-free route) forms only P32.
 cudaError_t mixed_setup(int64_t n, const double* L, const double* G2, int precision, float* L32, float* P32,

@@ -13,6 +13,9 @@
 
 #include <algorithm>
 
+#include <map>
+#include <mutex>
+
 #include "ils_internal.h"
 
 namespace ils {
@@ -73,19 +76,19 @@ __global__ void __launch_bounds__(256) gemm_tn_f32_kernel(int64_t n, const float
 __device__ __forceinline__ float ld_op(const float* p, int64_t i) { return p[i]; }
 __device__ __forceinline__ float ld_op(const __nv_bfloat16* p, int64_t i) { return __bfloat162float(p[i]); }
 
-constexpr int kSweepWarps = 2;
-
 // out(:,c) = M^T v(:,c) (+ add(:,c)); column i of M is row i of the operator.  KR is the
-// number of right-hand sides, fixed at compile time so no predicated work is issued.
+// number of right-hand sides, fixed at compile time so no predicated work is issued.  Each
+// warp takes whole rows; the launch shape (warps per CTA, CTAs) is picked by tune_sweeps,
+// and the result does not depend on it (every row is reduced in the same order).
 template <typename TM, int KR>
-__global__ void __launch_bounds__(32 * kSweepWarps) sweep_kernel(MixedArgs a, const TM* __restrict__ M,
-                                                                 const float* __restrict__ v,
-                                                                 const float* __restrict__ add,
-                                                                 float* __restrict__ out) {
+__global__ void __launch_bounds__(256) sweep_kernel(MixedArgs a, const TM* __restrict__ M,
+                                                    const float* __restrict__ v,
+                                                    const float* __restrict__ add,
+                                                    float* __restrict__ out) {
   if (*((volatile int32_t*)&a.st->done)) return;
   const int64_t n = a.n;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int64_t i = (int64_t)blockIdx.x * kSweepWarps + w; i < n; i += (int64_t)gridDim.x * kSweepWarps) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int64_t i = (int64_t)blockIdx.x * nw + w; i < n; i += (int64_t)gridDim.x * nw) {
     const TM* col = M + i * n;
     float acc[KR];
 #pragma unroll
@@ -104,17 +107,18 @@ __global__ void __launch_bounds__(32 * kSweepWarps) sweep_kernel(MixedArgs a, co
 }
 
 template <typename TM>
-void launch_sweep(const MixedArgs& a, int blocks, const TM* M, const float* v, const float* add, float* out,
+void launch_sweep(const MixedArgs& a, SweepShape sh, const TM* M, const float* v, const float* add, float* out,
                   cudaStream_t s) {
+  const dim3 grid((unsigned)sh.blocks), block((unsigned)(32 * sh.warps));
   switch ((int)a.k) {
-    case 1: sweep_kernel<TM, 1><<<blocks, 32 * kSweepWarps, 0, s>>>(a, M, v, add, out); break;
-    case 2: sweep_kernel<TM, 2><<<blocks, 32 * kSweepWarps, 0, s>>>(a, M, v, add, out); break;
-    case 3: sweep_kernel<TM, 3><<<blocks, 32 * kSweepWarps, 0, s>>>(a, M, v, add, out); break;
-    case 4: sweep_kernel<TM, 4><<<blocks, 32 * kSweepWarps, 0, s>>>(a, M, v, add, out); break;
-    case 5: sweep_kernel<TM, 5><<<blocks, 32 * kSweepWarps, 0, s>>>(a, M, v, add, out); break;
-    case 6: sweep_kernel<TM, 6><<<blocks, 32 * kSweepWarps, 0, s>>>(a, M, v, add, out); break;
-    case 7: sweep_kernel<TM, 7><<<blocks, 32 * kSweepWarps, 0, s>>>(a, M, v, add, out); break;
-    default: sweep_kernel<TM, 8><<<blocks, 32 * kSweepWarps, 0, s>>>(a, M, v, add, out); break;
+    case 1: sweep_kernel<TM, 1><<<grid, block, 0, s>>>(a, M, v, add, out); break;
+    case 2: sweep_kernel<TM, 2><<<grid, block, 0, s>>>(a, M, v, add, out); break;
+    case 3: sweep_kernel<TM, 3><<<grid, block, 0, s>>>(a, M, v, add, out); break;
+    case 4: sweep_kernel<TM, 4><<<grid, block, 0, s>>>(a, M, v, add, out); break;
+    case 5: sweep_kernel<TM, 5><<<grid, block, 0, s>>>(a, M, v, add, out); break;
+    case 6: sweep_kernel<TM, 6><<<grid, block, 0, s>>>(a, M, v, add, out); break;
+    case 7: sweep_kernel<TM, 7><<<grid, block, 0, s>>>(a, M, v, add, out); break;
+    default: sweep_kernel<TM, 8><<<grid, block, 0, s>>>(a, M, v, add, out); break;
   }
   note_launch();
 }
@@ -349,25 +353,129 @@ cudaError_t mixed_setup(int64_t n, const double* L, const double* G2, int precis
   return e;
 }
 
-int mixed_sweep_blocks(int64_t n) {
-  return (int)std::max<int64_t>(1, std::min<int64_t>((n + kSweepWarps - 1) / kSweepWarps, 1024));
+// ---------------------------------------------------------------------------------------
+// Sweep-shape autotuner.  For each (n rounded up to 32, k class, operator type) the first
+// setup that needs it times every candidate shape on the handle's own operators and keeps
+// the fastest for the rest of the process.  Candidates: 1, 2, 4 or 8 warps per CTA, with
+// one, two or four rows per warp in the first wave (CTAs = ceil(n / (warps x rows))).
+// ---------------------------------------------------------------------------------------
+namespace {
+struct TuneKey {
+  int64_t nb;
+  int kc;
+  int bf16;
+  bool operator<(const TuneKey& o) const {
+    return nb != o.nb ? nb < o.nb : (kc != o.kc ? kc < o.kc : bf16 < o.bf16);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, SweepShape> g_tune;
+
+TuneKey tune_key(int64_t n, int64_t k, bool bf16) { return TuneKey{(n + 31) / 32, k <= 2 ? 1 : 8, bf16 ? 1 : 0}; }
+
+SweepShape default_shape(int64_t n) {
+  return SweepShape{2, (int32_t)std::max<int64_t>(1, std::min<int64_t>((n + 1) / 2, 1024))};
+}
+
+template <typename TM>
+cudaError_t time_shape(const MixedArgs& a, SweepShape sh, const TM* M, const float* v, float* out, cudaStream_t s,
+                       float* ms) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) {
+    for (int r = 0; r < 2; ++r) launch_sweep<TM>(a, sh, M, v, nullptr, out, s);
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < 5; ++r) launch_sweep<TM>(a, sh, M, v, nullptr, out, s);
+    cudaEventRecord(e1, s);
+    e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return e == cudaSuccess ? cudaGetLastError() : e;
+}
+}  // namespace
+
+SweepShape sweep_shape(int64_t n, int64_t k, bool bf16) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tune.find(tune_key(n, k, bf16));
+  return it != g_tune.end() ? it->second : default_shape(n);
+}
+
+cudaError_t tune_sweeps(int64_t n, int precision, const float* P32, const float* Bt32, const void* Bt16,
+                        float* scratch_in, float* scratch_out, SolveState* st, cudaStream_t s) {
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    bool all = g_tune.count(tune_key(n, 1, false)) && g_tune.count(tune_key(n, 8, false));
+    if (precision == ILS_BF16_REFINE)
+      all = all && g_tune.count(tune_key(n, 1, true)) && g_tune.count(tune_key(n, 8, true));
+    if (all) return cudaSuccess;
+  }
+  cudaError_t e = cudaMemsetAsync(st, 0, sizeof(SolveState), s);  // done = 0: the kernels run
+  if (e != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(scratch_in, 0, sizeof(float) * n * kMaxRhsPerPass, s)) != cudaSuccess) return e;
+  for (int bf = 0; bf < 2; ++bf) {
+    const bool bf16 = bf == 1;
+    if (bf16 && precision != ILS_BF16_REFINE) continue;
+    for (int64_t k : {1, 8}) {
+      const TuneKey key = tune_key(n, k, bf16);
+      {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        if (g_tune.count(key)) continue;
+      }
+      MixedArgs a{};
+      a.n = n;
+      a.k = k;
+      a.st = st;
+      SweepShape best = default_shape(n);
+      float best_ms = 1e30f;
+      for (int warps : {1, 2, 4, 8}) {
+        for (int rows : {1, 2, 4}) {
+          const SweepShape sh{warps, (int32_t)std::max<int64_t>(1, (n + warps * rows - 1) / (warps * rows))};
+          float ms = 0.f;
+          e = bf16 ? time_shape<__nv_bfloat16>(a, sh, static_cast<const __nv_bfloat16*>(Bt16), scratch_in,
+                                               scratch_out, s, &ms)
+                   : time_shape<float>(a, sh, Bt32 ? Bt32 : P32, scratch_in, scratch_out, s, &ms);
+          if (e != cudaSuccess) return e;
+          if (ms < best_ms) {
+            best_ms = ms;
+            best = sh;
+          }
+        }
+      }
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      g_tune[key] = best;
+    }
+  }
+  return cudaSuccess;
+}
+
+int ils_tuned_shape_impl(int64_t n, int64_t k, int bf16, int* warps, int* blocks) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tune.find(tune_key(n, k, bf16 != 0));
+  if (it == g_tune.end()) return 0;
+  if (warps) *warps = it->second.warps;
+  if (blocks) *blocks = it->second.blocks;
+  return 1;
 }
 
 // One refinement step after the residual launch: r32, d_1 = P r, d_{s+1} = B d_s + P r, x += d.
 cudaError_t mixed_correct(const MixedArgs& a, int precision, cudaStream_t s) {
   residual_to_f32_kernel<<<grid_small(a.n * a.k), 256, 0, s>>>(a);
   note_launch();
-  const int blocks = mixed_sweep_blocks(a.n);
+  const SweepShape sh32 = sweep_shape(a.n, a.k, false);
   // c = P r  (kept in a.c32; also the first iterate d_1)
-  launch_sweep<float>(a, blocks, a.P32, a.r32, nullptr, a.c32, s);
+  launch_sweep<float>(a, sh32, a.P32, a.r32, nullptr, a.c32, s);
   const float* dcur = a.c32;
   float* bufs[2] = {a.d32[0], a.d32[1]};
   for (int sw = 1; sw < a.sweeps; ++sw) {
     float* dn = bufs[sw & 1];
     if (precision == ILS_BF16_REFINE)
-      launch_sweep<__nv_bfloat16>(a, blocks, static_cast<const __nv_bfloat16*>(a.Bt16), dcur, a.c32, dn, s);
+      launch_sweep<__nv_bfloat16>(a, sweep_shape(a.n, a.k, true), static_cast<const __nv_bfloat16*>(a.Bt16), dcur,
+                                  a.c32, dn, s);
     else
-      launch_sweep<float>(a, blocks, a.Bt32, dcur, a.c32, dn, s);
+      launch_sweep<float>(a, sh32, a.Bt32, dcur, a.c32, dn, s);
     dcur = dn;
   }
   refine_update_kernel<<<grid_small(a.n * a.k), 256, 0, s>>>(a, dcur);
@@ -385,8 +493,8 @@ cudaError_t mixed_correct_mf(const MixedArgs& a, int precision, int64_t q, const
                              double* d64, float* t32, cudaStream_t s) {
   residual_to_f32_kernel<<<grid_small(a.n * a.k), 256, 0, s>>>(a);
   note_launch();
-  const int blocks = mixed_sweep_blocks(a.n);
-  launch_sweep<float>(a, blocks, a.P32, a.r32, nullptr, a.c32, s);
+  const SweepShape sh32 = sweep_shape(a.n, a.k, false);
+  launch_sweep<float>(a, sh32, a.P32, a.r32, nullptr, a.c32, s);
   const float* dcur = a.c32;
   float* bufs[2] = {a.d32[0], a.d32[1]};
   const int prec = precision == ILS_BF16_REFINE ? 2 : 1;
@@ -400,7 +508,7 @@ cudaError_t mixed_correct_mf(const MixedArgs& a, int precision, int64_t q, const
     sweep_rhs_kernel<<<grid_small(a.n * a.k), 256, 0, s>>>(a, v, t32);
     note_launch();
     float* dn = bufs[sw & 1];
-    launch_sweep<float>(a, blocks, a.P32, t32, nullptr, dn, s);
+    launch_sweep<float>(a, sh32, a.P32, t32, nullptr, dn, s);
     dcur = dn;
   }
   refine_update_kernel<<<grid_small(a.n * a.k), 256, 0, s>>>(a, dcur);

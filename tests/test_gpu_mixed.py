@@ -77,3 +77,23 @@ def test_mixed_precision_needs_sp(ils):
     with pytest.raises(ils.ILSError) as e:
         ils.Solver(colmajor(inst.A), inst.p, ils.options(precision=ils.ILS_FP32_REFINE, method=ils.ILS_SP_SCD))
     assert e.value.code == ils.ILS_ERR_INVALID_ARG
+
+
+def test_sweep_autotuner_picks_a_shape_and_keeps_results(ils):
+    """The first mixed setup of an n tunes the sweep shape; solving with the tuned shape gives
+    the same answer as the oracle to 1e-10 (the shape does not change the arithmetic)."""
+    import torch
+    inst = W.dense_gaussian(2400, 600, 300, 0.3, 77)
+    s = ils.Solver(colmajor(inst.A), inst.p, ils.options(precision=ils.ILS_BF16_REFINE))
+    for k in (1, 8):
+        for bf16 in (False, True):
+            sh = ils.binding.tuned_shape(inst.n, k, bf16)
+            assert sh is not None
+            warps, blocks = sh
+            assert warps in (1, 2, 4, 8) and blocks >= 1
+    x = vec(np.zeros(inst.n))
+    info = s.solve(vec(inst.b), x, tol=1e-12)
+    torch.cuda.synchronize()
+    xs = O.qr_cholesky_solve(inst.A, inst.b, inst.p)
+    assert info.status == ils.ILS_OK and relerr(x.cpu().numpy(), xs) <= 1e-10
+    s.close()
