@@ -463,20 +463,70 @@ __device__ __forceinline__ void load_cols(StepCols<T>& out, const StepPick& sp, 
   }
 }
 
-// Sum over the cluster of (v0, v1, v2): lane r stores this CTA's triple into CTA r's
-// slot (double-buffered by round), a cluster barrier publishes the stores, and every
-// CTA adds the CS triples in rank order.
-template <class T, int CS>
-__device__ __forceinline__ void cluster_sum3(T& v0, T& v1, T& v2, T* slots, int& round, int rank,
-                                             cooperative_groups::cluster_group& cl) {
-  T* buf = slots + (round & 1) * 4 * CS;
-  if (threadIdx.x < CS) {
-    T* dst = cl.map_shared_rank(buf + 4 * rank, threadIdx.x);
-    dst[0] = v0;
-    dst[1] = v1;
-    dst[2] = v2;
+// Distributed-shared-memory exchange.  Lane r of every CTA writes this CTA's triple into
+// slot `rank` of CTA r with st.async, which also counts the bytes on CTA r's mbarrier for
+// that buffer; each CTA waits for its own mbarrier (CS triples), so no cluster-wide
+// barrier (and no release fence) sits on the chain.  Buffers alternate by round: a peer
+// can only write round R + 2 after this CTA has sent round R + 1, i.e. after it has read
+// round R.  Waits are bounded by the global timer (2 s); on a timeout the chain records
+// ILS_ERR_TIMEOUT and stops.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint32_t map_rank(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void xbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)));
+}
+__device__ __forceinline__ void xbar_expect(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool xbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t addr = smem_addr(bar);
+  uint64_t t0 = 0;
+  for (uint32_t spin = 0;; ++spin) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((spin & 63) == 0) {
+      uint64_t t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      if (spin == 0) t0 = t;
+      else if (t - t0 > 2000000000ull) return false;
+    }
   }
-  cl.sync();  // release our stores, acquire everyone's
+}
+__device__ __forceinline__ void st_async_triple(uint32_t raddr, uint32_t rbar, float v0, float v1, float v2) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];"
+               ::"r"(raddr), "f"(v0), "f"(v1), "f"(v2), "f"(0.f), "r"(rbar) : "memory");
+}
+__device__ __forceinline__ void st_async_triple(uint32_t raddr, uint32_t rbar, double v0, double v1, double v2) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f64 [%0], {%1, %2}, [%3];"
+               ::"r"(raddr), "d"(v0), "d"(v1), "r"(rbar) : "memory");
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f64 [%0], {%1, %2}, [%3];"
+               ::"r"(raddr + 16u), "d"(v2), "d"(0.0), "r"(rbar) : "memory");
+}
+
+// Sum over the cluster of (v0, v1, v2), added in rank order (the same in every CTA).
+// Returns false on a timed-out wait.
+template <class T, int CS>
+__device__ __forceinline__ bool cluster_sum3(T& v0, T& v1, T& v2, T* slots, uint64_t* xbar, int& round, int rank) {
+  const int b = round & 1;
+  T* buf = slots + b * 4 * CS;  // [CS][4]
+  uint64_t* bar = xbar + b;
+  if (threadIdx.x == 0) xbar_expect(bar, (uint32_t)(CS * 4 * sizeof(T)));
+  if (threadIdx.x < CS) {
+    const uint32_t r = threadIdx.x;
+    st_async_triple(map_rank(smem_addr(buf + 4 * rank), r), map_rank(smem_addr(bar), r), v0, v1, v2);
+  }
+  const bool ok = xbar_wait(bar, (uint32_t)((round >> 1) & 1));
   T s0 = buf[0], s1 = buf[1], s2 = buf[2];
 #pragma unroll
   for (int r = 1; r < CS; ++r) {
@@ -488,6 +538,7 @@ __device__ __forceinline__ void cluster_sum3(T& v0, T& v1, T& v2, T* slots, int&
   v1 = s1;
   v2 = s2;
   ++round;
+  return ok;
 }
 
 template <class T, int CS>
@@ -499,6 +550,7 @@ struct ChainCtx {
   T* z;
   T* res;
   T* slots;
+  uint64_t* xbar;
   T* e;
   PickRing* ring;
   int c, rank, n, i0, ni;
@@ -539,7 +591,11 @@ __device__ __forceinline__ void chain_step(ChainCtx<T, CS>& x, int64_t t, const 
   d2 = warp_sum_t(d2);
   const int own = p0.j1 - x.i0;
   T s1 = (own >= 0 && own < x.ni) ? x.res[own] : T(0);
-  cluster_sum3<T, CS>(d1, d2, s1, x.slots, x.round, x.rank, cl);
+  if (!cluster_sum3<T, CS>(d1, d2, s1, x.slots, x.xbar, x.round, x.rank)) {
+    atomicCAS(&x.a.st->status, 0, ILS_ERR_TIMEOUT);
+    x.stop = true;
+    return;
+  }
   // RK step on A_1^T w = bhat (step 9), RGS step on A_1 z = w (step 11)
   const T delta = (s1 - d1) * T(p0.inv1);
   const T eps = fma(delta, T(p0.c12), d2) * T(p0.inv2);
@@ -589,7 +645,11 @@ __device__ __forceinline__ void chain_step(ChainCtx<T, CS>& x, int64_t t, const 
     for (int i = lane; i < x.ni; i += 32) acc = fma(x.res[i], x.res[i], acc);
     acc = warp_sum_t(acc);
     T u1 = T(0), u2 = T(0);
-    cluster_sum3<T, CS>(acc, u1, u2, x.slots, x.round, x.rank, cl);
+    if (!cluster_sum3<T, CS>(acc, u1, u2, x.slots, x.xbar, x.round, x.rank)) {
+      atomicCAS(&x.a.st->status, 0, ILS_ERR_TIMEOUT);
+      x.stop = true;
+      return;
+    }
     if ((double)acc <= x.target2) x.stop = true;
   }
 }
@@ -620,12 +680,19 @@ __global__ void __launch_bounds__(32) rkrgs_cluster_kernel(RandArgs a, SparseCol
   extern __shared__ double smem[];
   double* cum = smem;                                 // n
   x.res = reinterpret_cast<T*>(cum + ((n + 1) & ~1));  // nres (16-byte aligned): s = bhat - Abar1 z
-  x.z = x.res + nres;                                 // n
-  x.slots = x.z + n;                                  // 2 x 4 CS
-  x.e = x.slots + 8 * CS;                             // S: e = w - A_1 z on rows r0 .. r0+S-1
+  x.slots = x.res + nres;                             // 2 x CS x 4 (16-byte aligned: st.async targets)
+  x.z = x.slots + 8 * CS;                             // n
+  x.e = x.z + n;                                      // S: e = w - A_1 z on rows r0 .. r0+S-1
   x.cum = cum;
   __shared__ PickRing ring;
+  __shared__ __align__(8) uint64_t xbar[2];
   x.ring = &ring;
+  x.xbar = xbar;
+  if (lane == 0) {
+    xbar_init(&xbar[0]);
+    xbar_init(&xbar[1]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
   for (int s = lane; s < n; s += 32) {
     cum[s] = a.cum[s];
     x.z[s] = T(0);
