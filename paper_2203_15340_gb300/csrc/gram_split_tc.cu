@@ -359,6 +359,64 @@ __global__ void split_kernel(int K, int n, const double* __restrict__ A, int64_t
   }
 }
 
+// The two kernels above in one pass for K <= 512 * 32: one CTA per column keeps the
+// column's bit patterns in registers, reduces the largest exponent field, and splits.
+constexpr int kFuseThreads = 512;
+constexpr int kFusePer = 32;
+
+__global__ void __launch_bounds__(kFuseThreads)
+exponent_split_kernel(int K, int n, const double* __restrict__ A, int64_t lda, int* __restrict__ exps,
+                      __nv_bfloat16* __restrict__ D, int64_t ldk, int32_t* err) {
+  const int j = blockIdx.x;
+  long long bits[kFusePer];
+  int mx = 0;
+#pragma unroll
+  for (int i = 0; i < kFusePer; ++i) {
+    const int r = threadIdx.x + kFuseThreads * i;
+    bits[i] = r < K ? __double_as_longlong(__ldg(A + r + (int64_t)j * lda)) : 0ll;
+    mx = max(mx, (int)((bits[i] >> 52) & 0x7FF));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  __shared__ int red[kFuseThreads / 32];
+  __shared__ int e_j;
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int m = 0;
+    for (int w = 0; w < kFuseThreads / 32; ++w) m = max(m, red[w]);
+    e_j = (m == 0 || m == 0x7FF) ? 0 : m - 1022;  // normal values with field f lie in [2^(f-1023), 2^(f-1022))
+    exps[j] = e_j;
+  }
+  __syncthreads();
+  const int ej = e_j;
+#pragma unroll
+  for (int i = 0; i < kFusePer; ++i) {
+    const int r = threadIdx.x + kFuseThreads * i;
+    if (r >= K) continue;
+    const int f = (int)((bits[i] >> 52) & 0x7FF);
+    long long V = 0;
+    if (f == 0x7FF) {
+      atomicExch(err, 2);
+    } else if (f != 0) {
+      const unsigned long long mant = (unsigned long long)(bits[i] & 0xFFFFFFFFFFFFFll) | (1ull << 52);
+      const int sh = 1075 - f - kBeta * kSlices + ej;
+      if (sh < 64) {
+        const unsigned long long half = (sh > 0) ? (1ull << (sh - 1)) : 0ull;
+        const unsigned long long mag = (sh > 0) ? ((mant + half) >> sh) : (mant << (-sh));
+        V = (bits[i] < 0) ? -(long long)mag : (long long)mag;
+      }
+    }
+#pragma unroll
+    for (int t = kSlices - 1; t >= 1; --t) {
+      int d = (int)(V & 31);
+      if (d >= 16) d -= 32;
+      V = (V - d) >> kBeta;
+      D[((int64_t)t * n + j) * ldk + r] = __int2bfloat16_rn(d);
+    }
+    D[(int64_t)j * ldk + r] = __int2bfloat16_rn((int)V);
+  }
+}
+
 // C(i,j) for the upper tiles: sum of the tile's items in a fixed order, mirrored.
 __global__ void split_reduce_kernel(SplitParams P, double* __restrict__ C, int64_t ldc) {
   const int items_per_tile = P.n_pairs * P.n_kchunks;
@@ -431,18 +489,24 @@ cudaError_t gram_split_tc(int64_t K, int64_t n, const double* A, int64_t lda, do
   if (!encode) return cudaErrorNotSupported;
   const int64_t ldk = ((K + 7) / 8) * 8;
   __nv_bfloat16* D = static_cast<__nv_bfloat16*>(slices);
-  column_exponent_kernel<<<(unsigned)n, 256, 0, s>>>((int)K, (int)n, A, lda, exps);
-  note_launch();
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
   if (ldk != K) {  // zero the padding rows so TMA never reads stale values inside ldk
     e = cudaMemsetAsync(D, 0, sizeof(__nv_bfloat16) * (size_t)kSlices * n * ldk, s);
     if (e != cudaSuccess) return e;
   }
-  split_kernel<<<dim3((unsigned)std::min<int64_t>((K + 255) / 256, 64), (unsigned)n), 256, 0, s>>>(
-      (int)K, (int)n, A, lda, exps, D, ldk, err);
-  note_launch();
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (K <= (int64_t)kFuseThreads * kFusePer) {
+    exponent_split_kernel<<<(unsigned)n, kFuseThreads, 0, s>>>((int)K, (int)n, A, lda, exps, D, ldk, err);
+    note_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  } else {
+    column_exponent_kernel<<<(unsigned)n, 256, 0, s>>>((int)K, (int)n, A, lda, exps);
+    note_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    split_kernel<<<dim3((unsigned)std::min<int64_t>((K + 255) / 256, 64), (unsigned)n), 256, 0, s>>>(
+        (int)K, (int)n, A, lda, exps, D, ldk, err);
+    note_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
 
   CUtensorMap map;
   const cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)n, (cuuint64_t)kSlices};

@@ -789,8 +789,7 @@ ils_status ils_refactor(ils_handle h, const double* A, int64_t lda, ils_stream_t
   h->stream = (cudaStream_t)stream;
   cudaStream_t s = h->stream;
   ILS_CK(mark(h, 0));
-  ILS_CK(cudaMemcpy2DAsync(h->A, sizeof(double) * h->m, A, sizeof(double) * lda, sizeof(double) * h->m, h->n,
-                           cudaMemcpyDeviceToDevice, s));
+  ILS_CK(copy_matrix_f64(h->m, h->n, A, lda, h->A, s));
   ils_status st = compute_setup(h);
   if (st == ILS_OK) st = setup_finish(h);
   if (st == ILS_OK && h->opt.timing) collect_timings(h);
@@ -955,8 +954,7 @@ ils_status ils_batch_setup(ils_batch* out, int64_t count, const ils_problem* pro
     st = create_handle(&b->h[i], pr.m, pr.n, pr.p, pr.q, pr.A, pr.lda, o, s);
     if (st != ILS_OK) break;
     ils_handle h = b->h[i];
-    if (cudaMemcpy2DAsync(h->A, sizeof(double) * h->m, pr.A, sizeof(double) * pr.lda, sizeof(double) * h->m, h->n,
-                          cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+    if (copy_matrix_f64(h->m, h->n, pr.A, pr.lda, h->A, s) != cudaSuccess) {
       cudaGetLastError();
       st = ILS_ERR_CUDA;
       break;
@@ -1037,8 +1035,7 @@ ils_status ils_batch_capture(ils_batch b, int refactor, int64_t k, const double*
     b->cap_ldx[i] = lx;
     if (refactor) {
       const ils_problem& pr = b->probs[i];
-      if (cudaMemcpy2DAsync(h->A, sizeof(double) * h->m, pr.A, sizeof(double) * pr.lda, sizeof(double) * h->m,
-                            h->n, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+      if (copy_matrix_f64(h->m, h->n, pr.A, pr.lda, h->A, h->stream) != cudaSuccess)
         st = ILS_ERR_CUDA;
       if (st == ILS_OK) st = compute_setup(h);
     }

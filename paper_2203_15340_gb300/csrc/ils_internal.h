@@ -74,6 +74,9 @@ cudaError_t diag_block_inverse_f32(int64_t n, const float* L, float* Dinv, cudaS
 cudaError_t trsm_binv_f32(int64_t n, int64_t k, const float* L, float* Dinv, float* X, int64_t ldx,
                           bool forward, bool backward, cudaStream_t s);
 
+// dst (m x n, ld m) = src (m x n, ld lda), both device memory.
+cudaError_t copy_matrix_f64(int64_t m, int64_t n, const double* src, int64_t lda, double* dst, cudaStream_t s);
+
 // Elementwise helpers.
 cudaError_t set_identity_f64(int64_t n, double* M, int64_t ld, cudaStream_t s);
 cudaError_t axpby_mat_f64(int64_t n, double alpha, const double* X, double beta, const double* Y,
