@@ -559,17 +559,26 @@ ils_status pass_end(ils_handle h, double* X, int64_t ldx, ils_info* agg) {
   cudaStream_t s = h->stream;
   const int64_t cap = h->opt.max_outer + 1;
   int64_t chunk = std::max<int64_t>(first_chunk(h), 1);
-  for (;;) {
-    ILS_CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
-    ILS_CK(cudaStreamSynchronize(s));
-    if (h->h_st->done || h->pass_launched >= cap) break;
-    chunk = std::min<int64_t>(chunk * 2, 1024);
-    ils_status st = pass_launch(h, chunk);
-    if (st != ILS_OK) return st;
-  }
-  if (!h->h_st->done) return ILS_ERR_TIMEOUT;  // cannot happen: the cap launch always finishes
+  // The answer and the per-column results are enqueued with the first state read, so a
+  // pass that finished within its first chunk costs one host round trip; if it has not,
+  // they are enqueued again once it has.
+  ILS_CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
   ils_status st = pass_finish_enqueue(h, X, ldx);
   if (st != ILS_OK) return st;
+  ILS_CK(cudaStreamSynchronize(s));
+  if (h->h_st->done) {
+    pass_collect(h, agg);
+    return ILS_OK;
+  }
+  for (;;) {
+    if (h->h_st->done || h->pass_launched >= cap) break;
+    chunk = std::min<int64_t>(chunk * 2, 1024);
+    if ((st = pass_launch(h, chunk)) != ILS_OK) return st;
+    ILS_CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+    ILS_CK(cudaStreamSynchronize(s));
+  }
+  if (!h->h_st->done) return ILS_ERR_TIMEOUT;  // cannot happen: the cap launch always finishes
+  if ((st = pass_finish_enqueue(h, X, ldx)) != ILS_OK) return st;
   ILS_CK(cudaStreamSynchronize(s));
   pass_collect(h, agg);
   return ILS_OK;

@@ -80,14 +80,18 @@ __device__ __forceinline__ float ld_op(const __nv_bfloat16* p, int64_t i) { retu
 // number of right-hand sides, fixed at compile time so no predicated work is issued.  Each
 // warp takes whole rows; the launch shape (warps per CTA, CTAs) is picked by tune_sweeps,
 // and the result does not depend on it (every row is reduced in the same order).
-template <typename TM, int KR>
+// v may be the FP64 residual itself (the first sweep of a refinement step reads it
+// directly); with update_x the sweep also adds its result to the FP64 iterate of the
+// unfinished columns (the last sweep of the step).
+template <typename TM, typename TV, int KR>
 __global__ void __launch_bounds__(256) sweep_kernel(MixedArgs a, const TM* __restrict__ M,
-                                                    const float* __restrict__ v,
+                                                    const TV* __restrict__ v,
                                                     const float* __restrict__ add,
-                                                    float* __restrict__ out) {
+                                                    float* __restrict__ out, int update_x) {
   if (*((volatile int32_t*)&a.st->done)) return;
   const int64_t n = a.n;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double* x = update_x ? (*((volatile int32_t*)&a.st->cur) ? a.X1 : a.X0) : nullptr;
   for (int64_t i = (int64_t)blockIdx.x * nw + w; i < n; i += (int64_t)gridDim.x * nw) {
     const TM* col = M + i * n;
     float acc[KR];
@@ -96,29 +100,33 @@ __global__ void __launch_bounds__(256) sweep_kernel(MixedArgs a, const TM* __res
     for (int64_t j = lane; j < n; j += 32) {
       const float mv = ld_op(col, j);
 #pragma unroll
-      for (int c = 0; c < KR; ++c) acc[c] = fmaf(mv, v[j + c * n], acc[c]);
+      for (int c = 0; c < KR; ++c) acc[c] = fmaf(mv, (float)v[j + c * n], acc[c]);
     }
 #pragma unroll
     for (int c = 0; c < KR; ++c) {
       const float sv = warp_sum_f(acc[c]);
-      if (lane == 0) out[i + c * n] = sv + (add ? add[i + c * n] : 0.f);
+      if (lane == 0) {
+        const float o = sv + (add ? add[i + c * n] : 0.f);
+        out[i + c * n] = o;
+        if (update_x && !a.col_done[c]) x[i + c * n] += (double)o;
+      }
     }
   }
 }
 
-template <typename TM>
-void launch_sweep(const MixedArgs& a, SweepShape sh, const TM* M, const float* v, const float* add, float* out,
-                  cudaStream_t s) {
+template <typename TM, typename TV = float>
+void launch_sweep(const MixedArgs& a, SweepShape sh, const TM* M, const TV* v, const float* add, float* out,
+                  cudaStream_t s, int update_x = 0) {
   const dim3 grid((unsigned)sh.blocks), block((unsigned)(32 * sh.warps));
   switch ((int)a.k) {
-    case 1: sweep_kernel<TM, 1><<<grid, block, 0, s>>>(a, M, v, add, out); break;
-    case 2: sweep_kernel<TM, 2><<<grid, block, 0, s>>>(a, M, v, add, out); break;
-    case 3: sweep_kernel<TM, 3><<<grid, block, 0, s>>>(a, M, v, add, out); break;
-    case 4: sweep_kernel<TM, 4><<<grid, block, 0, s>>>(a, M, v, add, out); break;
-    case 5: sweep_kernel<TM, 5><<<grid, block, 0, s>>>(a, M, v, add, out); break;
-    case 6: sweep_kernel<TM, 6><<<grid, block, 0, s>>>(a, M, v, add, out); break;
-    case 7: sweep_kernel<TM, 7><<<grid, block, 0, s>>>(a, M, v, add, out); break;
-    default: sweep_kernel<TM, 8><<<grid, block, 0, s>>>(a, M, v, add, out); break;
+    case 1: sweep_kernel<TM, TV, 1><<<grid, block, 0, s>>>(a, M, v, add, out, update_x); break;
+    case 2: sweep_kernel<TM, TV, 2><<<grid, block, 0, s>>>(a, M, v, add, out, update_x); break;
+    case 3: sweep_kernel<TM, TV, 3><<<grid, block, 0, s>>>(a, M, v, add, out, update_x); break;
+    case 4: sweep_kernel<TM, TV, 4><<<grid, block, 0, s>>>(a, M, v, add, out, update_x); break;
+    case 5: sweep_kernel<TM, TV, 5><<<grid, block, 0, s>>>(a, M, v, add, out, update_x); break;
+    case 6: sweep_kernel<TM, TV, 6><<<grid, block, 0, s>>>(a, M, v, add, out, update_x); break;
+    case 7: sweep_kernel<TM, TV, 7><<<grid, block, 0, s>>>(a, M, v, add, out, update_x); break;
+    default: sweep_kernel<TM, TV, 8><<<grid, block, 0, s>>>(a, M, v, add, out, update_x); break;
   }
   note_launch();
 }
@@ -462,24 +470,22 @@ int ils_tuned_shape_impl(int64_t n, int64_t k, int bf16, int* warps, int* blocks
 
 // One refinement step after the residual launch: r32, d_1 = P r, d_{s+1} = B d_s + P r, x += d.
 cudaError_t mixed_correct(const MixedArgs& a, int precision, cudaStream_t s) {
-  residual_to_f32_kernel<<<grid_small(a.n * a.k), 256, 0, s>>>(a);
-  note_launch();
   const SweepShape sh32 = sweep_shape(a.n, a.k, false);
-  // c = P r  (kept in a.c32; also the first iterate d_1)
-  launch_sweep<float>(a, sh32, a.P32, a.r32, nullptr, a.c32, s);
+  // c = P r, read straight from the FP64 residual (kept in a.c32; also the first iterate
+  // d_1); the last sweep adds d to x.
+  launch_sweep<float, double>(a, sh32, a.P32, a.r, nullptr, a.c32, s, a.sweeps == 1 ? 1 : 0);
   const float* dcur = a.c32;
   float* bufs[2] = {a.d32[0], a.d32[1]};
   for (int sw = 1; sw < a.sweeps; ++sw) {
     float* dn = bufs[sw & 1];
+    const int last = sw + 1 == a.sweeps ? 1 : 0;
     if (precision == ILS_BF16_REFINE)
       launch_sweep<__nv_bfloat16>(a, sweep_shape(a.n, a.k, true), static_cast<const __nv_bfloat16*>(a.Bt16), dcur,
-                                  a.c32, dn, s);
+                                  a.c32, dn, s, last);
     else
-      launch_sweep<float>(a, sh32, a.Bt32, dcur, a.c32, dn, s);
+      launch_sweep<float>(a, sh32, a.Bt32, dcur, a.c32, dn, s, last);
     dcur = dn;
   }
-  refine_update_kernel<<<grid_small(a.n * a.k), 256, 0, s>>>(a, dcur);
-  note_launch();
   return cudaGetLastError();
 }
 
