@@ -262,24 +262,43 @@ gemv_cols_kernel(int64_t n, const double* __restrict__ M, int64_t ldm, const dou
 constexpr int kNB = 32;
 constexpr int kPanelWarps = 4;
 
+template <typename T>
 struct CholBatch {
-  double* M[2];       // matrices (ld n), lower triangles factored in place
-  double* inv_diag[2];  // 1 / L_ii, filled panel by panel
+  T* M[2];         // matrices (ld n), lower triangles factored in place
+  T* inv_diag[2];  // 1 / L_ii, filled panel by panel
+  T* stash[2];     // 32 x 32 factored diagonal block of the current panel
   int32_t* status;
 };
 
+// Pivot test: NONFINITE, NOT_SPD or 0.  FP64 looks at the bit pattern (integer pipes, not
+// the scarce FP64 one); FP32 compares directly.
+__device__ __forceinline__ int pivot_code(double d) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(d);
+  if (((bits >> 52) & 0x7ffull) == 0x7ffull) return ILS_ERR_NONFINITE;
+  if ((bits >> 63) != 0ull || bits == 0ull) return ILS_ERR_NOT_SPD;
+  return 0;
+}
+__device__ __forceinline__ int pivot_code(float d) {
+  if (!isfinite(d)) return ILS_ERR_NONFINITE;
+  if (!(d > 0.f)) return ILS_ERR_NOT_SPD;
+  return 0;
+}
+__device__ __forceinline__ double rsqrt_t(double d) { return rsqrt(d); }
+__device__ __forceinline__ float rsqrt_t(float d) { return rsqrtf(d); }
+
 __device__ void set_status(int32_t* status, int32_t code) { atomicCAS(status, 0, code); }
 
+template <typename T>
 __global__ void __launch_bounds__(32 * kPanelWarps)
-chol_panel_kernel(int64_t n, CholBatch cb, int64_t k0, int nb) {
-  double* L = cb.M[blockIdx.z];
-  double* inv = cb.inv_diag[blockIdx.z];
-  __shared__ double a[kNB][kNB + 1];
-  __shared__ double rinv[kNB];
+chol_panel_kernel(int64_t n, CholBatch<T> cb, int64_t k0, int nb) {
+  T* L = cb.M[blockIdx.z];
+  T* inv = cb.inv_diag[blockIdx.z];
+  __shared__ T a[kNB][kNB + 1];
+  __shared__ T rinv[kNB];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   for (int e = tid; e < kNB * kNB; e += blockDim.x) {
     const int r = e & 31, c = e >> 5;
-    a[r][c] = (r < nb && c < nb && r >= c) ? L[(k0 + r) + (k0 + c) * n] : (r == c ? 1.0 : 0.0);
+    a[r][c] = (r < nb && c < nb && r >= c) ? L[(k0 + r) + (k0 + c) * n] : (r == c ? T(1) : T(0));
   }
   __syncthreads();
   // Pivot c: every thread reads a[c][c] and forms rs = 1/sqrt(a_cc) itself, then
@@ -288,21 +307,17 @@ chol_panel_kernel(int64_t n, CholBatch cb, int64_t k0, int nb) {
   for (int c = 0; c < kNB; ++c) {
     __syncthreads();
     if (c > 0 && w == 0 && lane >= c - 1) a[lane][c - 1] *= rinv[c - 1];
-    double d = a[c][c];
-    // pivot tests on the bit pattern (integer pipe, not the scarce FP64 one)
-    const unsigned long long bits = (unsigned long long)__double_as_longlong(d);
-    if (((bits >> 52) & 0x7ffull) == 0x7ffull) {
-      if (tid == 0 && blockIdx.x == 0) set_status(cb.status, ILS_ERR_NONFINITE);
-      d = 1.0;
-    } else if ((bits >> 63) != 0ull || bits == 0ull) {
-      if (tid == 0 && blockIdx.x == 0) set_status(cb.status, ILS_ERR_NOT_SPD);
-      d = 1.0;
+    T d = a[c][c];
+    const int code = pivot_code(d);
+    if (code != 0) {
+      if (tid == 0 && blockIdx.x == 0) set_status(cb.status, code);
+      d = T(1);
     }
-    const double rs = rsqrt(d);
+    const T rs = rsqrt_t(d);
     if (tid == 0) rinv[c] = rs;
     const int j = lane;
     if (j > c) {
-      const double tj = a[j][c] * (rs * rs);
+      const T tj = a[j][c] * (rs * rs);
       for (int i = j + ((w - j) % kPanelWarps + kPanelWarps) % kPanelWarps; i < kNB; i += kPanelWarps)
         a[i][j] = fma(-a[i][c], tj, a[i][j]);
     }
@@ -310,10 +325,15 @@ chol_panel_kernel(int64_t n, CholBatch cb, int64_t k0, int nb) {
   __syncthreads();
   if (w == 0 && lane >= kNB - 1) a[lane][kNB - 1] *= rinv[kNB - 1];
   __syncthreads();
+  // The factored block goes to the stash, and into L only when this CTA is the only one:
+  // other CTAs of the launch may start late and still have to read the unfactored block.
+  // The trailing-update launch that follows moves the stash into L.
   if (blockIdx.x == 0) {
+    T* stash = cb.stash[blockIdx.z];
     for (int e = tid; e < kNB * kNB; e += blockDim.x) {
       const int r = e & 31, c = e >> 5;
-      if (r < nb && c < nb && r >= c) L[(k0 + r) + (k0 + c) * n] = a[r][c];
+      stash[e] = a[r][c];
+      if (gridDim.x == 1 && r < nb && c < nb && r >= c) L[(k0 + r) + (k0 + c) * n] = a[r][c];
     }
     if (tid < nb) inv[k0 + tid] = rinv[tid];
   }
@@ -324,16 +344,16 @@ chol_panel_kernel(int64_t n, CholBatch cb, int64_t k0, int nb) {
   for (int64_t row = k0 + nb + (int64_t)blockIdx.x * kPanelWarps + w; row < n; row += 2 * stride) {
     const int64_t row2 = row + stride;
     const bool two = row2 < n;
-    double x = lane < nb ? L[row + (k0 + lane) * n] : 0.0;
-    double y = (two && lane < nb) ? L[row2 + (k0 + lane) * n] : 0.0;
+    T x = lane < nb ? L[row + (k0 + lane) * n] : T(0);
+    T y = (two && lane < nb) ? L[row2 + (k0 + lane) * n] : T(0);
     for (int c = 0; c < nb; ++c) {
-      const double xc = __shfl_sync(0xffffffffu, x, c) * rinv[c];
-      const double yc = __shfl_sync(0xffffffffu, y, c) * rinv[c];
+      const T xc = __shfl_sync(0xffffffffu, x, c) * rinv[c];
+      const T yc = __shfl_sync(0xffffffffu, y, c) * rinv[c];
       if (lane == c) {
         x = xc;
         y = yc;
       } else if (lane > c) {
-        const double l = a[lane][c];
+        const T l = a[lane][c];
         x = fma(-xc, l, x);
         y = fma(-yc, l, y);
       }
@@ -346,26 +366,34 @@ chol_panel_kernel(int64_t n, CholBatch cb, int64_t k0, int nb) {
 }
 
 // Trailing update A22 -= L21 L21^T on lower 16 x 16 tiles (two elements per thread).
+template <typename T>
 __global__ void __launch_bounds__(128)
-syrk16_kernel(int64_t n, CholBatch cb, int64_t k0, int nb) {
-  double* L = cb.M[blockIdx.z];
+syrk16_kernel(int64_t n, CholBatch<T> cb, int64_t k0, int nb) {
+  T* L = cb.M[blockIdx.z];
   const int bi = blockIdx.x, bj = blockIdx.y;
+  if (bi == 0 && bj == 0) {  // the panel's factored diagonal block, kept aside by the panel launch
+    const T* stash = cb.stash[blockIdx.z];
+    for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x) {
+      const int r = e & 31, c = e >> 5;
+      if (r < nb && c < nb && r >= c) L[(k0 + r) + (k0 + c) * n] = stash[e];
+    }
+  }
   if (bi < bj) return;
   const int64_t k1 = k0 + nb;
   const int64_t ri0 = k1 + (int64_t)bi * 16, rj0 = k1 + (int64_t)bj * 16;
-  __shared__ double Pi[16][kNB + 1];
-  __shared__ double Pj[16][kNB + 1];
+  __shared__ T Pi[16][kNB + 1];
+  __shared__ T Pj[16][kNB + 1];
   for (int e = threadIdx.x; e < 16 * kNB; e += blockDim.x) {
     const int r = e & 15, c = e >> 4;
-    Pi[r][c] = (ri0 + r < n && c < nb) ? L[(ri0 + r) + (k0 + c) * n] : 0.0;
-    Pj[r][c] = (rj0 + r < n && c < nb) ? L[(rj0 + r) + (k0 + c) * n] : 0.0;
+    Pi[r][c] = (ri0 + r < n && c < nb) ? L[(ri0 + r) + (k0 + c) * n] : T(0);
+    Pj[r][c] = (rj0 + r < n && c < nb) ? L[(rj0 + r) + (k0 + c) * n] : T(0);
   }
   __syncthreads();
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // ty in 0..7
-  double acc0 = 0.0, acc1 = 0.0;
+  T acc0 = T(0), acc1 = T(0);
 #pragma unroll 8
   for (int c = 0; c < kNB; ++c) {
-    const double pj = Pj[tx][c];
+    const T pj = Pj[tx][c];
     acc0 = fma(Pi[ty][c], pj, acc0);
     acc1 = fma(Pi[ty + 8][c], pj, acc1);
   }
@@ -962,13 +990,15 @@ cudaError_t copy_matrix_f64(int64_t m, int64_t n, const double* src, int64_t lda
   return cudaGetLastError();
 }
 
-cudaError_t cholesky_f64_batch(int64_t n, int count, double* const* mats, double* const* inv_diag, int32_t* status,
-                               cudaStream_t s) {
+template <typename T>
+cudaError_t cholesky_batch_t(int64_t n, int count, T* const* mats, T* const* inv_diag, T* stash, int32_t* status,
+                             cudaStream_t s) {
   if (count < 1 || count > 2) return cudaErrorInvalidValue;
-  CholBatch cb;
+  CholBatch<T> cb;
   for (int i = 0; i < 2; ++i) {
     cb.M[i] = mats[i < count ? i : 0];
     cb.inv_diag[i] = inv_diag[i < count ? i : 0];
+    cb.stash[i] = stash + (size_t)(i < count ? i : 0) * kNB * kNB;
   }
   cb.status = status;
   for (int64_t k0 = 0; k0 < n; k0 += kNB) {
@@ -977,19 +1007,25 @@ cudaError_t cholesky_f64_batch(int64_t n, int count, double* const* mats, double
     const int64_t per_matrix = std::max<int64_t>(1, num_sms() / count);
     const unsigned panel_ctas =
         (unsigned)std::max<int64_t>(1, std::min<int64_t>((rest + kPanelWarps - 1) / kPanelWarps, per_matrix));
-    chol_panel_kernel<<<dim3(panel_ctas, 1, count), 32 * kPanelWarps, 0, s>>>(n, cb, k0, nb);
+    chol_panel_kernel<T><<<dim3(panel_ctas, 1, count), 32 * kPanelWarps, 0, s>>>(n, cb, k0, nb);
     note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (rest <= 0) break;
     const unsigned nt = (unsigned)((rest + 15) / 16);
-    syrk16_kernel<<<dim3(nt, nt, count), 128, 0, s>>>(n, cb, k0, nb);
+    syrk16_kernel<T><<<dim3(nt, nt, count), 128, 0, s>>>(n, cb, k0, nb);
     note_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
+
+cudaError_t cholesky_f64_batch(int64_t n, int count, double* const* mats, double* const* inv_diag, double* stash,
+                               int32_t* status, cudaStream_t s) {
+  return cholesky_batch_t<double>(n, count, mats, inv_diag, stash, status, s);
+}
+
 
 template <typename T>
 cudaError_t trsm_lower_t(int64_t n, int64_t k, const T* L, T* X, int64_t ldx, bool forward, bool backward,

@@ -76,6 +76,7 @@ struct ils_handle_s {
   SparseCols sc{};
   int32_t* cnt_fill = nullptr;  // 2n
   int32_t* sp_err = nullptr;
+  double* stash64 = nullptr;   // 2 x 1024: the Cholesky panels' diagonal-block stash
   SolveState* st = nullptr;
   int32_t* dstatus = nullptr;
   // pinned host mirrors
@@ -237,6 +238,7 @@ void carve(ils_handle h, Carver& c, size_t work_elems) {
   }
   h->st = c.take<SolveState>(1);
   h->dstatus = c.take<int32_t>(1);
+  h->stash64 = c.take<double>(2 * 1024);
 }
 
 size_t setup_work_elems(int64_t m, int64_t n, int64_t p, int64_t q) {
@@ -297,7 +299,7 @@ ils_status compute_setup_mf(ils_handle h) {
   {
     double* mats[2] = {h->L, h->L};
     double* invd[2] = {h->inv_diag, h->inv_diag};
-    ILS_CK(cholesky_f64_batch(n, 1, mats, invd, h->dstatus, s));
+    ILS_CK(cholesky_f64_batch(n, 1, mats, invd, h->stash64, h->dstatus, s));
   }
   ILS_CK(mark(h, 4));
   ILS_CK(cudaMemcpyAsync(h->h_status, h->dstatus, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -374,7 +376,7 @@ ils_status compute_products(ils_handle h) {
   {
     double* mats[2] = {h->L, h->P};
     double* invd[2] = {h->inv_diag, h->inv_diag + n};
-    ILS_CK(cholesky_f64_batch(n, 2, mats, invd, h->dstatus, s));
+    ILS_CK(cholesky_f64_batch(n, 2, mats, invd, h->stash64, h->dstatus, s));
   }
   ILS_CK(mark(h, 4));
   ILS_CK(cudaMemcpyAsync(h->h_status, h->dstatus, sizeof(int32_t), cudaMemcpyDeviceToHost, s));

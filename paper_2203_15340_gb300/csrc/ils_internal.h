@@ -54,9 +54,10 @@ cudaError_t gemv_cols_f64(int64_t n, int64_t k, const double* M, int64_t ldm, co
                           int64_t ldx, double* Y, int64_t ldy, cudaStream_t s);
 
 // In-place blocked Cholesky of the lower triangles of `count` (1 or 2) n x n matrices
-// (ld n), factored together.  inv_diag[i] (length n) receives 1 / L_jj.  status (device
-// int) is set to ILS_ERR_NOT_SPD or ILS_ERR_NONFINITE on a bad pivot of any matrix.
-cudaError_t cholesky_f64_batch(int64_t n, int count, double* const* mats, double* const* inv_diag,
+// (ld n), factored together.  inv_diag[i] (length n) receives 1 / L_jj.  stash: count x
+// 1024 scratch elements.  status (device int) is set to ILS_ERR_NOT_SPD or
+// ILS_ERR_NONFINITE on a bad pivot of any matrix.
+cudaError_t cholesky_f64_batch(int64_t n, int count, double* const* mats, double* const* inv_diag, double* stash,
                                int32_t* status, cudaStream_t s);
 
 // X := L^{-1} X (lower = forward) then, if both, X := L^{-T} X.  X n x k (ldx).
