@@ -145,3 +145,21 @@ def test_batched_graph_full_config(ils):
         worst = max(worst, max(relerr(x[:, j], xs[:, j]) for j in range(8)))
     assert worst <= 1e-10
     bs.close()
+
+
+def test_batched_graph_repeated_replays_are_identical(ils):
+    """Replays of one captured setup+solve give the same statuses and bitwise the same X every
+    time, with all 256 problems' kernels in flight together (a race between CTAs of one
+    launch would show up here as a spurious status or a changed answer)."""
+    import torch
+    insts = W.config4_batched()
+    bs, s, _, _, _, X_graph, infos = _graph_case(ils, insts, ils.options(precision=2), 8, refactor=True)
+    first = [to_np_colmajor(X) for X in X_graph]
+    for rep in range(4):
+        with torch.cuda.stream(s):
+            infos = bs.run(stream=s)
+        torch.cuda.synchronize()
+        assert all(info.status == ils.ILS_OK for info in infos), rep
+        for x0, X in zip(first, X_graph):
+            assert np.array_equal(x0, to_np_colmajor(X)), rep
+    bs.close()
