@@ -40,10 +40,12 @@ constexpr int kSlices = 10;     // 50 bits below each column's scale
 constexpr int kBM = 128;        // output tile rows (columns of D_t)
 constexpr int kBN = 128;        // output tile cols (columns of D_u)
 constexpr int kBK = 64;         // K per stage: 64 BF16 = one 128-byte swizzle row
-constexpr int kStages = 6;
+constexpr int kStages = 4;
+constexpr int kGroup = 2;       // digit pairs (t, u), (t, u + 1) per CTA: one A slice, two B slices
 constexpr int kKChunk = 16384;  // K rows per work item: 16384 * 32^2 = 2^24 (exact FP32 sums)
 constexpr int kThreads = 192;   // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
 constexpr uint32_t kTileBytes = kBM * kBK * 2;  // 16 KB per operand tile
+constexpr uint32_t kStageBytes = (1 + kGroup) * kTileBytes;
 constexpr uint64_t kWaitNs = 4000000000ull;  // bound on any mbarrier wait (4 s)
 
 // ------------------------------- device helpers ----------------------------------------
@@ -148,24 +150,26 @@ struct SplitParams {
   int K;            // rows of A (reduction length)
   int n_tiles;      // ceil(n / 128)
   int n_pairs;      // ordered slice pairs (t, u) with t + u <= S + 1
+  int n_groups;     // work groups of up to kGroup pairs sharing t
   int n_kchunks;
   const int* exps;  // per-column exponents e_j (device)
   double* partial;  // [item][128][128] FP64 scaled products
   int32_t* err;     // device error flag
 };
 
-// Work item -> (K chunk, upper tile pair, slice pair).  Items of one K chunk run together
-// so the chunk's slices stay in L2; the partial-product slot keeps the items of a tile
-// contiguous for the reduction: slot = (tile * n_pairs + pair) * n_kchunks + kc.
-__device__ __forceinline__ void decode_item(int item, const SplitParams& P, int* bi, int* bj, int* t, int* u,
-                                            int* kc, int* slot) {
+// Work item -> (K chunk, upper tile pair, digit group).  A group is (t, u0) and, when
+// u0 + 1 <= S + 1 - t, also (t, u0 + 1): the CTA loads D_t once for both products.  Items
+// of one K chunk run together.  Partial-product slots stay per digit pair, with the items
+// of a tile contiguous for the reduction: slot = (tile * n_pairs + pair) * n_kchunks + kc.
+__device__ __forceinline__ void decode_item(int item, const SplitParams& P, int* bi, int* bj, int* t, int* u0,
+                                            int* nb, int* kc, int* tile_out) {
   const int n_upper = P.n_tiles * (P.n_tiles + 1) / 2;
-  const int per_chunk = n_upper * P.n_pairs;
+  const int per_chunk = n_upper * P.n_groups;
   *kc = item / per_chunk;
   const int rest = item % per_chunk;
-  int tile = rest / P.n_pairs;
-  const int pair = rest % P.n_pairs;
-  *slot = (tile * P.n_pairs + pair) * P.n_kchunks + *kc;
+  int tile = rest / P.n_groups;
+  const int group = rest % P.n_groups;
+  *tile_out = tile;
   // upper tile pairs (bi <= bj) in row-major order
   int r = 0;
   while (tile >= P.n_tiles - r) {
@@ -174,30 +178,39 @@ __device__ __forceinline__ void decode_item(int item, const SplitParams& P, int*
   }
   *bi = r;
   *bj = r + tile;
-  // ordered pairs with t + u <= S + 1 (1-based), enumerated by t then u
-  int p = pair, tt = 1;
-  while (p >= kSlices + 1 - tt) {
-    p -= kSlices + 1 - tt;
+  // groups enumerated by t, then u0 = 1, 1 + kGroup, ...
+  int g = group, tt = 1;
+  while (g >= (kSlices + 1 - tt + kGroup - 1) / kGroup) {
+    g -= (kSlices + 1 - tt + kGroup - 1) / kGroup;
     ++tt;
   }
   *t = tt;
-  *u = 1 + p;
+  *u0 = 1 + kGroup * g;
+  const int left = kSlices + 1 - tt - (*u0 - 1);
+  *nb = left < kGroup ? left : kGroup;
+}
+
+// Index of the ordered digit pair (t, u) among those with t + u <= S + 1 (by t, then u).
+__device__ __forceinline__ int pair_index(int t, int u) {
+  int p = 0;
+  for (int tt = 1; tt < t; ++tt) p += kSlices + 1 - tt;
+  return p + (u - 1);
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
 gram_split_mma_kernel(const __grid_constant__ CUtensorMap tmap, SplitParams P) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* tiles = smem;  // kStages x (A tile, B tile)
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * 2 * kTileBytes);
+  uint8_t* tiles = smem;  // kStages x (A tile, kGroup B tiles)
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
   uint64_t* empty = full + kStages;
   uint64_t* acc_full = empty + kStages;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_full + 1);
   __shared__ int s_abort;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int bi, bj, t, u, kc, slot;
-  decode_item(blockIdx.x, P, &bi, &bj, &t, &u, &kc, &slot);
+  int bi, bj, t, u0, nb, kc, tile;
+  decode_item(blockIdx.x, P, &bi, &bj, &t, &u0, &nb, &kc, &tile);
   const int k_begin = kc * kKChunk;
   const int k_end = min(P.K, k_begin + kKChunk);
   const int nk = (k_end - k_begin + kBK - 1) / kBK;
@@ -213,7 +226,7 @@ gram_split_mma_kernel(const __grid_constant__ CUtensorMap tmap, SplitParams P) {
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(kBN));
+                 "r"(kGroup * kBN));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -233,12 +246,12 @@ gram_split_mma_kernel(const __grid_constant__ CUtensorMap tmap, SplitParams P) {
         break;
       }
       if (*((volatile int*)&s_abort)) break;
-      uint8_t* a_tile = tiles + (size_t)s * 2 * kTileBytes;
-      uint8_t* b_tile = a_tile + kTileBytes;
-      mbar_expect_tx(&full[s], 2 * kTileBytes);
+      uint8_t* a_tile = tiles + (size_t)s * kStageBytes;
+      mbar_expect_tx(&full[s], (uint32_t)(1 + nb) * kTileBytes);
       const int k = k_begin + kb * kBK;
       tma_load_3d(a_tile, &tmap, &full[s], k, bi * kBM, t - 1);
-      tma_load_3d(b_tile, &tmap, &full[s], k, bj * kBN, u - 1);
+      for (int g = 0; g < nb; ++g)
+        tma_load_3d(a_tile + (1 + g) * kTileBytes, &tmap, &full[s], k, bj * kBN, u0 + g - 1);
       ++issued;
     }
   } else if (warp == 1 && lane == 0) {
@@ -254,12 +267,14 @@ gram_split_mma_kernel(const __grid_constant__ CUtensorMap tmap, SplitParams P) {
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a_addr = smem_u32(tiles + (size_t)s * 2 * kTileBytes);
-      const uint32_t b_addr = a_addr + kTileBytes;
+      const uint32_t a_addr = smem_u32(tiles + (size_t)s * kStageBytes);
 #pragma unroll
       for (int kk = 0; kk < kBK / 16; ++kk) {
-        mma_bf16(tmem_acc, smem_desc_sw128(a_addr + kk * 32), smem_desc_sw128(b_addr + kk * 32),
-                 (kb > 0 || kk > 0) ? 1u : 0u);
+        for (int g = 0; g < nb; ++g) {  // accumulator g: TMEM columns g * kBN ..
+          const uint32_t b_addr = a_addr + (1 + g) * kTileBytes;
+          mma_bf16(tmem_acc + (uint32_t)(g * kBN), smem_desc_sw128(a_addr + kk * 32),
+                   smem_desc_sw128(b_addr + kk * 32), (kb > 0 || kk > 0) ? 1u : 0u);
+        }
       }
       mma_commit(&empty[s]);  // frees the stage once these MMAs have read it
     }
@@ -272,20 +287,24 @@ gram_split_mma_kernel(const __grid_constant__ CUtensorMap tmap, SplitParams P) {
     const int q = warp & 3;  // this warp may read TMEM lanes 32q .. 32q+31
     const int row = q * 32 + lane;
     const int gi = bi * kBM + row;
-    double* out = P.partial + (size_t)slot * kBM * kBN;  // column-major 128 x 128 tile
     if (!ok) {
       atomicExch(P.err, 1);
     } else if (!*((volatile int*)&s_abort)) {
       const int ei = gi < P.n ? P.exps[gi] : 0;
+      for (int g = 0; g < nb; ++g) {
+        const int u = u0 + g;
+        const int slot = (tile * P.n_pairs + pair_index(t, u)) * P.n_kchunks + kc;
+        double* out = P.partial + (size_t)slot * kBM * kBN;  // column-major 128 x 128 tile
 #pragma unroll 1
-      for (int c0 = 0; c0 < kBN; c0 += 32) {
-        uint32_t v[32];
-        tmem_ld_32x32b_x32(tmem_acc + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+        for (int c0 = 0; c0 < kBN; c0 += 32) {
+          uint32_t v[32];
+          tmem_ld_32x32b_x32(tmem_acc + ((uint32_t)(q * 32) << 16) + (uint32_t)(g * kBN + c0), v);
 #pragma unroll
-        for (int c = 0; c < 32; ++c) {
-          const int gj = bj * kBN + c0 + c;
-          const int ej = gj < P.n ? P.exps[gj] : 0;
-          out[(size_t)(c0 + c) * kBM + row] = scaled_f32_to_f64(v[c], ei + ej - kBeta * (t + u));
+          for (int c = 0; c < 32; ++c) {
+            const int gj = bj * kBN + c0 + c;
+            const int ej = gj < P.n ? P.exps[gj] : 0;
+            out[(size_t)(c0 + c) * kBM + row] = scaled_f32_to_f64(v[c], ei + ej - kBeta * (t + u));
+          }
         }
       }
     }
@@ -298,7 +317,7 @@ gram_split_mma_kernel(const __grid_constant__ CUtensorMap tmap, SplitParams P) {
   __syncthreads();
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_acc), "r"(kBN));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_acc), "r"(kGroup * kBN));
   }
 }
 
@@ -464,7 +483,13 @@ int num_pairs() {
   return c;
 }
 
-size_t smem_bytes() { return 1024 + (size_t)kStages * 2 * kTileBytes + (2 * kStages + 2) * sizeof(uint64_t) + 16; }
+int num_groups() {
+  int c = 0;
+  for (int t = 1; t <= kSlices; ++t) c += (kSlices + 1 - t + kGroup - 1) / kGroup;
+  return c;
+}
+
+size_t smem_bytes() { return 1024 + (size_t)kStages * kStageBytes + (2 * kStages + 2) * sizeof(uint64_t) + 16; }
 
 }  // namespace
 
@@ -523,12 +548,13 @@ cudaError_t gram_split_tc(int64_t K, int64_t n, const double* A, int64_t lda, do
   P.K = (int)K;
   P.n_tiles = (int)((n + kBM - 1) / kBM);
   P.n_pairs = num_pairs();
+  P.n_groups = num_groups();
   P.n_kchunks = (int)std::max<int64_t>(1, (K + kKChunk - 1) / kKChunk);
   P.exps = exps;
   P.partial = partial;
   P.err = err;
   const int n_upper = P.n_tiles * (P.n_tiles + 1) / 2;
-  const int items = n_upper * P.n_pairs * P.n_kchunks;
+  const int items = n_upper * P.n_groups * P.n_kchunks;
   const size_t smem = smem_bytes();
   e = cudaFuncSetAttribute(gram_split_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
