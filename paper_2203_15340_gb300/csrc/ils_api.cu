@@ -623,6 +623,159 @@ void pass_collect(ils_handle h, ils_info* agg) {
   if (st != 0 && agg->status == 0) agg->status = st;
 }
 
+// ---------------------------------------------------------------------------------------
+// Wide SP (many right-hand sides at once, FP64, explicit route): with k columns the
+// products of Alg. 1 are dense GEMMs, bbar = A^T J B (m x n x k), c = P bbar, and per step
+// B X_k and H X_k (n x n x k), so one pass covers every column instead of passes of
+// kMaxRhsPerPass.  A column stops on the same test as the narrow path and keeps x_k.
+// ---------------------------------------------------------------------------------------
+constexpr int kWideMinRhs = 32;
+constexpr int kWideThreads = 256;
+
+__global__ void __launch_bounds__(kWideThreads)
+wide_step_kernel(int64_t n, const double* __restrict__ BX, const double* __restrict__ HX,
+                 const double* __restrict__ bb, const double* __restrict__ cc, const double* __restrict__ bn,
+                 const double* __restrict__ Xa, double* __restrict__ Xb, int32_t* __restrict__ done,
+                 double* __restrict__ rr_out, int64_t* __restrict__ iters, int64_t it, int64_t max_outer, double tol2,
+                 int32_t* __restrict__ remaining, int32_t* __restrict__ status) {
+  const int64_t c = blockIdx.x;
+  const size_t off = (size_t)c * n;
+  __shared__ double red[kWideThreads / 32];
+  __shared__ int finish;
+  if (done[c]) {
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) Xb[off + i] = Xa[off + i];
+    return;
+  }
+  double part = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double r = bb[off + i] - HX[off + i];
+    part = fma(r, r, part);
+  }
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double rr = 0.0;
+    for (int w = 0; w < kWideThreads / 32; ++w) rr += red[w];
+    const bool finite = isfinite(rr);
+    const bool conv = finite && rr <= tol2 * bn[c];
+    finish = (!finite || conv || it >= max_outer) ? 1 : 0;
+    if (finish) {
+      done[c] = 1;
+      rr_out[c] = rr;
+      iters[c] = it;
+      atomicSub(remaining, 1);
+      if (!finite) atomicCAS(status, 0, ILS_ERR_NONFINITE);
+      else if (!conv) atomicCAS(status, 0, ILS_ERR_NO_CONVERGENCE);
+    }
+  }
+  __syncthreads();
+  if (finish) {
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) Xb[off + i] = Xa[off + i];  // return x_k
+  } else {
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) Xb[off + i] = BX[off + i] + cc[off + i];
+  }
+}
+
+__global__ void wide_init_kernel(int64_t k, int32_t* done, int32_t* remaining, int32_t* status) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < k; c += (int64_t)gridDim.x * blockDim.x)
+    done[c] = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *remaining = (int32_t)k;
+    *status = 0;
+  }
+}
+
+ils_status wide_solve(ils_handle h, int64_t k, const double* B, int64_t ldb, double* X, int64_t ldx, int x0_zero,
+                      double tol, ils_info* agg) {
+  cudaStream_t s = h->stream;
+  const int64_t m = h->m, n = h->n, p = h->p;
+  const size_t nk = (size_t)n * (size_t)k;
+  const size_t work = std::max(gemm_tn_work_elems(m, n, k, false, nullptr), gemm_tn_work_elems(n, n, k, false, nullptr));
+  Carver dry{nullptr, 0, true};
+  auto layout = [&](Carver& c, double** bufs, double** bn, double** rr, int64_t** it, int32_t** dn, int32_t** rem,
+                    int32_t** stt, double** wk) {
+    for (int i = 0; i < 6; ++i) bufs[i] = c.take<double>(nk);
+    *bn = c.take<double>(k);
+    *rr = c.take<double>(k);
+    *it = c.take<int64_t>(k);
+    *dn = c.take<int32_t>(k);
+    *rem = c.take<int32_t>(1);
+    *stt = c.take<int32_t>(1);
+    *wk = c.take<double>(std::max<size_t>(work, 1));
+  };
+  double* bufs[6];
+  double *bn, *rr, *wk;
+  int64_t* itv;
+  int32_t *dn, *rem, *stt;
+  layout(dry, bufs, &bn, &rr, &itv, &dn, &rem, &stt, &wk);
+  void* block = nullptr;
+  if (cudaMallocAsync(&block, dry.off, s) != cudaSuccess) {
+    cudaGetLastError();
+    return ILS_ERR_OOM;
+  }
+  Carver real{(char*)block, 0, false};
+  layout(real, bufs, &bn, &rr, &itv, &dn, &rem, &stt, &wk);
+  double *bb = bufs[0], *cc = bufs[1], *Xa = bufs[2], *Xb = bufs[3], *BX = bufs[4], *HX = bufs[5];
+  ils_status st = ILS_OK;
+  auto ck = [&](cudaError_t e, const char* what, int line) {
+    if (e != cudaSuccess && st == ILS_OK) st = record_cuda_error(e, what, line);
+    return st == ILS_OK;
+  };
+  // bbar = A^T J B (Alg. 1 step 4), c = P bbar
+  ck(gemm_tn_f64(m, n, k, h->A, m, B, ldb, p, bb, n, false, false, wk, s), "gemm bbar", __LINE__);
+  if (st == ILS_OK) ck(sq_norms_cols_f64(n, k, bb, n, bn, s), "norms", __LINE__);
+  if (st == ILS_OK) ck(gemm_tn_f64(n, n, k, h->P, n, bb, n, n, cc, n, false, false, wk, s), "gemm c", __LINE__);
+  if (st == ILS_OK) {
+    if (x0_zero) ck(cudaMemsetAsync(Xa, 0, sizeof(double) * nk, s), "memset", __LINE__);
+    else ck(cudaMemcpy2DAsync(Xa, sizeof(double) * n, X, sizeof(double) * ldx, sizeof(double) * n, k,
+                              cudaMemcpyDeviceToDevice, s), "copy x0", __LINE__);
+  }
+  if (st == ILS_OK) {
+    wide_init_kernel<<<(unsigned)std::min<int64_t>((k + 255) / 256, 1024), 256, 0, s>>>(k, dn, rem, stt);
+    note_launch();
+    ck(cudaGetLastError(), "wide init", __LINE__);
+  }
+  int32_t* h_rem = h->h_status + 4;
+  int32_t* h_stt = h->h_status + 5;
+  for (int64_t it = 0; st == ILS_OK && it <= h->opt.max_outer; ++it) {
+    // x_{k+1} = B x_k + c (Alg. 1 step 6) and r_k = bbar - H x_k, for every column at once
+    ck(gemm_tn_f64(n, n, k, h->Bt, n, Xa, n, n, BX, n, false, false, wk, s), "gemm B x", __LINE__);
+    if (st == ILS_OK) ck(gemm_tn_f64(n, n, k, h->H, n, Xa, n, n, HX, n, false, false, wk, s), "gemm H x", __LINE__);
+    if (st != ILS_OK) break;
+    wide_step_kernel<<<(unsigned)k, kWideThreads, 0, s>>>(n, BX, HX, bb, cc, bn, Xa, Xb, dn, rr, itv, it,
+                                                          h->opt.max_outer, tol * tol, rem, stt);
+    note_launch();
+    if (!ck(cudaGetLastError(), "wide step", __LINE__)) break;
+    std::swap(Xa, Xb);
+    ck(cudaMemcpyAsync(h_rem, rem, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "d2h", __LINE__);
+    if (st == ILS_OK) ck(cudaStreamSynchronize(s), "sync", __LINE__);
+    if (st == ILS_OK && *h_rem == 0) break;
+  }
+  // Every column has finished (the step with it == max_outer finishes the rest): Xa holds
+  // each column's returned iterate.
+  std::vector<double> hrr(k), hbn(k);
+  std::vector<int64_t> hit(k);
+  if (st == ILS_OK)
+    ck(cudaMemcpy2DAsync(X, sizeof(double) * ldx, Xa, sizeof(double) * n, sizeof(double) * n, k,
+                         cudaMemcpyDeviceToDevice, s), "copy x", __LINE__);
+  if (st == ILS_OK) ck(cudaMemcpyAsync(hrr.data(), rr, sizeof(double) * k, cudaMemcpyDeviceToHost, s), "d2h", __LINE__);
+  if (st == ILS_OK) ck(cudaMemcpyAsync(hbn.data(), bn, sizeof(double) * k, cudaMemcpyDeviceToHost, s), "d2h", __LINE__);
+  if (st == ILS_OK) ck(cudaMemcpyAsync(hit.data(), itv, sizeof(int64_t) * k, cudaMemcpyDeviceToHost, s), "d2h", __LINE__);
+  if (st == ILS_OK) ck(cudaMemcpyAsync(h_stt, stt, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "d2h", __LINE__);
+  if (st == ILS_OK) ck(cudaStreamSynchronize(s), "sync", __LINE__);
+  cudaFreeAsync(block, s);
+  if (st != ILS_OK) return st;
+  for (int64_t c = 0; c < k; ++c) {
+    const double rel = hbn[c] > 0.0 ? std::sqrt(hrr[c] / hbn[c]) : std::sqrt(hrr[c]);
+    agg->relres = std::max(agg->relres, rel);
+    if (rel != rel) agg->relres = rel;
+    agg->outer_iters = std::max<int64_t>(agg->outer_iters, hit[c]);
+  }
+  if (*h_stt != 0 && agg->status == 0) agg->status = *h_stt;
+  return ILS_OK;
+}
+
 ils_status sp_pass(ils_handle h, int64_t c0, int64_t kk, const double* B, int64_t ldb, double* X, int64_t ldx,
                    int x0_zero, double tol, ils_info* agg) {
   ils_status st = pass_begin(h, c0, kk, B, ldb, X, ldx, x0_zero, tol);
@@ -837,6 +990,12 @@ ils_status ils_solve_many(ils_handle h, int64_t k, const double* B, int64_t ldb,
   h->stream = (cudaStream_t)stream;
   ils_info agg;
   std::memset(&agg, 0, sizeof(agg));
+  if (k >= kWideMinRhs && h->opt.method == ILS_SP && h->opt.precision == ILS_FP64 && !h->mf && !h->sparse) {
+    ils_status st = wide_solve(h, k, B, ldb, X, ldx, x0_zero, tol, &agg);
+    if (st != ILS_OK) agg.status = st;
+    if (info) *info = agg;
+    return (ils_status)agg.status;
+  }
   for (int64_t c0 = 0; c0 < k; c0 += kMaxRhsPerPass) {
     const int64_t kk = std::min<int64_t>(kMaxRhsPerPass, k - c0);
     ils_status st = sp_pass(h, c0, kk, B + c0 * ldb, ldb, X + c0 * ldx, ldx, x0_zero, tol, &agg);

@@ -146,3 +146,35 @@ def test_not_spd_and_nonfinite_inputs(ils):
     info = s.solve(vec(ok.b), x, tol=1e-12, allow=(ils.ILS_ERR_NONFINITE,))
     assert info.status == ils.ILS_ERR_NONFINITE
     s.close()
+
+
+def test_many_rhs_wide_path_matches_oracle(ils):
+    """40 right-hand sides in one call take the GEMM-based path (all columns per step); each
+    column matches the oracle to 1e-10 and the 8-column passes to 1e-12, with a warm start
+    that is already converged for one column (it returns x0 after zero steps)."""
+    import torch
+    inst = W.dense_gaussian(1600, 400, 120, 0.3, 21)
+    rng = np.random.default_rng(5)
+    k = 40
+    Bm = inst.A @ rng.standard_normal((inst.n, k)) + 1e-3 * rng.standard_normal((inst.m, k))
+    Xs = O.normal_equation_solve(inst.A, Bm, inst.p)
+    s = ils.Solver(colmajor(inst.A), inst.p)
+    Bt = colmajor(Bm)
+    Xw = torch.zeros((k, inst.n), dtype=torch.float64, device="cuda")
+    info = s.solve_many(Bt, Xw, tol=1e-12)
+    Xn = torch.zeros((k, inst.n), dtype=torch.float64, device="cuda")
+    for c0 in range(0, k, 8):
+        s.solve_many(Bt[c0:c0 + 8], Xn[c0:c0 + 8], tol=1e-12)
+    torch.cuda.synchronize()
+    xw, xn = to_np_colmajor(Xw), to_np_colmajor(Xn)
+    assert info.status == ils.ILS_OK
+    for c in range(k):
+        assert relerr(xw[:, c], Xs[:, c]) <= 1e-10
+        assert relerr(xw[:, c], xn[:, c]) <= 1e-12
+    X0 = torch.zeros((k, inst.n), dtype=torch.float64, device="cuda")
+    X0[3] = torch.from_numpy(Xs[:, 3]).cuda()
+    info2 = s.solve_many(Bt, X0, x0_zero=False, tol=1e-10)
+    torch.cuda.synchronize()
+    assert info2.status == ils.ILS_OK
+    assert np.array_equal(X0[3].cpu().numpy(), Xs[:, 3])
+    s.close()
