@@ -1026,6 +1026,12 @@ cudaError_t cholesky_f64_batch(int64_t n, int count, double* const* mats, double
   return cholesky_batch_t<double>(n, count, mats, inv_diag, stash, status, s);
 }
 
+cudaError_t cholesky_f32(int64_t n, float* M, float* inv_diag, float* stash, int32_t* status, cudaStream_t s) {
+  float* mats[2] = {M, M};
+  float* invd[2] = {inv_diag, inv_diag};
+  return cholesky_batch_t<float>(n, 1, mats, invd, stash, status, s);
+}
+
 
 template <typename T>
 cudaError_t trsm_lower_t(int64_t n, int64_t k, const T* L, T* X, int64_t ldx, bool forward, bool backward,

@@ -77,6 +77,18 @@ struct ils_handle_s {
   int32_t* cnt_fill = nullptr;  // 2n
   int32_t* sp_err = nullptr;
   double* stash64 = nullptr;   // 2 x 1024: the Cholesky panels' diagonal-block stash
+  // Overlapped mixed setup (single handles, split Grams): A_2^T A_2 and the SPD test of H
+  // (an FP32 Cholesky, confirmed in FP64 when it fails) run on a second stream while the
+  // FP64 Cholesky of Abar1 runs on the handle's stream.
+  bool overlap = false;
+  cudaStream_t s_aux = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_g1 = nullptr, ev_g2 = nullptr, ev_join = nullptr;
+  void* gs_slices2 = nullptr;
+  double* gs_partial2 = nullptr;
+  int* gs_exps2 = nullptr;
+  float* H32 = nullptr;
+  float* stash32 = nullptr;
+  int32_t* dstatus2 = nullptr;
   SolveState* st = nullptr;
   int32_t* dstatus = nullptr;
   // pinned host mirrors
@@ -221,6 +233,14 @@ void carve(ils_handle h, Carver& c, size_t work_elems) {
     h->gs_partial = c.take<double>(std::max(w1.partial_elems, w2.partial_elems));
     h->gs_exps = c.take<int>((size_t)h->n);
     h->gs_err = c.take<int32_t>(1);
+    if (h->overlap) {
+      h->gs_slices2 = c.take<uint16_t>(w2.slice_elems);
+      h->gs_partial2 = c.take<double>(w2.partial_elems);
+      h->gs_exps2 = c.take<int>((size_t)h->n);
+      h->H32 = c.take<float>((size_t)h->n * (size_t)h->n);
+      h->stash32 = c.take<float>(1024);
+      h->dstatus2 = c.take<int32_t>(1);
+    }
   }
   if (h->sparse) {
     const size_t nnz = (size_t)std::max<int64_t>(h->nnz, 1);
@@ -337,7 +357,10 @@ ils_status compute_setup_sparse(ils_handle h, const int32_t* rowptr, const int32
 }
 
 // All setup products for the current contents of h->A.
+ils_status compute_setup_overlap(ils_handle h);
+
 ils_status compute_setup(ils_handle h) {
+  if (h->overlap) return compute_setup_overlap(h);
   cudaStream_t s = h->stream;
   const int64_t m = h->m, n = h->n, p = h->p, q = h->q;
   ILS_CK(mark(h, 1));
@@ -400,10 +423,66 @@ ils_status compute_products(ils_handle h) {
   return ILS_OK;
 }
 
+// Mixed precision with split Grams on one handle: the second stream computes Abar2 and
+// tests H while the handle's stream factors Abar1 (Alg. 1 step 2) and forms P and B.
+ils_status compute_setup_overlap(ils_handle h) {
+  cudaStream_t s = h->stream, a = h->s_aux;
+  const int64_t m = h->m, n = h->n, p = h->p, q = h->q;
+  ILS_CK(mark(h, 1));
+  ILS_CK(cudaMemsetAsync(h->gs_err, 0, sizeof(int32_t), s));
+  ILS_CK(cudaMemsetAsync(h->dstatus2, 0, sizeof(int32_t), s));
+  ILS_CK(cudaEventRecord(h->ev_start, s));
+  ILS_CK(cudaStreamWaitEvent(a, h->ev_start, 0));
+  // Abar1 = A_1^T A_1 here, Abar2 = A_2^T A_2 there (Alg. 1 steps 2-3)
+  ILS_CK(gram_split_tc(p, n, h->A, m, h->G1, n, h->gs_slices, h->gs_partial, h->gs_exps, h->gs_err, s));
+  ILS_CK(cudaEventRecord(h->ev_g1, s));
+  ILS_CK(gram_split_tc(q, n, h->A + p, m, h->G2, n, h->gs_slices2, h->gs_partial2, h->gs_exps2, h->gs_err, a));
+  ILS_CK(cudaEventRecord(h->ev_g2, a));
+  // Condition (1.3) on the second stream: H = Abar1 - Abar2 factored in FP32 as a test.
+  ILS_CK(cudaStreamWaitEvent(a, h->ev_g1, 0));
+  ILS_CK(axpby_mat_f64(n, 1.0, h->G1, -1.0, h->G2, h->H, a));
+  ILS_CK(convert_f64_to_f32(n * n, h->H, h->H32, a));
+  ILS_CK(cholesky_f32(n, h->H32, reinterpret_cast<float*>(h->inv_diag + n), h->stash32, h->dstatus2, a));
+  ILS_CK(cudaMemcpyAsync(h->h_status + 3, h->dstatus2, sizeof(int32_t), cudaMemcpyDeviceToHost, a));
+  ILS_CK(cudaEventRecord(h->ev_join, a));
+  ILS_CK(mark(h, 2));
+  ILS_CK(mark(h, 3));
+  // Cholesky of Abar1 (FP64)
+  ILS_CK(cudaMemcpyAsync(h->L, h->G1, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, s));
+  ILS_CK(cudaMemsetAsync(h->dstatus, 0, sizeof(int32_t), s));
+  {
+    double* mats[2] = {h->L, h->L};
+    double* invd[2] = {h->inv_diag, h->inv_diag};
+    ILS_CK(cholesky_f64_batch(n, 1, mats, invd, h->stash64, h->dstatus, s));
+  }
+  ILS_CK(mark(h, 4));
+  ILS_CK(cudaMemcpyAsync(h->h_status, h->dstatus, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  ILS_CK(cudaStreamWaitEvent(s, h->ev_g2, 0));
+  ILS_CK(cudaMemcpyAsync(h->h_status + 1, h->gs_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  ILS_CK(mixed_setup(n, h->L, h->G2, h->opt.precision, h->L32, h->P32, h->G2_32, h->Bt32, h->Bt16,
+                     reinterpret_cast<float*>(h->Dinv), s));
+  ILS_CK(cudaStreamWaitEvent(s, h->ev_join, 0));
+  ILS_CK(mark(h, 5));
+  return ILS_OK;
+}
+
 // Wait for the setup enqueued by compute_setup and report its pivot / input status.
 ils_status setup_finish(ils_handle h) {
   ILS_CK(cudaStreamSynchronize(h->stream));
   if (h->sparse && h->h_status[2] != 0) return (ils_status)h->h_status[2];
+  if (h->overlap && h->h_status[3] != 0 && h->h_status[1] == 0 && *h->h_status == 0) {
+    // The FP32 test of H failed: the FP64 factorization decides (in the P buffer).
+    cudaStream_t s = h->stream;
+    const int64_t n = h->n;
+    ILS_CK(cudaMemcpyAsync(h->P, h->H, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, s));
+    ILS_CK(cudaMemsetAsync(h->dstatus2, 0, sizeof(int32_t), s));
+    double* mats[2] = {h->P, h->P};
+    double* invd[2] = {h->inv_diag + n, h->inv_diag + n};
+    ILS_CK(cholesky_f64_batch(n, 1, mats, invd, h->stash64, h->dstatus2, s));
+    ILS_CK(cudaMemcpyAsync(h->h_status + 3, h->dstatus2, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    ILS_CK(cudaStreamSynchronize(s));
+    if (h->h_status[3] != 0) return (ils_status)h->h_status[3];
+  }
   h->h_status[1] = h->opt.gram == ILS_GRAM_SPLIT ? h->h_status[1] : 0;
   if (h->h_status[1] != 0) return h->h_status[1] == 2 ? ILS_ERR_NONFINITE : ILS_ERR_TIMEOUT;
   if (*h->h_status != 0) return (ils_status)*h->h_status;
@@ -421,6 +500,12 @@ ils_status tune_handle(ils_handle h) {
 void free_handle(ils_handle h) {
   if (!h) return;
   if (h->block) cudaFreeAsync(h->block, h->stream);
+  if (h->s_aux) {
+    cudaStreamSynchronize(h->s_aux);
+    cudaStreamDestroy(h->s_aux);
+  }
+  for (cudaEvent_t e : {h->ev_start, h->ev_g1, h->ev_g2, h->ev_join})
+    if (e) cudaEventDestroy(e);
   if (h->h_st) cudaFreeHost(h->h_st);
   for (cudaEvent_t e : h->ev)
     if (e) cudaEventDestroy(e);
@@ -787,7 +872,8 @@ ils_status sp_pass(ils_handle h, int64_t c0, int64_t kk, const double* B, int64_
 // Validate a problem, allocate its handle and carve its device memory (stream-ordered
 // on `stream`); nothing is computed yet.
 ils_status create_handle(ils_handle* out, int64_t m, int64_t n, int64_t p, int64_t q, const double* A, int64_t lda,
-                         const ils_options* o, cudaStream_t stream, int64_t sparse_nnz = -1) {
+                         const ils_options* o, cudaStream_t stream, int64_t sparse_nnz = -1,
+                         bool overlap_ok = true) {
   *out = nullptr;
   const bool sparse = sparse_nnz >= 0;
   if (n < 1 || n > kMaxN || p < n || q < 0 || m != p + q || m > ((int64_t)1 << 31)) return ILS_ERR_INVALID_ARG;
@@ -831,6 +917,8 @@ ils_status create_handle(ils_handle* out, int64_t m, int64_t n, int64_t p, int64
   h->sparse = sparse;
   h->nnz = sparse ? sparse_nnz : 0;
   h->stream = stream;
+  h->overlap = overlap_ok && !sparse && !mf && opt.method == ILS_SP && opt.precision != ILS_FP64 &&
+               opt.gram == ILS_GRAM_SPLIT && q > 0;
   if (sparse && opt.method == ILS_SP_RK_RGS && opt.chain_ctas >= 0) {
     const double col_entries = (double)sparse_nnz * ((double)p / (double)m) / (double)n;  // A_1 entries per column
     const bool fp32 = opt.precision == ILS_FP32_REFINE;
@@ -853,6 +941,16 @@ ils_status create_handle(ils_handle* out, int64_t m, int64_t n, int64_t p, int64
   }
   Carver real{(char*)h->block, 0, false};
   carve(h, real, work);
+  if (h->overlap) {
+    bool ok = cudaStreamCreateWithFlags(&h->s_aux, cudaStreamNonBlocking) == cudaSuccess;
+    for (cudaEvent_t* e : {&h->ev_start, &h->ev_g1, &h->ev_g2, &h->ev_join})
+      ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      free_handle(h);
+      return ILS_ERR_CUDA;
+    }
+  }
   const size_t host_bytes = align_up(sizeof(SolveState)) + align_up(sizeof(int32_t)) +
                             4 * align_up(sizeof(double) * kMaxRhsPerPass);
   char* hb = nullptr;
@@ -1121,7 +1219,7 @@ ils_status ils_batch_setup(ils_batch* out, int64_t count, const ils_problem* pro
   for (int64_t i = 0; i < count && st == ILS_OK; ++i) {
     const ils_problem& pr = probs[i];
     cudaStream_t s = b->streams[i % ns];
-    st = create_handle(&b->h[i], pr.m, pr.n, pr.p, pr.q, pr.A, pr.lda, o, s);
+    st = create_handle(&b->h[i], pr.m, pr.n, pr.p, pr.q, pr.A, pr.lda, o, s, -1, false);
     if (st != ILS_OK) break;
     ils_handle h = b->h[i];
     if (copy_matrix_f64(h->m, h->n, pr.A, pr.lda, h->A, s) != cudaSuccess) {

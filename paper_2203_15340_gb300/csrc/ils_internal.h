@@ -60,6 +60,9 @@ cudaError_t gemv_cols_f64(int64_t n, int64_t k, const double* M, int64_t ldm, co
 cudaError_t cholesky_f64_batch(int64_t n, int count, double* const* mats, double* const* inv_diag, double* stash,
                                int32_t* status, cudaStream_t s);
 
+// The same factorization of one FP32 matrix (an SPD test).
+cudaError_t cholesky_f32(int64_t n, float* M, float* inv_diag, float* stash, int32_t* status, cudaStream_t s);
+
 // X := L^{-1} X (lower = forward) then, if both, X := L^{-T} X.  X n x k (ldx).
 cudaError_t trsm_lower_f64(int64_t n, int64_t k, const double* L, double* X, int64_t ldx,
                            bool forward, bool backward, cudaStream_t s);
@@ -191,6 +194,7 @@ int ils_tuned_shape_impl(int64_t n, int64_t k, int bf16, int* warps, int* blocks
 cudaError_t mixed_setup(int64_t n, const double* L, const double* G2, int precision, float* L32, float* P32,
                         float* G2_32, float* Bt32, void* Bt16, float* Dinv32, cudaStream_t s);
 cudaError_t mixed_correct(const MixedArgs& a, int precision, cudaStream_t s);
+cudaError_t convert_f64_to_f32(int64_t count, const double* src, float* dst, cudaStream_t s);
 cudaError_t mixed_correct_mf(const MixedArgs& a, int precision, int64_t q, const void* Aq_lo, void* part, double* v,
                              double* d64, float* t32, cudaStream_t s);
 

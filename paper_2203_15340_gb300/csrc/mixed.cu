@@ -333,6 +333,12 @@ cudaError_t tri_inverse_f32(int64_t n, float* X, float* W, float* Dinv, cudaStre
   return cudaSuccess;
 }
 
+cudaError_t convert_f64_to_f32(int64_t count, const double* src, float* dst, cudaStream_t s) {
+  f64_to_f32_kernel<<<grid_small(count), 256, 0, s>>>(count, src, dst);
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t mixed_setup(int64_t n, const double* L, const double* G2, int precision, float* L32, float* P32,
                         float* G2_32, float* Bt32, void* Bt16, float* Dinv32, cudaStream_t s) {
   const int64_t nn = n * n;

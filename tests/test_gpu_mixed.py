@@ -97,3 +97,14 @@ def test_sweep_autotuner_picks_a_shape_and_keeps_results(ils):
     xs = O.qr_cholesky_solve(inst.A, inst.b, inst.p)
     assert info.status == ils.ILS_OK and relerr(x.cpu().numpy(), xs) <= 1e-10
     s.close()
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_mixed_setup_rejects_indefinite_h(ils, prec):
+    """A_1^T A_1 is SPD but A^T J A is not: the mixed setup (whose H test runs in FP32 beside
+    the FP64 factorization of A_1^T A_1, confirmed in FP64) reports NOT_SPD."""
+    bad = W.dense_gaussian(400, 300, 60, 2.0, 3)
+    assert not O.is_spd(O.normal_matrix(bad.A, bad.p))
+    with pytest.raises(ils.ILSError) as e:
+        ils.Solver(colmajor(bad.A), bad.p, ils.options(precision=prec))
+    assert e.value.code == ils.ILS_ERR_NOT_SPD
