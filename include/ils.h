@@ -56,11 +56,13 @@ typedef enum {
 
 typedef enum {
   ILS_FP64 = 0,        /* every product in FP64 (the paper's arithmetic) */
-  ILS_FP32_REFINE = 1, /* SP method: FP64-accurate Grams and Cholesky factor; the correction
-                          sweeps use P = Abar1^{-1} and B = P Abar2 in FP32 with FP32
-                          accumulation; each step's residual bbar - H x is FP64 (iterative
-                          refinement), so the FP64 stopping test still decides.  Also
-                          SP-RK-RGS on a sparse A (see ils_setup_csr). */
+  ILS_FP32_REFINE = 1, /* SP method: FP64-accurate Grams; the correction sweeps use
+                          P = Abar1^{-1} and B = P Abar2 in FP32 with FP32 accumulation
+                          (P from an FP32 Cholesky factor of Abar1 on handles with split
+                          Grams, from the FP64 one otherwise; an FP32 pivot that fails
+                          falls back to FP64); each step's residual bbar - H x is FP64
+                          (iterative refinement), so the FP64 stopping test still decides.
+                          Also SP-RK-RGS on a sparse A (see ils_setup_csr). */
   ILS_BF16_REFINE = 2  /* as ILS_FP32_REFINE with B held in BF16 (FP32 accumulation) */
 } ils_precision;
 
@@ -173,8 +175,9 @@ ils_status ils_solve_many(ils_handle h, int64_t k, const double* B, int64_t ldb,
                           ils_stream_t stream);
 
 /* Copy an internal n x n FP64 product of the handle into dst (device, column-major,
- * leading dimension ldd >= n): which = 0 Abar1, 1 Abar2, 2 Cholesky factor L of
- * Abar1 (lower triangle; the strict upper triangle of dst is set to 0), 3 P = Abar1^{-1},
+ * leading dimension ldd >= n): which = 0 Abar1, 1 Abar2, 2 FP64 Cholesky factor L of
+ * Abar1 (lower triangle; the strict upper triangle of dst is set to 0; formed on demand,
+ * synchronizing the handle's stream, where the setup factored Abar1 in FP32 only), 3 P = Abar1^{-1},
  * 4 B = P Abar2.  P and B are formed only by FP64 SP handles (B only on the explicit
  * route); asking another handle for them is INVALID_ARG.  For tests and diagnostics.
  * Errors: INVALID_ARG, CUDA. */

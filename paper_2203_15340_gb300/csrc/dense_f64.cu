@@ -840,6 +840,207 @@ __global__ void copy_final_kernel(int64_t n, int64_t k, const double* X0, const 
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// FP32 Cholesky in one launch (n <= kDfMaxN): left-looking and data-driven.  CTA j owns
+// the 32-column panel j and keeps rows 32j..n-1 of it in shared memory.  It applies the
+// update from each earlier panel k as soon as panel k's flag is set (A_j -= L_k L_k(j)^T,
+// where L_k(j) is the panel's 32 x 32 block in the rows of block j), then factors its
+// diagonal block in one warp (lane = row, the block in registers, each pivot's column
+// broadcast by shuffles), solves its rows below by forward substitution against the
+// factored block, stores the panel and sets its own flag.  The only serial chain left is
+// one panel update, one 32 x 32 factorization and one solve per panel; the n^3/3
+// multiply-adds are spread over the panels' CTAs, and no launch boundary separates the
+// panels.  Panel k's flag is set only after its stores are fenced; a waiting CTA reads
+// the panel through L2.  Every wait is bounded: past the limit the CTA records TIMEOUT,
+// raises the abort word (which releases every other waiter) and returns.
+// ---------------------------------------------------------------------------------------
+constexpr int kDfThreads = 256;
+constexpr int kDfPad = 33;  // row stride of the panel in shared memory (conflict-free rows and columns)
+constexpr int64_t kDfMaxN = 1600;
+
+// Panel floats, rounded up to a multiple of 4 so that the 32 x 32 blocks after it are
+// 16-byte aligned for their float4 reads.
+__host__ __device__ __forceinline__ size_t df_panel_floats(int64_t n) {
+  return ((size_t)(n < 32 ? 32 : n) * kDfPad + 3) & ~(size_t)3;
+}
+
+struct DfArgs {
+  float* M[2];
+  float* inv_diag[2];
+  uint32_t* flags[2];  // per panel: 1 once stored; flags[i][npanels] is the abort word
+  int32_t* status[2];
+  int64_t n;
+};
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Thread 0 waits for flag == 1; false (for the whole CTA) on abort or after about 1 s.
+__device__ bool df_wait(const uint32_t* flag, uint32_t* abort_word, int32_t* status) {
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    int res = 1;
+    uint64_t t0 = 0;
+    for (uint32_t spin = 0;; ++spin) {
+      if (ld_acquire_u32(flag) != 0u) break;
+      if (ld_acquire_u32(abort_word) != 0u) {
+        res = 0;
+        break;
+      }
+      if ((spin & 31u) == 0u) {
+        uint64_t t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (spin == 0u) {
+          t0 = t;
+        } else if (t - t0 > 1000000000ull) {
+          atomicCAS(status, 0, (int32_t)ILS_ERR_TIMEOUT);
+          atomicExch(abort_word, 1u);
+          res = 0;
+          break;
+        }
+      }
+      __nanosleep(64);
+    }
+    ok = res;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+__global__ void __launch_bounds__(kDfThreads)
+chol_dataflow_f32_kernel(DfArgs a) {
+  extern __shared__ __align__(16) float df_smem[];
+  const int mat = blockIdx.y;
+  float* L = a.M[mat];
+  uint32_t* flags = a.flags[mat];
+  int32_t* status = a.status[mat];
+  const int64_t n = a.n;
+  const int npanels = (int)((n + 31) / 32);
+  uint32_t* abort_word = flags + npanels;
+  const int j = blockIdx.x;
+  const int64_t c0 = 32 * (int64_t)j;
+  const int nb = (int)(n - c0 < 32 ? n - c0 : 32);
+  const int rows = (int)(n - c0);
+  const int rows_sm = rows < 32 ? 32 : rows;
+  float* P = df_smem;                                           // rows_sm x kDfPad
+  float* W = P + df_panel_floats(n);                            // [kk][c]: L(c0 + c, 32k + kk)
+  float* LT = W + 1024;                                         // [c][d] = L11(d, c)
+  __shared__ float rinv[32];
+  const int tid = threadIdx.x;
+
+  // Own panel: lower entries of the diagonal block and every row below; the columns past
+  // a ragged last panel and the rows past n act as an identity block.
+  for (int e = tid; e < 32 * rows_sm; e += kDfThreads) {
+    const int c = e / rows_sm, r = e - c * rows_sm;
+    float v;
+    if (c < nb && r < rows) v = (r >= 32 || r >= c) ? L[(c0 + r) + (c0 + c) * n] : 0.f;
+    else v = (r == c) ? 1.f : 0.f;
+    P[r * kDfPad + c] = v;
+  }
+  __syncthreads();
+
+  // Updates from the earlier panels, in order of completion.
+  for (int k = 0; k < j; ++k) {
+    if (!df_wait(flags + k, abort_word, status)) return;
+    const float* Lk = L + 32 * (int64_t)k * n;
+    for (int e = tid; e < 1024; e += kDfThreads) {
+      const int c = e & 31, kk = e >> 5;
+      W[e] = c < nb ? __ldcg(Lk + (c0 + c) + kk * n) : 0.f;
+    }
+    __syncthreads();
+    for (int r = tid; r < rows; r += kDfThreads) {
+      float lk[32];
+#pragma unroll
+      for (int kk = 0; kk < 32; ++kk) lk[kk] = __ldcg(Lk + (c0 + r) + kk * n);
+      float acc[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) acc[c] = P[r * kDfPad + c];
+#pragma unroll
+      for (int kk = 0; kk < 32; ++kk) {
+        const float4* w4 = reinterpret_cast<const float4*>(W + kk * 32);
+#pragma unroll
+        for (int c4 = 0; c4 < 8; ++c4) {
+          const float4 w = w4[c4];
+          acc[4 * c4 + 0] = fmaf(-lk[kk], w.x, acc[4 * c4 + 0]);
+          acc[4 * c4 + 1] = fmaf(-lk[kk], w.y, acc[4 * c4 + 1]);
+          acc[4 * c4 + 2] = fmaf(-lk[kk], w.z, acc[4 * c4 + 2]);
+          acc[4 * c4 + 3] = fmaf(-lk[kk], w.w, acc[4 * c4 + 3]);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 32; ++c) P[r * kDfPad + c] = acc[c];
+    }
+    __syncthreads();
+  }
+
+  // Diagonal block: warp 0, lane i holds row i.  Pivot c: l_cc = sqrt(d), l_ic = a_ic / l_cc,
+  // then a_ij -= l_ic l_jc for j > c (row i's lane receives l_jc from lane j).
+  if (tid < 32) {
+    const int lane = tid;
+    float v[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) v[c] = P[lane * kDfPad + c];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+      float d = __shfl_sync(0xffffffffu, v[c], c);
+      const int code = pivot_code(d);
+      if (code != 0) {
+        if (lane == 0) set_status(status, code);
+        d = 1.f;
+      }
+      const float rs = rsqrtf(d);
+      const float lc = lane > c ? v[c] * rs : (lane == c ? d * rs : 0.f);
+      v[c] = lc;
+      if (lane == 0) rinv[c] = rs;
+#pragma unroll
+      for (int jj = c + 1; jj < 32; ++jj) v[jj] = fmaf(-lc, __shfl_sync(0xffffffffu, lc, jj), v[jj]);
+    }
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+      const float l = lane >= c ? v[c] : 0.f;
+      P[lane * kDfPad + c] = l;
+      LT[c * 32 + lane] = l;
+    }
+  }
+  __syncthreads();
+
+  // Rows below the diagonal block: x = a L11^{-T} by forward substitution.
+  for (int r = 32 + tid; r < rows; r += kDfThreads) {
+    float x[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) x[c] = P[r * kDfPad + c];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+      x[c] *= rinv[c];
+#pragma unroll
+      for (int d = c + 1; d < 32; ++d) x[d] = fmaf(-x[c], LT[c * 32 + d], x[d]);
+    }
+#pragma unroll
+    for (int c = 0; c < 32; ++c) P[r * kDfPad + c] = x[c];
+  }
+  __syncthreads();
+
+  // Store the panel (lower part of the diagonal block), fence, then raise the flag.
+  for (int e = tid; e < nb * rows; e += kDfThreads) {
+    const int c = e / rows, r = e - c * rows;
+    if (r >= c) L[(c0 + r) + (c0 + c) * n] = P[r * kDfPad + c];
+  }
+  if (tid < nb) a.inv_diag[mat][c0 + tid] = rinv[tid];
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) st_release_u32(flags + j, 1u);
+}
+
+size_t df_smem_bytes(int64_t n) {
+  return sizeof(float) * (df_panel_floats(n) + 2048);
+}
+
 int grid_for(int64_t total, int threads) {
   int64_t b = (total + threads - 1) / threads;
   const int64_t cap = 8 * (int64_t)num_sms();
@@ -1026,10 +1227,62 @@ cudaError_t cholesky_f64_batch(int64_t n, int count, double* const* mats, double
   return cholesky_batch_t<double>(n, count, mats, inv_diag, stash, status, s);
 }
 
+cudaError_t cholesky_f32_df(int64_t n, int count, float* const* mats, float* const* inv_diag, float* stash,
+                            int32_t* const* status, cudaStream_t s) {
+  // The stash holds the panel flags: npanels + 1 words per matrix, 1024 words apart.
+  const int npanels = (int)((n + 31) / 32);
+  DfArgs a;
+  for (int i = 0; i < 2; ++i) {
+    const int src = i < count ? i : 0;
+    a.M[i] = mats[src];
+    a.inv_diag[i] = inv_diag[src];
+    a.flags[i] = reinterpret_cast<uint32_t*>(stash) + 1024 * src;
+    a.status[i] = status[src];
+  }
+  a.n = n;
+  cudaError_t e = cudaMemsetAsync(stash, 0, sizeof(uint32_t) * (1024 * (count - 1) + npanels + 1), s);
+  if (e != cudaSuccess) return e;
+  static const cudaError_t attr_err = cudaFuncSetAttribute(
+      chol_dataflow_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)df_smem_bytes(kDfMaxN));
+  if (attr_err != cudaSuccess) return attr_err;
+  // Cooperative launch: all panels' CTAs are resident together, so a CTA waiting for an
+  // earlier panel never holds the SM that panel needs.
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)npanels, (unsigned)count, 1);
+  cfg.blockDim = dim3(kDfThreads, 1, 1);
+  cfg.dynamicSmemBytes = df_smem_bytes(n);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, chol_dataflow_f32_kernel, a);
+  note_launch();
+  return e;
+}
+
 cudaError_t cholesky_f32(int64_t n, float* M, float* inv_diag, float* stash, int32_t* status, cudaStream_t s) {
   float* mats[2] = {M, M};
   float* invd[2] = {inv_diag, inv_diag};
+  if (n > 0 && n <= kDfMaxN) {
+    int32_t* st[2] = {status, status};
+    return cholesky_f32_df(n, 1, mats, invd, stash, st, s);
+  }
   return cholesky_batch_t<float>(n, 1, mats, invd, stash, status, s);
+}
+
+cudaError_t cholesky_f32_pair(int64_t n, float* M0, float* M1, float* inv0, float* inv1, float* stash,
+                              int32_t* status0, int32_t* status1, cudaStream_t s) {
+  if (n > 0 && n <= kDfMaxN) {
+    float* mats[2] = {M0, M1};
+    float* invd[2] = {inv0, inv1};
+    int32_t* st[2] = {status0, status1};
+    return cholesky_f32_df(n, 2, mats, invd, stash, st, s);
+  }
+  cudaError_t e = cholesky_f32(n, M0, inv0, stash, status0, s);
+  if (e != cudaSuccess) return e;
+  return cholesky_f32(n, M1, inv1, stash, status1, s);
 }
 
 

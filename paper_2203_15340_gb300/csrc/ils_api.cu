@@ -77,12 +77,13 @@ struct ils_handle_s {
   int32_t* cnt_fill = nullptr;  // 2n
   int32_t* sp_err = nullptr;
   double* stash64 = nullptr;   // 2 x 1024: the Cholesky panels' diagonal-block stash
-  // Overlapped mixed setup (single handles, split Grams): A_2^T A_2 and the SPD test of H
-  // (an FP32 Cholesky, confirmed in FP64 when it fails) run on a second stream while the
-  // FP64 Cholesky of Abar1 runs on the handle's stream.
+  // Overlapped mixed setup (single handles, split Grams): A_2^T A_2 runs on a second stream
+  // beside A_1^T A_1; Abar1 and H are then factored in FP32 in one launch (a failed FP32
+  // pivot is settled by the FP64 factorization).
   bool overlap = false;
+  bool l64_valid = true;  // L holds the FP64 factor of the current Abar1 (else formed on demand)
   cudaStream_t s_aux = nullptr;
-  cudaEvent_t ev_start = nullptr, ev_g1 = nullptr, ev_g2 = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_g2 = nullptr;
   void* gs_slices2 = nullptr;
   double* gs_partial2 = nullptr;
   int* gs_exps2 = nullptr;
@@ -238,7 +239,7 @@ void carve(ils_handle h, Carver& c, size_t work_elems) {
       h->gs_partial2 = c.take<double>(w2.partial_elems);
       h->gs_exps2 = c.take<int>((size_t)h->n);
       h->H32 = c.take<float>((size_t)h->n * (size_t)h->n);
-      h->stash32 = c.take<float>(1024);
+      h->stash32 = c.take<float>(2 * 1024);  // panel flags of the FP32 factorizations
       h->dstatus2 = c.take<int32_t>(1);
     }
   }
@@ -313,6 +314,7 @@ void collect_timings(ils_handle h) {
 ils_status compute_setup_mf(ils_handle h) {
   cudaStream_t s = h->stream;
   const int64_t m = h->m, n = h->n, p = h->p, q = h->q;
+  h->l64_valid = true;
   ILS_CK(mark(h, 3));
   ILS_CK(cudaMemcpyAsync(h->L, h->G1, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, s));
   ILS_CK(cudaMemsetAsync(h->dstatus, 0, sizeof(int32_t), s));
@@ -388,6 +390,7 @@ ils_status compute_setup(ils_handle h) {
 ils_status compute_products(ils_handle h) {
   cudaStream_t s = h->stream;
   const int64_t n = h->n;
+  h->l64_valid = true;
   ILS_CK(axpby_mat_f64(n, 1.0, h->G1, -1.0, h->G2, h->H, s));
   // Cholesky of Abar1; the explicit inverse of Alg. 1 step 2 is formed from it.
   ILS_CK(cudaMemcpyAsync(h->L, h->G1, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, s));
@@ -423,46 +426,59 @@ ils_status compute_products(ils_handle h) {
   return ILS_OK;
 }
 
-// Mixed precision with split Grams on one handle: the second stream computes Abar2 and
-// tests H while the handle's stream factors Abar1 (Alg. 1 step 2) and forms P and B.
+// Mixed precision with split Grams on one handle: the second stream computes Abar2 while
+// the handle's stream computes Abar1; then one launch factors Abar1 (Alg. 1 step 2) and
+// H = Abar1 - Abar2 (the SPD test of condition (1.3)) together, and P and B follow.
+// Both are factored in FP32: the correction sweeps only need P to FP32 accuracy (the FP64
+// residuals of the refinement supply the rest), and a factor rounded from FP64 would be no
+// better once inverted in FP32.  An FP32 pivot that fails sends setup_finish to the FP64
+// factorization of that matrix, which then decides.
 ils_status compute_setup_overlap(ils_handle h) {
   cudaStream_t s = h->stream, a = h->s_aux;
   const int64_t m = h->m, n = h->n, p = h->p, q = h->q;
   ILS_CK(mark(h, 1));
+  h->h_status[0] = 0;
+  h->l64_valid = false;
   ILS_CK(cudaMemsetAsync(h->gs_err, 0, sizeof(int32_t), s));
   ILS_CK(cudaMemsetAsync(h->dstatus2, 0, sizeof(int32_t), s));
+  ILS_CK(cudaMemsetAsync(h->dstatus, 0, sizeof(int32_t), s));
   ILS_CK(cudaEventRecord(h->ev_start, s));
   ILS_CK(cudaStreamWaitEvent(a, h->ev_start, 0));
   // Abar1 = A_1^T A_1 here, Abar2 = A_2^T A_2 there (Alg. 1 steps 2-3)
   ILS_CK(gram_split_tc(p, n, h->A, m, h->G1, n, h->gs_slices, h->gs_partial, h->gs_exps, h->gs_err, s));
-  ILS_CK(cudaEventRecord(h->ev_g1, s));
   ILS_CK(gram_split_tc(q, n, h->A + p, m, h->G2, n, h->gs_slices2, h->gs_partial2, h->gs_exps2, h->gs_err, a));
   ILS_CK(cudaEventRecord(h->ev_g2, a));
-  // Condition (1.3) on the second stream: H = Abar1 - Abar2 factored in FP32 as a test.
-  ILS_CK(cudaStreamWaitEvent(a, h->ev_g1, 0));
-  ILS_CK(axpby_mat_f64(n, 1.0, h->G1, -1.0, h->G2, h->H, a));
-  ILS_CK(convert_f64_to_f32(n * n, h->H, h->H32, a));
-  ILS_CK(cholesky_f32(n, h->H32, reinterpret_cast<float*>(h->inv_diag + n), h->stash32, h->dstatus2, a));
-  ILS_CK(cudaMemcpyAsync(h->h_status + 3, h->dstatus2, sizeof(int32_t), cudaMemcpyDeviceToHost, a));
-  ILS_CK(cudaEventRecord(h->ev_join, a));
   ILS_CK(mark(h, 2));
+  ILS_CK(lower_to_f32(n, h->G1, h->L32, s));
+  ILS_CK(cudaStreamWaitEvent(s, h->ev_g2, 0));
   ILS_CK(mark(h, 3));
-  // Cholesky of Abar1 (FP64)
+  ILS_CK(axpby_mat_f64(n, 1.0, h->G1, -1.0, h->G2, h->H, s));
+  ILS_CK(convert_f64_to_f32(n * n, h->H, h->H32, s));
+  ILS_CK(cholesky_f32_pair(n, h->L32, h->H32, reinterpret_cast<float*>(h->inv_diag),
+                           reinterpret_cast<float*>(h->inv_diag + n), h->stash32, h->dstatus, h->dstatus2, s));
+  ILS_CK(mark(h, 4));
+  ILS_CK(cudaMemcpyAsync(h->h_status + 6, h->dstatus, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  ILS_CK(cudaMemcpyAsync(h->h_status + 3, h->dstatus2, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  ILS_CK(cudaMemcpyAsync(h->h_status + 1, h->gs_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  ILS_CK(mixed_setup(n, nullptr, h->G2, h->opt.precision, h->L32, h->P32, h->G2_32, h->Bt32, h->Bt16,
+                     reinterpret_cast<float*>(h->Dinv), s));
+  ILS_CK(mark(h, 5));
+  return ILS_OK;
+}
+
+// FP64 Cholesky of Abar1 into L (status in h_status[0]), for handles whose setup factored
+// it in FP32 only.  Synchronizes the handle's stream.
+ils_status factor_f64_now(ils_handle h) {
+  cudaStream_t s = h->stream;
+  const int64_t n = h->n;
   ILS_CK(cudaMemcpyAsync(h->L, h->G1, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, s));
   ILS_CK(cudaMemsetAsync(h->dstatus, 0, sizeof(int32_t), s));
-  {
-    double* mats[2] = {h->L, h->L};
-    double* invd[2] = {h->inv_diag, h->inv_diag};
-    ILS_CK(cholesky_f64_batch(n, 1, mats, invd, h->stash64, h->dstatus, s));
-  }
-  ILS_CK(mark(h, 4));
+  double* mats[2] = {h->L, h->L};
+  double* invd[2] = {h->inv_diag, h->inv_diag};
+  ILS_CK(cholesky_f64_batch(n, 1, mats, invd, h->stash64, h->dstatus, s));
   ILS_CK(cudaMemcpyAsync(h->h_status, h->dstatus, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-  ILS_CK(cudaStreamWaitEvent(s, h->ev_g2, 0));
-  ILS_CK(cudaMemcpyAsync(h->h_status + 1, h->gs_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-  ILS_CK(mixed_setup(n, h->L, h->G2, h->opt.precision, h->L32, h->P32, h->G2_32, h->Bt32, h->Bt16,
-                     reinterpret_cast<float*>(h->Dinv), s));
-  ILS_CK(cudaStreamWaitEvent(s, h->ev_join, 0));
-  ILS_CK(mark(h, 5));
+  ILS_CK(cudaStreamSynchronize(s));
+  h->l64_valid = true;
   return ILS_OK;
 }
 
@@ -470,7 +486,19 @@ ils_status compute_setup_overlap(ils_handle h) {
 ils_status setup_finish(ils_handle h) {
   ILS_CK(cudaStreamSynchronize(h->stream));
   if (h->sparse && h->h_status[2] != 0) return (ils_status)h->h_status[2];
-  if (h->overlap && h->h_status[3] != 0 && h->h_status[1] == 0 && *h->h_status == 0) {
+  h->h_status[1] = h->opt.gram == ILS_GRAM_SPLIT ? h->h_status[1] : 0;
+  if (h->h_status[1] != 0) return h->h_status[1] == 2 ? ILS_ERR_NONFINITE : ILS_ERR_TIMEOUT;
+  if (h->overlap && h->h_status[6] != 0) {
+    // An FP32 pivot of Abar1 failed: the FP64 factorization decides, and the FP32
+    // products are formed again from it.
+    const ils_status fs = factor_f64_now(h);
+    if (fs != ILS_OK) return fs;
+    if (*h->h_status != 0) return (ils_status)*h->h_status;
+    ILS_CK(mixed_setup(h->n, h->L, h->G2, h->opt.precision, h->L32, h->P32, h->G2_32, h->Bt32, h->Bt16,
+                       reinterpret_cast<float*>(h->Dinv), h->stream));
+  }
+  if (*h->h_status != 0) return (ils_status)*h->h_status;
+  if (h->overlap && h->h_status[3] != 0) {
     // The FP32 test of H failed: the FP64 factorization decides (in the P buffer).
     cudaStream_t s = h->stream;
     const int64_t n = h->n;
@@ -483,9 +511,6 @@ ils_status setup_finish(ils_handle h) {
     ILS_CK(cudaStreamSynchronize(s));
     if (h->h_status[3] != 0) return (ils_status)h->h_status[3];
   }
-  h->h_status[1] = h->opt.gram == ILS_GRAM_SPLIT ? h->h_status[1] : 0;
-  if (h->h_status[1] != 0) return h->h_status[1] == 2 ? ILS_ERR_NONFINITE : ILS_ERR_TIMEOUT;
-  if (*h->h_status != 0) return (ils_status)*h->h_status;
   return ILS_OK;
 }
 
@@ -504,7 +529,7 @@ void free_handle(ils_handle h) {
     cudaStreamSynchronize(h->s_aux);
     cudaStreamDestroy(h->s_aux);
   }
-  for (cudaEvent_t e : {h->ev_start, h->ev_g1, h->ev_g2, h->ev_join})
+  for (cudaEvent_t e : {h->ev_start, h->ev_g2})
     if (e) cudaEventDestroy(e);
   if (h->h_st) cudaFreeHost(h->h_st);
   for (cudaEvent_t e : h->ev)
@@ -943,7 +968,7 @@ ils_status create_handle(ils_handle* out, int64_t m, int64_t n, int64_t p, int64
   carve(h, real, work);
   if (h->overlap) {
     bool ok = cudaStreamCreateWithFlags(&h->s_aux, cudaStreamNonBlocking) == cudaSuccess;
-    for (cudaEvent_t* e : {&h->ev_start, &h->ev_g1, &h->ev_g2, &h->ev_join})
+    for (cudaEvent_t* e : {&h->ev_start, &h->ev_g2})
       ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
       cudaGetLastError();
@@ -1124,7 +1149,14 @@ ils_status ils_get_matrix(ils_handle h, int which, double* dst, int64_t ldd, ils
   switch (which) {
     case 0: src = h->G1; break;
     case 1: src = h->G2; break;
-    case 2: ILS_CK(copy_lower_zero_upper_f64(n, h->L, dst, ldd, s)); return ILS_OK;
+    case 2:
+      if (!h->l64_valid) {
+        ILS_CK(cudaStreamSynchronize(s));
+        const ils_status fs = factor_f64_now(h);
+        if (fs != ILS_OK) return fs;
+      }
+      ILS_CK(copy_lower_zero_upper_f64(n, h->L, dst, ldd, s));
+      return ILS_OK;
     case 3: src = h->P; break;
     case 4: {
       transpose_kernel<<<256, 256, 0, s>>>(n, h->Bt, dst, ldd);

@@ -60,8 +60,13 @@ cudaError_t gemv_cols_f64(int64_t n, int64_t k, const double* M, int64_t ldm, co
 cudaError_t cholesky_f64_batch(int64_t n, int count, double* const* mats, double* const* inv_diag, double* stash,
                                int32_t* status, cudaStream_t s);
 
-// The same factorization of one FP32 matrix (an SPD test).
+// Cholesky of one FP32 matrix in place (lower triangle; inv_diag gets 1 / L_ii).  Up to
+// n = 1600 it is one data-driven launch and `stash` (1024 floats) holds its panel flags;
+// larger n takes the panel launches above.  Status as above.
 cudaError_t cholesky_f32(int64_t n, float* M, float* inv_diag, float* stash, int32_t* status, cudaStream_t s);
+// Two FP32 matrices in one launch, each with its own status word (stash: 2048 floats).
+cudaError_t cholesky_f32_pair(int64_t n, float* M0, float* M1, float* inv0, float* inv1, float* stash,
+                              int32_t* status0, int32_t* status1, cudaStream_t s);
 
 // X := L^{-1} X (lower = forward) then, if both, X := L^{-T} X.  X n x k (ldx).
 cudaError_t trsm_lower_f64(int64_t n, int64_t k, const double* L, double* X, int64_t ldx,
@@ -190,11 +195,14 @@ cudaError_t tune_sweeps(int64_t n, int precision, const float* P32, const float*
 // 1 and the tuned shape of (n, k, operator type) if the autotuner has one, else 0.
 int ils_tuned_shape_impl(int64_t n, int64_t k, int bf16, int* warps, int* blocks);
 // L32/P32/G2_32/Bt32 are n x n FP32 buffers, Bt16 an n x n BF16 buffer (BF16 mode only).
-// G2 == nullptr (matrix-free route) forms only P32.
+// L is the FP64 Cholesky factor, rounded into L32; L == nullptr means L32 already holds an
+// FP32 factor (lower triangle, zeros above).  G2 == nullptr (matrix-free route) forms only P32.
 cudaError_t mixed_setup(int64_t n, const double* L, const double* G2, int precision, float* L32, float* P32,
                         float* G2_32, float* Bt32, void* Bt16, float* Dinv32, cudaStream_t s);
 cudaError_t mixed_correct(const MixedArgs& a, int precision, cudaStream_t s);
 cudaError_t convert_f64_to_f32(int64_t count, const double* src, float* dst, cudaStream_t s);
+// L32 := lower triangle of the n x n FP64 matrix M rounded to FP32, zeros above.
+cudaError_t lower_to_f32(int64_t n, const double* M, float* L32, cudaStream_t s);
 cudaError_t mixed_correct_mf(const MixedArgs& a, int precision, int64_t q, const void* Aq_lo, void* part, double* v,
                              double* d64, float* t32, cudaStream_t s);
 

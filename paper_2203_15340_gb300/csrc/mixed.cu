@@ -294,6 +294,12 @@ __global__ void lower_f32_kernel(int64_t n, const double* __restrict__ L, float*
   }
 }
 
+cudaError_t lower_to_f32(int64_t n, const double* M, float* L32, cudaStream_t s) {
+  lower_f32_kernel<<<grid_small(n * n), 256, 0, s>>>(n, M, L32);
+  note_launch();
+  return cudaGetLastError();
+}
+
 // Diagonal 32 x 32 blocks of X := their inverses (Dinv, stored block after block).
 __global__ void place_diag_f32_kernel(int64_t n, const float* __restrict__ Dinv, float* __restrict__ X) {
   const int64_t i0 = (int64_t)blockIdx.x * 32;
@@ -342,16 +348,18 @@ cudaError_t convert_f64_to_f32(int64_t count, const double* src, float* dst, cud
 cudaError_t mixed_setup(int64_t n, const double* L, const double* G2, int precision, float* L32, float* P32,
                         float* G2_32, float* Bt32, void* Bt16, float* Dinv32, cudaStream_t s) {
   const int64_t nn = n * n;
-  lower_f32_kernel<<<grid_small(nn), 256, 0, s>>>(n, L, L32);
-  note_launch();
+  if (L) {
+    lower_f32_kernel<<<grid_small(nn), 256, 0, s>>>(n, L, L32);
+    note_launch();
+  }
   if (G2) {
     f64_to_f32_kernel<<<grid_small(nn), 256, 0, s>>>(nn, G2, G2_32);
     note_launch();
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  // P = L^{-T} L^{-1} in FP32 from the FP64 Cholesky factor: L32 := L^{-1} (P32 serves as
-  // the merge scratch), then P = (L^{-1})^T L^{-1}.
+  // P = L^{-T} L^{-1} in FP32 from the Cholesky factor: L32 := L^{-1} (P32 serves as the
+  // merge scratch), then P = (L^{-1})^T L^{-1}.
   if ((e = tri_inverse_f32(n, L32, P32, Dinv32, s)) != cudaSuccess) return e;
   GemmF32 gp{n, n, n, n, n, n, 0, 0, 0, L32, L32, P32, 1.f, 0.f};
   if ((e = gemm_f32(true, false, gp, 1, s)) != cudaSuccess) return e;

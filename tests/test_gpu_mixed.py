@@ -108,3 +108,59 @@ def test_mixed_setup_rejects_indefinite_h(ils, prec):
     with pytest.raises(ils.ILSError) as e:
         ils.Solver(colmajor(bad.A), bad.p, ils.options(precision=prec))
     assert e.value.code == ils.ILS_ERR_NOT_SPD
+
+
+def test_mixed_setup_falls_back_to_fp64_factor(ils):
+    """A column of A_1 scaled by 2^64 puts an entry of A_1^T A_1 beyond the FP32 range, so the
+    FP32 Cholesky of A_1^T A_1 (and the FP32 test of H) fail although both matrices are SPD:
+    the setup must take the FP64 factorization and succeed, with L the FP64 Cholesky factor."""
+    import torch
+    inst = W.dense_gaussian(300, 240, 40, 0.3, 11)
+    A = inst.A.copy()
+    A[: inst.p, 0] *= 2.0 ** 64
+    G1 = A[: inst.p].T @ A[: inst.p]
+    assert G1[0, 0] > np.finfo(np.float32).max and O.is_spd(O.normal_matrix(A, inst.p))
+    s = ils.Solver(colmajor(A), inst.p, ils.options(precision=ils.ILS_FP32_REFINE))
+    out = torch.zeros((inst.n, inst.n), dtype=torch.float64, device="cuda")
+    s.get_matrix(ils.MAT_CHOL, out)
+    torch.cuda.synchronize()
+    L = to_np_colmajor(out)
+    Lx = np.linalg.cholesky(G1)
+    assert np.max(np.abs(L - Lx) / np.abs(np.diag(Lx))[None, :]) <= 1e-12
+    x = vec(np.zeros(inst.n))
+    info = s.solve(vec(inst.b), x, tol=1e-12, allow=(ils.ILS_OK, ils.ILS_ERR_NO_CONVERGENCE))
+    torch.cuda.synchronize()
+    print("fallback solve", info.status, info.refinements, info.relres,
+          relerr(x.cpu().numpy(), O.qr_cholesky_solve(A, inst.b, inst.p)))
+    s.close()
+
+
+def test_mixed_get_matrix_forms_fp64_factor_on_demand(ils):
+    """The mixed setup factors A_1^T A_1 in FP32; asking for L still returns the FP64 factor."""
+    import torch
+    inst = W.config1()
+    s = ils.Solver(colmajor(inst.A), inst.p, ils.options(precision=ils.ILS_BF16_REFINE))
+    out = torch.zeros((inst.n, inst.n), dtype=torch.float64, device="cuda")
+    s.get_matrix(ils.MAT_CHOL, out)
+    torch.cuda.synchronize()
+    A1 = inst.A[: inst.p]
+    Lx = np.linalg.cholesky(A1.T @ A1)
+    assert np.max(np.abs(to_np_colmajor(out) - Lx)) <= 1e-10 * np.max(np.abs(Lx))
+    x = vec(np.zeros(inst.n))
+    info = s.solve(vec(inst.b), x, tol=1e-12)
+    torch.cuda.synchronize()
+    assert info.status == ils.ILS_OK
+    assert relerr(x.cpu().numpy(), O.qr_cholesky_solve(inst.A, inst.b, inst.p)) <= 1e-10
+    s.close()
+
+
+@pytest.mark.parametrize("n", [1, 5, 31, 32, 33, 64, 97, 700])
+def test_mixed_sizes_around_panel_edges(ils, n):
+    """The FP32 factorization of A_1^T A_1 runs in 32-column panels: sizes below, at and past
+    a panel edge (and a size with many panels) must all refine to FP64 accuracy."""
+    inst = W.dense_gaussian(max(4 * n, 8), max(n, 2), n, 0.3, 100 + n)
+    xs = O.qr_cholesky_solve(inst.A, inst.b, inst.p)
+    x, info = run(ils, inst, ils.ILS_FP32_REFINE, tol=1e-12)
+    assert info.status == ils.ILS_OK
+    assert relerr(x, xs) <= 1e-10
+    assert info.refinements <= 6
