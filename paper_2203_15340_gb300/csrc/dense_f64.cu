@@ -789,6 +789,17 @@ __global__ void __launch_bounds__(32 * kIterWarps) sp_iter_kernel(SpIterArgs a) 
   __threadfence();
   __shared__ int32_t newly_done[kMaxRhsPerPass];
   __shared__ int all_done;
+  // ||r_k||^2 per column: every thread of the last CTA adds a strided share of the per-CTA
+  // partials (a serial sum would chain gridDim.x dependent FP64 additions).
+  __shared__ double rr_w[kIterWarps][KR];
+#pragma unroll
+  for (int c = 0; c < KR; ++c) {
+    double v = 0.0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) v += __ldcg(&a.partials[(int64_t)b * k + c]);
+    v = warp_sum(v);
+    if (lane == 0) rr_w[w][c] = v;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
     int all = 1;
     const int64_t it = st->iters;
@@ -796,7 +807,7 @@ __global__ void __launch_bounds__(32 * kIterWarps) sp_iter_kernel(SpIterArgs a) 
       newly_done[c] = 0;
       if (done_c[c]) continue;
       double rr = 0.0;
-      for (unsigned b = 0; b < gridDim.x; ++b) rr += __ldcg(&a.partials[(int64_t)b * k + c]);
+      for (int ww = 0; ww < kIterWarps; ++ww) rr += rr_w[ww][c];
       const bool finite = isfinite(rr);
       const bool conv = finite && rr <= a.tol2 * a.bnorm2[c];
       if (!finite || conv || it >= st->max_outer) {
@@ -841,33 +852,29 @@ __global__ void copy_final_kernel(int64_t n, int64_t k, const double* X0, const 
 }
 
 // ---------------------------------------------------------------------------------------
-// FP32 Cholesky in one launch (n <= kDfMaxN): left-looking and data-driven.  CTA j owns
-// the 32-column panel j and keeps rows 32j..n-1 of it in shared memory.  It applies the
-// update from each earlier panel k as soon as panel k's flag is set (A_j -= L_k L_k(j)^T,
-// where L_k(j) is the panel's 32 x 32 block in the rows of block j), then factors its
-// diagonal block in one warp (lane = row, the block in registers, each pivot's column
-// broadcast by shuffles), solves its rows below by forward substitution against the
-// factored block, stores the panel and sets its own flag.  The only serial chain left is
-// one panel update, one 32 x 32 factorization and one solve per panel; the n^3/3
-// multiply-adds are spread over the panels' CTAs, and no launch boundary separates the
-// panels.  Panel k's flag is set only after its stores are fenced; a waiting CTA reads
-// the panel through L2.  Every wait is bounded: past the limit the CTA records TIMEOUT,
-// raises the abort word (which releases every other waiter) and returns.
+// FP32 Cholesky in one launch (n <= kDfMaxN): left-looking, data-driven at the grain of
+// 32-row chunks.  CTA j owns the 32-column panel j; its warp w owns the chunks t = w,
+// w + 8, ... (rows 32j + 32t .. + 31, one row per lane, the 32 columns in registers).
+// A chunk is updated by every earlier panel k as soon as the chunk of panel k covering
+// the same rows is published (A_j(t) -= L_k(t') L_k(j)^T, where L_k(j) is panel k's
+// 32 x 32 block in the rows of block j, staged in shared memory by warp 0, which reads it
+// anyway for chunk 0), then solved against the factored diagonal block and published
+// under its own flag.  Warp 0 factors the diagonal block (lane = row, each pivot's column
+// broadcast by shuffles) as soon as chunk 0 is updated.  The next panel's diagonal block
+// therefore waits only for one chunk of this panel, not for the whole panel, and the
+// n^3/3 multiply-adds are spread over the CTAs' warps without any launch boundary.
+// A chunk's flag is set only after its stores are fenced; waiting warps read it through
+// L2.  Every wait is bounded: past the limit the warp records TIMEOUT, raises the abort
+// word (which releases every other waiter) and returns.
 // ---------------------------------------------------------------------------------------
-constexpr int kDfThreads = 256;
-constexpr int kDfPad = 33;  // row stride of the panel in shared memory (conflict-free rows and columns)
-constexpr int64_t kDfMaxN = 1600;
-
-// Panel floats, rounded up to a multiple of 4 so that the 32 x 32 blocks after it are
-// 16-byte aligned for their float4 reads.
-__host__ __device__ __forceinline__ size_t df_panel_floats(int64_t n) {
-  return ((size_t)(n < 32 ? 32 : n) * kDfPad + 3) & ~(size_t)3;
-}
+constexpr int kDfWarps = 8;
+constexpr int kDfThreads = 32 * kDfWarps;
+constexpr int64_t kDfMaxN = 768;  // the staged 32 x 32 blocks of all earlier panels fit in shared memory
 
 struct DfArgs {
   float* M[2];
   float* inv_diag[2];
-  uint32_t* flags[2];  // per panel: 1 once stored; flags[i][npanels] is the abort word
+  uint32_t* flags[2];  // flags[i][k * npanels + t]: chunk t of panel k stored; [npanels^2]: abort
   int32_t* status[2];
   int64_t n;
 };
@@ -877,26 +884,45 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
 __device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint32_t ld_acquire_smem(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(smem_addr(p)) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_smem(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"(smem_addr(p)), "r"(v) : "memory");
+}
 
-// Thread 0 waits for flag == 1; false (for the whole CTA) on abort or after about 1 s.
-__device__ bool df_wait(const uint32_t* flag, uint32_t* abort_word, int32_t* status) {
-  __shared__ int ok;
-  if (threadIdx.x == 0) {
-    int res = 1;
+// One warp waits until *flag != 0 (global when `global`, else this CTA's shared memory).
+// Returns false on abort or after about 1 s (then TIMEOUT is recorded and abort raised).
+__device__ __forceinline__ bool df_wait_warp(const uint32_t* flag, bool global, uint32_t* abort_word,
+                                             int32_t* status) {
+  int res = 1;
+  if ((threadIdx.x & 31) == 0) {
     uint64_t t0 = 0;
     for (uint32_t spin = 0;; ++spin) {
-      if (ld_acquire_u32(flag) != 0u) break;
-      if (ld_acquire_u32(abort_word) != 0u) {
-        res = 0;
+      // Relaxed polls; the fence after a poll that sees the flag makes it an acquire.
+      if ((global ? ld_relaxed_u32(flag) : ld_acquire_smem(flag)) != 0u) {
+        if (global) asm volatile("fence.acq_rel.gpu;" ::: "memory");
         break;
       }
-      if ((spin & 31u) == 0u) {
+      if ((spin & 15u) == 15u) {
+        if (ld_acquire_u32(abort_word) != 0u) {
+          res = 0;
+          break;
+        }
         uint64_t t;
         asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-        if (spin == 0u) {
+        if (t0 == 0) {
           t0 = t;
         } else if (t - t0 > 1000000000ull) {
           atomicCAS(status, 0, (int32_t)ILS_ERR_TIMEOUT);
@@ -905,12 +931,12 @@ __device__ bool df_wait(const uint32_t* flag, uint32_t* abort_word, int32_t* sta
           break;
         }
       }
-      __nanosleep(64);
+      if (spin >= 64u) __nanosleep(32);
     }
-    ok = res;
   }
-  __syncthreads();
-  return ok != 0;
+  res = __shfl_sync(0xffffffffu, res, 0);
+  __syncwarp();
+  return res != 0;
 }
 
 __global__ void __launch_bounds__(kDfThreads)
@@ -921,125 +947,135 @@ chol_dataflow_f32_kernel(DfArgs a) {
   uint32_t* flags = a.flags[mat];
   int32_t* status = a.status[mat];
   const int64_t n = a.n;
-  const int npanels = (int)((n + 31) / 32);
-  uint32_t* abort_word = flags + npanels;
+  const int np = (int)((n + 31) / 32);
+  uint32_t* abort_word = flags + (size_t)np * np;
   const int j = blockIdx.x;
   const int64_t c0 = 32 * (int64_t)j;
   const int nb = (int)(n - c0 < 32 ? n - c0 : 32);
-  const int rows = (int)(n - c0);
-  const int rows_sm = rows < 32 ? 32 : rows;
-  float* P = df_smem;                                           // rows_sm x kDfPad
-  float* W = P + df_panel_floats(n);                            // [kk][c]: L(c0 + c, 32k + kk)
-  float* LT = W + 1024;                                         // [c][d] = L11(d, c)
-  __shared__ float rinv[32];
-  const int tid = threadIdx.x;
-
-  // Own panel: lower entries of the diagonal block and every row below; the columns past
-  // a ragged last panel and the rows past n act as an identity block.
-  for (int e = tid; e < 32 * rows_sm; e += kDfThreads) {
-    const int c = e / rows_sm, r = e - c * rows_sm;
-    float v;
-    if (c < nb && r < rows) v = (r >= 32 || r >= c) ? L[(c0 + r) + (c0 + c) * n] : 0.f;
-    else v = (r == c) ? 1.f : 0.f;
-    P[r * kDfPad + c] = v;
-  }
+  const int nchunks = (int)((n - c0 + 31) / 32);
+  float* W = df_smem;                     // [k][kk][c] = L(c0 + c, 32k + kk)
+  float* LT = W + (size_t)np * 1024;      // [c][d] = L11(d, c)
+  float* rinv = LT + 1024;                // 1 / L11(c, c)
+  uint32_t* wready = reinterpret_cast<uint32_t*>(rinv + 32);  // [k]: W block k staged
+  uint32_t* l11_ready = wready + np;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i <= np; i += kDfThreads) wready[i] = 0u;
   __syncthreads();
 
-  // Updates from the earlier panels, in order of completion.
-  for (int k = 0; k < j; ++k) {
-    if (!df_wait(flags + k, abort_word, status)) return;
-    const float* Lk = L + 32 * (int64_t)k * n;
-    for (int e = tid; e < 1024; e += kDfThreads) {
-      const int c = e & 31, kk = e >> 5;
-      W[e] = c < nb ? __ldcg(Lk + (c0 + c) + kk * n) : 0.f;
+  for (int t = w; t < nchunks; t += kDfWarps) {
+    const int64_t r = c0 + 32 * (int64_t)t + lane;  // this lane's row
+    const bool live = r < n;
+    float acc[32];
+    if (t == 0) {
+      // Lower part of the diagonal block; past a ragged end it acts as an identity block.
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        acc[c] = (c < nb && lane < nb) ? (lane >= c ? L[r + (c0 + c) * n] : 0.f) : (lane == c ? 1.f : 0.f);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 32; ++c) acc[c] = live ? L[r + (c0 + c) * n] : 0.f;
     }
-    __syncthreads();
-    for (int r = tid; r < rows; r += kDfThreads) {
+    // Updates from the earlier panels, each once its chunk over these rows is stored.
+    for (int k = 0; k < j; ++k) {
+      if (!df_wait_warp(flags + (size_t)k * np + (j - k + t), true, abort_word, status)) return;
+      const float* Lk = L + 32 * (int64_t)k * n;
       float lk[32];
 #pragma unroll
-      for (int kk = 0; kk < 32; ++kk) lk[kk] = __ldcg(Lk + (c0 + r) + kk * n);
-      float acc[32];
+      for (int kk = 0; kk < 32; ++kk) lk[kk] = live ? __ldcg(Lk + r + kk * n) : 0.f;
+      float* Wk = W + (size_t)k * 1024;
+      if (t == 0) {
+        // These rows are panel k's block in the rows of block j: stage it for the other warps.
 #pragma unroll
-      for (int c = 0; c < 32; ++c) acc[c] = P[r * kDfPad + c];
+        for (int kk = 0; kk < 32; ++kk) Wk[kk * 32 + lane] = lk[kk];
+        __syncwarp();
+        if (lane == 0) st_release_smem(wready + k, 1u);
+        __syncwarp();
+      } else if (!df_wait_warp(wready + k, false, abort_word, status)) {
+        return;
+      }
 #pragma unroll
       for (int kk = 0; kk < 32; ++kk) {
-        const float4* w4 = reinterpret_cast<const float4*>(W + kk * 32);
+        const float4* w4 = reinterpret_cast<const float4*>(Wk + kk * 32);
 #pragma unroll
         for (int c4 = 0; c4 < 8; ++c4) {
-          const float4 w = w4[c4];
-          acc[4 * c4 + 0] = fmaf(-lk[kk], w.x, acc[4 * c4 + 0]);
-          acc[4 * c4 + 1] = fmaf(-lk[kk], w.y, acc[4 * c4 + 1]);
-          acc[4 * c4 + 2] = fmaf(-lk[kk], w.z, acc[4 * c4 + 2]);
-          acc[4 * c4 + 3] = fmaf(-lk[kk], w.w, acc[4 * c4 + 3]);
+          const float4 v = w4[c4];
+          acc[4 * c4 + 0] = fmaf(-lk[kk], v.x, acc[4 * c4 + 0]);
+          acc[4 * c4 + 1] = fmaf(-lk[kk], v.y, acc[4 * c4 + 1]);
+          acc[4 * c4 + 2] = fmaf(-lk[kk], v.z, acc[4 * c4 + 2]);
+          acc[4 * c4 + 3] = fmaf(-lk[kk], v.w, acc[4 * c4 + 3]);
         }
       }
-#pragma unroll
-      for (int c = 0; c < 32; ++c) P[r * kDfPad + c] = acc[c];
     }
-    __syncthreads();
-  }
-
-  // Diagonal block: warp 0, lane i holds row i.  Pivot c: l_cc = sqrt(d), l_ic = a_ic / l_cc,
-  // then a_ij -= l_ic l_jc for j > c (row i's lane receives l_jc from lane j).
-  if (tid < 32) {
-    const int lane = tid;
-    float v[32];
+    if (t == 0) {
+      // Diagonal block, lane i = row i.  Pivot c: every lane posts a_ic to a shared column
+      // buffer; with d = a_cc and rs = 1/sqrt(d): l_cc = d rs, l_ic = a_ic rs, and
+      // a_ij -= (a_ic rs^2) a_jc for j > c, a_jc read back from the buffer (4 at a time).
+      float* colbuf = LT;  // the factor's column buffer until the factor is written there
 #pragma unroll
-    for (int c = 0; c < 32; ++c) v[c] = P[lane * kDfPad + c];
+      for (int c = 0; c < 32; ++c) {
+        colbuf[(c & 1) * 32 + lane] = acc[c];
+        __syncwarp();
+        float d = colbuf[(c & 1) * 32 + c];
+        const int code = pivot_code(d);
+        if (code != 0) {
+          if (lane == 0) set_status(status, code);
+          d = 1.f;
+        }
+        const float rs = rsqrtf(d);
+        const float ti = lane > c ? acc[c] * (rs * rs) : 0.f;
+        acc[c] = lane > c ? acc[c] * rs : (lane == c ? d * rs : 0.f);
+        if (lane == 0) rinv[c] = rs;
+        const float4* col4 = reinterpret_cast<const float4*>(colbuf + (c & 1) * 32);
 #pragma unroll
-    for (int c = 0; c < 32; ++c) {
-      float d = __shfl_sync(0xffffffffu, v[c], c);
-      const int code = pivot_code(d);
-      if (code != 0) {
-        if (lane == 0) set_status(status, code);
-        d = 1.f;
+        for (int q = (c + 1) / 4; q < 8; ++q) {
+          const float4 v = col4[q];
+          if (4 * q + 0 > c) acc[4 * q + 0] = fmaf(-ti, v.x, acc[4 * q + 0]);
+          if (4 * q + 1 > c) acc[4 * q + 1] = fmaf(-ti, v.y, acc[4 * q + 1]);
+          if (4 * q + 2 > c) acc[4 * q + 2] = fmaf(-ti, v.z, acc[4 * q + 2]);
+          if (4 * q + 3 > c) acc[4 * q + 3] = fmaf(-ti, v.w, acc[4 * q + 3]);
+        }
       }
-      const float rs = rsqrtf(d);
-      const float lc = lane > c ? v[c] * rs : (lane == c ? d * rs : 0.f);
-      v[c] = lc;
-      if (lane == 0) rinv[c] = rs;
+      __syncwarp();
 #pragma unroll
-      for (int jj = c + 1; jj < 32; ++jj) v[jj] = fmaf(-lc, __shfl_sync(0xffffffffu, lc, jj), v[jj]);
-    }
+      for (int c = 0; c < 32; ++c) LT[c * 32 + lane] = lane >= c ? acc[c] : 0.f;
+      __syncwarp();
+      if (lane == 0) st_release_smem(l11_ready, 1u);
 #pragma unroll
-    for (int c = 0; c < 32; ++c) {
-      const float l = lane >= c ? v[c] : 0.f;
-      P[lane * kDfPad + c] = l;
-      LT[c * 32 + lane] = l;
+      for (int c = 0; c < 32; ++c)
+        if (c < nb && lane < nb && lane >= c) L[r + (c0 + c) * n] = acc[c];
+      if (lane < nb) a.inv_diag[mat][c0 + lane] = rinv[lane];
+    } else {
+      // Rows below the diagonal block: x = a L11^{-T} by forward substitution.
+      if (!df_wait_warp(l11_ready, false, abort_word, status)) return;
+      const float4* lt4 = reinterpret_cast<const float4*>(LT);
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        acc[c] *= rinv[c];
+#pragma unroll
+        for (int q = (c + 1) / 4; q < 8; ++q) {
+          const float4 v = lt4[c * 8 + q];
+          if (4 * q + 0 > c) acc[4 * q + 0] = fmaf(-acc[c], v.x, acc[4 * q + 0]);
+          if (4 * q + 1 > c) acc[4 * q + 1] = fmaf(-acc[c], v.y, acc[4 * q + 1]);
+          if (4 * q + 2 > c) acc[4 * q + 2] = fmaf(-acc[c], v.z, acc[4 * q + 2]);
+          if (4 * q + 3 > c) acc[4 * q + 3] = fmaf(-acc[c], v.w, acc[4 * q + 3]);
+        }
+      }
+      if (live) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) L[r + (c0 + c) * n] = acc[c];
+      }
+      // The warp barrier orders every lane's stores before lane 0's release.
+      __syncwarp();
+      if (lane == 0) st_release_u32(flags + (size_t)j * np + t, 1u);
     }
   }
-  __syncthreads();
-
-  // Rows below the diagonal block: x = a L11^{-T} by forward substitution.
-  for (int r = 32 + tid; r < rows; r += kDfThreads) {
-    float x[32];
-#pragma unroll
-    for (int c = 0; c < 32; ++c) x[c] = P[r * kDfPad + c];
-#pragma unroll
-    for (int c = 0; c < 32; ++c) {
-      x[c] *= rinv[c];
-#pragma unroll
-      for (int d = c + 1; d < 32; ++d) x[d] = fmaf(-x[c], LT[c * 32 + d], x[d]);
-    }
-#pragma unroll
-    for (int c = 0; c < 32; ++c) P[r * kDfPad + c] = x[c];
-  }
-  __syncthreads();
-
-  // Store the panel (lower part of the diagonal block), fence, then raise the flag.
-  for (int e = tid; e < nb * rows; e += kDfThreads) {
-    const int c = e / rows, r = e - c * rows;
-    if (r >= c) L[(c0 + r) + (c0 + c) * n] = P[r * kDfPad + c];
-  }
-  if (tid < nb) a.inv_diag[mat][c0 + tid] = rinv[tid];
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) st_release_u32(flags + j, 1u);
 }
 
 size_t df_smem_bytes(int64_t n) {
-  return sizeof(float) * (df_panel_floats(n) + 2048);
+  const size_t np = (size_t)((n + 31) / 32);
+  return sizeof(float) * (np * 1024 + 1024 + 32) + sizeof(uint32_t) * (np + 1);
 }
+
 
 int grid_for(int64_t total, int threads) {
   int64_t b = (total + threads - 1) / threads;
@@ -1229,7 +1265,7 @@ cudaError_t cholesky_f64_batch(int64_t n, int count, double* const* mats, double
 
 cudaError_t cholesky_f32_df(int64_t n, int count, float* const* mats, float* const* inv_diag, float* stash,
                             int32_t* const* status, cudaStream_t s) {
-  // The stash holds the panel flags: npanels + 1 words per matrix, 1024 words apart.
+  // The stash holds the chunk flags: npanels^2 + 1 words per matrix, 1024 words apart.
   const int npanels = (int)((n + 31) / 32);
   DfArgs a;
   for (int i = 0; i < 2; ++i) {
@@ -1240,7 +1276,7 @@ cudaError_t cholesky_f32_df(int64_t n, int count, float* const* mats, float* con
     a.status[i] = status[src];
   }
   a.n = n;
-  cudaError_t e = cudaMemsetAsync(stash, 0, sizeof(uint32_t) * (1024 * (count - 1) + npanels + 1), s);
+  cudaError_t e = cudaMemsetAsync(stash, 0, sizeof(uint32_t) * (1024 * (count - 1) + npanels * npanels + 1), s);
   if (e != cudaSuccess) return e;
   static const cudaError_t attr_err = cudaFuncSetAttribute(
       chol_dataflow_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)df_smem_bytes(kDfMaxN));

@@ -14,15 +14,17 @@
 //      2^{-beta S - 1} times the column scale.
 //   3. For every ordered pair (t, u) with t + u <= S + 1 the tensor cores form
 //      D_t^T D_u with FP32 accumulation.  All partial sums are integers below
-//      K_chunk 2^(2 beta) < 2^24, so the FP32 accumulation is exact.
+//      K_chunk 2^(2 beta) < 2^24, so the FP32 accumulation is exact.  On the diagonal
+//      tiles of the Gram, D_u^T D_t is the transpose of D_t^T D_u and is not formed.
 //   4. The epilogue scales each exact product by 2^{e_i + e_j - beta (t + u)} (an exponent
 //      shift on the bit pattern) and a reduction adds the products of a tile in FP64 in a
 //      fixed order (deterministic).
 //
 // The tcgen05 kernel is warp-specialised: warp 0 issues TMA loads of 128 x 64 BF16 tiles
-// (128B swizzle) into a 6-stage shared-memory ring, warp 1 issues 128x128x16 MMAs into a
-// TMEM accumulator, warps 2-5 drain TMEM.  Every mbarrier wait is bounded; on a timeout
-// the kernel records an error flag, stops issuing work, frees its TMEM and returns.
+// (128B swizzle) of up to four digit slices into a 3-stage shared-memory ring, warp 1
+// issues 128x128x16 MMAs of up to four digit pairs into four TMEM accumulators, warps 2-5
+// drain TMEM.  Every mbarrier wait is bounded; on a timeout the kernel records an error
+// flag, stops issuing work, frees its TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -40,12 +42,11 @@ constexpr int kSlices = 10;     // 50 bits below each column's scale
 constexpr int kBM = 128;        // output tile rows (columns of D_t)
 constexpr int kBN = 128;        // output tile cols (columns of D_u)
 constexpr int kBK = 64;         // K per stage: 64 BF16 = one 128-byte swizzle row
-constexpr int kStages = 4;
-constexpr int kGroup = 2;       // digit pairs (t, u), (t, u + 1) per CTA: one A slice, two B slices
+constexpr int kStages = 3;
 constexpr int kKChunk = 16384;  // K rows per work item: 16384 * 32^2 = 2^24 (exact FP32 sums)
 constexpr int kThreads = 192;   // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
 constexpr uint32_t kTileBytes = kBM * kBK * 2;  // 16 KB per operand tile
-constexpr uint32_t kStageBytes = (1 + kGroup) * kTileBytes;
+constexpr uint32_t kStageBytes = 4 * kTileBytes;  // up to four digit tiles per stage
 constexpr uint64_t kWaitNs = 4000000000ull;  // bound on any mbarrier wait (4 s)
 
 // ------------------------------- device helpers ----------------------------------------
@@ -149,59 +150,127 @@ struct SplitParams {
   int n;            // Gram order
   int K;            // rows of A (reduction length)
   int n_tiles;      // ceil(n / 128)
-  int n_pairs;      // ordered slice pairs (t, u) with t + u <= S + 1
-  int n_groups;     // work groups of up to kGroup pairs sharing t
   int n_kchunks;
   const int* exps;  // per-column exponents e_j (device)
-  double* partial;  // [item][128][128] FP64 scaled products
+  double* partial;  // [tile][product slot][K chunk][128][128] FP64 scaled products
   int32_t* err;     // device error flag
 };
 
-// Work item -> (K chunk, upper tile pair, digit group).  A group is (t, u0) and, when
-// u0 + 1 <= S + 1 - t, also (t, u0 + 1): the CTA loads D_t once for both products.  Items
-// of one K chunk run together.  Partial-product slots stay per digit pair, with the items
-// of a tile contiguous for the reduction: slot = (tile * n_pairs + pair) * n_kchunks + kc.
-__device__ __forceinline__ void decode_item(int item, const SplitParams& P, int* bi, int* bj, int* t, int* u0,
-                                            int* nb, int* kc, int* tile_out) {
+// Work groups.  The digit pairs (t, u) with t + u <= S + 1 are taken in 2 x 2 blocks
+// (a, b): t in {2a-1, 2a}, u in {2b-1, 2b}, a + b <= S/2 + 1.  A CTA loads the (up to)
+// four digit tiles of its block once per K step and forms the block's (up to) four
+// products into four TMEM accumulators: one tile load per product instead of 1.5 for
+// pairs sharing only the A tile.  On a diagonal tile pair (bi = bj) the product (u, t) is
+// the transpose of (t, u), so only blocks with a <= b are formed, and inside a block
+// with a = b only t <= u (its two tiles serve as both operands); the reduction adds each
+// cross product twice, once transposed.
+constexpr int kHalf = kSlices / 2;
+constexpr int kMaxTiles = 4;
+constexpr int kMaxProd = 4;
+static_assert(kSlices % 2 == 0, "digit blocks pair the slices");
+
+struct GroupDesc {
+  int ntiles, nprod;
+  int digit[kMaxTiles];  // 1-based digit of each loaded tile
+  int side[kMaxTiles];   // 0: columns of tile bi, 1: columns of tile bj
+  int ia[kMaxProd], ib[kMaxProd];  // loaded-tile index of each product's A and B operand
+  int t[kMaxProd], u[kMaxProd];
+  int slot0;             // product slot (within the tile) of the group's first product
+};
+
+__host__ __device__ inline bool block_valid(bool diag, int a, int b) {
+  return a + b <= kHalf + 1 && (!diag || a <= b);
+}
+
+// Group g of a diagonal (diag) or off-diagonal tile pair, in row-major order of (a, b).
+__host__ __device__ inline void block_desc(bool diag, int g, GroupDesc& d) {
+  int slot = 0;
+  for (int a = 1; a <= kHalf; ++a) {
+    for (int b = 1; b <= kHalf; ++b) {
+      if (!block_valid(diag, a, b)) continue;
+      GroupDesc cur = {};
+      cur.slot0 = slot;
+      const bool same = diag && a == b;
+      cur.ntiles = same ? 2 : 4;
+      cur.digit[0] = 2 * a - 1;
+      cur.digit[1] = 2 * a;
+      cur.side[0] = cur.side[1] = 0;
+      if (!same) {
+        cur.digit[2] = 2 * b - 1;
+        cur.digit[3] = 2 * b;
+        cur.side[2] = cur.side[3] = 1;
+      }
+      cur.nprod = 0;
+      for (int i = 0; i < 2; ++i) {
+        for (int j = 0; j < 2; ++j) {
+          const int t = 2 * a - 1 + i, u = 2 * b - 1 + j;
+          if (t + u > kSlices + 1 || (same && t > u)) continue;
+          cur.ia[cur.nprod] = i;
+          cur.ib[cur.nprod] = same ? j : 2 + j;
+          cur.t[cur.nprod] = t;
+          cur.u[cur.nprod] = u;
+          ++cur.nprod;
+        }
+      }
+      if (g == 0) {
+        d = cur;
+        return;
+      }
+      --g;
+      slot += cur.nprod;
+    }
+  }
+}
+
+__host__ __device__ inline int num_blocks(bool diag) {
+  int c = 0;
+  for (int a = 1; a <= kHalf; ++a)
+    for (int b = 1; b <= kHalf; ++b) c += block_valid(diag, a, b) ? 1 : 0;
+  return c;
+}
+
+// Product slots per tile (the off-diagonal count, every ordered pair: the larger one).
+__host__ __device__ inline int slots_per_tile() {
+  int c = 0;
+  for (int t = 1; t <= kSlices; ++t) c += kSlices + 1 - t;
+  return c;
+}
+
+// Work item -> (K chunk, upper tile pair, group).  Items of one K chunk run together;
+// inside a chunk the upper tile pairs go in row-major order (bi <= bj), each with its
+// groups.
+__device__ __forceinline__ void decode_item(int item, const SplitParams& P, int* bi, int* bj, int* g, int* kc,
+                                            int* tile_out) {
+  const int nd = num_blocks(true), no = num_blocks(false);
   const int n_upper = P.n_tiles * (P.n_tiles + 1) / 2;
-  const int per_chunk = n_upper * P.n_groups;
+  const int per_chunk = P.n_tiles * nd + (n_upper - P.n_tiles) * no;
   *kc = item / per_chunk;
-  const int rest = item % per_chunk;
-  int tile = rest / P.n_groups;
-  const int group = rest % P.n_groups;
-  *tile_out = tile;
-  // upper tile pairs (bi <= bj) in row-major order
-  int r = 0;
-  while (tile >= P.n_tiles - r) {
-    tile -= P.n_tiles - r;
+  int rest = item % per_chunk;
+  int r = 0, tile = 0;
+  for (;;) {
+    const int row_items = nd + (P.n_tiles - r - 1) * no;
+    if (rest < row_items) break;
+    rest -= row_items;
+    tile += P.n_tiles - r;
     ++r;
   }
   *bi = r;
-  *bj = r + tile;
-  // groups enumerated by t, then u0 = 1, 1 + kGroup, ...
-  int g = group, tt = 1;
-  while (g >= (kSlices + 1 - tt + kGroup - 1) / kGroup) {
-    g -= (kSlices + 1 - tt + kGroup - 1) / kGroup;
-    ++tt;
+  if (rest < nd) {
+    *bj = r;
+    *g = rest;
+  } else {
+    rest -= nd;
+    *bj = r + 1 + rest / no;
+    *g = rest % no;
   }
-  *t = tt;
-  *u0 = 1 + kGroup * g;
-  const int left = kSlices + 1 - tt - (*u0 - 1);
-  *nb = left < kGroup ? left : kGroup;
-}
-
-// Index of the ordered digit pair (t, u) among those with t + u <= S + 1 (by t, then u).
-__device__ __forceinline__ int pair_index(int t, int u) {
-  int p = 0;
-  for (int tt = 1; tt < t; ++tt) p += kSlices + 1 - tt;
-  return p + (u - 1);
+  *tile_out = tile + (*bj - r);
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
 gram_split_mma_kernel(const __grid_constant__ CUtensorMap tmap, SplitParams P) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* tiles = smem;  // kStages x (A tile, kGroup B tiles)
+  uint8_t* tiles = smem;  // kStages x (up to kMaxTiles digit tiles)
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
   uint64_t* empty = full + kStages;
   uint64_t* acc_full = empty + kStages;
@@ -209,8 +278,10 @@ gram_split_mma_kernel(const __grid_constant__ CUtensorMap tmap, SplitParams P) {
   __shared__ int s_abort;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int bi, bj, t, u0, nb, kc, tile;
-  decode_item(blockIdx.x, P, &bi, &bj, &t, &u0, &nb, &kc, &tile);
+  int bi, bj, g, kc, tile;
+  decode_item(blockIdx.x, P, &bi, &bj, &g, &kc, &tile);
+  GroupDesc gd;
+  block_desc(bi == bj, g, gd);
   const int k_begin = kc * kKChunk;
   const int k_end = min(P.K, k_begin + kKChunk);
   const int nk = (k_end - k_begin + kBK - 1) / kBK;
@@ -226,7 +297,7 @@ gram_split_mma_kernel(const __grid_constant__ CUtensorMap tmap, SplitParams P) {
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(kGroup * kBN));
+                 "r"(kMaxProd * kBN));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -237,6 +308,13 @@ gram_split_mma_kernel(const __grid_constant__ CUtensorMap tmap, SplitParams P) {
   int issued = 0;  // stages handed to TMA by the producer
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer ----------------
+    int trow[kMaxTiles], tdig[kMaxTiles];
+#pragma unroll
+    for (int i = 0; i < kMaxTiles; ++i) {
+      trow[i] = (gd.side[i] ? bj : bi) * kBM;
+      tdig[i] = gd.digit[i] - 1;
+    }
+    const int ntiles = gd.ntiles;
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % kStages;
       const uint32_t ph = (uint32_t)(kb / kStages) & 1u;
@@ -246,39 +324,44 @@ gram_split_mma_kernel(const __grid_constant__ CUtensorMap tmap, SplitParams P) {
         break;
       }
       if (*((volatile int*)&s_abort)) break;
-      uint8_t* a_tile = tiles + (size_t)s * kStageBytes;
-      mbar_expect_tx(&full[s], (uint32_t)(1 + nb) * kTileBytes);
+      uint8_t* stage = tiles + (size_t)s * kStageBytes;
+      mbar_expect_tx(&full[s], (uint32_t)ntiles * kTileBytes);
       const int k = k_begin + kb * kBK;
-      tma_load_3d(a_tile, &tmap, &full[s], k, bi * kBM, t - 1);
-      for (int g = 0; g < nb; ++g)
-        tma_load_3d(a_tile + (1 + g) * kTileBytes, &tmap, &full[s], k, bj * kBN, u0 + g - 1);
+#pragma unroll
+      for (int i = 0; i < kMaxTiles; ++i)
+        if (i < ntiles) tma_load_3d(stage + i * kTileBytes, &tmap, &full[s], k, trow[i], tdig[i]);
       ++issued;
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer ----------------
-    bool ok = true;
+    uint32_t aoff[kMaxProd], boff[kMaxProd];
+#pragma unroll
+    for (int p = 0; p < kMaxProd; ++p) {
+      aoff[p] = (uint32_t)gd.ia[p] * kTileBytes;
+      boff[p] = (uint32_t)gd.ib[p] * kTileBytes;
+    }
+    const int nprod = gd.nprod;
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % kStages;
       const uint32_t ph = (uint32_t)(kb / kStages) & 1u;
       if (!mbar_wait(&full[s], ph)) {
         atomicExch(P.err, 1);
         s_abort = 1;
-        ok = false;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a_addr = smem_u32(tiles + (size_t)s * kStageBytes);
+      const uint32_t st_addr = smem_u32(tiles + (size_t)s * kStageBytes);
 #pragma unroll
       for (int kk = 0; kk < kBK / 16; ++kk) {
-        for (int g = 0; g < nb; ++g) {  // accumulator g: TMEM columns g * kBN ..
-          const uint32_t b_addr = a_addr + (1 + g) * kTileBytes;
-          mma_bf16(tmem_acc + (uint32_t)(g * kBN), smem_desc_sw128(a_addr + kk * 32),
-                   smem_desc_sw128(b_addr + kk * 32), (kb > 0 || kk > 0) ? 1u : 0u);
+#pragma unroll
+        for (int p = 0; p < kMaxProd; ++p) {  // accumulator p: TMEM columns p * kBN ..
+          if (p < nprod)
+            mma_bf16(tmem_acc + (uint32_t)(p * kBN), smem_desc_sw128(st_addr + aoff[p] + kk * 32),
+                     smem_desc_sw128(st_addr + boff[p] + kk * 32), (kb > 0 || kk > 0) ? 1u : 0u);
         }
       }
       mma_commit(&empty[s]);  // frees the stage once these MMAs have read it
     }
-    (void)ok;
     mma_commit(acc_full);  // arrives when every MMA issued above has completed
   } else if (warp >= 2) {
     // ---------------- epilogue: TMEM -> scaled FP64 partial ----------------
@@ -291,19 +374,20 @@ gram_split_mma_kernel(const __grid_constant__ CUtensorMap tmap, SplitParams P) {
       atomicExch(P.err, 1);
     } else if (!*((volatile int*)&s_abort)) {
       const int ei = gi < P.n ? P.exps[gi] : 0;
-      for (int g = 0; g < nb; ++g) {
-        const int u = u0 + g;
-        const int slot = (tile * P.n_pairs + pair_index(t, u)) * P.n_kchunks + kc;
+      const int nslots = slots_per_tile();
+      for (int p = 0; p < gd.nprod; ++p) {
+        const int slot = (tile * nslots + gd.slot0 + p) * P.n_kchunks + kc;
         double* out = P.partial + (size_t)slot * kBM * kBN;  // column-major 128 x 128 tile
+        const int sc_tu = -kBeta * (gd.t[p] + gd.u[p]);
 #pragma unroll 1
         for (int c0 = 0; c0 < kBN; c0 += 32) {
           uint32_t v[32];
-          tmem_ld_32x32b_x32(tmem_acc + ((uint32_t)(q * 32) << 16) + (uint32_t)(g * kBN + c0), v);
+          tmem_ld_32x32b_x32(tmem_acc + ((uint32_t)(q * 32) << 16) + (uint32_t)(p * kBN + c0), v);
 #pragma unroll
           for (int c = 0; c < 32; ++c) {
             const int gj = bj * kBN + c0 + c;
             const int ej = gj < P.n ? P.exps[gj] : 0;
-            out[(size_t)(c0 + c) * kBM + row] = scaled_f32_to_f64(v[c], ei + ej - kBeta * (t + u));
+            out[(size_t)(c0 + c) * kBM + row] = scaled_f32_to_f64(v[c], ei + ej + sc_tu);
           }
         }
       }
@@ -317,7 +401,7 @@ gram_split_mma_kernel(const __grid_constant__ CUtensorMap tmap, SplitParams P) {
   __syncthreads();
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_acc), "r"(kGroup * kBN));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_acc), "r"(kMaxProd * kBN));
   }
 }
 
@@ -436,10 +520,14 @@ exponent_split_kernel(int K, int n, const double* __restrict__ A, int64_t lda, i
   }
 }
 
-// C(i,j) for the upper tiles: sum of the tile's items in a fixed order, mirrored.
+// C(i,j) for the upper tiles: the tile's products in slot order (K chunks inner), added in
+// FP64 in that fixed order, then mirrored.  The loop visits the products in the order of
+// block_desc.  On a diagonal tile each cross product (t != u) is added twice, the second
+// time transposed: it stands for the product (u, t) as well.
 __global__ void split_reduce_kernel(SplitParams P, double* __restrict__ C, int64_t ldc) {
-  const int items_per_tile = P.n_pairs * P.n_kchunks;
+  const int nslots = slots_per_tile();
   const int n_upper = P.n_tiles * (P.n_tiles + 1) / 2;
+  const size_t tile_elems = (size_t)kBM * kBN;
   const int64_t total = (int64_t)n_upper * kBM * kBN;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     int tile = (int)(e / (kBM * kBN));
@@ -453,10 +541,30 @@ __global__ void split_reduce_kernel(SplitParams P, double* __restrict__ C, int64
     }
     const int bi = r, bj = r + tt;
     const int gi = bi * kBM + row, gj = bj * kBN + col;
-    if (gi >= P.n || gj >= P.n || (bi == bj && gi > gj)) continue;
-    const double* base = P.partial + (size_t)tile * items_per_tile * kBM * kBN + local;
+    const bool diag = bi == bj;
+    if (gi >= P.n || gj >= P.n || (diag && gi > gj)) continue;
+    const double* base = P.partial + (size_t)tile * nslots * P.n_kchunks * tile_elems;
+    const int tr = col + row * kBM;  // the transposed element
     double s = 0.0;
-    for (int it = 0; it < items_per_tile; ++it) s += base[(size_t)it * kBM * kBN];
+    int slot = 0;
+    for (int a = 1; a <= kHalf; ++a) {
+      for (int b = 1; b <= kHalf; ++b) {
+        if (!block_valid(diag, a, b)) continue;
+        const bool same = diag && a == b;
+        for (int i = 0; i < 2; ++i) {
+          for (int j = 0; j < 2; ++j) {
+            const int t = 2 * a - 1 + i, u = 2 * b - 1 + j;
+            if (t + u > kSlices + 1 || (same && t > u)) continue;
+            const double* pr = base + (size_t)slot * P.n_kchunks * tile_elems;
+            for (int kc = 0; kc < P.n_kchunks; ++kc) {
+              s += pr[kc * tile_elems + local];
+              if (diag && t != u) s += pr[kc * tile_elems + tr];
+            }
+            ++slot;
+          }
+        }
+      }
+    }
     C[gi + (int64_t)gj * ldc] = s;
     C[gj + (int64_t)gi * ldc] = s;
   }
@@ -477,18 +585,6 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
   return fn;
 }
 
-int num_pairs() {
-  int c = 0;
-  for (int t = 1; t <= kSlices; ++t) c += kSlices + 1 - t;
-  return c;
-}
-
-int num_groups() {
-  int c = 0;
-  for (int t = 1; t <= kSlices; ++t) c += (kSlices + 1 - t + kGroup - 1) / kGroup;
-  return c;
-}
-
 size_t smem_bytes() { return 1024 + (size_t)kStages * kStageBytes + (2 * kStages + 2) * sizeof(uint64_t) + 16; }
 
 }  // namespace
@@ -500,7 +596,7 @@ GramSplitWork gram_split_work(int64_t K, int64_t n) {
   const int64_t n_upper = n_tiles * (n_tiles + 1) / 2;
   const int64_t n_kchunks = std::max<int64_t>(1, (K + kKChunk - 1) / kKChunk);
   w.slice_elems = (size_t)kSlices * (size_t)n * (size_t)ldk;
-  w.partial_elems = (size_t)n_upper * num_pairs() * n_kchunks * kBM * kBN;
+  w.partial_elems = (size_t)n_upper * slots_per_tile() * n_kchunks * kBM * kBN;
   w.exps = (size_t)n;
   return w;
 }
@@ -547,14 +643,12 @@ cudaError_t gram_split_tc(int64_t K, int64_t n, const double* A, int64_t lda, do
   P.n = (int)n;
   P.K = (int)K;
   P.n_tiles = (int)((n + kBM - 1) / kBM);
-  P.n_pairs = num_pairs();
-  P.n_groups = num_groups();
   P.n_kchunks = (int)std::max<int64_t>(1, (K + kKChunk - 1) / kKChunk);
   P.exps = exps;
   P.partial = partial;
   P.err = err;
   const int n_upper = P.n_tiles * (P.n_tiles + 1) / 2;
-  const int items = n_upper * P.n_groups * P.n_kchunks;
+  const int items = (P.n_tiles * num_blocks(true) + (n_upper - P.n_tiles) * num_blocks(false)) * P.n_kchunks;
   const size_t smem = smem_bytes();
   e = cudaFuncSetAttribute(gram_split_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

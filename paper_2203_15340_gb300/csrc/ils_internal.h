@@ -61,7 +61,7 @@ cudaError_t cholesky_f64_batch(int64_t n, int count, double* const* mats, double
                                int32_t* status, cudaStream_t s);
 
 // Cholesky of one FP32 matrix in place (lower triangle; inv_diag gets 1 / L_ii).  Up to
-// n = 1600 it is one data-driven launch and `stash` (1024 floats) holds its panel flags;
+// n = 768 it is one data-driven launch and `stash` (1024 floats) holds its chunk flags;
 // larger n takes the panel launches above.  Status as above.
 cudaError_t cholesky_f32(int64_t n, float* M, float* inv_diag, float* stash, int32_t* status, cudaStream_t s);
 // Two FP32 matrices in one launch, each with its own status word (stash: 2048 floats).
