@@ -78,8 +78,8 @@ struct ils_handle_s {
   int32_t* sp_err = nullptr;
   double* stash64 = nullptr;   // 2 x 1024: the Cholesky panels' diagonal-block stash
   // Overlapped mixed setup (single handles, split Grams): A_2^T A_2 runs on a second stream
-  // beside A_1^T A_1; Abar1 and H are then factored in FP32 in one launch (a failed FP32
-  // pivot is settled by the FP64 factorization).
+  // beside A_1^T A_1; Abar1 is then inverted and H tested in FP32 in one launch (a failed
+  // FP32 pivot is settled by the FP64 factorization).
   bool overlap = false;
   bool l64_valid = true;  // L holds the FP64 factor of the current Abar1 (else formed on demand)
   cudaStream_t s_aux = nullptr;
@@ -88,6 +88,7 @@ struct ils_handle_s {
   double* gs_partial2 = nullptr;
   int* gs_exps2 = nullptr;
   float* H32 = nullptr;
+  float* gj = nullptr;  // exchange buffers of the explicit FP32 inverse
   float* stash32 = nullptr;
   int32_t* dstatus2 = nullptr;
   SolveState* st = nullptr;
@@ -240,6 +241,7 @@ void carve(ils_handle h, Carver& c, size_t work_elems) {
       h->gs_exps2 = c.take<int>((size_t)h->n);
       h->H32 = c.take<float>((size_t)h->n * (size_t)h->n);
       h->stash32 = c.take<float>(2 * 1024);  // panel flags of the FP32 factorizations
+      h->gj = c.take<float>(spd_inverse_scratch_floats(h->n));
       h->dstatus2 = c.take<int32_t>(1);
     }
   }
@@ -427,12 +429,13 @@ ils_status compute_products(ils_handle h) {
 }
 
 // Mixed precision with split Grams on one handle: the second stream computes Abar2 while
-// the handle's stream computes Abar1; then one launch factors Abar1 (Alg. 1 step 2) and
-// H = Abar1 - Abar2 (the SPD test of condition (1.3)) together, and P and B follow.
-// Both are factored in FP32: the correction sweeps only need P to FP32 accuracy (the FP64
-// residuals of the refinement supply the rest), and a factor rounded from FP64 would be no
-// better once inverted in FP32.  An FP32 pivot that fails sends setup_finish to the FP64
-// factorization of that matrix, which then decides.
+// the handle's stream computes Abar1; then one launch forms P = Abar1^{-1} (Alg. 1 step 2)
+// by block Gauss-Jordan elimination and, in lockstep, tests H = Abar1 - Abar2 for
+// condition (1.3) the same way, and B follows.  Both run in FP32: the correction sweeps
+// only need P to FP32 accuracy (the FP64 residuals of the refinement supply the rest).  A
+// pivot that fails in FP32 sends setup_finish to the FP64 factorization of that matrix,
+// which then decides.  Where the inverse's tiles do not fit one cooperative wave, both
+// matrices are factored by Cholesky in FP32 instead and P is formed from the factor.
 ils_status compute_setup_overlap(ils_handle h) {
   cudaStream_t s = h->stream, a = h->s_aux;
   const int64_t m = h->m, n = h->n, p = h->p, q = h->q;
@@ -449,19 +452,32 @@ ils_status compute_setup_overlap(ils_handle h) {
   ILS_CK(gram_split_tc(q, n, h->A + p, m, h->G2, n, h->gs_slices2, h->gs_partial2, h->gs_exps2, h->gs_err, a));
   ILS_CK(cudaEventRecord(h->ev_g2, a));
   ILS_CK(mark(h, 2));
-  ILS_CK(lower_to_f32(n, h->G1, h->L32, s));
+  ILS_CK(convert_f64_to_f32(n * n, h->G1, h->L32, s));  // Abar1, both triangles
   ILS_CK(cudaStreamWaitEvent(s, h->ev_g2, 0));
   ILS_CK(mark(h, 3));
   ILS_CK(axpby_mat_f64(n, 1.0, h->G1, -1.0, h->G2, h->H, s));
   ILS_CK(convert_f64_to_f32(n * n, h->H, h->H32, s));
-  ILS_CK(cholesky_f32_pair(n, h->L32, h->H32, reinterpret_cast<float*>(h->inv_diag),
-                           reinterpret_cast<float*>(h->inv_diag + n), h->stash32, h->dstatus, h->dstatus2, s));
+  const float* mats[2] = {h->L32, h->H32};
+  float* outs[2] = {h->P32, nullptr};
+  int32_t* sts[2] = {h->dstatus, h->dstatus2};
+  const cudaError_t gj = spd_inverse_f32(n, 2, mats, outs, h->gj, sts, s);
+  const bool inverted = gj == cudaSuccess;
+  if (!inverted) {
+    if (gj != cudaErrorNotSupported) ILS_CK(gj);
+    cudaGetLastError();
+    ILS_CK(lower_to_f32(n, h->G1, h->L32, s));
+    ILS_CK(cholesky_f32_pair(n, h->L32, h->H32, reinterpret_cast<float*>(h->inv_diag),
+                             reinterpret_cast<float*>(h->inv_diag + n), h->stash32, h->dstatus, h->dstatus2, s));
+  }
   ILS_CK(mark(h, 4));
   ILS_CK(cudaMemcpyAsync(h->h_status + 6, h->dstatus, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   ILS_CK(cudaMemcpyAsync(h->h_status + 3, h->dstatus2, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   ILS_CK(cudaMemcpyAsync(h->h_status + 1, h->gs_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-  ILS_CK(mixed_setup(n, nullptr, h->G2, h->opt.precision, h->L32, h->P32, h->G2_32, h->Bt32, h->Bt16,
-                     reinterpret_cast<float*>(h->Dinv), s));
+  if (inverted)
+    ILS_CK(mixed_setup_b(n, h->G2, h->opt.precision, h->P32, h->G2_32, h->Bt32, h->Bt16, s));
+  else
+    ILS_CK(mixed_setup(n, nullptr, h->G2, h->opt.precision, h->L32, h->P32, h->G2_32, h->Bt32, h->Bt16,
+                       reinterpret_cast<float*>(h->Dinv), s));
   ILS_CK(mark(h, 5));
   return ILS_OK;
 }

@@ -199,7 +199,22 @@ int ils_tuned_shape_impl(int64_t n, int64_t k, int bf16, int* warps, int* blocks
 // FP32 factor (lower triangle, zeros above).  G2 == nullptr (matrix-free route) forms only P32.
 cudaError_t mixed_setup(int64_t n, const double* L, const double* G2, int precision, float* L32, float* P32,
                         float* G2_32, float* Bt32, void* Bt16, float* Dinv32, cudaStream_t s);
+// B^T (FP32, and BF16 in BF16 mode) from P32 and Abar2: G2 (FP64) is rounded into G2_32
+// first unless it is nullptr (then G2_32 already holds it).
+cudaError_t mixed_setup_b(int64_t n, const double* G2, int precision, const float* P32, float* G2_32, float* Bt32,
+                          void* Bt16, cudaStream_t s);
 cudaError_t mixed_correct(const MixedArgs& a, int precision, cudaStream_t s);
+
+// ---- explicit SPD inverse (spd_gj.cu) ------------------------------------------------------
+// P[i] := A[i]^{-1} for count (1 or 2) n x n FP32 symmetric matrices (both triangles
+// stored, column-major) by block Gauss-Jordan elimination in one cooperative launch;
+// P[i] == nullptr tests A[i] only.  status[i] gets NOT_SPD / NONFINITE on a failed pivot
+// (the FP32 counterpart of the Cholesky pivot test) and TIMEOUT if a grid barrier wait ran
+// out.  `scratch` holds spd_inverse_scratch_floats(n) floats.  cudaErrorNotSupported when
+// the tiles do not fit one cooperative wave (the caller takes another route).
+size_t spd_inverse_scratch_floats(int64_t n);
+cudaError_t spd_inverse_f32(int64_t n, int count, const float* const* A, float* const* P, float* scratch,
+                            int32_t* const* status, cudaStream_t s);
 cudaError_t convert_f64_to_f32(int64_t count, const double* src, float* dst, cudaStream_t s);
 // L32 := lower triangle of the n x n FP64 matrix M rounded to FP32, zeros above.
 cudaError_t lower_to_f32(int64_t n, const double* M, float* L32, cudaStream_t s);

@@ -364,6 +364,18 @@ cudaError_t mixed_setup(int64_t n, const double* L, const double* G2, int precis
   GemmF32 gp{n, n, n, n, n, n, 0, 0, 0, L32, L32, P32, 1.f, 0.f};
   if ((e = gemm_f32(true, false, gp, 1, s)) != cudaSuccess) return e;
   if (!G2) return cudaSuccess;  // matrix-free route: B is never formed
+  return mixed_setup_b(n, nullptr, precision, P32, G2_32, Bt32, Bt16, s);
+}
+
+cudaError_t mixed_setup_b(int64_t n, const double* G2, int precision, const float* P32, float* G2_32, float* Bt32,
+                          void* Bt16, cudaStream_t s) {
+  const int64_t nn = n * n;
+  cudaError_t e;
+  if (G2) {
+    f64_to_f32_kernel<<<grid_small(nn), 256, 0, s>>>(nn, G2, G2_32);
+    note_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   // B^T = Abar2 P (both symmetric), so column i of B^T is row i of B = P Abar2.
   GemmF32 gb{n, n, n, n, n, n, 0, 0, 0, G2_32, P32, Bt32, 1.f, 0.f};
   if ((e = gemm_f32(false, false, gb, 1, s)) != cudaSuccess) return e;

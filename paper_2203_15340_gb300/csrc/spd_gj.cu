@@ -1,0 +1,359 @@
+// Explicit inverse of symmetric positive definite matrices by block Gauss-Jordan
+// elimination (the sweep operator), FP32, one cooperative launch.
+//
+// P = Abar1^{-1} of Alg. 1 step 2, formed without a separate triangular factor and
+// inverse.  Sweeping the 32 x 32 pivot block k of a symmetric A (D = A_kk) replaces
+//   A_kk <- -D^{-1},  A_ik <- A_ik D^{-1},  A_kj <- D^{-1} A_kj,  A_ij <- A_ij - A_ik D^{-1} A_kj
+// (i, j != k); after every block has been swept, A holds -A^{-1}.  The pivot blocks D are
+// the Schur complements that a Cholesky factorization meets, so the scalar sweep of D
+// (which yields -D^{-1}) also tests condition (1.3): a pivot that is not positive and
+// finite is reported as NOT_SPD / NONFINITE, like a failed Cholesky pivot.
+//
+// Work split: the lower 32 x 32 tiles of every matrix are spread over the CTAs and stay in
+// their shared memory for the whole launch.  In step k, block column k (old values) and
+// D^{-1} are read from a global exchange buffer; every tile is updated; the owners of
+// block column / row k+1 then post the next block column and the owner of tile (k+1,k+1)
+// sweeps it and posts its D^{-1}; one grid barrier separates the steps.  The exchange
+// buffers alternate between steps, so a step's posts never overwrite what a slower CTA
+// of the step before still reads.  The grid barrier waits are bounded: past about 1 s the
+// CTA records TIMEOUT, raises the abort word and every waiter returns.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "ils_internal.h"
+
+namespace ils {
+namespace {
+
+constexpr int kGjThreads = 256;
+constexpr int kGjMaxOwn = 4;  // tiles a CTA keeps in shared memory
+constexpr int kGjPad = 33;    // row stride of a tile in shared memory
+constexpr int kGjTile = 32 * kGjPad;
+
+struct GjArgs {
+  const float* A[2];  // n x n column-major, symmetric, both triangles stored
+  float* P[2];        // the inverse, full (nullptr: status only)
+  float* C[2];        // 2 x (nb * 32 x 32): block column k, row-major per row
+  float* D[2];        // 2 x (32 x 32): D^{-1} of pivot block k, row-major
+  int32_t* status[2];
+  uint32_t* sync;  // [0] arrivals, [1] generation, [2] abort
+  int64_t n;
+  int nb;     // 32-row blocks
+  int count;  // matrices (1 or 2)
+  int tiles;  // lower tiles per matrix
+};
+
+__device__ __forceinline__ uint32_t gj_ld_acquire(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint32_t gj_ld_relaxed(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid-wide barrier of a cooperative launch (generation counting).  False on abort or
+// after about 1 s of waiting, which is recorded as TIMEOUT and raises the abort word.
+__device__ bool gj_barrier(uint32_t* sync, int32_t* status) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int res = 1;
+    const uint32_t gen = gj_ld_relaxed(sync + 1);
+    __threadfence();
+    if (atomicAdd(sync, 1u) == gridDim.x - 1) {
+      sync[0] = 0u;
+      __threadfence();
+      atomicAdd(sync + 1, 1u);
+    } else {
+      uint64_t t0 = 0;
+      for (uint32_t spin = 0;; ++spin) {
+        if (gj_ld_acquire(sync + 1) != gen) break;
+        if ((spin & 15u) == 15u) {
+          if (gj_ld_acquire(sync + 2) != 0u) {
+            res = 0;
+            break;
+          }
+          uint64_t t;
+          asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+          if (t0 == 0) {
+            t0 = t;
+          } else if (t - t0 > 1000000000ull) {
+            atomicCAS(status, 0, (int32_t)ILS_ERR_TIMEOUT);
+            atomicExch(sync + 2, 1u);
+            res = 0;
+            break;
+          }
+        }
+        if (spin >= 64u) __nanosleep(32);
+      }
+    }
+    ok = res;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// Lower tile t of an nb-block matrix, row-major over the lower triangle: (i, j), i >= j.
+__device__ __forceinline__ void gj_tile_ij(int t, int* i, int* j) {
+  int r = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+  while (r * (r + 1) / 2 > t) --r;
+  while ((r + 1) * (r + 2) / 2 <= t) ++r;
+  *i = r;
+  *j = t - r * (r + 1) / 2;
+}
+
+__device__ __forceinline__ int gj_pivot_code(float d) {
+  if (!isfinite(d)) return ILS_ERR_NONFINITE;
+  if (!(d > 0.f)) return ILS_ERR_NOT_SPD;
+  return 0;
+}
+
+// Warp 0: scalar sweeps of all 32 pivots of the tile T (in place), leaving -D^{-1}; lane =
+// row, the row in registers, the pivot row broadcast through `prow` (2 x 32 floats).  A
+// failed pivot is recorded and replaced by 1 so that the launch runs to its end.
+__device__ void gj_sweep_pivot(float* T, float* prow, int32_t* status) {
+  const int lane = threadIdx.x & 31;
+  float v[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) v[c] = T[lane * kGjPad + c];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) {
+    float* pr = prow + (c & 1) * 32;
+    if (lane == c) {
+#pragma unroll
+      for (int q = 0; q < 32; ++q) pr[q] = v[q];
+    }
+    __syncwarp();
+    float d = pr[c];
+    const int code = gj_pivot_code(d);
+    if (code != 0) {
+      if (lane == 0) atomicCAS(status, 0, code);
+      d = 1.f;
+    }
+    const float rd = __frcp_rn(d);
+    if (lane == c) {
+#pragma unroll
+      for (int q = 0; q < 32; ++q) v[q] = q == c ? -rd : v[q] * rd;
+    } else {
+      const float t = v[c] * rd;
+#pragma unroll
+      for (int q = 0; q < 32; ++q) v[q] = q == c ? t : fmaf(-t, pr[q], v[q]);
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int c = 0; c < 32; ++c) T[lane * kGjPad + c] = v[c];
+}
+
+// acc[q] += sum_m L(r, m) R(m, c0 + q) for the thread's outputs r = tid / 8,
+// c0 = 4 (tid % 8), q < 4; with rt, R(c0 + q, m) (the product L R^T).
+__device__ __forceinline__ void gj_mm4(const float* L, const float* R, bool rt, float acc[4]) {
+  const int r = threadIdx.x >> 3, c0 = (threadIdx.x & 7) * 4;
+#pragma unroll 8
+  for (int m = 0; m < 32; ++m) {
+    const float a = L[r * kGjPad + m];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] = fmaf(a, rt ? R[(c0 + q) * kGjPad + m] : R[m * kGjPad + c0 + q], acc[q]);
+  }
+}
+
+// Stage a 32 x 32 row-major global block (16-byte aligned) into a padded shared tile.
+__device__ __forceinline__ void gj_stage(float* dst, const float* src) {
+  for (int e = threadIdx.x; e < 256; e += kGjThreads) {
+    const float4 v = __ldcg(reinterpret_cast<const float4*>(src) + e);
+    const int r = e >> 3, c = (e & 7) * 4;
+    dst[r * kGjPad + c] = v.x;
+    dst[r * kGjPad + c + 1] = v.y;
+    dst[r * kGjPad + c + 2] = v.z;
+    dst[r * kGjPad + c + 3] = v.w;
+  }
+}
+
+// Post sign * (a padded shared tile, or its transpose) as a 32 x 32 row-major global block.
+__device__ __forceinline__ void gj_post(float* dst, const float* T, bool transpose, float sign) {
+  for (int e = threadIdx.x; e < 1024; e += kGjThreads) {
+    const int r = e >> 5, c = e & 31;
+    dst[e] = sign * (transpose ? T[c * kGjPad + r] : T[r * kGjPad + c]);
+  }
+}
+
+// After tile (i, j) of matrix m is final for the steps before k1: post what step k1 needs
+// from it into exchange buffer q.
+__device__ void gj_post_for(const GjArgs& a, int m, int i, int j, int k1, int q, float* T, float* prow) {
+  float* Cq = a.C[m] + (size_t)q * a.nb * 1024;
+  if (i == k1 && j == k1) {
+    if (threadIdx.x < 32) gj_sweep_pivot(T, prow, a.status[m]);  // T := -D^{-1}
+    __syncthreads();
+    gj_post(a.D[m] + q * 1024, T, false, -1.f);
+  } else if (j == k1) {
+    gj_post(Cq + (size_t)i * 1024, T, false, 1.f);  // A(block i, block k1)
+  } else if (i == k1) {
+    gj_post(Cq + (size_t)j * 1024, T, true, 1.f);   // A(block j, block k1) = A(k1, j)^T
+  }
+}
+
+__global__ void __launch_bounds__(kGjThreads) spd_gj_kernel(GjArgs a) {
+  extern __shared__ __align__(16) float gj_smem[];
+  float* own = gj_smem;                 // kGjMaxOwn tiles
+  float* Ci = own + kGjMaxOwn * kGjTile;  // C_k(i)
+  float* Cj = Ci + kGjTile;             // C_k(j)
+  float* Dm = Cj + kGjTile;             // D^{-1}
+  float* X = Dm + kGjTile;              // C_k(i) D^{-1}
+  float* prow = X + kGjTile;            // 2 x 32: pivot rows of the scalar sweeps
+  const int64_t n = a.n;
+  const int total = a.count * a.tiles;
+  const int tid = threadIdx.x;
+  const int r = tid >> 3, c0 = (tid & 7) * 4;
+
+  int om[kGjMaxOwn], oi[kGjMaxOwn], oj[kGjMaxOwn];
+#pragma unroll
+  for (int s = 0; s < kGjMaxOwn; ++s) {
+    const int task = blockIdx.x + s * gridDim.x;
+    om[s] = task < total ? task / a.tiles : -1;
+    if (task < total) gj_tile_ij(task % a.tiles, &oi[s], &oj[s]);
+    else oi[s] = oj[s] = 0;
+  }
+  // Own tiles; indices past n act as an identity block.
+#pragma unroll
+  for (int s = 0; s < kGjMaxOwn; ++s) {
+    if (om[s] < 0) continue;
+    float* T = own + s * kGjTile;
+    const float* A = a.A[om[s]];
+    for (int e = tid; e < 1024; e += kGjThreads) {
+      const int rr = e & 31, cc = e >> 5;
+      const int64_t gi = 32 * (int64_t)oi[s] + rr, gj = 32 * (int64_t)oj[s] + cc;
+      T[rr * kGjPad + cc] = (gi < n && gj < n) ? A[gi + gj * n] : (gi == gj ? 1.f : 0.f);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int s = 0; s < kGjMaxOwn; ++s) {
+    if (om[s] < 0) continue;
+    gj_post_for(a, om[s], oi[s], oj[s], 0, 0, own + s * kGjTile, prow);
+    __syncthreads();
+  }
+
+  for (int k = 0; k < a.nb; ++k) {
+    if (!gj_barrier(a.sync, a.status[0])) return;
+    const int p = k & 1;
+#pragma unroll
+    for (int s = 0; s < kGjMaxOwn; ++s) {
+      if (om[s] < 0) continue;
+      const int m = om[s], i = oi[s], j = oj[s];
+      float* T = own + s * kGjTile;
+      if (!(i == k && j == k)) {  // the pivot tile was swept when it was posted
+        const float* Cp = a.C[m] + (size_t)p * a.nb * 1024;
+        gj_stage(Dm, a.D[m] + p * 1024);
+        if (j != k && i != k) {
+          gj_stage(Ci, Cp + (size_t)i * 1024);
+          gj_stage(Cj, Cp + (size_t)j * 1024);
+        }
+        __syncthreads();
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        if (j == k) {
+          gj_mm4(T, Dm, false, acc);  // A_ik D^{-1}
+        } else if (i == k) {
+          gj_mm4(Dm, T, false, acc);  // D^{-1} A_kj
+        } else {
+          gj_mm4(Ci, Dm, false, acc);  // X = A_ik D^{-1}
+#pragma unroll
+          for (int q = 0; q < 4; ++q) X[r * kGjPad + c0 + q] = acc[q];
+          __syncthreads();
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[q] = 0.f;
+          gj_mm4(X, Cj, true, acc);  // X A_kj with A_kj = C_k(j)^T
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[q] = T[r * kGjPad + c0 + q] - acc[q];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) T[r * kGjPad + c0 + q] = acc[q];
+        __syncthreads();
+      }
+      if (k + 1 < a.nb) {
+        gj_post_for(a, m, i, j, k + 1, p ^ 1, T, prow);
+        __syncthreads();
+      }
+    }
+  }
+  // Every tile now holds -(A^{-1}); write the inverse, both triangles.
+#pragma unroll
+  for (int s = 0; s < kGjMaxOwn; ++s) {
+    if (om[s] < 0 || !a.P[om[s]]) continue;
+    float* P = a.P[om[s]];
+    const float* T = own + s * kGjTile;
+    for (int e = tid; e < 1024; e += kGjThreads) {
+      const int rr = e & 31, cc = e >> 5;
+      const int64_t gi = 32 * (int64_t)oi[s] + rr, gj = 32 * (int64_t)oj[s] + cc;
+      // a diagonal tile writes its lower half twice, so each element has one writer
+      if (gi < n && gj < n && (oi[s] != oj[s] || rr >= cc)) {
+        const float v = -T[rr * kGjPad + cc];
+        P[gi + gj * n] = v;
+        P[gj + gi * n] = v;
+      }
+    }
+  }
+}
+
+size_t gj_smem_bytes() { return sizeof(float) * ((size_t)(kGjMaxOwn + 4) * kGjTile + 64); }
+
+}  // namespace
+
+size_t spd_inverse_scratch_floats(int64_t n) {
+  const size_t nb = (size_t)((n + 31) / 32);
+  return 2 * (2 * nb * 1024 + 2048) + 64;
+}
+
+cudaError_t spd_inverse_f32(int64_t n, int count, const float* const* A, float* const* P, float* scratch,
+                            int32_t* const* status, cudaStream_t s) {
+  if (n <= 0 || count < 1 || count > 2) return cudaErrorInvalidValue;
+  const int nb = (int)((n + 31) / 32);
+  const int tiles = nb * (nb + 1) / 2;
+  const int total = count * tiles;
+  int dev = 0, sms = 0, coop = 0, occ = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, spd_gj_kernel, kGjThreads, gj_smem_bytes());
+  if (e != cudaSuccess) return e;
+  const int64_t grid_max = (int64_t)occ * sms;
+  const int grid = (int)std::min<int64_t>(total, grid_max);
+  if (!coop || grid < 1 || (int64_t)grid * kGjMaxOwn < total) return cudaErrorNotSupported;
+  GjArgs a;
+  const size_t per = 2 * (size_t)nb * 1024 + 2048;
+  for (int i = 0; i < 2; ++i) {
+    const int src = i < count ? i : 0;
+    a.A[i] = A[src];
+    a.P[i] = P[src];
+    a.C[i] = scratch + (size_t)src * per;
+    a.D[i] = a.C[i] + 2 * (size_t)nb * 1024;
+    a.status[i] = status[src];
+  }
+  a.sync = reinterpret_cast<uint32_t*>(scratch + 2 * per);
+  a.n = n;
+  a.nb = nb;
+  a.count = count;
+  a.tiles = tiles;
+  if ((e = cudaMemsetAsync(a.sync, 0, 4 * sizeof(uint32_t), s)) != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid, 1, 1);
+  cfg.blockDim = dim3(kGjThreads, 1, 1);
+  cfg.dynamicSmemBytes = gj_smem_bytes();
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, spd_gj_kernel, a);
+  note_launch();
+  return e;
+}
+
+}  // namespace ils
