@@ -114,8 +114,11 @@ __device__ __forceinline__ int gj_pivot_code(float d) {
 }
 
 // Warp 0: scalar sweeps of all 32 pivots of the tile T (in place), leaving -D^{-1}; lane =
-// row, the row in registers, the pivot row broadcast through `prow` (2 x 32 floats).  A
-// failed pivot is recorded and replaced by 1 so that the launch runs to its end.
+// row, the row in registers.  A sweep keeps the matrix symmetric, so pivot row c is
+// column c: every lane posts its column-c entry to `prow` (2 x 32 floats, alternating)
+// and reads the row back four entries at a time.  Every lane, the pivot lane included,
+// applies the same multiply and multiply-add per entry, so the warp never diverges.  A failed pivot is recorded and replaced by 1 so
+// that the launch runs to its end.
 __device__ void gj_sweep_pivot(float* T, float* prow, int32_t* status) {
   const int lane = threadIdx.x & 31;
   float v[32];
@@ -124,26 +127,33 @@ __device__ void gj_sweep_pivot(float* T, float* prow, int32_t* status) {
 #pragma unroll
   for (int c = 0; c < 32; ++c) {
     float* pr = prow + (c & 1) * 32;
-    if (lane == c) {
-#pragma unroll
-      for (int q = 0; q < 32; ++q) pr[q] = v[q];
-    }
+    pr[lane] = v[c];
     __syncwarp();
-    float d = pr[c];
+    float row[32];
+#pragma unroll
+    for (int q4 = 0; q4 < 8; ++q4) {
+      const float4 w = reinterpret_cast<const float4*>(pr)[q4];
+      row[4 * q4] = w.x;
+      row[4 * q4 + 1] = w.y;
+      row[4 * q4 + 2] = w.z;
+      row[4 * q4 + 3] = w.w;
+    }
+    float d = row[c];
     const int code = gj_pivot_code(d);
     if (code != 0) {
       if (lane == 0) atomicCAS(status, 0, code);
       d = 1.f;
     }
-    const float rd = __frcp_rn(d);
-    if (lane == c) {
+    const float rd = __fdividef(1.f, d);
+    const bool piv = lane == c;
+    // a_iq <- alpha a_iq + beta a_cq: off the pivot alpha = 1, beta = -a_ic / d; the pivot
+    // row becomes a_cq / d (alpha = 0, beta = 1/d; row[q] = a_qc = a_cq by symmetry).
+    const float t = v[c] * rd;
+    const float alpha = piv ? 0.f : 1.f, beta = piv ? rd : -t;
 #pragma unroll
-      for (int q = 0; q < 32; ++q) v[q] = q == c ? -rd : v[q] * rd;
-    } else {
-      const float t = v[c] * rd;
-#pragma unroll
-      for (int q = 0; q < 32; ++q) v[q] = q == c ? t : fmaf(-t, pr[q], v[q]);
-    }
+    for (int q = 0; q < 32; ++q)
+      if (q != c) v[q] = fmaf(beta, row[q], alpha * v[q]);
+    v[c] = piv ? -rd : t;
   }
   __syncwarp();
 #pragma unroll
