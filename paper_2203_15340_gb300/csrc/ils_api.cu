@@ -93,6 +93,7 @@ struct ils_handle_s {
   int32_t* dstatus2 = nullptr;
   SolveState* st = nullptr;
   int32_t* dstatus = nullptr;
+  uint32_t* coop_sync = nullptr;  // grid-barrier words of the one-launch solve
   // pinned host mirrors
   SolveState* h_st = nullptr;
   int32_t* h_status = nullptr;
@@ -195,7 +196,9 @@ void carve(ils_handle h, Carver& c, size_t work_elems) {
   h->col_done = c.take<int32_t>(kMaxRhsPerPass);
   h->col_rr = c.take<double>(kMaxRhsPerPass);
   h->col_iters = c.take<int64_t>(kMaxRhsPerPass);
-  h->partials = c.take<double>((size_t)sp_iterate_blocks(h->n) * kMaxRhsPerPass);
+  // per-CTA partial sums: of the SP step launches, or of the one-launch solve (a CTA per SM)
+  h->partials = c.take<double>(std::max<size_t>((size_t)sp_iterate_blocks(h->n) * kMaxRhsPerPass, 2048));
+  h->coop_sync = c.take<uint32_t>(4);
   h->bhat = c.take<double>(nk);
   h->col_target2 = c.take<double>(kMaxRhsPerPass);
   h->col_inner = c.take<int64_t>(kMaxRhsPerPass);
@@ -657,6 +660,15 @@ ils_status pass_launch(ils_handle h, int64_t count) {
   const int method = h->opt.method;
   const int64_t cap = h->opt.max_outer + 1;
   const int64_t todo = std::min(count, cap - h->pass_launched);
+  if (todo > 0 && h->pass_launched == 0 && h->pass_mixed && !h->mf && !h->sparse && h->pass_k == 1) {
+    // One right-hand side on the explicit route: the whole refinement in one launch.
+    const cudaError_t e = mixed_solve_fused(h->pa, h->pma, h->opt.precision, h->coop_sync, s);
+    if (e == cudaSuccess) {
+      h->pass_launched = cap;
+      return ILS_OK;
+    }
+    if (e != cudaErrorNotSupported) ILS_CK(e);
+  }
   for (int64_t i = 0; i < todo; ++i) {
     if (h->mf) {
       for (int c = 0; c < (int)h->pass_k; ++c)

@@ -130,6 +130,14 @@ struct SpIterArgs {
   SolveState* st;
 };
 cudaError_t sp_iterate_f64(const SpIterArgs& a, cudaStream_t s);
+
+struct MixedArgs;
+// The mixed-precision refinement of one right-hand side (explicit route), every outer step
+// up to st->max_outer, in one cooperative launch (solve_fused.cu); same state and results
+// as sp_iterate_f64 (mode 2) + mixed_correct per step.  `sync`: 4 words.
+// cudaErrorNotSupported when k != 1 or cooperative launch is unavailable.
+cudaError_t mixed_solve_fused(const SpIterArgs& sa, const MixedArgs& ma, int precision, uint32_t* sync,
+                              cudaStream_t s);
 int sp_iterate_blocks(int64_t n);
 
 // Copy the final iterate buffer (chosen on the device) into the user's X.
