@@ -15,10 +15,11 @@
 //   3. For every ordered pair (t, u) with t + u <= S + 1 the tensor cores form
 //      D_t^T D_u with FP32 accumulation.  All partial sums are integers below
 //      K_chunk 2^(2 beta) < 2^24, so the FP32 accumulation is exact.  On the diagonal
-//      tiles of the Gram, D_u^T D_t is the transpose of D_t^T D_u and is not formed.
-//   4. The epilogue scales each exact product by 2^{e_i + e_j - beta (t + u)} (an exponent
-//      shift on the bit pattern) and a reduction adds the products of a tile in FP64 in a
-//      fixed order (deterministic).
+//      tiles of the Gram, D_u^T D_t is the transpose of D_t^T D_u: it is not formed, the
+//      epilogue stores the transpose in its place.
+//   4. The epilogue stores each exact product as it stands (FP32); a reduction scales it by
+//      2^{e_i + e_j - beta (t + u)} into FP64 (an exponent shift on the bit pattern) and
+//      adds the products of a tile in FP64 in a fixed order (deterministic).
 //
 // The tcgen05 kernel is warp-specialised: warp 0 issues TMA loads of 128 x 64 BF16 tiles
 // (128B swizzle) of up to four digit slices into a 3-stage shared-memory ring, warp 1
@@ -152,7 +153,7 @@ struct SplitParams {
   int n_tiles;      // ceil(n / 128)
   int n_kchunks;
   const int* exps;  // per-column exponents e_j (device)
-  double* partial;  // [tile][product slot][K chunk][128][128] FP64 scaled products
+  double* partial;  // [tile][product slot][K chunk][128][128] exact products, FP32 bit patterns
   int32_t* err;     // device error flag
 };
 
@@ -162,8 +163,8 @@ struct SplitParams {
 // products into four TMEM accumulators: one tile load per product instead of 1.5 for
 // pairs sharing only the A tile.  On a diagonal tile pair (bi = bj) the product (u, t) is
 // the transpose of (t, u), so only blocks with a <= b are formed, and inside a block
-// with a = b only t <= u (its two tiles serve as both operands); the reduction adds each
-// cross product twice, once transposed.
+// with a = b only t <= u (its two tiles serve as both operands); the epilogue stores each
+// cross product a second time, transposed, as the product (u, t).
 constexpr int kHalf = kSlices / 2;
 constexpr int kMaxTiles = 4;
 constexpr int kMaxProd = 4;
@@ -229,11 +230,18 @@ __host__ __device__ inline int num_blocks(bool diag) {
   return c;
 }
 
-// Product slots per tile (the off-diagonal count, every ordered pair: the larger one).
+// Product slots per tile: one per ordered pair (t, u) with t + u <= S + 1.
 __host__ __device__ inline int slots_per_tile() {
   int c = 0;
   for (int t = 1; t <= kSlices; ++t) c += kSlices + 1 - t;
   return c;
+}
+
+// Slot of the ordered pair (t, u) (by t, then u).
+__host__ __device__ inline int pair_slot(int t, int u) {
+  int p = 0;
+  for (int tt = 1; tt < t; ++tt) p += kSlices + 1 - tt;
+  return p + (u - 1);
 }
 
 // Work item -> (K chunk, upper tile pair, group).  Items of one K chunk run together;
@@ -364,30 +372,36 @@ gram_split_mma_kernel(const __grid_constant__ CUtensorMap tmap, SplitParams P) {
     }
     mma_commit(acc_full);  // arrives when every MMA issued above has completed
   } else if (warp >= 2) {
-    // ---------------- epilogue: TMEM -> scaled FP64 partial ----------------
+    // ---------------- epilogue: TMEM -> partial products (exact FP32) ----------------
     const bool ok = mbar_wait(acc_full, 0);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const int q = warp & 3;  // this warp may read TMEM lanes 32q .. 32q+31
     const int row = q * 32 + lane;
-    const int gi = bi * kBM + row;
     if (!ok) {
       atomicExch(P.err, 1);
     } else if (!*((volatile int*)&s_abort)) {
-      const int ei = gi < P.n ? P.exps[gi] : 0;
       const int nslots = slots_per_tile();
+      uint32_t* part = reinterpret_cast<uint32_t*>(P.partial);
       for (int p = 0; p < gd.nprod; ++p) {
-        const int slot = (tile * nslots + gd.slot0 + p) * P.n_kchunks + kc;
-        double* out = P.partial + (size_t)slot * kBM * kBN;  // column-major 128 x 128 tile
-        const int sc_tu = -kBeta * (gd.t[p] + gd.u[p]);
+        const int t = gd.t[p], u = gd.u[p];
+        const size_t tile_elems = (size_t)kBM * kBN;
+        // The exact integer products stay FP32 bit patterns; the reduction scales them.
+        uint32_t* out = part + ((size_t)(tile * nslots + pair_slot(t, u)) * P.n_kchunks + kc) * tile_elems;
+        // On a diagonal tile a cross product also stands for (u, t): its transpose goes to
+        // that slot, 32 consecutive entries per thread.
+        uint32_t* out_t = (bi == bj && t != u)
+                              ? part + ((size_t)(tile * nslots + pair_slot(u, t)) * P.n_kchunks + kc) * tile_elems
+                              : nullptr;
 #pragma unroll 1
         for (int c0 = 0; c0 < kBN; c0 += 32) {
           uint32_t v[32];
           tmem_ld_32x32b_x32(tmem_acc + ((uint32_t)(q * 32) << 16) + (uint32_t)(p * kBN + c0), v);
 #pragma unroll
-          for (int c = 0; c < 32; ++c) {
-            const int gj = bj * kBN + c0 + c;
-            const int ej = gj < P.n ? P.exps[gj] : 0;
-            out[(size_t)(c0 + c) * kBM + row] = scaled_f32_to_f64(v[c], ei + ej + sc_tu);
+          for (int c = 0; c < 32; ++c) out[(size_t)(c0 + c) * kBM + row] = v[c];  // column-major 128 x 128
+          if (out_t) {
+            uint4* dst = reinterpret_cast<uint4*>(out_t + (size_t)row * kBM + c0);
+#pragma unroll
+            for (int c = 0; c < 32; c += 4) dst[c / 4] = make_uint4(v[c], v[c + 1], v[c + 2], v[c + 3]);
           }
         }
       }
@@ -520,15 +534,15 @@ exponent_split_kernel(int K, int n, const double* __restrict__ A, int64_t lda, i
   }
 }
 
-// C(i,j) for the upper tiles: the tile's products in slot order (K chunks inner), added in
-// FP64 in that fixed order, then mirrored.  The loop visits the products in the order of
-// block_desc.  On a diagonal tile each cross product (t != u) is added twice, the second
-// time transposed: it stands for the product (u, t) as well.
+// C(i,j) for the upper tiles: each stored product (an exact integer in FP32) is scaled by
+// 2^{e_i + e_j - beta (t + u)} into FP64, and the tile's products are added in slot order
+// (K chunks inner), a fixed order, then mirrored.  Every tile has all its ordered-pair
+// slots (a diagonal tile's transposed slots were written by the epilogue).
 __global__ void split_reduce_kernel(SplitParams P, double* __restrict__ C, int64_t ldc) {
-  const int nslots = slots_per_tile();
+  const int items_per_tile = slots_per_tile() * P.n_kchunks;
   const int n_upper = P.n_tiles * (P.n_tiles + 1) / 2;
-  const size_t tile_elems = (size_t)kBM * kBN;
   const int64_t total = (int64_t)n_upper * kBM * kBN;
+  const uint32_t* part = reinterpret_cast<const uint32_t*>(P.partial);
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     int tile = (int)(e / (kBM * kBN));
     const int local = (int)(e % (kBM * kBN));
@@ -541,28 +555,15 @@ __global__ void split_reduce_kernel(SplitParams P, double* __restrict__ C, int64
     }
     const int bi = r, bj = r + tt;
     const int gi = bi * kBM + row, gj = bj * kBN + col;
-    const bool diag = bi == bj;
-    if (gi >= P.n || gj >= P.n || (diag && gi > gj)) continue;
-    const double* base = P.partial + (size_t)tile * nslots * P.n_kchunks * tile_elems;
-    const int tr = col + row * kBM;  // the transposed element
+    if (gi >= P.n || gj >= P.n || (bi == bj && gi > gj)) continue;
+    const int eij = P.exps[gi] + P.exps[gj];
+    const uint32_t* base = part + (size_t)tile * items_per_tile * kBM * kBN + local;
     double s = 0.0;
-    int slot = 0;
-    for (int a = 1; a <= kHalf; ++a) {
-      for (int b = 1; b <= kHalf; ++b) {
-        if (!block_valid(diag, a, b)) continue;
-        const bool same = diag && a == b;
-        for (int i = 0; i < 2; ++i) {
-          for (int j = 0; j < 2; ++j) {
-            const int t = 2 * a - 1 + i, u = 2 * b - 1 + j;
-            if (t + u > kSlices + 1 || (same && t > u)) continue;
-            const double* pr = base + (size_t)slot * P.n_kchunks * tile_elems;
-            for (int kc = 0; kc < P.n_kchunks; ++kc) {
-              s += pr[kc * tile_elems + local];
-              if (diag && t != u) s += pr[kc * tile_elems + tr];
-            }
-            ++slot;
-          }
-        }
+    int it = 0;
+    for (int t = 1; t <= kSlices; ++t) {
+      for (int u = 1; u <= kSlices + 1 - t; ++u) {
+        const int sc = eij - kBeta * (t + u);
+        for (int kc = 0; kc < P.n_kchunks; ++kc, ++it) s += scaled_f32_to_f64(base[(size_t)it * kBM * kBN], sc);
       }
     }
     C[gi + (int64_t)gj * ldc] = s;

@@ -367,6 +367,65 @@ cudaError_t mixed_setup(int64_t n, const double* L, const double* G2, int precis
   return mixed_setup_b(n, nullptr, precision, P32, G2_32, Bt32, Bt16, s);
 }
 
+// C = A B for n x n column-major FP32 matrices: 32 x 32 output tiles (n = 500 gives 256
+// CTAs, more than the 64 of the 64 x 64 kernel), 2 x 2 outputs per thread, 32-deep K
+// slices in shared memory with the next slice fetched into registers meanwhile.
+__global__ void __launch_bounds__(256) gemm_nn32_f32_kernel(int64_t n, const float* __restrict__ A,
+                                                            const float* __restrict__ B, float* __restrict__ C) {
+  __shared__ __align__(16) float As[32][33];  // [k][m]
+  __shared__ __align__(16) float Bs[32][33];  // [k][n]
+  const int64_t m0 = (int64_t)blockIdx.x * 32, n0 = (int64_t)blockIdx.y * 32;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  float acc[2][2] = {};
+  float ra[4], rb[4];
+  auto fetch = [&](int64_t k0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + 256 * q;
+      const int lo = e & 31, hi = e >> 5;  // A: (m = lo, k = hi); B: (k = lo, n = hi)
+      ra[q] = (m0 + lo < n && k0 + hi < n) ? A[(m0 + lo) + (k0 + hi) * n] : 0.f;
+      rb[q] = (k0 + lo < n && n0 + hi < n) ? B[(k0 + lo) + (n0 + hi) * n] : 0.f;
+    }
+  };
+  auto stash = [&]() {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + 256 * q;
+      const int lo = e & 31, hi = e >> 5;
+      As[hi][lo] = ra[q];
+      Bs[lo][hi] = rb[q];
+    }
+  };
+  fetch(0);
+  stash();
+  __syncthreads();
+  for (int64_t k0 = 0; k0 < n; k0 += 32) {
+    const bool more = k0 + 32 < n;
+    if (more) fetch(k0 + 32);
+#pragma unroll
+    for (int kk = 0; kk < 32; ++kk) {
+      const float a0 = As[kk][2 * ty], a1 = As[kk][2 * ty + 1];
+      const float b0 = Bs[kk][2 * tx], b1 = Bs[kk][2 * tx + 1];
+      acc[0][0] = fmaf(a0, b0, acc[0][0]);
+      acc[0][1] = fmaf(a0, b1, acc[0][1]);
+      acc[1][0] = fmaf(a1, b0, acc[1][0]);
+      acc[1][1] = fmaf(a1, b1, acc[1][1]);
+    }
+    __syncthreads();
+    if (more) {
+      stash();
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int64_t gm = m0 + 2 * ty + i, gn = n0 + 2 * tx + j;
+      if (gm < n && gn < n) C[gm + gn * n] = acc[i][j];
+    }
+}
+
 cudaError_t mixed_setup_b(int64_t n, const double* G2, int precision, const float* P32, float* G2_32, float* Bt32,
                           void* Bt16, cudaStream_t s) {
   const int64_t nn = n * n;
@@ -377,8 +436,10 @@ cudaError_t mixed_setup_b(int64_t n, const double* G2, int precision, const floa
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   // B^T = Abar2 P (both symmetric), so column i of B^T is row i of B = P Abar2.
-  GemmF32 gb{n, n, n, n, n, n, 0, 0, 0, G2_32, P32, Bt32, 1.f, 0.f};
-  if ((e = gemm_f32(false, false, gb, 1, s)) != cudaSuccess) return e;
+  const dim3 grid((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32));
+  gemm_nn32_f32_kernel<<<grid, 256, 0, s>>>(n, G2_32, P32, Bt32);
+  note_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (precision == ILS_BF16_REFINE) {
     f32_to_bf16_kernel<<<grid_small(nn), 256, 0, s>>>(nn, Bt32, static_cast<__nv_bfloat16*>(Bt16));
     note_launch();
