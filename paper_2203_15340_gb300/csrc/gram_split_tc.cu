@@ -535,8 +535,8 @@ exponent_split_kernel(int K, int n, const double* __restrict__ A, int64_t lda, i
 }
 
 // C(i,j) for the upper tiles: each stored product (an exact integer in FP32) is scaled by
-// 2^{e_i + e_j - beta (t + u)} into FP64, and the tile's products are added in slot order
-// (K chunks inner), a fixed order, then mirrored.  Every tile has all its ordered-pair
+// 2^{e_i + e_j - beta (t + u)} into FP64; per K chunk the products of each t are added in
+// u order and those sums in t order (a fixed order), then mirrored.  Every tile has all its ordered-pair
 // slots (a diagonal tile's transposed slots were written by the epilogue).
 __global__ void split_reduce_kernel(SplitParams P, double* __restrict__ C, int64_t ldc) {
   const int items_per_tile = slots_per_tile() * P.n_kchunks;
@@ -558,13 +558,22 @@ __global__ void split_reduce_kernel(SplitParams P, double* __restrict__ C, int64
     if (gi >= P.n || gj >= P.n || (bi == bj && gi > gj)) continue;
     const int eij = P.exps[gi] + P.exps[gj];
     const uint32_t* base = part + (size_t)tile * items_per_tile * kBM * kBN + local;
+    const size_t slot_stride = (size_t)P.n_kchunks * kBM * kBN;
     double s = 0.0;
-    int it = 0;
-    for (int t = 1; t <= kSlices; ++t) {
-      for (int u = 1; u <= kSlices + 1 - t; ++u) {
-        const int sc = eij - kBeta * (t + u);
-        for (int kc = 0; kc < P.n_kchunks; ++kc, ++it) s += scaled_f32_to_f64(base[(size_t)it * kBM * kBN], sc);
+    for (int kc = 0; kc < P.n_kchunks; ++kc) {
+      // every slot's load issued at once; one partial sum per t, added in t order
+      double acc[kSlices];
+      int slot = 0;
+#pragma unroll
+      for (int t = 1; t <= kSlices; ++t) {
+        acc[t - 1] = 0.0;
+#pragma unroll
+        for (int u = 1; u <= kSlices + 1 - t; ++u, ++slot)
+          acc[t - 1] += scaled_f32_to_f64(__ldcg(base + slot * slot_stride + (size_t)kc * kBM * kBN),
+                                          eij - kBeta * (t + u));
       }
+#pragma unroll
+      for (int t = 0; t < kSlices; ++t) s += acc[t];
     }
     C[gi + (int64_t)gj * ldc] = s;
     C[gj + (int64_t)gi * ldc] = s;
