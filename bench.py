@@ -2,15 +2,16 @@
 """ILS solves/s on GB300 for the dense 20000 x 500 instance (p = 16000, q = 4000).
 
 One step = one complete solve of a fresh instance through the C ABI: every setup
-product (ils_refactor: the Gram matrices A_1^T A_1 and A_2^T A_2, the Cholesky
-factorizations of A_1^T A_1 and A^T J A, P = (A_1^T A_1)^{-1} and B = P A_2^T A_2)
-followed by ils_solve (A^T J b and the iterations to the tolerance).  The headline
-path is mixed-precision SP: FP64-accurate Gram matrices from exact BF16 digit
-products on the tcgen05 tensor cores, FP64 Cholesky, FP32 sweeps with P and B, and
-FP64 residual refinement.  Plain FP64 SP (the paper's Alg. 1 in FP64 throughout) is
-timed the same way on the same instance and reported beside it.  The inputs are
-resident in HBM when a step starts; A (80 MB) fits in L2, so L2 is flushed before
-every step (a 256 MiB write, outside the timed events).
+product (ils_refactor: the Gram matrices A_1^T A_1 and A_2^T A_2, P = (A_1^T A_1)^{-1},
+the SPD test of A^T J A, and B = P A_2^T A_2) followed by ils_solve (A^T J b and the
+iterations to the tolerance).  The headline path is mixed-precision SP: FP64-accurate
+Gram matrices from exact BF16 digit products on the tcgen05 tensor cores, P by FP32
+block Gauss-Jordan elimination in one cooperative launch (which also tests A^T J A),
+FP32 sweeps with P and B, and FP64 residual refinement, the whole refinement in one
+cooperative launch.  Plain FP64 SP (the paper's Alg. 1 in FP64 throughout: FP64 Grams,
+FP64 Cholesky, P and B) is timed the same way on the same instance and reported beside
+it.  The inputs are resident in HBM when a step starts; A (80 MB) fits in L2, so L2 is
+flushed before every step (a 256 MiB write, outside the timed events).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun every rank runs its own replica (weak scaling); rank 0 prints one
@@ -34,6 +35,8 @@ METRIC = "ILS solves/s at rel err ≤1e-10: mixed+batched+warm vs plain FP64 SP,
 WORKLOAD = "dense ILS 20000x500 (A_1 16000x500 N(0,1), A_2 4000x500 0.3*N(0,1)), single RHS, seed 1"
 TOL_RELRES = 1e-11  # relres target; kappa(A^T J A) ~ 2.5 here, so the error bound is ~2.5e-11
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (FMA pipe) rate from the profiling recipe
+# FP32 SIMT peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (max SM clock)
+FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 BF16_PEAK_TFLOPS = 1982.7  # measured cuBLAS BF16 burst rate on this machine (MEASURED_PEAKS.json)
 
 
@@ -554,16 +557,51 @@ def main():
         return
     ms_step = 1e3 * mixed["total_s"] / args.steps
     ph = mixed["phases"]
-    # Dominant kernel group of the headline step: the FP64 Cholesky factorizations of
-    # A_1^T A_1 and A^T J A (2 n^3 / 3 algorithmic flops), latency-bound FP64 chains.
-    chol_ms = ph["cholesky"]
-    chol_flops = 2.0 * n ** 3 / 3.0
-    chol_ach = chol_flops / (chol_ms * 1e-3) / 1e12
-    # Tensor-core Gram A_1^T A_1: algorithmic p n (n+1) flops (FP64-accurate result).
-    gram_ms = ph["gram1"]
-    gram_flops = float(p) * n * (n + 1)
+    # The two largest kernels of the headline step, each timed alone with CUDA events on
+    # the handle's stream (options.timing):
+    #  * spd_gj_kernel: P = Abar1^{-1} by FP32 block Gauss-Jordan and the test of H; the
+    #    sweep operator makes n^3 multiply-adds per matrix, 4 n^3 flops for the two.
+    #  * gram_split_mma_kernel (A_1^T A_1): executed BF16 MMA flops, 2 x 128 x 128 x p per
+    #    digit product and tile pair; 55 products on an off-diagonal tile pair, 30 on a
+    #    diagonal one (the transposed cross products are not formed).
+    gj_ms = ph["factor"]
+    gj_flops = 4.0 * n ** 3
+    gj_ach = gj_flops / (gj_ms * 1e-3) / 1e12
+    mma_ms = ph["gram1_mma"]
     n_tiles = (n + 127) // 128
-    tensor_flops = 2.0 * 128 * 128 * p * (n_tiles * (n_tiles + 1) // 2) * 55  # executed BF16 MMA flops
+    n_upper = n_tiles * (n_tiles + 1) // 2
+    tensor_flops = 2.0 * 128 * 128 * p * ((n_upper - n_tiles) * 55 + n_tiles * 30)
+    mma_ach = tensor_flops / (mma_ms * 1e-3) / 1e12
+    gram_ms = ph["gram1"]
+    gram_flops = float(p) * n * (n + 1)  # the FP64-accurate product A_1^T A_1
+    roof_gj = {
+        "kernel": "spd_gj_kernel (P = Abar1^{-1} by FP32 block Gauss-Jordan, with the SPD test of A^T J A)",
+        "bound": "alu",
+        "achieved": gj_ach,
+        "peak": FP32_SIMT_PEAK_TFLOPS,
+        "peak_source": "FP32 SIMT rate from unit counts: 152 SMs x 128 lanes x 2 flops x 2.07 GHz",
+        "unit": "TFLOP/s",
+        "frac": gj_ach / FP32_SIMT_PEAK_TFLOPS,
+        "traffic": None,
+        "kernel_ms": gj_ms,
+        "share_of_step": gj_ms / ms_step,
+        "note": "latency-bound: 16 block steps, each a 32-pivot scalar sweep in one warp and a grid barrier",
+    }
+    roof_mma = {
+        "kernel": "gram_split_mma_kernel (A_1^T A_1 to FP64 accuracy from exact BF16 digit products)",
+        "bound": "tensor",
+        "achieved": mma_ach,
+        "peak": BF16_PEAK_TFLOPS,
+        "peak_source": "measured cuBLAS BF16 burst (MEASURED_PEAKS.json)",
+        "unit": "TFLOP/s (executed BF16 MMA flops)",
+        "frac": mma_ach / BF16_PEAK_TFLOPS,
+        "traffic": None,
+        "kernel_ms": mma_ms,
+        "share_of_step": mma_ms / ms_step,
+        "gram_phase_ms": gram_ms,
+        "fp64_equivalent_tflops_of_phase": gram_flops / (gram_ms * 1e-3) / 1e12,
+        "note": "L2-bound: every digit tile is re-read by the CTAs of its tile pair",
+    }
     stream = measure_stream(ils, torch, np, dev)
     configs = {}
     if not args.no_configs:
@@ -586,8 +624,9 @@ def main():
         "data": "synthetic",
         "config": {
             "workload": WORKLOAD,
-            "method": "SP (Alg. 1), mixed precision: tensor-core FP64-accurate Grams, FP64 Cholesky, "
-                      "FP32 sweeps, FP64 residual refinement",
+            "method": "SP (Alg. 1), mixed precision: tensor-core FP64-accurate Grams, P by FP32 block "
+                      "Gauss-Jordan (with the SPD test of A^T J A), FP32 sweeps, FP64 residual refinement in "
+                      "one cooperative launch",
             "tol_relres": TOL_RELRES,
             "relerr_vs_oracle": mixed["relerr"],
             "refinements": mixed["info"]["refinements"],
@@ -603,30 +642,9 @@ def main():
             "setup_phases_ms": {k: round(v, 4) for k, v in plain["phases"].items()},
             "speedup_of_headline": value / plain_value,
         },
-        "roofline": {
-            "kernel": "FP64 Cholesky of A_1^T A_1 and A^T J A (potrf_diag + trsm_panel + syrk_trailing)",
-            "bound": "alu",
-            "achieved": chol_ach,
-            "peak": FP64_PEAK_TFLOPS,
-            "peak_source": "nominal FP64 rate of the profiling recipe (FP64 is absent from MEASURED_PEAKS.json)",
-            "unit": "TFLOP/s",
-            "frac": chol_ach / FP64_PEAK_TFLOPS,
-            "traffic": None,
-            "kernel_ms": chol_ms,
-            "share_of_step": chol_ms / ms_step,
-            "note": "latency-bound: 64-cycle dependent FP64 FMA and 440-cycle FP64 rsqrt on the pivot chain",
-        },
-        "roofline_tensor_gram": {
-            "kernel": "gram_split_mma_kernel + digit split + reduce (A_1^T A_1 to FP64 accuracy)",
-            "bound": "tensor",
-            "achieved": tensor_flops / (gram_ms * 1e-3) / 1e12,
-            "peak": BF16_PEAK_TFLOPS,
-            "unit": "TFLOP/s (executed BF16 MMA flops)",
-            "frac": tensor_flops / (gram_ms * 1e-3) / 1e12 / BF16_PEAK_TFLOPS,
-            "fp64_equivalent_tflops": gram_flops / (gram_ms * 1e-3) / 1e12,
-            "kernel_ms": gram_ms,
-            "share_of_step": gram_ms / ms_step,
-        },
+        "roofline": roof_gj if gj_ms >= mma_ms else roof_mma,
+        "roofline_gj_inverse": roof_gj,
+        "roofline_tensor_gram": roof_mma,
         "roofline_stream": {
             "kernel": "aq_stream_kernel (one-pass A_2^T (A_2 x), matrix-free route), tall instance A_2 262144x500",
             "bound": "hbm",

@@ -185,9 +185,13 @@ ils_status ils_get_matrix(ils_handle h, int which, double* dst, int64_t ldd, ils
 
 /* Setup phase times of the last ils_setup / ils_refactor on h, in milliseconds,
  * measured with CUDA events on the handle's stream when options.timing != 0
- * (zeros otherwise).  out [host] receives min(count, 6) values:
- *   0 Abar1 Gram, 1 Abar2 Gram, 2 the two Cholesky factorizations,
- *   3 P = Abar1^{-1} and B = P Abar2, 4 the whole setup, 5 the copy of A.
+ * (zeros otherwise).  out [host] receives min(count, 7) values:
+ *   0 Abar1 Gram, 1 the wait for the Abar2 Gram (its own time where it runs alone),
+ *   2 the factor step: the Cholesky factorizations of Abar1 and H, or on a mixed-precision
+ *     single handle the one-launch FP32 inverse of Abar1 with the test of H,
+ *   3 the products that follow (P and B, or B alone after the inverse),
+ *   4 the whole setup, 5 the copy of A, 6 the tensor-core kernel of the Abar1 Gram alone
+ *   (split Grams only).
  * Returns the number of values written, or -1 on a bad argument. */
 int ils_get_timings(ils_handle h, double* out, int count);
 

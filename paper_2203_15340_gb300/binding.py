@@ -290,9 +290,9 @@ class Solver:
 
     def timings(self):
         """Setup phase times (ms) of the last setup/refactor when options.timing was set."""
-        buf = (ctypes.c_double * 6)()
-        n = lib().ils_get_timings(self.h, buf, 6)
-        keys = ["gram1", "gram2", "cholesky", "inverse_and_B", "setup", "copy_A"]
+        buf = (ctypes.c_double * 7)()
+        n = lib().ils_get_timings(self.h, buf, 7)
+        keys = ["gram1", "gram2", "factor", "products", "setup", "copy_A", "gram1_mma"]
         return {k: buf[i] for i, k in enumerate(keys[:max(n, 0)])}
 
     def close(self):

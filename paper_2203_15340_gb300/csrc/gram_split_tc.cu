@@ -612,7 +612,8 @@ GramSplitWork gram_split_work(int64_t K, int64_t n) {
 }
 
 cudaError_t gram_split_tc(int64_t K, int64_t n, const double* A, int64_t lda, double* C, int64_t ldc, void* slices,
-                          double* partial, int* exps, int32_t* err, cudaStream_t s) {
+                          double* partial, int* exps, int32_t* err, cudaStream_t s, cudaEvent_t mma_begin,
+                          cudaEvent_t mma_end) {
   if (n <= 0) return cudaSuccess;
   if (K <= 0) return cudaMemset2DAsync(C, sizeof(double) * ldc, 0, sizeof(double) * n, n, s);
   if (K > (int64_t)1 << 30 || n > 65535) return cudaErrorInvalidValue;
@@ -662,9 +663,11 @@ cudaError_t gram_split_tc(int64_t K, int64_t n, const double* A, int64_t lda, do
   const size_t smem = smem_bytes();
   e = cudaFuncSetAttribute(gram_split_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  if (mma_begin && (e = cudaEventRecord(mma_begin, s)) != cudaSuccess) return e;
   gram_split_mma_kernel<<<items, kThreads, smem, s>>>(map, P);
   note_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (mma_end && (e = cudaEventRecord(mma_end, s)) != cudaSuccess) return e;
   split_reduce_kernel<<<1024, 256, 0, s>>>(P, C, ldc);
   note_launch();
   return cudaGetLastError();

@@ -109,8 +109,8 @@ struct ils_handle_s {
   int64_t pass_launched = 0;
   bool pass_mixed = false;
   // setup phase timing (options.timing != 0)
-  cudaEvent_t ev[7] = {};
-  double t_ms[6] = {};
+  cudaEvent_t ev[8] = {};  // 6, 7: around the tensor-core kernel of the Abar1 Gram
+  double t_ms[7] = {};
 };
 
 namespace ils {
@@ -294,6 +294,16 @@ cudaError_t mark(ils_handle h, int i) {
   return cudaEventRecord(h->ev[i], h->stream);
 }
 
+// Timing events 6 and 7 (around the Abar1 Gram's tensor-core kernel), created on demand.
+cudaEvent_t timing_event(ils_handle h, int i) {
+  if (!h->opt.timing) return nullptr;
+  if (!h->ev[i] && cudaEventCreate(&h->ev[i]) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return h->ev[i];
+}
+
 void collect_timings(ils_handle h) {
   for (double& t : h->t_ms) t = 0.0;
   if (!h->opt.timing) return;
@@ -310,6 +320,7 @@ void collect_timings(ils_handle h) {
   h->t_ms[3] = el(4, 5);
   h->t_ms[4] = el(0, 5);
   h->t_ms[5] = el(0, 1);
+  h->t_ms[6] = el(6, 7);
 }
 
 // Matrix-free route after Abar1: Cholesky of Abar1, P (FP64, or FP32 for the mixed
@@ -374,7 +385,8 @@ ils_status compute_setup(ils_handle h) {
   // Abar1 = A_1^T A_1, Abar2 = A_2^T A_2 (Alg. 1 steps 2-3; Alg. 2 step 2; Alg. 5 step 2).
   if (h->opt.gram == ILS_GRAM_SPLIT) {
     ILS_CK(cudaMemsetAsync(h->gs_err, 0, sizeof(int32_t), s));
-    ILS_CK(gram_split_tc(p, n, h->A, m, h->G1, n, h->gs_slices, h->gs_partial, h->gs_exps, h->gs_err, s));
+    ILS_CK(gram_split_tc(p, n, h->A, m, h->G1, n, h->gs_slices, h->gs_partial, h->gs_exps, h->gs_err, s,
+                         timing_event(h, 6), timing_event(h, 7)));
   } else {
     ILS_CK(gemm_tn_f64(p, n, n, h->A, m, h->A, m, p, h->G1, n, true, false, h->work, s));
   }
@@ -451,15 +463,16 @@ ils_status compute_setup_overlap(ils_handle h) {
   ILS_CK(cudaEventRecord(h->ev_start, s));
   ILS_CK(cudaStreamWaitEvent(a, h->ev_start, 0));
   // Abar1 = A_1^T A_1 here, Abar2 = A_2^T A_2 there (Alg. 1 steps 2-3)
-  ILS_CK(gram_split_tc(p, n, h->A, m, h->G1, n, h->gs_slices, h->gs_partial, h->gs_exps, h->gs_err, s));
+  ILS_CK(gram_split_tc(p, n, h->A, m, h->G1, n, h->gs_slices, h->gs_partial, h->gs_exps, h->gs_err, s,
+                       timing_event(h, 6), timing_event(h, 7)));
   ILS_CK(gram_split_tc(q, n, h->A + p, m, h->G2, n, h->gs_slices2, h->gs_partial2, h->gs_exps2, h->gs_err, a));
   ILS_CK(cudaEventRecord(h->ev_g2, a));
   ILS_CK(mark(h, 2));
   ILS_CK(convert_f64_to_f32(n * n, h->G1, h->L32, s));  // Abar1, both triangles
   ILS_CK(cudaStreamWaitEvent(s, h->ev_g2, 0));
-  ILS_CK(mark(h, 3));
   ILS_CK(axpby_mat_f64(n, 1.0, h->G1, -1.0, h->G2, h->H, s));
   ILS_CK(convert_f64_to_f32(n * n, h->H, h->H32, s));
+  ILS_CK(mark(h, 3));
   const float* mats[2] = {h->L32, h->H32};
   float* outs[2] = {h->P32, nullptr};
   int32_t* sts[2] = {h->dstatus, h->dstatus2};
@@ -1123,7 +1136,7 @@ ils_status ils_aq_product(ils_handle h, const double* x, double* v, int prec, il
 
 int ils_get_timings(ils_handle h, double* out, int count) {
   if (!h || !out || count < 0) return -1;
-  const int c = count < 6 ? count : 6;
+  const int c = count < 7 ? count : 7;
   for (int i = 0; i < c; ++i) out[i] = h->t_ms[i];
   return c;
 }

@@ -147,14 +147,16 @@ cudaError_t copy_final_f64(int64_t n, int64_t k, const double* X0, const double*
 // ---- FP64-accurate Gram from exact integer slice products on tcgen05 (gram_split_tc.cu) ----
 struct GramSplitWork {
   size_t slice_elems = 0;    // BF16 slices
-  size_t partial_elems = 0;  // FP64 partial products
+  size_t partial_elems = 0;  // partial products (FP32 values in a buffer of this many doubles)
   size_t exps = 0;           // int exponents
 };
 GramSplitWork gram_split_work(int64_t K, int64_t n);
 // C = A^T A for the K x n column-major A (lda), both triangles written.  err (device int)
-// is set to 1 on a tensor-pipeline timeout and 2 on a non-finite input.
+// is set to 1 on a tensor-pipeline timeout and 2 on a non-finite input.  mma_begin /
+// mma_end, when set, are recorded on s around the tensor-core launch alone.
 cudaError_t gram_split_tc(int64_t K, int64_t n, const double* A, int64_t lda, double* C, int64_t ldc,
-                          void* slices, double* partial, int* exps, int32_t* err, cudaStream_t s);
+                          void* slices, double* partial, int* exps, int32_t* err, cudaStream_t s,
+                          cudaEvent_t mma_begin = nullptr, cudaEvent_t mma_end = nullptr);
 
 // ---- matrix-free A_2 products (stream.cu) ---------------------------------------------------
 // Row-major copy of A_2 (q x n, column-major source with leading dimension lda) with rows
