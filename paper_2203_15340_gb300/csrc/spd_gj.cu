@@ -10,13 +10,14 @@
 // finite is reported as NOT_SPD / NONFINITE, like a failed Cholesky pivot.
 //
 // Work split: the lower 32 x 32 tiles of every matrix are spread over the CTAs and stay in
-// their shared memory for the whole launch.  In step k, block column k (old values) and
-// D^{-1} are read from a global exchange buffer; every tile is updated; the owners of
-// block column / row k+1 then post the next block column and the owner of tile (k+1,k+1)
-// sweeps it and posts its D^{-1}; one grid barrier separates the steps.  The exchange
-// buffers alternate between steps, so a step's posts never overwrite what a slower CTA
-// of the step before still reads.  The grid barrier waits are bounded: past about 1 s the
-// CTA records TIMEOUT, raises the abort word and every waiter returns.
+// their shared memory for the whole launch.  Step k of a tile needs D_k^{-1} and the old
+// blocks k of its block rows i and j (block column k before step k); their producers
+// post them to global memory once and raise a flag for each, so every tile waits only
+// for what it reads (data-driven, no grid barrier).  The critical path is the chain of
+// pivot blocks: the owner of tile (k+1,k+1) updates it with D_k^{-1}, sweeps it and posts
+// D_{k+1}^{-1}.  Posts are fenced before their flag is raised; waits read through L2.
+// Every wait is bounded: past about 1 s the CTA records TIMEOUT, raises the abort word
+// (which releases every other waiter) and returns.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -35,10 +36,11 @@ constexpr int kGjTile = 32 * kGjPad;
 struct GjArgs {
   const float* A[2];  // n x n column-major, symmetric, both triangles stored
   float* P[2];        // the inverse, full (nullptr: status only)
-  float* C[2];        // 2 x (nb * 32 x 32): block column k, row-major per row
-  float* D[2];        // 2 x (32 x 32): D^{-1} of pivot block k, row-major
+  float* C[2];        // nb x nb blocks of 32 x 32: C(k, i) = block (i, k) before step k, row-major
+  float* D[2];        // nb blocks of 32 x 32: D_k^{-1}, row-major
+  uint32_t* flag[2];  // [k * nb + i]: C(k, i) posted; [nb * nb + k]: D_k^{-1} posted
   int32_t* status[2];
-  uint32_t* sync;  // [0] arrivals, [1] generation, [2] abort
+  uint32_t* abort_word;
   int64_t n;
   int nb;     // 32-row blocks
   int count;  // matrices (1 or 2)
@@ -56,46 +58,47 @@ __device__ __forceinline__ uint32_t gj_ld_relaxed(const uint32_t* p) {
   return v;
 }
 
-// Grid-wide barrier of a cooperative launch (generation counting).  False on abort or
-// after about 1 s of waiting, which is recorded as TIMEOUT and raises the abort word.
-__device__ bool gj_barrier(uint32_t* sync, int32_t* status) {
+// Thread 0 waits until *flag != 0 (relaxed polls; an acquire fence once it is seen), then
+// the CTA goes on.  False on abort or after about 1 s, recorded as TIMEOUT.
+__device__ bool gj_wait(const uint32_t* flag, uint32_t* abort_word, int32_t* status) {
   __shared__ int ok;
-  __syncthreads();
   if (threadIdx.x == 0) {
     int res = 1;
-    const uint32_t gen = gj_ld_relaxed(sync + 1);
-    __threadfence();
-    if (atomicAdd(sync, 1u) == gridDim.x - 1) {
-      sync[0] = 0u;
-      __threadfence();
-      atomicAdd(sync + 1, 1u);
-    } else {
-      uint64_t t0 = 0;
-      for (uint32_t spin = 0;; ++spin) {
-        if (gj_ld_acquire(sync + 1) != gen) break;
-        if ((spin & 15u) == 15u) {
-          if (gj_ld_acquire(sync + 2) != 0u) {
-            res = 0;
-            break;
-          }
-          uint64_t t;
-          asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-          if (t0 == 0) {
-            t0 = t;
-          } else if (t - t0 > 1000000000ull) {
-            atomicCAS(status, 0, (int32_t)ILS_ERR_TIMEOUT);
-            atomicExch(sync + 2, 1u);
-            res = 0;
-            break;
-          }
-        }
-        if (spin >= 64u) __nanosleep(32);
+    uint64_t t0 = 0;
+    for (uint32_t spin = 0;; ++spin) {
+      if (gj_ld_relaxed(flag) != 0u) {
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        break;
       }
+      if ((spin & 15u) == 15u) {
+        if (gj_ld_acquire(abort_word) != 0u) {
+          res = 0;
+          break;
+        }
+        uint64_t t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t0 == 0) {
+          t0 = t;
+        } else if (t - t0 > 1000000000ull) {
+          atomicCAS(status, 0, (int32_t)ILS_ERR_TIMEOUT);
+          atomicExch(abort_word, 1u);
+          res = 0;
+          break;
+        }
+      }
+      if (spin >= 64u) __nanosleep(32);
     }
     ok = res;
   }
   __syncthreads();
   return ok != 0;
+}
+
+// After the CTA's stores of a post: order them before the flag (CTA barrier, then a
+// release store by thread 0).
+__device__ __forceinline__ void gj_raise(uint32_t* flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(flag), "r"(1u) : "memory");
 }
 
 // Lower tile t of an nb-block matrix, row-major over the lower triangle: (i, j), i >= j.
@@ -193,17 +196,20 @@ __device__ __forceinline__ void gj_post(float* dst, const float* T, bool transpo
 }
 
 // After tile (i, j) of matrix m is final for the steps before k1: post what step k1 needs
-// from it into exchange buffer q.
-__device__ void gj_post_for(const GjArgs& a, int m, int i, int j, int k1, int q, float* T, float* prow) {
-  float* Cq = a.C[m] + (size_t)q * a.nb * 1024;
+// from it and raise its flag.
+__device__ void gj_post_for(const GjArgs& a, int m, int i, int j, int k1, float* T, float* prow) {
+  const int nb = a.nb;
   if (i == k1 && j == k1) {
     if (threadIdx.x < 32) gj_sweep_pivot(T, prow, a.status[m]);  // T := -D^{-1}
     __syncthreads();
-    gj_post(a.D[m] + q * 1024, T, false, -1.f);
+    gj_post(a.D[m] + (size_t)k1 * 1024, T, false, -1.f);
+    gj_raise(a.flag[m] + (size_t)nb * nb + k1);
   } else if (j == k1) {
-    gj_post(Cq + (size_t)i * 1024, T, false, 1.f);  // A(block i, block k1)
+    gj_post(a.C[m] + ((size_t)k1 * nb + i) * 1024, T, false, 1.f);  // A(block i, block k1)
+    gj_raise(a.flag[m] + (size_t)k1 * nb + i);
   } else if (i == k1) {
-    gj_post(Cq + (size_t)j * 1024, T, true, 1.f);   // A(block j, block k1) = A(k1, j)^T
+    gj_post(a.C[m] + ((size_t)k1 * nb + j) * 1024, T, true, 1.f);   // A(block j, block k1) = A(k1, j)^T
+    gj_raise(a.flag[m] + (size_t)k1 * nb + j);
   }
 }
 
@@ -244,24 +250,26 @@ __global__ void __launch_bounds__(kGjThreads) spd_gj_kernel(GjArgs a) {
 #pragma unroll
   for (int s = 0; s < kGjMaxOwn; ++s) {
     if (om[s] < 0) continue;
-    gj_post_for(a, om[s], oi[s], oj[s], 0, 0, own + s * kGjTile, prow);
+    gj_post_for(a, om[s], oi[s], oj[s], 0, own + s * kGjTile, prow);
     __syncthreads();
   }
 
-  for (int k = 0; k < a.nb; ++k) {
-    if (!gj_barrier(a.sync, a.status[0])) return;
-    const int p = k & 1;
+  const int nb = a.nb;
+  for (int k = 0; k < nb; ++k) {
 #pragma unroll
     for (int s = 0; s < kGjMaxOwn; ++s) {
       if (om[s] < 0) continue;
       const int m = om[s], i = oi[s], j = oj[s];
       float* T = own + s * kGjTile;
       if (!(i == k && j == k)) {  // the pivot tile was swept when it was posted
-        const float* Cp = a.C[m] + (size_t)p * a.nb * 1024;
-        gj_stage(Dm, a.D[m] + p * 1024);
+        const uint32_t* fl = a.flag[m];
+        if (!gj_wait(fl + (size_t)nb * nb + k, a.abort_word, a.status[m])) return;
+        gj_stage(Dm, a.D[m] + (size_t)k * 1024);
         if (j != k && i != k) {
-          gj_stage(Ci, Cp + (size_t)i * 1024);
-          gj_stage(Cj, Cp + (size_t)j * 1024);
+          if (!gj_wait(fl + (size_t)k * nb + i, a.abort_word, a.status[m])) return;
+          if (j != i && !gj_wait(fl + (size_t)k * nb + j, a.abort_word, a.status[m])) return;
+          gj_stage(Ci, a.C[m] + ((size_t)k * nb + i) * 1024);
+          gj_stage(Cj, a.C[m] + ((size_t)k * nb + j) * 1024);
         }
         __syncthreads();
         float acc[4] = {0.f, 0.f, 0.f, 0.f};
@@ -285,8 +293,8 @@ __global__ void __launch_bounds__(kGjThreads) spd_gj_kernel(GjArgs a) {
         for (int q = 0; q < 4; ++q) T[r * kGjPad + c0 + q] = acc[q];
         __syncthreads();
       }
-      if (k + 1 < a.nb) {
-        gj_post_for(a, m, i, j, k + 1, p ^ 1, T, prow);
+      if (k + 1 < nb) {
+        gj_post_for(a, m, i, j, k + 1, T, prow);
         __syncthreads();
       }
     }
@@ -316,7 +324,10 @@ size_t gj_smem_bytes() { return sizeof(float) * ((size_t)(kGjMaxOwn + 4) * kGjTi
 
 size_t spd_inverse_scratch_floats(int64_t n) {
   const size_t nb = (size_t)((n + 31) / 32);
-  return 2 * (2 * nb * 1024 + 2048) + 64;
+  // per matrix: C (nb^2 blocks), D (nb blocks), flags (nb^2 + nb words, padded to 16 bytes);
+  // then the abort word
+  const size_t blocks = nb * nb + nb;
+  return 2 * (blocks * 1024 + ((blocks + 3) & ~(size_t)3)) + 64;
 }
 
 cudaError_t spd_inverse_f32(int64_t n, int count, const float* const* A, float* const* P, float* scratch,
@@ -336,21 +347,28 @@ cudaError_t spd_inverse_f32(int64_t n, int count, const float* const* A, float* 
   const int grid = (int)std::min<int64_t>(total, grid_max);
   if (!coop || grid < 1 || (int64_t)grid * kGjMaxOwn < total) return cudaErrorNotSupported;
   GjArgs a;
-  const size_t per = 2 * (size_t)nb * 1024 + 2048;
+  const size_t blocks = (size_t)nb * nb + nb;
+  const size_t per = blocks * 1024 + ((blocks + 3) & ~(size_t)3);  // floats, then flag words (16-byte steps)
   for (int i = 0; i < 2; ++i) {
     const int src = i < count ? i : 0;
+    float* base = scratch + (size_t)src * per;
     a.A[i] = A[src];
     a.P[i] = P[src];
-    a.C[i] = scratch + (size_t)src * per;
-    a.D[i] = a.C[i] + 2 * (size_t)nb * 1024;
+    a.C[i] = base;
+    a.D[i] = base + (size_t)nb * nb * 1024;
+    a.flag[i] = reinterpret_cast<uint32_t*>(base + blocks * 1024);
     a.status[i] = status[src];
   }
-  a.sync = reinterpret_cast<uint32_t*>(scratch + 2 * per);
+  a.abort_word = reinterpret_cast<uint32_t*>(scratch + 2 * per);
   a.n = n;
   a.nb = nb;
   a.count = count;
   a.tiles = tiles;
-  if ((e = cudaMemsetAsync(a.sync, 0, 4 * sizeof(uint32_t), s)) != cudaSuccess) return e;
+  for (int i = 0; i < count; ++i)
+    if ((e = cudaMemsetAsync(a.flag[i], 0, sizeof(uint32_t) * blocks, s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(a.abort_word, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
+  // Cooperative launch: every CTA is resident, so a CTA waiting on a flag never holds the
+  // SM its producer needs.
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid, 1, 1);
   cfg.blockDim = dim3(kGjThreads, 1, 1);
