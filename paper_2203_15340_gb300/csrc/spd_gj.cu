@@ -30,7 +30,7 @@ namespace {
 
 constexpr int kGjThreads = 256;
 constexpr int kGjMaxOwn = 4;  // tiles a CTA keeps in shared memory
-constexpr int kGjPad = 33;    // row stride of a tile in shared memory
+constexpr int kGjPad = 36;    // row stride of a tile in shared memory (16-byte rows)
 constexpr int kGjTile = 32 * kGjPad;
 
 struct GjArgs {
@@ -116,74 +116,102 @@ __device__ __forceinline__ int gj_pivot_code(float d) {
   return 0;
 }
 
-// Warp 0: scalar sweeps of all 32 pivots of the tile T (in place), leaving -D^{-1}; lane =
-// row, the row in registers.  A sweep keeps the matrix symmetric, so pivot row c is
-// column c: every lane posts its column-c entry to `prow` (2 x 32 floats, alternating)
-// and reads the row back four entries at a time.  Every lane, the pivot lane included,
-// applies the same multiply and multiply-add per entry, so the warp never diverges.  A failed pivot is recorded and replaced by 1 so
-// that the launch runs to its end.
+// Warps 0-3: sweeps of all 32 pivots of the tile T (in place), leaving -D^{-1}; lane =
+// row, warp w holding columns 8w .. 8w+7 of it in registers.  The pivots are swept two at
+// a time (a 2 x 2 block pivot, which equals two successive scalar sweeps): with the block
+// M = [a b; b d] of pivots c, c+1,
+//   rows i off the pivots:  [t0 t1] = [a_ic a_i,c+1] M^{-1},  a_iq -= t0 a_cq + t1 a_c+1,q,
+//   pivot rows:             a_Pq <- M^{-1} a_Pq,  the block itself <- -M^{-1}.
+// A sweep keeps the matrix symmetric, so pivot rows c, c+1 are columns c, c+1: the warp
+// holding them posts both to `prow` (4 x 32 floats, alternating halves), a barrier of the
+// four warps follows, and every lane reads its two entries and the rows' entries of its
+// warp's columns.  Every lane applies the same multiply and two multiply-adds per entry.
+// The block's scalar pivots are a and det / a; one that is not positive and finite is
+// recorded (a is replaced by 1 and det by a, so that the launch runs to its end).
 __device__ void gj_sweep_pivot(float* T, float* prow, int32_t* status) {
-  const int lane = threadIdx.x & 31;
-  float v[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;  // w < 4
+  const int q0 = 8 * w;
+  float v[8];
 #pragma unroll
-  for (int c = 0; c < 32; ++c) v[c] = T[lane * kGjPad + c];
+  for (int q = 0; q < 8; ++q) v[q] = T[lane * kGjPad + q0 + q];
 #pragma unroll
-  for (int c = 0; c < 32; ++c) {
-    float* pr = prow + (c & 1) * 32;
-    pr[lane] = v[c];
-    __syncwarp();
-    float row[32];
-#pragma unroll
-    for (int q4 = 0; q4 < 8; ++q4) {
-      const float4 w = reinterpret_cast<const float4*>(pr)[q4];
-      row[4 * q4] = w.x;
-      row[4 * q4 + 1] = w.y;
-      row[4 * q4 + 2] = w.z;
-      row[4 * q4 + 3] = w.w;
+  for (int c = 0; c < 32; c += 2) {
+    float* pr = prow + ((c >> 1) & 1) * 64;
+    const bool owner = w == (c >> 3);
+    if (owner) {
+      pr[lane] = v[c & 7];
+      pr[32 + lane] = v[(c + 1) & 7];
     }
-    float d = row[c];
-    const int code = gj_pivot_code(d);
-    if (code != 0) {
-      if (lane == 0) atomicCAS(status, 0, code);
-      d = 1.f;
-    }
-    const float rd = __fdividef(1.f, d);
-    const bool piv = lane == c;
-    // a_iq <- alpha a_iq + beta a_cq: off the pivot alpha = 1, beta = -a_ic / d; the pivot
-    // row becomes a_cq / d (alpha = 0, beta = 1/d; row[q] = a_qc = a_cq by symmetry).
-    const float t = v[c] * rd;
-    const float alpha = piv ? 0.f : 1.f, beta = piv ? rd : -t;
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+    const float ai0 = pr[lane], ai1 = pr[32 + lane];  // a_ic, a_i,c+1
+    float r0[8], r1[8];                               // a_cq, a_c+1,q of this warp's columns
 #pragma unroll
-    for (int q = 0; q < 32; ++q)
-      if (q != c) v[q] = fmaf(beta, row[q], alpha * v[q]);
-    v[c] = piv ? -rd : t;
+    for (int h = 0; h < 2; ++h) {
+      const float4 w0 = reinterpret_cast<const float4*>(pr + q0)[h];
+      const float4 w1 = reinterpret_cast<const float4*>(pr + 32 + q0)[h];
+      r0[4 * h] = w0.x;
+      r0[4 * h + 1] = w0.y;
+      r0[4 * h + 2] = w0.z;
+      r0[4 * h + 3] = w0.w;
+      r1[4 * h] = w1.x;
+      r1[4 * h + 1] = w1.y;
+      r1[4 * h + 2] = w1.z;
+      r1[4 * h + 3] = w1.w;
+    }
+    float a = pr[c], b = pr[c + 1], d = pr[32 + c + 1];
+    const int code = gj_pivot_code(a);
+    if (code != 0) a = 1.f;
+    float det = fmaf(a, d, -b * b);
+    const int code2 = gj_pivot_code(det);
+    if (code2 != 0) det = a;
+    if ((code != 0 || code2 != 0) && threadIdx.x == 0) atomicCAS(status, 0, code != 0 ? code : code2);
+    const float rdet = __fdividef(1.f, det);
+    const float m00 = d * rdet, m01 = -b * rdet, m11 = a * rdet;  // M^{-1}
+    const bool p0 = lane == c, p1 = lane == c + 1;
+    const float t0 = fmaf(ai0, m00, ai1 * m01), t1 = fmaf(ai0, m01, ai1 * m11);
+    const float alpha = (p0 || p1) ? 0.f : 1.f;
+    const float beta0 = p0 ? m00 : (p1 ? m01 : -t0);
+    const float beta1 = p0 ? m01 : (p1 ? m11 : -t1);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = fmaf(beta1, r1[q], fmaf(beta0, r0[q], alpha * v[q]));
+    if (owner) {  // the pivot columns themselves
+      v[c & 7] = p0 ? -m00 : (p1 ? -m01 : t0);
+      v[(c + 1) & 7] = p0 ? -m01 : (p1 ? -m11 : t1);
+    }
   }
-  __syncwarp();
 #pragma unroll
-  for (int c = 0; c < 32; ++c) T[lane * kGjPad + c] = v[c];
+  for (int q = 0; q < 8; ++q) T[lane * kGjPad + q0 + q] = v[q];
 }
 
 // acc[q] += sum_m L(r, m) R(m, c0 + q) for the thread's outputs r = tid / 8,
-// c0 = 4 (tid % 8), q < 4; with rt, R(c0 + q, m) (the product L R^T).
-__device__ __forceinline__ void gj_mm4(const float* L, const float* R, bool rt, float acc[4]) {
+// c0 = 4 (tid % 8), q < 4 (R read four columns at a time).
+__device__ __forceinline__ void gj_mm4(const float* L, const float* R, float acc[4]) {
   const int r = threadIdx.x >> 3, c0 = (threadIdx.x & 7) * 4;
 #pragma unroll 8
   for (int m = 0; m < 32; ++m) {
     const float a = L[r * kGjPad + m];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) acc[q] = fmaf(a, rt ? R[(c0 + q) * kGjPad + m] : R[m * kGjPad + c0 + q], acc[q]);
+    const float4 b = *reinterpret_cast<const float4*>(R + m * kGjPad + c0);
+    acc[0] = fmaf(a, b.x, acc[0]);
+    acc[1] = fmaf(a, b.y, acc[1]);
+    acc[2] = fmaf(a, b.z, acc[2]);
+    acc[3] = fmaf(a, b.w, acc[3]);
   }
 }
 
-// Stage a 32 x 32 row-major global block (16-byte aligned) into a padded shared tile.
-__device__ __forceinline__ void gj_stage(float* dst, const float* src) {
+// Stage a 32 x 32 row-major global block (16-byte aligned) into a padded shared tile, or
+// its transpose.
+__device__ __forceinline__ void gj_stage(float* dst, const float* src, bool transpose = false) {
   for (int e = threadIdx.x; e < 256; e += kGjThreads) {
     const float4 v = __ldcg(reinterpret_cast<const float4*>(src) + e);
     const int r = e >> 3, c = (e & 7) * 4;
-    dst[r * kGjPad + c] = v.x;
-    dst[r * kGjPad + c + 1] = v.y;
-    dst[r * kGjPad + c + 2] = v.z;
-    dst[r * kGjPad + c + 3] = v.w;
+    if (transpose) {
+      dst[c * kGjPad + r] = v.x;
+      dst[(c + 1) * kGjPad + r] = v.y;
+      dst[(c + 2) * kGjPad + r] = v.z;
+      dst[(c + 3) * kGjPad + r] = v.w;
+    } else {
+      *reinterpret_cast<float4*>(dst + r * kGjPad + c) = v;
+    }
   }
 }
 
@@ -200,7 +228,7 @@ __device__ __forceinline__ void gj_post(float* dst, const float* T, bool transpo
 __device__ void gj_post_for(const GjArgs& a, int m, int i, int j, int k1, float* T, float* prow) {
   const int nb = a.nb;
   if (i == k1 && j == k1) {
-    if (threadIdx.x < 32) gj_sweep_pivot(T, prow, a.status[m]);  // T := -D^{-1}
+    if (threadIdx.x < 128) gj_sweep_pivot(T, prow, a.status[m]);  // T := -D^{-1}
     __syncthreads();
     gj_post(a.D[m] + (size_t)k1 * 1024, T, false, -1.f);
     gj_raise(a.flag[m] + (size_t)nb * nb + k1);
@@ -220,7 +248,7 @@ __global__ void __launch_bounds__(kGjThreads) spd_gj_kernel(GjArgs a) {
   float* Cj = Ci + kGjTile;             // C_k(j)
   float* Dm = Cj + kGjTile;             // D^{-1}
   float* X = Dm + kGjTile;              // C_k(i) D^{-1}
-  float* prow = X + kGjTile;            // 2 x 32: pivot rows of the scalar sweeps
+  float* prow = X + kGjTile;            // 4 x 32: pivot rows of the block sweeps
   const int64_t n = a.n;
   const int total = a.count * a.tiles;
   const int tid = threadIdx.x;
@@ -263,32 +291,31 @@ __global__ void __launch_bounds__(kGjThreads) spd_gj_kernel(GjArgs a) {
       float* T = own + s * kGjTile;
       if (!(i == k && j == k)) {  // the pivot tile was swept when it was posted
         const uint32_t* fl = a.flag[m];
-        if (!gj_wait(fl + (size_t)nb * nb + k, a.abort_word, a.status[m])) return;
-        gj_stage(Dm, a.D[m] + (size_t)k * 1024);
+        // The blocks of column k are posted a step before D_k^{-1}: stage them first.
         if (j != k && i != k) {
           if (!gj_wait(fl + (size_t)k * nb + i, a.abort_word, a.status[m])) return;
           if (j != i && !gj_wait(fl + (size_t)k * nb + j, a.abort_word, a.status[m])) return;
           gj_stage(Ci, a.C[m] + ((size_t)k * nb + i) * 1024);
-          gj_stage(Cj, a.C[m] + ((size_t)k * nb + j) * 1024);
+          gj_stage(Cj, a.C[m] + ((size_t)k * nb + j) * 1024, true);  // C_k(j)^T = A_kj
         }
+        if (!gj_wait(fl + (size_t)nb * nb + k, a.abort_word, a.status[m])) return;
+        gj_stage(Dm, a.D[m] + (size_t)k * 1024);
         __syncthreads();
         float acc[4] = {0.f, 0.f, 0.f, 0.f};
-        if (j == k) {
-          gj_mm4(T, Dm, false, acc);  // A_ik D^{-1}
-        } else if (i == k) {
-          gj_mm4(Dm, T, false, acc);  // D^{-1} A_kj
+        if (j == k || i == k) {
+          if (j == k) gj_mm4(T, Dm, acc);  // A_ik D^{-1}
+          else gj_mm4(Dm, T, acc);         // D^{-1} A_kj
+          __syncthreads();                 // T is an operand: all reads before the write
         } else {
-          gj_mm4(Ci, Dm, false, acc);  // X = A_ik D^{-1}
-#pragma unroll
-          for (int q = 0; q < 4; ++q) X[r * kGjPad + c0 + q] = acc[q];
+          gj_mm4(Ci, Dm, acc);  // X = A_ik D^{-1}
+          *reinterpret_cast<float4*>(X + r * kGjPad + c0) = make_float4(acc[0], acc[1], acc[2], acc[3]);
           __syncthreads();
 #pragma unroll
           for (int q = 0; q < 4; ++q) acc[q] = 0.f;
-          gj_mm4(X, Cj, true, acc);  // X A_kj with A_kj = C_k(j)^T
+          gj_mm4(X, Cj, acc);  // X A_kj
 #pragma unroll
           for (int q = 0; q < 4; ++q) acc[q] = T[r * kGjPad + c0 + q] - acc[q];
         }
-        __syncthreads();
 #pragma unroll
         for (int q = 0; q < 4; ++q) T[r * kGjPad + c0 + q] = acc[q];
         __syncthreads();
@@ -318,7 +345,7 @@ __global__ void __launch_bounds__(kGjThreads) spd_gj_kernel(GjArgs a) {
   }
 }
 
-size_t gj_smem_bytes() { return sizeof(float) * ((size_t)(kGjMaxOwn + 4) * kGjTile + 64); }
+size_t gj_smem_bytes() { return sizeof(float) * ((size_t)(kGjMaxOwn + 4) * kGjTile + 128); }
 
 }  // namespace
 
