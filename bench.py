@@ -37,6 +37,10 @@ TOL_RELRES = 1e-11  # relres target; kappa(A^T J A) ~ 2.5 here, so the error bou
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (FMA pipe) rate from the profiling recipe
 # FP32 SIMT peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (max SM clock)
 FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
+# of each kernel as it stands, on the headline step; None once a kernel changes.
+MMA_TRAFFIC_BYTES = 160_487_936 + 9_351_424
+GJ_TRAFFIC_BYTES = 1_282_048 + 3_840
 BF16_PEAK_TFLOPS = 1982.7  # measured cuBLAS BF16 burst rate on this machine (MEASURED_PEAKS.json)
 
 
@@ -582,10 +586,10 @@ def main():
         "peak_source": "FP32 SIMT rate from unit counts: 152 SMs x 128 lanes x 2 flops x 2.07 GHz",
         "unit": "TFLOP/s",
         "frac": gj_ach / FP32_SIMT_PEAK_TFLOPS,
-        "traffic": None,
+        "traffic": GJ_TRAFFIC_BYTES,
         "kernel_ms": gj_ms,
         "share_of_step": gj_ms / ms_step,
-        "note": "latency-bound: 16 block steps, each a 32-pivot scalar sweep in one warp and a grid barrier",
+        "note": "latency-bound: the chain of 16 pivot blocks (update, 2x2-block sweep by four warps, flag handoff)",
     }
     roof_mma = {
         "kernel": "gram_split_mma_kernel (A_1^T A_1 to FP64 accuracy from exact BF16 digit products)",
@@ -595,12 +599,12 @@ def main():
         "peak_source": "measured cuBLAS BF16 burst (MEASURED_PEAKS.json)",
         "unit": "TFLOP/s (executed BF16 MMA flops)",
         "frac": mma_ach / BF16_PEAK_TFLOPS,
-        "traffic": None,
+        "traffic": MMA_TRAFFIC_BYTES,
         "kernel_ms": mma_ms,
         "share_of_step": mma_ms / ms_step,
         "gram_phase_ms": gram_ms,
         "fp64_equivalent_tflops_of_phase": gram_flops / (gram_ms * 1e-3) / 1e12,
-        "note": "L2-bound: every digit tile is re-read by the CTAs of its tile pair",
+        "note": "one wave of 126 CTAs; each 2x2 digit block loads its tiles once, L2 feeds the tensor pipe",
     }
     stream = measure_stream(ils, torch, np, dev)
     configs = {}

@@ -164,3 +164,14 @@ def test_mixed_sizes_around_panel_edges(ils, n):
     assert info.status == ils.ILS_OK
     assert relerr(x, xs) <= 1e-10
     assert info.refinements <= 6
+
+
+def test_mixed_large_n_takes_factor_route(ils):
+    """n = 1200 has more lower tiles than one cooperative wave of the Gauss-Jordan inverse
+    holds, so the setup factors A_1^T A_1 and H by Cholesky in FP32 instead; the solve must
+    still refine to FP64 accuracy."""
+    inst = W.dense_gaussian(4800, 1200, 1200, 0.3, 120)
+    xs = O.qr_cholesky_solve(inst.A, inst.b, inst.p)
+    x, info = run(ils, inst, ils.ILS_FP32_REFINE, tol=1e-12)
+    assert info.status == ils.ILS_OK
+    assert relerr(x, xs) <= 1e-10
