@@ -155,6 +155,18 @@ ils_status ils_setup_csr(ils_handle* h, int64_t m, int64_t n, int64_t p, int64_t
  * NOT_SPD the handle stays valid but must not be used to solve. */
 ils_status ils_refactor(ils_handle h, const double* A, int64_t lda, ils_stream_t stream);
 
+/* As ils_refactor without waiting for the setup: the copy of A and every setup product
+ * are enqueued on `stream` and the call returns (the first call for a given n on a
+ * mixed-precision handle waits once, to tune the sweep shapes).  A is read before any
+ * later work on `stream`.  The next ils_solve / ils_solve_many on h, on the same stream,
+ * runs behind the setup and then reports the setup's status: a failed setup's status
+ * (NOT_SPD, NONFINITE, TIMEOUT, ...) replaces the solve's and x is unspecified; where an
+ * FP64 factorization has to settle a failed FP32 pivot test, that solve performs it and
+ * solves again.  On a mixed-precision single handle with split Grams the solve's
+ * A^T J b (Alg. 1 step 4) runs on a second stream beside the setup's last products.
+ * Timings (ils_get_timings) are read at that solve.  Errors: INVALID_ARG, CUDA. */
+ils_status ils_refactor_async(ils_handle h, const double* A, int64_t lda, ils_stream_t stream);
+
 /* Solve for one right-hand side with the handle's method.
  *   b    length m, FP64.
  *   x    length n, FP64.  In: x0 unless x0_zero != 0.  Out: the solution.

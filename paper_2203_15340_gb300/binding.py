@@ -88,6 +88,7 @@ SIGNATURES = {
     "ils_setup_csr": (ctypes.c_int, [ctypes.POINTER(_P), _I64, _I64, _I64, _I64, _I64, _P, _P, _P,
                                      ctypes.POINTER(ils_options), _P]),
     "ils_refactor": (ctypes.c_int, [_P, _P, _I64, _P]),
+    "ils_refactor_async": (ctypes.c_int, [_P, _P, _I64, _P]),
     "ils_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ils_info), _P]),
     "ils_solve_many": (ctypes.c_int, [_P, _I64, _P, _I64, _P, _I64, ctypes.c_int, ctypes.c_double,
                                       ctypes.POINTER(ils_info), _P]),
@@ -257,6 +258,11 @@ class Solver:
     def refactor(self, At, stream=None):
         ptr, lda = _colmajor_ptr(At, self.m, self.n)
         return _check(lib().ils_refactor(self.h, ptr, lda, _stream_ptr(stream)), "ils_refactor")
+
+    def refactor_async(self, At, stream=None):
+        """Enqueue the setup for new values of A; the next solve reports its status."""
+        ptr, lda = _colmajor_ptr(At, self.m, self.n)
+        return _check(lib().ils_refactor_async(self.h, ptr, lda, _stream_ptr(stream)), "ils_refactor_async")
 
     def solve(self, b, x, x0_zero=True, tol=1e-12, stream=None, allow=(ILS_OK,)):
         """Solve into the CUDA tensor ``x`` (length n) for ``b`` (length m)."""

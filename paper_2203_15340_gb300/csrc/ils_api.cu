@@ -82,8 +82,10 @@ struct ils_handle_s {
   // FP32 pivot is settled by the FP64 factorization).
   bool overlap = false;
   bool l64_valid = true;  // L holds the FP64 factor of the current Abar1 (else formed on demand)
+  bool pending = false;   // a setup enqueued by ils_refactor_async whose status is not yet read
   cudaStream_t s_aux = nullptr;
   cudaEvent_t ev_start = nullptr, ev_g2 = nullptr;
+  cudaEvent_t ev_acopy = nullptr, ev_rhs = nullptr;  // A copied; A^T J b ready (solve after an async setup)
   void* gs_slices2 = nullptr;
   double* gs_partial2 = nullptr;
   int* gs_exps2 = nullptr;
@@ -514,9 +516,11 @@ ils_status factor_f64_now(ils_handle h) {
   return ILS_OK;
 }
 
-// Wait for the setup enqueued by compute_setup and report its pivot / input status.
-ils_status setup_finish(ils_handle h) {
-  ILS_CK(cudaStreamSynchronize(h->stream));
+// The status of the setup enqueued by compute_setup, once its stream has been synchronized;
+// runs the FP64 factorizations that settle failed FP32 tests (*redone: P and B were formed
+// again from the FP64 factor).
+ils_status setup_check(ils_handle h, bool* redone) {
+  if (redone) *redone = false;
   if (h->sparse && h->h_status[2] != 0) return (ils_status)h->h_status[2];
   h->h_status[1] = h->opt.gram == ILS_GRAM_SPLIT ? h->h_status[1] : 0;
   if (h->h_status[1] != 0) return h->h_status[1] == 2 ? ILS_ERR_NONFINITE : ILS_ERR_TIMEOUT;
@@ -528,6 +532,7 @@ ils_status setup_finish(ils_handle h) {
     if (*h->h_status != 0) return (ils_status)*h->h_status;
     ILS_CK(mixed_setup(h->n, h->L, h->G2, h->opt.precision, h->L32, h->P32, h->G2_32, h->Bt32, h->Bt16,
                        reinterpret_cast<float*>(h->Dinv), h->stream));
+    if (redone) *redone = true;
   }
   if (*h->h_status != 0) return (ils_status)*h->h_status;
   if (h->overlap && h->h_status[3] != 0) {
@@ -546,6 +551,12 @@ ils_status setup_finish(ils_handle h) {
   return ILS_OK;
 }
 
+// Wait for the setup enqueued by compute_setup and report its pivot / input status.
+ils_status setup_finish(ils_handle h) {
+  ILS_CK(cudaStreamSynchronize(h->stream));
+  return setup_check(h, nullptr);
+}
+
 // Autotune the sweep shapes for this handle's n once per process (mixed precision only).
 ils_status tune_handle(ils_handle h) {
   if (h->opt.precision == ILS_FP64 || h->opt.method != ILS_SP) return ILS_OK;
@@ -561,7 +572,7 @@ void free_handle(ils_handle h) {
     cudaStreamSynchronize(h->s_aux);
     cudaStreamDestroy(h->s_aux);
   }
-  for (cudaEvent_t e : {h->ev_start, h->ev_g2})
+  for (cudaEvent_t e : {h->ev_start, h->ev_g2, h->ev_acopy, h->ev_rhs})
     if (e) cudaEventDestroy(e);
   if (h->h_st) cudaFreeHost(h->h_st);
   for (cudaEvent_t e : h->ev)
@@ -580,9 +591,22 @@ ils_status pass_begin(ils_handle h, int64_t c0, int64_t kk, const double* B, int
   cudaStream_t s = h->stream;
   const int64_t m = h->m, n = h->n, p = h->p;
   // bbar = A^T J b (Alg. 1 step 4), c = P bbar.
-  if (h->sparse) ILS_CK(sparse_rhs_bar(n, p, kk, h->sc, B, ldb, h->bbar, n, s));
-  else ILS_CK(rhs_bar_f64(m, n, p, kk, h->A, m, B, ldb, h->bbar, n, s));
-  ILS_CK(sq_norms_cols_f64(n, kk, h->bbar, n, h->bnorm2, s));
+  if (h->sparse) {
+    ILS_CK(sparse_rhs_bar(n, p, kk, h->sc, B, ldb, h->bbar, n, s));
+    ILS_CK(sq_norms_cols_f64(n, kk, h->bbar, n, h->bnorm2, s));
+  } else if (h->pending && h->overlap) {
+    // After an asynchronous setup, A^T J b needs only the copy of A: the second stream
+    // forms it beside the setup's last products.
+    cudaStream_t a = h->s_aux;
+    ILS_CK(cudaStreamWaitEvent(a, h->ev_acopy, 0));
+    ILS_CK(rhs_bar_f64(m, n, p, kk, h->A, m, B, ldb, h->bbar, n, a));
+    ILS_CK(sq_norms_cols_f64(n, kk, h->bbar, n, h->bnorm2, a));
+    ILS_CK(cudaEventRecord(h->ev_rhs, a));
+    ILS_CK(cudaStreamWaitEvent(s, h->ev_rhs, 0));
+  } else {
+    ILS_CK(rhs_bar_f64(m, n, p, kk, h->A, m, B, ldb, h->bbar, n, s));
+    ILS_CK(sq_norms_cols_f64(n, kk, h->bbar, n, h->bnorm2, s));
+  }
   if (h->opt.precision == ILS_FP64 && !h->mf) ILS_CK(gemv_cols_f64(n, kk, h->P, n, h->bbar, n, h->cvec, n, s));
   if (x0_zero) {
     ILS_CK(cudaMemsetAsync(h->X0, 0, sizeof(double) * n * kk, s));
@@ -1009,7 +1033,7 @@ ils_status create_handle(ils_handle* out, int64_t m, int64_t n, int64_t p, int64
   carve(h, real, work);
   if (h->overlap) {
     bool ok = cudaStreamCreateWithFlags(&h->s_aux, cudaStreamNonBlocking) == cudaSuccess;
-    for (cudaEvent_t* e : {&h->ev_start, &h->ev_g2})
+    for (cudaEvent_t* e : {&h->ev_start, &h->ev_g2, &h->ev_acopy, &h->ev_rhs})
       ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
       cudaGetLastError();
@@ -1116,6 +1140,7 @@ ils_status ils_refactor(ils_handle h, const double* A, int64_t lda, ils_stream_t
   if (!h || !A || lda < h->m || h->sparse) return ILS_ERR_INVALID_ARG;
   h->stream = (cudaStream_t)stream;
   cudaStream_t s = h->stream;
+  h->pending = false;
   ILS_CK(mark(h, 0));
   ILS_CK(copy_matrix_f64(h->m, h->n, A, lda, h->A, s));
   ils_status st = compute_setup(h);
@@ -1123,6 +1148,21 @@ ils_status ils_refactor(ils_handle h, const double* A, int64_t lda, ils_stream_t
   if (st == ILS_OK && h->opt.timing) collect_timings(h);
   if (st == ILS_OK) st = tune_handle(h);
   return st;
+}
+
+ils_status ils_refactor_async(ils_handle h, const double* A, int64_t lda, ils_stream_t stream) {
+  if (!h || !A || lda < h->m || h->sparse) return ILS_ERR_INVALID_ARG;
+  h->stream = (cudaStream_t)stream;
+  cudaStream_t s = h->stream;
+  h->pending = false;
+  ILS_CK(mark(h, 0));
+  ILS_CK(copy_matrix_f64(h->m, h->n, A, lda, h->A, s));
+  if (h->overlap) ILS_CK(cudaEventRecord(h->ev_acopy, s));
+  ils_status st = compute_setup(h);
+  if (st != ILS_OK) return st;
+  h->pending = true;
+  // The sweep shapes are tuned once per process; that first time waits for the setup.
+  return tune_handle(h);
 }
 
 ils_status ils_aq_product(ils_handle h, const double* x, double* v, int prec, ils_stream_t stream) {
@@ -1147,17 +1187,49 @@ int ils_tuned_shape(int64_t n, int64_t k, int bf16, int* warps, int* blocks) {
   return ils::ils_tuned_shape_impl(n, k, bf16, warps, blocks);
 }
 
+ils_status solve_many_now(ils_handle h, int64_t k, const double* B, int64_t ldb, double* X, int64_t ldx,
+                          int x0_zero, double tol, ils_info* info);
+
 ils_status ils_solve_many(ils_handle h, int64_t k, const double* B, int64_t ldb, double* X, int64_t ldx,
                           int x0_zero, double tol, ils_info* info, ils_stream_t stream) {
   if (!h || k < 0 || (k > 0 && (!B || !X)) || ldb < h->m || ldx < h->n || !(tol >= 0.0))
     return ILS_ERR_INVALID_ARG;
   h->stream = (cudaStream_t)stream;
+  if (h->pending) {
+    // The setup was enqueued without a wait: solve behind it, then read its status (the
+    // solve synchronized the stream).  A failed setup's status replaces the solve's; where
+    // an FP64 factorization had to settle a failed FP32 test and formed P and B again, the
+    // solve runs again on them.
+    ils_info agg;
+    std::memset(&agg, 0, sizeof(agg));
+    ils_status st = solve_many_now(h, k, B, ldb, X, ldx, x0_zero, tol, &agg);
+    h->pending = false;
+    bool redone = false;
+    const ils_status sst = setup_check(h, &redone);
+    if (sst == ILS_OK && h->opt.timing) collect_timings(h);
+    if (sst != ILS_OK) {
+      agg.status = sst;
+      if (info) *info = agg;
+      return sst;
+    }
+    if (redone) return ils_solve_many(h, k, B, ldb, X, ldx, x0_zero, tol, info, stream);
+    if (info) *info = agg;
+    return st;
+  }
   ils_info agg;
   std::memset(&agg, 0, sizeof(agg));
+  const ils_status st = solve_many_now(h, k, B, ldb, X, ldx, x0_zero, tol, &agg);
+  if (info) *info = agg;
+  return st;
+}
+
+// The solve proper (ils_solve_many after its checks).
+ils_status solve_many_now(ils_handle h, int64_t k, const double* B, int64_t ldb, double* X, int64_t ldx,
+                          int x0_zero, double tol, ils_info* info) {
+  ils_info& agg = *info;
   if (k >= kWideMinRhs && h->opt.method == ILS_SP && h->opt.precision == ILS_FP64 && !h->mf && !h->sparse) {
     ils_status st = wide_solve(h, k, B, ldb, X, ldx, x0_zero, tol, &agg);
     if (st != ILS_OK) agg.status = st;
-    if (info) *info = agg;
     return (ils_status)agg.status;
   }
   for (int64_t c0 = 0; c0 < k; c0 += kMaxRhsPerPass) {
@@ -1165,11 +1237,9 @@ ils_status ils_solve_many(ils_handle h, int64_t k, const double* B, int64_t ldb,
     ils_status st = sp_pass(h, c0, kk, B + c0 * ldb, ldb, X + c0 * ldx, ldx, x0_zero, tol, &agg);
     if (st != ILS_OK) {
       agg.status = st;
-      if (info) *info = agg;
       return st;
     }
   }
-  if (info) *info = agg;
   return (ils_status)agg.status;
 }
 

@@ -29,7 +29,7 @@ def libpath():
 def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ("ils_setup", "ils_solve", "ils_solve_many", "ils_destroy", "ils_options_default",
-                     "ils_status_string", "ils_refactor", "ils_setup_csr", "ils_batch_capture", "ils_batch_run"):
+                     "ils_status_string", "ils_refactor", "ils_refactor_async", "ils_setup_csr", "ils_batch_capture", "ils_batch_run"):
         assert required in names
 
 
