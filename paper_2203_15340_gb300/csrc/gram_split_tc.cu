@@ -483,7 +483,8 @@ constexpr int kFusePer = 32;
 
 __global__ void __launch_bounds__(kFuseThreads)
 exponent_split_kernel(int K, int n, const double* __restrict__ A, int64_t lda, int* __restrict__ exps,
-                      __nv_bfloat16* __restrict__ D, int64_t ldk, int32_t* err) {
+                      __nv_bfloat16* __restrict__ D, int64_t ldk, int32_t* err, double* __restrict__ Acopy,
+                      int64_t ldcopy) {
   const int j = blockIdx.x;
   long long bits[kFusePer];
   int mx = 0;
@@ -492,6 +493,13 @@ exponent_split_kernel(int K, int n, const double* __restrict__ A, int64_t lda, i
     const int r = threadIdx.x + kFuseThreads * i;
     bits[i] = r < K ? __double_as_longlong(__ldg(A + r + (int64_t)j * lda)) : 0ll;
     mx = max(mx, (int)((bits[i] >> 52) & 0x7FF));
+  }
+  if (Acopy) {  // the caller's copy of A, written while the column is in registers
+#pragma unroll
+    for (int i = 0; i < kFusePer; ++i) {
+      const int r = threadIdx.x + kFuseThreads * i;
+      if (r < K) Acopy[r + (int64_t)j * ldcopy] = __longlong_as_double(bits[i]);
+    }
   }
   for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   __shared__ int red[kFuseThreads / 32];
@@ -613,7 +621,7 @@ GramSplitWork gram_split_work(int64_t K, int64_t n) {
 
 cudaError_t gram_split_tc(int64_t K, int64_t n, const double* A, int64_t lda, double* C, int64_t ldc, void* slices,
                           double* partial, int* exps, int32_t* err, cudaStream_t s, cudaEvent_t mma_begin,
-                          cudaEvent_t mma_end) {
+                          cudaEvent_t mma_end, double* a_copy, int64_t ld_copy, cudaEvent_t copied) {
   if (n <= 0) return cudaSuccess;
   if (K <= 0) return cudaMemset2DAsync(C, sizeof(double) * ldc, 0, sizeof(double) * n, n, s);
   if (K > (int64_t)1 << 30 || n > 65535) return cudaErrorInvalidValue;
@@ -627,10 +635,14 @@ cudaError_t gram_split_tc(int64_t K, int64_t n, const double* A, int64_t lda, do
     if (e != cudaSuccess) return e;
   }
   if (K <= (int64_t)kFuseThreads * kFusePer) {
-    exponent_split_kernel<<<(unsigned)n, kFuseThreads, 0, s>>>((int)K, (int)n, A, lda, exps, D, ldk, err);
+    exponent_split_kernel<<<(unsigned)n, kFuseThreads, 0, s>>>((int)K, (int)n, A, lda, exps, D, ldk, err, a_copy,
+                                                               ld_copy);
     note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   } else {
+    if (a_copy && (e = cudaMemcpy2DAsync(a_copy, sizeof(double) * ld_copy, A, sizeof(double) * lda,
+                                         sizeof(double) * K, n, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+      return e;
     column_exponent_kernel<<<(unsigned)n, 256, 0, s>>>((int)K, (int)n, A, lda, exps);
     note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -640,6 +652,7 @@ cudaError_t gram_split_tc(int64_t K, int64_t n, const double* A, int64_t lda, do
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
 
+  if (copied && (e = cudaEventRecord(copied, s)) != cudaSuccess) return e;
   CUtensorMap map;
   const cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)n, (cuuint64_t)kSlices};
   const cuuint64_t strides[2] = {(cuuint64_t)ldk * 2, (cuuint64_t)ldk * 2 * (cuuint64_t)n};

@@ -377,7 +377,7 @@ ils_status compute_setup_sparse(ils_handle h, const int32_t* rowptr, const int32
 }
 
 // All setup products for the current contents of h->A.
-ils_status compute_setup_overlap(ils_handle h);
+ils_status compute_setup_overlap(ils_handle h, const double* src = nullptr, int64_t lda_src = 0);
 
 ils_status compute_setup(ils_handle h) {
   if (h->overlap) return compute_setup_overlap(h);
@@ -453,9 +453,19 @@ ils_status compute_products(ils_handle h) {
 // pivot that fails in FP32 sends setup_finish to the FP64 factorization of that matrix,
 // which then decides.  Where the inverse's tiles do not fit one cooperative wave, both
 // matrices are factored by Cholesky in FP32 instead and P is formed from the factor.
-ils_status compute_setup_overlap(ils_handle h) {
+//
+// With src, the new A is read from the caller's buffer (leading dimension lda_src) and the
+// digit splits write the handle's copy of it on the way (no separate copy pass); ev_acopy
+// is recorded on the handle's stream once A_1's rows are copied (A_2's are copied on the
+// second stream before its Gram).
+ils_status compute_setup_overlap(ils_handle h, const double* src, int64_t lda_src) {
   cudaStream_t s = h->stream, a = h->s_aux;
   const int64_t m = h->m, n = h->n, p = h->p, q = h->q;
+  const bool copy = src != nullptr;
+  if (!copy) {
+    src = h->A;
+    lda_src = m;
+  }
   ILS_CK(mark(h, 1));
   h->h_status[0] = 0;
   h->l64_valid = false;
@@ -465,9 +475,11 @@ ils_status compute_setup_overlap(ils_handle h) {
   ILS_CK(cudaEventRecord(h->ev_start, s));
   ILS_CK(cudaStreamWaitEvent(a, h->ev_start, 0));
   // Abar1 = A_1^T A_1 here, Abar2 = A_2^T A_2 there (Alg. 1 steps 2-3)
-  ILS_CK(gram_split_tc(p, n, h->A, m, h->G1, n, h->gs_slices, h->gs_partial, h->gs_exps, h->gs_err, s,
-                       timing_event(h, 6), timing_event(h, 7)));
-  ILS_CK(gram_split_tc(q, n, h->A + p, m, h->G2, n, h->gs_slices2, h->gs_partial2, h->gs_exps2, h->gs_err, a));
+  ILS_CK(gram_split_tc(p, n, src, lda_src, h->G1, n, h->gs_slices, h->gs_partial, h->gs_exps, h->gs_err, s,
+                       timing_event(h, 6), timing_event(h, 7), copy ? h->A : nullptr, m,
+                       copy ? h->ev_acopy : nullptr));
+  ILS_CK(gram_split_tc(q, n, src + p, lda_src, h->G2, n, h->gs_slices2, h->gs_partial2, h->gs_exps2, h->gs_err, a,
+                       nullptr, nullptr, copy ? h->A + p : nullptr, m));
   ILS_CK(cudaEventRecord(h->ev_g2, a));
   ILS_CK(mark(h, 2));
   ILS_CK(convert_f64_to_f32(n * n, h->G1, h->L32, s));  // Abar1, both triangles
@@ -1142,8 +1154,13 @@ ils_status ils_refactor(ils_handle h, const double* A, int64_t lda, ils_stream_t
   cudaStream_t s = h->stream;
   h->pending = false;
   ILS_CK(mark(h, 0));
-  ILS_CK(copy_matrix_f64(h->m, h->n, A, lda, h->A, s));
-  ils_status st = compute_setup(h);
+  ils_status st;
+  if (h->overlap) {  // the digit splits copy A into the handle
+    st = compute_setup_overlap(h, A, lda);
+  } else {
+    ILS_CK(copy_matrix_f64(h->m, h->n, A, lda, h->A, s));
+    st = compute_setup(h);
+  }
   if (st == ILS_OK) st = setup_finish(h);
   if (st == ILS_OK && h->opt.timing) collect_timings(h);
   if (st == ILS_OK) st = tune_handle(h);
@@ -1156,9 +1173,13 @@ ils_status ils_refactor_async(ils_handle h, const double* A, int64_t lda, ils_st
   cudaStream_t s = h->stream;
   h->pending = false;
   ILS_CK(mark(h, 0));
-  ILS_CK(copy_matrix_f64(h->m, h->n, A, lda, h->A, s));
-  if (h->overlap) ILS_CK(cudaEventRecord(h->ev_acopy, s));
-  ils_status st = compute_setup(h);
+  ils_status st;
+  if (h->overlap) {  // the digit splits copy A into the handle and record ev_acopy
+    st = compute_setup_overlap(h, A, lda);
+  } else {
+    ILS_CK(copy_matrix_f64(h->m, h->n, A, lda, h->A, s));
+    st = compute_setup(h);
+  }
   if (st != ILS_OK) return st;
   h->pending = true;
   // The sweep shapes are tuned once per process; that first time waits for the setup.

@@ -153,10 +153,13 @@ struct GramSplitWork {
 GramSplitWork gram_split_work(int64_t K, int64_t n);
 // C = A^T A for the K x n column-major A (lda), both triangles written.  err (device int)
 // is set to 1 on a tensor-pipeline timeout and 2 on a non-finite input.  mma_begin /
-// mma_end, when set, are recorded on s around the tensor-core launch alone.
+// mma_end, when set, are recorded on s around the tensor-core launch alone.  With a_copy,
+// A is also copied there (leading dimension ld_copy), by the digit split where it can, and
+// `copied` (if set) is recorded once the copy is complete.
 cudaError_t gram_split_tc(int64_t K, int64_t n, const double* A, int64_t lda, double* C, int64_t ldc,
                           void* slices, double* partial, int* exps, int32_t* err, cudaStream_t s,
-                          cudaEvent_t mma_begin = nullptr, cudaEvent_t mma_end = nullptr);
+                          cudaEvent_t mma_begin = nullptr, cudaEvent_t mma_end = nullptr, double* a_copy = nullptr,
+                          int64_t ld_copy = 0, cudaEvent_t copied = nullptr);
 
 // ---- matrix-free A_2 products (stream.cu) ---------------------------------------------------
 // Row-major copy of A_2 (q x n, column-major source with leading dimension lda) with rows
