@@ -146,6 +146,32 @@ __device__ void fs_sweep(int64_t n, const TM* M, const TV* v, const float* add, 
   }
 }
 
+// The same product with the warp's row of M held in registers (R entries per lane, one row
+// per warp, n <= 32 R); vs is zero past n.
+template <int R, typename TV>
+__device__ void fs_sweep_reg(int64_t n, int64_t i, const float (&m)[R], const TV* v, const float* add, float* out,
+                             double* x, float* vs) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t j = threadIdx.x; j < 32 * R; j += kFsThreads) vs[j] = j < n ? fs_vec(v, j) : 0.f;
+  __syncthreads();
+  if (i >= n) return;
+  float acc0 = 0.f, acc1 = 0.f;
+#pragma unroll
+  for (int u = 0; u < R; u += 2) {
+    acc0 = fmaf(m[u], vs[lane + 32 * u], acc0);
+    if (u + 1 < R) acc1 = fmaf(m[u + 1], vs[lane + 32 * (u + 1)], acc1);
+  }
+  const float s = fs_warp_sum(acc0 + acc1);
+  if (lane == 0) {
+    const float o = s + (add ? __ldcg(add + i) : 0.f);
+    out[i] = o;
+    if (x) x[i] += (double)o;
+  }
+}
+
+// R > 0: every warp owns one row and keeps that row of H, P and B in registers for the
+// whole solve (n <= 32 R); R = 0: rows are streamed from L2 in every phase.
+template <int R>
 __global__ void __launch_bounds__(kFsThreads) mixed_solve_fused_kernel(FusedArgs a) {
   const int64_t n = a.n;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -159,12 +185,43 @@ __global__ void __launch_bounds__(kFsThreads) mixed_solve_fused_kernel(FusedArgs
   int64_t it = *((volatile int64_t*)&a.st->iters);
   const int64_t max_outer = a.st->max_outer;
   const double target = a.tol2 * a.bnorm2[0];
+  const int64_t row = (int64_t)blockIdx.x * kFsWarps + w;  // the warp's row (R > 0)
+  constexpr int RR = R > 0 ? R : 1;
+  double hr[RR];
+  float pr[RR], br[RR];
+  if (R > 0) {
+#pragma unroll
+    for (int u = 0; u < RR; ++u) {
+      const int64_t j = lane + 32 * u;
+      const bool ok = row < n && j < n;
+      hr[u] = ok ? __ldg(a.H + row * n + j) : 0.0;
+      pr[u] = ok ? __ldg(a.P32 + row * n + j) : 0.f;
+      br[u] = ok ? (a.bf16 ? __bfloat162float(a.Bt16[row * n + j]) : __ldg(a.Bt32 + row * n + j)) : 0.f;
+    }
+  }
   for (;;) {
     // r = bbar - H x (FP64) and this CTA's share of ||r||^2
     double rp = 0.0;
-    for (int64_t j = threadIdx.x; j < n; j += kFsThreads) xs[j] = __ldcg(a.x + j);
+    const int64_t nst = R > 0 ? 32 * R : n;  // staged entries (zero past n)
+    for (int64_t j = threadIdx.x; j < nst; j += kFsThreads) xs[j] = j < n ? __ldcg(a.x + j) : 0.0;
     __syncthreads();
-    for (int64_t i = (int64_t)blockIdx.x * kFsWarps + w; i < n; i += tw) {
+    if (R > 0) {
+      if (row < n) {
+        double acc0 = 0.0, acc1 = 0.0;
+#pragma unroll
+        for (int u = 0; u < RR; u += 2) {
+          acc0 = fma(hr[u], xs[lane + 32 * u], acc0);
+          if (u + 1 < RR) acc1 = fma(hr[u + 1], xs[lane + 32 * (u + 1)], acc1);
+        }
+        const double s = fs_warp_sum(acc0 + acc1);
+        if (lane == 0) {
+          const double r = a.bbar[row] - s;
+          a.r[row] = r;
+          rp = r * r;
+        }
+      }
+    }
+    for (int64_t i = (int64_t)blockIdx.x * kFsWarps + w; R == 0 && i < n; i += tw) {
       const double* hrow = a.H + i * n;
       double acc[4] = {0.0, 0.0, 0.0, 0.0};
       int64_t j = lane;
@@ -221,13 +278,15 @@ __global__ void __launch_bounds__(kFsThreads) mixed_solve_fused_kernel(FusedArgs
     ++it;
     // d_1 = P r; d_{s+1} = B d_s + d_1; the last sweep adds d to x
     const bool one = a.sweeps == 1;
-    fs_sweep(n, a.P32, (const double*)a.r, (const float*)nullptr, a.c32, one ? a.x : nullptr, vs);
+    if (R > 0) fs_sweep_reg<RR>(n, row, pr, (const double*)a.r, (const float*)nullptr, a.c32, one ? a.x : nullptr, vs);
+    else fs_sweep(n, a.P32, (const double*)a.r, (const float*)nullptr, a.c32, one ? a.x : nullptr, vs);
     if (!fs_barrier(a)) return;
     const float* dcur = a.c32;
     for (int sw = 1; sw < a.sweeps; ++sw) {
       float* dn = a.d32[sw & 1];
       double* xu = sw + 1 == a.sweeps ? a.x : nullptr;
-      if (a.bf16) fs_sweep(n, a.Bt16, dcur, a.c32, dn, xu, vs);
+      if (R > 0) fs_sweep_reg<RR>(n, row, br, dcur, a.c32, dn, xu, vs);
+      else if (a.bf16) fs_sweep(n, a.Bt16, dcur, a.c32, dn, xu, vs);
       else fs_sweep(n, a.Bt32, dcur, a.c32, dn, xu, vs);
       if (!fs_barrier(a)) return;
       dcur = dn;
@@ -247,14 +306,21 @@ cudaError_t mixed_solve_fused(const SpIterArgs& sa, const MixedArgs& ma, int pre
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mixed_solve_fused_kernel, kFsThreads,
-                                                                           sizeof(double) * 4096);
+    for (auto k : {mixed_solve_fused_kernel<0>, mixed_solve_fused_kernel<4>, mixed_solve_fused_kernel<8>,
+                   mixed_solve_fused_kernel<16>}) {
+      int o = 0;
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, kFsThreads, sizeof(double) * 4096);
+      occ = occ == 0 ? o : std::min(occ, o);
+    }
     if (e != cudaSuccess) return e;
     if (!coop || occ < 1) return cudaErrorNotSupported;
     max_grid = sms;
   }
   // a warp per row where n allows: fewer CTAs make each grid barrier cheaper
   const int grid = (int)std::min<int64_t>(max_grid, std::max<int64_t>(1, (sa.n + kFsWarps - 1) / kFsWarps));
+  // rows in registers when every warp has at most one row of at most 512 entries
+  const bool one_row = (int64_t)grid * kFsWarps >= sa.n;
+  const int R = !one_row ? 0 : (sa.n <= 128 ? 4 : (sa.n <= 256 ? 8 : (sa.n <= 512 ? 16 : 0)));
   FusedArgs a;
   a.n = sa.n;
   a.sweeps = ma.sweeps;
@@ -282,14 +348,19 @@ cudaError_t mixed_solve_fused(const SpIterArgs& sa, const MixedArgs& ma, int pre
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid, 1, 1);
   cfg.blockDim = dim3(kFsThreads, 1, 1);
-  cfg.dynamicSmemBytes = sizeof(double) * (size_t)sa.n;
+  cfg.dynamicSmemBytes = sizeof(double) * (size_t)std::max<int64_t>(sa.n, 32 * R);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, mixed_solve_fused_kernel, a);
+  switch (R) {
+    case 4: e = cudaLaunchKernelEx(&cfg, mixed_solve_fused_kernel<4>, a); break;
+    case 8: e = cudaLaunchKernelEx(&cfg, mixed_solve_fused_kernel<8>, a); break;
+    case 16: e = cudaLaunchKernelEx(&cfg, mixed_solve_fused_kernel<16>, a); break;
+    default: e = cudaLaunchKernelEx(&cfg, mixed_solve_fused_kernel<0>, a); break;
+  }
   note_launch();
   return e;
 }
