@@ -1416,6 +1416,21 @@ cudaError_t axpby_mat_f64(int64_t n, double alpha, const double* X, double beta,
   return cudaGetLastError();
 }
 
+__global__ void hdiff_kernel(int64_t total, const double* __restrict__ X, const double* __restrict__ Y,
+                             double* __restrict__ Z, float* __restrict__ Z32) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const double z = X[e] - Y[e];
+    Z[e] = z;
+    Z32[e] = (float)z;
+  }
+}
+
+cudaError_t diff_mat_f64_f32(int64_t n, const double* X, const double* Y, double* Z, float* Z32, cudaStream_t s) {
+  hdiff_kernel<<<grid_for(n * n, 256), 256, 0, s>>>(n * n, X, Y, Z, Z32);
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t copy_lower_zero_upper_f64(int64_t n, const double* L, double* dst, int64_t ldd, cudaStream_t s) {
   copy_lower_kernel<<<grid_for(n * n, 256), 256, 0, s>>>(n, L, dst, ldd);
   note_launch();

@@ -480,12 +480,12 @@ ils_status compute_setup_overlap(ils_handle h, const double* src, int64_t lda_sr
                        copy ? h->ev_acopy : nullptr));
   ILS_CK(gram_split_tc(q, n, src + p, lda_src, h->G2, n, h->gs_slices2, h->gs_partial2, h->gs_exps2, h->gs_err, a,
                        nullptr, nullptr, copy ? h->A + p : nullptr, m));
+  ILS_CK(convert_f64_to_f32(n * n, h->G2, h->G2_32, a));  // Abar2 in FP32, for B
   ILS_CK(cudaEventRecord(h->ev_g2, a));
   ILS_CK(mark(h, 2));
   ILS_CK(convert_f64_to_f32(n * n, h->G1, h->L32, s));  // Abar1, both triangles
   ILS_CK(cudaStreamWaitEvent(s, h->ev_g2, 0));
-  ILS_CK(axpby_mat_f64(n, 1.0, h->G1, -1.0, h->G2, h->H, s));
-  ILS_CK(convert_f64_to_f32(n * n, h->H, h->H32, s));
+  ILS_CK(diff_mat_f64_f32(n, h->G1, h->G2, h->H, h->H32, s));  // H = Abar1 - Abar2, and in FP32
   ILS_CK(mark(h, 3));
   const float* mats[2] = {h->L32, h->H32};
   float* outs[2] = {h->P32, nullptr};
@@ -504,7 +504,7 @@ ils_status compute_setup_overlap(ils_handle h, const double* src, int64_t lda_sr
   ILS_CK(cudaMemcpyAsync(h->h_status + 3, h->dstatus2, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   ILS_CK(cudaMemcpyAsync(h->h_status + 1, h->gs_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   if (inverted)
-    ILS_CK(mixed_setup_b(n, h->G2, h->opt.precision, h->P32, h->G2_32, h->Bt32, h->Bt16, s));
+    ILS_CK(mixed_setup_b(n, nullptr, h->opt.precision, h->P32, h->G2_32, h->Bt32, h->Bt16, s));
   else
     ILS_CK(mixed_setup(n, nullptr, h->G2, h->opt.precision, h->L32, h->P32, h->G2_32, h->Bt32, h->Bt16,
                        reinterpret_cast<float*>(h->Dinv), s));

@@ -89,7 +89,9 @@ cudaError_t copy_matrix_f64(int64_t m, int64_t n, const double* src, int64_t lda
 // Elementwise helpers.
 cudaError_t set_identity_f64(int64_t n, double* M, int64_t ld, cudaStream_t s);
 cudaError_t axpby_mat_f64(int64_t n, double alpha, const double* X, double beta, const double* Y,
-                          double* Z, cudaStream_t s);  // Z = alpha X + beta Y, n*n contiguous
+                          double* Z, cudaStream_t s);
+// Z = X - Y (n x n, FP64) and its FP32 rounding Z32, in one pass.
+cudaError_t diff_mat_f64_f32(int64_t n, const double* X, const double* Y, double* Z, float* Z32, cudaStream_t s);  // Z = alpha X + beta Y, n*n contiguous
 cudaError_t copy_lower_zero_upper_f64(int64_t n, const double* L, double* dst, int64_t ldd,
                                       cudaStream_t s);
 cudaError_t sq_norms_cols_f64(int64_t n, int64_t k, const double* X, int64_t ldx, double* out,

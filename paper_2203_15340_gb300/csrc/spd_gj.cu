@@ -116,37 +116,40 @@ __device__ __forceinline__ int gj_pivot_code(float d) {
   return 0;
 }
 
-// Warps 0-3: sweeps of all 32 pivots of the tile T (in place), leaving -D^{-1}; lane =
-// row, warp w holding columns 8w .. 8w+7 of it in registers.  The pivots are swept two at
+// kSweepWarps warps: sweeps of all 32 pivots of the tile T (in place), leaving -D^{-1};
+// lane = row, warp w holding its kSweepCols columns of it in registers.  The pivots are swept two at
 // a time (a 2 x 2 block pivot, which equals two successive scalar sweeps): with the block
 // M = [a b; b d] of pivots c, c+1,
 //   rows i off the pivots:  [t0 t1] = [a_ic a_i,c+1] M^{-1},  a_iq -= t0 a_cq + t1 a_c+1,q,
 //   pivot rows:             a_Pq <- M^{-1} a_Pq,  the block itself <- -M^{-1}.
 // A sweep keeps the matrix symmetric, so pivot rows c, c+1 are columns c, c+1: the warp
 // holding them posts both to `prow` (4 x 32 floats, alternating halves), a barrier of the
-// four warps follows, and every lane reads its two entries and the rows' entries of its
+// sweeping warps follows, and every lane reads its two entries and the rows' entries of its
 // warp's columns.  Every lane applies the same multiply and two multiply-adds per entry.
 // The block's scalar pivots are a and det / a; one that is not positive and finite is
 // recorded (a is replaced by 1 and det by a, so that the launch runs to its end).
+constexpr int kSweepWarps = 4;
+constexpr int kSweepCols = 32 / kSweepWarps;
+
 __device__ void gj_sweep_pivot(float* T, float* prow, int32_t* status) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;  // w < 4
-  const int q0 = 8 * w;
-  float v[8];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;  // w < kSweepWarps
+  const int q0 = kSweepCols * w;
+  float v[kSweepCols];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) v[q] = T[lane * kGjPad + q0 + q];
+  for (int q = 0; q < kSweepCols; ++q) v[q] = T[lane * kGjPad + q0 + q];
 #pragma unroll
   for (int c = 0; c < 32; c += 2) {
     float* pr = prow + ((c >> 1) & 1) * 64;
-    const bool owner = w == (c >> 3);
+    const bool owner = w == c / kSweepCols;
     if (owner) {
-      pr[lane] = v[c & 7];
-      pr[32 + lane] = v[(c + 1) & 7];
+      pr[lane] = v[c % kSweepCols];
+      pr[32 + lane] = v[(c + 1) % kSweepCols];
     }
-    asm volatile("bar.sync 1, 128;" ::: "memory");
+    asm volatile("bar.sync 1, %0;" ::"r"(32 * kSweepWarps) : "memory");
     const float ai0 = pr[lane], ai1 = pr[32 + lane];  // a_ic, a_i,c+1
-    float r0[8], r1[8];                               // a_cq, a_c+1,q of this warp's columns
+    float r0[kSweepCols], r1[kSweepCols];            // a_cq, a_c+1,q of this warp's columns
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < kSweepCols / 4; ++h) {
       const float4 w0 = reinterpret_cast<const float4*>(pr + q0)[h];
       const float4 w1 = reinterpret_cast<const float4*>(pr + 32 + q0)[h];
       r0[4 * h] = w0.x;
@@ -173,14 +176,14 @@ __device__ void gj_sweep_pivot(float* T, float* prow, int32_t* status) {
     const float beta0 = p0 ? m00 : (p1 ? m01 : -t0);
     const float beta1 = p0 ? m01 : (p1 ? m11 : -t1);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = fmaf(beta1, r1[q], fmaf(beta0, r0[q], alpha * v[q]));
+    for (int q = 0; q < kSweepCols; ++q) v[q] = fmaf(beta1, r1[q], fmaf(beta0, r0[q], alpha * v[q]));
     if (owner) {  // the pivot columns themselves
-      v[c & 7] = p0 ? -m00 : (p1 ? -m01 : t0);
-      v[(c + 1) & 7] = p0 ? -m01 : (p1 ? -m11 : t1);
+      v[c % kSweepCols] = p0 ? -m00 : (p1 ? -m01 : t0);
+      v[(c + 1) % kSweepCols] = p0 ? -m01 : (p1 ? -m11 : t1);
     }
   }
 #pragma unroll
-  for (int q = 0; q < 8; ++q) T[lane * kGjPad + q0 + q] = v[q];
+  for (int q = 0; q < kSweepCols; ++q) T[lane * kGjPad + q0 + q] = v[q];
 }
 
 // acc[q] += sum_m L(r, m) R(m, c0 + q) for the thread's outputs r = tid / 8,
@@ -228,7 +231,7 @@ __device__ __forceinline__ void gj_post(float* dst, const float* T, bool transpo
 __device__ void gj_post_for(const GjArgs& a, int m, int i, int j, int k1, float* T, float* prow) {
   const int nb = a.nb;
   if (i == k1 && j == k1) {
-    if (threadIdx.x < 128) gj_sweep_pivot(T, prow, a.status[m]);  // T := -D^{-1}
+    if (threadIdx.x < 32 * kSweepWarps) gj_sweep_pivot(T, prow, a.status[m]);  // T := -D^{-1}
     __syncthreads();
     gj_post(a.D[m] + (size_t)k1 * 1024, T, false, -1.f);
     gj_raise(a.flag[m] + (size_t)nb * nb + k1);
