@@ -476,10 +476,10 @@ __global__ void split_kernel(int K, int n, const double* __restrict__ A, int64_t
   }
 }
 
-// The two kernels above in one pass for K <= 512 * 32: one CTA per column keeps the
+// The two kernels above in one pass for K <= 1024 * 16: one CTA per column keeps the
 // column's bit patterns in registers, reduces the largest exponent field, and splits.
-constexpr int kFuseThreads = 512;
-constexpr int kFusePer = 32;
+constexpr int kFuseThreads = 1024;
+constexpr int kFusePer = 16;
 
 __global__ void __launch_bounds__(kFuseThreads)
 exponent_split_kernel(int K, int n, const double* __restrict__ A, int64_t lda, int* __restrict__ exps,
