@@ -17,9 +17,10 @@
 //      K_chunk 2^(2 beta) < 2^24, so the FP32 accumulation is exact.  On the diagonal
 //      tiles of the Gram, D_u^T D_t is the transpose of D_t^T D_u: it is not formed, the
 //      epilogue stores the transpose in its place.
-//   4. The epilogue stores each exact product as it stands (FP32); a reduction scales it by
-//      2^{e_i + e_j - beta (t + u)} into FP64 (an exponent shift on the bit pattern) and
-//      adds the products of a tile in FP64 in a fixed order (deterministic).
+//   4. The epilogue stores each exact product as it stands (FP32).  A reduction adds the
+//      products of equal t + u exactly as 64-bit integers, scales each of the 10 group
+//      sums by 2^{e_i + e_j - beta (t + u)} into FP64 and adds them in order of t + u
+//      (a fixed order: deterministic).
 //
 // The tcgen05 kernel is warp-specialised: warp 0 issues TMA loads of 128 x 64 BF16 tiles
 // (128B swizzle) of up to four digit slices into a 3-stage shared-memory ring, warp 1
@@ -134,17 +135,6 @@ __device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&v)
         "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-// (double)x * 2^sc for an FP32 x holding an exact integer, built from x's bit pattern with
-// integer operations (sign, rebased exponent, widened significand).
-__device__ __forceinline__ double scaled_f32_to_f64(uint32_t xb, int sc) {
-  if ((xb & 0x7FFFFFFFu) == 0u) return 0.0;
-  const unsigned long long sign = (unsigned long long)(xb >> 31) << 63;
-  const int ef = (int)((xb >> 23) & 0xFF);  // integers >= 1 are normal floats
-  const unsigned long long exp64 = (unsigned long long)(ef - 127 + 1023 + sc) << 52;
-  const unsigned long long man = (unsigned long long)(xb & 0x7FFFFFu) << 29;
-  return __longlong_as_double((long long)(sign | exp64 | man));
 }
 
 struct SplitParams {
@@ -542,19 +532,27 @@ exponent_split_kernel(int K, int n, const double* __restrict__ A, int64_t lda, i
   }
 }
 
-// C(i,j) for the upper tiles: each stored product (an exact integer in FP32) is scaled by
-// 2^{e_i + e_j - beta (t + u)} into FP64; per K chunk the products of each t are added in
-// u order and those sums in t order (a fixed order), then mirrored.  Every tile has all its ordered-pair
-// slots (a diagonal tile's transposed slots were written by the epilogue).
+// C(i,j) for the upper tiles.  Every stored product is an exact integer held in FP32.
+// The products of equal t + u carry the same scale 2^{e_i + e_j - beta (t + u)}, so they
+// are added exactly in integers first (at most 10 terms below 2^24 each per K chunk), and
+// only the 10 scaled group sums are added in FP64, in order of t + u (a fixed order, and
+// fewer roundings than one FP64 addition per product).  Then the tile is mirrored.  Every
+// tile has all its ordered-pair slots (a diagonal tile's transposed slots were written by
+// the epilogue).  A thread takes two adjacent rows of one column (8-byte loads).
+constexpr int kScales = kSlices;  // t + u = 2 .. S + 1
+
 __global__ void split_reduce_kernel(SplitParams P, double* __restrict__ C, int64_t ldc) {
   const int items_per_tile = slots_per_tile() * P.n_kchunks;
   const int n_upper = P.n_tiles * (P.n_tiles + 1) / 2;
-  const int64_t total = (int64_t)n_upper * kBM * kBN;
+  const int64_t total2 = (int64_t)n_upper * kBM * kBN / 2;  // pairs of rows
   const uint32_t* part = reinterpret_cast<const uint32_t*>(P.partial);
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    int tile = (int)(e / (kBM * kBN));
-    const int local = (int)(e % (kBM * kBN));
-    const int row = local % kBM, col = local / kBM;
+  const size_t tile_elems = (size_t)kBM * kBN;
+  for (int64_t e2 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e2 < total2;
+       e2 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = 2 * e2;
+    const int tile = (int)(e / tile_elems);
+    const int local = (int)(e % tile_elems);
+    const int row = local % kBM, col = local / kBM;  // rows row, row + 1 of column col
     int r = 0;
     int tt = tile;
     while (tt >= P.n_tiles - r) {
@@ -563,28 +561,36 @@ __global__ void split_reduce_kernel(SplitParams P, double* __restrict__ C, int64
     }
     const int bi = r, bj = r + tt;
     const int gi = bi * kBM + row, gj = bj * kBN + col;
-    if (gi >= P.n || gj >= P.n || (bi == bj && gi > gj)) continue;
-    const int eij = P.exps[gi] + P.exps[gj];
-    const uint32_t* base = part + (size_t)tile * items_per_tile * kBM * kBN + local;
-    const size_t slot_stride = (size_t)P.n_kchunks * kBM * kBN;
-    double s = 0.0;
+    if (gj >= P.n || gi >= P.n || (bi == bj && gi > gj)) continue;  // the second row is past both too
+    const uint32_t* base = part + (size_t)tile * items_per_tile * tile_elems + local;
+    long long V[2][kScales];
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int g = 0; g < kScales; ++g) V[q][g] = 0;
     for (int kc = 0; kc < P.n_kchunks; ++kc) {
-      // every slot's load issued at once; one partial sum per t, added in t order
-      double acc[kSlices];
       int slot = 0;
 #pragma unroll
       for (int t = 1; t <= kSlices; ++t) {
-        acc[t - 1] = 0.0;
 #pragma unroll
-        for (int u = 1; u <= kSlices + 1 - t; ++u, ++slot)
-          acc[t - 1] += scaled_f32_to_f64(__ldcg(base + slot * slot_stride + (size_t)kc * kBM * kBN),
-                                          eij - kBeta * (t + u));
+        for (int u = 1; u <= kSlices + 1 - t; ++u, ++slot) {
+          const uint2 w = __ldcg(reinterpret_cast<const uint2*>(base + ((size_t)slot * P.n_kchunks + kc) * tile_elems));
+          V[0][t + u - 2] += (long long)__float2int_rz(__uint_as_float(w.x));
+          V[1][t + u - 2] += (long long)__float2int_rz(__uint_as_float(w.y));
+        }
       }
-#pragma unroll
-      for (int t = 0; t < kSlices; ++t) s += acc[t];
     }
-    C[gi + (int64_t)gj * ldc] = s;
-    C[gj + (int64_t)gi * ldc] = s;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int gq = gi + q;
+      if (gq >= P.n || (bi == bj && gq > gj)) continue;
+      const int eij = P.exps[gq] + P.exps[gj];
+      double s = 0.0;
+#pragma unroll
+      for (int g = 0; g < kScales; ++g) s += ldexp((double)V[q][g], eij - kBeta * (g + 2));
+      C[gq + (int64_t)gj * ldc] = s;
+      C[gj + (int64_t)gq * ldc] = s;
+    }
   }
 }
 
