@@ -163,7 +163,8 @@ ils_status ils_refactor(ils_handle h, const double* A, int64_t lda, ils_stream_t
  * (NOT_SPD, NONFINITE, TIMEOUT, ...) replaces the solve's and x is unspecified; where an
  * FP64 factorization has to settle a failed FP32 pivot test, that solve performs it and
  * solves again.  On a mixed-precision single handle with split Grams the solve's
- * A^T J b (Alg. 1 step 4) runs on a second stream beside the setup's last products.
+ * A^T J b (Alg. 1 step 4) runs on a second stream beside the setup's last products, and
+ * the FP32 test of H (condition (1.3)) on a third stream beside the solve.
  * Timings (ils_get_timings) are read at that solve.  Errors: INVALID_ARG, CUDA. */
 ils_status ils_refactor_async(ils_handle h, const double* A, int64_t lda, ils_stream_t stream);
 
@@ -198,10 +199,13 @@ ils_status ils_get_matrix(ils_handle h, int which, double* dst, int64_t ldd, ils
 /* Setup phase times of the last ils_setup / ils_refactor on h, in milliseconds,
  * measured with CUDA events on the handle's stream when options.timing != 0
  * (zeros otherwise).  out [host] receives min(count, 7) values:
- *   0 Abar1 Gram, 1 the wait for the Abar2 Gram (its own time where it runs alone),
+ *   0 Abar1 Gram, 1 the wait for the Abar2 Gram (its own time where it runs alone; on a
+ *     mixed-precision single handle the FP32 copy of Abar1, the Abar2 Gram running on),
  *   2 the factor step: the Cholesky factorizations of Abar1 and H, or on a mixed-precision
- *     single handle the one-launch FP32 inverse of Abar1 with the test of H,
- *   3 the products that follow (P and B, or B alone after the inverse),
+ *     single handle the one-launch FP32 inverse of Abar1 (H is tested on another stream),
+ *   3 the products that follow (P and B, or B alone after the inverse), with any wait for
+ *     the Abar2 Gram (the FP32 test of H of a mixed single handle runs beside them and
+ *     the next solve, and is not part of any phase),
  *   4 the whole setup, 5 the copy of A, 6 the tensor-core kernel of the Abar1 Gram alone
  *   (split Grams only).
  * Returns the number of values written, or -1 on a bad argument. */

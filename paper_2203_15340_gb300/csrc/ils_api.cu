@@ -78,19 +78,21 @@ struct ils_handle_s {
   int32_t* sp_err = nullptr;
   double* stash64 = nullptr;   // 2 x 1024: the Cholesky panels' diagonal-block stash
   // Overlapped mixed setup (single handles, split Grams): A_2^T A_2 runs on a second stream
-  // beside A_1^T A_1; Abar1 is then inverted and H tested in FP32 in one launch (a failed
-  // FP32 pivot is settled by the FP64 factorization).
+  // beside A_1^T A_1; Abar1 is inverted in FP32 on the handle's stream while a third stream
+  // forms H and tests it in FP32 (a failed FP32 pivot is settled by the FP64 factorization).
   bool overlap = false;
   bool l64_valid = true;  // L holds the FP64 factor of the current Abar1 (else formed on demand)
   bool pending = false;   // a setup enqueued by ils_refactor_async whose status is not yet read
-  cudaStream_t s_aux = nullptr;
-  cudaEvent_t ev_start = nullptr, ev_g2 = nullptr;
+  cudaStream_t s_aux = nullptr, s_h = nullptr;  // A_2^T A_2 and A^T J b; H and its test
+  cudaEvent_t ev_start = nullptr, ev_g2 = nullptr, ev_g1 = nullptr;
+  cudaEvent_t ev_hd = nullptr, ev_h = nullptr;  // H formed; H tested (status copied)
   cudaEvent_t ev_acopy = nullptr, ev_rhs = nullptr;  // A copied; A^T J b ready (solve after an async setup)
   void* gs_slices2 = nullptr;
   double* gs_partial2 = nullptr;
   int* gs_exps2 = nullptr;
   float* H32 = nullptr;
-  float* gj = nullptr;  // exchange buffers of the explicit FP32 inverse
+  float* gj = nullptr;   // exchange buffers of the explicit FP32 inverse of Abar1
+  float* gj2 = nullptr;  // and of the FP32 test of H
   float* stash32 = nullptr;
   int32_t* dstatus2 = nullptr;
   SolveState* st = nullptr;
@@ -247,6 +249,7 @@ void carve(ils_handle h, Carver& c, size_t work_elems) {
       h->H32 = c.take<float>((size_t)h->n * (size_t)h->n);
       h->stash32 = c.take<float>(2 * 1024);  // panel flags of the FP32 factorizations
       h->gj = c.take<float>(spd_inverse_scratch_floats(h->n));
+      h->gj2 = c.take<float>(spd_inverse_scratch_floats(h->n));
       h->dstatus2 = c.take<int32_t>(1);
     }
   }
@@ -446,13 +449,14 @@ ils_status compute_products(ils_handle h) {
 }
 
 // Mixed precision with split Grams on one handle: the second stream computes Abar2 while
-// the handle's stream computes Abar1; then one launch forms P = Abar1^{-1} (Alg. 1 step 2)
-// by block Gauss-Jordan elimination and, in lockstep, tests H = Abar1 - Abar2 for
-// condition (1.3) the same way, and B follows.  Both run in FP32: the correction sweeps
-// only need P to FP32 accuracy (the FP64 residuals of the refinement supply the rest).  A
-// pivot that fails in FP32 sends setup_finish to the FP64 factorization of that matrix,
-// which then decides.  Where the inverse's tiles do not fit one cooperative wave, both
-// matrices are factored by Cholesky in FP32 instead and P is formed from the factor.
+// the handle's stream computes Abar1.  The handle's stream then forms P = Abar1^{-1}
+// (Alg. 1 step 2) by block Gauss-Jordan elimination, while a third stream, once both Grams
+// are done, forms H = Abar1 - Abar2 and tests it for condition (1.3) the same way; B
+// follows P.  Both eliminations run in FP32: the correction sweeps only need P to FP32
+// accuracy (the FP64 residuals of the refinement supply the rest).  A pivot that fails in
+// FP32 sends setup_finish to the FP64 factorization of that matrix, which then decides.
+// Where the inverse's tiles do not fit one cooperative wave, both matrices are factored by
+// Cholesky in FP32 on the handle's stream instead and P is formed from the factor.
 //
 // With src, the new A is read from the caller's buffer (leading dimension lda_src) and the
 // digit splits write the handle's copy of it on the way (no separate copy pass); ev_acopy
@@ -466,6 +470,8 @@ ils_status compute_setup_overlap(ils_handle h, const double* src, int64_t lda_sr
     src = h->A;
     lda_src = m;
   }
+  // The previous setup's test of H may still run on the third stream: it reads G1, G2 and H32.
+  ILS_CK(cudaStreamWaitEvent(s, h->ev_h, 0));
   ILS_CK(mark(h, 1));
   h->h_status[0] = 0;
   h->l64_valid = false;
@@ -482,32 +488,53 @@ ils_status compute_setup_overlap(ils_handle h, const double* src, int64_t lda_sr
                        nullptr, nullptr, copy ? h->A + p : nullptr, m));
   ILS_CK(convert_f64_to_f32(n * n, h->G2, h->G2_32, a));  // Abar2 in FP32, for B
   ILS_CK(cudaEventRecord(h->ev_g2, a));
+  ILS_CK(cudaEventRecord(h->ev_g1, s));
   ILS_CK(mark(h, 2));
   ILS_CK(convert_f64_to_f32(n * n, h->G1, h->L32, s));  // Abar1, both triangles
-  ILS_CK(cudaStreamWaitEvent(s, h->ev_g2, 0));
-  ILS_CK(diff_mat_f64_f32(n, h->G1, h->G2, h->H, h->H32, s));  // H = Abar1 - Abar2, and in FP32
   ILS_CK(mark(h, 3));
-  const float* mats[2] = {h->L32, h->H32};
-  float* outs[2] = {h->P32, nullptr};
-  int32_t* sts[2] = {h->dstatus, h->dstatus2};
-  const cudaError_t gj = spd_inverse_f32(n, 2, mats, outs, h->gj, sts, s);
+  // P = Abar1^{-1} right after the Abar1 Gram; H = Abar1 - Abar2 is formed and tested on
+  // the third stream once both Grams are done (the second stream stays free for A^T J b).
+  const float* mat1[2] = {h->L32, nullptr};
+  float* out1[2] = {h->P32, nullptr};
+  int32_t* st1[2] = {h->dstatus, nullptr};
+  const cudaError_t gj = spd_inverse_f32(n, 1, mat1, out1, h->gj, st1, s);
   const bool inverted = gj == cudaSuccess;
-  if (!inverted) {
+  if (inverted) {
+    cudaStream_t t = h->s_h;
+    ILS_CK(cudaStreamWaitEvent(t, h->ev_g1, 0));
+    ILS_CK(cudaStreamWaitEvent(t, h->ev_g2, 0));
+    ILS_CK(diff_mat_f64_f32(n, h->G1, h->G2, h->H, h->H32, t));  // H = Abar1 - Abar2, and in FP32
+    ILS_CK(cudaEventRecord(h->ev_hd, t));
+    // The SPD test of H runs on beside the rest of the setup and the next solve; its status
+    // is read by setup_check, which synchronizes this stream first.
+    const float* mat2[2] = {h->H32, nullptr};
+    float* out2[2] = {nullptr, nullptr};
+    int32_t* st2[2] = {h->dstatus2, nullptr};
+    ILS_CK(spd_inverse_f32(n, 1, mat2, out2, h->gj2, st2, t));
+    ILS_CK(cudaMemcpyAsync(h->h_status + 3, h->dstatus2, sizeof(int32_t), cudaMemcpyDeviceToHost, t));
+    ILS_CK(cudaEventRecord(h->ev_h, t));
+  } else {
     if (gj != cudaErrorNotSupported) ILS_CK(gj);
     cudaGetLastError();
+    ILS_CK(cudaStreamWaitEvent(s, h->ev_g2, 0));
+    ILS_CK(diff_mat_f64_f32(n, h->G1, h->G2, h->H, h->H32, s));
     ILS_CK(lower_to_f32(n, h->G1, h->L32, s));
     ILS_CK(cholesky_f32_pair(n, h->L32, h->H32, reinterpret_cast<float*>(h->inv_diag),
                              reinterpret_cast<float*>(h->inv_diag + n), h->stash32, h->dstatus, h->dstatus2, s));
   }
   ILS_CK(mark(h, 4));
-  ILS_CK(cudaMemcpyAsync(h->h_status + 6, h->dstatus, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-  ILS_CK(cudaMemcpyAsync(h->h_status + 3, h->dstatus2, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-  ILS_CK(cudaMemcpyAsync(h->h_status + 1, h->gs_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  ILS_CK(cudaStreamWaitEvent(s, h->ev_g2, 0));
   if (inverted)
     ILS_CK(mixed_setup_b(n, nullptr, h->opt.precision, h->P32, h->G2_32, h->Bt32, h->Bt16, s));
   else
     ILS_CK(mixed_setup(n, nullptr, h->G2, h->opt.precision, h->L32, h->P32, h->G2_32, h->Bt32, h->Bt16,
                        reinterpret_cast<float*>(h->Dinv), s));
+  if (inverted)
+    ILS_CK(cudaStreamWaitEvent(s, h->ev_hd, 0));  // the solve's residuals read H
+  else
+    ILS_CK(cudaMemcpyAsync(h->h_status + 3, h->dstatus2, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  ILS_CK(cudaMemcpyAsync(h->h_status + 6, h->dstatus, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  ILS_CK(cudaMemcpyAsync(h->h_status + 1, h->gs_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   ILS_CK(mark(h, 5));
   return ILS_OK;
 }
@@ -533,6 +560,7 @@ ils_status factor_f64_now(ils_handle h) {
 // again from the FP64 factor).
 ils_status setup_check(ils_handle h, bool* redone) {
   if (redone) *redone = false;
+  if (h->overlap && h->s_h) ILS_CK(cudaStreamSynchronize(h->s_h));  // the test of H
   if (h->sparse && h->h_status[2] != 0) return (ils_status)h->h_status[2];
   h->h_status[1] = h->opt.gram == ILS_GRAM_SPLIT ? h->h_status[1] : 0;
   if (h->h_status[1] != 0) return h->h_status[1] == 2 ? ILS_ERR_NONFINITE : ILS_ERR_TIMEOUT;
@@ -580,11 +608,12 @@ ils_status tune_handle(ils_handle h) {
 void free_handle(ils_handle h) {
   if (!h) return;
   if (h->block) cudaFreeAsync(h->block, h->stream);
-  if (h->s_aux) {
-    cudaStreamSynchronize(h->s_aux);
-    cudaStreamDestroy(h->s_aux);
-  }
-  for (cudaEvent_t e : {h->ev_start, h->ev_g2, h->ev_acopy, h->ev_rhs})
+  for (cudaStream_t x : {h->s_aux, h->s_h})
+    if (x) {
+      cudaStreamSynchronize(x);
+      cudaStreamDestroy(x);
+    }
+  for (cudaEvent_t e : {h->ev_start, h->ev_g2, h->ev_g1, h->ev_hd, h->ev_h, h->ev_acopy, h->ev_rhs})
     if (e) cudaEventDestroy(e);
   if (h->h_st) cudaFreeHost(h->h_st);
   for (cudaEvent_t e : h->ev)
@@ -1044,8 +1073,9 @@ ils_status create_handle(ils_handle* out, int64_t m, int64_t n, int64_t p, int64
   Carver real{(char*)h->block, 0, false};
   carve(h, real, work);
   if (h->overlap) {
-    bool ok = cudaStreamCreateWithFlags(&h->s_aux, cudaStreamNonBlocking) == cudaSuccess;
-    for (cudaEvent_t* e : {&h->ev_start, &h->ev_g2, &h->ev_acopy, &h->ev_rhs})
+    bool ok = cudaStreamCreateWithFlags(&h->s_aux, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&h->s_h, cudaStreamNonBlocking) == cudaSuccess;
+    for (cudaEvent_t* e : {&h->ev_start, &h->ev_g2, &h->ev_g1, &h->ev_hd, &h->ev_h, &h->ev_acopy, &h->ev_rhs})
       ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
       cudaGetLastError();
