@@ -510,7 +510,7 @@ ils_status compute_setup_overlap(ils_handle h, const double* src, int64_t lda_sr
     const float* mat2[2] = {h->H32, nullptr};
     float* out2[2] = {nullptr, nullptr};
     int32_t* st2[2] = {h->dstatus2, nullptr};
-    ILS_CK(spd_inverse_f32(n, 1, mat2, out2, h->gj2, st2, t));
+    ILS_CK(spd_inverse_f32(n, 1, mat2, out2, h->gj2, st2, t, /*wide_first=*/true));
     ILS_CK(cudaMemcpyAsync(h->h_status + 3, h->dstatus2, sizeof(int32_t), cudaMemcpyDeviceToHost, t));
     ILS_CK(cudaEventRecord(h->ev_h, t));
   } else {

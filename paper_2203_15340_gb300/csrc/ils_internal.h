@@ -224,12 +224,14 @@ cudaError_t mixed_correct(const MixedArgs& a, int precision, cudaStream_t s);
 // P[i] := A[i]^{-1} for count (1 or 2) n x n FP32 symmetric matrices (both triangles
 // stored, column-major) by block Gauss-Jordan elimination in one cooperative launch;
 // P[i] == nullptr tests A[i] only.  status[i] gets NOT_SPD / NONFINITE on a failed pivot
-// (the FP32 counterpart of the Cholesky pivot test) and TIMEOUT if a grid barrier wait ran
-// out.  `scratch` holds spd_inverse_scratch_floats(n) floats.  cudaErrorNotSupported when
-// the tiles do not fit one cooperative wave (the caller takes another route).
+// (the FP32 counterpart of the Cholesky pivot test) and TIMEOUT if a flag wait ran out.
+// Tiles are 32 x 32 where each gets a CTA of its own, else 64 x 64 (wide_first: 64 x 64
+// wherever they fit, fewer CTAs for a launch beside other work).  `scratch` holds
+// spd_inverse_scratch_floats(n) floats.  cudaErrorNotSupported when neither fits (nothing
+// is enqueued; the caller takes another route).
 size_t spd_inverse_scratch_floats(int64_t n);
 cudaError_t spd_inverse_f32(int64_t n, int count, const float* const* A, float* const* P, float* scratch,
-                            int32_t* const* status, cudaStream_t s);
+                            int32_t* const* status, cudaStream_t s, bool wide_first = false);
 cudaError_t convert_f64_to_f32(int64_t count, const double* src, float* dst, cudaStream_t s);
 // L32 := lower triangle of the n x n FP64 matrix M rounded to FP32, zeros above.
 cudaError_t lower_to_f32(int64_t n, const double* M, float* L32, cudaStream_t s);

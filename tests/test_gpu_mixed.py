@@ -166,11 +166,31 @@ def test_mixed_sizes_around_panel_edges(ils, n):
     assert info.refinements <= 6
 
 
-def test_mixed_large_n_takes_factor_route(ils):
-    """n = 1200 has more lower tiles than one cooperative wave of the Gauss-Jordan inverse
-    holds, so the setup factors A_1^T A_1 and H by Cholesky in FP32 instead; the solve must
-    still refine to FP64 accuracy."""
+def test_mixed_large_n_takes_wide_inverse_blocks(ils):
+    """n = 1200: 32-wide tiles of the Gauss-Jordan inverse would have to share CTAs, so it
+    sweeps 64-wide pivot blocks; the solve must still refine to FP64 accuracy."""
     inst = W.dense_gaussian(4800, 1200, 1200, 0.3, 120)
+    xs = O.qr_cholesky_solve(inst.A, inst.b, inst.p)
+    x, info = run(ils, inst, ils.ILS_FP32_REFINE, tol=1e-12)
+    assert info.status == ils.ILS_OK
+    assert relerr(x, xs) <= 1e-10
+
+
+def test_mixed_wide_blocks_reject_indefinite_h(ils):
+    """n = 1100 (64-wide inverse blocks) with A^T J A indefinite: the FP32 test of H on the
+    third stream fails, the FP64 factorization confirms it, and the setup reports NOT_SPD."""
+    bad = W.dense_gaussian(3300, 2200, 1100, 2.0, 5)
+    assert not O.is_spd(O.normal_matrix(bad.A, bad.p))
+    with pytest.raises(ils.ILSError) as e:
+        ils.Solver(colmajor(bad.A), bad.p, ils.options(precision=ils.ILS_FP32_REFINE))
+    assert e.value.code == ils.ILS_ERR_NOT_SPD
+
+
+def test_mixed_largest_n_takes_cholesky_route(ils):
+    """n = 2304 has more lower tiles than one cooperative wave of the inverse holds at
+    either block size (152 SMs), so the setup factors A_1^T A_1 and H by Cholesky in FP32
+    and forms P from the factor; the solve must still refine to FP64 accuracy."""
+    inst = W.dense_gaussian(9216, 2304, 2304, 0.3, 121)
     xs = O.qr_cholesky_solve(inst.A, inst.b, inst.p)
     x, info = run(ils, inst, ils.ILS_FP32_REFINE, tol=1e-12)
     assert info.status == ils.ILS_OK
