@@ -6,8 +6,8 @@ product (ils_refactor_async: the Gram matrices A_1^T A_1 and A_2^T A_2, P = (A_1
 the SPD test of A^T J A, and B = P A_2^T A_2) followed by ils_solve (A^T J b and the
 iterations to the tolerance).  The headline path is mixed-precision SP: FP64-accurate
 Gram matrices from exact BF16 digit products on the tcgen05 tensor cores, P by FP32
-block Gauss-Jordan elimination in one cooperative launch (which also tests A^T J A),
-FP32 sweeps with P and B, and FP64 residual refinement, the whole refinement in one
+block Gauss-Jordan elimination in one cooperative launch (a second launch on another
+stream tests A^T J A the same way), FP32 sweeps with P and B, and FP64 residual refinement, the whole refinement in one
 cooperative launch.  Plain FP64 SP (the paper's Alg. 1 in FP64 throughout: FP64 Grams,
 FP64 Cholesky, P and B) is timed the same way on the same instance and reported beside
 it.  The inputs are resident in HBM when a step starts; A (80 MB) fits in L2, so L2 is
@@ -40,7 +40,7 @@ FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
 # of each kernel as it stands, on the headline step; None once a kernel changes.
 MMA_TRAFFIC_BYTES = 160_487_936 + 9_351_424
-GJ_TRAFFIC_BYTES = 1_282_048 + 3_840
+GJ_TRAFFIC_BYTES = 693_504 + 0
 BF16_PEAK_TFLOPS = 1982.7  # measured cuBLAS BF16 burst rate on this machine (MEASURED_PEAKS.json)
 
 
@@ -563,13 +563,14 @@ def main():
     ph = mixed["phases"]
     # The two largest kernels of the headline step, each timed alone with CUDA events on
     # the handle's stream (options.timing):
-    #  * spd_gj_kernel: P = Abar1^{-1} by FP32 block Gauss-Jordan and the test of H; the
-    #    sweep operator makes n^3 multiply-adds per matrix, 4 n^3 flops for the two.
+    #  * spd_gj_kernel: P = Abar1^{-1} by FP32 block Gauss-Jordan (the test of H is its own
+    #    launch on another stream, outside this phase); the sweep operator makes n^3
+    #    multiply-adds per matrix.
     #  * gram_split_mma_kernel (A_1^T A_1): executed BF16 MMA flops, 2 x 128 x 128 x p per
     #    digit product and tile pair; 55 products on an off-diagonal tile pair, 30 on a
     #    diagonal one (the transposed cross products are not formed).
     gj_ms = ph["factor"]
-    gj_flops = 4.0 * n ** 3
+    gj_flops = 2.0 * n ** 3  # the sweep of one n x n matrix (Abar1): n^3 multiply-adds
     gj_ach = gj_flops / (gj_ms * 1e-3) / 1e12
     mma_ms = ph["gram1_mma"]
     n_tiles = (n + 127) // 128
@@ -579,7 +580,7 @@ def main():
     gram_ms = ph["gram1"]
     gram_flops = float(p) * n * (n + 1)  # the FP64-accurate product A_1^T A_1
     roof_gj = {
-        "kernel": "spd_gj_kernel (P = Abar1^{-1} by FP32 block Gauss-Jordan, with the SPD test of A^T J A)",
+        "kernel": "spd_gj_kernel<32> (P = Abar1^{-1} by FP32 block Gauss-Jordan; the SPD test of A^T J A is a second launch on another stream)",
         "bound": "alu",
         "achieved": gj_ach,
         "peak": FP32_SIMT_PEAK_TFLOPS,
@@ -589,7 +590,7 @@ def main():
         "traffic": GJ_TRAFFIC_BYTES,
         "kernel_ms": gj_ms,
         "share_of_step": gj_ms / ms_step,
-        "note": "latency-bound: the chain of 16 pivot blocks (update, 2x2-block sweep by four warps, flag handoff)",
+        "note": "latency-bound: the chain of 16 pivot blocks of 32 (update, 2x2-block sweep by four warps, flag handoff)",
     }
     roof_mma = {
         "kernel": "gram_split_mma_kernel (A_1^T A_1 to FP64 accuracy from exact BF16 digit products)",
@@ -629,7 +630,7 @@ def main():
         "config": {
             "workload": WORKLOAD,
             "method": "SP (Alg. 1), mixed precision: tensor-core FP64-accurate Grams, P by FP32 block "
-                      "Gauss-Jordan (with the SPD test of A^T J A), FP32 sweeps, FP64 residual refinement in "
+                      "Gauss-Jordan (the SPD test of A^T J A beside it on another stream), FP32 sweeps, FP64 residual refinement in "
                       "one cooperative launch",
             "tol_relres": TOL_RELRES,
             "relerr_vs_oracle": mixed["relerr"],
