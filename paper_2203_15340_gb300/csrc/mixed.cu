@@ -37,41 +37,6 @@ __global__ void f32_to_bf16_kernel(int64_t count, const float* __restrict__ src,
     dst[e] = __float2bfloat16_rn(src[e]);
 }
 
-__global__ void identity_f32_kernel(int64_t n, float* M) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * n; e += (int64_t)gridDim.x * blockDim.x)
-    M[e] = ((uint32_t)e % (uint32_t)n == (uint32_t)e / (uint32_t)n) ? 1.f : 0.f;
-}
-
-// C = X^T Y in FP32 (X, Y n x n column-major): 32 x 32 tiles, one output per thread.
-__global__ void __launch_bounds__(256) gemm_tn_f32_kernel(int64_t n, const float* __restrict__ X,
-                                                          const float* __restrict__ Y, float* __restrict__ C) {
-  __shared__ float Xs[32][33];
-  __shared__ float Ys[32][33];
-  const int64_t i0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
-  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;  // ty in 0..7
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
-  for (int64_t k0 = 0; k0 < n; k0 += 32) {
-    for (int rr = ty; rr < 32; rr += 8) {
-      const int64_t k = k0 + tx;
-      Xs[rr][tx] = (k < n && i0 + rr < n) ? X[k + (i0 + rr) * n] : 0.f;
-      Ys[rr][tx] = (k < n && j0 + rr < n) ? Y[k + (j0 + rr) * n] : 0.f;
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int kk = 0; kk < 32; ++kk) {
-      const float yv = Ys[tx][kk];
-#pragma unroll
-      for (int a = 0; a < 4; ++a) acc[a] = fmaf(Xs[ty + 8 * a][kk], yv, acc[a]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const int64_t gi = i0 + ty + 8 * a, gj = j0 + tx;
-    if (gi < n && gj < n) C[gi + gj * n] = acc[a];
-  }
-}
-
 // Operator element loads for the sweep GEMV (FP32 or BF16 storage, FP32 arithmetic).
 __device__ __forceinline__ float ld_op(const float* p, int64_t i) { return p[i]; }
 __device__ __forceinline__ float ld_op(const __nv_bfloat16* p, int64_t i) { return __bfloat162float(p[i]); }

@@ -101,8 +101,8 @@ def test_sweep_autotuner_picks_a_shape_and_keeps_results(ils):
 
 @pytest.mark.parametrize("prec", [1, 2])
 def test_mixed_setup_rejects_indefinite_h(ils, prec):
-    """A_1^T A_1 is SPD but A^T J A is not: the mixed setup (whose H test runs in FP32 beside
-    the FP64 factorization of A_1^T A_1, confirmed in FP64) reports NOT_SPD."""
+    """A_1^T A_1 is SPD but A^T J A is not: the mixed setup (whose FP32 test of H on a third
+    stream fails and is confirmed in FP64) reports NOT_SPD."""
     bad = W.dense_gaussian(400, 300, 60, 2.0, 3)
     assert not O.is_spd(O.normal_matrix(bad.A, bad.p))
     with pytest.raises(ils.ILSError) as e:
@@ -112,7 +112,7 @@ def test_mixed_setup_rejects_indefinite_h(ils, prec):
 
 def test_mixed_setup_falls_back_to_fp64_factor(ils):
     """A column of A_1 scaled by 2^64 puts an entry of A_1^T A_1 beyond the FP32 range, so the
-    FP32 Cholesky of A_1^T A_1 (and the FP32 test of H) fail although both matrices are SPD:
+    FP32 inverse of A_1^T A_1 (and the FP32 test of H) fail although both matrices are SPD:
     the setup must take the FP64 factorization and succeed, with L the FP64 Cholesky factor."""
     import torch
     inst = W.dense_gaussian(300, 240, 40, 0.3, 11)
