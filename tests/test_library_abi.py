@@ -75,3 +75,37 @@ def test_csr_setup_rejections_without_gpu(libpath):
         o = binding.options(**kw)
         assert lib.ils_setup_csr(ctypes.byref(h), 10, 5, 8, 2, 20, fake, fake, fake, ctypes.byref(o), None) == bad
     assert not h.value
+
+
+def test_null_handles_are_rejected_on_the_host(libpath):
+    """Every call that takes a handle refuses a null one before any CUDA call, and the
+    destroy calls accept null (the header's error contract; runs without a GPU)."""
+    from paper_2203_15340_gb300 import binding
+    lib = binding.lib()
+    bad = binding.ILS_ERR_INVALID_ARG
+    fake = 256  # never dereferenced
+    assert lib.ils_refactor(None, fake, 10, None) == bad
+    assert lib.ils_refactor_async(None, fake, 10, None) == bad
+    assert lib.ils_solve(None, fake, fake, 1, 1e-10, None, None) == bad
+    assert lib.ils_solve_many(None, 1, fake, 10, fake, 10, 1, 1e-10, None, None) == bad
+    assert lib.ils_get_matrix(None, 0, fake, 10, None) == bad
+    assert lib.ils_aq_product(None, fake, fake, 0, None) == bad
+    out = (ctypes.c_double * 7)()
+    assert lib.ils_get_timings(None, out, 7) == -1
+    assert lib.ils_batch_solve(None, 1, None, None, None, None, 1, 1e-10, None, None) == bad
+    assert lib.ils_batch_capture(None, 0, 1, None, None, None, None, 1, 1e-10, 4, None) == bad
+    assert lib.ils_batch_run(None, None, None) == bad
+    assert lib.ils_batch_setup(None, 1, None, None, None) == bad
+    b = ctypes.c_void_p()
+    assert lib.ils_batch_setup(ctypes.byref(b), 0, None, None, None) == bad and not b.value
+    assert lib.ils_mlp_create(None, 16, 256, 256, 0, None) == bad
+    m = ctypes.c_void_p()
+    assert lib.ils_mlp_create(ctypes.byref(m), 0, 256, 256, 0, None) == bad and not m.value
+    assert lib.ils_mlp_num_params(None) == -1
+    assert lib.ils_mlp_get_params(None, fake, None) == bad
+    assert lib.ils_mlp_set_params(None, fake, None) == bad
+    assert lib.ils_mlp_forward(None, 1, fake, fake, 256, 1, None) == bad
+    assert lib.ils_solve_param(None, None, 1, fake, fake, 10, fake, 10, 1e-10, None, None) == bad
+    lib.ils_destroy(None)
+    lib.ils_batch_destroy(None)
+    lib.ils_mlp_destroy(None)
