@@ -46,6 +46,13 @@ __all__ = [
     "scd_pick_rank",
     "scd_rank_law",
     "scd_literal_law",
+    "scd_fixed_rank_from_uniform",
+    "scd_fixed_survival",
+    "scd_fixed_rank_law",
+    "scd_fixed_literal_law",
+    "normal_matrix_condition",
+    "error_certificate",
+    "sp_rk_rgs_gram_solve",
 ]
 
 
@@ -110,6 +117,23 @@ def relres(A, b, p, x):
 def paper_rr(A, b, p, x):
     """The paper's stopping quantity RR = ||A^T J (A x - b)||^2 / ||A^T J b||^2 (Sec. 5)."""
     return relres(A, b, p, x) ** 2
+
+
+def normal_matrix_condition(A, p):
+    """kappa_2(H) = lambda_max(H) / lambda_min(H) of H = A^T J A (SPD under (1.3))."""
+    lam = np.linalg.eigvalsh(normal_matrix(A, p))
+    return float(lam[-1] / lam[0])
+
+
+def error_certificate(A, b, p, x, kappa=None):
+    """kappa(H) * relres(x): an upper bound on ||x - x*|| / ||x*||.
+
+    With r = bbar - H x, x - x* = -H^{-1} r, so ||x - x*|| <= ||H^{-1}|| ||r||; and
+    bbar = H x* gives ||x*|| >= ||bbar|| / ||H||.  Dividing, the relative error is at
+    most ||H|| ||H^{-1}|| ||r|| / ||bbar|| = kappa_2(H) relres.
+    """
+    k = normal_matrix_condition(A, p) if kappa is None else kappa
+    return k * relres(A, b, p, x)
 
 
 def energy_norm(v, G):
@@ -320,6 +344,87 @@ def scd_rank_law(absr):
     return prob
 
 
+FIXED_ALPHA_SEARCH_MAX = 16  # alpha up to this: bisection on the first product form
+
+
+def scd_fixed_survival(i, n, alpha):
+    """P(rank > i) = C(n-i, alpha) / C(n, alpha) for a fixed subset size alpha (Sec. 4: a
+    uniform alpha-subset, argmax of r_s^2 over it).
+
+    The i-th largest |r_s| is picked exactly when it is in the subset and none of the i-1
+    larger ones is, so the pick's rank exceeds i when the subset avoids the top i.
+    Evaluated in FP64 as a product of exact-integer ratios, taken left to right:
+      alpha <= FIXED_ALPHA_SEARCH_MAX:  prod_{s=0}^{alpha-1} (n-i-s) / (n-s)
+      otherwise:                        prod_{s=0}^{i-1} (n-alpha-s) / (n-s)
+    (both equal the binomial ratio; each is non-increasing in i after rounding, because
+    every factor is, and a zero factor makes it 0 for i > n - alpha).
+    """
+    prod = 1.0
+    if alpha <= FIXED_ALPHA_SEARCH_MAX:
+        for s in range(alpha):
+            num = n - i - s
+            if num <= 0:
+                return 0.0
+            prod = prod * (float(num) / float(n - s))
+    else:
+        for s in range(i):
+            num = n - alpha - s
+            if num <= 0:
+                return 0.0
+            prod = prod * (float(num) / float(n - s))
+    return prod
+
+
+def scd_fixed_rank_from_uniform(u, n, alpha):
+    """Rank i in 1..n-alpha+1 of the index picked with a fixed subset size alpha, by inverse
+    CDF: the smallest i with P(rank > i) <= 1 - u (``scd_fixed_survival``).
+
+    For small alpha the rank is found by bisection, otherwise by a scan from i = 1 (the
+    expected rank is (n+1)/(alpha+1), small there).  alpha = n gives i = 1 (greedy, the
+    Motzkin rule); alpha = 1 gives a uniform rank.
+    """
+    thr = 1.0 - u
+    hi = n - alpha + 1
+    if alpha <= FIXED_ALPHA_SEARCH_MAX:
+        lo = 1
+        while lo < hi:
+            mid = (lo + hi) // 2
+            if scd_fixed_survival(mid, n, alpha) <= thr:
+                hi = mid
+            else:
+                lo = mid + 1
+        return lo
+    i = 1
+    prod = float(n - alpha) / float(n)  # the survival at i = 1, extended one factor per step
+    while i < hi and not (prod <= thr):
+        prod = prod * (float(n - alpha - i) / float(n - i))
+        i += 1
+    return i
+
+
+def scd_fixed_rank_law(absr, alpha):
+    """Law of the picked index under the fixed-alpha rank sampler: the i-th largest |r_s|
+    with probability C(n-i, alpha-1) / C(n, alpha)."""
+    n = len(absr)
+    order = sorted(range(n), key=lambda s: (-absr[s], s))
+    prob = np.zeros(n)
+    for i in range(1, n - alpha + 2):
+        prob[order[i - 1]] = math.comb(n - i, alpha - 1) / math.comb(n, alpha)
+    return prob
+
+
+def scd_fixed_literal_law(absr, alpha):
+    """Exact law of argmax over a uniform alpha-subset, by enumerating every subset (tiny n)."""
+    from itertools import combinations
+    n = len(absr)
+    prob = np.zeros(n)
+    subs = list(combinations(range(n), alpha))
+    for tau in subs:
+        j = max(tau, key=lambda s: (absr[s], -s))
+        prob[j] += 1.0 / len(subs)
+    return prob
+
+
 def rk_step(A1, w, bhat, j, norms2):
     """RK step on A_1^T w = bhat (Alg. 2 step 9; RK of Sec. 3.1 on the rows of A_1^T).
 
@@ -351,7 +456,7 @@ def scd_step(G1, beta, r, j):
 
 
 def sp_rk_rgs_solve(A, b, p, x0=None, tol=1e-12, max_outer=20000, max_inner=None, theta=0.1,
-                    seed=0, chain=0, check_every=None, same_index=False, record=False):
+                    seed=0, chain=0, check_every=None, same_index=False, record=False, warm_inner=False):
     """SP-RK-RGS method, Alg. 2.
 
     Outer: bhat = Abar2 x_k + bbar (step 5), z = w = 0 (step 6).  Inner step t:
@@ -365,6 +470,11 @@ def sp_rk_rgs_solve(A, b, p, x0=None, tol=1e-12, max_outer=20000, max_inner=None
     Draws come from Philox4x32-10 (``step_uniforms(seed, chain, k, t)``): j1 from
     u0, j2 from u1, each by ``invcdf_pick``.  ``same_index`` forces j2 = j1,
     the SP-RCD special case of Sec. 4.
+
+    ``warm_inner`` (not in the paper, which restarts at 0 in step 6) starts the inner
+    solve at z = x_k, w = A_1 x_k instead: w stays in range(A_1), the inner fixed point
+    Abar1^{-1} bhat is unchanged, and the start's residual bhat - Abar1 x_k is the outer
+    residual bbar - H x_k, which the inner stop measures against.
     """
     A = np.asarray(A, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
@@ -387,8 +497,8 @@ def sp_rk_rgs_solve(A, b, p, x0=None, tol=1e-12, max_outer=20000, max_inner=None
         if rel <= tol or k == max_outer:
             break
         bhat = G2 @ x + bb
-        w = np.zeros(p)
-        z = np.zeros(n)
+        w = A1 @ x if warm_inner else np.zeros(p)
+        z = x.copy() if warm_inner else np.zeros(n)
         target = theta * np.linalg.norm(r_out)
         t_done = max_inner
         for t in range(max_inner):
@@ -411,8 +521,67 @@ def sp_rk_rgs_solve(A, b, p, x0=None, tol=1e-12, max_outer=20000, max_inner=None
     return x, info
 
 
+def sp_rk_rgs_gram_solve(A, b, p, x0=None, tol=1e-12, max_outer=20000, max_inner=None, theta=0.1,
+                         seed=0, chain=0, check_every=None, same_index=False, warm_inner=False):
+    """SP-RK-RGS, Alg. 2, with the inner vectors carried in Gram space (not in the paper).
+
+    From w = 0, every RK step adds a multiple of a column of A_1 to w, so w = A_1 y for a
+    coefficient vector y that gains delta in entry j1.  Keeping g = Abar1 y (= A_1^T w)
+    and h = Abar1 z (= A_1^T A_1 z), the two steps of Alg. 2 become
+        delta = (bhat_j1 - g_j1) / Abar1_{j1 j1};  y_j1 += delta;  g += delta Abar1(:, j1)
+        eps   = (g_j2 - h_j2) / Abar1_{j2 j2};     z_j2 += eps;    h += eps Abar1(:, j2)
+    because A_1(:,j)^T w = g_j, A_1(:,j)^T A_1 z = h_j and ||A_1(:,j)||^2 = Abar1_jj.  In
+    exact arithmetic z is the iterate of the column form (``sp_rk_rgs_solve``) under the
+    same draws, at O(n) work per step instead of O(p).  The inner stop reads
+    ||bhat - h||, the exact quantity the column form recomputes.
+    """
+    A = np.asarray(A, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    n = A.shape[1]
+    A1 = A[:p]
+    G1, G2 = gram_blocks(A, p)
+    bb = rhs_bar(A, b, p)
+    norms2, cum = column_cumsum(A1)
+    max_inner = 200 * n if max_inner is None else max_inner
+    check_every = n if check_every is None else check_every
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    bnorm = np.linalg.norm(bb)
+    info = SolveInfo()
+    for k in range(max_outer + 1):
+        r_out = residual(A, b, p, x)
+        rel = np.linalg.norm(r_out) / bnorm
+        info.history.append(rel)
+        if rel <= tol or k == max_outer:
+            break
+        bhat = G2 @ x + bb
+        z = x.copy() if warm_inner else np.zeros(n)
+        g = G1 @ z  # w = A_1 z at a warm start (y = z), else w = 0
+        h = g.copy()
+        target = theta * np.linalg.norm(r_out)
+        t_done = max_inner
+        for t in range(max_inner):
+            u0, u1 = step_uniforms(seed, chain, k, t)
+            j1 = invcdf_pick(cum, u0)
+            delta = (bhat[j1] - g[j1]) / G1[j1, j1]
+            g = g + delta * G1[:, j1]
+            j2 = j1 if same_index else invcdf_pick(cum, u1)
+            eps = (g[j2] - h[j2]) / G1[j2, j2]
+            z = z.copy()
+            z[j2] += eps
+            h = h + eps * G1[:, j2]
+            if (t + 1) % check_every == 0 and np.linalg.norm(bhat - h) <= target:
+                t_done = t + 1
+                break
+        info.inner_iters.append(t_done)
+        x = z
+        info.outer_iters += 1
+    info.relres = rel
+    info.converged = rel <= tol
+    return x, info
+
+
 def sp_scd_solve(A, b, p, x0=None, tol=1e-12, max_outer=20000, max_inner=None, theta=0.1,
-                 sampler="rank", alpha=None, seed=0, chain=0, record=False, rng=None):
+                 sampler="rank", alpha=None, seed=0, chain=0, record=False, rng=None, warm_inner=False):
     """SP-SCD method in the form the paper ran, Alg. 5.
 
     Outer: bhat = Abar2 x_k + bbar (step 4), beta = 0 and r = bhat (step 5).
@@ -428,6 +597,11 @@ def sp_scd_solve(A, b, p, x0=None, tol=1e-12, max_outer=20000, max_inner=None, t
         ``step_uniforms(seed, chain, k, t)``.
       * ``"greedy"``: alpha = n, the Motzkin rule argmax_s r_s^2.
       * ``"fixed"``: a uniform subset of fixed size ``alpha`` (from ``rng``).
+      * ``"fixed_rank"``: the equal-in-law rank form of ``"fixed"``: the i-th largest
+        |r_s| with i = ``scd_fixed_rank_from_uniform(u0, n, alpha)``, u0 from Philox.
+
+    ``warm_inner`` (not in the paper, which restarts at beta = 0 in step 5) starts the
+    inner solve at beta = x_k, r = bhat - Abar1 x_k (= bbar - H x_k).
     """
     A = np.asarray(A, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
@@ -449,7 +623,7 @@ def sp_scd_solve(A, b, p, x0=None, tol=1e-12, max_outer=20000, max_inner=None, t
         if rel <= tol or k == max_outer:
             break
         bhat = G2 @ x + bb
-        beta = np.zeros(n)
+        beta = x.copy() if warm_inner else np.zeros(n)
         r = bhat - G1 @ beta
         target = theta * np.linalg.norm(r_out)
         t_done = max_inner
@@ -467,6 +641,10 @@ def sp_scd_solve(A, b, p, x0=None, tol=1e-12, max_outer=20000, max_inner=None, t
                 j = scd_pick_literal(r, a_t, rng.choice(n, size=a_t, replace=False))
             elif sampler == "fixed":
                 j = scd_pick_literal(r, alpha, rng.choice(n, size=alpha, replace=False))
+            elif sampler == "fixed_rank":
+                u0, _ = step_uniforms(seed, chain, k, t)
+                i = scd_fixed_rank_from_uniform(u0, n, alpha)
+                j = int(np.lexsort((np.arange(n), -np.abs(r)))[i - 1])
             else:
                 raise ValueError(sampler)
             if record and k == 0:

@@ -225,3 +225,93 @@ def test_rk_rgs_converges(c1):
     inst, xs = c1
     x, info = O.sp_rk_rgs_solve(inst.A, inst.b, inst.p, tol=1e-12)
     assert info.converged and relerr(x, xs) <= 1e-10
+
+
+# ---------------------------------------------------------------------------------------
+# Fixed subset size alpha (Sec. 4: alpha = n is the Motzkin greedy rule), the error
+# certificate, the inner warm start and the Gram-space form of RK-RGS.
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [1, 2, 5, 7])
+def test_scd_fixed_rank_law_equals_literal_law(n):
+    """argmax over a uniform alpha-subset, enumerated subset by subset, has the rank law
+    C(n-i, alpha-1) / C(n, alpha) for every alpha (tie-free |r|)."""
+    absr = np.random.default_rng(n).permutation(np.arange(1, n + 1)).astype(float)
+    for alpha in range(1, n + 1):
+        lit = O.scd_fixed_literal_law(absr, alpha)
+        assert np.allclose(lit, O.scd_fixed_rank_law(absr, alpha), rtol=0, atol=1e-15), alpha
+        assert abs(lit.sum() - 1.0) <= 1e-14
+
+
+@pytest.mark.parametrize("n,alpha", [(7, 1), (7, 3), (50, 1), (50, 2), (50, 16), (50, 17), (50, 40), (50, 50),
+                                     (301, 5), (301, 120)])
+def test_scd_fixed_rank_inverse_cdf(n, alpha):
+    """On a fine uniform grid of u the sampled rank has the law C(n-i, alpha-1)/C(n, alpha):
+    both the bisection form (alpha <= 16) and the scan form (alpha > 16)."""
+    us = (np.arange(100000) + 0.5) / 100000
+    ranks = np.array([O.scd_fixed_rank_from_uniform(u, n, alpha) for u in us])
+    assert ranks.min() >= 1 and ranks.max() <= n - alpha + 1
+    freq = np.bincount(ranks, minlength=n + 1)[1:] / us.size
+    law = np.array([math.comb(n - i, alpha - 1) / math.comb(n, alpha) for i in range(1, n + 1)])
+    assert np.max(np.abs(freq - law)) <= 2e-5
+
+
+def test_scd_fixed_alpha_n_is_greedy(c1):
+    """alpha = n: the subset is everything, so the fixed-alpha sampler makes the greedy picks."""
+    inst, _ = c1
+    kw = dict(tol=0.0, max_outer=1, max_inner=80, theta=1e-300, record=True)
+    _, a = O.sp_scd_solve(inst.A, inst.b, inst.p, sampler="fixed_rank", alpha=inst.n, **kw)
+    _, g = O.sp_scd_solve(inst.A, inst.b, inst.p, sampler="greedy", **kw)
+    assert a.picks == g.picks and len(a.picks) == 80
+
+
+@pytest.mark.parametrize("alpha", [1, 2, 17])
+def test_scd_fixed_alpha_converges(c1, alpha):
+    inst, xs = c1
+    x, info = O.sp_scd_solve(inst.A, inst.b, inst.p, tol=1e-12, sampler="fixed_rank", alpha=alpha, seed=4)
+    assert info.converged and np.linalg.norm(x - xs) <= 1e-10 * np.linalg.norm(xs)
+
+
+def test_error_certificate_bounds_the_error():
+    """kappa(H) relres bounds ||x - x*|| / ||x*|| for any x (checked on perturbed iterates
+    of three instances), and kappa of a diagonal H is the ratio of its extreme entries."""
+    rng = np.random.default_rng(9)
+    for seed in range(3):
+        inst = W.dense_gaussian(120, 30, 12, 0.3, 50 + seed)
+        xs = O.qr_cholesky_solve(inst.A, inst.b, inst.p)
+        kap = O.normal_matrix_condition(inst.A, inst.p)
+        for scale in (1e-2, 1e-6, 1e-11):
+            x = xs + scale * np.linalg.norm(xs) * rng.standard_normal(xs.shape) / math.sqrt(xs.size)
+            err = np.linalg.norm(x - xs) / np.linalg.norm(xs)
+            assert err <= O.error_certificate(inst.A, inst.b, inst.p, x, kappa=kap) * (1 + 1e-6)
+    d1, d2 = np.array([4.0, 3.0, 5.0]), np.array([1.0, 2.0, 0.5])
+    A = np.vstack([np.diag(d1), np.diag(d2)])
+    lam = d1 ** 2 - d2 ** 2
+    assert abs(O.normal_matrix_condition(A, 3) - lam.max() / lam.min()) <= 1e-13 * lam.max() / lam.min()
+
+
+def test_rk_rgs_gram_form_equals_column_form(c1):
+    """Gram-space RK-RGS follows the column form step for step under the same draws."""
+    inst, _ = c1
+    kw = dict(tol=0.0, max_outer=2, max_inner=300, check_every=10 ** 9, seed=5)
+    for same in (False, True):
+        xc, _ = O.sp_rk_rgs_solve(inst.A, inst.b, inst.p, same_index=same, **kw)
+        xg, _ = O.sp_rk_rgs_gram_solve(inst.A, inst.b, inst.p, same_index=same, **kw)
+        assert np.linalg.norm(xg - xc) <= 1e-12 * np.linalg.norm(xc)
+
+
+@pytest.mark.parametrize("solver", ["rk_rgs", "rk_rgs_gram", "scd"])
+def test_warm_inner_start_keeps_the_sp_step(c1, solver):
+    """With the inner solve run to convergence, one outer step equals SP's step from either
+    start (the inner fixed point is Abar1^{-1} bhat, Theorem 3.1), and a full warm-started
+    solve converges to x* with fewer inner steps than the cold one."""
+    inst, xs = c1
+    fn = {"rk_rgs": O.sp_rk_rgs_solve, "rk_rgs_gram": O.sp_rk_rgs_gram_solve, "scd": O.sp_scd_solve}[solver]
+    x0 = xs + 0.1 * np.random.default_rng(1).standard_normal(inst.n)
+    x_sp, _ = O.sp_solve(inst.A, inst.b, inst.p, x0=x0, tol=0.0, max_outer=1)
+    x_w, _ = fn(inst.A, inst.b, inst.p, x0=x0, tol=0.0, max_outer=1, theta=1e-13, max_inner=400000, warm_inner=True)
+    assert np.linalg.norm(x_w - x_sp) <= 1e-10 * np.linalg.norm(x_sp)
+    _, cold = fn(inst.A, inst.b, inst.p, tol=1e-12, seed=3)
+    xw, warm = fn(inst.A, inst.b, inst.p, tol=1e-12, seed=3, warm_inner=True)
+    assert warm.converged and np.linalg.norm(xw - xs) <= 1e-10 * np.linalg.norm(xs)
+    assert sum(warm.inner_iters) < sum(cold.inner_iters)

@@ -57,3 +57,54 @@ def test_adam_first_step_is_signed_lr():
     g = np.array([0.3, -2.0, 1e-3])
     p, m, v = M.adam_step(np.zeros(3), g, np.zeros(3), np.zeros(3), 1, 0.01)
     assert np.allclose(p, -0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12)
+
+
+def _fp32_network_sim(params, Theta, T):
+    """The network's loss gradient evaluated entirely in numpy float32 (a stand-in for an
+    FP32 device computation; only the bound helper is under test here)."""
+    from scipy.special import erf
+    f = np.float32
+    W1, b1, W2, b2, W3, b3 = [p.astype(f) for p in params]
+    th = Theta.astype(f)
+
+    def gelu(z):
+        return (f(0.5) * z * (f(1) + erf(z * f(0.70710678)).astype(f))).astype(f)
+
+    def gelu_grad(z):
+        Phi = (f(0.5) * (f(1) + erf(z * f(0.70710678)).astype(f))).astype(f)
+        return (Phi + z * (np.exp(-f(0.5) * z * z) / f(math.sqrt(2 * math.pi))).astype(f)).astype(f)
+
+    z1 = th @ W1.T + b1
+    h1 = gelu(z1)
+    z2 = h1 @ W2.T + b2
+    h2 = gelu(z2)
+    y = h2 @ W3.T + b3
+    dy = (f(2) * (y - T.astype(f)) / f(y.size)).astype(f)
+    dz2 = (dy @ W3) * gelu_grad(z2)
+    dz1 = (dz2 @ W2) * gelu_grad(z1)
+    return y, M.flatten([dz1.T @ th, dz1.sum(0), dz2.T @ h1, dz2.sum(0), dy.T @ h2, dy.sum(0)])
+
+
+def test_fp32_error_bounds_hold_and_catch_wrong_entries():
+    """The entry-by-entry bounds the GPU gradient test uses: an FP32 evaluation stays inside
+    them, while one entry off by 1e-3 relative, swapped with its neighbour or zeroed falls
+    outside."""
+    from tests.helpers import mlp_error_bounds
+    d_in, d_h, d_out = 16, 64, 48
+    rng = np.random.default_rng(12)
+    params = []
+    for shp in M.shapes(d_in, d_h, d_out):
+        fan = shp[1] if len(shp) == 2 else d_in
+        params.append((rng.uniform(-1, 1, size=shp) / math.sqrt(fan)).astype(np.float32).astype(np.float64))
+    Theta = rng.uniform(-1, 1, size=(40, d_in)).astype(np.float32).astype(np.float64)
+    T = rng.standard_normal((40, d_out))
+    _, go = M.loss_and_grad(params, Theta, T)
+    yo = M.forward(params, Theta)["y"]
+    y32, g32 = _fp32_network_sim(params, Theta, T)
+    yb, gb = mlp_error_bounds(params, Theta, T)
+    assert np.all(np.abs(g32 - go) <= gb) and np.all(np.abs(y32 - yo) <= yb)
+    i = int(np.argmax(np.abs(go)))
+    for bad in (g32 * np.where(np.arange(g32.size) == i, 1.001, 1.0),
+                np.where(np.arange(g32.size) == i, 0.0, g32),
+                np.where(np.arange(g32.size) == i, g32[i + 1], g32)):
+        assert np.any(np.abs(bad - go) > gb)
