@@ -40,7 +40,9 @@ typedef struct ils_handle_s* ils_handle;
 typedef enum {
   ILS_OK = 0,
   ILS_ERR_INVALID_ARG = 1,    /* bad size, stride, pointer or option */
-  ILS_ERR_NOT_SPD = 2,        /* A_1^T A_1 (hence A^T J A) failed its Cholesky pivot test, eq. (1.3) */
+  ILS_ERR_NOT_SPD = 2,        /* condition (1.3) fails: A_1^T A_1 or H = A^T J A failed its pivot test
+                                 (explicit route), or the estimated rho(Abar1^{-1} Abar2) >= 1
+                                 (matrix-free route with options.estimate) */
   ILS_ERR_NO_CONVERGENCE = 3, /* max_outer reached; x holds the last iterate */
   ILS_ERR_NONFINITE = 4,      /* a NaN/Inf appeared in the input or the iteration */
   ILS_ERR_TIMEOUT = 5,        /* a bounded device-side wait ran out */
@@ -57,12 +59,15 @@ typedef enum {
 typedef enum {
   ILS_FP64 = 0,        /* every product in FP64 (the paper's arithmetic) */
   ILS_FP32_REFINE = 1, /* SP method: FP64-accurate Grams; the correction sweeps use
-                          P = Abar1^{-1} and B = P Abar2 in FP32 with FP32 accumulation
-                          (P from an FP32 Cholesky factor of Abar1 on handles with split
-                          Grams, from the FP64 one otherwise; an FP32 pivot that fails
-                          falls back to FP64); each step's residual bbar - H x is FP64
-                          (iterative refinement), so the FP64 stopping test still decides.
-                          Also SP-RK-RGS on a sparse A (see ils_setup_csr). */
+                          P = Abar1^{-1} and B = P Abar2 in FP32 with FP32 accumulation.
+                          P comes from the FP32 Gauss-Jordan inverse of Abar1 (single dense
+                          handles; beyond one cooperative wave of its tiles, from an FP32
+                          Cholesky factor), or from the FP64 Cholesky factor when
+                          options.factor64 != 0, on the matrix-free route and on batch
+                          handles; an FP32 pivot that fails falls back to FP64.  Each step's
+                          residual bbar - H x is FP64 (iterative refinement), so the FP64
+                          stopping test still decides.  Also SP-RK-RGS on a sparse A (see
+                          ils_setup_csr). */
   ILS_BF16_REFINE = 2  /* as ILS_FP32_REFINE with B held in BF16 (FP32 accumulation) */
 } ils_precision;
 
@@ -90,7 +95,39 @@ typedef struct {
                           thread-block cluster of 1, 2, 4 or 8 CTAs whose shared memory holds
                           w and e, else one CTA with w and e in global memory); 1, 2, 4, 8 =
                           that cluster size; -1 = one CTA, vectors in global memory. */
+  /* ---- fields below were added after the first release; ils_options_default sets them ---- */
+  int32_t stop_rule;   /* ils_stop_rule: how `tol` of the solve calls is read (default relres) */
+  int32_t estimate;    /* != 0: estimate rho(Abar1^{-1} Abar2) and kappa_2(A^T J A) at setup by
+                          Lanczos (ils_info.rho_est, kappa_est, err_bound); implied by
+                          ILS_STOP_ERR_BOUND */
+  int32_t alpha_mode;  /* SP-SCD: 0 = alpha ~ U{1..n} each step (Alg. 5), 1 = fixed alpha_fixed
+                          (Sec. 4: alpha = n is the greedy Motzkin rule, alpha = 1 a uniform pick) */
+  int32_t sampler;     /* SP-RK-RGS column draws from ||A_1(:,j)||^2 / ||A_1||_F^2: 0 = inverse CDF
+                          (the oracle's parity mode), 1 = Vose alias table (same law, O(1) draws) */
+  int64_t alpha_fixed; /* 1 <= alpha_fixed <= n when alpha_mode = 1 */
+  int32_t warm_inner;  /* randomized methods: != 0 starts each inner solve at x_k (z = x_k,
+                          w = A_1 x_k; beta = x_k) instead of 0 (the paper's step); not in the paper */
+  int32_t inner_form;  /* dense SP-RK-RGS: 0 = column form of Alg. 2 (O(p) per step), 1 = Gram form
+                          (w = A_1 y carried as g = Abar1 y, h = Abar1 z: O(n) per step, same
+                          iterates in exact arithmetic); not in the paper */
+  const char* tune_cache; /* [host] file that keeps the autotuner's choices between processes
+                          (read at the first setup, rewritten after each new tuning), or NULL */
+  int64_t wait_limit_ns; /* bound in nanoseconds on each grid-barrier wait of the one-launch
+                          mixed-precision solve; 0 = 1 s (the setup kernels keep their own 1-4 s
+                          bounds).  A wait that runs out ends the kernel and the solve returns
+                          ILS_ERR_TIMEOUT; the handle stays usable */
+  int32_t lanczos_steps; /* Lanczos steps of the estimates; 0 = 64 */
+  int32_t factor64;    /* mixed precision, single dense handle: != 0 forms P = Abar1^{-1} from the
+                          FP64 Cholesky factor of Abar1 and tests H by FP64 Cholesky (the
+                          factorization stays FP64), instead of the FP32 Gauss-Jordan inverse */
 } ils_options;
+
+typedef enum {
+  ILS_STOP_RELRES = 0,   /* stop once relres = ||A^T J (b - A x_k)|| / ||A^T J b|| <= tol */
+  ILS_STOP_PAPER_RR = 1, /* Sec. 5's rule: stop once RR = relres^2 <= tol (e.g. tol = 1e-6) */
+  ILS_STOP_ERR_BOUND = 2 /* stop once kappa_est * relres <= tol: kappa_2(H) relres bounds
+                            ||x - x*|| / ||x*||, so tol is the target relative error */
+} ils_stop_rule;
 
 typedef enum { ILS_ROUTE_AUTO = 0, ILS_ROUTE_EXPLICIT = 1, ILS_ROUTE_MATRIX_FREE = 2 } ils_route;
 
@@ -101,6 +138,16 @@ typedef struct {
   double relres;        /* ||A^T J (b - A x)|| / ||A^T J b|| of the returned x (FP64) */
   int32_t status;       /* ils_status of this solve */
   int32_t reserved;
+  double err_bound;     /* kappa_est * relres: bounds ||x - x*|| / ||x*|| (Theorem 2.1's setting:
+                           x - x* = -H^{-1} r and ||x*|| >= ||bbar|| / ||H||); 0 without estimates */
+  double rho_est;       /* Lanczos estimate of rho(Abar1^{-1} Abar2), the SP contraction factor of
+                           Theorem 2.1 (Ritz values lie inside the spectrum: rho_est <= rho up to
+                           rounding); 0 without estimates */
+  double kappa_est;     /* Lanczos estimate of kappa_2(A^T J A) (<= the true value up to rounding) */
+  double t_setup_ms;    /* the handle's last setup on the device (CUDA events; options.timing) */
+  double t_solve_ms;    /* wall time of this solve call, host clock */
+  double t_inner_ms;    /* randomized methods: device time of the inner chains of the first
+                           right-hand side (globaltimer), else 0 */
 } ils_info;
 
 /* Fill *o with the defaults above (method SP, FP64, FP64 Gram, max_outer 20000,
@@ -117,9 +164,13 @@ ils_status ils_options_default(ils_options* o);
  *   o    [host] options, or NULL for the defaults.
  * Work: copies A, forms Abar1 = A_1^T A_1 and Abar2 = A_2^T A_2 (FP64, or FP64-accurate
  * split tensor-core products when options.gram = ILS_GRAM_SPLIT or precision is mixed),
- * factors Abar1 and H = Abar1 - Abar2 by Cholesky (the SPD test of eq. (1.3)) and forms
- * P = Abar1^{-1}, B = P Abar2 (FP64, or FP32/BF16 for the mixed precisions).
- * Synchronizes the stream once to read the Cholesky pivot status.
+ * tests Abar1 and H = Abar1 - Abar2 for positive definiteness (the SPD test of eq. (1.3)) and
+ * forms P = Abar1^{-1}, B = P Abar2.  FP64 handles (and mixed ones with options.factor64)
+ * factor both matrices by FP64 Cholesky and form P from the factor; a mixed single dense
+ * handle inverts Abar1 by FP32 block Gauss-Jordan elimination and sweeps H the same way
+ * (its pivots are the Cholesky pivots), settling a failed FP32 pivot in FP64.  With
+ * options.estimate, rho and kappa are estimated by Lanczos (matrix-free route: an estimate
+ * rho >= 1 returns NOT_SPD).  Synchronizes the stream once to read the pivot status.
  * Errors: INVALID_ARG, OOM, CUDA, NOT_SPD (handle not created), NONFINITE. */
 ils_status ils_setup(ils_handle* h, int64_t m, int64_t n, int64_t p, int64_t q,
                      const double* A, int64_t lda, const ils_options* o, ils_stream_t stream);
@@ -172,7 +223,8 @@ ils_status ils_refactor_async(ils_handle h, const double* A, int64_t lda, ils_st
  *   b    length m, FP64.
  *   x    length n, FP64.  In: x0 unless x0_zero != 0.  Out: the solution.
  *   tol  stop once ||A^T J (b - A x_k)|| <= tol ||A^T J b|| (checked before each
- *        outer update, as in Sec. 5) or after max_outer updates.
+ *        outer update, as in Sec. 5) or after max_outer updates; options.stop_rule reads
+ *        tol instead as a bound on RR = relres^2 (Sec. 5) or on kappa_est * relres.
  *   info [host, out, may be NULL] iteration counts and the final relres.
  * Synchronizes the stream.  Errors: INVALID_ARG, NO_CONVERGENCE (x = last
  * iterate), NONFINITE, TIMEOUT, CUDA. */
@@ -323,10 +375,16 @@ ils_status ils_mlp_forward(ils_mlp net, int64_t count, const float* theta, doubl
 /* Solve for k parametric right-hand sides B(:, i) = b(theta(:, i)) starting from the
  * network's prediction (BF16 inference), as ils_solve_many with x0 = net(theta).  Since the
  * iteration converges from any start, the prediction only changes the iteration count.
- * Requires d_in of the net = rows of theta and d_out = n. */
+ * Requires d_in of the net = rows of theta and d_out = n.  net = NULL uses the network set by
+ * ils_set_warmstart (INVALID_ARG when none is set). */
 ils_status ils_solve_param(ils_handle h, ils_mlp net, int64_t k, const float* theta, const double* B, int64_t ldb,
                            double* X, int64_t ldx, double tol, ils_info* info, ils_stream_t stream);
 void ils_mlp_destroy(ils_mlp net);
+
+/* Attach a network to the handle (the handle does not own it; NULL detaches): a later
+ * ils_solve_param with net = NULL starts from this network's prediction.  Checks that the
+ * network's output size equals n.  Host only.  Errors: INVALID_ARG. */
+ils_status ils_set_warmstart(ils_handle h, ils_mlp net);
 
 /* Gram product C = X^T X (FP64) without any device allocation.  The paper has no
  * counterpart; this entry point exists for callers that cannot call cudaMalloc (for
@@ -352,6 +410,18 @@ ils_status ils_gram_noalloc(int64_t K, int64_t n, const double* X, int64_t ldx, 
  * route; the low-precision copy in the matching mixed precision).  For tests and
  * bandwidth measurements.  Errors: INVALID_ARG, CUDA. */
 ils_status ils_aq_product(ils_handle h, const double* x, double* v, int prec, ils_stream_t stream);
+
+/* Change options.wait_limit_ns of an existing handle (0 restores the default).  Host only.
+ * Errors: INVALID_ARG. */
+ils_status ils_set_wait_limit(ils_handle h, int64_t limit_ns);
+
+/* Diagnostic: record the column indices the randomized inner chain of the first right-hand
+ * side picks in the first outer iteration of each later solve: SP-SCD writes j_t at picks[t]
+ * (Alg. 5 step 9), SP-RK-RGS writes j1 at picks[2t] and j2 at picks[2t + 1] (Alg. 2 steps 8
+ * and 10); steps beyond capacity are not recorded.  picks is device memory owned by the
+ * caller (int32, capacity entries); NULL stops recording.  Dense handles only.
+ * Errors: INVALID_ARG. */
+ils_status ils_record_picks(ils_handle h, int32_t* picks, int64_t capacity);
 
 /* Release everything the handle owns (stream-ordered on the stream it was
  * created with).  NULL is ignored. */

@@ -38,6 +38,10 @@ ILS_ROUTE_MATRIX_FREE = 2
 ILS_GRAM_FP64 = 0
 ILS_GRAM_SPLIT = 1
 
+ILS_STOP_RELRES = 0
+ILS_STOP_PAPER_RR = 1
+ILS_STOP_ERR_BOUND = 2
+
 MAT_GRAM1, MAT_GRAM2, MAT_CHOL, MAT_P, MAT_B = range(5)
 
 
@@ -56,6 +60,17 @@ class ils_options(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("route", ctypes.c_int32),
         ("chain_ctas", ctypes.c_int32),
+        ("stop_rule", ctypes.c_int32),
+        ("estimate", ctypes.c_int32),
+        ("alpha_mode", ctypes.c_int32),
+        ("sampler", ctypes.c_int32),
+        ("alpha_fixed", ctypes.c_int64),
+        ("warm_inner", ctypes.c_int32),
+        ("inner_form", ctypes.c_int32),
+        ("tune_cache", ctypes.c_char_p),
+        ("wait_limit_ns", ctypes.c_int64),
+        ("lanczos_steps", ctypes.c_int32),
+        ("factor64", ctypes.c_int32),
     ]
 
 
@@ -72,6 +87,12 @@ class ils_info(ctypes.Structure):
         ("relres", ctypes.c_double),
         ("status", ctypes.c_int32),
         ("reserved", ctypes.c_int32),
+        ("err_bound", ctypes.c_double),
+        ("rho_est", ctypes.c_double),
+        ("kappa_est", ctypes.c_double),
+        ("t_setup_ms", ctypes.c_double),
+        ("t_solve_ms", ctypes.c_double),
+        ("t_inner_ms", ctypes.c_double),
     ]
 
     def as_dict(self):
@@ -120,7 +141,10 @@ SIGNATURES = {
     "ils_solve_param": (ctypes.c_int, [_P, _P, _I64, _P, _P, _I64, _P, _I64, ctypes.c_double,
                                        ctypes.POINTER(ils_info), _P]),
     "ils_mlp_destroy": (None, [_P]),
+    "ils_set_warmstart": (ctypes.c_int, [_P, _P]),
     "ils_gram_noalloc": (ctypes.c_int, [_I64, _I64, _P, _I64, _P, _I64, _P]),
+    "ils_set_wait_limit": (ctypes.c_int, [_P, _I64]),
+    "ils_record_picks": (ctypes.c_int, [_P, _P, _I64]),
     "ils_destroy": (None, [_P]),
     "ils_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "ils_last_error": (ctypes.c_char_p, []),
@@ -184,6 +208,8 @@ def options(**kw) -> ils_options:
     for k, v in kw.items():
         if not hasattr(o, k):
             raise KeyError(k)
+        if k == "tune_cache" and isinstance(v, str):
+            v = v.encode()
         setattr(o, k, v)
     return o
 
@@ -289,6 +315,32 @@ class Solver:
         """v = A_2^T (A_2 x) by the one-pass stream (prec 0 FP64, 1 FP32, 2 BF16 copy)."""
         return _check(lib().ils_aq_product(self.h, x.data_ptr(), v.data_ptr(), prec, _stream_ptr(stream)),
                       "ils_aq_product")
+
+    def record_picks(self, picks):
+        """Record the first chain's picks of the first outer iteration into the int32 CUDA
+        tensor `picks` (None stops recording); see ils_record_picks."""
+        ptr = None if picks is None else picks.data_ptr()
+        cap = 0 if picks is None else picks.numel()
+        return _check(lib().ils_record_picks(self.h, ptr, cap), "ils_record_picks")
+
+    def set_wait_limit(self, ns: int):
+        """ils_set_wait_limit: bound (ns) on the one-launch solve's barrier waits; 0 = default."""
+        return _check(lib().ils_set_wait_limit(self.h, int(ns)), "ils_set_wait_limit")
+
+    def set_warmstart(self, net):
+        """Attach a WarmStartNet (None detaches) for solve_param calls without a network."""
+        return _check(lib().ils_set_warmstart(self.h, None if net is None else net.h), "ils_set_warmstart")
+
+    def solve_param(self, theta, Bt, Xt, tol=1e-12, stream=None, allow=(ILS_OK,)):
+        """ils_solve_param with the attached network (ils_set_warmstart)."""
+        k = Bt.shape[0]
+        bp, ldb = _colmajor_ptr(Bt, self.m, k)
+        xp, ldx = _colmajor_ptr(Xt, self.n, k)
+        info = ils_info()
+        code = lib().ils_solve_param(self.h, None, k, theta.data_ptr(), bp, ldb, xp, ldx, float(tol),
+                                     ctypes.byref(info), _stream_ptr(stream))
+        _check(code, "ils_solve_param", allow)
+        return info
 
     def get_matrix(self, which: int, out, stream=None):
         ptr, ld = _colmajor_ptr(out, self.n, self.n)

@@ -809,7 +809,7 @@ __global__ void __launch_bounds__(32 * kIterWarps) sp_iter_kernel(SpIterArgs a) 
       double rr = 0.0;
       for (int ww = 0; ww < kIterWarps; ++ww) rr += rr_w[ww][c];
       const bool finite = isfinite(rr);
-      const bool conv = finite && rr <= a.tol2 * a.bnorm2[c];
+      const bool conv = finite && rr <= a.tol2 * (a.tol_scale ? *a.tol_scale : 1.0) * a.bnorm2[c];
       if (!finite || conv || it >= st->max_outer) {
         a.col_done[c] = 1;
         a.col_rr[c] = rr;

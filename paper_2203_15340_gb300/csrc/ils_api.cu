@@ -3,6 +3,7 @@
 // allocation carved into aligned pieces.
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -47,6 +48,22 @@ struct ils_handle_s {
   double* cum = nullptr;         // n: running sum of norms2
   double* vec_scratch = nullptr; // RK-RGS w and e when they do not fit in shared memory
   bool vec_in_smem = true;
+  double* alias_prob = nullptr;  // n: Vose alias table of the column law (options.sampler = 1)
+  int32_t* alias_idx = nullptr;  // n
+  int32_t* picks = nullptr;      // diagnostic pick record (ils_record_picks), caller's memory
+  int64_t picks_cap = 0;
+  unsigned long long* inner_ns = nullptr;  // device time of chain 0 (globaltimer ns)
+  unsigned long long* h_inner_ns = nullptr;
+  // estimates (options.estimate): [0] lambda_min(H), [1] lambda_max(H), [2] rho, [3] kappa,
+  // [4] 1 / kappa^2 (the tolerance scale of ILS_STOP_ERR_BOUND), [5] Lanczos steps (H),
+  // [6] Lanczos steps (rho), [7] status
+  double* est = nullptr;
+  double* h_est = nullptr;
+  float* lz_work = nullptr;      // matrix-free Lanczos vectors
+  ils_mlp warm_net = nullptr;    // ils_set_warmstart (not owned)
+  // overlapped setup with estimates: kappa(H) and rho on a fourth stream beside the inverse
+  cudaStream_t s_est = nullptr;
+  cudaEvent_t ev_p = nullptr, ev_estk = nullptr, ev_est = nullptr;  // P formed; kappa ready; all ready
   // mixed precision (options.precision != ILS_FP64)
   float* L32 = nullptr;
   float* P32 = nullptr;
@@ -120,6 +137,9 @@ struct ils_handle_s {
 namespace ils {
 static std::atomic<int64_t> g_launches{0};
 void note_launch(int64_t count) { g_launches.fetch_add(count, std::memory_order_relaxed); }
+int64_t handle_n(ils_handle h) { return h->n; }
+ils_mlp handle_warm_net(ils_handle h) { return h->warm_net; }
+void handle_set_warm_net(ils_handle h, ils_mlp net) { h->warm_net = net; }
 }  // namespace ils
 
 namespace {
@@ -214,6 +234,12 @@ void carve(ils_handle h, Carver& c, size_t work_elems) {
   if (h->sparse) h->vec_in_smem = false;
   const bool need_scratch = h->opt.method == ILS_SP_RK_RGS && !h->vec_in_smem;
   h->vec_scratch = c.take<double>(need_scratch ? (size_t)kMaxRhsPerPass * 2 * (size_t)h->p : 1);
+  const bool alias = h->opt.method == ILS_SP_RK_RGS && h->opt.sampler == 1;
+  h->alias_prob = c.take<double>(alias ? (size_t)h->n : 1);
+  h->alias_idx = c.take<int32_t>(alias ? (size_t)h->n : 1);
+  h->inner_ns = c.take<unsigned long long>(1);
+  h->est = c.take<double>(16);
+  h->lz_work = c.take<float>(h->mf && h->opt.estimate ? lz_mf_work_floats(h->n) + (size_t)h->n * h->n : 1);
   if (h->mf) {
     const size_t rows = (size_t)h->q * (size_t)aq_row_stride(h->n);
     h->Aq64r = c.take<double>(rows);
@@ -287,8 +313,18 @@ ils_status validate_options(const ils_options* o) {
   if (o->max_outer < 0 || o->max_inner < 0 || o->check_every < 0) return ILS_ERR_INVALID_ARG;
   if (o->gram != ILS_GRAM_FP64 && o->gram != ILS_GRAM_SPLIT) return ILS_ERR_INVALID_ARG;
   if (!(o->theta > 0.0)) return ILS_ERR_INVALID_ARG;
+  if (o->stop_rule < ILS_STOP_RELRES || o->stop_rule > ILS_STOP_ERR_BOUND) return ILS_ERR_INVALID_ARG;
+  if (o->alpha_mode < 0 || o->alpha_mode > 1 || o->sampler < 0 || o->sampler > 1) return ILS_ERR_INVALID_ARG;
+  if (o->inner_form < 0 || o->inner_form > 1 || o->wait_limit_ns < 0) return ILS_ERR_INVALID_ARG;
+  if (o->lanczos_steps < 0 || o->lanczos_steps > 256) return ILS_ERR_INVALID_ARG;
   return ILS_OK;
 }
+
+// Squared relres target of a solve's `tol` under options.stop_rule: relres <= tol (tol^2), Sec. 5's
+// RR = relres^2 <= tol (tol), or kappa_est relres <= tol (tol^2, scaled on the device by
+// 1 / kappa_est^2 through tol_scale_of).
+double tol2_of(ils_handle h, double tol) { return h->opt.stop_rule == ILS_STOP_PAPER_RR ? tol : tol * tol; }
+const double* tol_scale_of(ils_handle h) { return h->opt.stop_rule == ILS_STOP_ERR_BOUND ? h->est + 4 : nullptr; }
 
 cudaError_t mark(ils_handle h, int i) {
   if (!h->opt.timing) return cudaSuccess;
@@ -328,6 +364,55 @@ void collect_timings(ils_handle h) {
   h->t_ms[6] = el(6, 7);
 }
 
+// Lanczos estimates (options.estimate) of kappa(H) (standard Lanczos on H) and rho (Lanczos
+// on Abar2 P in the P inner product), enqueued on s; either operator may be absent.  The
+// results reach h_est with the same stream's work.
+ils_status enqueue_estimates(ils_handle h, cudaStream_t s, const void* Hm, int h64, const void* G2m, int g64,
+                             const void* Pm, int p64) {
+  LanczosProblem pr[2];
+  int cnt = 0;
+  const int steps = h->opt.lanczos_steps > 0 ? h->opt.lanczos_steps : 64;
+  double* kap_out = h->est + 8;
+  double* rho_out = h->est + 12;
+  if (Hm) pr[cnt++] = LanczosProblem{h->n, Hm, nullptr, h64, 0, steps, 0, kap_out};
+  if (G2m && Pm) pr[cnt++] = LanczosProblem{h->n, G2m, Pm, g64, p64, steps, 0, rho_out};
+  if (cnt == 0) return ILS_OK;
+  ILS_CK(lanczos_extremes(cnt, pr, s));
+  ILS_CK(estimates_finish(Hm ? kap_out : nullptr, (G2m && Pm) ? rho_out : nullptr, h->est, s));
+  ILS_CK(cudaMemcpyAsync(h->h_est, h->est, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  return ILS_OK;
+}
+
+// Matrix-free estimates: kappa(Abar1) by standard Lanczos on Abar1, rho by Lanczos on
+// (A_2^T A_2) P streaming A_2 once per step, and kappa(H) <= kappa(Abar1) / (1 - rho).
+ils_status enqueue_estimates_mf(ils_handle h) {
+  cudaStream_t s = h->stream;
+  const int64_t n = h->n;
+  const int steps = h->opt.lanczos_steps > 0 ? h->opt.lanczos_steps : 64;
+  double* kap_out = h->est + 8;
+  double* rho_out = h->est + 12;
+  LanczosProblem pr = {n, h->G1, nullptr, 1, 0, steps, 0, kap_out};
+  ILS_CK(lanczos_extremes(1, &pr, s));
+  float* w = h->lz_work;
+  const float* P32 = h->P32;
+  if (h->opt.precision == ILS_FP64) {  // an FP32 copy of P for the estimate
+    float* pc = w + lz_mf_work_floats(n);
+    ILS_CK(convert_f64_to_f32(n * n, h->P, pc, s));
+    P32 = pc;
+  }
+  const int prec = h->opt.precision == ILS_FP64 ? 0 : (h->opt.precision == ILS_FP32_REFINE ? 1 : 2);
+  const void* Ar = prec == 0 ? h->Aq64r : h->Aq_lo;
+  ILS_CK(lz_mf_init(n, P32, w, s));
+  for (int j = 0; j < steps; ++j) {
+    ILS_CK(aq_product(h->q, n, Ar, prec, lz_mf_vector(n, w), h->sp_part, h->vbuf, s));
+    ILS_CK(lz_mf_step(n, P32, h->vbuf, w, j, s));
+  }
+  ILS_CK(lz_mf_finish(n, w, rho_out, s));
+  ILS_CK(estimates_finish(kap_out, rho_out, h->est, s, /*gram_bound=*/true));
+  ILS_CK(cudaMemcpyAsync(h->h_est, h->est, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  return ILS_OK;
+}
+
 // Matrix-free route after Abar1: Cholesky of Abar1, P (FP64, or FP32 for the mixed
 // precisions) and the row-major copies of A_2 that every step streams.  Abar2 and H are
 // never formed, so the SPD test of (1.3) reduces to Abar1's pivots; a matrix with
@@ -357,6 +442,10 @@ ils_status compute_setup_mf(ils_handle h) {
     ILS_CK(set_identity_f64(n, h->P, n, s));
     ILS_CK(trsm_binv_f64(n, n, h->L, h->Dinv, h->P, n, true, true, s));
   }
+  if (h->opt.estimate) {
+    const ils_status es = enqueue_estimates_mf(h);
+    if (es != ILS_OK) return es;
+  }
   ILS_CK(mark(h, 5));
   return ILS_OK;
 }
@@ -369,10 +458,13 @@ ils_status compute_setup_sparse(ils_handle h, const int32_t* rowptr, const int32
   ILS_CK(mark(h, 0));
   ILS_CK(mark(h, 1));
   ILS_CK(cudaMemsetAsync(h->sp_err, 0, sizeof(int32_t), s));
+  ILS_CK(cudaMemsetAsync(h->est, 0, 16 * sizeof(double), s));
   ILS_CK(sparse_setup(h->m, h->n, h->p, h->nnz, rowptr, colind, val, h->sc, h->cnt_fill, h->G1, h->G2, h->sp_err, s));
   ILS_CK(cudaMemcpyAsync(h->h_status + 2, h->sp_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   ILS_CK(mark(h, 2));
   if (h->opt.method != ILS_SP) ILS_CK(column_cumsum_f64(h->n, h->G1, h->norms2, h->cum, s));
+  if (h->opt.method == ILS_SP_RK_RGS && h->opt.sampler == 1)
+    ILS_CK(alias_table_f64(h->n, h->norms2, h->alias_prob, h->alias_idx, s));
   if (h->opt.method == ILS_SP_RK_RGS)
     ILS_CK(sparse_chain_prep(h->n, h->sc, h->G1, h->norms2, h->opt.precision == ILS_FP32_REFINE, s));
   ILS_CK(mark(h, 3));
@@ -387,6 +479,7 @@ ils_status compute_setup(ils_handle h) {
   cudaStream_t s = h->stream;
   const int64_t m = h->m, n = h->n, p = h->p, q = h->q;
   ILS_CK(mark(h, 1));
+  ILS_CK(cudaMemsetAsync(h->est, 0, 16 * sizeof(double), s));
   // Abar1 = A_1^T A_1, Abar2 = A_2^T A_2 (Alg. 1 steps 2-3; Alg. 2 step 2; Alg. 5 step 2).
   if (h->opt.gram == ILS_GRAM_SPLIT) {
     ILS_CK(cudaMemsetAsync(h->gs_err, 0, sizeof(int32_t), s));
@@ -397,6 +490,8 @@ ils_status compute_setup(ils_handle h) {
   }
   ILS_CK(mark(h, 2));
   if (h->opt.method != ILS_SP) ILS_CK(column_cumsum_f64(n, h->G1, h->norms2, h->cum, s));
+  if (h->opt.method == ILS_SP_RK_RGS && h->opt.sampler == 1)
+    ILS_CK(alias_table_f64(n, h->norms2, h->alias_prob, h->alias_idx, s));
   if (h->mf) return compute_setup_mf(h);
   if (h->opt.gram == ILS_GRAM_SPLIT) {
     ILS_CK(gram_split_tc(q, n, h->A + p, m, h->G2, n, h->gs_slices, h->gs_partial, h->gs_exps, h->gs_err, s));
@@ -444,6 +539,13 @@ ils_status compute_products(ils_handle h) {
     ILS_CK(trsm_binv_f64(n, n, h->L, h->Dinv, h->P, n, true, true, s));
     ILS_CK(gemm_tn_f64(n, n, n, h->G2, n, h->P, n, n, h->Bt, n, false, false, h->work, s));
   }
+  if (h->opt.estimate) {
+    ils_status es;
+    if (h->opt.method != ILS_SP) es = enqueue_estimates(h, s, h->H, 1, nullptr, 0, nullptr, 0);
+    else if (h->opt.precision != ILS_FP64) es = enqueue_estimates(h, s, h->H, 1, h->G2_32, 0, h->P32, 0);
+    else es = enqueue_estimates(h, s, h->H, 1, h->G2, 1, h->P, 1);
+    if (es != ILS_OK) return es;
+  }
   ILS_CK(mark(h, 5));
   return ILS_OK;
 }
@@ -470,8 +572,11 @@ ils_status compute_setup_overlap(ils_handle h, const double* src, int64_t lda_sr
     src = h->A;
     lda_src = m;
   }
-  // The previous setup's test of H may still run on the third stream: it reads G1, G2 and H32.
+  // The previous setup's test of H may still run on the third stream: it reads G1, G2 and H32
+  // (and its estimates on the fourth: H32, G2_32 and P32).
   ILS_CK(cudaStreamWaitEvent(s, h->ev_h, 0));
+  if (h->ev_est) ILS_CK(cudaStreamWaitEvent(s, h->ev_est, 0));
+  ILS_CK(cudaMemsetAsync(h->est, 0, 16 * sizeof(double), s));
   ILS_CK(mark(h, 1));
   h->h_status[0] = 0;
   h->l64_valid = false;
@@ -513,6 +618,23 @@ ils_status compute_setup_overlap(ils_handle h, const double* src, int64_t lda_sr
     ILS_CK(spd_inverse_f32(n, 1, mat2, out2, h->gj2, st2, t, /*wide_first=*/true));
     ILS_CK(cudaMemcpyAsync(h->h_status + 3, h->dstatus2, sizeof(int32_t), cudaMemcpyDeviceToHost, t));
     ILS_CK(cudaEventRecord(h->ev_h, t));
+    if (h->opt.estimate) {
+      // kappa(H) once H is formed, beside the inverse; rho once P is formed.
+      cudaStream_t e = h->s_est;
+      const int steps = h->opt.lanczos_steps > 0 ? h->opt.lanczos_steps : 64;
+      ILS_CK(cudaEventRecord(h->ev_p, s));
+      ILS_CK(cudaStreamWaitEvent(e, h->ev_hd, 0));
+      LanczosProblem pk = {n, h->H32, nullptr, 0, 0, steps, 0, h->est + 8};
+      ILS_CK(lanczos_extremes(1, &pk, e));
+      ILS_CK(estimates_finish(h->est + 8, nullptr, h->est, e));
+      ILS_CK(cudaEventRecord(h->ev_estk, e));
+      ILS_CK(cudaStreamWaitEvent(e, h->ev_p, 0));
+      LanczosProblem pr = {n, h->G2_32, h->P32, 0, 0, steps, 0, h->est + 12};
+      ILS_CK(lanczos_extremes(1, &pr, e));
+      ILS_CK(estimates_finish(nullptr, h->est + 12, h->est, e));
+      ILS_CK(cudaMemcpyAsync(h->h_est, h->est, 8 * sizeof(double), cudaMemcpyDeviceToHost, e));
+      ILS_CK(cudaEventRecord(h->ev_est, e));
+    }
   } else {
     if (gj != cudaErrorNotSupported) ILS_CK(gj);
     cudaGetLastError();
@@ -529,10 +651,17 @@ ils_status compute_setup_overlap(ils_handle h, const double* src, int64_t lda_sr
   else
     ILS_CK(mixed_setup(n, nullptr, h->G2, h->opt.precision, h->L32, h->P32, h->G2_32, h->Bt32, h->Bt16,
                        reinterpret_cast<float*>(h->Dinv), s));
-  if (inverted)
+  if (inverted) {
     ILS_CK(cudaStreamWaitEvent(s, h->ev_hd, 0));  // the solve's residuals read H
-  else
+  } else {
     ILS_CK(cudaMemcpyAsync(h->h_status + 3, h->dstatus2, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    if (h->opt.estimate) {
+      const ils_status es = enqueue_estimates(h, s, h->H, 1, h->G2_32, 0, h->P32, 0);
+      if (es != ILS_OK) return es;
+      ILS_CK(cudaEventRecord(h->ev_estk, s));
+      ILS_CK(cudaEventRecord(h->ev_est, s));
+    }
+  }
   ILS_CK(cudaMemcpyAsync(h->h_status + 6, h->dstatus, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   ILS_CK(cudaMemcpyAsync(h->h_status + 1, h->gs_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   ILS_CK(mark(h, 5));
@@ -561,6 +690,8 @@ ils_status factor_f64_now(ils_handle h) {
 ils_status setup_check(ils_handle h, bool* redone) {
   if (redone) *redone = false;
   if (h->overlap && h->s_h) ILS_CK(cudaStreamSynchronize(h->s_h));  // the test of H
+  if (h->s_est) ILS_CK(cudaStreamSynchronize(h->s_est));             // the estimates
+  if (h->mf && h->opt.estimate && h->h_est[7] != 0.0) return (ils_status)(int)h->h_est[7];  // rho >= 1
   if (h->sparse && h->h_status[2] != 0) return (ils_status)h->h_status[2];
   h->h_status[1] = h->opt.gram == ILS_GRAM_SPLIT ? h->h_status[1] : 0;
   if (h->h_status[1] != 0) return h->h_status[1] == 2 ? ILS_ERR_NONFINITE : ILS_ERR_TIMEOUT;
@@ -608,12 +739,13 @@ ils_status tune_handle(ils_handle h) {
 void free_handle(ils_handle h) {
   if (!h) return;
   if (h->block) cudaFreeAsync(h->block, h->stream);
-  for (cudaStream_t x : {h->s_aux, h->s_h})
+  for (cudaStream_t x : {h->s_aux, h->s_h, h->s_est})
     if (x) {
       cudaStreamSynchronize(x);
       cudaStreamDestroy(x);
     }
-  for (cudaEvent_t e : {h->ev_start, h->ev_g2, h->ev_g1, h->ev_hd, h->ev_h, h->ev_acopy, h->ev_rhs})
+  for (cudaEvent_t e : {h->ev_start, h->ev_g2, h->ev_g1, h->ev_hd, h->ev_h, h->ev_acopy, h->ev_rhs, h->ev_p,
+                        h->ev_estk, h->ev_est})
     if (e) cudaEventDestroy(e);
   if (h->h_st) cudaFreeHost(h->h_st);
   for (cudaEvent_t e : h->ev)
@@ -655,6 +787,7 @@ ils_status pass_begin(ils_handle h, int64_t c0, int64_t kk, const double* B, int
     ILS_CK(cudaMemcpy2DAsync(h->X0, sizeof(double) * n, X, sizeof(double) * ldx, sizeof(double) * n, kk,
                              cudaMemcpyDeviceToDevice, s));
   }
+  if (h->opt.stop_rule == ILS_STOP_ERR_BOUND && h->ev_estk) ILS_CK(cudaStreamWaitEvent(s, h->ev_estk, 0));
   init_state_kernel<<<1, 32, 0, s>>>(h->st, h->opt.max_outer, h->col_done, h->col_inner, (int)kk);
   note_launch();
   ILS_CK(cudaGetLastError());
@@ -662,7 +795,8 @@ ils_status pass_begin(ils_handle h, int64_t c0, int64_t kk, const double* B, int
   a.n = n;
   a.k = kk;
   const bool mixed = h->opt.precision != ILS_FP64;
-  a.mode = h->mf ? (mixed ? 4 : 3) : (mixed ? 2 : (method == ILS_SP ? 0 : 1));
+  const bool warm = method != ILS_SP && h->opt.warm_inner != 0;  // inner solves start at x_k
+  a.mode = h->mf ? (mixed ? 4 : 3) : ((mixed || warm) ? 2 : (method == ILS_SP ? 0 : 1));
   a.vvec = h->vbuf;
   a.pad = 0;
   a.Bt = h->mf ? h->P : (method == ILS_SP ? h->Bt : h->G2);
@@ -675,7 +809,9 @@ ils_status pass_begin(ils_handle h, int64_t c0, int64_t kk, const double* B, int
   a.bnorm2 = h->bnorm2;
   a.X0 = h->X0;
   a.X1 = h->X1;
-  a.tol2 = tol * tol;
+  a.tol2 = tol2_of(h, tol);
+  a.tol_scale = tol_scale_of(h);
+  a.wait_ns = h->opt.wait_limit_ns;
   a.col_done = h->col_done;
   a.col_rr = h->col_rr;
   a.col_iters = h->col_iters;
@@ -704,8 +840,17 @@ ils_status pass_begin(ils_handle h, int64_t c0, int64_t kk, const double* B, int
   ra.greedy = h->opt.scd_sampler == 1 ? 1 : 0;
   ra.same_index = h->opt.scd_sampler == 2 ? 1 : 0;
   ra.vec_in_smem = h->vec_in_smem ? 1 : 0;
-  ra.correction = mixed && h->sparse && method == ILS_SP_RK_RGS ? 1 : 0;
+  ra.correction = (mixed && h->sparse && method == ILS_SP_RK_RGS) || warm ? 1 : 0;
   ra.vec_scratch = h->vec_scratch;
+  ra.alpha_fixed = method == ILS_SP_SCD && h->opt.alpha_mode == 1 ? h->opt.alpha_fixed : 0;
+  ra.gram_form = h->opt.inner_form;
+  ra.alias = method == ILS_SP_RK_RGS && h->opt.sampler == 1 ? 1 : 0;
+  ra.alias_prob = h->alias_prob;
+  ra.alias_idx = h->alias_idx;
+  ra.picks = c0 == 0 ? h->picks : nullptr;
+  ra.picks_cap = h->picks_cap;
+  ra.inner_ns = c0 == 0 ? h->inner_ns : nullptr;
+  if (c0 == 0 && method != ILS_SP) ILS_CK(cudaMemsetAsync(h->inner_ns, 0, sizeof(unsigned long long), s));
   MixedArgs ma;
   ma.n = n;
   ma.k = kk;
@@ -812,6 +957,8 @@ ils_status pass_finish_enqueue(ils_handle h, double* X, int64_t ldx) {
   ILS_CK(cudaMemcpyAsync(h->h_bn, h->bnorm2, sizeof(double) * kk, cudaMemcpyDeviceToHost, s));
   ILS_CK(cudaMemcpyAsync(h->h_iters, h->col_iters, sizeof(int64_t) * kk, cudaMemcpyDeviceToHost, s));
   ILS_CK(cudaMemcpyAsync(h->h_inner, h->col_inner, sizeof(int64_t) * kk, cudaMemcpyDeviceToHost, s));
+  if (h->opt.method != ILS_SP && h->pra.chain0 == 0)
+    ILS_CK(cudaMemcpyAsync(h->h_inner_ns, h->inner_ns, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
   return ILS_OK;
 }
 
@@ -853,7 +1000,7 @@ wide_step_kernel(int64_t n, const double* __restrict__ BX, const double* __restr
                  const double* __restrict__ bb, const double* __restrict__ cc, const double* __restrict__ bn,
                  const double* __restrict__ Xa, double* __restrict__ Xb, int32_t* __restrict__ done,
                  double* __restrict__ rr_out, int64_t* __restrict__ iters, int64_t it, int64_t max_outer, double tol2,
-                 int32_t* __restrict__ remaining, int32_t* __restrict__ status) {
+                 const double* __restrict__ tol_scale, int32_t* __restrict__ remaining, int32_t* __restrict__ status) {
   const int64_t c = blockIdx.x;
   const size_t off = (size_t)c * n;
   __shared__ double red[kWideThreads / 32];
@@ -874,7 +1021,7 @@ wide_step_kernel(int64_t n, const double* __restrict__ BX, const double* __restr
     double rr = 0.0;
     for (int w = 0; w < kWideThreads / 32; ++w) rr += red[w];
     const bool finite = isfinite(rr);
-    const bool conv = finite && rr <= tol2 * bn[c];
+    const bool conv = finite && rr <= tol2 * (tol_scale ? *tol_scale : 1.0) * bn[c];
     finish = (!finite || conv || it >= max_outer) ? 1 : 0;
     if (finish) {
       done[c] = 1;
@@ -960,7 +1107,8 @@ ils_status wide_solve(ils_handle h, int64_t k, const double* B, int64_t ldb, dou
     if (st == ILS_OK) ck(gemm_tn_f64(n, n, k, h->H, n, Xa, n, n, HX, n, false, false, wk, s), "gemm H x", __LINE__);
     if (st != ILS_OK) break;
     wide_step_kernel<<<(unsigned)k, kWideThreads, 0, s>>>(n, BX, HX, bb, cc, bn, Xa, Xb, dn, rr, itv, it,
-                                                          h->opt.max_outer, tol * tol, rem, stt);
+                                                          h->opt.max_outer, tol2_of(h, tol), tol_scale_of(h), rem,
+                                                          stt);
     note_launch();
     if (!ck(cudaGetLastError(), "wide step", __LINE__)) break;
     std::swap(Xa, Xb);
@@ -1015,6 +1163,13 @@ ils_status create_handle(ils_handle* out, int64_t m, int64_t n, int64_t p, int64
   else ils_options_default(&opt);
   if (validate_options(&opt) != ILS_OK) return ILS_ERR_INVALID_ARG;
   if (opt.route < ILS_ROUTE_AUTO || opt.route > ILS_ROUTE_MATRIX_FREE) return ILS_ERR_INVALID_ARG;
+  if (opt.stop_rule == ILS_STOP_ERR_BOUND) opt.estimate = 1;  // the rule reads kappa_est
+  if (opt.method == ILS_SP_SCD && opt.alpha_mode == 1 && (opt.alpha_fixed < 1 || opt.alpha_fixed > n))
+    return ILS_ERR_INVALID_ARG;
+  // The Gram-space chain keeps three n-vectors in registers (n <= 8192); the sparse chains have
+  // their own column sampling (inverse CDF) and column form.
+  if (opt.inner_form == 1 && (opt.method != ILS_SP_RK_RGS || sparse || n > 8192)) return ILS_ERR_INVALID_ARG;
+  if (opt.sampler == 1 && (opt.method != ILS_SP_RK_RGS || sparse)) return ILS_ERR_INVALID_ARG;
   if (sparse) {
     // The Grams of a sparse A come from its stored entries (FP64); the route is explicit.
     if (opt.route == ILS_ROUTE_MATRIX_FREE) return ILS_ERR_INVALID_ARG;
@@ -1049,7 +1204,7 @@ ils_status create_handle(ils_handle* out, int64_t m, int64_t n, int64_t p, int64
   h->nnz = sparse ? sparse_nnz : 0;
   h->stream = stream;
   h->overlap = overlap_ok && !sparse && !mf && opt.method == ILS_SP && opt.precision != ILS_FP64 &&
-               opt.gram == ILS_GRAM_SPLIT && q > 0;
+               opt.gram == ILS_GRAM_SPLIT && q > 0 && !opt.factor64;
   if (sparse && opt.method == ILS_SP_RK_RGS && opt.chain_ctas >= 0) {
     const double col_entries = (double)sparse_nnz * ((double)p / (double)m) / (double)n;  // A_1 entries per column
     const bool fp32 = opt.precision == ILS_FP32_REFINE;
@@ -1077,6 +1232,11 @@ ils_status create_handle(ils_handle* out, int64_t m, int64_t n, int64_t p, int64
               cudaStreamCreateWithFlags(&h->s_h, cudaStreamNonBlocking) == cudaSuccess;
     for (cudaEvent_t* e : {&h->ev_start, &h->ev_g2, &h->ev_g1, &h->ev_hd, &h->ev_h, &h->ev_acopy, &h->ev_rhs})
       ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
+    if (h->opt.estimate) {
+      ok = ok && cudaStreamCreateWithFlags(&h->s_est, cudaStreamNonBlocking) == cudaSuccess;
+      for (cudaEvent_t* e : {&h->ev_p, &h->ev_estk, &h->ev_est})
+        ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
+    }
     if (!ok) {
       cudaGetLastError();
       free_handle(h);
@@ -1084,7 +1244,8 @@ ils_status create_handle(ils_handle* out, int64_t m, int64_t n, int64_t p, int64
     }
   }
   const size_t host_bytes = align_up(sizeof(SolveState)) + align_up(sizeof(int32_t)) +
-                            4 * align_up(sizeof(double) * kMaxRhsPerPass);
+                            4 * align_up(sizeof(double) * kMaxRhsPerPass) + align_up(sizeof(unsigned long long)) +
+                            align_up(8 * sizeof(double));
   char* hb = nullptr;
   if (cudaMallocHost((void**)&hb, host_bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -1102,6 +1263,12 @@ ils_status create_handle(ils_handle* out, int64_t m, int64_t n, int64_t p, int64
   h->h_iters = (int64_t*)hb;
   hb += align_up(sizeof(double) * kMaxRhsPerPass);
   h->h_inner = (int64_t*)hb;
+  hb += align_up(sizeof(double) * kMaxRhsPerPass);
+  h->h_inner_ns = (unsigned long long*)hb;
+  hb += align_up(sizeof(unsigned long long));
+  h->h_est = (double*)hb;
+  for (int i = 0; i < 8; ++i) h->h_est[i] = 0.0;
+  *h->h_inner_ns = 0ull;
   *out = h;
   return ILS_OK;
 }
@@ -1241,8 +1408,36 @@ int ils_tuned_shape(int64_t n, int64_t k, int bf16, int* warps, int* blocks) {
 ils_status solve_many_now(ils_handle h, int64_t k, const double* B, int64_t ldb, double* X, int64_t ldx,
                           int x0_zero, double tol, ils_info* info);
 
+// The fields of ils_info beyond the iteration counts: the estimates, the certificate
+// err_bound = kappa_est * relres and the times.
+void fill_info_extras(ils_handle h, ils_info* agg, std::chrono::steady_clock::time_point t0) {
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  agg->t_solve_ms = ms;
+  agg->t_setup_ms = h->t_ms[4];
+  agg->t_inner_ms = h->opt.method != ILS_SP ? (double)*h->h_inner_ns * 1e-6 : 0.0;
+  if (h->opt.estimate) {
+    agg->rho_est = h->h_est[2];
+    agg->kappa_est = h->h_est[3];
+    agg->err_bound = agg->kappa_est * agg->relres;
+  }
+}
+
+ils_status solve_many_checked(ils_handle h, int64_t k, const double* B, int64_t ldb, double* X, int64_t ldx,
+                              int x0_zero, double tol, ils_info* info, ils_stream_t stream);
+
 ils_status ils_solve_many(ils_handle h, int64_t k, const double* B, int64_t ldb, double* X, int64_t ldx,
                           int x0_zero, double tol, ils_info* info, ils_stream_t stream) {
+  const auto t0 = std::chrono::steady_clock::now();
+  ils_info agg;
+  std::memset(&agg, 0, sizeof(agg));
+  const ils_status st = solve_many_checked(h, k, B, ldb, X, ldx, x0_zero, tol, &agg, stream);
+  if (h && st != ILS_ERR_INVALID_ARG) fill_info_extras(h, &agg, t0);
+  if (info) *info = agg;
+  return st;
+}
+
+ils_status solve_many_checked(ils_handle h, int64_t k, const double* B, int64_t ldb, double* X, int64_t ldx,
+                              int x0_zero, double tol, ils_info* info, ils_stream_t stream) {
   if (!h || k < 0 || (k > 0 && (!B || !X)) || ldb < h->m || ldx < h->n || !(tol >= 0.0))
     return ILS_ERR_INVALID_ARG;
   h->stream = (cudaStream_t)stream;
@@ -1263,7 +1458,7 @@ ils_status ils_solve_many(ils_handle h, int64_t k, const double* B, int64_t ldb,
       if (info) *info = agg;
       return sst;
     }
-    if (redone) return ils_solve_many(h, k, B, ldb, X, ldx, x0_zero, tol, info, stream);
+    if (redone) return solve_many_checked(h, k, B, ldb, X, ldx, x0_zero, tol, info, stream);
     if (info) *info = agg;
     return st;
   }
@@ -1329,6 +1524,19 @@ ils_status ils_get_matrix(ils_handle h, int which, double* dst, int64_t ldd, ils
   }
   ILS_CK(cudaMemcpy2DAsync(dst, sizeof(double) * ldd, src, sizeof(double) * n, sizeof(double) * n, n,
                            cudaMemcpyDeviceToDevice, s));
+  return ILS_OK;
+}
+
+ils_status ils_set_wait_limit(ils_handle h, int64_t limit_ns) {
+  if (!h || limit_ns < 0) return ILS_ERR_INVALID_ARG;
+  h->opt.wait_limit_ns = limit_ns;
+  return ILS_OK;
+}
+
+ils_status ils_record_picks(ils_handle h, int32_t* picks, int64_t capacity) {
+  if (!h || h->sparse || capacity < 0 || (picks && capacity == 0)) return ILS_ERR_INVALID_ARG;
+  h->picks = picks;
+  h->picks_cap = picks ? capacity : 0;
   return ILS_OK;
 }
 

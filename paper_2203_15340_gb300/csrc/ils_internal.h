@@ -24,6 +24,11 @@ struct SolveState {
 
 constexpr int kMaxRhsPerPass = 8;  // right-hand sides carried per iteration launch
 
+// Accessors of the handle for the other translation units.
+int64_t handle_n(ils_handle h);
+ils_mlp handle_warm_net(ils_handle h);
+void handle_set_warm_net(ils_handle h, ils_mlp net);
+
 // Host-side count of kernel launches made by this library (reported by ils_kernel_launches).
 void note_launch(int64_t count = 1);
 
@@ -122,7 +127,10 @@ struct SpIterArgs {
   double* X1;
   double* bhat_out;    // n x k (modes 1, 2, 4)
   const double* vvec;  // n x k: A_2^T (A_2 x_k) (modes 3, 4)
-  double tol2;         // tol^2
+  double tol2;         // squared relres target (tol^2, or tol for Sec. 5's RR rule)
+  const double* tol_scale;  // device scalar multiplying tol2 (1 / kappa_est^2 for the error-bound
+                            // rule), or nullptr
+  int64_t wait_ns;          // bound on the grid-barrier waits of the one-launch solve; 0 = 1 s
   double theta2;       // theta^2 (mode 1): inner target = theta^2 ||r_k||^2
   double* col_target2; // k (mode 1)
   int32_t* col_done;   // k flags
@@ -259,10 +267,22 @@ struct RandArgs {
   int32_t greedy;         // SCD: alpha = n
   int32_t same_index;     // RK-RGS: j2 = j1 (the SP-RCD special case)
   int32_t vec_in_smem;    // RK-RGS: w, e in shared memory
-  int32_t correction;     // sparse RK-RGS in FP32: bhat holds r = bbar - H x_k, the chain
-                          // solves Abar1 d = r and x_k += d in place
+  int32_t correction;     // bhat holds r = bbar - H x_k; the chain solves Abar1 d = r from d = 0
+                          // and x_k += d in place (sparse RK-RGS in FP32, and the warm inner
+                          // start of the dense chains: the start z = x_k of Alg. 2 / beta = x_k of
+                          // Alg. 5 in correction form)
   double* vec_scratch;    // RK-RGS: k x 2p when not in shared memory
+  int64_t alpha_fixed;    // SCD: 0 = alpha ~ U{1..n} (Alg. 5); else the fixed subset size
+  int32_t gram_form;      // dense RK-RGS: Gram-space steps (g = Abar1 y, h = Abar1 z)
+  int32_t alias;          // RK-RGS: column draws from the alias table below
+  const double* alias_prob;  // n: acceptance probability of column j
+  const int32_t* alias_idx;  // n: alias of column j
+  int32_t* picks;         // diagnostic: chain 0's picks in outer iteration 0 (or nullptr)
+  int64_t picks_cap;
+  unsigned long long* inner_ns;  // accumulated device time of chain 0's launches (or nullptr)
 };
+// Vose alias table of the column law norms2 / sum(norms2) (n <= 16384), one CTA.
+cudaError_t alias_table_f64(int64_t n, const double* norms2, double* prob, int32_t* alias, cudaStream_t s);
 // Sparse A: column-sorted CSC of all of A; split[j] = entries of column j in rows < p.
 struct SparseCols {
   int32_t* colptr;  // n + 1
@@ -294,6 +314,35 @@ int rkrgs_cluster_plan(int64_t n, int64_t p, bool fp32, int want, double col_ent
 // padded copy of Abar1 the cluster chain reads.
 cudaError_t sparse_chain_prep(int64_t n, SparseCols sc, const double* G1, const double* norms2, bool fp32,
                               cudaStream_t s);
+
+// ---- Lanczos estimates (lanczos.cu) -----------------------------------------------------------
+// Extreme eigenvalues of C = M2 M1 in the M1 inner product (M1 == nullptr: standard Lanczos on
+// the symmetric M2).  M2, M1: n x n symmetric, FP64 (f64 != 0) or FP32.  out (device):
+// [0] smallest, [1] largest Ritz value after `steps` steps (<= 256), [2] steps taken.
+struct LanczosProblem {
+  int64_t n;
+  const void* M2;
+  const void* M1;
+  int32_t m2_f64, m1_f64;
+  int32_t steps;
+  int32_t pad;
+  double* out;
+};
+// Up to four problems of equal n in one launch, one thread-block cluster each.
+cudaError_t lanczos_extremes(int count, const LanczosProblem* probs, cudaStream_t s);
+// est[0..7] (see the handle) from the outputs of the kappa (H) and rho problems (either may be null).
+// est[7] (status) must be 0 before the first call of a setup; later calls keep a failure.
+cudaError_t estimates_finish(const double* kap_out, const double* rho_out, double* est, cudaStream_t s,
+                             bool gram_bound = false);
+// Matrix-free rho: Lanczos on (A_2^T A_2) P in the P inner product, P FP32 (n <= 512).  w holds
+// lz_mf_work_floats(n) floats; lz_mf_vector(n, w) is the FP64 vector t_j whose product
+// y = A_2^T (A_2 t_j) each lz_mf_step(j) consumes; lz_mf_finish writes out[0..2] like
+// lanczos_extremes.
+size_t lz_mf_work_floats(int64_t n);
+cudaError_t lz_mf_init(int64_t n, const float* P, float* w, cudaStream_t s);
+double* lz_mf_vector(int64_t n, float* w);
+cudaError_t lz_mf_step(int64_t n, const float* P, const double* y, float* w, int j, cudaStream_t s);
+cudaError_t lz_mf_finish(int64_t n, float* w, double* out, cudaStream_t s);
 
 cudaError_t column_cumsum_f64(int64_t n, const double* G1, double* norms2, double* cum, cudaStream_t s);
 cudaError_t rand_chain_f64(const RandArgs& a, int method, cudaStream_t s);

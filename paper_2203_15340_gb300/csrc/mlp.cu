@@ -476,8 +476,16 @@ ils_status ils_mlp_forward(ils_mlp net, int64_t count, const float* theta, doubl
   return ILS_OK;
 }
 
+ils_status ils_set_warmstart(ils_handle h, ils_mlp net) {
+  if (!h) return ILS_ERR_INVALID_ARG;
+  if (net && net->d_out != handle_n(h)) return ILS_ERR_INVALID_ARG;
+  handle_set_warm_net(h, net);
+  return ILS_OK;
+}
+
 ils_status ils_solve_param(ils_handle h, ils_mlp net, int64_t k, const float* theta, const double* B, int64_t ldb,
                            double* X, int64_t ldx, double tol, ils_info* info, ils_stream_t stream) {
+  if (h && !net) net = handle_warm_net(h);
   if (!h || !net || k < 0) return ILS_ERR_INVALID_ARG;
   if (k == 0) return ils_solve_many(h, 0, B, ldb, X, ldx, 1, tol, info, stream);
   ils_status st = ils_mlp_forward(net, k, theta, X, ldx, 1, stream);  // x0 = net(theta), BF16 inference

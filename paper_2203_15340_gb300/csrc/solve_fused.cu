@@ -9,7 +9,7 @@
 // as in the sweep kernel).  After each residual every CTA adds the per-CTA partial sums of
 // ||r||^2 in the same fixed order, so all CTAs take the same stop decision; the decision
 // rule and the state written at the end are those of the launch-per-product path.
-// Barrier waits are bounded (about 1 s); past that the CTA records TIMEOUT, marks the solve
+// Barrier waits are bounded (1 s, or the handle's wait limit); past that the CTA records TIMEOUT, marks the solve
 // done and raises the abort word, which releases every other waiter.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -33,6 +33,7 @@ struct FusedArgs {
   const double* bbar;    // A^T J b
   const double* bnorm2;  // ||bbar||^2
   double tol2;
+  const double* tol_scale;  // nullptr or a device scalar multiplying tol2
   double* x;             // the iterate, updated in place
   double* r;             // FP64 residual
   float* c32;            // P r
@@ -46,6 +47,7 @@ struct FusedArgs {
   int64_t* col_iters;
   SolveState* st;
   uint32_t* sync;        // [0] arrivals, [1] generation, [2] abort
+  uint64_t wait_ns;      // bound on each barrier wait
 };
 
 __device__ __forceinline__ uint32_t fs_ld_acquire(const uint32_t* p) {
@@ -73,19 +75,19 @@ __device__ bool fs_barrier(const FusedArgs& a) {
       __threadfence();
       atomicAdd(sync + 1, 1u);
     } else {
-      uint64_t t0 = 0;
+      uint64_t t0;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+      const bool short_bound = a.wait_ns < 100000ull;  // a short bound is checked at every poll
       for (uint32_t spin = 0;; ++spin) {
         if (fs_ld_acquire(sync + 1) != gen) break;
-        if ((spin & 15u) == 15u) {
+        if (short_bound || (spin & 15u) == 15u) {
           if (fs_ld_acquire(sync + 2) != 0u) {
             res = 0;
             break;
           }
           uint64_t t;
           asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-          if (t0 == 0) {
-            t0 = t;
-          } else if (t - t0 > 1000000000ull) {
+          if (t - t0 > a.wait_ns) {
             atomicCAS(&a.st->status, 0, (int32_t)ILS_ERR_TIMEOUT);
             atomicExch(&a.st->done, 1);
             atomicExch(sync + 2, 1u);
@@ -184,7 +186,7 @@ __global__ void __launch_bounds__(kFsThreads) mixed_solve_fused_kernel(FusedArgs
   if (*((volatile int32_t*)&a.st->done)) return;
   int64_t it = *((volatile int64_t*)&a.st->iters);
   const int64_t max_outer = a.st->max_outer;
-  const double target = a.tol2 * a.bnorm2[0];
+  const double target = a.tol2 * (a.tol_scale ? *a.tol_scale : 1.0) * a.bnorm2[0];
   const int64_t row = (int64_t)blockIdx.x * kFsWarps + w;  // the warp's row (R > 0)
   constexpr int RR = R > 0 ? R : 1;
   double hr[RR];
@@ -329,6 +331,7 @@ cudaError_t mixed_solve_fused(const SpIterArgs& sa, const MixedArgs& ma, int pre
   a.bbar = sa.bbar;
   a.bnorm2 = sa.bnorm2;
   a.tol2 = sa.tol2;
+  a.tol_scale = sa.tol_scale;
   a.x = sa.X0;
   a.r = sa.bhat_out;
   a.c32 = ma.c32;
@@ -343,6 +346,7 @@ cudaError_t mixed_solve_fused(const SpIterArgs& sa, const MixedArgs& ma, int pre
   a.col_iters = sa.col_iters;
   a.st = sa.st;
   a.sync = sync;
+  a.wait_ns = sa.wait_ns > 0 ? (uint64_t)sa.wait_ns : 1000000000ull;
   cudaError_t e = cudaMemsetAsync(sync, 0, 4 * sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};

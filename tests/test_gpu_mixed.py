@@ -128,11 +128,13 @@ def test_mixed_setup_falls_back_to_fp64_factor(ils):
     Lx = np.linalg.cholesky(G1)
     assert np.max(np.abs(L - Lx) / np.abs(np.diag(Lx))[None, :]) <= 1e-12
     x = vec(np.zeros(inst.n))
-    info = s.solve(vec(inst.b), x, tol=1e-12)
+    info = s.solve(vec(inst.b), x, tol=1e-14)
     torch.cuda.synchronize()
     # Column scaling is a congruence (D A^T J A D), so rho(B) and the refinement's contraction
     # are those of the unscaled problem; the solve must reach the oracle's x* like any other.
-    assert info.status == ils.ILS_OK and info.relres <= 1e-12
+    # The 2-norm relres is dominated by the scaled row, so the unscaled columns need a
+    # tighter relres than 1e-12 to reach 1e-10 (relres 1e-12 left 1.9e-10 here).
+    assert info.status == ils.ILS_OK and info.relres <= 1e-14
     assert relerr(x.cpu().numpy(), O.qr_cholesky_solve(A, inst.b, inst.p)) <= 1e-10
     s.close()
 
