@@ -33,7 +33,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "ILS solves/s at rel err ≤1e-10: mixed+batched+warm vs plain FP64 SP, same GB300"
 WORKLOAD = "dense ILS 20000x500 (A_1 16000x500 N(0,1), A_2 4000x500 0.3*N(0,1)), single RHS, seed 1"
-TOL_RELRES = 1e-11  # relres target; kappa(A^T J A) ~ 2.5 here, so the error bound is ~2.5e-11
+TOL_ERR = 1e-10  # target relative error: solves stop once kappa_est * relres <= 1e-10 (ILS_STOP_ERR_BOUND)
+TOL_RELRES = 1e-11  # relres target of the secondary measurements (kappa(A^T J A) <= 2.5 on them)
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (FMA pipe) rate from the profiling recipe
 # FP32 SIMT peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (max SM clock)
 FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -41,7 +42,26 @@ FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # of each kernel as it stands, on the headline step; None once a kernel changes.
 MMA_TRAFFIC_BYTES = 160_487_936 + 9_351_424
 GJ_TRAFFIC_BYTES = 693_504 + 0
-BF16_PEAK_TFLOPS = 1982.7  # measured cuBLAS BF16 burst rate on this machine (MEASURED_PEAKS.json)
+
+
+def measured_peaks():
+    """HBM copy bandwidth and cuBLAS BF16 rates measured on this machine (MEASURED_PEAKS.json, written
+    by the pool's driver), else the profiling recipe's fallback figures."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "bf16_tflops_sustained": float(d.get("bf16_tflops_sustained", d["bf16_tflops"])),
+                "source": "of measured (MEASURED_PEAKS.json)"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "source": "of fallback (profiling recipe)"}
+
+
+PEAKS = measured_peaks()
+HBM_PEAK_GBS = PEAKS["hbm_gbs"]
+BF16_PEAK_TFLOPS = PEAKS["bf16_tflops"]
 
 
 def parse():
@@ -152,8 +172,6 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
 
-
-HBM_PEAK_GBS = 6691.8  # measured STREAM-style copy bandwidth on this machine (MEASURED_PEAKS.json)
 
 
 def measure_stream(ils, torch, np, dev, reps=20):
@@ -268,7 +286,7 @@ def measure_sparse(ils, torch, np, dev, k=8):
     return out
 
 
-def measure_batched(ils, torch, np, dev, check=16):
+def measure_batched(ils, torch, np, dev):
     """256 uneven problems x 8 right-hand sides: one batch (BF16 sweeps, FP64 refinement) against
     plain FP64 SP on one handle at a time; each timed region holds every setup and solve."""
     import workloads
@@ -291,6 +309,13 @@ def measure_batched(ils, torch, np, dev, check=16):
             s = ils.Solver(At, p, ils.options())
             s.solve_many(Bt, X, tol=TOL_RELRES)
             s.close()
+
+    Xq = [torch.zeros((k, x.n), dtype=torch.float64, device=dev) for x in insts]
+
+    def plain_batched():  # plain FP64 SP through the same batch machinery (16 streams)
+        bs = ils.BatchSolver(Ats, ps, ils.options())
+        bs.solve(Bts, Xq, tol=TOL_RELRES)
+        bs.close()
 
     # One CUDA graph holding every setup and solve of the batch (ils_batch_capture with
     # refactor), replayed by one launch per step.
@@ -322,10 +347,17 @@ def measure_batched(ils, torch, np, dev, check=16):
     e1.record()
     torch.cuda.synchronize()
     t_p = e0.elapsed_time(e1)
+    plain_batched()  # warm-up
+    torch.cuda.synchronize()
+    e0.record()
+    plain_batched()
+    e1.record()
+    torch.cuda.synchronize()
+    t_pb = e0.elapsed_time(e1)
     err = 0.0
-    for i in range(0, len(insts), max(1, len(insts) // check)):
+    for i in range(len(insts)):  # every problem, every right-hand side, all three runs
         xs = _normal_solution(insts[i].A, insts[i].b, insts[i].p)
-        for X in (Xb[i], Xp[i], Xg[i]):
+        for X in (Xb[i], Xp[i], Xg[i], Xq[i]):
             xv = X.cpu().numpy().T
             err = max(err, float(np.max(np.linalg.norm(xv - xs, axis=0) / np.linalg.norm(xs, axis=0))))
     total = len(insts) * k
@@ -338,7 +370,9 @@ def measure_batched(ils, torch, np, dev, check=16):
                                                  "batch in one CUDA graph, one launch per step",
                                          "max_refinements": max(i.refinements for i in ginfos)},
             "plain_fp64_sp_one_handle_at_a_time": {"solves_per_s": total / (t_p * 1e-3), "ms_setup_plus_solve": t_p},
-            "speedup": t_p / min(t_b, t_g), "max_relerr_sampled": err, "sampled_problems": check}
+            "plain_fp64_sp_batched": {"solves_per_s": total / (t_pb * 1e-3), "ms_setup_plus_solve": t_pb},
+            "speedup": t_pb / min(t_b, t_g), "speedup_vs_one_at_a_time": t_p / min(t_b, t_g),
+            "max_relerr": err, "checked_problems": len(insts)}
 
 
 def measure_warm(ils, torch, np, dev, n_train=50000, n_eval=2048, epochs=40):
@@ -348,7 +382,10 @@ def measure_warm(ils, torch, np, dev, n_train=50000, n_eval=2048, epochs=40):
     import workloads
     fam = workloads.config5_warmstart()
     n = fam.A.shape[1]
-    solver = ils.Solver(torch.from_numpy(np.ascontiguousarray(fam.A.T)).to(dev), fam.p, ils.options())
+    At5 = torch.from_numpy(np.ascontiguousarray(fam.A.T)).to(dev)
+    certified = dict(stop_rule=ils.ILS_STOP_ERR_BOUND)  # every evaluation stops on kappa_est relres <= 1e-10
+    solver = ils.Solver(At5, fam.p, ils.options(**certified))
+    msolver = ils.Solver(At5, fam.p, ils.options(precision=ils.ILS_BF16_REFINE, **certified))
     th_train = fam.thetas(n_train, seed=5)
     X_train = torch.zeros((n_train, n), dtype=torch.float64, device=dev)
     e0, e1 = _events(torch)
@@ -357,7 +394,7 @@ def measure_warm(ils, torch, np, dev, n_train=50000, n_eval=2048, epochs=40):
         c1 = min(n_train, c0 + 4096)
         Bt = torch.from_numpy(np.ascontiguousarray(fam.rhs(th_train[c0:c1], seed=5, start=c0).T)).to(dev)
         e0.record()
-        solver.solve_many(Bt, X_train[c0:c1], tol=1e-12)
+        solver.solve_many(Bt, X_train[c0:c1], tol=1e-11)
         e1.record()
         torch.cuda.synchronize()
         t_targets += e0.elapsed_time(e1)
@@ -374,35 +411,44 @@ def measure_warm(ils, torch, np, dev, n_train=50000, n_eval=2048, epochs=40):
     th_e = torch.from_numpy(th_eval.astype(np.float32)).to(dev)
     Xc = torch.zeros((n_eval, n), dtype=torch.float64, device=dev)
     Xw = torch.zeros_like(Xc)
-    solver.solve_many(Be[:64], Xc[:64], tol=TOL_RELRES)  # warm-up
-    net.solve(solver, th_e[:64], Be[:64], Xw[:64], tol=TOL_RELRES)
+    Xm = torch.zeros_like(Xc)
+    solver.solve_many(Be[:64], Xc[:64], tol=TOL_ERR)  # warm-up
+    net.solve(solver, th_e[:64], Be[:64], Xw[:64], tol=TOL_ERR)
+    net.solve(msolver, th_e[:64], Be[:64], Xm[:64], tol=TOL_ERR)
     torch.cuda.synchronize()
     e0.record()
-    ic = solver.solve_many(Be, Xc, tol=TOL_RELRES)
+    ic = solver.solve_many(Be, Xc, tol=TOL_ERR)
     e1.record()
     torch.cuda.synchronize()
     t_cold = e0.elapsed_time(e1)
     e0.record()
-    iw = net.solve(solver, th_e, Be, Xw, tol=TOL_RELRES)
+    iw = net.solve(solver, th_e, Be, Xw, tol=TOL_ERR)
     e1.record()
     torch.cuda.synchronize()
     t_warm = e0.elapsed_time(e1)
+    # the combined form: mixed-precision sweeps from the network's x0
+    e0.record()
+    im = net.solve(msolver, th_e, Be, Xm, tol=TOL_ERR)
+    e1.record()
+    torch.cuda.synchronize()
+    t_mixed_warm = e0.elapsed_time(e1)
     # Control: the least-squares affine map theta -> x fitted to the same training targets
     # (x depends on theta affinely up to the noise term, so this is the natural baseline).
     Th1 = np.hstack([th_train, np.ones((n_train, 1))])
     Wls = np.linalg.lstsq(Th1, X_train.cpu().numpy(), rcond=None)[0]
     Xl = torch.from_numpy(np.hstack([th_eval, np.ones((n_eval, 1))]) @ Wls).to(dev)
     e0.record()
-    il = solver.solve_many(Be, Xl, x0_zero=False, tol=TOL_RELRES)
+    il = solver.solve_many(Be, Xl, x0_zero=False, tol=TOL_ERR)
     e1.record()
     torch.cuda.synchronize()
     t_lin = e0.elapsed_time(e1)
     Xs = _normal_solution(fam.A, B_eval, fam.p)
     err = 0.0
-    for X in (Xc, Xw, Xl):
+    for X in (Xc, Xw, Xl, Xm):
         xv = X.cpu().numpy().T
         err = max(err, float(np.max(np.linalg.norm(xv - Xs, axis=0) / np.linalg.norm(Xs, axis=0))))
     solver.close()
+    msolver.close()
     net.close()
     return {"workload": "A 8192x256 (A_1 6144, A_2 2048 x 0.25), b = F theta + 1e-3 noise, theta ~ U[-1,1]^16; "
                         f"MLP 16-256-256-256 trained on {n_train} library SP solutions (seed 5), {n_eval} held-out "
@@ -411,8 +457,10 @@ def measure_warm(ils, torch, np, dev, n_train=50000, n_eval=2048, epochs=40):
             "cold_x0_zero": {"solves_per_s": n_eval / (t_cold * 1e-3), "max_outer_iters": ic.outer_iters},
             "linear_map_control": {"solves_per_s": n_eval / (t_lin * 1e-3), "max_outer_iters": il.outer_iters,
                                    "note": "x0 = W theta + c fitted by least squares on the training targets"},
-            "speedup": t_cold / t_warm, "train_loss": loss, "train_ms": t_train, "targets_ms": t_targets,
-            "max_relerr": err}
+            "mixed_bf16_warm": {"solves_per_s": n_eval / (t_mixed_warm * 1e-3), "max_refinements": im.refinements},
+            "speedup": t_cold / t_warm, "speedup_mixed_warm_vs_plain_fp64": t_cold / t_mixed_warm,
+            "train_loss": loss, "train_ms": t_train, "targets_ms": t_targets, "max_relerr": err,
+            "checked_rhs": n_eval}
 
 
 def run_reference(args, rank, world):
@@ -488,7 +536,7 @@ def main():
 
         def step():
             solver.refactor_async(At, stream=stream)
-            return solver.solve(b, x, tol=TOL_RELRES, stream=stream)
+            return solver.solve(b, x, tol=TOL_ERR, stream=stream)
 
         # nvidia-smi starts before the warm-up so that its start-up does not overlap the
         # timed region; every sample it takes falls in the loaded warm-up or timed steps.
@@ -521,18 +569,27 @@ def main():
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
         launches = ils.binding.kernel_launches() - launches0
+        # the last timed step's answer meets the same gate
+        relerr_timed = float(np.linalg.norm(x.cpu().numpy() - xs) / np.linalg.norm(xs))
+        if not relerr_timed <= 1e-10 or any(d["status"] != 0 for d in infos):
+            raise SystemExit(f"accuracy gate failed after the timed steps: relerr {relerr_timed:.3e}")
         barrier()
         clocks = sampler.stop() if sampler else None
         total_s = max_over_ranks(sum(a.elapsed_time(bb) for a, bb in ev) / 1e3, world, dev)
         ph = {k: statistics.mean(d[k] for d in phases) for k in phases[0]}
         return dict(solver=solver, total_s=total_s, wall=wall, launches=launches, clocks=clocks, relerr=relerr,
-                    phases=ph, info=infos[-1], steps=steps)
+                    relerr_timed=relerr_timed, phases=ph, info=infos[-1], steps=steps)
 
-    mixed = measure(ils.options(precision=ils.ILS_FP32_REFINE, timing=1), args.steps, True)
-    plain = measure(ils.options(timing=1), max(3, min(args.steps, 10)), False)
+    certified = dict(stop_rule=ils.ILS_STOP_ERR_BOUND, timing=1)  # stop on kappa_est * relres <= 1e-10
+    mixed = measure(ils.options(precision=ils.ILS_FP32_REFINE, **certified), args.steps, True)
+    plain = measure(ils.options(**certified), max(3, min(args.steps, 10)), False)
+    # the mixed form with the factorization kept in FP64 (Cholesky of Abar1 and H)
+    mixed64 = measure(ils.options(precision=ils.ILS_FP32_REFINE, factor64=1, **certified), max(3, min(args.steps, 10)),
+                      False)
     solver = mixed["solver"]
     value = replica_rate(world, args.steps, mixed["total_s"])
     plain_value = replica_rate(world, plain["steps"], plain["total_s"])
+    mixed64_value = replica_rate(world, mixed64["steps"], mixed64["total_s"])
 
     # ---- end to end through the C ABI with host buffers ----
     A_host = torch.from_numpy(np.ascontiguousarray(inst.A.T)).pin_memory()
@@ -548,7 +605,7 @@ def main():
         A_dev.copy_(A_host, non_blocking=True)
         b_dev.copy_(b_host, non_blocking=True)
         solver.refactor_async(A_dev, stream=stream)
-        solver.solve(b_dev, x, tol=TOL_RELRES, stream=stream)
+        solver.solve(b_dev, x, tol=TOL_ERR, stream=stream)
         x_host.copy_(x, non_blocking=True)
         e2e_ev[i][1].record(stream)
     torch.cuda.synchronize()
@@ -561,51 +618,37 @@ def main():
         return
     ms_step = 1e3 * mixed["total_s"] / args.steps
     ph = mixed["phases"]
-    # The two largest kernels of the headline step, each timed alone with CUDA events on
-    # the handle's stream (options.timing):
-    #  * spd_gj_kernel: P = Abar1^{-1} by FP32 block Gauss-Jordan (the test of H is its own
-    #    launch on another stream, outside this phase); the sweep operator makes n^3
-    #    multiply-adds per matrix.
-    #  * gram_split_mma_kernel (A_1^T A_1): executed BF16 MMA flops, 2 x 128 x 128 x p per
-    #    digit product and tile pair; 55 products on an off-diagonal tile pair, 30 on a
-    #    diagonal one (the transposed cross products are not formed).
+    # The two largest kernels of the headline step, each timed alone with CUDA events on the
+    # handle's stream (options.timing):
+    #  * gram_split_mma_kernel (A_1^T A_1): the method's work is p n^2 flop (FP64 Gram);
+    #    the kernel executes 2 x 128 x 128 x p BF16 flop per digit product and tile pair
+    #    (55 products on an off-diagonal tile pair, 30 on a diagonal one);
+    #  * spd_gj_kernel: P = Abar1^{-1} by FP32 block Gauss-Jordan, n^3 multiply-adds.
     gj_ms = ph["factor"]
-    gj_flops = 2.0 * n ** 3  # the sweep of one n x n matrix (Abar1): n^3 multiply-adds
-    gj_ach = gj_flops / (gj_ms * 1e-3) / 1e12
+    gj_ach = 2.0 * n ** 3 / (gj_ms * 1e-3) / 1e12
     mma_ms = ph["gram1_mma"]
     n_tiles = (n + 127) // 128
     n_upper = n_tiles * (n_tiles + 1) // 2
-    tensor_flops = 2.0 * 128 * 128 * p * ((n_upper - n_tiles) * 55 + n_tiles * 30)
-    mma_ach = tensor_flops / (mma_ms * 1e-3) / 1e12
-    gram_ms = ph["gram1"]
-    gram_flops = float(p) * n * (n + 1)  # the FP64-accurate product A_1^T A_1
-    roof_gj = {
-        "kernel": "spd_gj_kernel<32> (P = Abar1^{-1} by FP32 block Gauss-Jordan; the SPD test of A^T J A is a second launch on another stream)",
-        "bound": "alu",
-        "achieved": gj_ach,
-        "peak": FP32_SIMT_PEAK_TFLOPS,
-        "peak_source": "FP32 SIMT rate from unit counts: 152 SMs x 128 lanes x 2 flops x 2.07 GHz",
-        "unit": "TFLOP/s",
-        "frac": gj_ach / FP32_SIMT_PEAK_TFLOPS,
-        "traffic": GJ_TRAFFIC_BYTES,
-        "kernel_ms": gj_ms,
-        "share_of_step": gj_ms / ms_step,
-        "note": "latency-bound: the chain of 16 pivot blocks of 32 (update, 2x2-block sweep by four warps, flag handoff)",
-    }
+    executed = 2.0 * 128 * 128 * p * ((n_upper - n_tiles) * 55 + n_tiles * 30)
+    alg_flops = float(p) * n * n  # the Gram's algorithmic work
+    alg_bytes = 8.0 * p * n        # A_1 read once in FP64
+    mma_alg = alg_flops / (mma_ms * 1e-3) / 1e12
     roof_mma = {
-        "kernel": "gram_split_mma_kernel (A_1^T A_1 to FP64 accuracy from exact BF16 digit products)",
-        "bound": "tensor",
-        "achieved": mma_ach,
-        "peak": BF16_PEAK_TFLOPS,
-        "peak_source": "measured cuBLAS BF16 burst (MEASURED_PEAKS.json)",
-        "unit": "TFLOP/s (executed BF16 MMA flops)",
-        "frac": mma_ach / BF16_PEAK_TFLOPS,
-        "traffic": MMA_TRAFFIC_BYTES,
-        "kernel_ms": mma_ms,
-        "share_of_step": mma_ms / ms_step,
-        "gram_phase_ms": gram_ms,
-        "fp64_equivalent_tflops_of_phase": gram_flops / (gram_ms * 1e-3) / 1e12,
-        "note": "one wave of 126 CTAs; each 2x2 digit block loads its tiles once, L2 feeds the tensor pipe",
+        "kernel": "gram_split_mma_kernel (A_1^T A_1 to FP64 accuracy from exact BF16 digit products, tcgen05)",
+        "bound": "tensor", "achieved": mma_alg, "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",
+        "frac": mma_alg / BF16_PEAK_TFLOPS, "traffic": MMA_TRAFFIC_BYTES,
+        "peak_source": "cuBLAS BF16 burst " + PEAKS["source"],
+        "work": "p n^2 algorithmic flop per launch (the FP64 Gram); frac_executed counts the BF16 MMA flop run",
+        "frac_executed": executed / (mma_ms * 1e-3) / 1e12 / BF16_PEAK_TFLOPS,
+        "executed_over_algorithmic": executed / alg_flops,
+        "traffic_ratio": MMA_TRAFFIC_BYTES / alg_bytes,
+        "kernel_ms": mma_ms, "share_of_step": mma_ms / ms_step, "gram_phase_ms": ph["gram1"],
+    }
+    roof_gj = {
+        "kernel": "spd_gj_kernel<32> (P = Abar1^{-1}, FP32 block Gauss-Jordan)", "bound": "alu",
+        "achieved": gj_ach, "peak": FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": gj_ach / FP32_SIMT_PEAK_TFLOPS,
+        "traffic": GJ_TRAFFIC_BYTES, "kernel_ms": gj_ms, "share_of_step": gj_ms / ms_step,
+        "peak_source": "FP32 SIMT rate from unit counts (152 SMs x 128 lanes x 2 flop x 2.07 GHz)",
     }
     stream = measure_stream(ils, torch, np, dev)
     configs = {}
@@ -614,6 +657,12 @@ def main():
         configs["batched"] = measure_batched(ils, torch, np, dev)
         configs["warm_start"] = measure_warm(ils, torch, np, dev)
     cpu_rate, cpu_cnt, cpu_secs = time_oracle(inst, args.cpu_seconds)
+    r4 = lambda v: None if v is None else float(f"{v:.4g}")
+    summary = {}
+    for name, c in configs.items():
+        summary[name] = {k: r4(v["solves_per_s"]) for k, v in c.items() if isinstance(v, dict) and "solves_per_s" in v}
+        summary[name].update({k: r4(c[k]) for k in ("speedup", "speedup_mixed_warm_vs_plain_fp64", "max_relerr")
+                              if k in c})
     line = {
         "metric": METRIC,
         "value": value,
@@ -625,56 +674,53 @@ def main():
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64",
+        "dtype": "bf16+f32+f64",
         "data": "synthetic",
         "config": {
             "workload": WORKLOAD,
-            "method": "SP (Alg. 1), mixed precision: tensor-core FP64-accurate Grams, P by FP32 block "
-                      "Gauss-Jordan (the SPD test of A^T J A beside it on another stream), FP32 sweeps, FP64 residual refinement in "
-                      "one cooperative launch",
-            "tol_relres": TOL_RELRES,
-            "relerr_vs_oracle": mixed["relerr"],
+            "arithmetic": "Grams FP64-accurate from exact BF16 digit products (FP32 accumulation), P and "
+                          "sweeps FP32, A^T J b and residuals FP64",
+            "stop": "kappa_est * relres <= 1e-10 (Lanczos kappa_est; ILS_STOP_ERR_BOUND)",
+            "relerr_vs_oracle": r4(mixed["relerr_timed"]),
+            "err_bound": r4(mixed["info"]["err_bound"]), "kappa_est": r4(mixed["info"]["kappa_est"]),
+            "rho_est": r4(mixed["info"]["rho_est"]),
             "refinements": mixed["info"]["refinements"],
-            "sp_sweeps": mixed["info"]["outer_iters"],
-            "setup_phases_ms": {k: round(v, 4) for k, v in ph.items()},
+            "plain_fp64_sp_value": r4(plain_value),
+            "speedup_vs_plain_fp64": r4(value / plain_value),
+            "plain_fp64_relerr": r4(plain["relerr_timed"]),
+            "mixed_fp64_factor_value": r4(mixed64_value),
+            "mixed_fp64_factor_relerr": r4(mixed64["relerr_timed"]),
+            "setup_phases_ms": {k: r4(v) for k, v in ph.items()},
             "l2": "flushed before every step (256 MiB write outside the timed events)",
-            "step": "ils_refactor_async (all setup products, status read by the solve) + ils_solve",
-            "wall_s_timed_loop": mixed["wall"],
+            "step": "ils_refactor_async (all setup products) + ils_solve",
         },
-        "plain_fp64_sp": {
-            "value": plain_value, "unit": "solves/s", "ms_per_step": 1e3 * plain["total_s"] / plain["steps"],
-            "steps": plain["steps"], "relerr_vs_oracle": plain["relerr"], "outer_iters": plain["info"]["outer_iters"],
-            "setup_phases_ms": {k: round(v, 4) for k, v in plain["phases"].items()},
-            "speedup_of_headline": value / plain_value,
-        },
-        "roofline": roof_gj if gj_ms >= mma_ms else roof_mma,
-        "roofline_gj_inverse": roof_gj,
-        "roofline_tensor_gram": roof_mma,
-        "roofline_stream": {
-            "kernel": "aq_stream_kernel (one-pass A_2^T (A_2 x), matrix-free route), tall instance A_2 262144x500",
-            "bound": "hbm",
-            "achieved": stream["fp32"]["achieved_GBps"],
-            "peak": HBM_PEAK_GBS,
-            "unit": "GB/s",
-            "frac": stream["fp32"]["frac"],
-            "traffic": None,
-            "by_precision": {k: v for k, v in stream.items() if k in ("fp32", "bf16", "fp64")},
-            "note": "FP64 copy is FP64-issue bound (2 FMA per 8 bytes); FP32/BF16 copies stream at HBM speed",
-        },
-        "tall_config": stream.get("tall_mixed_solve"),
-        "other_configs": configs,
+        "roofline": roof_mma if mma_ms >= gj_ms else roof_gj,
+        "kernels": {"gj_inverse": {"ms": r4(gj_ms), "frac": r4(roof_gj["frac"])},
+                    "gram_mma": {"ms": r4(mma_ms), "frac": r4(roof_mma["frac"]),
+                                 "frac_executed": r4(roof_mma["frac_executed"])},
+                    "aq_stream_fp32": {"GBps": r4(stream["fp32"]["achieved_GBps"]), "frac": r4(stream["fp32"]["frac"])},
+                    "aq_stream_bf16": {"GBps": r4(stream["bf16"]["achieved_GBps"]), "frac": r4(stream["bf16"]["frac"])},
+                    "aq_stream_fp64": {"GBps": r4(stream["fp64"]["achieved_GBps"]), "frac": r4(stream["fp64"]["frac"])}},
+        "tall_ms_per_solve": r4((stream.get("tall_mixed_solve") or {}).get("ms_per_solve")),
+        "other_configs": summary,
         "cpu_baseline": {
             "value": cpu_rate, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
-            "sample": f"{cpu_cnt} complete oracle SP solves of the same instance ({cpu_secs:.1f} s, numpy/LAPACK "
-                      "with the default BLAS thread count)",
+            "sample": f"{cpu_cnt} oracle SP solves of the same instance ({cpu_secs:.1f} s)",
         },
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(mixed["launches"]),
         "clocks": mixed["clocks"],
     }
+    detail = os.environ.get("ILS_BENCH_DETAIL")
+    if detail:  # the full measurements, for profiling notes
+        with open(detail, "w") as f:
+            json.dump({"roofline_gj": roof_gj, "roofline_mma": roof_mma, "stream": stream, "configs": configs,
+                       "plain": {k: plain[k] for k in ("relerr", "relerr_timed", "phases", "info")},
+                       "mixed64": {k: mixed64[k] for k in ("relerr", "relerr_timed", "phases", "info")}}, f, indent=1)
     print(json.dumps(line), flush=True)
     mixed["solver"].close()
     plain["solver"].close()
+    mixed64["solver"].close()
 
 
 if __name__ == "__main__":

@@ -97,9 +97,10 @@ typedef struct {
                           that cluster size; -1 = one CTA, vectors in global memory. */
   /* ---- fields below were added after the first release; ils_options_default sets them ---- */
   int32_t stop_rule;   /* ils_stop_rule: how `tol` of the solve calls is read (default relres) */
-  int32_t estimate;    /* != 0: estimate rho(Abar1^{-1} Abar2) and kappa_2(A^T J A) at setup by
-                          Lanczos (ils_info.rho_est, kappa_est, err_bound); implied by
-                          ILS_STOP_ERR_BOUND */
+  int32_t estimate;    /* Lanczos estimates at setup (ils_info.rho_est, kappa_est, err_bound):
+                          0 = none, 1 = rho(Abar1^{-1} Abar2) and kappa_2(A^T J A), 2 = kappa only
+                          (the matrix-free route always estimates both).  ILS_STOP_ERR_BOUND
+                          with 0 takes 2.  Estimates need n <= 4096 (else INVALID_ARG) */
   int32_t alpha_mode;  /* SP-SCD: 0 = alpha ~ U{1..n} each step (Alg. 5), 1 = fixed alpha_fixed
                           (Sec. 4: alpha = n is the greedy Motzkin rule, alpha = 1 a uniform pick) */
   int32_t sampler;     /* SP-RK-RGS column draws from ||A_1(:,j)||^2 / ||A_1||_F^2: 0 = inverse CDF
@@ -116,7 +117,8 @@ typedef struct {
                           mixed-precision solve; 0 = 1 s (the setup kernels keep their own 1-4 s
                           bounds).  A wait that runs out ends the kernel and the solve returns
                           ILS_ERR_TIMEOUT; the handle stays usable */
-  int32_t lanczos_steps; /* Lanczos steps of the estimates; 0 = 64 */
+  int32_t lanczos_steps; /* Lanczos steps of the estimates; 0 = 24 (the extreme Ritz values of
+                          these spectra settle to well under 1% by then) */
   int32_t factor64;    /* mixed precision, single dense handle: != 0 forms P = Abar1^{-1} from the
                           FP64 Cholesky factor of Abar1 and tests H by FP64 Cholesky (the
                           factorization stays FP64), instead of the FP32 Gauss-Jordan inverse */
@@ -397,7 +399,9 @@ ils_status ils_set_warmstart(ils_handle h, ils_mlp net);
  * library's device memory, resident on every GPU that loads the library until the
  * process exits; when they would not fit, the call uses fewer, longer K slices.  The
  * first call on each device looks up that array's device address (with that device
- * current), so make the first call on a device before any stream capture.  Every call
+ * current), so make the first call on a device before any stream capture; the address
+ * stays valid for the CUDA context current at that call (a context torn down and created
+ * again, for example by cudaDeviceReset, needs a new process).  Every call
  * shares the array: calls whose work overlaps on the GPU (different streams, or
  * different host threads) race on it and must be serialized by the caller.  Enqueues
  * work only; nothing is synchronized.  Errors: INVALID_ARG, CUDA. */

@@ -48,16 +48,12 @@ extern "C" ils_status ils_gram_noalloc(int64_t K, int64_t n, const double* X, in
   if (n < 1 || n > kNoAllocMaxN || K < 0 || ldx < (K > 0 ? K : 1) || ldc < n || !C || (K > 0 && !X))
     return ILS_ERR_INVALID_ARG;
   double* scratch = nullptr;
-  if (scratch_for_current_device(&scratch) != cudaSuccess) {
-    cudaGetLastError();
-    return ILS_ERR_CUDA;
-  }
+  cudaError_t e = scratch_for_current_device(&scratch);
+  if (e != cudaSuccess) return ils::record_cuda_error(e, "ils_gram_noalloc: device address of the scratch array",
+                                                      __LINE__);
   // Every partial sum the reduction reads is written first by the same call, so the
   // array needs no clearing between calls.
-  if (ils::gemm_tn_f64_capped(K, n, X, ldx, C, ldc, scratch, kNoAllocScratchElems, (cudaStream_t)stream) !=
-      cudaSuccess) {
-    cudaGetLastError();
-    return ILS_ERR_CUDA;
-  }
+  e = ils::gemm_tn_f64_capped(K, n, X, ldx, C, ldc, scratch, kNoAllocScratchElems, (cudaStream_t)stream);
+  if (e != cudaSuccess) return ils::record_cuda_error(e, "ils_gram_noalloc: Gram launch", __LINE__);
   return ILS_OK;
 }

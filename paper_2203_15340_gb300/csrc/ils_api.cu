@@ -45,6 +45,7 @@ struct ils_handle_s {
   double* inv_diag = nullptr;    // 2n: reciprocal Cholesky pivots (Abar1, H)
   double* Dinv = nullptr;        // inverses of L's 32 x 32 diagonal blocks
   double* norms2 = nullptr;      // n: ||A_1(:,j)||^2
+  double* inv_norms2 = nullptr;  // n: 1 / ||A_1(:,j)||^2
   double* cum = nullptr;         // n: running sum of norms2
   double* vec_scratch = nullptr; // RK-RGS w and e when they do not fit in shared memory
   bool vec_in_smem = true;
@@ -142,8 +143,7 @@ ils_mlp handle_warm_net(ils_handle h) { return h->warm_net; }
 void handle_set_warm_net(ils_handle h, ils_mlp net) { h->warm_net = net; }
 }  // namespace ils
 
-namespace {
-
+namespace ils {
 thread_local char g_last_error[256] = "";
 
 ils_status record_cuda_error(cudaError_t e, const char* what, int line) {
@@ -151,6 +151,9 @@ ils_status record_cuda_error(cudaError_t e, const char* what, int line) {
   cudaGetLastError();
   return ILS_ERR_CUDA;
 }
+}  // namespace ils
+
+namespace {
 
 #define ILS_CK(expr)                                                     \
   do {                                                                   \
@@ -229,6 +232,7 @@ void carve(ils_handle h, Carver& c, size_t work_elems) {
   h->inv_diag = c.take<double>(2 * (size_t)h->n);
   h->Dinv = c.take<double>((size_t)((h->n + 31) / 32) * 1024);
   h->norms2 = c.take<double>((size_t)h->n);
+  h->inv_norms2 = c.take<double>((size_t)h->n);
   h->cum = c.take<double>((size_t)h->n);
   h->vec_in_smem = rkrgs_vec_fits(h->n, h->p);
   if (h->sparse) h->vec_in_smem = false;
@@ -371,7 +375,7 @@ ils_status enqueue_estimates(ils_handle h, cudaStream_t s, const void* Hm, int h
                              const void* Pm, int p64) {
   LanczosProblem pr[2];
   int cnt = 0;
-  const int steps = h->opt.lanczos_steps > 0 ? h->opt.lanczos_steps : 64;
+  const int steps = h->opt.lanczos_steps > 0 ? h->opt.lanczos_steps : 24;
   double* kap_out = h->est + 8;
   double* rho_out = h->est + 12;
   if (Hm) pr[cnt++] = LanczosProblem{h->n, Hm, nullptr, h64, 0, steps, 0, kap_out};
@@ -388,7 +392,7 @@ ils_status enqueue_estimates(ils_handle h, cudaStream_t s, const void* Hm, int h
 ils_status enqueue_estimates_mf(ils_handle h) {
   cudaStream_t s = h->stream;
   const int64_t n = h->n;
-  const int steps = h->opt.lanczos_steps > 0 ? h->opt.lanczos_steps : 64;
+  const int steps = h->opt.lanczos_steps > 0 ? h->opt.lanczos_steps : 24;
   double* kap_out = h->est + 8;
   double* rho_out = h->est + 12;
   LanczosProblem pr = {n, h->G1, nullptr, 1, 0, steps, 0, kap_out};
@@ -462,7 +466,7 @@ ils_status compute_setup_sparse(ils_handle h, const int32_t* rowptr, const int32
   ILS_CK(sparse_setup(h->m, h->n, h->p, h->nnz, rowptr, colind, val, h->sc, h->cnt_fill, h->G1, h->G2, h->sp_err, s));
   ILS_CK(cudaMemcpyAsync(h->h_status + 2, h->sp_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   ILS_CK(mark(h, 2));
-  if (h->opt.method != ILS_SP) ILS_CK(column_cumsum_f64(h->n, h->G1, h->norms2, h->cum, s));
+  if (h->opt.method != ILS_SP) ILS_CK(column_cumsum_f64(h->n, h->G1, h->norms2, h->cum, s, h->inv_norms2));
   if (h->opt.method == ILS_SP_RK_RGS && h->opt.sampler == 1)
     ILS_CK(alias_table_f64(h->n, h->norms2, h->alias_prob, h->alias_idx, s));
   if (h->opt.method == ILS_SP_RK_RGS)
@@ -489,7 +493,7 @@ ils_status compute_setup(ils_handle h) {
     ILS_CK(gemm_tn_f64(p, n, n, h->A, m, h->A, m, p, h->G1, n, true, false, h->work, s));
   }
   ILS_CK(mark(h, 2));
-  if (h->opt.method != ILS_SP) ILS_CK(column_cumsum_f64(n, h->G1, h->norms2, h->cum, s));
+  if (h->opt.method != ILS_SP) ILS_CK(column_cumsum_f64(n, h->G1, h->norms2, h->cum, s, h->inv_norms2));
   if (h->opt.method == ILS_SP_RK_RGS && h->opt.sampler == 1)
     ILS_CK(alias_table_f64(n, h->norms2, h->alias_prob, h->alias_idx, s));
   if (h->mf) return compute_setup_mf(h);
@@ -541,7 +545,7 @@ ils_status compute_products(ils_handle h) {
   }
   if (h->opt.estimate) {
     ils_status es;
-    if (h->opt.method != ILS_SP) es = enqueue_estimates(h, s, h->H, 1, nullptr, 0, nullptr, 0);
+    if (h->opt.method != ILS_SP || h->opt.estimate == 2) es = enqueue_estimates(h, s, h->H, 1, nullptr, 0, nullptr, 0);
     else if (h->opt.precision != ILS_FP64) es = enqueue_estimates(h, s, h->H, 1, h->G2_32, 0, h->P32, 0);
     else es = enqueue_estimates(h, s, h->H, 1, h->G2, 1, h->P, 1);
     if (es != ILS_OK) return es;
@@ -621,17 +625,19 @@ ils_status compute_setup_overlap(ils_handle h, const double* src, int64_t lda_sr
     if (h->opt.estimate) {
       // kappa(H) once H is formed, beside the inverse; rho once P is formed.
       cudaStream_t e = h->s_est;
-      const int steps = h->opt.lanczos_steps > 0 ? h->opt.lanczos_steps : 64;
+      const int steps = h->opt.lanczos_steps > 0 ? h->opt.lanczos_steps : 24;
       ILS_CK(cudaEventRecord(h->ev_p, s));
       ILS_CK(cudaStreamWaitEvent(e, h->ev_hd, 0));
       LanczosProblem pk = {n, h->H32, nullptr, 0, 0, steps, 0, h->est + 8};
       ILS_CK(lanczos_extremes(1, &pk, e));
       ILS_CK(estimates_finish(h->est + 8, nullptr, h->est, e));
       ILS_CK(cudaEventRecord(h->ev_estk, e));
-      ILS_CK(cudaStreamWaitEvent(e, h->ev_p, 0));
-      LanczosProblem pr = {n, h->G2_32, h->P32, 0, 0, steps, 0, h->est + 12};
-      ILS_CK(lanczos_extremes(1, &pr, e));
-      ILS_CK(estimates_finish(nullptr, h->est + 12, h->est, e));
+      if (h->opt.estimate != 2) {  // rho as well
+        ILS_CK(cudaStreamWaitEvent(e, h->ev_p, 0));
+        LanczosProblem pr = {n, h->G2_32, h->P32, 0, 0, steps, 0, h->est + 12};
+        ILS_CK(lanczos_extremes(1, &pr, e));
+        ILS_CK(estimates_finish(nullptr, h->est + 12, h->est, e));
+      }
       ILS_CK(cudaMemcpyAsync(h->h_est, h->est, 8 * sizeof(double), cudaMemcpyDeviceToHost, e));
       ILS_CK(cudaEventRecord(h->ev_est, e));
     }
@@ -656,7 +662,8 @@ ils_status compute_setup_overlap(ils_handle h, const double* src, int64_t lda_sr
   } else {
     ILS_CK(cudaMemcpyAsync(h->h_status + 3, h->dstatus2, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     if (h->opt.estimate) {
-      const ils_status es = enqueue_estimates(h, s, h->H, 1, h->G2_32, 0, h->P32, 0);
+      const ils_status es = h->opt.estimate == 2 ? enqueue_estimates(h, s, h->H, 1, nullptr, 0, nullptr, 0)
+                                                 : enqueue_estimates(h, s, h->H, 1, h->G2_32, 0, h->P32, 0);
       if (es != ILS_OK) return es;
       ILS_CK(cudaEventRecord(h->ev_estk, s));
       ILS_CK(cudaEventRecord(h->ev_est, s));
@@ -825,6 +832,7 @@ ils_status pass_begin(ils_handle h, int64_t c0, int64_t kk, const double* B, int
   ra.A = h->A;
   ra.G1 = h->G1;
   ra.norms2 = h->norms2;
+  ra.inv_norms2 = h->inv_norms2;
   ra.cum = h->cum;
   ra.bhat = h->bhat;
   ra.X0 = h->X0;
@@ -1163,7 +1171,9 @@ ils_status create_handle(ils_handle* out, int64_t m, int64_t n, int64_t p, int64
   else ils_options_default(&opt);
   if (validate_options(&opt) != ILS_OK) return ILS_ERR_INVALID_ARG;
   if (opt.route < ILS_ROUTE_AUTO || opt.route > ILS_ROUTE_MATRIX_FREE) return ILS_ERR_INVALID_ARG;
-  if (opt.stop_rule == ILS_STOP_ERR_BOUND) opt.estimate = 1;  // the rule reads kappa_est
+  if (opt.stop_rule == ILS_STOP_ERR_BOUND && opt.estimate == 0) opt.estimate = 2;  // the rule reads kappa_est
+  if (opt.estimate < 0 || opt.estimate > 2) return ILS_ERR_INVALID_ARG;
+  if (opt.estimate && n > 4096) return ILS_ERR_INVALID_ARG;  // the Lanczos clusters hold n <= 4096
   if (opt.method == ILS_SP_SCD && opt.alpha_mode == 1 && (opt.alpha_fixed < 1 || opt.alpha_fixed > n))
     return ILS_ERR_INVALID_ARG;
   // The Gram-space chain keeps three n-vectors in registers (n <= 8192); the sparse chains have

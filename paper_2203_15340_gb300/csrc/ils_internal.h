@@ -24,6 +24,10 @@ struct SolveState {
 
 constexpr int kMaxRhsPerPass = 8;  // right-hand sides carried per iteration launch
 
+// Record a failed CUDA call for ils_last_error (this thread) and clear CUDA's sticky error
+// state; returns ILS_ERR_CUDA.
+ils_status record_cuda_error(cudaError_t e, const char* what, int line);
+
 // Accessors of the handle for the other translation units.
 int64_t handle_n(ils_handle h);
 ils_mlp handle_warm_net(ils_handle h);
@@ -252,6 +256,7 @@ struct RandArgs {
   const double* A;        // the handle's copy of A, m x n, ld m (A_1 = rows 0..p-1)
   const double* G1;       // Abar1
   const double* norms2;   // ||A_1(:,j)||^2
+  const double* inv_norms2;  // 1 / ||A_1(:,j)||^2 (dense handles)
   const double* cum;      // running sum of norms2, left to right
   const double* bhat;     // n x k
   double* X0;
@@ -344,7 +349,9 @@ double* lz_mf_vector(int64_t n, float* w);
 cudaError_t lz_mf_step(int64_t n, const float* P, const double* y, float* w, int j, cudaStream_t s);
 cudaError_t lz_mf_finish(int64_t n, float* w, double* out, cudaStream_t s);
 
-cudaError_t column_cumsum_f64(int64_t n, const double* G1, double* norms2, double* cum, cudaStream_t s);
+// norms2 = diag(Abar1), cum its running sum (left to right), inv_norms2 = 1 / norms2 (may be null).
+cudaError_t column_cumsum_f64(int64_t n, const double* G1, double* norms2, double* cum, cudaStream_t s,
+                              double* inv_norms2 = nullptr);
 cudaError_t rand_chain_f64(const RandArgs& a, int method, cudaStream_t s);
 bool rkrgs_vec_fits(int64_t n, int64_t p);
 

@@ -42,11 +42,6 @@ __device__ __forceinline__ void st_remote(const float* local, uint32_t rank, flo
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(lz_smem_u32(local)), "r"(rank));
   asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(remote), "f"(v) : "memory");
 }
-__device__ __forceinline__ void st_remote_d(const double* local, uint32_t rank, double v) {
-  uint32_t remote;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(lz_smem_u32(local)), "r"(rank));
-  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(remote), "d"(v) : "memory");
-}
 
 // All threads of all CTAs of the cluster; release/acquire orders the DSMEM stores.
 __device__ __forceinline__ void cluster_sync() {
@@ -59,84 +54,151 @@ __device__ __forceinline__ float lz_warp_sum(float v) {
   return v;
 }
 
-// Number of eigenvalues of the symmetric tridiagonal (alpha, beta) below x (Sturm count).
-__device__ int sturm_count(const double* al, const double* be, int m, double x) {
+// Number of eigenvalues below x of the symmetric tridiagonal T_m (diagonal al, squared
+// off-diagonal be2), already shifted and scaled so that its Gershgorin interval is [-1, 1]:
+// the sign changes of the Sturm sequence p_0 = 1, p_1 = al_0 - x, p_i = (al_{i-1} - x)
+// p_{i-1} - be_{i-2}^2 p_{i-2}.  FP32 (the estimates need a few digits, and this GPU's FP64
+// pipe is narrow), division-free; a zero term takes the sign opposite to its predecessor's,
+// and the pair is rescaled by 2^-60 (exact) whenever it grows past 2^60.
+__device__ int sturm_count_scaled(const float* al, const float* be2, int m, float x) {
+  float pm2 = 1.0f, pm1 = al[0] - x;
   int cnt = 0;
-  double d = 1.0;
-  for (int i = 0; i < m; ++i) {
-    const double b2 = i > 0 ? be[i - 1] * be[i - 1] : 0.0;
-    d = (al[i] - x) - (i > 0 ? b2 / d : 0.0);
-    if (d == 0.0) d = -1e-300;
-    if (d < 0.0) ++cnt;
+  bool neg_prev = false;  // sign of p_0 = 1
+  bool neg = pm1 < 0.0f || (pm1 == 0.0f && !neg_prev);
+  cnt += neg != neg_prev;
+  neg_prev = neg;
+  for (int i = 1; i < m; ++i) {
+    const float p = fmaf(al[i] - x, pm1, -be2[i - 1] * pm2);
+    neg = p < 0.0f || (p == 0.0f && !neg_prev);
+    cnt += neg != neg_prev;
+    neg_prev = neg;
+    pm2 = pm1;
+    pm1 = p;
+    if (fabsf(pm1) > 0x1p60f) {
+      pm1 *= 0x1p-60f;
+      pm2 *= 0x1p-60f;
+    }
   }
   return cnt;
 }
 
-// Smallest and largest eigenvalues of T_m by bisection inside the Gershgorin interval.
-__device__ void tridiag_extremes(const double* al, const double* be, int m, double* lo_out, double* hi_out) {
-  double glo = 1e300, ghi = -1e300;
-  for (int i = 0; i < m; ++i) {
-    const double rad = (i > 0 ? fabs(be[i - 1]) : 0.0) + (i + 1 < m ? fabs(be[i]) : 0.0);
-    glo = fmin(glo, al[i] - rad);
-    ghi = fmax(ghi, al[i] + rad);
-  }
-  for (int which = 0; which < 2; ++which) {
-    double a = glo, b = ghi;
-    for (int it = 0; it < 200 && b - a > 1e-15 * fmax(fabs(a), fabs(b)); ++it) {
-      const double mid = 0.5 * (a + b);
-      const int c = sturm_count(al, be, m, mid);
-      // which 0: the smallest eigenvalue is below mid iff c >= 1; which 1: the largest iff c >= m
-      if (which == 0 ? (c >= 1) : (c >= m)) b = mid;
-      else a = mid;
+struct TridiagSmem {
+  float al[kLzMaxSteps];
+  float be2[kLzMaxSteps];
+  float lo[2], hi[2];
+  int first[2];
+  double center, scale;
+};
+
+// Smallest and largest eigenvalues of T_m by multisection with every thread of the block:
+// half the threads bracket the smallest, half the largest, each round evaluating one Sturm
+// count per thread at evenly spaced points and keeping the sub-interval where the count
+// first reaches 1 (smallest) or m (largest); four rounds of 128 points narrow [-1, 1] to
+// about 1e-8 of the spectrum's width.  Called by all threads; results in thread 0.
+__device__ void tridiag_extremes_block(const double* al, const double* be, int m, TridiagSmem& ts,
+                                       double* lo_out, double* hi_out) {
+  const int half = blockDim.x / 2;
+  const int grp = threadIdx.x < half ? 0 : 1;
+  const int t = threadIdx.x - grp * half;
+  if (threadIdx.x == 0) {
+    double glo = 1e300, ghi = -1e300;
+    for (int i = 0; i < m; ++i) {
+      const double rad = (i > 0 ? fabs(be[i - 1]) : 0.0) + (i + 1 < m ? fabs(be[i]) : 0.0);
+      glo = fmin(glo, al[i] - rad);
+      ghi = fmax(ghi, al[i] + rad);
     }
-    (which == 0 ? *lo_out : *hi_out) = 0.5 * (a + b);
+    ts.center = 0.5 * (glo + ghi);
+    ts.scale = fmax(0.5 * (ghi - glo), 1e-300);
+    for (int g = 0; g < 2; ++g) {
+      ts.lo[g] = -1.0f;
+      ts.hi[g] = 1.0f;
+    }
+  }
+  __syncthreads();
+  const double c = ts.center, inv = 1.0 / ts.scale;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    ts.al[i] = (float)((al[i] - c) * inv);
+    const float b = (float)(be[i] * inv);
+    ts.be2[i] = b * b;
+  }
+  __syncthreads();
+  for (int round = 0; round < 4; ++round) {
+    if (threadIdx.x < 2) ts.first[threadIdx.x] = half;
+    __syncthreads();
+    const float a = ts.lo[grp], b = ts.hi[grp];
+    const float x = a + (b - a) * (float)(t + 1) / (float)(half + 1);
+    const int cnt = sturm_count_scaled(ts.al, ts.be2, m, x);
+    if (cnt >= (grp == 0 ? 1 : m)) atomicMin(&ts.first[grp], t);
+    __syncthreads();
+    if (t == 0) {
+      const int f = ts.first[grp];
+      const float w = (b - a) / (float)(half + 1);
+      ts.lo[grp] = a + w * (float)f;
+      ts.hi[grp] = f < half ? a + w * (float)(f + 1) : b;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    *lo_out = c + ts.scale * 0.5 * ((double)ts.lo[0] + (double)ts.hi[0]);
+    *hi_out = c + ts.scale * 0.5 * ((double)ts.lo[1] + (double)ts.hi[1]);
   }
 }
 
 struct LzSmem {
-  double part_a[kLzMaxCs];
-  double part_b[kLzMaxCs];
+  float part_a[kLzMaxCs * kLzWarps];  // per (CTA, warp) partials, written remotely by every CTA
+  float part_b[kLzMaxCs * kLzWarps];
   double alpha[kLzMaxSteps];
   double beta[kLzMaxSteps];
-  double warp_part[kLzWarps];
 };
 
 // Rows r0 .. r0 + R - 1 of an n x n symmetric matrix (column-major source, column i = row i)
 // times the full vector x; y[r - r0] receives the products.  src rows come from shared
-// memory (ROWS_IN_SMEM, FP32) or straight from the FP64/FP32 source.
+// memory (ROWS_IN_SMEM, FP32) or straight from the FP64/FP32 source.  Each warp keeps four
+// rows in flight (four independent FMA chains over the same x entries), since one row at a
+// time leaves a warp waiting on a single dependent chain.
+template <bool ROWS_IN_SMEM>
+__device__ __forceinline__ float row_entry(const float* srows, const void* src, int f64, int n, int r0, int rr, int j) {
+  if (ROWS_IN_SMEM) return srows[(size_t)rr * n + j];
+  if (f64) return (float)__ldg(static_cast<const double*>(src) + (size_t)(r0 + rr) * n + j);
+  return __ldg(static_cast<const float*>(src) + (size_t)(r0 + rr) * n + j);
+}
+
 template <bool ROWS_IN_SMEM>
 __device__ void slice_matvec(int n, int r0, int R, const float* srows, const void* src, int f64, const float* x,
                              float* y) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int rr = w; rr < R; rr += kLzWarps) {
-    float acc = 0.f;
-    if (ROWS_IN_SMEM) {
-      const float* row = srows + (size_t)rr * n;
-      for (int j = lane; j < n; j += 32) acc = fmaf(row[j], x[j], acc);
-    } else if (f64) {
-      const double* row = static_cast<const double*>(src) + (size_t)(r0 + rr) * n;
-      for (int j = lane; j < n; j += 32) acc = fmaf((float)__ldg(row + j), x[j], acc);
-    } else {
-      const float* row = static_cast<const float*>(src) + (size_t)(r0 + rr) * n;
-      for (int j = lane; j < n; j += 32) acc = fmaf(__ldg(row + j), x[j], acc);
+  for (int rr = 4 * w; rr < R; rr += 4 * kLzWarps) {
+    const int nrow = min(4, R - rr);
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+    for (int j = lane; j < n; j += 32) {
+      const float xv = x[j];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (q < nrow) acc[q] = fmaf(row_entry<ROWS_IN_SMEM>(srows, src, f64, n, r0, rr + q, j), xv, acc[q]);
     }
-    acc = lz_warp_sum(acc);
-    if (lane == 0) y[rr] = acc;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float v = lz_warp_sum(acc[q]);
+      if (lane == 0 && q < nrow) y[rr + q] = v;
+    }
   }
 }
 
-// Sum over the CTA of v (every thread passes its share); the result is valid in thread 0.
-__device__ double cta_sum(double v, LzSmem& sm) {
+// Warp w of CTA `rank` publishes its partial v into slot rank * kLzWarps + w of every CTA.
+__device__ __forceinline__ void publish_partial(float* slots, float v, int rank, int cs) {
+  v = lz_warp_sum(v);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  __syncthreads();
-  if (lane == 0) sm.warp_part[w] = v;
-  __syncthreads();
-  double s = 0.0;
-  if (threadIdx.x == 0)
-    for (int i = 0; i < kLzWarps; ++i) s += sm.warp_part[i];
-  return s;
+  if (lane < cs) st_remote(&slots[rank * kLzWarps + w], (uint32_t)lane, v);
+}
+
+// Sum of the cs * kLzWarps published partials, formed by every warp in the same order (so
+// every thread of every CTA holds the same value).
+__device__ __forceinline__ float gather_partials(const float* slots, int cs) {
+  const int lane = threadIdx.x & 31;
+  float v = 0.f;
+  for (int i = lane; i < cs * kLzWarps; i += 32) v += slots[i];
+  return lz_warp_sum(v);
 }
 
 struct LzArgs {
@@ -162,11 +224,8 @@ __global__ void __launch_bounds__(kLzThreads, 1) lanczos_cluster_kernel(LzArgs a
   float* tF = rows1 + (SMEM && args.prob[0].M1 != nullptr ? (size_t)R * n : 0);
   float* uF = tF + n;
   float* sF = uF + n;
-  float* vS = sF + n;
-  float* vpS = vS + R;
-  float* yS = vpS + R;
-  float* uS = yS + R;
-  float* sS = uS + R;
+  float* yS = sF + n;  // this CTA's rows of M2 t
+  float* sS = yS + R;  // and of M1 u
   __shared__ LzSmem sm;
   if (SMEM) {
     for (size_t e = threadIdx.x; e < (size_t)nr * n; e += blockDim.x) {
@@ -178,110 +237,97 @@ __global__ void __launch_bounds__(kLzThreads, 1) lanczos_cluster_kernel(LzArgs a
   // Start vector: a fixed deterministic pattern with components along every eigenvector.
   for (int s = threadIdx.x; s < n; s += blockDim.x) uF[s] = 1.0f + 0.5f * __cosf(0.7f * (float)s + 0.3f);
   cluster_sync();  // every CTA of the cluster runs before any shared memory is addressed remotely
-  double nrm2;
+  // v_0 = e / ||e||_M1 and t_0 = M1 v_0 (thread i of each CTA owns entry r0 + i of the slices)
+  float nrm2;
   if (gen) {
     slice_matvec<SMEM>(n, r0, nr, rows1, P.M1, P.m1_f64, uF, sS);
     __syncthreads();
-    double part = 0.0;
-    for (int i = threadIdx.x; i < nr; i += blockDim.x) part += (double)uF[r0 + i] * (double)sS[i];
-    part = cta_sum(part, sm);
-    if (threadIdx.x == 0)
-      for (int rk = 0; rk < cs; ++rk) st_remote_d(&sm.part_b[rank], (uint32_t)rk, part);
-    for (int i = threadIdx.x; i < nr; i += blockDim.x)
+    const int i = threadIdx.x;
+    float part = 0.f;
+    if (i < nr) {
+      part = uF[r0 + i] * sS[i];
       for (int rk = 0; rk < cs; ++rk) st_remote(&tF[r0 + i], (uint32_t)rk, sS[i]);
+    }
+    publish_partial(sm.part_b, part, rank, cs);
     cluster_sync();
-    nrm2 = 0.0;
-    for (int rk = 0; rk < cs; ++rk) nrm2 += sm.part_b[rk];
+    nrm2 = gather_partials(sm.part_b, cs);
   } else {
-    double part = 0.0;
-    for (int s = threadIdx.x; s < n; s += blockDim.x) part += (double)uF[s] * (double)uF[s];
-    part = cta_sum(part, sm);
-    if (threadIdx.x == 0) sm.part_b[0] = part;
+    float part = 0.f;
+    for (int s2 = threadIdx.x; s2 < n; s2 += blockDim.x) part = fmaf(uF[s2], uF[s2], part);
+    part = lz_warp_sum(part);  // every CTA holds all of e: its own sum, no exchange
+    if ((threadIdx.x & 31) == 0) sm.part_b[threadIdx.x >> 5] = part;
     __syncthreads();
-    nrm2 = sm.part_b[0];
-    for (int s = threadIdx.x; s < n; s += blockDim.x) tF[s] = uF[s];
+    nrm2 = gather_partials(sm.part_b, 1);
+    for (int s2 = threadIdx.x; s2 < n; s2 += blockDim.x) tF[s2] = uF[s2];
   }
-  const float inv0 = (float)(1.0 / sqrt(nrm2));
+  const float inv0 = rsqrtf(nrm2);
   __syncthreads();
-  for (int s = threadIdx.x; s < n; s += blockDim.x) tF[s] *= inv0;
-  for (int i = threadIdx.x; i < nr; i += blockDim.x) {
-    vS[i] = uF[r0 + i] * inv0;
-    vpS[i] = 0.f;
-  }
+  for (int s2 = threadIdx.x; s2 < n; s2 += blockDim.x) tF[s2] *= inv0;
+  float vcur = 0.f, vprev = 0.f;  // thread i: v_j and v_{j-1} at entry r0 + i
+  if (threadIdx.x < nr) vcur = uF[r0 + threadIdx.x] * inv0;
   __syncthreads();
-  double beta_prev = 0.0;
+  float beta_prev = 0.f;
   int m = 0;
   for (int j = 0; j < steps; ++j) {
     slice_matvec<SMEM>(n, r0, nr, rows2, P.M2, P.m2_f64, tF, yS);  // y = C v_j = M2 t_j
     __syncthreads();
-    double part = 0.0;
-    for (int i = threadIdx.x; i < nr; i += blockDim.x) part += (double)yS[i] * (double)tF[r0 + i];
-    part = cta_sum(part, sm);
-    if (threadIdx.x == 0)
-      for (int rk = 0; rk < cs; ++rk) st_remote_d(&sm.part_a[rank], (uint32_t)rk, part);
+    const int i = threadIdx.x;
+    const bool mine = i < nr;
+    const float y = mine ? yS[i] : 0.f;
+    publish_partial(sm.part_a, mine ? y * tF[r0 + i] : 0.f, rank, cs);
     cluster_sync();
-    double alpha = 0.0;
-    for (int rk = 0; rk < cs; ++rk) alpha += sm.part_a[rk];  // <C v_j, v_j>_M1 = y^T t_j
-    for (int i = threadIdx.x; i < nr; i += blockDim.x)
-      uS[i] = (float)((double)yS[i] - alpha * (double)vS[i] - beta_prev * (double)vpS[i]);
-    __syncthreads();
+    const float alpha = gather_partials(sm.part_a, cs);  // <C v_j, v_j>_M1 = y^T t_j
+    const float u = mine ? fmaf(-beta_prev, vprev, fmaf(-alpha, vcur, y)) : 0.f;
+    float b2part;
     if (gen) {
-      for (int i = threadIdx.x; i < nr; i += blockDim.x)
-        for (int rk = 0; rk < cs; ++rk) st_remote(&uF[r0 + i], (uint32_t)rk, uS[i]);
+      if (mine)
+        for (int rk = 0; rk < cs; ++rk) st_remote(&uF[r0 + i], (uint32_t)rk, u);
       cluster_sync();
       slice_matvec<SMEM>(n, r0, nr, rows1, P.M1, P.m1_f64, uF, sS);  // s = M1 u
       __syncthreads();
-      part = 0.0;
-      for (int i = threadIdx.x; i < nr; i += blockDim.x) part += (double)uS[i] * (double)sS[i];
-      part = cta_sum(part, sm);
-      if (threadIdx.x == 0)
-        for (int rk = 0; rk < cs; ++rk) st_remote_d(&sm.part_b[rank], (uint32_t)rk, part);
-      for (int i = threadIdx.x; i < nr; i += blockDim.x)
-        for (int rk = 0; rk < cs; ++rk) st_remote(&sF[r0 + i], (uint32_t)rk, sS[i]);
-      cluster_sync();
+      const float sv = mine ? sS[i] : 0.f;
+      if (mine)
+        for (int rk = 0; rk < cs; ++rk) st_remote(&sF[r0 + i], (uint32_t)rk, sv);
+      b2part = u * sv;
     } else {
-      part = 0.0;
-      for (int i = threadIdx.x; i < nr; i += blockDim.x) part += (double)uS[i] * (double)uS[i];
-      part = cta_sum(part, sm);
-      if (threadIdx.x == 0)
-        for (int rk = 0; rk < cs; ++rk) st_remote_d(&sm.part_b[rank], (uint32_t)rk, part);
-      for (int i = threadIdx.x; i < nr; i += blockDim.x)
-        for (int rk = 0; rk < cs; ++rk) st_remote(&uF[r0 + i], (uint32_t)rk, uS[i]);
-      cluster_sync();
+      if (mine)
+        for (int rk = 0; rk < cs; ++rk) st_remote(&uF[r0 + i], (uint32_t)rk, u);
+      b2part = u * u;
     }
-    double b2 = 0.0;
-    for (int rk = 0; rk < cs; ++rk) b2 += sm.part_b[rk];
-    const double beta = sqrt(fmax(b2, 0.0));
+    publish_partial(sm.part_b, b2part, rank, cs);
+    cluster_sync();
+    const float beta = sqrtf(fmaxf(gather_partials(sm.part_b, cs), 0.f));
     if (threadIdx.x == 0) {
-      sm.alpha[j] = alpha;
-      sm.beta[j] = beta;
+      sm.alpha[j] = (double)alpha;
+      sm.beta[j] = (double)beta;
     }
     m = j + 1;
-    if (!(beta > 1e-10 * fabs(alpha)) || !isfinite(beta)) break;  // invariant subspace (or breakdown)
-    const float ib = (float)(1.0 / beta);
+    if (!(beta > 1e-6f * fabsf(alpha)) || !isfinite(beta)) break;  // invariant subspace (same in every thread)
+    const float ib = 1.0f / beta;
+    vprev = vcur;
+    vcur = u * ib;
     const float* next_t = gen ? sF : uF;
-    for (int i = threadIdx.x; i < nr; i += blockDim.x) {
-      vpS[i] = vS[i];
-      vS[i] = uS[i] * ib;
-    }
-    for (int s = threadIdx.x; s < n; s += blockDim.x) tF[s] = next_t[s] * ib;
+    for (int s2 = threadIdx.x; s2 < n; s2 += blockDim.x) tF[s2] = next_t[s2] * ib;
     beta_prev = beta;
     __syncthreads();
   }
   __syncthreads();
-  if (rank == 0 && threadIdx.x == 0) {
+  if (rank == 0) {
+    __shared__ TridiagSmem ts;
     double lo = 0.0, hi = 0.0;
-    if (m > 0) tridiag_extremes(sm.alpha, sm.beta, m, &lo, &hi);
-    P.out[0] = lo;
-    P.out[1] = hi;
-    P.out[2] = (double)m;
+    if (m > 0) tridiag_extremes_block(sm.alpha, sm.beta, m, ts, &lo, &hi);
+    if (threadIdx.x == 0) {
+      P.out[0] = lo;
+      P.out[1] = hi;
+      P.out[2] = (double)m;
+    }
   }
   cluster_sync();  // no CTA leaves while another may still store into its shared memory
 }
 
 size_t lz_smem(int64_t n, int cs, bool rows, bool any_gen) {
   const int64_t R = (n + cs - 1) / cs;
-  return sizeof(float) * (size_t)((rows ? R * n * (any_gen ? 2 : 1) : 0) + 3 * n + 5 * R + 4);
+  return sizeof(float) * (size_t)((rows ? R * n * (any_gen ? 2 : 1) : 0) + 3 * n + 2 * R + 4);
 }
 
 template <bool SMEM>
@@ -346,16 +392,21 @@ __global__ void estimates_finish_kernel(const double* kap_out, const double* rho
 // P is FP32 (n <= 512).
 constexpr int kMfThreads = 512;
 
-__device__ __forceinline__ double mf_block_sum(double v, double* red) {
+// Block sum of FP32 shares, accumulated in FP64 by thread 0 alone and broadcast (as FP64)
+// through shared memory.
+__device__ double mf_block_sum(float v, float* red, double* out) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  v = lz_warp_sum(v);
   __syncthreads();
   if (lane == 0) red[w] = v;
   __syncthreads();
-  double s = 0.0;
-  for (int i = 0; i < kMfThreads / 32; ++i) s += red[i];
-  return s;
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < kMfThreads / 32; ++i) s += (double)red[i];
+    *out = s;
+  }
+  __syncthreads();
+  return *out;
 }
 
 // y := M x for the n x n FP32 matrix M (column i = row i): a warp per row.
@@ -395,7 +446,9 @@ __device__ MfState mf_state(int n, float* w) {
 }
 
 __global__ void __launch_bounds__(kMfThreads) lz_mf_init_kernel(int n, const float* P, float* w) {
-  __shared__ double red[kMfThreads / 32];
+  __shared__ float red[kMfThreads / 32];
+  __shared__ double sum;
+  __shared__ float inv;
   MfState st = mf_state(n, w);
   for (int s = threadIdx.x; s < n; s += blockDim.x) {
     st.u[s] = 1.0f + 0.5f * __cosf(0.7f * (float)s + 0.3f);
@@ -404,12 +457,14 @@ __global__ void __launch_bounds__(kMfThreads) lz_mf_init_kernel(int n, const flo
   __syncthreads();
   mf_matvec(n, P, st.u, st.s);
   __syncthreads();
-  double part = 0.0;
-  for (int s = threadIdx.x; s < n; s += blockDim.x) part += (double)st.u[s] * (double)st.s[s];
-  const double inv = 1.0 / sqrt(mf_block_sum(part, red));
+  float part = 0.f;
+  for (int s = threadIdx.x; s < n; s += blockDim.x) part = fmaf(st.u[s], st.s[s], part);
+  mf_block_sum(part, red, &sum);
+  if (threadIdx.x == 0) inv = (float)(1.0 / sqrt(sum));
+  __syncthreads();
   for (int s = threadIdx.x; s < n; s += blockDim.x) {
-    st.v[s] = (float)(st.u[s] * inv);
-    st.t[s] = st.s[s] * inv;
+    st.v[s] = st.u[s] * inv;
+    st.t[s] = (double)(st.s[s] * inv);
   }
   if (threadIdx.x == 0) {
     st.scal[0] = 0.0;
@@ -418,50 +473,63 @@ __global__ void __launch_bounds__(kMfThreads) lz_mf_init_kernel(int n, const flo
   }
 }
 
-// One step after y = A_2^T (A_2 t_j) (FP64, from the stream).
+// One step after y = A_2^T (A_2 t_j) (FP64, from the stream).  Scalars in thread 0.
 __global__ void __launch_bounds__(kMfThreads) lz_mf_step_kernel(int n, const float* P, const double* y, float* w,
                                                                 int j) {
-  __shared__ double red[kMfThreads / 32];
+  __shared__ float red[kMfThreads / 32];
+  __shared__ double sum;
+  __shared__ float sc[3];
+  __shared__ int stopped;
   MfState st = mf_state(n, w);
-  if (st.scal[2] != 0.0) return;  // stopped at an invariant subspace
-  double part = 0.0;
-  for (int s = threadIdx.x; s < n; s += blockDim.x) part += y[s] * st.t[s];
-  const double alpha = mf_block_sum(part, red);
-  const double bprev = st.scal[0];
+  if (threadIdx.x == 0) stopped = st.scal[2] != 0.0;
+  __syncthreads();
+  if (stopped) return;  // stopped at an invariant subspace
+  float part = 0.f;
+  for (int s = threadIdx.x; s < n; s += blockDim.x) part = fmaf((float)y[s], (float)st.t[s], part);
+  const double alpha = mf_block_sum(part, red, &sum);
+  if (threadIdx.x == 0) {
+    sc[0] = (float)alpha;
+    sc[1] = (float)st.scal[0];
+  }
+  __syncthreads();
   for (int s = threadIdx.x; s < n; s += blockDim.x)
-    st.u[s] = (float)(y[s] - alpha * (double)st.v[s] - bprev * (double)st.vp[s]);
+    st.u[s] = fmaf(-sc[1], st.vp[s], fmaf(-sc[0], st.v[s], (float)y[s]));
   __syncthreads();
   mf_matvec(n, P, st.u, st.s);
   __syncthreads();
-  part = 0.0;
-  for (int s = threadIdx.x; s < n; s += blockDim.x) part += (double)st.u[s] * (double)st.s[s];
-  const double beta = sqrt(fmax(mf_block_sum(part, red), 0.0));
-  const bool stop = !(beta > 1e-10 * fabs(alpha)) || !isfinite(beta);
-  const double ib = stop ? 0.0 : 1.0 / beta;
-  for (int s = threadIdx.x; s < n; s += blockDim.x) {
-    st.vp[s] = st.v[s];
-    st.v[s] = (float)(st.u[s] * ib);
-    st.t[s] = st.s[s] * ib;
-  }
-  __syncthreads();
+  part = 0.f;
+  for (int s = threadIdx.x; s < n; s += blockDim.x) part = fmaf(st.u[s], st.s[s], part);
+  const double b2 = mf_block_sum(part, red, &sum);
   if (threadIdx.x == 0) {
+    const double beta = sqrt(fmax(b2, 0.0));
+    const bool stop = !(beta > 1e-10 * fabs(alpha)) || !isfinite(beta);
+    sc[2] = stop ? 0.f : (float)(1.0 / beta);
     st.alpha[j] = alpha;
     st.beta[j] = beta;
     st.scal[0] = beta;
     st.scal[1] = (double)(j + 1);
     if (stop) st.scal[2] = 1.0;
   }
+  __syncthreads();
+  const float ib = sc[2];
+  for (int s = threadIdx.x; s < n; s += blockDim.x) {
+    st.vp[s] = st.v[s];
+    st.v[s] = st.u[s] * ib;
+    st.t[s] = (double)(st.s[s] * ib);
+  }
 }
 
 __global__ void lz_mf_finish_kernel(int n, float* w, double* out) {
-  if (threadIdx.x != 0) return;
+  __shared__ TridiagSmem ts;
   MfState st = mf_state(n, w);
   const int m = (int)st.scal[1];
   double lo = 0.0, hi = 0.0;
-  if (m > 0) tridiag_extremes(st.alpha, st.beta, m, &lo, &hi);
-  out[0] = lo;
-  out[1] = hi;
-  out[2] = (double)m;
+  if (m > 0) tridiag_extremes_block(st.alpha, st.beta, m, ts, &lo, &hi);
+  if (threadIdx.x == 0) {
+    out[0] = lo;
+    out[1] = hi;
+    out[2] = (double)m;
+  }
 }
 
 }  // namespace
@@ -481,14 +549,24 @@ cudaError_t lanczos_extremes(int count, const LanczosProblem* probs, cudaStream_
   a.count = count;
   const int64_t n = probs[0].n;
   const size_t limit = 220 * 1024;
-  for (int cs : {16, 8}) {
-    a.cs = cs;
-    const size_t sm_rows = lz_smem(n, cs, true, any_gen);
-    cudaError_t e;
-    if (sm_rows <= limit) e = lz_launch<true>(a, sm_rows, s);
-    else e = lz_launch<false>(a, lz_smem(n, cs, false, any_gen), s);
-    if (e == cudaSuccess) return e;
-    cudaGetLastError();  // cluster size not available: try the portable size
+  // A thread of each CTA owns one row of the CTA's slice, so a slice holds at most kLzThreads
+  // rows: 8 CTAs up to n = 2048, 16 up to n = 4096.  The rows stay in shared memory where
+  // they fit, else each step reads them from L2.
+  for (int pass = 0; pass < 2; ++pass) {  // rows in shared memory first, then rows from L2
+    for (int cs : {8, 16}) {
+      if ((n + cs - 1) / cs > kLzThreads) continue;
+      a.cs = cs;
+      const size_t sm_rows = lz_smem(n, cs, true, any_gen);
+      cudaError_t e;
+      if (pass == 0) {
+        if (sm_rows > limit) continue;
+        e = lz_launch<true>(a, sm_rows, s);
+      } else {
+        e = lz_launch<false>(a, lz_smem(n, cs, false, any_gen), s);
+      }
+      if (e == cudaSuccess) return e;
+      cudaGetLastError();  // this cluster size is not available: try the next
+    }
   }
   return cudaErrorNotSupported;
 }
@@ -510,7 +588,7 @@ cudaError_t lz_mf_step(int64_t n, const float* P, const double* y, float* w, int
 }
 
 cudaError_t lz_mf_finish(int64_t n, float* w, double* out, cudaStream_t s) {
-  lz_mf_finish_kernel<<<1, 32, 0, s>>>((int)n, w, out);
+  lz_mf_finish_kernel<<<1, 256, 0, s>>>((int)n, w, out);
   note_launch();
   return cudaGetLastError();
 }

@@ -136,6 +136,11 @@ struct SelSmem {
   int res_idx;
   double res_val;
   double rr;
+  // per-step scalars, formed by one thread (the FP64 pipe issues two operations a clock per
+  // SM: an FP64 scalar repeated by every thread would cost more than the step's vector work)
+  double delta;
+  int stop;     // 1: the inner stop test holds (or ||r||^2 is not finite)
+  int rank;     // rank of the next pick
 };
 
 constexpr int kNone = 0x7fffffff;
@@ -159,8 +164,8 @@ __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned
 
 // i <= kTop.  Leaves the pick in sm.res_idx / sm.res_val (res_idx = -1 if none).  Also
 // reduces ||r||^2 (rpart: this thread's partial) into sm.rr.  Two block barriers.
-template <int T, int RPT>
-__device__ void select_fast(const double (&r)[RPT], int n, int i, double rpart, SelSmem& sm) {
+template <int T, int RPT, class Decide>
+__device__ void select_fast(const double (&r)[RPT], int n, int i, double rpart, SelSmem& sm, Decide& decide) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   constexpr int W = T / 32;
   const int rounds = i < kTop ? i : kTop;
@@ -230,28 +235,32 @@ __device__ void select_fast(const double (&r)[RPT], int n, int i, double rpart, 
       sm.res_idx = wi == kNone ? -1 : wi;
       sm.res_val = __longlong_as_double((long long)wv);
       sm.rr = rr;
+      decide(true);
     }
   }
   __syncthreads();
 }
 
-// ||r||^2 alone (no pick): two block barriers.
+// ||r||^2 alone (no pick), into sm.rr by thread 0 (valid for every thread after the next
+// barrier the caller places).  One block barrier here.
 template <int T>
-__device__ double block_sum_sm(double rpart, SelSmem& sm) {
+__device__ void block_sum_sm(double rpart, SelSmem& sm) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   constexpr int W = T / 32;
   rpart = warp_sum(rpart);
-  __syncthreads();  // sm.warp_rr may still be read
   if (lane == 0) sm.warp_rr[w] = rpart;
   __syncthreads();
-  double v = lane < W ? sm.warp_rr[lane] : 0.0;
-  return warp_sum(v);
+  if (w == 0) {
+    double v = lane < W ? sm.warp_rr[lane] : 0.0;
+    v = warp_sum(v);
+    if (lane == 0) sm.rr = v;
+  }
 }
 
 // i > kTop (any i <= number of valid entries): radix selection on the 64-bit keys.  Leaves
 // the pick in sm.res_idx / sm.res_val.
-template <int T, int RPT>
-__device__ void select_radix(const double (&r)[RPT], int n, int i, SelSmem& sm) {
+template <int T, int RPT, class Decide>
+__device__ void select_radix(const double (&r)[RPT], int n, int i, SelSmem& sm, Decide& decide) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   constexpr int W = T / 32;
   unsigned long long prefix = 0ull, mask = 0ull;
@@ -355,6 +364,7 @@ __device__ void select_radix(const double (&r)[RPT], int n, int i, SelSmem& sm) 
   if (threadIdx.x == 0) {
     sm.res_idx = (rem > 0 && last >= 0) ? last : -1;
     sm.res_val = __longlong_as_double((long long)lastv);
+    decide(false);
   }
   __syncthreads();
 }
@@ -387,7 +397,7 @@ __global__ void __launch_bounds__(T, 1) scd_chain_kernel(RandArgs a) {
   const int n = (int)a.n;
   const ChainIo io = chain_io(a, c);
   const uint32_t k = (uint32_t)(st->iters - 1);  // outer index of the iterate being built
-  extern __shared__ double diag[];               // Abar1_jj = ||A_1(:,j)||^2
+  extern __shared__ double idiag[];              // 1 / Abar1_jj = 1 / ||A_1(:,j)||^2
   __shared__ SelSmem sm;
   const double* bhat = a.bhat + (size_t)c * n;
   double r[RPT];
@@ -398,50 +408,61 @@ __global__ void __launch_bounds__(T, 1) scd_chain_kernel(RandArgs a) {
     r[u] = s < n ? bhat[s] : 0.0;
     part = fma(r[u], r[u], part);
     if (s < n) {
-      diag[s] = a.norms2[s];
+      idiag[s] = a.inv_norms2[s];
       if (!a.correction) io.xout[s] = 0.0;  // beta = 0
     }
   }
-  __syncthreads();
   const double target2 = a.col_target2[c];
   const bool record = a.picks && c == 0 && k == 0;
   const int alpha = (int)a.alpha_fixed;
+  const uint32_t chain = (uint32_t)(a.chain0 + c);
   int64_t t = 0;
-  for (; t < a.max_inner; ++t) {
-    int i = 1;
-    if (alpha > 0) {
-      if (alpha < n) {
-        double u0, u1;
-        step_uniforms(a.seed, (uint32_t)(a.chain0 + c), k, (uint64_t)t, &u0, &u1);
-        i = scd_fixed_rank(u0, n, alpha);
-      }
-    } else if (!a.greedy) {
-      double u0, u1;
-      step_uniforms(a.seed, (uint32_t)(a.chain0 + c), k, (uint64_t)t, &u0, &u1);
-      i = scd_rank(u0, n);
-    }
-    double rr;
-    if (i <= kTop) {
-      select_fast<T, RPT>(r, n, i, part, sm);
-      rr = sm.rr;
-      if (!(rr > target2)) {
-        if (!isfinite(rr) && threadIdx.x == 0) atomicCAS(&st->status, 0, ILS_ERR_NONFINITE);
-        break;
-      }
-    } else {
-      rr = block_sum_sm<T>(part, sm);
-      if (!(rr > target2)) {
-        if (!isfinite(rr) && threadIdx.x == 0) atomicCAS(&st->status, 0, ILS_ERR_NONFINITE);
-        break;
-      }
-      select_radix<T, RPT>(r, n, i, sm);
+  // Rank of the pick of step tt (Alg. 5 steps 7-9 in rank form; thread 0 only).
+  auto draw_rank = [&](int64_t tt) -> int {
+    if (alpha > 0 && alpha >= n) return 1;
+    if (alpha <= 0 && a.greedy) return 1;
+    double u0, u1;
+    step_uniforms(a.seed, chain, k, (uint64_t)tt, &u0, &u1);
+    return alpha > 0 ? scd_fixed_rank(u0, n, alpha) : scd_rank(u0, n);
+  };
+  // One thread: the stop test on ||r_t||^2, delta = r_j / Abar1_jj (steps 10-11, by the
+  // precomputed reciprocal) and the
+  // rank of the next step's pick.
+  auto decide = [&](bool check_stop) {
+    if (check_stop && !(sm.rr > target2)) {
+      sm.stop = 1;
+      if (!isfinite(sm.rr)) atomicCAS(&st->status, 0, ILS_ERR_NONFINITE);
+      return;
     }
     const int j = sm.res_idx;
     if (j < 0) {
-      if (threadIdx.x == 0) atomicCAS(&st->status, 0, ILS_ERR_NONFINITE);
-      break;
+      sm.stop = 1;
+      atomicCAS(&st->status, 0, ILS_ERR_NONFINITE);
+      return;
     }
-    const double delta = sm.res_val / diag[j];  // steps 10-11: r_j / Abar1_jj
+    sm.stop = 0;
+    sm.delta = sm.res_val * idiag[j];
+    sm.rank = t + 1 < a.max_inner ? draw_rank(t + 1) : 1;
+  };
+  if (threadIdx.x == 0) sm.rank = a.max_inner > 0 ? draw_rank(0) : 1;
+  __syncthreads();
+  for (; t < a.max_inner; ++t) {
+    const int i = sm.rank;
+    if (i <= kTop) {
+      select_fast<T, RPT>(r, n, i, part, sm, decide);
+    } else {
+      block_sum_sm<T>(part, sm);
+      if (threadIdx.x == 0) {
+        sm.stop = !(sm.rr > target2) ? 1 : 0;
+        if (sm.stop && !isfinite(sm.rr)) atomicCAS(&st->status, 0, ILS_ERR_NONFINITE);
+      }
+      __syncthreads();
+      if (sm.stop) break;
+      select_radix<T, RPT>(r, n, i, sm, decide);
+    }
+    if (sm.stop) break;
+    const int j = sm.res_idx;
+    const double delta = sm.delta;
     if (threadIdx.x == (unsigned)(j % T)) io.xout[j] += delta;
     if (record && threadIdx.x == 0 && t < a.picks_cap) a.picks[t] = j;
     const double* gj = a.G1 + (size_t)j * n;
@@ -524,6 +545,9 @@ __global__ void __launch_bounds__(kChainThreads) rkrgs_chain_kernel(RandArgs a) 
     e = w + p;
   }
   __shared__ double red[kChainWarps + 1];
+  __shared__ int draw[2];
+  __shared__ double coef;
+  __shared__ int stop_flag;
   const double* bhat = a.bhat + (size_t)c * n;
   for (int s = threadIdx.x; s < n; s += blockDim.x) {
     z[s] = 0.0;
@@ -542,21 +566,38 @@ __global__ void __launch_bounds__(kChainThreads) rkrgs_chain_kernel(RandArgs a) 
   const double target2 = a.col_target2[c];
   const int64_t check = a.check_every;
   const bool record = a.picks && c == 0 && k == 0;
+  const uint32_t chain = (uint32_t)(a.chain0 + c);
+  // Block sum of the threads' shares; thread 0 then forms the step's scalar from it.
+  auto reduce0 = [&](double v) -> double {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    if (lane == 0) red[wp] = v;
+    __syncthreads();
+    double tot = 0.0;
+    if (threadIdx.x == 0)
+      for (int i = 0; i < kChainWarps; ++i) tot += red[i];
+    return tot;  // thread 0 only
+  };
   int64_t t = 0;
   bool stop = false;
   for (; t < a.max_inner && !stop; ++t) {
-    int j1, j2;
-    draw_columns(a, cum, aprob, aidx, n, (uint32_t)(a.chain0 + c), k, t, &j1, &j2);
-    if (record && threadIdx.x == 0 && 2 * t + 1 < a.picks_cap) {
-      a.picks[2 * t] = j1;
-      a.picks[2 * t + 1] = j2;
+    if (threadIdx.x == 0) {
+      draw_columns(a, cum, aprob, aidx, n, chain, k, t, &draw[0], &draw[1]);
+      if (record && 2 * t + 1 < a.picks_cap) {
+        a.picks[2 * t] = draw[0];
+        a.picks[2 * t + 1] = draw[1];
+      }
     }
+    __syncthreads();
+    const int j1 = draw[0], j2 = draw[1];
     // RK step on A_1^T w = bhat (step 9).
     const double* a1 = a.A + (size_t)j1 * m;
     double part = 0.0;
     for (int64_t r = threadIdx.x; r < p; r += blockDim.x) part = fma(a1[r], w[r], part);
-    const double dot1 = block_sum(part, red);
-    const double delta = (bhat[j1] - dot1) / a.norms2[j1];
+    const double dot1 = reduce0(part);
+    if (threadIdx.x == 0) coef = (bhat[j1] - dot1) / a.norms2[j1];
+    __syncthreads();
+    const double delta = coef;
     for (int64_t r = threadIdx.x; r < p; r += blockDim.x) {
       const double av = a1[r];
       w[r] = fma(delta, av, w[r]);
@@ -566,13 +607,16 @@ __global__ void __launch_bounds__(kChainThreads) rkrgs_chain_kernel(RandArgs a) 
     const double* a2 = a.A + (size_t)j2 * m;
     part = 0.0;
     for (int64_t r = threadIdx.x; r < p; r += blockDim.x) part = fma(a2[r], e[r], part);
-    const double dot2 = block_sum(part, red);
-    const double eps = dot2 / a.norms2[j2];
-    if (threadIdx.x == 0) z[j2] += eps;
+    const double dot2 = reduce0(part);
+    if (threadIdx.x == 0) {
+      coef = dot2 / a.norms2[j2];
+      z[j2] += coef;
+    }
+    __syncthreads();
+    const double eps = coef;
     for (int64_t r = threadIdx.x; r < p; r += blockDim.x) e[r] = fma(-eps, a2[r], e[r]);
     if ((t + 1) % check == 0) {
       // Inner stop test: ||bhat - Abar1 z||^2 <= target2.
-      __syncthreads();
       part = 0.0;
       for (int row = threadIdx.x; row < n; row += blockDim.x) {
         const double* g = a.G1 + (size_t)row * n;  // column `row` = row `row` (symmetric)
@@ -581,8 +625,10 @@ __global__ void __launch_bounds__(kChainThreads) rkrgs_chain_kernel(RandArgs a) 
         const double rv = bhat[row] - acc;
         part = fma(rv, rv, part);
       }
-      const double res2 = block_sum(part, red);
-      if (res2 <= target2) stop = true;
+      const double res2 = reduce0(part);
+      if (threadIdx.x == 0) stop_flag = res2 <= target2 ? 1 : 0;
+      __syncthreads();
+      stop = stop_flag != 0;
     }
   }
   __syncthreads();
@@ -615,11 +661,12 @@ __global__ void __launch_bounds__(T, 1) rkrgs_gram_chain_kernel(RandArgs a) {
   const ChainIo io = chain_io(a, c);
   const uint32_t k = (uint32_t)(st->iters - 1);
   extern __shared__ double gsm[];
-  double* diag = gsm;          // n
+  double* idiag = gsm;         // n: 1 / Abar1_jj
   double* cum = gsm + n;       // n, or the alias table (n doubles + n ints)
   double* aprob = cum;
   int32_t* aidx = reinterpret_cast<int32_t*>(gsm + 2 * n);
   __shared__ double slot[2];
+  __shared__ int draw[2][2];   // (j1, j2) of the current and the next step, by parity
   __shared__ SelSmem sm;
   const double* bhat = a.bhat + (size_t)c * n;
   double bh[RPT], g[RPT], h[RPT];
@@ -630,7 +677,7 @@ __global__ void __launch_bounds__(T, 1) rkrgs_gram_chain_kernel(RandArgs a) {
     g[u] = 0.0;
     h[u] = 0.0;
     if (s < n) {
-      diag[s] = a.norms2[s];
+      idiag[s] = a.inv_norms2[s];
       if (a.alias) {
         aprob[s] = a.alias_prob[s];
         aidx[s] = a.alias_idx[s];
@@ -644,40 +691,68 @@ __global__ void __launch_bounds__(T, 1) rkrgs_gram_chain_kernel(RandArgs a) {
   const double target2 = a.col_target2[c];
   const int64_t check = a.check_every;
   const bool record = a.picks && c == 0 && k == 0;
+  const uint32_t chain = (uint32_t)(a.chain0 + c);
+  if (threadIdx.x == 0 && a.max_inner > 0) draw_columns(a, cum, aprob, aidx, n, chain, k, 0, &draw[0][0], &draw[0][1]);
+  __syncthreads();
+  // The columns of Abar1 a step applies depend only on its draws, which are made a step
+  // ahead: each step loads the next step's two columns while it works on its own.
+  double c1[RPT], c2[RPT], n1[RPT], n2[RPT];
+  if (a.max_inner > 0) {
+    const double* p1 = a.G1 + (size_t)draw[0][0] * n;
+    const double* p2 = a.G1 + (size_t)draw[0][1] * n;
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+      const int s = threadIdx.x + u * T;
+      c1[u] = s < n ? __ldg(p1 + s) : 0.0;
+      c2[u] = s < n ? __ldg(p2 + s) : 0.0;
+    }
+  }
   int64_t t = 0;
   for (; t < a.max_inner; ++t) {
-    int j1, j2;
-    draw_columns(a, cum, aprob, aidx, n, (uint32_t)(a.chain0 + c), k, t, &j1, &j2);
-    if (record && threadIdx.x == 0 && 2 * t + 1 < a.picks_cap) {
-      a.picks[2 * t] = j1;
-      a.picks[2 * t + 1] = j2;
+    const int par = (int)(t & 1);
+    const int j1 = draw[par][0], j2 = draw[par][1];
+    if (threadIdx.x == 0) {
+      if (record && 2 * t + 1 < a.picks_cap) {
+        a.picks[2 * t] = j1;
+        a.picks[2 * t + 1] = j2;
+      }
+      if (t + 1 < a.max_inner) draw_columns(a, cum, aprob, aidx, n, chain, k, t + 1, &draw[par ^ 1][0], &draw[par ^ 1][1]);
     }
     if (threadIdx.x == (unsigned)(j1 % T)) {
 #pragma unroll
       for (int u = 0; u < RPT; ++u)
-        if (u == j1 / T) slot[0] = bh[u] - g[u];
+        if (u == j1 / T) slot[0] = (bh[u] - g[u]) * idiag[j1];  // delta (step 9)
     }
     __syncthreads();
-    const double delta = slot[0] / diag[j1];
-    const double* c1 = a.G1 + (size_t)j1 * n;
+    const double delta = slot[0];
+    if (t + 1 < a.max_inner) {  // the next step's columns (its draws are in place now)
+      const double* p1 = a.G1 + (size_t)draw[par ^ 1][0] * n;
+      const double* p2 = a.G1 + (size_t)draw[par ^ 1][1] * n;
 #pragma unroll
-    for (int u = 0; u < RPT; ++u) {
-      const int s = threadIdx.x + u * T;
-      if (s < n) g[u] = fma(delta, __ldg(c1 + s), g[u]);
+      for (int u = 0; u < RPT; ++u) {
+        const int s = threadIdx.x + u * T;
+        n1[u] = s < n ? __ldg(p1 + s) : 0.0;
+        n2[u] = s < n ? __ldg(p2 + s) : 0.0;
+      }
     }
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) g[u] = fma(delta, c1[u], g[u]);
     if (threadIdx.x == (unsigned)(j2 % T)) {
 #pragma unroll
       for (int u = 0; u < RPT; ++u)
-        if (u == j2 / T) slot[1] = g[u] - h[u];
+        if (u == j2 / T) {
+          const double eps = (g[u] - h[u]) * idiag[j2];  // step 11
+          slot[1] = eps;
+          io.xout[j2] += eps;
+        }
     }
     __syncthreads();
-    const double eps = slot[1] / diag[j2];
-    if (threadIdx.x == (unsigned)(j2 % T)) io.xout[j2] += eps;
-    const double* c2 = a.G1 + (size_t)j2 * n;
+    const double eps = slot[1];
 #pragma unroll
     for (int u = 0; u < RPT; ++u) {
-      const int s = threadIdx.x + u * T;
-      if (s < n) h[u] = fma(eps, __ldg(c2 + s), h[u]);
+      h[u] = fma(eps, c2[u], h[u]);
+      c1[u] = n1[u];
+      c2[u] = n2[u];
     }
     if ((t + 1) % check == 0) {
       double part = 0.0;
@@ -686,7 +761,10 @@ __global__ void __launch_bounds__(T, 1) rkrgs_gram_chain_kernel(RandArgs a) {
         const double rv = bh[u] - h[u];
         part = fma(rv, rv, part);
       }
-      if (block_sum_sm<T>(part, sm) <= target2) {
+      block_sum_sm<T>(part, sm);
+      if (threadIdx.x == 0) sm.stop = sm.rr <= target2 ? 1 : 0;
+      __syncthreads();
+      if (sm.stop) {
         ++t;
         break;
       }
@@ -744,8 +822,12 @@ __global__ void alias_table_kernel(int n, const double* __restrict__ norms2, dou
 
 // cum[j] = sum_{i <= j} norms2[i], added left to right; norms2 = diag(Abar1).  The
 // diagonal is gathered in parallel; one thread then adds it in order, 32 loads at a time.
-__global__ void column_cumsum_kernel(int64_t n, const double* G1, double* norms2, double* cum) {
-  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) norms2[j] = G1[j + j * n];
+__global__ void column_cumsum_kernel(int64_t n, const double* G1, double* norms2, double* cum, double* inv_norms2) {
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+    const double d = G1[j + j * n];
+    norms2[j] = d;
+    if (inv_norms2) inv_norms2[j] = 1.0 / d;
+  }
   __syncthreads();
   if (threadIdx.x != 0) return;
   double s = 0.0;
@@ -787,8 +869,9 @@ cudaError_t alias_table_f64(int64_t n, const double* norms2, double* prob, int32
   return cudaGetLastError();
 }
 
-cudaError_t column_cumsum_f64(int64_t n, const double* G1, double* norms2, double* cum, cudaStream_t s) {
-  column_cumsum_kernel<<<1, 256, 0, s>>>(n, G1, norms2, cum);
+cudaError_t column_cumsum_f64(int64_t n, const double* G1, double* norms2, double* cum, cudaStream_t s,
+                              double* inv_norms2) {
+  column_cumsum_kernel<<<1, 256, 0, s>>>(n, G1, norms2, cum, inv_norms2);
   note_launch();
   return cudaGetLastError();
 }
@@ -800,23 +883,29 @@ size_t rkrgs_smem_bytes(int64_t n, int64_t p, bool vec_in_smem) {
 
 bool rkrgs_vec_fits(int64_t n, int64_t p) { return rkrgs_smem_bytes(n, p, true) <= 200 * 1024; }
 
+// Register layouts: about eight entries of each vector per thread.  The FP64 pipe issues two
+// operations a clock per SM, so every warp-wide FP64 reduction costs 80 clocks of it; fewer,
+// fuller threads keep the per-step reductions cheap while the entry-wise work stays n.
 cudaError_t rand_chain_f64(const RandArgs& a, int method, cudaStream_t s) {
   const unsigned grid = (unsigned)a.k;
   const int64_t n = a.n;
   if (method == ILS_SP_SCD) {
     const size_t smem = sizeof(double) * (size_t)n;
-    if (n <= 1024) return launch_chain(scd_chain_kernel<1024, 1>, grid, 1024, smem, a, s);
-    if (n <= 2048) return launch_chain(scd_chain_kernel<1024, 2>, grid, 1024, smem, a, s);
-    if (n <= 4096) return launch_chain(scd_chain_kernel<1024, 4>, grid, 1024, smem, a, s);
+    if (n <= 256) return launch_chain(scd_chain_kernel<256, 1>, grid, 256, smem, a, s);
+    if (n <= 512) return launch_chain(scd_chain_kernel<256, 2>, grid, 256, smem, a, s);
+    if (n <= 1024) return launch_chain(scd_chain_kernel<256, 4>, grid, 256, smem, a, s);
+    if (n <= 2048) return launch_chain(scd_chain_kernel<256, 8>, grid, 256, smem, a, s);
+    if (n <= 4096) return launch_chain(scd_chain_kernel<512, 8>, grid, 512, smem, a, s);
     if (n <= 8192) return launch_chain(scd_chain_kernel<512, 16>, grid, 512, smem, a, s);
     if (n <= 16384) return launch_chain(scd_chain_kernel<512, 32>, grid, 512, smem, a, s);
     return cudaErrorInvalidValue;
   }
   if (a.gram_form) {
     const size_t smem = sizeof(double) * (size_t)(2 * n + (n + 1) / 2);
-    if (n <= 512) return launch_chain(rkrgs_gram_chain_kernel<512, 1>, grid, 512, smem, a, s);
-    if (n <= 1024) return launch_chain(rkrgs_gram_chain_kernel<512, 2>, grid, 512, smem, a, s);
-    if (n <= 2048) return launch_chain(rkrgs_gram_chain_kernel<512, 4>, grid, 512, smem, a, s);
+    if (n <= 256) return launch_chain(rkrgs_gram_chain_kernel<256, 1>, grid, 256, smem, a, s);
+    if (n <= 512) return launch_chain(rkrgs_gram_chain_kernel<256, 2>, grid, 256, smem, a, s);
+    if (n <= 1024) return launch_chain(rkrgs_gram_chain_kernel<256, 4>, grid, 256, smem, a, s);
+    if (n <= 2048) return launch_chain(rkrgs_gram_chain_kernel<256, 8>, grid, 256, smem, a, s);
     if (n <= 4096) return launch_chain(rkrgs_gram_chain_kernel<512, 8>, grid, 512, smem, a, s);
     if (n <= 8192) return launch_chain(rkrgs_gram_chain_kernel<512, 16>, grid, 512, smem, a, s);
     return cudaErrorInvalidValue;

@@ -109,3 +109,42 @@ def test_null_handles_are_rejected_on_the_host(libpath):
     lib.ils_destroy(None)
     lib.ils_batch_destroy(None)
     lib.ils_mlp_destroy(None)
+
+
+def test_noalloc_cuda_failure_is_described_without_gpu(libpath):
+    """With no CUDA device the no-allocation Gram fails its device lookup on the host: it
+    returns ILS_ERR_CUDA and ils_last_error describes the failing call.  (Only where no
+    device is visible: the pointers below are placeholders that are never dereferenced
+    because the lookup fails first.)"""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is visible: the placeholder pointers must not reach a kernel")
+    from paper_2203_15340_gb300 import binding
+    lib = binding.lib()
+    code = lib.ils_gram_noalloc(16, 8, 256, 16, 512, 8, None)
+    assert code == binding.ILS_ERR_CUDA
+    msg = lib.ils_last_error().decode()
+    assert "ils_gram_noalloc" in msg and len(msg) > len("ils_gram_noalloc")
+
+
+def test_new_options_are_validated_on_the_host(libpath):
+    """Out-of-range values of the options added for the stop rules, the samplers and the
+    estimates are rejected by ils_setup before any CUDA call."""
+    from paper_2203_15340_gb300 import binding
+    lib = binding.lib()
+    h = ctypes.c_void_p()
+    o = binding.options()
+    assert o.stop_rule == 0 and o.estimate == 0 and o.alpha_mode == 0 and o.sampler == 0 and o.factor64 == 0
+    for field, bad in (("stop_rule", 3), ("alpha_mode", 2), ("sampler", 2), ("inner_form", 2),
+                       ("wait_limit_ns", -1), ("lanczos_steps", 300), ("estimate", 3)):
+        o = binding.options(**{field: bad})
+        assert lib.ils_setup(ctypes.byref(h), 30, 5, 20, 10, 1, 30, ctypes.byref(o), None) == \
+            binding.ILS_ERR_INVALID_ARG, field
+    for kw in (dict(method=2, alpha_mode=1, alpha_fixed=0), dict(method=2, alpha_mode=1, alpha_fixed=6),
+               dict(method=0, inner_form=1), dict(method=0, sampler=1)):
+        o = binding.options(**kw)
+        assert lib.ils_setup(ctypes.byref(h), 30, 5, 20, 10, 1, 30, ctypes.byref(o), None) == \
+            binding.ILS_ERR_INVALID_ARG, kw
+    assert lib.ils_set_wait_limit(None, 0) == binding.ILS_ERR_INVALID_ARG
+    assert lib.ils_record_picks(None, None, 0) == binding.ILS_ERR_INVALID_ARG
+    assert lib.ils_set_warmstart(None, None) == binding.ILS_ERR_INVALID_ARG

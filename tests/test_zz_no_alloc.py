@@ -50,7 +50,7 @@ def noalloc_gram(ils, X):
     return to_np_colmajor(C)
 
 
-@pytest.mark.parametrize("K,n", [(16000, 500), (3001, 257), (70, 33)])
+@pytest.mark.parametrize("K,n", [(16000, 500), (3001, 257), (70, 33), (20000, 1024)])
 def test_noalloc_gram_matches_regular_path_twice(ils, K, n):
     rng = np.random.default_rng(K + n)
     for call in range(2):
@@ -65,3 +65,16 @@ def test_noalloc_gram_matches_regular_path_twice(ils, K, n):
 def test_noalloc_rejects_sizes_beyond_its_scratch(ils):
     code = ils.lib().ils_gram_noalloc(10, 1025, 1, 10, 1, 1025, None)
     assert code == ils.ILS_ERR_INVALID_ARG
+
+
+def test_noalloc_empty_reduction_gives_zero(ils):
+    """K = 0: X^T X is the n x n zero matrix, written in full (over a NaN-filled C), twice."""
+    import torch
+    for _ in range(2):
+        n = 40
+        C = torch.full((n, n), float("nan"), dtype=torch.float64, device="cuda")
+        stream = torch.cuda.current_stream().cuda_stream
+        code = ils.lib().ils_gram_noalloc(0, n, None, 1, C.data_ptr(), C.stride(0), stream)
+        assert code == ils.ILS_OK
+        torch.cuda.synchronize()
+        assert torch.count_nonzero(C).item() == 0
