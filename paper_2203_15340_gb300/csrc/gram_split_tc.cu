@@ -138,11 +138,14 @@ __device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&v)
 }
 
 struct SplitParams {
-  int n;            // Gram order
+  int n;            // Gram order (columns of X)
+  int n2;           // columns of Y (general product X^T Y); n for the Gram
   int K;            // rows of A (reduction length)
   int n_tiles;      // ceil(n / 128)
+  int n_tiles2;     // ceil(n2 / 128)
   int n_kchunks;
-  const int* exps;  // per-column exponents e_j (device)
+  const int* exps;  // per-column exponents e_j of X (device)
+  const int* exps2; // of Y
   double* partial;  // [tile][product slot][K chunk][128][128] exact products, FP32 bit patterns
   int32_t* err;     // device error flag
 };
@@ -264,8 +267,27 @@ __device__ __forceinline__ void decode_item(int item, const SplitParams& P, int*
   *tile_out = tile + (*bj - r);
 }
 
+// General product X^T Y: item -> (K chunk, tile pair (bi, bj) row-major over n_tiles x
+// n_tiles2, group); every tile pair takes all ordered digit pairs.
+__device__ __forceinline__ void decode_item_gen(int item, const SplitParams& P, int* bi, int* bj, int* g, int* kc,
+                                                int* tile_out) {
+  const int no = num_blocks(false);
+  const int per_chunk = P.n_tiles * P.n_tiles2 * no;
+  *kc = item / per_chunk;
+  const int rest = item % per_chunk;
+  const int tile = rest / no;
+  *g = rest % no;
+  *bi = tile / P.n_tiles2;
+  *bj = tile % P.n_tiles2;
+  *tile_out = tile;
+}
+
+// SYM: the Gram X^T X (upper tile pairs, transposed cross products on diagonal tiles);
+// otherwise X^T Y with X's digits from tmap and Y's from tmap2.
+template <bool SYM>
 __global__ void __launch_bounds__(kThreads, 1)
-gram_split_mma_kernel(const __grid_constant__ CUtensorMap tmap, SplitParams P) {
+gram_split_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmap2,
+                      SplitParams P) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* tiles = smem;  // kStages x (up to kMaxTiles digit tiles)
@@ -277,9 +299,11 @@ gram_split_mma_kernel(const __grid_constant__ CUtensorMap tmap, SplitParams P) {
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int bi, bj, g, kc, tile;
-  decode_item(blockIdx.x, P, &bi, &bj, &g, &kc, &tile);
+  if (SYM) decode_item(blockIdx.x, P, &bi, &bj, &g, &kc, &tile);
+  else decode_item_gen(blockIdx.x, P, &bi, &bj, &g, &kc, &tile);
+  const bool diag = SYM && bi == bj;
   GroupDesc gd;
-  block_desc(bi == bj, g, gd);
+  block_desc(diag, g, gd);
   const int k_begin = kc * kKChunk;
   const int k_end = min(P.K, k_begin + kKChunk);
   const int nk = (k_end - k_begin + kBK - 1) / kBK;
@@ -327,7 +351,9 @@ gram_split_mma_kernel(const __grid_constant__ CUtensorMap tmap, SplitParams P) {
       const int k = k_begin + kb * kBK;
 #pragma unroll
       for (int i = 0; i < kMaxTiles; ++i)
-        if (i < ntiles) tma_load_3d(stage + i * kTileBytes, &tmap, &full[s], k, trow[i], tdig[i]);
+        if (i < ntiles)
+          tma_load_3d(stage + i * kTileBytes, (SYM || gd.side[i] == 0) ? &tmap : &tmap2, &full[s], k, trow[i],
+                      tdig[i]);
       ++issued;
     }
   } else if (warp == 1 && lane == 0) {
@@ -379,7 +405,7 @@ gram_split_mma_kernel(const __grid_constant__ CUtensorMap tmap, SplitParams P) {
         uint32_t* out = part + ((size_t)(tile * nslots + pair_slot(t, u)) * P.n_kchunks + kc) * tile_elems;
         // On a diagonal tile a cross product also stands for (u, t): its transpose goes to
         // that slot, 32 consecutive entries per thread.
-        uint32_t* out_t = (bi == bj && t != u)
+        uint32_t* out_t = (diag && t != u)
                               ? part + ((size_t)(tile * nslots + pair_slot(u, t)) * P.n_kchunks + kc) * tile_elems
                               : nullptr;
 #pragma unroll 1
@@ -436,8 +462,9 @@ __global__ void column_exponent_kernel(int K, int n, const double* __restrict__ 
 // [-16, 15] from the least significant end, the top digit taking the rest (|d_1| <= 32).
 // This equals the digit expansion by repeated rounding to nearest, using integer work
 // only (GB300's FP64 pipe is the scarce unit).
+// Rows r >= sign_split are split negated (J's sign for a product A^T J B).
 __global__ void split_kernel(int K, int n, const double* __restrict__ A, int64_t lda, const int* __restrict__ exps,
-                             __nv_bfloat16* __restrict__ D, int64_t ldk, int32_t* err) {
+                             __nv_bfloat16* __restrict__ D, int64_t ldk, int32_t* err, int sign_split) {
   const int j = blockIdx.y;
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < K; r += gridDim.x * blockDim.x) {
     const long long bits = __double_as_longlong(A[r + (int64_t)j * lda]);
@@ -452,7 +479,7 @@ __global__ void split_kernel(int K, int n, const double* __restrict__ A, int64_t
       if (sh < 64) {
         const unsigned long long half = (sh > 0) ? (1ull << (sh - 1)) : 0ull;
         const unsigned long long mag = (sh > 0) ? ((mant + half) >> sh) : (mant << (-sh));
-        V = (bits < 0) ? -(long long)mag : (long long)mag;
+        V = ((bits < 0) != (r >= sign_split)) ? -(long long)mag : (long long)mag;
       }
     }
 #pragma unroll
@@ -474,7 +501,7 @@ constexpr int kFusePer = 16;
 __global__ void __launch_bounds__(kFuseThreads)
 exponent_split_kernel(int K, int n, const double* __restrict__ A, int64_t lda, int* __restrict__ exps,
                       __nv_bfloat16* __restrict__ D, int64_t ldk, int32_t* err, double* __restrict__ Acopy,
-                      int64_t ldcopy) {
+                      int64_t ldcopy, int sign_split) {
   const int j = blockIdx.x;
   long long bits[kFusePer];
   int mx = 0;
@@ -518,7 +545,7 @@ exponent_split_kernel(int K, int n, const double* __restrict__ A, int64_t lda, i
       if (sh < 64) {
         const unsigned long long half = (sh > 0) ? (1ull << (sh - 1)) : 0ull;
         const unsigned long long mag = (sh > 0) ? ((mant + half) >> sh) : (mant << (-sh));
-        V = (bits[i] < 0) ? -(long long)mag : (long long)mag;
+        V = ((bits[i] < 0) != (r >= sign_split)) ? -(long long)mag : (long long)mag;
       }
     }
 #pragma unroll
@@ -594,6 +621,55 @@ __global__ void split_reduce_kernel(SplitParams P, double* __restrict__ C, int64
   }
 }
 
+// The general product X^T Y (n x n2 output, every tile pair with all 55 ordered digit pairs):
+// the same exact grouping by t + u.  With C0, C = C0 - X^T Y (the FP64 residual
+// bbar - H X of a refinement step); C and C0 may be the same array.
+__global__ void gemm_reduce_kernel(SplitParams P, double* __restrict__ C, int64_t ldc, const double* C0,
+                                   int64_t ldc0) {
+  const int items_per_tile = slots_per_tile() * P.n_kchunks;
+  const int64_t total2 = (int64_t)P.n_tiles * P.n_tiles2 * kBM * kBN / 2;  // pairs of rows
+  const uint32_t* part = reinterpret_cast<const uint32_t*>(P.partial);
+  const size_t tile_elems = (size_t)kBM * kBN;
+  for (int64_t e2 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e2 < total2;
+       e2 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = 2 * e2;
+    const int tile = (int)(e / tile_elems);
+    const int local = (int)(e % tile_elems);
+    const int row = local % kBM, col = local / kBM;
+    const int bi = tile / P.n_tiles2, bj = tile % P.n_tiles2;
+    const int gi = bi * kBM + row, gj = bj * kBN + col;
+    if (gj >= P.n2 || gi >= P.n) continue;
+    const uint32_t* base = part + (size_t)tile * items_per_tile * tile_elems + local;
+    long long V[2][kScales];
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int g = 0; g < kScales; ++g) V[q][g] = 0;
+    for (int kc = 0; kc < P.n_kchunks; ++kc) {
+      int slot = 0;
+#pragma unroll
+      for (int t = 1; t <= kSlices; ++t) {
+#pragma unroll
+        for (int u = 1; u <= kSlices + 1 - t; ++u, ++slot) {
+          const uint2 w = __ldcg(reinterpret_cast<const uint2*>(base + ((size_t)slot * P.n_kchunks + kc) * tile_elems));
+          V[0][t + u - 2] += (long long)__float2int_rz(__uint_as_float(w.x));
+          V[1][t + u - 2] += (long long)__float2int_rz(__uint_as_float(w.y));
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int gq = gi + q;
+      if (gq >= P.n) continue;
+      const int eij = P.exps[gq] + P.exps2[gj];
+      double v = 0.0;
+#pragma unroll
+      for (int g = 0; g < kScales; ++g) v += ldexp((double)V[q][g], eij - kBeta * (g + 2));
+      C[gq + (int64_t)gj * ldc] = C0 ? C0[gq + (int64_t)gj * ldc0] - v : v;
+    }
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   static std::once_flag once;
@@ -625,16 +701,17 @@ GramSplitWork gram_split_work(int64_t K, int64_t n) {
   return w;
 }
 
-cudaError_t gram_split_tc(int64_t K, int64_t n, const double* A, int64_t lda, double* C, int64_t ldc, void* slices,
-                          double* partial, int* exps, int32_t* err, cudaStream_t s, cudaEvent_t mma_begin,
-                          cudaEvent_t mma_end, double* a_copy, int64_t ld_copy, cudaEvent_t copied) {
-  if (n <= 0) return cudaSuccess;
-  if (K <= 0) return cudaMemset2DAsync(C, sizeof(double) * ldc, 0, sizeof(double) * n, n, s);
-  if (K > (int64_t)1 << 30 || n > 65535) return cudaErrorInvalidValue;
-  PFN_cuTensorMapEncodeTiled_v12000 encode = get_encode_fn();
-  if (!encode) return cudaErrorNotSupported;
-  const int64_t ldk = ((K + 7) / 8) * 8;
+namespace {
+
+int64_t slice_ld(int64_t K) { return ((K + 7) / 8) * 8; }
+
+// Digits of the K x n matrix A (rows >= sign_split negated) into slices (kSlices x n x ldk BF16)
+// and the column exponents into exps; with a_copy, A is copied there on the way.
+cudaError_t split_into(int64_t K, int64_t n, const double* A, int64_t lda, int64_t sign_split, void* slices, int* exps,
+                       int32_t* err, cudaStream_t s, double* a_copy = nullptr, int64_t ld_copy = 0) {
+  const int64_t ldk = slice_ld(K);
   __nv_bfloat16* D = static_cast<__nv_bfloat16*>(slices);
+  const int ss = (int)std::min<int64_t>(sign_split, K);
   cudaError_t e;
   if (ldk != K) {  // zero the padding rows so TMA never reads stale values inside ldk
     e = cudaMemsetAsync(D, 0, sizeof(__nv_bfloat16) * (size_t)kSlices * n * ldk, s);
@@ -642,52 +719,117 @@ cudaError_t gram_split_tc(int64_t K, int64_t n, const double* A, int64_t lda, do
   }
   if (K <= (int64_t)kFuseThreads * kFusePer) {
     exponent_split_kernel<<<(unsigned)n, kFuseThreads, 0, s>>>((int)K, (int)n, A, lda, exps, D, ldk, err, a_copy,
-                                                               ld_copy);
+                                                               ld_copy, ss);
     note_launch();
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  } else {
-    if (a_copy && (e = cudaMemcpy2DAsync(a_copy, sizeof(double) * ld_copy, A, sizeof(double) * lda,
-                                         sizeof(double) * K, n, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
-      return e;
-    column_exponent_kernel<<<(unsigned)n, 256, 0, s>>>((int)K, (int)n, A, lda, exps);
-    note_launch();
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    split_kernel<<<dim3((unsigned)std::min<int64_t>((K + 255) / 256, 64), (unsigned)n), 256, 0, s>>>(
-        (int)K, (int)n, A, lda, exps, D, ldk, err);
-    note_launch();
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return cudaGetLastError();
   }
+  if (a_copy && (e = cudaMemcpy2DAsync(a_copy, sizeof(double) * ld_copy, A, sizeof(double) * lda, sizeof(double) * K,
+                                       n, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+    return e;
+  column_exponent_kernel<<<(unsigned)n, 256, 0, s>>>((int)K, (int)n, A, lda, exps);
+  note_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  split_kernel<<<dim3((unsigned)std::min<int64_t>((K + 255) / 256, 64), (unsigned)n), 256, 0, s>>>(
+      (int)K, (int)n, A, lda, exps, D, ldk, err, ss);
+  note_launch();
+  return cudaGetLastError();
+}
 
-  if (copied && (e = cudaEventRecord(copied, s)) != cudaSuccess) return e;
-  CUtensorMap map;
+// TMA map over the slices: (K, n, digit) BF16, 128 x 64 boxes, 128-byte swizzle.
+cudaError_t slices_map(const void* slices, int64_t K, int64_t n, CUtensorMap* map) {
+  PFN_cuTensorMapEncodeTiled_v12000 encode = get_encode_fn();
+  if (!encode) return cudaErrorNotSupported;
+  const int64_t ldk = slice_ld(K);
   const cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)n, (cuuint64_t)kSlices};
   const cuuint64_t strides[2] = {(cuuint64_t)ldk * 2, (cuuint64_t)ldk * 2 * (cuuint64_t)n};
   const cuuint32_t box[3] = {kBK, kBM, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
-  if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, D, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
-      CUDA_SUCCESS)
+  if (encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(slices), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
+  return cudaSuccess;
+}
 
+}  // namespace
+
+cudaError_t gram_split_tc(int64_t K, int64_t n, const double* A, int64_t lda, double* C, int64_t ldc, void* slices,
+                          double* partial, int* exps, int32_t* err, cudaStream_t s, cudaEvent_t mma_begin,
+                          cudaEvent_t mma_end, double* a_copy, int64_t ld_copy, cudaEvent_t copied) {
+  if (n <= 0) return cudaSuccess;
+  if (K <= 0) return cudaMemset2DAsync(C, sizeof(double) * ldc, 0, sizeof(double) * n, n, s);
+  if (K > (int64_t)1 << 30 || n > 65535) return cudaErrorInvalidValue;
+  cudaError_t e = split_into(K, n, A, lda, K, slices, exps, err, s, a_copy, ld_copy);
+  if (e != cudaSuccess) return e;
+  if (copied && (e = cudaEventRecord(copied, s)) != cudaSuccess) return e;
+  CUtensorMap map;
+  if ((e = slices_map(slices, K, n, &map)) != cudaSuccess) return e;
   SplitParams P;
-  P.n = (int)n;
+  P.n = P.n2 = (int)n;
   P.K = (int)K;
-  P.n_tiles = (int)((n + kBM - 1) / kBM);
+  P.n_tiles = P.n_tiles2 = (int)((n + kBM - 1) / kBM);
   P.n_kchunks = (int)std::max<int64_t>(1, (K + kKChunk - 1) / kKChunk);
-  P.exps = exps;
+  P.exps = P.exps2 = exps;
   P.partial = partial;
   P.err = err;
   const int n_upper = P.n_tiles * (P.n_tiles + 1) / 2;
   const int items = (P.n_tiles * num_blocks(true) + (n_upper - P.n_tiles) * num_blocks(false)) * P.n_kchunks;
   const size_t smem = smem_bytes();
-  e = cudaFuncSetAttribute(gram_split_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = cudaFuncSetAttribute(gram_split_mma_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (mma_begin && (e = cudaEventRecord(mma_begin, s)) != cudaSuccess) return e;
-  gram_split_mma_kernel<<<items, kThreads, smem, s>>>(map, P);
+  gram_split_mma_kernel<true><<<items, kThreads, smem, s>>>(map, map, P);
   note_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (mma_end && (e = cudaEventRecord(mma_end, s)) != cudaSuccess) return e;
   split_reduce_kernel<<<1024, 256, 0, s>>>(P, C, ldc);
+  note_launch();
+  return cudaGetLastError();
+}
+
+size_t digit_slice_elems(int64_t K, int64_t n) { return (size_t)kSlices * (size_t)n * (size_t)slice_ld(K); }
+
+size_t gemm_partial_elems(int64_t K, int64_t n1, int64_t n2) {
+  const int64_t t1 = (n1 + kBM - 1) / kBM, t2 = (n2 + kBN - 1) / kBN;
+  const int64_t kc = std::max<int64_t>(1, (K + kKChunk - 1) / kKChunk);
+  return (size_t)(t1 * t2) * slots_per_tile() * kc * kBM * kBN / 2;  // FP32 values in a double buffer
+}
+
+cudaError_t split_digits(int64_t K, int64_t n, const double* A, int64_t lda, int64_t sign_split, void* slices,
+                         int* exps, int32_t* err, cudaStream_t s) {
+  if (n <= 0 || K <= 0) return cudaSuccess;
+  if (K > (int64_t)1 << 30 || n > 65535) return cudaErrorInvalidValue;
+  return split_into(K, n, A, lda, sign_split, slices, exps, err, s);
+}
+
+cudaError_t gemm_split_tc(int64_t K, int64_t n1, int64_t n2, const void* slicesX, const int* expsX,
+                          const void* slicesY, const int* expsY, double* C, int64_t ldc, const double* C0,
+                          int64_t ldc0, double* partial, int32_t* err, cudaStream_t s) {
+  if (n1 <= 0 || n2 <= 0) return cudaSuccess;
+  if (K <= 0 || K > (int64_t)1 << 30 || n1 > 65535 || n2 > 65535) return cudaErrorInvalidValue;
+  CUtensorMap mx, my;
+  cudaError_t e;
+  if ((e = slices_map(slicesX, K, n1, &mx)) != cudaSuccess) return e;
+  if ((e = slices_map(slicesY, K, n2, &my)) != cudaSuccess) return e;
+  SplitParams P;
+  P.n = (int)n1;
+  P.n2 = (int)n2;
+  P.K = (int)K;
+  P.n_tiles = (int)((n1 + kBM - 1) / kBM);
+  P.n_tiles2 = (int)((n2 + kBN - 1) / kBN);
+  P.n_kchunks = (int)std::max<int64_t>(1, (K + kKChunk - 1) / kKChunk);
+  P.exps = expsX;
+  P.exps2 = expsY;
+  P.partial = partial;
+  P.err = err;
+  const int items = P.n_tiles * P.n_tiles2 * num_blocks(false) * P.n_kchunks;
+  const size_t smem = smem_bytes();
+  e = cudaFuncSetAttribute(gram_split_mma_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  gram_split_mma_kernel<false><<<items, kThreads, smem, s>>>(mx, my, P);
+  note_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  gemm_reduce_kernel<<<1024, 256, 0, s>>>(P, C, ldc, C0, ldc0);
   note_launch();
   return cudaGetLastError();
 }

@@ -1488,6 +1488,30 @@ ils_status solve_many_now(ils_handle h, int64_t k, const double* B, int64_t ldb,
     if (st != ILS_OK) agg.status = st;
     return (ils_status)agg.status;
   }
+  if (k >= kWideMinRhs && h->opt.method == ILS_SP && h->opt.precision != ILS_FP64 && !h->mf && !h->sparse) {
+    // Many right-hand sides, mixed precision: the FP64-accurate A^T J B and residuals as split
+    // digit products on the tensor cores, FP32 sweeps (wide_mixed.cu).
+    if (h->opt.stop_rule == ILS_STOP_ERR_BOUND && h->ev_estk) ILS_CK(cudaStreamWaitEvent(h->stream, h->ev_estk, 0));
+    WideMixedArgs wa;
+    wa.m = h->m;
+    wa.n = h->n;
+    wa.p = h->p;
+    wa.A = h->A;
+    wa.H = h->H;
+    wa.P32 = h->P32;
+    wa.Bt32 = h->Bt32;
+    wa.sweeps = h->opt.sweeps > 0 ? h->opt.sweeps : 3;
+    wa.max_outer = h->opt.max_outer;
+    wa.tol2 = tol2_of(h, tol);
+    wa.tol_scale = tol_scale_of(h);
+    WideMixedResult wr;
+    ILS_CK(wide_mixed_solve(wa, k, B, ldb, X, ldx, x0_zero, &wr, h->h_status + 8, h->stream));
+    agg.relres = wr.relres;
+    agg.refinements = wr.refinements;
+    agg.outer_iters = wr.refinements * wa.sweeps;
+    if (wr.status != 0) agg.status = wr.status;
+    return (ils_status)agg.status;
+  }
   for (int64_t c0 = 0; c0 < k; c0 += kMaxRhsPerPass) {
     const int64_t kk = std::min<int64_t>(kMaxRhsPerPass, k - c0);
     ils_status st = sp_pass(h, c0, kk, B + c0 * ldb, ldb, X + c0 * ldx, ldx, x0_zero, tol, &agg);

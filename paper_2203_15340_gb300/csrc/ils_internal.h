@@ -175,6 +175,40 @@ cudaError_t gram_split_tc(int64_t K, int64_t n, const double* A, int64_t lda, do
                           cudaEvent_t mma_begin = nullptr, cudaEvent_t mma_end = nullptr, double* a_copy = nullptr,
                           int64_t ld_copy = 0, cudaEvent_t copied = nullptr);
 
+// General product C = X^T Y (X: K x n1, Y: K x n2) to FP64 accuracy from the same exact digit
+// products, on digit slices made by split_digits (rows >= sign_split of the split matrix are
+// negated: J's sign for A^T J B).  C0 != nullptr gives C = C0 - X^T Y (C may equal C0).
+// partial holds gemm_partial_elems doubles; slices digit_slice_elems BF16 values; err as above.
+size_t digit_slice_elems(int64_t K, int64_t n);
+size_t gemm_partial_elems(int64_t K, int64_t n1, int64_t n2);
+cudaError_t split_digits(int64_t K, int64_t n, const double* A, int64_t lda, int64_t sign_split, void* slices,
+                         int* exps, int32_t* err, cudaStream_t s);
+cudaError_t gemm_split_tc(int64_t K, int64_t n1, int64_t n2, const void* slicesX, const int* expsX,
+                          const void* slicesY, const int* expsY, double* C, int64_t ldc, const double* C0,
+                          int64_t ldc0, double* partial, int32_t* err, cudaStream_t s);
+
+// ---- mixed precision for many right-hand sides (wide_mixed.cu) -----------------------------
+constexpr int64_t kWideMixedBlock = 1024;  // right-hand sides refined together
+struct WideMixedArgs {
+  int64_t m, n, p;
+  const double* A;       // m x n, ld m
+  const double* H;       // A^T J A (FP64)
+  const float* P32;      // Abar1^{-1}
+  const float* Bt32;     // (P Abar2)^T
+  int32_t sweeps;
+  int64_t max_outer;     // refinement cap
+  double tol2;
+  const double* tol_scale;
+};
+struct WideMixedResult {
+  double relres;         // largest relres over the columns
+  int64_t refinements;   // largest number of refinement steps
+  int32_t status;
+};
+// h_state: pinned host memory for 3 int32.  Synchronizes s once per refinement step.
+cudaError_t wide_mixed_solve(const WideMixedArgs& a, int64_t k, const double* B, int64_t ldb, double* X, int64_t ldx,
+                             int x0_zero, WideMixedResult* res, int32_t* h_state, cudaStream_t s);
+
 // ---- matrix-free A_2 products (stream.cu) ---------------------------------------------------
 // Row-major copy of A_2 (q x n, column-major source with leading dimension lda) with rows
 // padded to aq_row_stride(n) elements; prec 0 FP64, 1 FP32, 2 BF16.
@@ -231,6 +265,17 @@ cudaError_t mixed_setup(int64_t n, const double* L, const double* G2, int precis
 cudaError_t mixed_setup_b(int64_t n, const double* G2, int precision, const float* P32, float* G2_32, float* Bt32,
                           void* Bt16, cudaStream_t s);
 cudaError_t mixed_correct(const MixedArgs& a, int precision, cudaStream_t s);
+
+// FP32 GEMM C = alpha op(A) op(B) + beta C (column-major; ta/tb: transposed operand), batched
+// over `batch` with element strides sa, sb, sc (mixed.cu).
+struct GemmF32 {
+  int64_t M, N, K, lda, ldb, ldc, sa, sb, sc;
+  const float* A;
+  const float* B;
+  float* C;
+  float alpha, beta;
+};
+cudaError_t gemm_f32(bool ta, bool tb, const GemmF32& g, int64_t batch, cudaStream_t s);
 
 // ---- explicit SPD inverse (spd_gj.cu) ------------------------------------------------------
 // P[i] := A[i]^{-1} for count (1 or 2) n x n FP32 symmetric matrices (both triangles

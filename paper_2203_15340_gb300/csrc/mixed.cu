@@ -141,13 +141,6 @@ int grid_small(int64_t total) { return (int)std::max<int64_t>(1, std::min<int64_
 // over blockIdx.z with element strides.  64 x 64 tiles, 16-deep K slices in shared
 // memory, a 4 x 4 register tile per thread (two float4 shared-memory loads per 16 FMAs).
 // ---------------------------------------------------------------------------------------
-struct GemmF32 {
-  int64_t M, N, K, lda, ldb, ldc, sa, sb, sc;
-  const float* A;
-  const float* B;
-  float* C;
-  float alpha, beta;
-};
 
 // Shared-memory tiles are [k][64] with the 4-float groups of a row permuted by k (an XOR
 // swizzle): a warp's stores hit 32 different banks whichever operand layout it copies, and

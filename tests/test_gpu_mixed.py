@@ -199,3 +199,83 @@ def test_mixed_largest_n_takes_cholesky_route(ils):
     x, info = run(ils, inst, ils.ILS_FP32_REFINE, tol=1e-12)
     assert info.status == ils.ILS_OK
     assert relerr(x, xs) <= 1e-10
+
+
+# ---------------------------------------------------------------------------------------
+# Many right-hand sides (k >= 32): A^T J B and every residual b - H X as FP64-accurate split
+# digit products on the tensor cores, FP32 sweeps; every column must meet 1e-10.
+# ---------------------------------------------------------------------------------------
+
+def wide_case(ils, inst, k, precision, x0=None, **opt):
+    import torch
+    s = ils.Solver(colmajor(inst.A), inst.p, ils.options(precision=precision, **opt))
+    X = torch.zeros((k, inst.n), dtype=torch.float64, device="cuda")
+    if x0 is not None:
+        X.copy_(torch.from_numpy(np.ascontiguousarray(x0.T)))
+    info = s.solve_many(colmajor(inst.b), X, x0_zero=x0 is None, tol=1e-12)
+    torch.cuda.synchronize()
+    Xg = to_np_colmajor(X)
+    s.close()
+    return Xg, info
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_wide_mixed_ragged_tiles(ils, precision):
+    inst = W.dense_gaussian(900, 200, 70, 0.3, 17, k=40)  # n and k below one 128-wide tile
+    Xg, info = wide_case(ils, inst, 40, precision)
+    Xs = O.normal_equation_solve(inst.A, inst.b, inst.p)
+    assert info.status == ils.ILS_OK and info.relres <= 1e-12 and info.refinements >= 1
+    assert max(relerr(Xg[:, j], Xs[:, j]) for j in range(40)) <= 1e-10
+
+
+def test_wide_mixed_two_blocks_with_start(ils):
+    """1100 right-hand sides (a full 1024-column block and a ragged one), n = 300 (three
+    tiles, the last ragged), half of them started from a given x0."""
+    k = 1100
+    inst = W.dense_gaussian(2600, 400, 300, 0.3, 23, k=k)
+    Xs = O.normal_equation_solve(inst.A, inst.b, inst.p)
+    x0 = Xs + 0.05 * np.random.default_rng(2).standard_normal(Xs.shape)
+    Xg, info = wide_case(ils, inst, k, ils.ILS_BF16_REFINE, x0=x0)
+    assert info.status == ils.ILS_OK and info.relres <= 1e-12
+    errs = [relerr(Xg[:, j], Xs[:, j]) for j in range(k)]
+    assert max(errs) <= 1e-10, max(errs)
+
+
+def test_wide_mixed_error_bound_rule(ils):
+    """kappa_est relres <= 1e-10 for every column: every column's true error is below 1e-10."""
+    inst = W.dense_gaussian(1800, 400, 150, 0.3, 29, k=64)
+    Xg, info = wide_case(ils, inst, 64, ils.ILS_FP32_REFINE, stop_rule=2)
+    Xs = O.normal_equation_solve(inst.A, inst.b, inst.p)
+    assert info.status == ils.ILS_OK and info.err_bound <= 1e-10
+    assert max(relerr(Xg[:, j], Xs[:, j]) for j in range(64)) <= info.err_bound
+
+
+def test_wide_mixed_from_network_start(ils):
+    """The combined form: mixed-precision refinement of 96 parametric right-hand sides from
+    a trained network's x0 meets 1e-10 on every column and needs no more refinements than
+    the cold start."""
+    import torch
+    fam = W.config5_warmstart()
+    n = fam.A.shape[1]
+    plain = ils.Solver(colmajor(fam.A), fam.p, ils.options())
+    th_tr = fam.thetas(2048, seed=5)
+    Xtr = torch.zeros((2048, n), dtype=torch.float64, device="cuda")
+    plain.solve_many(colmajor(fam.rhs(th_tr, seed=5)), Xtr, tol=1e-12)
+    net = ils.WarmStartNet(16, 256, n, seed=1)
+    net.train(torch.from_numpy(th_tr.astype(np.float32)).cuda(), Xtr, epochs=40, batch=256, lr=1e-3)
+    th = fam.thetas(96, seed=55)
+    B = fam.rhs(th, seed=55)
+    s = ils.Solver(colmajor(fam.A), fam.p, ils.options(precision=ils.ILS_BF16_REFINE))
+    Xw = torch.zeros((96, n), dtype=torch.float64, device="cuda")
+    Xc = torch.zeros_like(Xw)
+    iw = net.solve(s, torch.from_numpy(th.astype(np.float32)).cuda(), colmajor(B), Xw, tol=1e-12)
+    ic = s.solve_many(colmajor(B), Xc, tol=1e-12)
+    torch.cuda.synchronize()
+    Xs = O.normal_equation_solve(fam.A, B, fam.p)
+    for X in (Xw, Xc):
+        Xg = to_np_colmajor(X)
+        assert max(relerr(Xg[:, j], Xs[:, j]) for j in range(96)) <= 1e-10
+    assert iw.status == ils.ILS_OK and iw.refinements <= ic.refinements
+    net.close()
+    s.close()
+    plain.close()
