@@ -111,8 +111,10 @@ typedef struct {
   int32_t inner_form;  /* dense SP-RK-RGS: 0 = column form of Alg. 2 (O(p) per step), 1 = Gram form
                           (w = A_1 y carried as g = Abar1 y, h = Abar1 z: O(n) per step, same
                           iterates in exact arithmetic); not in the paper */
-  const char* tune_cache; /* [host] file that keeps the autotuner's choices between processes
-                          (read at the first setup, rewritten after each new tuning), or NULL */
+  const char* tune_cache; /* [host] file that keeps the sweep autotuner's choices between
+                          processes: read at each mixed-precision setup (entries tuned on another
+                          GPU model are ignored), rewritten after each new tuning; NULL = none.
+                          The path is copied at setup */
   int64_t wait_limit_ns; /* bound in nanoseconds on each grid-barrier wait of the one-launch
                           mixed-precision solve; 0 = 1 s (the setup kernels keep their own 1-4 s
                           bounds).  A wait that runs out ends the kernel and the solve returns

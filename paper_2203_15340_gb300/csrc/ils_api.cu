@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "ils_internal.h"
@@ -62,6 +63,7 @@ struct ils_handle_s {
   double* h_est = nullptr;
   float* lz_work = nullptr;      // matrix-free Lanczos vectors
   ils_mlp warm_net = nullptr;    // ils_set_warmstart (not owned)
+  std::string tune_cache;        // options.tune_cache, copied at setup
   // overlapped setup with estimates: kappa(H) and rho on a fourth stream beside the inverse
   cudaStream_t s_est = nullptr;
   cudaEvent_t ev_p = nullptr, ev_estk = nullptr, ev_est = nullptr;  // P formed; kappa ready; all ready
@@ -739,7 +741,7 @@ ils_status setup_finish(ils_handle h) {
 ils_status tune_handle(ils_handle h) {
   if (h->opt.precision == ILS_FP64 || h->opt.method != ILS_SP) return ILS_OK;
   ILS_CK(tune_sweeps(h->n, h->opt.precision, h->P32, h->mf ? nullptr : h->Bt32, h->Bt16, h->r32, h->d32a, h->st,
-                     h->stream));
+                     h->stream, h->tune_cache.empty() ? nullptr : h->tune_cache.c_str()));
   return ILS_OK;
 }
 
@@ -1209,6 +1211,8 @@ ils_status create_handle(ils_handle* out, int64_t m, int64_t n, int64_t p, int64
   h->p = p;
   h->q = q;
   h->opt = opt;
+  if (opt.tune_cache) h->tune_cache = opt.tune_cache;
+  h->opt.tune_cache = nullptr;  // the handle keeps its own copy of the path
   h->mf = mf;
   h->sparse = sparse;
   h->nnz = sparse ? sparse_nnz : 0;

@@ -251,8 +251,10 @@ struct SweepShape {
 SweepShape sweep_shape(int64_t n, int64_t k, bool bf16);
 // Time the candidate shapes for (n, k) on the handle's operators (P32 and Bt32 or Bt16) and
 // cache the fastest, once per process.  Synchronizes `s`; not for use inside a capture.
+// cache: a file keeping the choices between processes (read first, rewritten after new tuning), or null.
 cudaError_t tune_sweeps(int64_t n, int precision, const float* P32, const float* Bt32, const void* Bt16,
-                        float* scratch_in, float* scratch_out, SolveState* st, cudaStream_t s);
+                        float* scratch_in, float* scratch_out, SolveState* st, cudaStream_t s,
+                        const char* cache = nullptr);
 // 1 and the tuned shape of (n, k, operator type) if the autotuner has one, else 0.
 int ils_tuned_shape_impl(int64_t n, int64_t k, int bf16, int* warps, int* blocks);
 // L32/P32/G2_32/Bt32 are n x n FP32 buffers, Bt16 an n x n BF16 buffer (BF16 mode only).

@@ -13,7 +13,9 @@
 
 #include <algorithm>
 
+#include <cstdio>
 #include <map>
+#include <string>
 #include <mutex>
 
 #include "ils_internal.h"
@@ -450,6 +452,62 @@ cudaError_t time_shape(const MixedArgs& a, SweepShape sh, const TM* M, const flo
 }
 }  // namespace
 
+// The autotuner's choices kept in a text file between processes: a header line naming the
+// GPU (model and SM count; a file from another GPU is ignored) and one line per key,
+// "nb k_class bf16 warps blocks".
+std::string tune_device_tag() {
+  int dev = 0;
+  cudaDeviceProp prop{};
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return "";
+  }
+  std::string name(prop.name);
+  for (char& c : name)
+    if (c == ' ' || c == '\n') c = '_';
+  return "ils-sweep-tune-v1 " + std::to_string(prop.multiProcessorCount) + " " + name;
+}
+
+void load_tune_cache(const char* path) {
+  if (!path || !*path) return;
+  std::FILE* f = std::fopen(path, "r");
+  if (!f) return;
+  char line[512];
+  const std::string tag = tune_device_tag();
+  if (!std::fgets(line, sizeof(line), f) || tag.empty() || std::string(line).rfind(tag, 0) != 0) {
+    std::fclose(f);
+    return;
+  }
+  long long nb;
+  int kc, bf, w, b;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  while (std::fscanf(f, "%lld %d %d %d %d", &nb, &kc, &bf, &w, &b) == 5) {
+    if (nb < 1 || (kc != 1 && kc != 8) || (bf != 0 && bf != 1) || (w != 1 && w != 2 && w != 4 && w != 8) || b < 1)
+      continue;  // a damaged line is ignored
+    g_tune.emplace(TuneKey{nb, kc, bf}, SweepShape{w, b});
+  }
+  std::fclose(f);
+}
+
+void save_tune_cache(const char* path) {
+  if (!path || !*path) return;
+  const std::string tag = tune_device_tag();
+  if (tag.empty()) return;
+  const std::string tmp = std::string(path) + ".tmp";
+  std::FILE* f = std::fopen(tmp.c_str(), "w");
+  if (!f) return;
+  std::fprintf(f, "%s\n", tag.c_str());
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (const auto& kv : g_tune)
+      std::fprintf(f, "%lld %d %d %d %d\n", (long long)kv.first.nb, kv.first.kc, kv.first.bf16, kv.second.warps,
+                   kv.second.blocks);
+  }
+  const bool ok = std::fclose(f) == 0;
+  if (ok) std::rename(tmp.c_str(), path);
+  else std::remove(tmp.c_str());
+}
+
 SweepShape sweep_shape(int64_t n, int64_t k, bool bf16) {
   std::lock_guard<std::mutex> lock(g_tune_mu);
   auto it = g_tune.find(tune_key(n, k, bf16));
@@ -457,7 +515,8 @@ SweepShape sweep_shape(int64_t n, int64_t k, bool bf16) {
 }
 
 cudaError_t tune_sweeps(int64_t n, int precision, const float* P32, const float* Bt32, const void* Bt16,
-                        float* scratch_in, float* scratch_out, SolveState* st, cudaStream_t s) {
+                        float* scratch_in, float* scratch_out, SolveState* st, cudaStream_t s, const char* cache) {
+  load_tune_cache(cache);
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     bool all = g_tune.count(tune_key(n, 1, false)) && g_tune.count(tune_key(n, 8, false));
@@ -501,6 +560,7 @@ cudaError_t tune_sweeps(int64_t n, int precision, const float* P32, const float*
       g_tune[key] = best;
     }
   }
+  save_tune_cache(cache);
   return cudaSuccess;
 }
 

@@ -279,3 +279,24 @@ def test_wide_mixed_from_network_start(ils):
     net.close()
     s.close()
     plain.close()
+
+
+def test_tune_cache_file(ils, tmp_path):
+    """options.tune_cache: the sweep shapes tuned at setup are written to the file (a header
+    naming the GPU, then one line per tuned key), and the handle solves as before."""
+    import torch
+    path = tmp_path / "sweep_tune.txt"
+    inst = W.dense_gaussian(1500, 300, 190, 0.3, 91)
+    s = ils.Solver(colmajor(inst.A), inst.p, ils.options(precision=ils.ILS_FP32_REFINE, tune_cache=str(path)))
+    lines = path.read_text().splitlines()
+    assert lines[0].startswith("ils-sweep-tune-v1 ")
+    keys = {tuple(int(v) for v in ln.split()[:3]) for ln in lines[1:]}
+    assert ((190 + 31) // 32, 1, 0) in keys and ((190 + 31) // 32, 8, 0) in keys
+    for ln in lines[1:]:
+        nb, kc, bf, w, b = (int(v) for v in ln.split())
+        assert w in (1, 2, 4, 8) and b >= 1
+    x = vec(np.zeros(inst.n))
+    info = s.solve(vec(inst.b), x, tol=1e-12)
+    torch.cuda.synchronize()
+    assert info.status == ils.ILS_OK and relerr(x.cpu().numpy(), O.qr_cholesky_solve(inst.A, inst.b, inst.p)) <= 1e-10
+    s.close()
