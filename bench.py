@@ -73,7 +73,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="bound on the CPU oracle sample")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the sparse, batched and warm-start measurements")
-    ap.add_argument("--only", choices=["stream", "sparse", "batched", "warm"],
+    ap.add_argument("--only", choices=["stream", "sparse", "batched", "warm", "paper"],
                     help="print only one secondary measurement (for profiling runs): the matrix-free stream on "
                          "the tall 278144 x 500 instance, or the sparse, batched or warm-start configuration")
     return ap.parse_args()
@@ -463,6 +463,57 @@ def measure_warm(ils, torch, np, dev, n_train=50000, n_eval=2048, epochs=40):
             "checked_rhs": n_eval}
 
 
+def measure_paper(ils, torch, np, dev):
+    """Paper-shape replay (Sec. 5.2, Tables 2-5): A_1 = rand(p, n), A_2 = d eye(q, n), b = rand,
+    x0 = 0, stop at RR = relres^2 < 1e-6, at reduced p with each table's p/n ratio and d
+    scaled to keep rho at its paper-size value.  Each case times one complete setup + solve
+    (CUDA events) for SP, SP-RK-RGS and SP-SCD in FP64 and checks RR on the host."""
+    import math
+    import workloads
+
+    def edge(p, n):
+        return p / 12.0 * (1.0 - math.sqrt(n / p)) ** 2
+
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_tables.json")))
+    paper_s = {2: {"SP": 559.3, "SP_RK_RGS": 514.6313, "SP_SCD": 227.7141},
+               4: {"SP": 566.9453, "SP_RK_RGS": 466.9094, "SP_SCD": 198.2734}}
+    out = {"note": "paper: MATLAB on an i7-9700 at p = 30000 (Table 2) / 50000 (Table 4), n = 13000; context only",
+           "cases": []}
+    for p in (5000, 10000):
+        for table in (2, 4):
+            p_ref = 30000 if table == 2 else 50000
+            n = int(round(p * 13000 / p_ref))
+            q = n if table == 2 else 1
+            d = 7.0 * math.sqrt(edge(p, n) / edge(p_ref, 13000))
+            inst = workloads.paper_table_workload(p, q, n, seed=table, diag=d)
+            At = torch.from_numpy(np.ascontiguousarray(inst.A.T)).to(dev)
+            b = torch.from_numpy(inst.b).to(dev)
+            A1, A2 = inst.A[:p], inst.A[p:]
+            bb = A1.T @ inst.b[:p] - A2.T @ inst.b[p:]
+            row = {"table": table, "p": p, "q": q, "n": n, "diag": round(d, 4)}
+            for name, kw in (("SP", dict(method=ils.ILS_SP)),
+                             ("SP_RK_RGS", dict(method=ils.ILS_SP_RK_RGS, theta=1e-3, seed=table)),
+                             ("SP_SCD", dict(method=ils.ILS_SP_SCD, theta=1e-3, seed=table))):
+                x = torch.zeros(n, dtype=torch.float64, device=dev)
+                opts = ils.options(stop_rule=ils.ILS_STOP_PAPER_RR, max_outer=gold["max_outer"], **kw)
+                e0, e1 = _events(torch)
+                torch.cuda.synchronize()
+                e0.record()
+                s = ils.Solver(At, p, opts)
+                info = s.solve(b, x, tol=gold["stop_rr"])
+                e1.record()
+                torch.cuda.synchronize()
+                xv = x.cpu().numpy()
+                r = A1.T @ (inst.b[:p] - A1 @ xv) - A2.T @ (inst.b[p:] - A2 @ xv)
+                rr = float(np.dot(r, r) / np.dot(bb, bb))
+                row[name] = {"seconds": e0.elapsed_time(e1) / 1e3, "IT": info.outer_iters,
+                             "inner_steps": info.inner_iters, "RR": rr, "RR_ok": rr < gold["stop_rr"],
+                             "paper_seconds_full_size": paper_s[table][name]}
+                s.close()
+            out["cases"].append(row)
+    return out
+
+
 def run_reference(args, rank, world):
     """Reference arm: the CPU oracle on the host cores (rank 0 only)."""
     if rank != 0:
@@ -509,7 +560,8 @@ def main():
         fn = {"stream": lambda: measure_stream(ils, torch, np, dev, reps=5),
               "sparse": lambda: measure_sparse(ils, torch, np, dev),
               "batched": lambda: measure_batched(ils, torch, np, dev),
-              "warm": lambda: measure_warm(ils, torch, np, dev)}[args.only]
+              "warm": lambda: measure_warm(ils, torch, np, dev),
+              "paper": lambda: measure_paper(ils, torch, np, dev)}[args.only]
         print(json.dumps(fn()), flush=True)
         return
     if world > 1:
