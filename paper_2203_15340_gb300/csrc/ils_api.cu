@@ -1247,7 +1247,11 @@ ils_status create_handle(ils_handle* out, int64_t m, int64_t n, int64_t p, int64
     for (cudaEvent_t* e : {&h->ev_start, &h->ev_g2, &h->ev_g1, &h->ev_hd, &h->ev_h, &h->ev_acopy, &h->ev_rhs})
       ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
     if (h->opt.estimate) {
-      ok = ok && cudaStreamCreateWithFlags(&h->s_est, cudaStreamNonBlocking) == cudaSuccess;
+      // The estimate's cluster becomes ready together with the cooperative inverse; the
+      // highest stream priority lets the block scheduler place it first.
+      int lo_prio = 0, hi_prio = 0;
+      ok = ok && cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio) == cudaSuccess;
+      ok = ok && cudaStreamCreateWithPriority(&h->s_est, cudaStreamNonBlocking, hi_prio) == cudaSuccess;
       for (cudaEvent_t* e : {&h->ev_p, &h->ev_estk, &h->ev_est})
         ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
     }
