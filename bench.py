@@ -40,7 +40,7 @@ FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (FMA pipe) rate from the profiling
 FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
 # of each kernel as it stands, on the headline step; None once a kernel changes.
-MMA_TRAFFIC_BYTES = 160_487_936 + 9_351_424
+MMA_TRAFFIC_BYTES = 160_445_440 + 8_962_816
 GJ_TRAFFIC_BYTES = 693_504 + 0
 
 
