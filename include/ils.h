@@ -90,7 +90,10 @@ typedef struct {
   int32_t sweeps;      /* mixed precision: SP sweeps per FP64 refinement step; 0 = 3 */
   uint64_t seed;       /* Philox4x32-10 key for the randomized methods */
   int32_t route;       /* SP only: 0 auto, 1 explicit B = P Abar2, 2 matrix-free (stream A_2 every
-                          step, never form Abar2; n <= 512).  Auto picks matrix-free when q > 32 n. */
+                          step, never form Abar2; n <= 512).  Auto takes the route with the lower
+                          modelled cost, setup + expected streams, from rates measured once per
+                          process (the first auto setup of a process synchronizes and runs about a
+                          millisecond of calibration kernels on synthetic data; see ils_route_model). */
   int32_t chain_ctas;  /* SP-RK-RGS on a sparse A: CTAs per inner chain.  0 = auto (the smallest
                           thread-block cluster of 1, 2, 4 or 8 CTAs whose shared memory holds
                           w and e, else one CTA with w and e in global memory); 1, 2, 4, 8 =
@@ -416,6 +419,16 @@ ils_status ils_gram_noalloc(int64_t K, int64_t n, const double* X, int64_t ldx, 
  * route; the low-precision copy in the matching mixed precision).  For tests and
  * bandwidth measurements.  Errors: INVALID_ARG, CUDA. */
 ils_status ils_aq_product(ils_handle h, const double* x, double* v, int prec, ils_stream_t stream);
+
+/* The last automatic route decision (options.route = auto) of this process, host only.  out
+ * receives min(count, 9) values: the modelled extra cost of the explicit route and of the
+ * matrix-free route in seconds (explicit: Abar2 = A_2^T A_2 by the Gram route of the
+ * handle's precision plus B = P Abar2; matrix-free: the row-major copies of A_2 plus the
+ * expected streams of a solve), the measured split-digit Gram rate and FP64 Gram rate (flop/s
+ * in p n^2 units), the measured stream rates of the FP64, FP32 and BF16 copies (bytes/s), the
+ * copy rate (bytes/s), and 1 if the matrix-free route was taken.  The paper has no
+ * counterpart (its SP forms B).  Returns the number of values written, -1 on a bad argument. */
+int ils_route_model(double* out, int count);
 
 /* Change options.wait_limit_ns of an existing handle (0 restores the default).  Host only.
  * Errors: INVALID_ARG. */

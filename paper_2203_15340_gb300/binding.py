@@ -143,6 +143,7 @@ SIGNATURES = {
     "ils_mlp_destroy": (None, [_P]),
     "ils_set_warmstart": (ctypes.c_int, [_P, _P]),
     "ils_gram_noalloc": (ctypes.c_int, [_I64, _I64, _P, _I64, _P, _I64, _P]),
+    "ils_route_model": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
     "ils_set_wait_limit": (ctypes.c_int, [_P, _I64]),
     "ils_record_picks": (ctypes.c_int, [_P, _P, _I64]),
     "ils_destroy": (None, [_P]),
@@ -181,6 +182,15 @@ def tuned_shape(n: int, k: int, bf16: bool = False):
     if lib().ils_tuned_shape(n, k, int(bool(bf16)), ctypes.byref(w), ctypes.byref(b)):
         return w.value, b.value
     return None
+
+
+def route_model():
+    """The last automatic route decision: dict of modelled costs, measured rates and the choice."""
+    buf = (ctypes.c_double * 9)()
+    n = lib().ils_route_model(buf, 9)
+    keys = ["explicit_s", "matrix_free_s", "gram_split_flops", "gram_f64_flops", "bw_fp64", "bw_fp32", "bw_bf16",
+            "copy_Bps", "matrix_free"]
+    return {k: buf[i] for i, k in enumerate(keys[:max(n, 0)])}
 
 
 def status_string(code: int) -> str:

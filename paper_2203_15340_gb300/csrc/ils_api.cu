@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -146,6 +147,8 @@ void handle_set_warm_net(ils_handle h, ils_mlp net) { h->warm_net = net; }
 }  // namespace ils
 
 namespace ils {
+std::mutex g_route_mu;
+double g_route_model[9] = {};  // the last automatic route decision (ils_route_model)
 thread_local char g_last_error[256] = "";
 
 ils_status record_cuda_error(cudaError_t e, const char* what, int line) {
@@ -1201,8 +1204,19 @@ ils_status create_handle(ils_handle* out, int64_t m, int64_t n, int64_t p, int64
   if (opt.route == ILS_ROUTE_MATRIX_FREE) {
     if (opt.method != ILS_SP || n > 512 || q < 1) return ILS_ERR_INVALID_ARG;
     mf = true;
-  } else if (opt.route == ILS_ROUTE_AUTO) {
-    mf = opt.method == ILS_SP && n <= 512 && q > 32 * n;
+  } else if (opt.route == ILS_ROUTE_AUTO && opt.method == ILS_SP && n <= 512 && q > 0 && !sparse) {
+    // The route that minimises setup + expected iterations by measured rates (route_tune.cu).
+    bool pick = false;
+    double model[8];
+    if (route_prefers_matrix_free(q, n, opt.precision, &pick, model) == cudaSuccess) {
+      mf = pick;
+      std::lock_guard<std::mutex> lock(g_route_mu);
+      std::memcpy(g_route_model, model, sizeof(model));
+      g_route_model[8] = pick ? 1.0 : 0.0;
+    } else {
+      cudaGetLastError();
+      mf = q > 32 * n;  // no measurement possible: the size rule
+    }
   }
   ils_handle h = new (std::nothrow) ils_handle_s();
   if (!h) return ILS_ERR_OOM;
@@ -1567,6 +1581,14 @@ ils_status ils_get_matrix(ils_handle h, int which, double* dst, int64_t ldd, ils
   ILS_CK(cudaMemcpy2DAsync(dst, sizeof(double) * ldd, src, sizeof(double) * n, sizeof(double) * n, n,
                            cudaMemcpyDeviceToDevice, s));
   return ILS_OK;
+}
+
+int ils_route_model(double* out, int count) {
+  if (!out || count < 0) return -1;
+  std::lock_guard<std::mutex> lock(ils::g_route_mu);
+  const int c = count < 9 ? count : 9;
+  for (int i = 0; i < c; ++i) out[i] = ils::g_route_model[i];
+  return c;
 }
 
 ils_status ils_set_wait_limit(ils_handle h, int64_t limit_ns) {

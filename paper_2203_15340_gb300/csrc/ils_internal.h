@@ -367,6 +367,13 @@ int rkrgs_cluster_plan(int64_t n, int64_t p, bool fp32, int want, double col_ent
 cudaError_t sparse_chain_prep(int64_t n, SparseCols sc, const double* G1, const double* norms2, bool fp32,
                               cudaStream_t s);
 
+// ---- route choice (route_tune.cu) ------------------------------------------------------------
+// Matrix-free or explicit for an SP problem with q rows of A_2 and n columns, by the cost
+// model of route_tune.cu with rates measured once per process (synchronizes on first use).
+// model (host, may be null) receives 8 values: the explicit and matrix-free costs in seconds,
+// the split and FP64 Gram rates (flop/s), the FP64/FP32/BF16 stream rates and the copy rate (B/s).
+cudaError_t route_prefers_matrix_free(int64_t q, int64_t n, int precision, bool* mf, double* model);
+
 // ---- Lanczos estimates (lanczos.cu) -----------------------------------------------------------
 // Extreme eigenvalues of C = M2 M1 in the M1 inner product (M1 == nullptr: standard Lanczos on
 // the symmetric M2).  M2, M1: n x n symmetric, FP64 (f64 != 0) or FP32.  out (device):

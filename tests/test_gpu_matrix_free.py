@@ -67,17 +67,18 @@ def test_matrix_free_solves(ils, precision):
 
 
 def test_auto_route_choice(ils):
+    """An auto-route handle has the A_2 stream exactly when the autotuner chose matrix-free."""
     import torch
-    tall = W.dense_gaussian(400, 40 * 12 + 1, 12, 0.05, 5)
-    s = ils.Solver(colmajor(tall.A), tall.p)  # q > 32 n: matrix-free
-    v = torch.empty(12, dtype=torch.float64, device="cuda")
-    s.aq_product(vec(np.ones(12)), v)
-    s.close()
-    short = W.config1()  # q = 2 n: explicit
-    s = ils.Solver(colmajor(short.A), short.p)
-    with pytest.raises(ils.ILSError):
-        s.aq_product(vec(np.ones(short.n)), torch.empty(short.n, dtype=torch.float64, device="cuda"))
-    s.close()
+    for inst in (W.dense_gaussian(400, 40 * 12 + 1, 12, 0.05, 5), W.config1()):
+        s = ils.Solver(colmajor(inst.A), inst.p)
+        mf = ils.binding.route_model()["matrix_free"] == 1.0
+        v = torch.empty(inst.n, dtype=torch.float64, device="cuda")
+        if mf:
+            s.aq_product(vec(np.ones(inst.n)), v)
+        else:
+            with pytest.raises(ils.ILSError):
+                s.aq_product(vec(np.ones(inst.n)), v)
+        s.close()
 
 
 def test_tall_bandwidth_configuration(ils):
@@ -89,3 +90,27 @@ def test_tall_bandwidth_configuration(ils):
     info = s.solve(vec(inst.b), x, tol=1e-12)
     assert info.status == ils.ILS_OK and relerr(x.cpu().numpy(), xs) <= 1e-10
     s.close()
+
+
+def test_route_autotuner_model(ils):
+    """route = auto takes the route with the lower modelled cost from measured rates: the
+    reported model is consistent with the choice, the rates are positive, config 2 (q = 4000,
+    n = 500) in mixed precision stays explicit (in FP64 its A_2^T A_2 on the FP64 pipe costs
+    more than streaming A_2), and every choice solves to 1e-10."""
+    import torch
+    import workloads as W2
+    for inst, expect_mf in ((W2.config2(), False), (W2.dense_gaussian(2000, 60000, 64, 0.05, 44), None)):
+        for prec in (0, 2):
+            s = ils.Solver(colmajor(inst.A), inst.p, ils.options(precision=prec))
+            m = ils.binding.route_model()
+            assert m["explicit_s"] > 0 and m["matrix_free_s"] > 0
+            assert all(m[k] > 0 for k in ("gram_split_flops", "gram_f64_flops", "bw_fp64", "bw_fp32", "bw_bf16"))
+            assert m["matrix_free"] == (1.0 if m["matrix_free_s"] < m["explicit_s"] else 0.0)
+            if expect_mf is not None and prec != 0:  # mixed: the split Gram makes Abar2 cheap
+                assert m["matrix_free"] == (1.0 if expect_mf else 0.0), (prec, m)
+            x = torch.zeros(inst.n, dtype=torch.float64, device="cuda")
+            info = s.solve(torch.from_numpy(inst.b).cuda(), x, tol=1e-12)
+            torch.cuda.synchronize()
+            xs = O.qr_cholesky_solve(inst.A, inst.b, inst.p)
+            assert info.status == ils.ILS_OK and relerr(x.cpu().numpy(), xs) <= 1e-10
+            s.close()
