@@ -250,8 +250,9 @@ ils_status ils_solve_many(ils_handle h, int64_t k, const double* B, int64_t ldb,
  * leading dimension ldd >= n): which = 0 Abar1, 1 Abar2, 2 FP64 Cholesky factor L of
  * Abar1 (lower triangle; the strict upper triangle of dst is set to 0; formed on demand,
  * synchronizing the handle's stream, where the setup factored Abar1 in FP32 only), 3 P = Abar1^{-1},
- * 4 B = P Abar2.  P and B are formed only by FP64 SP handles (B only on the explicit
- * route); asking another handle for them is INVALID_ARG.  For tests and diagnostics.
+ * 4 B = P Abar2.  P and B are formed only by FP64 SP handles; Abar2 and B only on the
+ * explicit route (a matrix-free handle streams A_2 instead); asking a handle for a matrix it
+ * does not form is INVALID_ARG.  For tests and diagnostics.
  * Errors: INVALID_ARG, CUDA. */
 ils_status ils_get_matrix(ils_handle h, int which, double* dst, int64_t ldd, ils_stream_t stream);
 

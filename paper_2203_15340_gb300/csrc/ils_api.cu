@@ -1208,7 +1208,9 @@ ils_status create_handle(ils_handle* out, int64_t m, int64_t n, int64_t p, int64
     // The route that minimises setup + expected iterations by measured rates (route_tune.cu).
     bool pick = false;
     double model[8];
-    if (route_prefers_matrix_free(q, n, opt.precision, &pick, model) == cudaSuccess) {
+    const bool split = opt.gram == ILS_GRAM_SPLIT || opt.precision != ILS_FP64;
+    const int est_steps = opt.estimate ? (opt.lanczos_steps > 0 ? opt.lanczos_steps : 24) : 0;
+    if (route_prefers_matrix_free(q, n, opt.precision, split, est_steps, &pick, model) == cudaSuccess) {
       mf = pick;
       std::lock_guard<std::mutex> lock(g_route_mu);
       std::memcpy(g_route_model, model, sizeof(model));
@@ -1555,7 +1557,7 @@ ils_status ils_get_matrix(ils_handle h, int which, double* dst, int64_t ldd, ils
   if (!h || !dst || ldd < h->n || which < 0 || which > 4) return ILS_ERR_INVALID_ARG;
   // P exists for FP64 SP handles, B for those on the explicit route
   if (which >= 3 && (h->opt.method != ILS_SP || h->opt.precision != ILS_FP64)) return ILS_ERR_INVALID_ARG;
-  if (which == 4 && h->mf) return ILS_ERR_INVALID_ARG;
+  if ((which == 1 || which == 4) && h->mf) return ILS_ERR_INVALID_ARG;  // never formed there
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t n = h->n;
   const double* src = nullptr;

@@ -372,7 +372,8 @@ cudaError_t sparse_chain_prep(int64_t n, SparseCols sc, const double* G1, const 
 // model of route_tune.cu with rates measured once per process (synchronizes on first use).
 // model (host, may be null) receives 8 values: the explicit and matrix-free costs in seconds,
 // the split and FP64 Gram rates (flop/s), the FP64/FP32/BF16 stream rates and the copy rate (B/s).
-cudaError_t route_prefers_matrix_free(int64_t q, int64_t n, int precision, bool* mf, double* model);
+cudaError_t route_prefers_matrix_free(int64_t q, int64_t n, int precision, bool split_gram, int estimate_steps,
+                                      bool* mf, double* model);
 
 // ---- Lanczos estimates (lanczos.cu) -----------------------------------------------------------
 // Extreme eigenvalues of C = M2 M1 in the M1 inner product (M1 == nullptr: standard Lanczos on

@@ -4,7 +4,8 @@
 //   explicit:    q n^2 / R_gram + 2 n^3 / R_f32                        (Abar2 and B)
 //   matrix-free: q n (8 + s) / R_copy + T_lo (a_s + q n s / BW_s) + T_64 (a_8 + q n 8 / BW_8)
 // with s the bytes of the low-precision copy (0 in FP64), T_lo and T_64 the expected number
-// of low-precision and FP64 streams of a solve, and the rates measured once per process on
+// of low-precision and FP64 streams of a solve (plus one stream per Lanczos step when the
+// handle estimates kappa and rho), and the rates measured once per process on
 // synthetic inputs of a fixed size (split or FP64 Gram throughput in the method's flops;
 // each copy's stream timed at two sizes, giving its bandwidth and its fixed cost a per stream).  n^2-sized per-step work is common to both and left out.
 #include <algorithm>
@@ -128,7 +129,8 @@ done:
 
 }  // namespace
 
-cudaError_t route_prefers_matrix_free(int64_t q, int64_t n, int precision, bool* mf, double* model) {
+cudaError_t route_prefers_matrix_free(int64_t q, int64_t n, int precision, bool split_gram, int estimate_steps,
+                                      bool* mf, double* model) {
   Rates r;
   {
     std::lock_guard<std::mutex> lock(g_rates_mu);
@@ -144,13 +146,18 @@ cudaError_t route_prefers_matrix_free(int64_t q, int64_t n, int precision, bool*
   // four FP64 residuals; FP64 SP about twelve iterations, each with one FP64 stream.
   const double t_lo = precision == ILS_FP64 ? 0.0 : 9.0;
   const double t_64 = precision == ILS_FP64 ? 12.0 : 4.0;
-  const double gram = precision == ILS_FP64 ? r.gram_f64 : r.gram_split;
+  const double gram = (precision == ILS_FP64 && !split_gram) ? r.gram_f64 : r.gram_split;
   const double f32_rate = 20e12;  // B = P Abar2 by the FP32 GEMM
   const double qd = (double)q, nd = (double)n;
   const double explicit_cost = qd * nd * nd / gram + 2.0 * nd * nd * nd / f32_rate;
+  // With estimates the matrix-free route streams A_2 once per Lanczos step (the explicit
+  // route's Lanczos works on n x n operators held on chip beside the setup).
+  const int est_prec = precision == ILS_FP64 ? 0 : lo;
+  const double est_bytes = precision == ILS_FP64 ? 8.0 : s_lo;
   const double mf_cost = qd * nd * (8.0 + s_lo) / r.copy +
                          (t_lo > 0.0 ? t_lo * (r.lat[lo] + qd * nd * s_lo / r.bw[lo]) : 0.0) +
-                         t_64 * (r.lat[0] + qd * nd * 8.0 / r.bw[0]);
+                         t_64 * (r.lat[0] + qd * nd * 8.0 / r.bw[0]) +
+                         estimate_steps * (r.lat[est_prec] + qd * nd * est_bytes / r.bw[est_prec]);
   *mf = n <= 512 && mf_cost < explicit_cost;
   if (model) {
     model[0] = explicit_cost;

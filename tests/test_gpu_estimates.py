@@ -53,7 +53,7 @@ def solve(ils, inst, opts, tol, **kw):
 
 
 @pytest.mark.parametrize("opts", [
-    dict(),                                     # FP64 SP, explicit route
+    dict(route=1),                              # FP64 SP, explicit route
     dict(precision=2),                          # mixed, overlapped setup (the headline path)
     dict(precision=1, factor64=1),              # mixed with the FP64 factorization
     dict(method=2),                             # SP-SCD: kappa only (P is never formed)

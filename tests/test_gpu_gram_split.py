@@ -34,7 +34,7 @@ def test_split_gram_meets_fp64_bound(ils, p, q, n):
     import torch
     s_ = 0.3 * min(1.0, (p ** 0.5 - n ** 0.5) / (q ** 0.5 + n ** 0.5))
     inst = W.dense_gaussian(p, q, n, s_, 7000 + n)
-    s = ils.Solver(colmajor(inst.A), p, ils.options(gram=ils.ILS_GRAM_SPLIT))
+    s = ils.Solver(colmajor(inst.A), p, ils.options(gram=ils.ILS_GRAM_SPLIT, route=ils.ILS_ROUTE_EXPLICIT))
     out = torch.empty((n, n), dtype=torch.float64, device="cuda")
     A1, A2 = inst.A[:p], inst.A[p:]
     G1o, G2o = O.gram_blocks(inst.A, p)

@@ -57,6 +57,9 @@ def test_matrix_free_solves(ils, precision):
     x = vec(np.zeros(n))
     info = s.solve(vec(inst.b), x, tol=1e-12)
     assert info.status == ils.ILS_OK and relerr(x.cpu().numpy(), xs) <= 1e-10
+    import torch
+    with pytest.raises(ils.ILSError):  # Abar2 is never formed on this route
+        s.get_matrix(ils.MAT_GRAM2, torch.empty((n, n), dtype=torch.float64, device="cuda"))
     if precision == 0:
         s2 = ils.Solver(colmajor(inst.A), p, ils.options(route=ils.ILS_ROUTE_EXPLICIT))
         x2 = vec(np.zeros(n))

@@ -43,7 +43,7 @@ def test_gram_cholesky_and_B_parity(ils, p, q, n):
     inst = W.dense_gaussian(p, q, n, 0.3 * min(1.0, (p ** 0.5 - n ** 0.5) / (q ** 0.5 + n ** 0.5 + 1e-9)),
                             1000 + n)
     assert O.is_spd(O.normal_matrix(inst.A, p))
-    s = ils.Solver(colmajor(inst.A), p)
+    s = ils.Solver(colmajor(inst.A), p, ils.options(route=ils.ILS_ROUTE_EXPLICIT))
     G1o, G2o = O.gram_blocks(inst.A, p)
     A1, A2 = inst.A[:p], inst.A[p:]
     out = torch.empty((n, n), dtype=torch.float64, device="cuda")
