@@ -585,6 +585,7 @@ def main():
     def measure(opts, steps, with_clocks):
         """Warm up, gate accuracy, then time `steps` complete solves (per-step events)."""
         solver = ils.Solver(At, p, opts, stream=stream)
+        route = "matrix_free" if ils.binding.route_model().get("matrix_free") == 1.0 else "explicit"
 
         def step():
             solver.refactor_async(At, stream=stream)
@@ -630,7 +631,7 @@ def main():
         total_s = max_over_ranks(sum(a.elapsed_time(bb) for a, bb in ev) / 1e3, world, dev)
         ph = {k: statistics.mean(d[k] for d in phases) for k in phases[0]}
         return dict(solver=solver, total_s=total_s, wall=wall, launches=launches, clocks=clocks, relerr=relerr,
-                    relerr_timed=relerr_timed, phases=ph, info=infos[-1], steps=steps)
+                    relerr_timed=relerr_timed, phases=ph, info=infos[-1], steps=steps, route=route)
 
     certified = dict(stop_rule=ils.ILS_STOP_ERR_BOUND, timing=1)  # stop on kappa_est * relres <= 1e-10
     mixed = measure(ils.options(precision=ils.ILS_FP32_REFINE, **certified), args.steps, True)
@@ -743,6 +744,7 @@ def main():
             "mixed_fp64_factor_value": r4(mixed64_value),
             "mixed_fp64_factor_relerr": r4(mixed64["relerr_timed"]),
             "setup_phases_ms": {k: r4(v) for k, v in ph.items()},
+            "routes": {"mixed": mixed["route"], "plain_fp64": plain["route"], "mixed_fp64_factor": mixed64["route"]},
             "l2": "flushed before every step (256 MiB write outside the timed events)",
             "step": "ils_refactor_async (all setup products) + ils_solve",
         },

@@ -18,9 +18,9 @@
 //      tiles of the Gram, D_u^T D_t is the transpose of D_t^T D_u: it is not formed, the
 //      epilogue stores the transpose in its place.
 //   4. The epilogue stores each exact product as it stands (FP32).  A reduction adds the
-//      products of equal t + u exactly as 64-bit integers, scales each of the 10 group
-//      sums by 2^{e_i + e_j - beta (t + u)} into FP64 and adds them in order of t + u
-//      (a fixed order: deterministic).
+//      products of equal t + u exactly as 64-bit integers, joins the 10 group sums (weight
+//      2^{e_i + e_j - beta (t + u)}) in exact integer parts and the parts in FP64 with at
+//      most two roundings, in a fixed order (deterministic).
 //
 // The tcgen05 kernel is warp-specialised: warp 0 issues TMA loads of 128 x 64 BF16 tiles
 // (128B swizzle) of up to four digit slices into a 3-stage shared-memory ring, warp 1
@@ -30,6 +30,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
+#include <cooperative_groups.h>
 
 #include <algorithm>
 #include <mutex>
@@ -108,15 +109,21 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor: kind::f16 with BF16 A/B, FP32 D, both K-major, M = 128, N = 128.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBN >> 3) << 17) |
-                            ((uint32_t)(kBM >> 4) << 24);
+// Instruction descriptors: kind::f16 with BF16 A/B, FP32 D, both K-major, M = 128 and
+// N = 128 or 256 (N = 256: two adjacent 128-row B tiles, i.e. two digit products that
+// share their A tile, in one instruction).
+constexpr uint32_t idesc_bf16(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+}
+constexpr uint32_t kIdesc = idesc_bf16(kBN);
+constexpr uint32_t kIdesc2 = idesc_bf16(2 * kBN);
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
 
@@ -169,6 +176,9 @@ struct GroupDesc {
   int side[kMaxTiles];   // 0: columns of tile bi, 1: columns of tile bj
   int ia[kMaxProd], ib[kMaxProd];  // loaded-tile index of each product's A and B operand
   int t[kMaxProd], u[kMaxProd];
+  int tcol[kMaxProd];    // TMEM accumulator of each product: 2 i + j for A tile i, B tile b0 + j
+  int jmask[2];          // per A tile i: bit j set when the product (i, j) is formed
+  int b0;                // loaded-tile index of the first B tile (the second follows it)
   int slot0;             // product slot (within the tile) of the group's first product
 };
 
@@ -195,14 +205,18 @@ __host__ __device__ inline void block_desc(bool diag, int g, GroupDesc& d) {
         cur.side[2] = cur.side[3] = 1;
       }
       cur.nprod = 0;
+      cur.b0 = same ? 0 : 2;
       for (int i = 0; i < 2; ++i) {
+        cur.jmask[i] = 0;
         for (int j = 0; j < 2; ++j) {
           const int t = 2 * a - 1 + i, u = 2 * b - 1 + j;
           if (t + u > kSlices + 1 || (same && t > u)) continue;
           cur.ia[cur.nprod] = i;
-          cur.ib[cur.nprod] = same ? j : 2 + j;
+          cur.ib[cur.nprod] = cur.b0 + j;
           cur.t[cur.nprod] = t;
           cur.u[cur.nprod] = u;
+          cur.tcol[cur.nprod] = 2 * i + j;
+          cur.jmask[i] |= 1 << j;
           ++cur.nprod;
         }
       }
@@ -224,7 +238,7 @@ __host__ __device__ inline int num_blocks(bool diag) {
 }
 
 // Product slots per tile: one per ordered pair (t, u) with t + u <= S + 1.
-__host__ __device__ inline int slots_per_tile() {
+__host__ __device__ constexpr int slots_per_tile() {
   int c = 0;
   for (int t = 1; t <= kSlices; ++t) c += kSlices + 1 - t;
   return c;
@@ -358,13 +372,10 @@ gram_split_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_con
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer ----------------
-    uint32_t aoff[kMaxProd], boff[kMaxProd];
-#pragma unroll
-    for (int p = 0; p < kMaxProd; ++p) {
-      aoff[p] = (uint32_t)gd.ia[p] * kTileBytes;
-      boff[p] = (uint32_t)gd.ib[p] * kTileBytes;
-    }
-    const int nprod = gd.nprod;
+    // Per A tile i: both products -> one N = 256 MMA over B tiles b0, b0 + 1 into
+    // accumulators 2i, 2i + 1; one product (i, j) -> an N = 128 MMA into accumulator 2i + j.
+    const uint32_t boff0 = (uint32_t)gd.b0 * kTileBytes;
+    const int jm0 = gd.jmask[0], jm1 = gd.jmask[1];
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % kStages;
       const uint32_t ph = (uint32_t)(kb / kStages) & 1u;
@@ -377,11 +388,17 @@ gram_split_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_con
       const uint32_t st_addr = smem_u32(tiles + (size_t)s * kStageBytes);
 #pragma unroll
       for (int kk = 0; kk < kBK / 16; ++kk) {
+        const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
 #pragma unroll
-        for (int p = 0; p < kMaxProd; ++p) {  // accumulator p: TMEM columns p * kBN ..
-          if (p < nprod)
-            mma_bf16(tmem_acc + (uint32_t)(p * kBN), smem_desc_sw128(st_addr + aoff[p] + kk * 32),
-                     smem_desc_sw128(st_addr + boff[p] + kk * 32), (kb > 0 || kk > 0) ? 1u : 0u);
+        for (int i = 0; i < 2; ++i) {  // A tile i: accumulators 2i (TMEM columns 2i kBN ..), 2i + 1
+          const int jm = i == 0 ? jm0 : jm1;
+          const uint64_t adesc = smem_desc_sw128(st_addr + (uint32_t)i * kTileBytes + kk * 32);
+          if (jm == 3)
+            mma_bf16(tmem_acc + (uint32_t)(2 * i * kBN), adesc, smem_desc_sw128(st_addr + boff0 + kk * 32), kIdesc2,
+                     acc);
+          else if (jm)
+            mma_bf16(tmem_acc + (uint32_t)((2 * i + (jm >> 1)) * kBN), adesc,
+                     smem_desc_sw128(st_addr + boff0 + (uint32_t)(jm >> 1) * kTileBytes + kk * 32), kIdesc, acc);
         }
       }
       mma_commit(&empty[s]);  // frees the stage once these MMAs have read it
@@ -411,7 +428,7 @@ gram_split_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_con
 #pragma unroll 1
         for (int c0 = 0; c0 < kBN; c0 += 32) {
           uint32_t v[32];
-          tmem_ld_32x32b_x32(tmem_acc + ((uint32_t)(q * 32) << 16) + (uint32_t)(p * kBN + c0), v);
+          tmem_ld_32x32b_x32(tmem_acc + ((uint32_t)(q * 32) << 16) + (uint32_t)(gd.tcol[p] * kBN + c0), v);
 #pragma unroll
           for (int c = 0; c < 32; ++c) out[(size_t)(c0 + c) * kBM + row] = v[c];  // column-major 128 x 128
           if (out_t) {
@@ -435,6 +452,11 @@ gram_split_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_con
   }
 }
 
+__device__ __forceinline__ int exponent_of_field(int m) {
+  // A normal value with exponent field f lies in [2^(f-1023), 2^(f-1022)).
+  return (m == 0 || m == 0x7FF) ? 0 : m - 1022;
+}
+
 // Per-column exponent e_j with max_r |A(r,j)| < 2^e_j (0 for a zero column), read from the
 // exponent fields of the FP64 bit patterns (integer work only).
 __global__ void column_exponent_kernel(int K, int n, const double* __restrict__ A, int64_t lda, int* __restrict__ exps) {
@@ -451,8 +473,7 @@ __global__ void column_exponent_kernel(int K, int n, const double* __restrict__ 
   if (threadIdx.x == 0) {
     int m = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = max(m, red[w]);
-    // A normal value with exponent field f lies in [2^(f-1023), 2^(f-1022)).
-    exps[j] = (m == 0 || m == 0x7FF) ? 0 : m - 1022;
+    exps[j] = exponent_of_field(m);
   }
 }
 
@@ -463,123 +484,212 @@ __global__ void column_exponent_kernel(int K, int n, const double* __restrict__ 
 // This equals the digit expansion by repeated rounding to nearest, using integer work
 // only (GB300's FP64 pipe is the scarce unit).
 // Rows r >= sign_split are split negated (J's sign for a product A^T J B).
-__global__ void split_kernel(int K, int n, const double* __restrict__ A, int64_t lda, const int* __restrict__ exps,
-                             __nv_bfloat16* __restrict__ D, int64_t ldk, int32_t* err, int sign_split) {
-  const int j = blockIdx.y;
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < K; r += gridDim.x * blockDim.x) {
-    const long long bits = __double_as_longlong(A[r + (int64_t)j * lda]);
-    const int f = (int)((bits >> 52) & 0x7FF);
-    long long V = 0;
-    if (f == 0x7FF) {
-      atomicExch(err, 2);
-    } else if (f != 0) {  // subnormals are below 2^-1022 and round to 0 at 50 bits
-      const unsigned long long mant = (unsigned long long)(bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-      // value = mant 2^(f - 1075); V = mant 2^(f - 1075 + kBeta*kSlices - e_j) with a right shift > 0
-      const int sh = 1075 - f - kBeta * kSlices + exps[j];
-      if (sh < 64) {
-        const unsigned long long half = (sh > 0) ? (1ull << (sh - 1)) : 0ull;
-        const unsigned long long mag = (sh > 0) ? ((mant + half) >> sh) : (mant << (-sh));
-        V = ((bits < 0) != (r >= sign_split)) ? -(long long)mag : (long long)mag;
+// A thread takes four consecutive rows r0 .. r0 + 3 of column j (one 8-byte store per
+// slice); rows in [K, ldk) get zero digits (the padding TMA reads).  The optional copy of
+// A is written on the way.  Grid: (ceil(ldk / 1024), n) blocks of 256 threads.
+__device__ __forceinline__ long long split_value(long long bits, int ej, bool negate, int32_t* err) {
+  const int f = (int)((bits >> 52) & 0x7FF);
+  if (f == 0x7FF) {
+    atomicExch(err, 2);
+    return 0;
+  }
+  if (f == 0) return 0;  // subnormals are below 2^-1022 and round to 0 at 50 bits
+  const unsigned long long mant = (unsigned long long)(bits & 0xFFFFFFFFFFFFFll) | (1ull << 52);
+  // value = mant 2^(f - 1075); V = mant 2^(f - 1075 + kBeta*kSlices - e_j), rounded
+  const int sh = 1075 - f - kBeta * kSlices + ej;
+  if (sh >= 64) return 0;
+  const unsigned long long half = (sh > 0) ? (1ull << (sh - 1)) : 0ull;
+  const unsigned long long mag = (sh > 0) ? ((mant + half) >> sh) : (mant << (-sh));
+  return ((bits < 0) != negate) ? -(long long)mag : (long long)mag;
+}
+
+// The digits of four consecutive rows r0 .. r0 + 3 of column j: one 8-byte store per slice.
+// Adding C = 16 (1 + 32 + ... + 32^(S-2)) turns the balanced digits d_t in [-16, 15] of
+// V into the plain base-32 digits d_t + 16 of W = V + C, and W >> 5 (S - 1) is the top
+// digit; so each digit is one 5-bit field of W.  A small integer u becomes its FP32 value
+// by one integer and one FP32 addition (the bit pattern of 1.5 2^23 + u, minus 1.5 2^23),
+// and, having at most 7 significant bits, its BF16 pattern is the float's upper half.
+// This keeps the split off the conversion pipe (a quarter of the ALU rate).
+__device__ __forceinline__ uint32_t small_int_bf16_bits(int u, float bias) {
+  return __float_as_uint(__int_as_float(0x4B400000 + u) - bias) >> 16;
+}
+
+__device__ __forceinline__ void store_digits4(const long long (&V)[4], __nv_bfloat16* __restrict__ D, int64_t ldk,
+                                              int n, int j, int64_t r0) {
+  constexpr long long kC = 16ll * ((1ll << (kBeta * (kSlices - 1))) - 1) / ((1ll << kBeta) - 1);
+  static_assert(kBeta == 5, "five-bit digit fields");
+  long long W[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) W[i] = V[i] + kC;
+#pragma unroll
+  for (int t = 0; t < kSlices; ++t) {
+    const int slice = kSlices - 1 - t;  // slice 0 holds the top digit
+    uint32_t h[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (t < kSlices - 1) {
+        const int u = (int)((unsigned long long)W[i] >> (kBeta * t)) & 31;  // d_t + 16
+        h[i] = small_int_bf16_bits(u, 12582912.0f + 16.0f);
+      } else {
+        const int top = (int)(W[i] >> (kBeta * t));  // |top| <= 32
+        h[i] = small_int_bf16_bits(top + 64, 12582912.0f + 64.0f);
       }
     }
-#pragma unroll
-    for (int t = kSlices - 1; t >= 1; --t) {
-      int d = (int)(V & 31);
-      if (d >= 16) d -= 32;
-      V = (V - d) >> kBeta;
-      D[((int64_t)t * n + j) * ldk + r] = __int2bfloat16_rn(d);
-    }
-    D[(int64_t)j * ldk + r] = __int2bfloat16_rn((int)V);  // top digit, |V| <= 32
+    *reinterpret_cast<uint2*>(D + ((int64_t)slice * n + j) * ldk + r0) =
+        make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
   }
 }
 
-// The two kernels above in one pass for K <= 1024 * 16: one CTA per column keeps the
-// column's bit patterns in registers, reduces the largest exponent field, and splits.
-constexpr int kFuseThreads = 1024;
-constexpr int kFusePer = 16;
+__global__ void split_rows4_kernel(int K, int64_t ldk, int n, const double* __restrict__ A, int64_t lda,
+                                   const int* __restrict__ exps, __nv_bfloat16* __restrict__ D, int32_t* err,
+                                   double* __restrict__ Acopy, int64_t ldcopy, int sign_split) {
+  const int j = blockIdx.y;
+  const int64_t r0 = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+  if (r0 >= ldk) return;
+  const int ej = exps[j];
+  long long V[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t r = r0 + i;
+    V[i] = 0;
+    if (r >= K) continue;
+    const long long bits = __double_as_longlong(__ldg(A + r + (int64_t)j * lda));
+    if (Acopy) Acopy[r + (int64_t)j * ldcopy] = __longlong_as_double(bits);
+    V[i] = split_value(bits, ej, r >= sign_split, err);
+  }
+  store_digits4(V, D, ldk, n, j, r0);
+}
 
-__global__ void __launch_bounds__(kFuseThreads)
-exponent_split_kernel(int K, int n, const double* __restrict__ A, int64_t lda, int* __restrict__ exps,
-                      __nv_bfloat16* __restrict__ D, int64_t ldk, int32_t* err, double* __restrict__ Acopy,
-                      int64_t ldcopy, int sign_split) {
-  const int j = blockIdx.x;
-  long long bits[kFusePer];
+// Exponent and digits in one pass: column j is taken by a cluster of C CTAs (grid (C, n),
+// cluster (C, 1, 1)), CTA c holding rows [4096 c, 4096 (c + 1)) in registers, 4
+// consecutive rows per thread and group of 1024.  The column's largest exponent field is
+// the maximum of the C CTAs' maxima, read through distributed shared memory; then every
+// CTA splits its rows.  Rows in [K, ldk) get zero digits.  Used for ldk <= 8 * 4096.
+constexpr int kClusterRows = 4096;
+constexpr int kClusterMax = 8;
+
+__global__ void __launch_bounds__(256) exponent_split_cluster_kernel(int K, int64_t ldk, int n,
+                                                                     const double* __restrict__ A, int64_t lda,
+                                                                     int* __restrict__ exps,
+                                                                     __nv_bfloat16* __restrict__ D, int32_t* err,
+                                                                     double* __restrict__ Acopy, int64_t ldcopy,
+                                                                     int sign_split) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  __shared__ int s_red[8];
+  __shared__ int s_max;
+  __shared__ int s_e;
+  const int j = blockIdx.y;
+  const int64_t base = (int64_t)blockIdx.x * kClusterRows;
+  constexpr int kGroups = kClusterRows / 1024;
+  long long bits[kGroups][4];
   int mx = 0;
 #pragma unroll
-  for (int i = 0; i < kFusePer; ++i) {
-    const int r = threadIdx.x + kFuseThreads * i;
-    bits[i] = r < K ? __double_as_longlong(__ldg(A + r + (int64_t)j * lda)) : 0ll;
-    mx = max(mx, (int)((bits[i] >> 52) & 0x7FF));
-  }
-  if (Acopy) {  // the caller's copy of A, written while the column is in registers
+  for (int g = 0; g < kGroups; ++g) {
 #pragma unroll
-    for (int i = 0; i < kFusePer; ++i) {
-      const int r = threadIdx.x + kFuseThreads * i;
-      if (r < K) Acopy[r + (int64_t)j * ldcopy] = __longlong_as_double(bits[i]);
+    for (int i = 0; i < 4; ++i) {
+      const int64_t r = base + g * 1024 + 4 * threadIdx.x + i;
+      bits[g][i] = r < K ? __double_as_longlong(__ldg(A + r + (int64_t)j * lda)) : 0ll;
+      mx = max(mx, (int)((bits[g][i] >> 52) & 0x7FF));
     }
   }
+  if (Acopy) {
+#pragma unroll
+    for (int g = 0; g < kGroups; ++g)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int64_t r = base + g * 1024 + 4 * threadIdx.x + i;
+        if (r < K) Acopy[r + (int64_t)j * ldcopy] = __longlong_as_double(bits[g][i]);
+      }
+  }
   for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  __shared__ int red[kFuseThreads / 32];
-  __shared__ int e_j;
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = mx;
   __syncthreads();
   if (threadIdx.x == 0) {
     int m = 0;
-    for (int w = 0; w < kFuseThreads / 32; ++w) m = max(m, red[w]);
-    e_j = (m == 0 || m == 0x7FF) ? 0 : m - 1022;  // normal values with field f lie in [2^(f-1023), 2^(f-1022))
-    exps[j] = e_j;
+    for (int w = 0; w < 8; ++w) m = max(m, s_red[w]);
+    s_max = m;
   }
-  __syncthreads();
-  const int ej = e_j;
+  cl.sync();  // every CTA's s_max is written
+  if (threadIdx.x == 0) {
+    int m = 0;
+    for (unsigned r = 0; r < cl.num_blocks(); ++r) m = max(m, *cl.map_shared_rank(&s_max, r));
+    s_e = exponent_of_field(m);
+    if (blockIdx.x == 0) exps[j] = s_e;
+  }
+  cl.sync();  // s_e is set, and no CTA leaves while another may still read its s_max
+  const int ej = s_e;
 #pragma unroll
-  for (int i = 0; i < kFusePer; ++i) {
-    const int r = threadIdx.x + kFuseThreads * i;
-    if (r >= K) continue;
-    const int f = (int)((bits[i] >> 52) & 0x7FF);
-    long long V = 0;
-    if (f == 0x7FF) {
-      atomicExch(err, 2);
-    } else if (f != 0) {
-      const unsigned long long mant = (unsigned long long)(bits[i] & 0xFFFFFFFFFFFFFll) | (1ull << 52);
-      const int sh = 1075 - f - kBeta * kSlices + ej;
-      if (sh < 64) {
-        const unsigned long long half = (sh > 0) ? (1ull << (sh - 1)) : 0ull;
-        const unsigned long long mag = (sh > 0) ? ((mant + half) >> sh) : (mant << (-sh));
-        V = ((bits[i] < 0) != (r >= sign_split)) ? -(long long)mag : (long long)mag;
-      }
-    }
+  for (int g = 0; g < kGroups; ++g) {
+    const int64_t r0 = base + g * 1024 + 4 * threadIdx.x;
+    if (r0 >= ldk) break;
+    long long V[4];
 #pragma unroll
-    for (int t = kSlices - 1; t >= 1; --t) {
-      int d = (int)(V & 31);
-      if (d >= 16) d -= 32;
-      V = (V - d) >> kBeta;
-      D[((int64_t)t * n + j) * ldk + r] = __int2bfloat16_rn(d);
-    }
-    D[(int64_t)j * ldk + r] = __int2bfloat16_rn((int)V);
+    for (int i = 0; i < 4; ++i) V[i] = split_value(bits[g][i], ej, base + g * 1024 + 4 * threadIdx.x + i >= sign_split, err);
+    store_digits4(V, D, ldk, n, j, r0);
   }
 }
 
 // C(i,j) for the upper tiles.  Every stored product is an exact integer held in FP32.
 // The products of equal t + u carry the same scale 2^{e_i + e_j - beta (t + u)}, so they
 // are added exactly in integers first (at most 10 terms below 2^24 each per K chunk), and
-// only the 10 scaled group sums are added in FP64, in order of t + u (a fixed order, and
-// fewer roundings than one FP64 addition per product).  Then the tile is mirrored.  Every
+// the 10 group sums are joined by combine_groups (below).  Then the tile is mirrored.  Every
 // tile has all its ordered-pair slots (a diagonal tile's transposed slots were written by
-// the epilogue).  A thread takes two adjacent rows of one column (8-byte loads).
+// the epilogue).  A thread takes one entry.
 constexpr int kScales = kSlices;  // t + u = 2 .. S + 1
+
+// Sum_g V[g] 2^(e - beta (g + 2)) for the exact integer group sums V[g] (g = t + u - 2).
+// Groups are joined four at a time by exact int64 Horner steps (each part stays below 2^53
+// for up to 1024 K chunks, so its conversion to FP64 is exact), then the parts by two
+// FMAs and one ldexp: at most two roundings, and a handful of FP64 instructions instead of
+// one conversion, scaling and addition per group (the FP64 pipe is GB300's scarce unit).
+constexpr int kPartLen = 4;
+constexpr int kParts = (kScales + kPartLen - 1) / kPartLen;
+
+__device__ __forceinline__ double combine_groups(const long long (&V)[kScales], int e) {
+  double acc = 0.0;
+  int prev_last = -1;
+#pragma unroll
+  for (int p = 0; p < kParts; ++p) {
+    const int g0 = p * kPartLen;
+    const int g1 = (g0 + kPartLen < kScales ? g0 + kPartLen : kScales) - 1;  // last group of part p
+    long long part = 0;
+#pragma unroll
+    for (int g = g0; g <= g1; ++g) part = part * (1ll << kBeta) + V[g];
+    acc = p == 0 ? (double)part : fma(acc, (double)(1ll << (kBeta * (g1 - prev_last))), (double)part);
+    prev_last = g1;
+  }
+  return ldexp(acc, e - kBeta * (kScales + 1));
+}
+
+// Group sums of one entry: every K chunk's exact products (FP32 integers), added by t + u.
+__device__ __forceinline__ void group_sums(const uint32_t* __restrict__ base, int n_kchunks, size_t tile_elems,
+                                           long long (&V)[kScales]) {
+#pragma unroll
+  for (int g = 0; g < kScales; ++g) V[g] = 0;
+  for (int kc = 0; kc < n_kchunks; ++kc) {
+    float w[slots_per_tile()];
+#pragma unroll
+    for (int slot = 0; slot < slots_per_tile(); ++slot)  // every load in flight before the sums
+      w[slot] = __uint_as_float(__ldcg(base + ((size_t)slot * n_kchunks + kc) * tile_elems));
+    int slot = 0;
+#pragma unroll
+    for (int t = 1; t <= kSlices; ++t)
+#pragma unroll
+      for (int u = 1; u <= kSlices + 1 - t; ++u, ++slot) V[t + u - 2] += (long long)__float2int_rz(w[slot]);
+  }
+}
 
 __global__ void split_reduce_kernel(SplitParams P, double* __restrict__ C, int64_t ldc) {
   const int items_per_tile = slots_per_tile() * P.n_kchunks;
   const int n_upper = P.n_tiles * (P.n_tiles + 1) / 2;
-  const int64_t total2 = (int64_t)n_upper * kBM * kBN / 2;  // pairs of rows
-  const uint32_t* part = reinterpret_cast<const uint32_t*>(P.partial);
   const size_t tile_elems = (size_t)kBM * kBN;
-  for (int64_t e2 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e2 < total2;
-       e2 += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t e = 2 * e2;
+  const int64_t total = (int64_t)n_upper * tile_elems;
+  const uint32_t* part = reinterpret_cast<const uint32_t*>(P.partial);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int tile = (int)(e / tile_elems);
     const int local = (int)(e % tile_elems);
-    const int row = local % kBM, col = local / kBM;  // rows row, row + 1 of column col
+    const int row = local % kBM, col = local / kBM;
     int r = 0;
     int tt = tile;
     while (tt >= P.n_tiles - r) {
@@ -588,36 +698,12 @@ __global__ void split_reduce_kernel(SplitParams P, double* __restrict__ C, int64
     }
     const int bi = r, bj = r + tt;
     const int gi = bi * kBM + row, gj = bj * kBN + col;
-    if (gj >= P.n || gi >= P.n || (bi == bj && gi > gj)) continue;  // the second row is past both too
-    const uint32_t* base = part + (size_t)tile * items_per_tile * tile_elems + local;
-    long long V[2][kScales];
-#pragma unroll
-    for (int q = 0; q < 2; ++q)
-#pragma unroll
-      for (int g = 0; g < kScales; ++g) V[q][g] = 0;
-    for (int kc = 0; kc < P.n_kchunks; ++kc) {
-      int slot = 0;
-#pragma unroll
-      for (int t = 1; t <= kSlices; ++t) {
-#pragma unroll
-        for (int u = 1; u <= kSlices + 1 - t; ++u, ++slot) {
-          const uint2 w = __ldcg(reinterpret_cast<const uint2*>(base + ((size_t)slot * P.n_kchunks + kc) * tile_elems));
-          V[0][t + u - 2] += (long long)__float2int_rz(__uint_as_float(w.x));
-          V[1][t + u - 2] += (long long)__float2int_rz(__uint_as_float(w.y));
-        }
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int gq = gi + q;
-      if (gq >= P.n || (bi == bj && gq > gj)) continue;
-      const int eij = P.exps[gq] + P.exps[gj];
-      double s = 0.0;
-#pragma unroll
-      for (int g = 0; g < kScales; ++g) s += ldexp((double)V[q][g], eij - kBeta * (g + 2));
-      C[gq + (int64_t)gj * ldc] = s;
-      C[gj + (int64_t)gq * ldc] = s;
-    }
+    if (gj >= P.n || gi >= P.n || (bi == bj && gi > gj)) continue;
+    long long V[kScales];
+    group_sums(part + (size_t)tile * items_per_tile * tile_elems + local, P.n_kchunks, tile_elems, V);
+    const double s = combine_groups(V, P.exps[gi] + P.exps[gj]);
+    C[gi + (int64_t)gj * ldc] = s;
+    C[gj + (int64_t)gi * ldc] = s;
   }
 }
 
@@ -627,46 +713,20 @@ __global__ void split_reduce_kernel(SplitParams P, double* __restrict__ C, int64
 __global__ void gemm_reduce_kernel(SplitParams P, double* __restrict__ C, int64_t ldc, const double* C0,
                                    int64_t ldc0) {
   const int items_per_tile = slots_per_tile() * P.n_kchunks;
-  const int64_t total2 = (int64_t)P.n_tiles * P.n_tiles2 * kBM * kBN / 2;  // pairs of rows
-  const uint32_t* part = reinterpret_cast<const uint32_t*>(P.partial);
   const size_t tile_elems = (size_t)kBM * kBN;
-  for (int64_t e2 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e2 < total2;
-       e2 += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t e = 2 * e2;
+  const int64_t total = (int64_t)P.n_tiles * P.n_tiles2 * tile_elems;
+  const uint32_t* part = reinterpret_cast<const uint32_t*>(P.partial);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int tile = (int)(e / tile_elems);
     const int local = (int)(e % tile_elems);
     const int row = local % kBM, col = local / kBM;
     const int bi = tile / P.n_tiles2, bj = tile % P.n_tiles2;
     const int gi = bi * kBM + row, gj = bj * kBN + col;
     if (gj >= P.n2 || gi >= P.n) continue;
-    const uint32_t* base = part + (size_t)tile * items_per_tile * tile_elems + local;
-    long long V[2][kScales];
-#pragma unroll
-    for (int q = 0; q < 2; ++q)
-#pragma unroll
-      for (int g = 0; g < kScales; ++g) V[q][g] = 0;
-    for (int kc = 0; kc < P.n_kchunks; ++kc) {
-      int slot = 0;
-#pragma unroll
-      for (int t = 1; t <= kSlices; ++t) {
-#pragma unroll
-        for (int u = 1; u <= kSlices + 1 - t; ++u, ++slot) {
-          const uint2 w = __ldcg(reinterpret_cast<const uint2*>(base + ((size_t)slot * P.n_kchunks + kc) * tile_elems));
-          V[0][t + u - 2] += (long long)__float2int_rz(__uint_as_float(w.x));
-          V[1][t + u - 2] += (long long)__float2int_rz(__uint_as_float(w.y));
-        }
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int gq = gi + q;
-      if (gq >= P.n) continue;
-      const int eij = P.exps[gq] + P.exps2[gj];
-      double v = 0.0;
-#pragma unroll
-      for (int g = 0; g < kScales; ++g) v += ldexp((double)V[q][g], eij - kBeta * (g + 2));
-      C[gq + (int64_t)gj * ldc] = C0 ? C0[gq + (int64_t)gj * ldc0] - v : v;
-    }
+    long long V[kScales];
+    group_sums(part + (size_t)tile * items_per_tile * tile_elems + local, P.n_kchunks, tile_elems, V);
+    const double v = combine_groups(V, P.exps[gi] + P.exps2[gj]);
+    C[gi + (int64_t)gj * ldc] = C0 ? C0[gi + (int64_t)gj * ldc0] - v : v;
   }
 }
 
@@ -713,24 +773,30 @@ cudaError_t split_into(int64_t K, int64_t n, const double* A, int64_t lda, int64
   __nv_bfloat16* D = static_cast<__nv_bfloat16*>(slices);
   const int ss = (int)std::min<int64_t>(sign_split, K);
   cudaError_t e;
-  if (ldk != K) {  // zero the padding rows so TMA never reads stale values inside ldk
-    e = cudaMemsetAsync(D, 0, sizeof(__nv_bfloat16) * (size_t)kSlices * n * ldk, s);
-    if (e != cudaSuccess) return e;
-  }
-  if (K <= (int64_t)kFuseThreads * kFusePer) {
-    exponent_split_kernel<<<(unsigned)n, kFuseThreads, 0, s>>>((int)K, (int)n, A, lda, exps, D, ldk, err, a_copy,
-                                                               ld_copy, ss);
+  const int64_t C = (ldk + kClusterRows - 1) / kClusterRows;
+  if (C <= kClusterMax) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)C, (unsigned)n);
+    cfg.blockDim = dim3(256);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, exponent_split_cluster_kernel, (int)K, ldk, (int)n, A, lda, exps, D, err, a_copy,
+                           ld_copy, ss);
     note_launch();
-    return cudaGetLastError();
-  }
-  if (a_copy && (e = cudaMemcpy2DAsync(a_copy, sizeof(double) * ld_copy, A, sizeof(double) * lda, sizeof(double) * K,
-                                       n, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
     return e;
-  column_exponent_kernel<<<(unsigned)n, 256, 0, s>>>((int)K, (int)n, A, lda, exps);
+  }
+  column_exponent_kernel<<<(unsigned)n, 1024, 0, s>>>((int)K, (int)n, A, lda, exps);
   note_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  split_kernel<<<dim3((unsigned)std::min<int64_t>((K + 255) / 256, 64), (unsigned)n), 256, 0, s>>>(
-      (int)K, (int)n, A, lda, exps, D, ldk, err, ss);
+  // ldk is a multiple of 8, so the threads' 4-row groups cover [0, ldk) exactly
+  split_rows4_kernel<<<dim3((unsigned)((ldk + 1023) / 1024), (unsigned)n), 256, 0, s>>>(
+      (int)K, ldk, (int)n, A, lda, exps, D, err, a_copy, ld_copy, ss);
   note_launch();
   return cudaGetLastError();
 }
@@ -782,7 +848,8 @@ cudaError_t gram_split_tc(int64_t K, int64_t n, const double* A, int64_t lda, do
   note_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (mma_end && (e = cudaEventRecord(mma_end, s)) != cudaSuccess) return e;
-  split_reduce_kernel<<<1024, 256, 0, s>>>(P, C, ldc);
+  split_reduce_kernel<<<(unsigned)std::min<int64_t>(((int64_t)n_upper * kBM * kBN + 255) / 256, 4096), 256, 0, s>>>(
+      P, C, ldc);
   note_launch();
   return cudaGetLastError();
 }
@@ -829,7 +896,8 @@ cudaError_t gemm_split_tc(int64_t K, int64_t n1, int64_t n2, const void* slicesX
   gram_split_mma_kernel<false><<<items, kThreads, smem, s>>>(mx, my, P);
   note_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  gemm_reduce_kernel<<<1024, 256, 0, s>>>(P, C, ldc, C0, ldc0);
+  gemm_reduce_kernel<<<(unsigned)std::min<int64_t>(((int64_t)P.n_tiles * P.n_tiles2 * kBM * kBN + 255) / 256, 4096),
+                       256, 0, s>>>(P, C, ldc, C0, ldc0);
   note_launch();
   return cudaGetLastError();
 }

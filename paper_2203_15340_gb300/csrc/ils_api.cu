@@ -799,7 +799,6 @@ ils_status pass_begin(ils_handle h, int64_t c0, int64_t kk, const double* B, int
     ILS_CK(cudaMemcpy2DAsync(h->X0, sizeof(double) * n, X, sizeof(double) * ldx, sizeof(double) * n, kk,
                              cudaMemcpyDeviceToDevice, s));
   }
-  if (h->opt.stop_rule == ILS_STOP_ERR_BOUND && h->ev_estk) ILS_CK(cudaStreamWaitEvent(s, h->ev_estk, 0));
   init_state_kernel<<<1, 32, 0, s>>>(h->st, h->opt.max_outer, h->col_done, h->col_inner, (int)kk);
   note_launch();
   ILS_CK(cudaGetLastError());
@@ -897,14 +896,24 @@ ils_status pass_launch(ils_handle h, int64_t count) {
   const int64_t cap = h->opt.max_outer + 1;
   const int64_t todo = std::min(count, cap - h->pass_launched);
   if (todo > 0 && h->pass_launched == 0 && h->pass_mixed && !h->mf && !h->sparse && h->pass_k == 1) {
-    // One right-hand side on the explicit route: the whole refinement in one launch.
-    const cudaError_t e = mixed_solve_fused(h->pa, h->pma, h->opt.precision, h->coop_sync, s);
+    // One right-hand side on the explicit route: the whole refinement in one launch.  Under
+    // the error-bound stop, a provisional launch runs beside the kappa estimate and a second
+    // one, after it, applies the final rule (solve_fused.cu).
+    const bool split = h->opt.stop_rule == ILS_STOP_ERR_BOUND && h->ev_estk;
+    const cudaError_t e = mixed_solve_fused(h->pa, h->pma, h->opt.precision, h->coop_sync, s, split ? 1 : 0);
     if (e == cudaSuccess) {
+      if (split) {
+        ILS_CK(cudaStreamWaitEvent(s, h->ev_estk, 0));
+        ILS_CK(mixed_solve_fused(h->pa, h->pma, h->opt.precision, h->coop_sync, s, 2));
+      }
       h->pass_launched = cap;
       return ILS_OK;
     }
     if (e != cudaErrorNotSupported) ILS_CK(e);
   }
+  // every other path reads kappa_est from its first step on
+  if (h->pass_launched == 0 && h->opt.stop_rule == ILS_STOP_ERR_BOUND && h->ev_estk)
+    ILS_CK(cudaStreamWaitEvent(s, h->ev_estk, 0));
   for (int64_t i = 0; i < todo; ++i) {
     if (h->mf) {
       for (int c = 0; c < (int)h->pass_k; ++c)

@@ -150,8 +150,11 @@ struct MixedArgs;
 // up to st->max_outer, in one cooperative launch (solve_fused.cu); same state and results
 // as sp_iterate_f64 (mode 2) + mixed_correct per step.  `sync`: 4 words.
 // cudaErrorNotSupported when k != 1 or cooperative launch is unavailable.
+// phase 0: the whole solve; 1: provisional, stopping on tol2 alone (col_done = 2 when that
+// is met: ||r||^2 and r of x are kept); 2: resume after a provisional launch with the final
+// rule (tol2 * tol_scale), refining on if the kept residual fails it.
 cudaError_t mixed_solve_fused(const SpIterArgs& sa, const MixedArgs& ma, int precision, uint32_t* sync,
-                              cudaStream_t s);
+                              cudaStream_t s, int phase = 0);
 int sp_iterate_blocks(int64_t n);
 
 // Copy the final iterate buffer (chosen on the device) into the user's X.

@@ -11,6 +11,10 @@
 // rule and the state written at the end are those of the launch-per-product path.
 // Barrier waits are bounded (1 s, or the handle's wait limit); past that the CTA records TIMEOUT, marks the solve
 // done and raises the abort word, which releases every other waiter.
+// Under the error-bound stop the refinement need not wait for kappa_est: a provisional
+// launch stops on relres <= tol (necessary, as kappa >= 1), and a second launch, ordered
+// after the estimate, applies kappa_est relres <= tol to the stored residual and refines
+// on only if that fails.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -48,6 +52,7 @@ struct FusedArgs {
   SolveState* st;
   uint32_t* sync;        // [0] arrivals, [1] generation, [2] abort
   uint64_t wait_ns;      // bound on each barrier wait
+  int32_t phase;         // 0: one launch; 1: provisional (stop on tol2 alone); 2: resume after 1
 };
 
 __device__ __forceinline__ uint32_t fs_ld_acquire(const uint32_t* p) {
@@ -186,7 +191,10 @@ __global__ void __launch_bounds__(kFsThreads) mixed_solve_fused_kernel(FusedArgs
   if (*((volatile int32_t*)&a.st->done)) return;
   int64_t it = *((volatile int64_t*)&a.st->iters);
   const int64_t max_outer = a.st->max_outer;
-  const double target = a.tol2 * (a.tol_scale ? *a.tol_scale : 1.0) * a.bnorm2[0];
+  // A provisional launch stops on tol2 alone: tol_scale <= 1, so that is necessary for the
+  // final rule, which a resuming launch applies to the stored ||r||^2 of the same x.
+  const double target = a.tol2 * (a.tol_scale && a.phase != 1 ? *a.tol_scale : 1.0) * a.bnorm2[0];
+  bool resume = a.phase == 2 && *((volatile int32_t*)a.col_done) == 2;
   const int64_t row = (int64_t)blockIdx.x * kFsWarps + w;  // the warp's row (R > 0)
   constexpr int RR = R > 0 ? R : 1;
   double hr[RR];
@@ -202,69 +210,84 @@ __global__ void __launch_bounds__(kFsThreads) mixed_solve_fused_kernel(FusedArgs
     }
   }
   for (;;) {
-    // r = bbar - H x (FP64) and this CTA's share of ||r||^2
-    double rp = 0.0;
-    const int64_t nst = R > 0 ? 32 * R : n;  // staged entries (zero past n)
-    for (int64_t j = threadIdx.x; j < nst; j += kFsThreads) xs[j] = j < n ? __ldcg(a.x + j) : 0.0;
-    __syncthreads();
-    if (R > 0) {
-      if (row < n) {
-        double acc0 = 0.0, acc1 = 0.0;
+    double rr;
+    if (resume) {  // r and ||r||^2 of this x were left by the provisional launch
+      resume = false;
+      rr = *((volatile double*)a.col_rr);
+    } else {
+      // r = bbar - H x (FP64) and this CTA's share of ||r||^2
+      double rp = 0.0;
+      const int64_t nst = R > 0 ? 32 * R : n;  // staged entries (zero past n)
+      for (int64_t j = threadIdx.x; j < nst; j += kFsThreads) xs[j] = j < n ? __ldcg(a.x + j) : 0.0;
+      __syncthreads();
+      if (R > 0) {
+        if (row < n) {
+          double acc0 = 0.0, acc1 = 0.0;
 #pragma unroll
-        for (int u = 0; u < RR; u += 2) {
-          acc0 = fma(hr[u], xs[lane + 32 * u], acc0);
-          if (u + 1 < RR) acc1 = fma(hr[u + 1], xs[lane + 32 * (u + 1)], acc1);
-        }
-        const double s = fs_warp_sum(acc0 + acc1);
-        if (lane == 0) {
-          const double r = a.bbar[row] - s;
-          a.r[row] = r;
-          rp = r * r;
+          for (int u = 0; u < RR; u += 2) {
+            acc0 = fma(hr[u], xs[lane + 32 * u], acc0);
+            if (u + 1 < RR) acc1 = fma(hr[u + 1], xs[lane + 32 * (u + 1)], acc1);
+          }
+          const double s = fs_warp_sum(acc0 + acc1);
+          if (lane == 0) {
+            const double r = a.bbar[row] - s;
+            a.r[row] = r;
+            rp = r * r;
+          }
         }
       }
-    }
-    for (int64_t i = (int64_t)blockIdx.x * kFsWarps + w; R == 0 && i < n; i += tw) {
-      const double* hrow = a.H + i * n;
-      double acc[4] = {0.0, 0.0, 0.0, 0.0};
-      int64_t j = lane;
+      for (int64_t i = (int64_t)blockIdx.x * kFsWarps + w; R == 0 && i < n; i += tw) {
+        const double* hrow = a.H + i * n;
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        int64_t j = lane;
 #pragma unroll 4
-      for (; j + 96 < n; j += 128) {
+        for (; j + 96 < n; j += 128) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) acc[u] = fma(__ldg(hrow + j + 32 * u), xs[j + 32 * u], acc[u]);
+          for (int u = 0; u < 4; ++u) acc[u] = fma(__ldg(hrow + j + 32 * u), xs[j + 32 * u], acc[u]);
+        }
+        for (; j < n; j += 32) acc[0] = fma(__ldg(hrow + j), xs[j], acc[0]);
+        const double s = fs_warp_sum((acc[0] + acc[1]) + (acc[2] + acc[3]));
+        if (lane == 0) {
+          const double r = a.bbar[i] - s;
+          a.r[i] = r;
+          rp = fma(r, r, rp);
+        }
       }
-      for (; j < n; j += 32) acc[0] = fma(__ldg(hrow + j), xs[j], acc[0]);
-      const double s = fs_warp_sum((acc[0] + acc[1]) + (acc[2] + acc[3]));
-      if (lane == 0) {
-        const double r = a.bbar[i] - s;
-        a.r[i] = r;
-        rp = fma(r, r, rp);
-      }
-    }
-    if (lane == 0) red[w] = rp;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int k = 0; k < kFsWarps; ++k) t += red[k];
-      a.partials[blockIdx.x] = t;
-    }
-    if (!fs_barrier(a)) return;
-    // ||r||^2: every CTA adds the partials in the same order
-    {
-      double v = 0.0;
-      for (unsigned b = threadIdx.x; b < gridDim.x; b += kFsThreads) v += __ldcg(a.partials + b);
-      v = fs_warp_sum(v);
-      if (lane == 0) red[w] = v;
+      if (lane == 0) red[w] = rp;
       __syncthreads();
       if (threadIdx.x == 0) {
         double t = 0.0;
         for (int k = 0; k < kFsWarps; ++k) t += red[k];
-        s_rr = t;
+        a.partials[blockIdx.x] = t;
       }
-      __syncthreads();
+      if (!fs_barrier(a)) return;
+      // ||r||^2: every CTA adds the partials in the same order
+      {
+        double v = 0.0;
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += kFsThreads) v += __ldcg(a.partials + b);
+        v = fs_warp_sum(v);
+        if (lane == 0) red[w] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          double t = 0.0;
+          for (int k = 0; k < kFsWarps; ++k) t += red[k];
+          s_rr = t;
+        }
+        __syncthreads();
+      }
+      rr = s_rr;
     }
-    const double rr = s_rr;
     const bool finite = isfinite(rr);
     const bool conv = finite && rr <= target;
+    if (conv && a.phase == 1) {  // provisional: the resuming launch decides with the final rule
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.col_rr[0] = rr;
+        a.col_iters[0] = it;
+        a.st->iters = it;
+        a.col_done[0] = 2;
+      }
+      return;
+    }
     if (!finite || conv || it >= max_outer) {
       if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.col_done[0] = 1;
@@ -299,7 +322,7 @@ __global__ void __launch_bounds__(kFsThreads) mixed_solve_fused_kernel(FusedArgs
 }  // namespace
 
 cudaError_t mixed_solve_fused(const SpIterArgs& sa, const MixedArgs& ma, int precision, uint32_t* sync,
-                              cudaStream_t s) {
+                              cudaStream_t s, int phase) {
   // the phase input vector is staged in shared memory: n doubles, at most 32 KB
   if (sa.k != 1 || ma.k != 1 || ma.sweeps < 1 || sa.n > 4096) return cudaErrorNotSupported;
   static int max_grid = 0;  // at most one CTA per SM: every CTA is resident with room to spare
@@ -347,6 +370,7 @@ cudaError_t mixed_solve_fused(const SpIterArgs& sa, const MixedArgs& ma, int pre
   a.st = sa.st;
   a.sync = sync;
   a.wait_ns = sa.wait_ns > 0 ? (uint64_t)sa.wait_ns : 1000000000ull;
+  a.phase = phase;
   cudaError_t e = cudaMemsetAsync(sync, 0, 4 * sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
