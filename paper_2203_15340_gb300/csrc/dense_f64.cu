@@ -842,8 +842,20 @@ __global__ void __launch_bounds__(32 * kIterWarps) sp_iter_kernel(SpIterArgs a) 
 }
 
 __global__ void copy_final_kernel(int64_t n, int64_t k, const double* X0, const double* X1,
-                                  const SolveState* st, double* X, int64_t ldx) {
+                                  const SolveState* st, double* X, int64_t ldx, ResultGather g) {
   const double* src = st->cur ? X1 : X0;
+  if (g.out && blockIdx.x == 0 && threadIdx.x < 32) {  // the pass's results, for one copy to the host
+    char* out = static_cast<char*>(g.out);
+    const int t = threadIdx.x;
+    if (t < (int)(sizeof(SolveState) / 4)) reinterpret_cast<uint32_t*>(out + kResSt)[t] = reinterpret_cast<const uint32_t*>(g.st)[t];
+    if (t < g.k) {
+      reinterpret_cast<double*>(out + kResRr)[t] = g.rr[t];
+      reinterpret_cast<double*>(out + kResBn)[t] = g.bn[t];
+      reinterpret_cast<int64_t*>(out + kResIters)[t] = g.iters[t];
+      reinterpret_cast<int64_t*>(out + kResInner)[t] = g.inner[t];
+    }
+    if (t == 0) *reinterpret_cast<unsigned long long*>(out + kResInnerNs) = g.inner_ns ? *g.inner_ns : 0ull;
+  }
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * k;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = (uint32_t)e % (uint32_t)n, c = (uint32_t)e / (uint32_t)n;
@@ -1466,8 +1478,10 @@ cudaError_t sp_iterate_f64(const SpIterArgs& a, cudaStream_t s) {
 }
 
 cudaError_t copy_final_f64(int64_t n, int64_t k, const double* X0, const double* X1, const SolveState* st,
-                           double* X, int64_t ldx, cudaStream_t s) {
-  copy_final_kernel<<<grid_for(n * k, 256), 256, 0, s>>>(n, k, X0, X1, st, X, ldx);
+                           double* X, int64_t ldx, cudaStream_t s, const ResultGather* gather) {
+  ResultGather g = {};
+  if (gather) g = *gather;
+  copy_final_kernel<<<grid_for(n * k, 256), 256, 0, s>>>(n, k, X0, X1, st, X, ldx, g);
   note_launch();
   return cudaGetLastError();
 }

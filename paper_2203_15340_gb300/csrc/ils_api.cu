@@ -56,6 +56,10 @@ struct ils_handle_s {
   int32_t* picks = nullptr;      // diagnostic pick record (ils_record_picks), caller's memory
   int64_t picks_cap = 0;
   unsigned long long* inner_ns = nullptr;  // device time of chain 0 (globaltimer ns)
+  char* res = nullptr;                     // the pass's results gathered for one copy (kResBytes)
+  float* Hh = nullptr;                     // H row-scaled in double-FP32 form (one-cluster solve)
+  float* Hl = nullptr;
+  int32_t* He = nullptr;
   unsigned long long* h_inner_ns = nullptr;
   // estimates (options.estimate): [0] lambda_min(H), [1] lambda_max(H), [2] rho, [3] kappa,
   // [4] 1 / kappa^2 (the tolerance scale of ILS_STOP_ERR_BOUND), [5] Lanczos steps (H),
@@ -247,6 +251,7 @@ void carve(ils_handle h, Carver& c, size_t work_elems) {
   h->alias_prob = c.take<double>(alias ? (size_t)h->n : 1);
   h->alias_idx = c.take<int32_t>(alias ? (size_t)h->n : 1);
   h->inner_ns = c.take<unsigned long long>(1);
+  h->res = c.take<char>(kResBytes);
   h->est = c.take<double>(16);
   h->lz_work = c.take<float>(h->mf && h->opt.estimate ? lz_mf_work_floats(h->n) + (size_t)h->n * h->n : 1);
   if (h->mf) {
@@ -270,6 +275,11 @@ void carve(ils_handle h, Carver& c, size_t work_elems) {
     h->c32 = c.take<float>(nk);
     h->d32a = c.take<float>(nk);
     h->d32b = c.take<float>(nk);
+    if (h->opt.method == ILS_SP && !h->mf && !h->sparse && h->n <= kClusterSolveMaxN) {
+      h->Hh = c.take<float>(nn);
+      h->Hl = c.take<float>(nn);
+      h->He = c.take<int32_t>((size_t)h->n);
+    }
   }
   if (h->opt.gram == ILS_GRAM_SPLIT) {
     GramSplitWork w1 = gram_split_work(h->p, h->n), w2 = gram_split_work(h->q, h->n);
@@ -518,6 +528,7 @@ ils_status compute_products(ils_handle h) {
   const int64_t n = h->n;
   h->l64_valid = true;
   ILS_CK(axpby_mat_f64(n, 1.0, h->G1, -1.0, h->G2, h->H, s));
+  if (h->Hh) ILS_CK(split_rows_df(n, h->H, h->Hh, h->Hl, h->He, s));
   // Cholesky of Abar1; the explicit inverse of Alg. 1 step 2 is formed from it.
   ILS_CK(cudaMemcpyAsync(h->L, h->G1, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, s));
   ILS_CK(cudaMemsetAsync(h->dstatus, 0, sizeof(int32_t), s));
@@ -618,6 +629,7 @@ ils_status compute_setup_overlap(ils_handle h, const double* src, int64_t lda_sr
     ILS_CK(cudaStreamWaitEvent(t, h->ev_g1, 0));
     ILS_CK(cudaStreamWaitEvent(t, h->ev_g2, 0));
     ILS_CK(diff_mat_f64_f32(n, h->G1, h->G2, h->H, h->H32, t));  // H = Abar1 - Abar2, and in FP32
+    if (h->Hh) ILS_CK(split_rows_df(n, h->H, h->Hh, h->Hl, h->He, t));
     ILS_CK(cudaEventRecord(h->ev_hd, t));
     // The SPD test of H runs on beside the rest of the setup and the next solve; its status
     // is read by setup_check, which synchronizes this stream first.
@@ -651,6 +663,7 @@ ils_status compute_setup_overlap(ils_handle h, const double* src, int64_t lda_sr
     cudaGetLastError();
     ILS_CK(cudaStreamWaitEvent(s, h->ev_g2, 0));
     ILS_CK(diff_mat_f64_f32(n, h->G1, h->G2, h->H, h->H32, s));
+    if (h->Hh) ILS_CK(split_rows_df(n, h->H, h->Hh, h->Hl, h->He, s));
     ILS_CK(lower_to_f32(n, h->G1, h->L32, s));
     ILS_CK(cholesky_f32_pair(n, h->L32, h->H32, reinterpret_cast<float*>(h->inv_diag),
                              reinterpret_cast<float*>(h->inv_diag + n), h->stash32, h->dstatus, h->dstatus2, s));
@@ -880,6 +893,9 @@ ils_status pass_begin(ils_handle h, int64_t c0, int64_t kk, const double* B, int
   ma.X1 = h->X1;
   ma.col_done = h->col_done;
   ma.st = h->st;
+  ma.Hh = h->Hh;
+  ma.Hl = h->Hl;
+  ma.He = h->He;
   h->pa = a;
   h->pra = ra;
   h->pma = ma;
@@ -944,10 +960,9 @@ ils_status pass_end(ils_handle h, double* X, int64_t ldx, ils_info* agg) {
   cudaStream_t s = h->stream;
   const int64_t cap = h->opt.max_outer + 1;
   int64_t chunk = std::max<int64_t>(first_chunk(h), 1);
-  // The answer and the per-column results are enqueued with the first state read, so a
-  // pass that finished within its first chunk costs one host round trip; if it has not,
-  // they are enqueued again once it has.
-  ILS_CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+  // The answer and the per-column results (with the state) are enqueued with the first
+  // state read, so a pass that finished within its first chunk costs one host round trip;
+  // if it has not, they are enqueued again once it has.
   ils_status st = pass_finish_enqueue(h, X, ldx);
   if (st != ILS_OK) return st;
   ILS_CK(cudaStreamSynchronize(s));
@@ -974,13 +989,13 @@ ils_status pass_end(ils_handle h, double* X, int64_t ldx, ils_info* agg) {
 ils_status pass_finish_enqueue(ils_handle h, double* X, int64_t ldx) {
   cudaStream_t s = h->stream;
   const int64_t n = h->n, kk = h->pass_k;
-  ILS_CK(copy_final_f64(n, kk, h->X0, h->X1, h->st, X, ldx, s));
-  ILS_CK(cudaMemcpyAsync(h->h_rr, h->col_rr, sizeof(double) * kk, cudaMemcpyDeviceToHost, s));
-  ILS_CK(cudaMemcpyAsync(h->h_bn, h->bnorm2, sizeof(double) * kk, cudaMemcpyDeviceToHost, s));
-  ILS_CK(cudaMemcpyAsync(h->h_iters, h->col_iters, sizeof(int64_t) * kk, cudaMemcpyDeviceToHost, s));
-  ILS_CK(cudaMemcpyAsync(h->h_inner, h->col_inner, sizeof(int64_t) * kk, cudaMemcpyDeviceToHost, s));
-  if (h->opt.method != ILS_SP && h->pra.chain0 == 0)
-    ILS_CK(cudaMemcpyAsync(h->h_inner_ns, h->inner_ns, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  const bool inner_time = h->opt.method != ILS_SP && h->pra.chain0 == 0;
+  const ResultGather g = {h->st, h->col_rr, h->bnorm2, h->col_iters, h->col_inner,
+                          inner_time ? h->inner_ns : nullptr, h->res, kk};
+  ILS_CK(copy_final_f64(n, kk, h->X0, h->X1, h->st, X, ldx, s, &g));
+  // one copy of the state and every per-column result (the inner time only where it was
+  // measured: the copy stops short of it otherwise)
+  ILS_CK(cudaMemcpyAsync(h->h_st, h->res, inner_time ? kResBytes : kResInnerNs, cudaMemcpyDeviceToHost, s));
   return ILS_OK;
 }
 
@@ -1286,29 +1301,24 @@ ils_status create_handle(ils_handle* out, int64_t m, int64_t n, int64_t p, int64
       return ILS_ERR_CUDA;
     }
   }
-  const size_t host_bytes = align_up(sizeof(SolveState)) + align_up(sizeof(int32_t)) +
-                            4 * align_up(sizeof(double) * kMaxRhsPerPass) + align_up(sizeof(unsigned long long)) +
-                            align_up(8 * sizeof(double));
+  // pinned host block: the gathered results (the device layout of h->res), then the setup
+  // status words and the estimates
+  const size_t host_bytes = align_up(kResBytes) + align_up(sizeof(int32_t) * 64) + align_up(8 * sizeof(double));
   char* hb = nullptr;
   if (cudaMallocHost((void**)&hb, host_bytes) != cudaSuccess) {
     cudaGetLastError();
     free_handle(h);
     return ILS_ERR_OOM;
   }
-  h->h_st = (SolveState*)hb;
-  hb += align_up(sizeof(SolveState));
+  h->h_st = (SolveState*)(hb + kResSt);
+  h->h_rr = (double*)(hb + kResRr);
+  h->h_bn = (double*)(hb + kResBn);
+  h->h_iters = (int64_t*)(hb + kResIters);
+  h->h_inner = (int64_t*)(hb + kResInner);
+  h->h_inner_ns = (unsigned long long*)(hb + kResInnerNs);
+  hb += align_up(kResBytes);
   h->h_status = (int32_t*)hb;
-  hb += align_up(sizeof(int32_t));
-  h->h_rr = (double*)hb;
-  hb += align_up(sizeof(double) * kMaxRhsPerPass);
-  h->h_bn = (double*)hb;
-  hb += align_up(sizeof(double) * kMaxRhsPerPass);
-  h->h_iters = (int64_t*)hb;
-  hb += align_up(sizeof(double) * kMaxRhsPerPass);
-  h->h_inner = (int64_t*)hb;
-  hb += align_up(sizeof(double) * kMaxRhsPerPass);
-  h->h_inner_ns = (unsigned long long*)hb;
-  hb += align_up(sizeof(unsigned long long));
+  hb += align_up(sizeof(int32_t) * 64);
   h->h_est = (double*)hb;
   for (int i = 0; i < 8; ++i) h->h_est[i] = 0.0;
   *h->h_inner_ns = 0ull;

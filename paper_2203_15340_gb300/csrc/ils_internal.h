@@ -24,6 +24,24 @@ struct SolveState {
 
 constexpr int kMaxRhsPerPass = 8;  // right-hand sides carried per iteration launch
 
+// The results of a pass, gathered on the device into one block so that a single copy
+// brings them to the host: the solve state, then per right-hand side ||r||^2, ||bbar||^2,
+// outer and inner iterations, then the inner chain time.  Byte offsets:
+constexpr size_t kResSt = 0, kResRr = 64, kResBn = kResRr + 8 * kMaxRhsPerPass,
+                 kResIters = kResBn + 8 * kMaxRhsPerPass, kResInner = kResIters + 8 * kMaxRhsPerPass,
+                 kResInnerNs = kResInner + 8 * kMaxRhsPerPass, kResBytes = kResInnerNs + 64;
+static_assert(sizeof(SolveState) <= kResRr, "state slot");
+struct ResultGather {
+  const SolveState* st;
+  const double* rr;
+  const double* bn;
+  const int64_t* iters;
+  const int64_t* inner;
+  const unsigned long long* inner_ns;  // may be null
+  void* out;                           // kResBytes on the device
+  int64_t k;
+};
+
 // Record a failed CUDA call for ils_last_error (this thread) and clear CUDA's sticky error
 // state; returns ILS_ERR_CUDA.
 ils_status record_cuda_error(cudaError_t e, const char* what, int line);
@@ -159,7 +177,7 @@ int sp_iterate_blocks(int64_t n);
 
 // Copy the final iterate buffer (chosen on the device) into the user's X.
 cudaError_t copy_final_f64(int64_t n, int64_t k, const double* X0, const double* X1,
-                           const SolveState* st, double* X, int64_t ldx, cudaStream_t s);
+                           const SolveState* st, double* X, int64_t ldx, cudaStream_t s, const ResultGather* gather = nullptr);
 
 // ---- FP64-accurate Gram from exact integer slice products on tcgen05 (gram_split_tc.cu) ----
 struct GramSplitWork {
@@ -244,7 +262,16 @@ struct MixedArgs {
   double* X1;
   const int32_t* col_done;
   SolveState* st;
+  // H row-scaled in double-FP32 form for the one-cluster solve (null: not formed this setup)
+  const float* Hh;
+  const float* Hl;
+  const int32_t* He;
 };
+// H(i, j) = 2^He[i] (Hh + Hl)(i, j) with |Hh + Hl| < 1 and Hl the FP32 rounding of what Hh
+// leaves: about 48 bits of every entry, kept in FP32 so that H x can run on the FP32 pipe
+// (solve_fused.cu).  H is n x n symmetric (row i = column i).
+cudaError_t split_rows_df(int64_t n, const double* H, float* Hh, float* Hl, int32_t* He, cudaStream_t s);
+constexpr int64_t kClusterSolveMaxN = 512;  // the one-cluster solve: 16 CTAs of 32 rows
 // Launch shape of the sweep GEMV: warps per CTA and CTAs (each warp takes whole rows).
 struct SweepShape {
   int32_t warps;

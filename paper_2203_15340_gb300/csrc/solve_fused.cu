@@ -53,6 +53,9 @@ struct FusedArgs {
   uint32_t* sync;        // [0] arrivals, [1] generation, [2] abort
   uint64_t wait_ns;      // bound on each barrier wait
   int32_t phase;         // 0: one launch; 1: provisional (stop on tol2 alone); 2: resume after 1
+  const float* Hh;       // the row-scaled double-FP32 H (split_rows_df), for the cluster kernel
+  const float* Hl;
+  const int32_t* He;
 };
 
 __device__ __forceinline__ uint32_t fs_ld_acquire(const uint32_t* p) {
@@ -319,6 +322,409 @@ __global__ void __launch_bounds__(kFsThreads) mixed_solve_fused_kernel(FusedArgs
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// The same refinement on one thread-block cluster (n <= 512): CTA c of CS = ceil(n / 32)
+// keeps rows 32 c .. 32 c + 31, their H entries in registers (FP64; warp w holds rows
+// 4 w .. 4 w + 3, lane l columns l + 32 u) and their P and B entries in shared memory.
+// After every product each CTA writes its 32 results into every CTA's copy of the vector
+// (distributed shared memory) and the cluster meets at its hardware barrier: no grid
+// barrier, no round trip through L2.  The squared residual is the sum of the CTAs'
+// partials in rank order, the same in every CTA, so all take the same decision.  Nothing
+// here spins: the barrier is the hardware's, and every CTA reaches each one.
+constexpr int kClRows = 32;       // rows per CTA
+constexpr int kClRowsPerWarp = 4;
+constexpr int kClMaxCtas = 16;
+
+__device__ __forceinline__ void cl_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t cl_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cl_smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+// Store v at the same shared-memory address of CTA `rank` of the cluster.
+__device__ __forceinline__ void cl_put(const float* local, uint32_t rank, float v) {
+  uint32_t remote;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(cl_smem_u32(local)), "r"(rank));
+  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(remote), "f"(v) : "memory");
+}
+__device__ __forceinline__ void cl_put(const double* local, uint32_t rank, double v) {
+  uint32_t remote;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(cl_smem_u32(local)), "r"(rank));
+  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(remote), "d"(v) : "memory");
+}
+
+// Lane 0 holds the warp's result v for row i: lanes 0 .. CS-1 write it to every CTA.
+template <typename T>
+__device__ __forceinline__ void cl_broadcast(T* vec, int64_t i, T v, int cs) {
+  const int lane = threadIdx.x & 31;
+  v = __shfl_sync(0xffffffffu, v, 0);
+  if (lane < cs) cl_put(vec + i, (uint32_t)lane, v);
+}
+
+// One FP32 product row block from shared memory: out_q = sum_j M(r_q, j) v_j for the warp's
+// rows r_q (M row-major with stride 32 R, zero past n, as is v); results in every lane.
+template <int R>
+__device__ __forceinline__ void cl_rows_f32(const float* M, const float* v, int w, float (&out)[kClRowsPerWarp]) {
+  const int lane = threadIdx.x & 31;
+  float acc[kClRowsPerWarp];
+#pragma unroll
+  for (int q = 0; q < kClRowsPerWarp; ++q) acc[q] = 0.f;
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    const int j = lane + 32 * u;
+    const float vj = v[j];
+#pragma unroll
+    for (int q = 0; q < kClRowsPerWarp; ++q) acc[q] = fmaf(M[(w * kClRowsPerWarp + q) * 32 * R + j], vj, acc[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < kClRowsPerWarp; ++q) out[q] = fs_warp_sum(acc[q]);
+}
+
+// The refinement's stop decision (shared by both kernels' exits): 0 go on, 1 stop, 2
+// provisional stop (phase 1: the resuming launch decides with the final rule).
+__device__ __forceinline__ int cl_decide(const FusedArgs& a, double rr, double target, int64_t it,
+                                         int64_t max_outer) {
+  const bool finite = isfinite(rr);
+  const bool conv = finite && rr <= target;
+  if (conv && a.phase == 1) return 2;
+  return (!finite || conv || it >= max_outer) ? 1 : 0;
+}
+
+// Rank 0 records the end of the solve (or the provisional stop); every CTA has written its
+// rows of x.
+__device__ __forceinline__ void cl_finish(const FusedArgs& a, int how, double rr, double target, int64_t it) {
+  a.col_rr[0] = rr;
+  a.col_iters[0] = it;
+  a.st->iters = it;
+  if (how == 2) {
+    a.col_done[0] = 2;
+    return;
+  }
+  const bool finite = isfinite(rr);
+  const bool conv = finite && rr <= target;
+  a.col_done[0] = 1;
+  if (!finite) atomicCAS(&a.st->status, 0, (int32_t)ILS_ERR_NONFINITE);
+  else if (!conv) atomicCAS(&a.st->status, 0, (int32_t)ILS_ERR_NO_CONVERGENCE);
+  a.st->done = 1;  // the answer is in x (buffer 0)
+}
+
+// (sh, sl) += p + e, with the rounding error of sh + p kept in sl (a double-FP32 sum)
+__device__ __forceinline__ void df_add(float& sh, float& sl, float p, float e) {
+  const float t = sh + p;
+  const float bp = t - sh;
+  const float err = (sh - (t - bp)) + (p - bp);
+  sh = t;
+  sl += err + e;
+}
+
+// v 2^k, by one multiplication where 2^k is a normal double (exact unless v 2^k is
+// subnormal), else by ldexp.
+__device__ __forceinline__ double times_pow2(double v, int k) {
+  if (k >= -1022 && k <= 1023) return v * __longlong_as_double((long long)(k + 1023) << 52);
+  return ldexp(v, k);
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(cl_smem_u32(dst)), "l"(src), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, int bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(cl_smem_u32(dst)), "l"(src), "r"(bytes)
+               : "memory");
+}
+
+// Rows row0 .. row0 + 31 of the n x n row-major FP32 matrix M into S (stride LD, zero past n
+// and past the last row), by asynchronous copies (16 bytes where n is a multiple of 4).
+template <int LD>
+__device__ __forceinline__ void cl_stage_rows(float* S, const float* M, int64_t n, int64_t row0) {
+  if ((n & 3) == 0 && ((reinterpret_cast<uintptr_t>(M) & 15) == 0)) {
+    for (int e = threadIdx.x; e < kClRows * LD / 4; e += kFsThreads) {
+      const int j = 4 * (e % (LD / 4));
+      const int64_t i = row0 + e / (LD / 4);
+      const int64_t have = (i < n && j < n) ? (n - j < 4 ? n - j : 4) : 0;
+      cp_async16(S + 4 * e, have ? M + i * n + j : M, (int)(4 * have));
+    }
+  } else {
+    for (int e = threadIdx.x; e < kClRows * LD; e += kFsThreads) {
+      const int j = e % LD;
+      const int64_t i = row0 + e / LD;
+      const bool ok = i < n && j < n;
+      cp_async4(S + e, ok ? M + i * n + j : M, ok ? 4 : 0);
+    }
+  }
+}
+
+template <int R>
+__global__ void __launch_bounds__(kFsThreads, 1) mixed_solve_cluster_kernel(FusedArgs a) {
+  constexpr int LD = 32 * R;  // padded length of every vector and matrix row (zero past n)
+  const int64_t n = a.n;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t rank = cl_rank();
+  const int cs = (int)gridDim.x;  // the grid is one cluster
+  const int64_t row0 = (int64_t)rank * kClRows;
+  extern __shared__ __align__(16) double cl_smem[];
+  double* xs = cl_smem;                                     // LD: x (FP64)
+  double* part = xs + LD;                                   // kClMaxCtas partial sums
+  float* vA = reinterpret_cast<float*>(part + kClMaxCtas);  // LD
+  float* vB = vA + LD;                                      // LD
+  float* xh = vB + LD;                                      // LD: x 2^-f, leading FP32 part
+  float* xl = xh + LD;                                      // LD: and the rest
+  float* Ps = xl + LD;                                      // kClRows x LD
+  float* Bs = Ps + kClRows * LD;                            // kClRows x LD
+  __shared__ int redi[kFsWarps];
+  __shared__ float th[kClRows], tl[kClRows];  // the CTA's row results, for warp 0's FP64 tail
+
+  if (*((volatile int32_t*)&a.st->done)) return;  // read before any barrier: the same in every CTA
+  int64_t it = *((volatile int64_t*)&a.st->iters);
+  const int64_t max_outer = a.st->max_outer;
+  const double target = a.tol2 * (a.tol_scale && a.phase != 1 ? *a.tol_scale : 1.0) * a.bnorm2[0];
+  bool resume = a.phase == 2 && *((volatile int32_t*)a.col_done) == 2;
+  // Warp 0 finishes the CTA's rows in FP64, lane l taking row row0 + l: one FP64
+  // instruction for all 32 rows (GB300's FP64 unit is narrow).
+  const int64_t my_row = row0 + lane;
+  const bool my_ok = w == 0 && my_row < n;
+  const double my_b = my_ok ? a.bbar[my_row] : 0.0;
+  const int my_e = my_ok ? a.He[my_row] : 0;
+  if (resume) {  // decide on the kept residual before loading anything
+    const double rr = *((volatile double*)a.col_rr);
+    const int how = cl_decide(a, rr, target, it, max_outer);
+    if (how != 0) {
+      if (rank == 0 && threadIdx.x == 0) cl_finish(a, how, rr, target, it);
+      return;
+    }
+  }
+
+  // this CTA's rows: P and B to shared memory (asynchronous), H (double-FP32) to registers
+  cl_stage_rows<LD>(Ps, a.P32, n, row0);
+  if (!a.bf16) cl_stage_rows<LD>(Bs, a.Bt32, n, row0);
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  if (a.bf16) {
+    for (int e = threadIdx.x; e < kClRows * LD; e += kFsThreads) {
+      const int64_t j = e % LD, i = row0 + e / LD;
+      Bs[e] = (i < n && j < n) ? __bfloat162float(a.Bt16[i * n + j]) : 0.f;
+    }
+  }
+  float hh[kClRowsPerWarp][R], hl[kClRowsPerWarp][R];
+#pragma unroll
+  for (int q = 0; q < kClRowsPerWarp; ++q) {
+    const int64_t i = row0 + w * kClRowsPerWarp + q;
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+      const int64_t j = lane + 32 * u;
+      const bool ok = i < n && j < n;
+      hh[q][u] = ok ? __ldg(a.Hh + i * n + j) : 0.f;
+      hl[q][u] = ok ? __ldg(a.Hl + i * n + j) : 0.f;
+    }
+  }
+  for (int j = threadIdx.x; j < LD; j += kFsThreads) {
+    xs[j] = j < n ? __ldcg(a.x + j) : 0.0;
+    vA[j] = (resume && j < n) ? (float)__ldcg(a.r + j) : 0.f;
+    vB[j] = 0.f;
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  cl_barrier();  // every CTA is running and initialized before any remote store
+
+  for (;;) {
+    double rr;
+    if (resume) {  // r (in vA) and ||r||^2 of this x were left by the provisional launch
+      resume = false;
+      rr = *((volatile double*)a.col_rr);
+    } else {
+      // x = 2^f (xh + xl) with |x 2^-f| < 1 (f from the largest exponent field of x)
+      int m = 0;
+      for (int j = threadIdx.x; j < n; j += kFsThreads)
+        m = max(m, (int)((__double_as_longlong(xs[j]) >> 52) & 0x7FF));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if (lane == 0) redi[w] = m;
+      __syncthreads();
+      m = 0;
+#pragma unroll
+      for (int k = 0; k < kFsWarps; ++k) m = max(m, redi[k]);
+      const int f = (m == 0 || m == 0x7FF) ? 0 : m - 1022;
+      for (int j = threadIdx.x; j < LD; j += kFsThreads) {
+        const double xi = j < n ? times_pow2(xs[j], -f) : 0.0;
+        const float hi = __double2float_rn(xi);
+        xh[j] = hi;
+        xl[j] = __double2float_rn(xi - (double)hi);
+      }
+      __syncthreads();
+      // r = bbar - H x for this CTA's rows, H x in double-FP32 (products split exactly by
+      // an FMA, cross terms in FP32, sums with their rounding errors carried); r to every
+      // CTA's vA, the partial ||r||^2 to part
+#pragma unroll
+      for (int q = 0; q < kClRowsPerWarp; ++q) {
+        float sh = 0.f, sl = 0.f;
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+          const int j = lane + 32 * u;
+          const float bh = xh[j], bl = xl[j];
+          const float p = hh[q][u] * bh;
+          const float e = fmaf(hh[q][u], bl, fmaf(hl[q][u], bh, fmaf(hh[q][u], bh, -p)));
+          df_add(sh, sl, p, e);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const float oh = __shfl_xor_sync(0xffffffffu, sh, o), ol = __shfl_xor_sync(0xffffffffu, sl, o);
+          df_add(sh, sl, oh, ol);
+        }
+        if (lane == 0) {
+          th[w * kClRowsPerWarp + q] = sh;
+          tl[w * kClRowsPerWarp + q] = sl;
+        }
+      }
+      __syncthreads();
+      if (w == 0) {
+        double r = 0.0;
+        if (my_ok) {
+          r = my_b - times_pow2((double)th[lane] + (double)tl[lane], my_e + f);
+          a.r[my_row] = r;
+          const float r32 = (float)r;
+          for (int k = 0; k < cs; ++k) cl_put(vA + my_row, (uint32_t)k, r32);
+        }
+        double rp = r * r;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) rp += __shfl_xor_sync(0xffffffffu, rp, o);
+        rp = __shfl_sync(0xffffffffu, rp, 0);  // one value, the same in every CTA
+        if (lane < cs) cl_put(part + rank, (uint32_t)lane, rp);
+      }
+      cl_barrier();
+      double t = 0.0;
+      for (int k = 0; k < cs; ++k) t += part[k];  // the same order in every CTA
+      rr = t;
+    }
+    const int how = cl_decide(a, rr, target, it, max_outer);
+    if (how != 0) {
+      for (int64_t j = row0 + threadIdx.x; j < n && j < row0 + kClRows; j += kFsThreads) a.x[j] = xs[j];
+      if (rank == 0 && threadIdx.x == 0) cl_finish(a, how, rr, target, it);
+      return;
+    }
+    ++it;
+    // c = d_1 = P r; d_{s+1} = B d_s + c; the last sweep adds d to x and broadcasts x
+    float c[kClRowsPerWarp], o[kClRowsPerWarp];
+    cl_rows_f32<R>(Ps, vA, w, c);
+    const float* vin = vB;
+    for (int sw = 0; sw < a.sweeps; ++sw) {
+      float* vout = (vin == vB) ? vA : vB;  // vA (r) is free once P r is formed
+      if (sw > 0) cl_rows_f32<R>(Bs, vin, w, o);
+      const bool last = sw + 1 == a.sweeps;
+#pragma unroll
+      for (int q = 0; q < kClRowsPerWarp; ++q) {
+        const int64_t i = row0 + w * kClRowsPerWarp + q;
+        const float d = sw > 0 ? o[q] + c[q] : c[q];
+        if (last) {
+          if (lane == 0) th[w * kClRowsPerWarp + q] = d;
+        } else if (i < n) {
+          cl_broadcast(sw == 0 ? vB : vout, i, d, cs);
+        }
+      }
+      if (last) {  // x += d: warp 0, one row per lane, x to every CTA
+        __syncthreads();
+        if (my_ok) {
+          const double xi = xs[my_row] + (double)th[lane];
+          for (int k = 0; k < cs; ++k) cl_put(xs + my_row, (uint32_t)k, xi);
+        }
+      }
+      cl_barrier();
+      if (sw > 0) vin = vout;
+    }
+  }
+}
+
+// H(i, j) = 2^e_i (hh + hl): one CTA per row; e_i from the largest exponent field of row i
+// (integer work), each scaled entry split into its FP32 rounding and the FP32 rounding of
+// the remainder.
+__global__ void split_rows_df_kernel(int64_t n, const double* __restrict__ H, float* __restrict__ Hh,
+                                     float* __restrict__ Hl, int32_t* __restrict__ He) {
+  __shared__ int red[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+    const double* row = H + i * n;
+    int m = 0;
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x)
+      m = max(m, (int)((__double_as_longlong(row[j]) >> 52) & 0x7FF));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) red[w] = m;
+    __syncthreads();
+    m = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) m = max(m, red[k]);
+    const int e = (m == 0 || m == 0x7FF) ? 0 : m - 1022;
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+      const double v = times_pow2(row[j], -e);
+      const float hi = __double2float_rn(v);
+      Hh[i * n + j] = hi;
+      Hl[i * n + j] = __double2float_rn(v - (double)hi);
+    }
+    if (threadIdx.x == 0) He[i] = e;
+    __syncthreads();  // red is reused by the next row
+  }
+}
+
+template <int R>
+cudaError_t launch_cluster_solve_r(const FusedArgs& a, int cs, cudaStream_t s) {
+  constexpr int LD = 32 * R;
+  const size_t smem = sizeof(double) * (LD + kClMaxCtas) + sizeof(float) * (4 * LD + 2 * kClRows * LD);
+  static int checked = 0;  // 1: the cluster fits, -1: it does not (per process)
+  if (checked == 0) {
+    cudaError_t e = cudaFuncSetAttribute(mixed_solve_cluster_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(mixed_solve_cluster_kernel<R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      checked = -1;
+    } else {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(kClMaxCtas, 1, 1);
+      cfg.blockDim = dim3(kFsThreads, 1, 1);
+      cfg.dynamicSmemBytes = smem;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = kClMaxCtas;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      int clusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&clusters, mixed_solve_cluster_kernel<R>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        clusters = 0;
+      }
+      checked = clusters >= 1 ? 1 : -1;
+    }
+  }
+  if (checked < 0) return cudaErrorNotSupported;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)cs, 1, 1);
+  cfg.blockDim = dim3(kFsThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, mixed_solve_cluster_kernel<R>, a);
+  note_launch();
+  return e;
+}
+
+// One cluster of ceil(n / 32) CTAs (n <= 512), or cudaErrorNotSupported (nothing enqueued).
+cudaError_t launch_cluster_solve(const FusedArgs& a, cudaStream_t s) {
+  const int cs = (int)((a.n + kClRows - 1) / kClRows);
+  if (a.n <= 128) return launch_cluster_solve_r<4>(a, cs, s);
+  if (a.n <= 256) return launch_cluster_solve_r<8>(a, cs, s);
+  return launch_cluster_solve_r<16>(a, cs, s);
+}
+
 }  // namespace
 
 cudaError_t mixed_solve_fused(const SpIterArgs& sa, const MixedArgs& ma, int precision, uint32_t* sync,
@@ -371,6 +777,15 @@ cudaError_t mixed_solve_fused(const SpIterArgs& sa, const MixedArgs& ma, int pre
   a.sync = sync;
   a.wait_ns = sa.wait_ns > 0 ? (uint64_t)sa.wait_ns : 1000000000ull;
   a.phase = phase;
+  // n <= 512 and no wait limit of the caller's (a limit asks for the bounded grid barrier):
+  // the cluster-resident kernel
+  a.Hh = ma.Hh;
+  a.Hl = ma.Hl;
+  a.He = ma.He;
+  if (sa.n <= (int64_t)kClRows * kClMaxCtas && sa.wait_ns <= 0 && ma.Hh && ma.Hl && ma.He) {
+    const cudaError_t ec = launch_cluster_solve(a, s);
+    if (ec != cudaErrorNotSupported) return ec;
+  }
   cudaError_t e = cudaMemsetAsync(sync, 0, 4 * sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -391,6 +806,13 @@ cudaError_t mixed_solve_fused(const SpIterArgs& sa, const MixedArgs& ma, int pre
   }
   note_launch();
   return e;
+}
+
+cudaError_t split_rows_df(int64_t n, const double* H, float* Hh, float* Hl, int32_t* He, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  split_rows_df_kernel<<<(unsigned)std::min<int64_t>(n, 4096), 256, 0, s>>>(n, H, Hh, Hl, He);
+  note_launch();
+  return cudaGetLastError();
 }
 
 }  // namespace ils
