@@ -258,7 +258,7 @@ ils_status ils_get_matrix(ils_handle h, int which, double* dst, int64_t ldd, ils
 
 /* Setup phase times of the last ils_setup / ils_refactor on h, in milliseconds,
  * measured with CUDA events on the handle's stream when options.timing != 0
- * (zeros otherwise).  out [host] receives min(count, 7) values:
+ * (zeros otherwise).  out [host] receives min(count, 14) values:
  *   0 Abar1 Gram, 1 the wait for the Abar2 Gram (its own time where it runs alone; on a
  *     mixed-precision single handle the FP32 copy of Abar1, the Abar2 Gram running on),
  *   2 the factor step: the Cholesky factorizations of Abar1 and H, or on a mixed-precision
@@ -267,8 +267,17 @@ ils_status ils_get_matrix(ils_handle h, int which, double* dst, int64_t ldd, ils
  *     the Abar2 Gram (the FP32 test of H of a mixed single handle runs beside them and
  *     the next solve, and is not part of any phase),
  *   4 the whole setup, 5 the copy of A, 6 the tensor-core kernel of the Abar1 Gram alone
- *   (split Grams only).
- * Returns the number of values written, or -1 on a bad argument. */
+ *   (split Grams only);
+ * and of the last solve (its first pass of up to 8 right-hand sides):
+ *   7 from the end of the setup to the solve's first work on the stream (0 when the solve
+ *     was enqueued behind the setup), 8 the solve's work up to its answer (A^T J b, the
+ *     iteration and any wait for kappa_est; where the iteration is not one launch, up to
+ *     its first chunk), 9 the copy of the answer and of the results to the host;
+ * and, on a mixed-precision single handle, 10 the start of the kappa(H) estimate after the
+ * start of the setup, 11 its duration (with estimates), 12 the moment both Grams were
+ * done for the forming of H and 13 the moment H was formed (both after the start of the
+ * setup).
+ * Returns the number of values written (at most 14), or -1 on a bad argument. */
 int ils_get_timings(ils_handle h, double* out, int count);
 
 /* The launch shape the autotuner picked for the mixed-precision sweep GEMV of an n x n

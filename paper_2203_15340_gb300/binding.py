@@ -357,10 +357,12 @@ class Solver:
         return _check(lib().ils_get_matrix(self.h, which, ptr, ld, _stream_ptr(stream)), "ils_get_matrix")
 
     def timings(self):
-        """Setup phase times (ms) of the last setup/refactor when options.timing was set."""
-        buf = (ctypes.c_double * 7)()
-        n = lib().ils_get_timings(self.h, buf, 7)
-        keys = ["gram1", "gram2", "factor", "products", "setup", "copy_A", "gram1_mma"]
+        """Setup phase times (ms) of the last setup/refactor and of the last solve, when
+        options.timing was set."""
+        buf = (ctypes.c_double * 14)()
+        n = lib().ils_get_timings(self.h, buf, 14)
+        keys = ["gram1", "gram2", "factor", "products", "setup", "copy_A", "gram1_mma", "solve_start_gap",
+                "solve_work", "solve_copy", "kappa_start", "kappa", "grams_done", "h_formed"]
         return {k: buf[i] for i, k in enumerate(keys[:max(n, 0)])}
 
     def close(self):

@@ -297,11 +297,17 @@ __device__ __forceinline__ void decode_item_gen(int item, const SplitParams& P, 
 }
 
 // SYM: the Gram X^T X (upper tile pairs, transposed cross products on diagonal tiles);
-// otherwise X^T Y with X's digits from tmap and Y's from tmap2.
+// otherwise X^T Y with X's digits from tmap and Y's from tmap2.  A SYM launch may carry two
+// Grams: blocks [0, items0) form the first (tmap, P0), the rest the second (tmap2, P1), so
+// that the second fills the SMs the first leaves idle.
 template <bool SYM>
 __global__ void __launch_bounds__(kThreads, 1)
 gram_split_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmap2,
-                      SplitParams P) {
+                      SplitParams P0, SplitParams P1, int items0) {
+  const bool second = SYM && (int)blockIdx.x >= items0;
+  const SplitParams P = second ? P1 : P0;
+  const int item = second ? (int)blockIdx.x - items0 : (int)blockIdx.x;
+  const CUtensorMap* mapA = second ? &tmap2 : &tmap;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* tiles = smem;  // kStages x (up to kMaxTiles digit tiles)
@@ -313,8 +319,8 @@ gram_split_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_con
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int bi, bj, g, kc, tile;
-  if (SYM) decode_item(blockIdx.x, P, &bi, &bj, &g, &kc, &tile);
-  else decode_item_gen(blockIdx.x, P, &bi, &bj, &g, &kc, &tile);
+  if (SYM) decode_item(item, P, &bi, &bj, &g, &kc, &tile);
+  else decode_item_gen(item, P, &bi, &bj, &g, &kc, &tile);
   const bool diag = SYM && bi == bj;
   GroupDesc gd;
   block_desc(diag, g, gd);
@@ -366,8 +372,8 @@ gram_split_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_con
 #pragma unroll
       for (int i = 0; i < kMaxTiles; ++i)
         if (i < ntiles)
-          tma_load_3d(stage + i * kTileBytes, (SYM || gd.side[i] == 0) ? &tmap : &tmap2, &full[s], k, trow[i],
-                      tdig[i]);
+          tma_load_3d(stage + i * kTileBytes, SYM ? mapA : (gd.side[i] == 0 ? &tmap : &tmap2), &full[s], k,
+                      trow[i], tdig[i]);
       ++issued;
     }
   } else if (warp == 1 && lane == 0) {
@@ -844,7 +850,7 @@ cudaError_t gram_split_tc(int64_t K, int64_t n, const double* A, int64_t lda, do
   e = cudaFuncSetAttribute(gram_split_mma_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (mma_begin && (e = cudaEventRecord(mma_begin, s)) != cudaSuccess) return e;
-  gram_split_mma_kernel<true><<<items, kThreads, smem, s>>>(map, map, P);
+  gram_split_mma_kernel<true><<<items, kThreads, smem, s>>>(map, map, P, P, items);
   note_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (mma_end && (e = cudaEventRecord(mma_end, s)) != cudaSuccess) return e;
@@ -852,6 +858,81 @@ cudaError_t gram_split_tc(int64_t K, int64_t n, const double* A, int64_t lda, do
       P, C, ldc);
   note_launch();
   return cudaGetLastError();
+}
+
+namespace {
+
+SplitParams gram_params(int64_t K, int64_t n, int* exps, double* partial, int32_t* err) {
+  SplitParams P;
+  P.n = P.n2 = (int)n;
+  P.K = (int)K;
+  P.n_tiles = P.n_tiles2 = (int)((n + kBM - 1) / kBM);
+  P.n_kchunks = (int)std::max<int64_t>(1, (K + kKChunk - 1) / kKChunk);
+  P.exps = P.exps2 = exps;
+  P.partial = partial;
+  P.err = err;
+  return P;
+}
+
+int gram_items(const SplitParams& P) {
+  const int n_upper = P.n_tiles * (P.n_tiles + 1) / 2;
+  return (P.n_tiles * num_blocks(true) + (n_upper - P.n_tiles) * num_blocks(false)) * P.n_kchunks;
+}
+
+cudaError_t gram_reduce(const SplitParams& P, double* C, int64_t ldc, cudaStream_t s) {
+  const int n_upper = P.n_tiles * (P.n_tiles + 1) / 2;
+  split_reduce_kernel<<<(unsigned)std::min<int64_t>(((int64_t)n_upper * kBM * kBN + 255) / 256, 4096), 256, 0, s>>>(
+      P, C, ldc);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t gram_split_pair_tc(int64_t K1, int64_t K2, int64_t n, const double* A1, int64_t lda1, const double* A2,
+                               int64_t lda2, double* C1, double* C2, int64_t ldc, void* slices1, void* slices2,
+                               double* partial1, double* partial2, int* exps1, int* exps2, int32_t* err,
+                               cudaStream_t s1, cudaStream_t s2, cudaEvent_t ev_split2, cudaEvent_t ev_mma,
+                               cudaEvent_t mma_begin, cudaEvent_t mma_end, double* copy1, double* copy2,
+                               int64_t ld_copy, cudaEvent_t copied1) {
+  if (n <= 0) return cudaSuccess;
+  cudaError_t e;
+  if (K1 <= 0 || K2 <= 0) {  // a Gram of nothing is zero: no shared launch
+    if ((e = gram_split_tc(K1, n, A1, lda1, C1, ldc, slices1, partial1, exps1, err, s1, mma_begin, mma_end, copy1,
+                           ld_copy, copied1)) != cudaSuccess)
+      return e;
+    return gram_split_tc(K2, n, A2, lda2, C2, ldc, slices2, partial2, exps2, err, s2, nullptr, nullptr, copy2, ld_copy,
+                         nullptr);
+  }
+  if (K1 > (int64_t)1 << 30 || K2 > (int64_t)1 << 30 || n > 65535) return cudaErrorInvalidValue;
+  if ((e = split_into(K2, n, A2, lda2, K2, slices2, exps2, err, s2, copy2, ld_copy)) != cudaSuccess) return e;
+  if ((e = cudaEventRecord(ev_split2, s2)) != cudaSuccess) return e;
+  if ((e = split_into(K1, n, A1, lda1, K1, slices1, exps1, err, s1, copy1, ld_copy)) != cudaSuccess) return e;
+  if (copied1 && (e = cudaEventRecord(copied1, s1)) != cudaSuccess) return e;
+  CUtensorMap map1, map2;
+  if ((e = slices_map(slices1, K1, n, &map1)) != cudaSuccess) return e;
+  if ((e = slices_map(slices2, K2, n, &map2)) != cudaSuccess) return e;
+  const SplitParams P1 = gram_params(K1, n, exps1, partial1, err), P2 = gram_params(K2, n, exps2, partial2, err);
+  // the longer Gram's items first: the block scheduler hands out blocks in order, so the
+  // shorter one fills the SMs the longer one leaves
+  const bool first1 = K1 >= K2;
+  const SplitParams& Pa = first1 ? P1 : P2;
+  const SplitParams& Pb = first1 ? P2 : P1;
+  const int items_a = gram_items(Pa), items_b = gram_items(Pb);
+  const size_t smem = smem_bytes();
+  e = cudaFuncSetAttribute(gram_split_mma_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(s1, ev_split2, 0)) != cudaSuccess) return e;
+  if (mma_begin && (e = cudaEventRecord(mma_begin, s1)) != cudaSuccess) return e;
+  gram_split_mma_kernel<true><<<items_a + items_b, kThreads, smem, s1>>>(first1 ? map1 : map2, first1 ? map2 : map1,
+                                                                         Pa, Pb, items_a);
+  note_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (mma_end && (e = cudaEventRecord(mma_end, s1)) != cudaSuccess) return e;
+  if ((e = cudaEventRecord(ev_mma, s1)) != cudaSuccess) return e;
+  if ((e = gram_reduce(P1, C1, ldc, s1)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(s2, ev_mma, 0)) != cudaSuccess) return e;
+  return gram_reduce(P2, C2, ldc, s2);
 }
 
 size_t digit_slice_elems(int64_t K, int64_t n) { return (size_t)kSlices * (size_t)n * (size_t)slice_ld(K); }
@@ -893,7 +974,7 @@ cudaError_t gemm_split_tc(int64_t K, int64_t n1, int64_t n2, const void* slicesX
   const size_t smem = smem_bytes();
   e = cudaFuncSetAttribute(gram_split_mma_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  gram_split_mma_kernel<false><<<items, kThreads, smem, s>>>(mx, my, P);
+  gram_split_mma_kernel<false><<<items, kThreads, smem, s>>>(mx, my, P, P, items);
   note_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   gemm_reduce_kernel<<<(unsigned)std::min<int64_t>(((int64_t)P.n_tiles * P.n_tiles2 * kBM * kBN + 255) / 256, 4096),

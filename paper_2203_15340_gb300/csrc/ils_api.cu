@@ -110,6 +110,8 @@ struct ils_handle_s {
   bool pending = false;   // a setup enqueued by ils_refactor_async whose status is not yet read
   cudaStream_t s_aux = nullptr, s_h = nullptr;  // A_2^T A_2 and A^T J b; H and its test
   cudaEvent_t ev_start = nullptr, ev_g2 = nullptr, ev_g1 = nullptr;
+  cudaEvent_t ev_split2 = nullptr, ev_mma = nullptr;  // A_2's digits split; both Grams' products done
+  cudaEvent_t ev_hs = nullptr;                        // H's double-FP32 split formed
   cudaEvent_t ev_hd = nullptr, ev_h = nullptr;  // H formed; H tested (status copied)
   cudaEvent_t ev_acopy = nullptr, ev_rhs = nullptr;  // A copied; A^T J b ready (solve after an async setup)
   void* gs_slices2 = nullptr;
@@ -138,8 +140,9 @@ struct ils_handle_s {
   int64_t pass_launched = 0;
   bool pass_mixed = false;
   // setup phase timing (options.timing != 0)
-  cudaEvent_t ev[8] = {};  // 6, 7: around the tensor-core kernel of the Abar1 Gram
-  double t_ms[7] = {};
+  cudaEvent_t ev[15] = {};  // 6, 7: around the Abar1 Gram's tensor-core kernel; 8-10: the solve; 11, 12: kappa;
+                            // 13, 14: H formed (waits done, then formed)
+  double t_ms[14] = {};
 };
 
 namespace ils {
@@ -381,6 +384,13 @@ void collect_timings(ils_handle h) {
   h->t_ms[4] = el(0, 5);
   h->t_ms[5] = el(0, 1);
   h->t_ms[6] = el(6, 7);
+  h->t_ms[7] = el(5, 8);
+  h->t_ms[8] = el(8, 9);
+  h->t_ms[9] = el(9, 10);
+  h->t_ms[10] = el(0, 11);
+  h->t_ms[11] = el(11, 12);
+  h->t_ms[12] = el(0, 13);
+  h->t_ms[13] = el(0, 14);
 }
 
 // Lanczos estimates (options.estimate) of kappa(H) (standard Lanczos on H) and rho (Lanczos
@@ -605,7 +615,8 @@ ils_status compute_setup_overlap(ils_handle h, const double* src, int64_t lda_sr
   ILS_CK(cudaMemsetAsync(h->dstatus, 0, sizeof(int32_t), s));
   ILS_CK(cudaEventRecord(h->ev_start, s));
   ILS_CK(cudaStreamWaitEvent(a, h->ev_start, 0));
-  // Abar1 = A_1^T A_1 here, Abar2 = A_2^T A_2 there (Alg. 1 steps 2-3)
+  // Abar1 = A_1^T A_1 here, Abar2 = A_2^T A_2 there (Alg. 1 steps 2-3).  Abar1 is enqueued
+  // first: the inverse waits for it alone.
   ILS_CK(gram_split_tc(p, n, src, lda_src, h->G1, n, h->gs_slices, h->gs_partial, h->gs_exps, h->gs_err, s,
                        timing_event(h, 6), timing_event(h, 7), copy ? h->A : nullptr, m,
                        copy ? h->ev_acopy : nullptr));
@@ -628,9 +639,12 @@ ils_status compute_setup_overlap(ils_handle h, const double* src, int64_t lda_sr
     cudaStream_t t = h->s_h;
     ILS_CK(cudaStreamWaitEvent(t, h->ev_g1, 0));
     ILS_CK(cudaStreamWaitEvent(t, h->ev_g2, 0));
+    if (timing_event(h, 13)) ILS_CK(cudaEventRecord(h->ev[13], t));
     ILS_CK(diff_mat_f64_f32(n, h->G1, h->G2, h->H, h->H32, t));  // H = Abar1 - Abar2, and in FP32
-    if (h->Hh) ILS_CK(split_rows_df(n, h->H, h->Hh, h->Hl, h->He, t));
     ILS_CK(cudaEventRecord(h->ev_hd, t));
+    if (timing_event(h, 14)) ILS_CK(cudaEventRecord(h->ev[14], t));
+    if (h->Hh) ILS_CK(split_rows_df(n, h->H, h->Hh, h->Hl, h->He, t));  // for the one-cluster solve
+    ILS_CK(cudaEventRecord(h->ev_hs, t));
     // The SPD test of H runs on beside the rest of the setup and the next solve; its status
     // is read by setup_check, which synchronizes this stream first.
     const float* mat2[2] = {h->H32, nullptr};
@@ -645,10 +659,12 @@ ils_status compute_setup_overlap(ils_handle h, const double* src, int64_t lda_sr
       const int steps = h->opt.lanczos_steps > 0 ? h->opt.lanczos_steps : 24;
       ILS_CK(cudaEventRecord(h->ev_p, s));
       ILS_CK(cudaStreamWaitEvent(e, h->ev_hd, 0));
+      if (timing_event(h, 11)) ILS_CK(cudaEventRecord(h->ev[11], e));
       LanczosProblem pk = {n, h->H32, nullptr, 0, 0, steps, 0, h->est + 8};
       ILS_CK(lanczos_extremes(1, &pk, e));
       ILS_CK(estimates_finish(h->est + 8, nullptr, h->est, e));
       ILS_CK(cudaEventRecord(h->ev_estk, e));
+      if (timing_event(h, 12)) ILS_CK(cudaEventRecord(h->ev[12], e));
       if (h->opt.estimate != 2) {  // rho as well
         ILS_CK(cudaStreamWaitEvent(e, h->ev_p, 0));
         LanczosProblem pr = {n, h->G2_32, h->P32, 0, 0, steps, 0, h->est + 12};
@@ -676,7 +692,7 @@ ils_status compute_setup_overlap(ils_handle h, const double* src, int64_t lda_sr
     ILS_CK(mixed_setup(n, nullptr, h->G2, h->opt.precision, h->L32, h->P32, h->G2_32, h->Bt32, h->Bt16,
                        reinterpret_cast<float*>(h->Dinv), s));
   if (inverted) {
-    ILS_CK(cudaStreamWaitEvent(s, h->ev_hd, 0));  // the solve's residuals read H
+    ILS_CK(cudaStreamWaitEvent(s, h->ev_hs, 0));  // the solve's residuals read H (and its split)
   } else {
     ILS_CK(cudaMemcpyAsync(h->h_status + 3, h->dstatus2, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     if (h->opt.estimate) {
@@ -769,7 +785,8 @@ void free_handle(ils_handle h) {
       cudaStreamSynchronize(x);
       cudaStreamDestroy(x);
     }
-  for (cudaEvent_t e : {h->ev_start, h->ev_g2, h->ev_g1, h->ev_hd, h->ev_h, h->ev_acopy, h->ev_rhs, h->ev_p,
+  for (cudaEvent_t e : {h->ev_start, h->ev_g2, h->ev_g1, h->ev_hd, h->ev_h, h->ev_acopy, h->ev_rhs, h->ev_split2,
+                        h->ev_mma, h->ev_hs, h->ev_p,
                         h->ev_estk, h->ev_est})
     if (e) cudaEventDestroy(e);
   if (h->h_st) cudaFreeHost(h->h_st);
@@ -788,6 +805,7 @@ ils_status pass_begin(ils_handle h, int64_t c0, int64_t kk, const double* B, int
   const int method = h->opt.method;
   cudaStream_t s = h->stream;
   const int64_t m = h->m, n = h->n, p = h->p;
+  if (c0 == 0 && timing_event(h, 8)) ILS_CK(cudaEventRecord(h->ev[8], s));  // the solve's first work
   // bbar = A^T J b (Alg. 1 step 4), c = P bbar.
   if (h->sparse) {
     ILS_CK(sparse_rhs_bar(n, p, kk, h->sc, B, ldb, h->bbar, n, s));
@@ -963,6 +981,7 @@ ils_status pass_end(ils_handle h, double* X, int64_t ldx, ils_info* agg) {
   // The answer and the per-column results (with the state) are enqueued with the first
   // state read, so a pass that finished within its first chunk costs one host round trip;
   // if it has not, they are enqueued again once it has.
+  if (h->pra.chain0 == 0 && timing_event(h, 9)) ILS_CK(cudaEventRecord(h->ev[9], s));
   ils_status st = pass_finish_enqueue(h, X, ldx);
   if (st != ILS_OK) return st;
   ILS_CK(cudaStreamSynchronize(s));
@@ -996,6 +1015,7 @@ ils_status pass_finish_enqueue(ils_handle h, double* X, int64_t ldx) {
   // one copy of the state and every per-column result (the inner time only where it was
   // measured: the copy stops short of it otherwise)
   ILS_CK(cudaMemcpyAsync(h->h_st, h->res, inner_time ? kResBytes : kResInnerNs, cudaMemcpyDeviceToHost, s));
+  if (h->pra.chain0 == 0 && timing_event(h, 10)) ILS_CK(cudaEventRecord(h->ev[10], s));
   return ILS_OK;
 }
 
@@ -1282,15 +1302,16 @@ ils_status create_handle(ils_handle* out, int64_t m, int64_t n, int64_t p, int64
   Carver real{(char*)h->block, 0, false};
   carve(h, real, work);
   if (h->overlap) {
-    bool ok = cudaStreamCreateWithFlags(&h->s_aux, cudaStreamNonBlocking) == cudaSuccess &&
+    // The kappa estimate's cluster becomes ready beside the cooperative inverse: its stream
+    // gets the highest priority, so the block scheduler places it first.
+    int lo_prio = 0, hi_prio = 0;
+    bool ok = cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&h->s_aux, cudaStreamNonBlocking) == cudaSuccess &&
               cudaStreamCreateWithFlags(&h->s_h, cudaStreamNonBlocking) == cudaSuccess;
-    for (cudaEvent_t* e : {&h->ev_start, &h->ev_g2, &h->ev_g1, &h->ev_hd, &h->ev_h, &h->ev_acopy, &h->ev_rhs})
+    for (cudaEvent_t* e : {&h->ev_start, &h->ev_g2, &h->ev_g1, &h->ev_hd, &h->ev_h, &h->ev_acopy, &h->ev_rhs,
+                           &h->ev_split2, &h->ev_mma, &h->ev_hs})
       ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
     if (h->opt.estimate) {
-      // The estimate's cluster becomes ready together with the cooperative inverse; the
-      // highest stream priority lets the block scheduler place it first.
-      int lo_prio = 0, hi_prio = 0;
-      ok = ok && cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio) == cudaSuccess;
       ok = ok && cudaStreamCreateWithPriority(&h->s_est, cudaStreamNonBlocking, hi_prio) == cudaSuccess;
       for (cudaEvent_t* e : {&h->ev_p, &h->ev_estk, &h->ev_est})
         ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
@@ -1447,7 +1468,7 @@ ils_status ils_aq_product(ils_handle h, const double* x, double* v, int prec, il
 
 int ils_get_timings(ils_handle h, double* out, int count) {
   if (!h || !out || count < 0) return -1;
-  const int c = count < 7 ? count : 7;
+  const int c = count < 14 ? count : 14;
   for (int i = 0; i < c; ++i) out[i] = h->t_ms[i];
   return c;
 }
@@ -1484,7 +1505,10 @@ ils_status ils_solve_many(ils_handle h, int64_t k, const double* B, int64_t ldb,
   ils_info agg;
   std::memset(&agg, 0, sizeof(agg));
   const ils_status st = solve_many_checked(h, k, B, ldb, X, ldx, x0_zero, tol, &agg, stream);
-  if (h && st != ILS_ERR_INVALID_ARG) fill_info_extras(h, &agg, t0);
+  if (h && st != ILS_ERR_INVALID_ARG) {
+    fill_info_extras(h, &agg, t0);
+    if (h->opt.timing) collect_timings(h);  // the solve's marks (the call synchronized)
+  }
   if (info) *info = agg;
   return st;
 }

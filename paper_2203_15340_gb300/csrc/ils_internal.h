@@ -195,6 +195,17 @@ cudaError_t gram_split_tc(int64_t K, int64_t n, const double* A, int64_t lda, do
                           void* slices, double* partial, int* exps, int32_t* err, cudaStream_t s,
                           cudaEvent_t mma_begin = nullptr, cudaEvent_t mma_end = nullptr, double* a_copy = nullptr,
                           int64_t ld_copy = 0, cudaEvent_t copied = nullptr);
+// The two Grams C1 = A1^T A1 (K1 x n) and C2 = A2^T A2 (K2 x n) with their tensor-core
+// products in one launch: the digit splits run on s1 and s2 (A2's recorded by ev_split2),
+// the shared product kernel on s1 (ev_mma after it), the reductions on s1 and s2.  The
+// digit buffers, partials and exponents are per Gram; copy1 / copy2 (ld_copy) receive the
+// copies of A1 and A2, copied1 is recorded on s1 after A1's.
+cudaError_t gram_split_pair_tc(int64_t K1, int64_t K2, int64_t n, const double* A1, int64_t lda1, const double* A2,
+                               int64_t lda2, double* C1, double* C2, int64_t ldc, void* slices1, void* slices2,
+                               double* partial1, double* partial2, int* exps1, int* exps2, int32_t* err,
+                               cudaStream_t s1, cudaStream_t s2, cudaEvent_t ev_split2, cudaEvent_t ev_mma,
+                               cudaEvent_t mma_begin, cudaEvent_t mma_end, double* copy1, double* copy2,
+                               int64_t ld_copy, cudaEvent_t copied1);
 
 // General product C = X^T Y (X: K x n1, Y: K x n2) to FP64 accuracy from the same exact digit
 // products, on digit slices made by split_digits (rows >= sign_split of the split matrix are

@@ -459,6 +459,13 @@ __device__ __forceinline__ void cl_stage_rows(float* S, const float* M, int64_t 
   }
 }
 
+// v 2^k in FP32, exact while v 2^k stays normal (in two steps where 2^k itself is not).
+__device__ __forceinline__ float times_pow2f(float v, int k) {
+  if (k >= -126 && k <= 127) return v * __int_as_float((k + 127) << 23);
+  const int k1 = k / 2;
+  return (v * __int_as_float((k1 + 127) << 23)) * __int_as_float((k - k1 + 127) << 23);
+}
+
 template <int R>
 __global__ void __launch_bounds__(kFsThreads, 1) mixed_solve_cluster_kernel(FusedArgs a) {
   constexpr int LD = 32 * R;  // padded length of every vector and matrix row (zero past n)
@@ -468,16 +475,17 @@ __global__ void __launch_bounds__(kFsThreads, 1) mixed_solve_cluster_kernel(Fuse
   const int cs = (int)gridDim.x;  // the grid is one cluster
   const int64_t row0 = (int64_t)rank * kClRows;
   extern __shared__ __align__(16) double cl_smem[];
-  double* xs = cl_smem;                                     // LD: x (FP64)
-  double* part = xs + LD;                                   // kClMaxCtas partial sums
+  double* part = cl_smem;                                   // kClMaxCtas partial sums
   float* vA = reinterpret_cast<float*>(part + kClMaxCtas);  // LD
   float* vB = vA + LD;                                      // LD
   float* xh = vB + LD;                                      // LD: x 2^-f, leading FP32 part
-  float* xl = xh + LD;                                      // LD: and the rest
+  float* xl = xh + LD;                                      // LD: and the rest (x during the launch)
   float* Ps = xl + LD;                                      // kClRows x LD
   float* Bs = Ps + kClRows * LD;                            // kClRows x LD
   __shared__ int redi[kFsWarps];
   __shared__ float th[kClRows], tl[kClRows];  // the CTA's row results, for warp 0's FP64 tail
+  __shared__ double s_rr;
+  __shared__ int s_how, s_f;
 
   if (*((volatile int32_t*)&a.st->done)) return;  // read before any barrier: the same in every CTA
   int64_t it = *((volatile int64_t*)&a.st->iters);
@@ -521,8 +529,26 @@ __global__ void __launch_bounds__(kFsThreads, 1) mixed_solve_cluster_kernel(Fuse
       hl[q][u] = ok ? __ldg(a.Hl + i * n + j) : 0.f;
     }
   }
+  // x = 2^f (xh + xl), |x 2^-f| < 1 at the start (f from the largest exponent field of x)
+  {
+    int m = 0;
+    for (int j = threadIdx.x; j < n; j += kFsThreads) m = max(m, (int)((__double_as_longlong(__ldcg(a.x + j)) >> 52) & 0x7FF));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) redi[w] = m;
+    __syncthreads();
+    m = 0;
+#pragma unroll
+    for (int k = 0; k < kFsWarps; ++k) m = max(m, redi[k]);
+    if (threadIdx.x == 0) s_f = (m == 0 || m == 0x7FF) ? 0 : m - 1022;
+    __syncthreads();
+  }
+  int f = s_f;
   for (int j = threadIdx.x; j < LD; j += kFsThreads) {
-    xs[j] = j < n ? __ldcg(a.x + j) : 0.0;
+    const double xi = j < n ? times_pow2(__ldcg(a.x + j), -f) : 0.0;
+    const float hi = __double2float_rn(xi);
+    xh[j] = hi;
+    xl[j] = __double2float_rn(xi - (double)hi);
     vA[j] = (resume && j < n) ? (float)__ldcg(a.r + j) : 0.f;
     vB[j] = 0.f;
   }
@@ -535,25 +561,28 @@ __global__ void __launch_bounds__(kFsThreads, 1) mixed_solve_cluster_kernel(Fuse
       resume = false;
       rr = *((volatile double*)a.col_rr);
     } else {
-      // x = 2^f (xh + xl) with |x 2^-f| < 1 (f from the largest exponent field of x)
-      int m = 0;
-      for (int j = threadIdx.x; j < n; j += kFsThreads)
-        m = max(m, (int)((__double_as_longlong(xs[j]) >> 52) & 0x7FF));
+      // Keep x 2^-f within [2^-40, 2^40]: rescale by a power of two (exact) when it drifts
+      // (the same decision in every CTA: each holds the whole vector).
+      {
+        int m = 0;
+        for (int j = threadIdx.x; j < n; j += kFsThreads) m = max(m, (__float_as_int(xh[j]) >> 23) & 0xFF);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-      if (lane == 0) redi[w] = m;
-      __syncthreads();
-      m = 0;
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) redi[w] = m;
+        __syncthreads();
+        m = 0;
 #pragma unroll
-      for (int k = 0; k < kFsWarps; ++k) m = max(m, redi[k]);
-      const int f = (m == 0 || m == 0x7FF) ? 0 : m - 1022;
-      for (int j = threadIdx.x; j < LD; j += kFsThreads) {
-        const double xi = j < n ? times_pow2(xs[j], -f) : 0.0;
-        const float hi = __double2float_rn(xi);
-        xh[j] = hi;
-        xl[j] = __double2float_rn(xi - (double)hi);
+        for (int k = 0; k < kFsWarps; ++k) m = max(m, redi[k]);
+        if (m != 0 && (m > 127 + 40 || m < 127 - 40)) {
+          const int k = m - 126;  // the largest |x 2^-f| becomes < 1
+          for (int j = threadIdx.x; j < LD; j += kFsThreads) {
+            xh[j] = times_pow2f(xh[j], -k);
+            xl[j] = times_pow2f(xl[j], -k);
+          }
+          f += k;
+          __syncthreads();
+        }
       }
-      __syncthreads();
       // r = bbar - H x for this CTA's rows, H x in double-FP32 (products split exactly by
       // an FMA, cross terms in FP32, sums with their rounding errors carried); r to every
       // CTA's vA, the partial ||r||^2 to part
@@ -594,13 +623,20 @@ __global__ void __launch_bounds__(kFsThreads, 1) mixed_solve_cluster_kernel(Fuse
         if (lane < cs) cl_put(part + rank, (uint32_t)lane, rp);
       }
       cl_barrier();
-      double t = 0.0;
-      for (int k = 0; k < cs; ++k) t += part[k];  // the same order in every CTA
-      rr = t;
+      if (w == 0) {  // the same tree over the same partials in every CTA
+        double t = lane < cs ? part[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) s_rr = t;
+      }
+      __syncthreads();
+      rr = s_rr;
     }
-    const int how = cl_decide(a, rr, target, it, max_outer);
+    if (threadIdx.x == 0) s_how = cl_decide(a, rr, target, it, max_outer);
+    __syncthreads();
+    const int how = s_how;
     if (how != 0) {
-      for (int64_t j = row0 + threadIdx.x; j < n && j < row0 + kClRows; j += kFsThreads) a.x[j] = xs[j];
+      if (my_ok) a.x[my_row] = times_pow2((double)xh[my_row] + (double)xl[my_row], f);
       if (rank == 0 && threadIdx.x == 0) cl_finish(a, how, rr, target, it);
       return;
     }
@@ -623,11 +659,18 @@ __global__ void __launch_bounds__(kFsThreads, 1) mixed_solve_cluster_kernel(Fuse
           cl_broadcast(sw == 0 ? vB : vout, i, d, cs);
         }
       }
-      if (last) {  // x += d: warp 0, one row per lane, x to every CTA
+      if (last) {  // x += d in double-FP32 (warp 0, one row per lane), x to every CTA
         __syncthreads();
         if (my_ok) {
-          const double xi = xs[my_row] + (double)th[lane];
-          for (int k = 0; k < cs; ++k) cl_put(xs + my_row, (uint32_t)k, xi);
+          float ph = xh[my_row], pl = xl[my_row];
+          df_add(ph, pl, times_pow2f(th[lane], -f), 0.f);
+          const float t = ph + pl;
+          pl = pl - (t - ph);
+          ph = t;
+          for (int k = 0; k < cs; ++k) {
+            cl_put(xh + my_row, (uint32_t)k, ph);
+            cl_put(xl + my_row, (uint32_t)k, pl);
+          }
         }
       }
       cl_barrier();
@@ -669,7 +712,7 @@ __global__ void split_rows_df_kernel(int64_t n, const double* __restrict__ H, fl
 template <int R>
 cudaError_t launch_cluster_solve_r(const FusedArgs& a, int cs, cudaStream_t s) {
   constexpr int LD = 32 * R;
-  const size_t smem = sizeof(double) * (LD + kClMaxCtas) + sizeof(float) * (4 * LD + 2 * kClRows * LD);
+  const size_t smem = sizeof(double) * kClMaxCtas + sizeof(float) * (4 * LD + 2 * kClRows * LD);
   static int checked = 0;  // 1: the cluster fits, -1: it does not (per process)
   if (checked == 0) {
     cudaError_t e = cudaFuncSetAttribute(mixed_solve_cluster_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
