@@ -40,7 +40,7 @@ FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (FMA pipe) rate from the profiling
 FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
 # of each kernel as it stands, on the headline step; None once a kernel changes.
-MMA_TRAFFIC_BYTES = 160_445_440 + 8_962_816
+MMA_TRAFFIC_BYTES = None  # the split Gram kernel changed (9 six-bit digits, chunked items): recaptured below
 GJ_TRAFFIC_BYTES = 693_504 + 0
 
 
@@ -675,14 +675,14 @@ def main():
     # handle's stream (options.timing):
     #  * gram_split_mma_kernel (A_1^T A_1): the method's work is p n^2 flop (FP64 Gram);
     #    the kernel executes 2 x 128 x 128 x p BF16 flop per digit product and tile pair
-    #    (55 products on an off-diagonal tile pair, 30 on a diagonal one);
+    #    (45 products on an off-diagonal tile pair, 25 on a diagonal one);
     #  * spd_gj_kernel: P = Abar1^{-1} by FP32 block Gauss-Jordan, n^3 multiply-adds.
     gj_ms = ph["factor"]
     gj_ach = 2.0 * n ** 3 / (gj_ms * 1e-3) / 1e12
     mma_ms = ph["gram1_mma"]
     n_tiles = (n + 127) // 128
     n_upper = n_tiles * (n_tiles + 1) // 2
-    executed = 2.0 * 128 * 128 * p * ((n_upper - n_tiles) * 55 + n_tiles * 30)
+    executed = 2.0 * 128 * 128 * p * ((n_upper - n_tiles) * 45 + n_tiles * 25)
     alg_flops = float(p) * n * n  # the Gram's algorithmic work
     alg_bytes = 8.0 * p * n        # A_1 read once in FP64
     mma_alg = alg_flops / (mma_ms * 1e-3) / 1e12
@@ -694,7 +694,7 @@ def main():
         "work": "p n^2 algorithmic flop per launch (the FP64 Gram); frac_executed counts the BF16 MMA flop run",
         "frac_executed": executed / (mma_ms * 1e-3) / 1e12 / BF16_PEAK_TFLOPS,
         "executed_over_algorithmic": executed / alg_flops,
-        "traffic_ratio": MMA_TRAFFIC_BYTES / alg_bytes,
+        "traffic_ratio": MMA_TRAFFIC_BYTES / alg_bytes if MMA_TRAFFIC_BYTES else None,
         "kernel_ms": mma_ms, "share_of_step": mma_ms / ms_step, "gram_phase_ms": ph["gram1"],
     }
     roof_gj = {

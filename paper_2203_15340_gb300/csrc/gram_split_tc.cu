@@ -5,20 +5,21 @@
 // (Abar1 = A_1^T A_1) and step 3 (Abar2 = A_2^T A_2) are therefore formed from exact
 // integer slice products:
 //
-//   1. Column j of A is scaled by 2^-e_j so that its entries lie in (-1, 1).
-//   2. Each scaled entry is split into S signed digits of beta bits by repeated rounding
-//      to nearest, a = sum_{t=1..S} 2^{-beta t} d_t with integers |d_1| <= 2^beta and
-//      |d_t| <= 2^(beta-1) after; every digit is exact in BF16.  Rounding (not
-//      truncation) leaves the digits' signs independent of the entry's sign, so the split
-//      and the omitted pairs add unbiased errors, and the error of the split is at most
-//      2^{-beta S - 1} times the column scale.
-//   3. For every ordered pair (t, u) with t + u <= S + 1 the tensor cores form
-//      D_t^T D_u with FP32 accumulation.  All partial sums are integers below
-//      K_chunk 2^(2 beta) < 2^24, so the FP32 accumulation is exact.  On the diagonal
-//      tiles of the Gram, D_u^T D_t is the transpose of D_t^T D_u: it is not formed, the
-//      epilogue stores the transpose in its place.
+//   1. Column j of A is scaled by 2^-e_j so that its entries lie in (-1/2, 1/2).
+//   2. Each scaled entry is rounded to a multiple of 2^(-beta S) (beta = 6, S = 9: 53 bits
+//      below the column's largest entry) and written in S balanced digits,
+//      a = sum_{t=1..S} 2^{-beta t} d_t with |d_t| <= 2^(beta-1) = 32; every digit is exact
+//      in BF16.  Rounding (not truncation) leaves the digits' signs independent of the
+//      entry's sign, so the split and the omitted pairs add unbiased errors, and the error
+//      of the split is at most 2^{-beta S - 1} times the column scale.
+//   3. For every ordered pair (t, u) with t + u <= S + 1 (45 pairs) the tensor cores form
+//      D_t^T D_u with FP32 accumulation over K chunks of at most 16384 rows.  All partial
+//      sums are integers of magnitude at most 16384 * 32^2 = 2^24, so the FP32
+//      accumulation is exact.  On the diagonal tiles of the Gram, D_u^T D_t is the
+//      transpose of D_t^T D_u: it is not formed, the epilogue stores the transpose in its
+//      place.
 //   4. The epilogue stores each exact product as it stands (FP32).  A reduction adds the
-//      products of equal t + u exactly as 64-bit integers, joins the 10 group sums (weight
+//      products of equal t + u exactly as 64-bit integers, joins the 9 group sums (weight
 //      2^{e_i + e_j - beta (t + u)}) in exact integer parts and the parts in FP64 with at
 //      most two roundings, in a fixed order (deterministic).
 //
@@ -40,13 +41,13 @@
 namespace ils {
 namespace {
 
-constexpr int kBeta = 5;        // bits per slice
-constexpr int kSlices = 10;     // 50 bits below each column's scale
+constexpr int kBeta = 6;        // bits per slice
+constexpr int kSlices = 9;      // 54 bits below the column scale (53 below its largest entry)
 constexpr int kBM = 128;        // output tile rows (columns of D_t)
 constexpr int kBN = 128;        // output tile cols (columns of D_u)
 constexpr int kBK = 64;         // K per stage: 64 BF16 = one 128-byte swizzle row
 constexpr int kStages = 3;
-constexpr int kKChunk = 16384;  // K rows per work item: 16384 * 32^2 = 2^24 (exact FP32 sums)
+constexpr int kKChunk = 16384;  // K rows per product at most: 16384 * 32^2 = 2^24 (exact FP32 sums)
 constexpr int kThreads = 192;   // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
 constexpr uint32_t kTileBytes = kBM * kBK * 2;  // 16 KB per operand tile
 constexpr uint32_t kStageBytes = 4 * kTileBytes;  // up to four digit tiles per stage
@@ -151,6 +152,11 @@ struct SplitParams {
   int n_tiles;      // ceil(n / 128)
   int n_tiles2;     // ceil(n2 / 128)
   int n_kchunks;
+  int kchunk;       // K rows per chunk (a multiple of 64, at most kKChunk)
+  // Gram launches hand out their items heaviest first: the groups of each MMA cost
+  // (1-4 N=128 units), diagonal (gd_*) and off-diagonal (go_*) tile pairs
+  int8_t nd_c[5], no_c[5];       // groups of cost c
+  int8_t gd_order[32], go_order[32];  // group ids, by cost from 4 down to 1
   const int* exps;  // per-column exponents e_j of X (device)
   const int* exps2; // of Y
   double* partial;  // [tile][product slot][K chunk][128][128] exact products, FP32 bit patterns
@@ -165,10 +171,9 @@ struct SplitParams {
 // the transpose of (t, u), so only blocks with a <= b are formed, and inside a block
 // with a = b only t <= u (its two tiles serve as both operands); the epilogue stores each
 // cross product a second time, transposed, as the product (u, t).
-constexpr int kHalf = kSlices / 2;
+constexpr int kHalf = (kSlices + 1) / 2;  // the last block holds digit S alone when S is odd
 constexpr int kMaxTiles = 4;
 constexpr int kMaxProd = 4;
-static_assert(kSlices % 2 == 0, "digit blocks pair the slices");
 
 struct GroupDesc {
   int ntiles, nprod;
@@ -195,13 +200,15 @@ __host__ __device__ inline void block_desc(bool diag, int g, GroupDesc& d) {
       GroupDesc cur = {};
       cur.slot0 = slot;
       const bool same = diag && a == b;
+      // stage slots 0, 1: digits 2a-1, 2a (A side); 2, 3: digits 2b-1, 2b (B side); a digit
+      // past S (the odd last block) is 0: its slot is not loaded
       cur.ntiles = same ? 2 : 4;
       cur.digit[0] = 2 * a - 1;
-      cur.digit[1] = 2 * a;
+      cur.digit[1] = 2 * a <= kSlices ? 2 * a : 0;
       cur.side[0] = cur.side[1] = 0;
       if (!same) {
         cur.digit[2] = 2 * b - 1;
-        cur.digit[3] = 2 * b;
+        cur.digit[3] = 2 * b <= kSlices ? 2 * b : 0;
         cur.side[2] = cur.side[3] = 1;
       }
       cur.nprod = 0;
@@ -210,7 +217,7 @@ __host__ __device__ inline void block_desc(bool diag, int g, GroupDesc& d) {
         cur.jmask[i] = 0;
         for (int j = 0; j < 2; ++j) {
           const int t = 2 * a - 1 + i, u = 2 * b - 1 + j;
-          if (t + u > kSlices + 1 || (same && t > u)) continue;
+          if (t > kSlices || u > kSlices || t + u > kSlices + 1 || (same && t > u)) continue;
           cur.ia[cur.nprod] = i;
           cur.ib[cur.nprod] = cur.b0 + j;
           cur.t[cur.nprod] = t;
@@ -251,34 +258,51 @@ __host__ __device__ inline int pair_slot(int t, int u) {
   return p + (u - 1);
 }
 
-// Work item -> (K chunk, upper tile pair, group).  Items of one K chunk run together;
-// inside a chunk the upper tile pairs go in row-major order (bi <= bj), each with its
-// groups.
+// MMA cost of a group in N = 128 units: per A tile, 2 for an N = 256 pair, 1 for one product.
+__host__ __device__ inline int group_cost(bool diag, int g) {
+  GroupDesc d;
+  block_desc(diag, g, d);
+  int c = 0;
+  for (int i = 0; i < 2; ++i) c += d.jmask[i] == 3 ? 2 : (d.jmask[i] ? 1 : 0);
+  return c;
+}
+
+// Work item -> (K chunk, upper tile pair, group), heaviest groups first (the block
+// scheduler hands out blocks in order, so the light ones fill in at the end).  Within a
+// cost class: K chunk, then the diagonal tile pairs, then the off-diagonal ones (row-major,
+// bi < bj), each with its groups of that cost.
 __device__ __forceinline__ void decode_item(int item, const SplitParams& P, int* bi, int* bj, int* g, int* kc,
                                             int* tile_out) {
-  const int nd = num_blocks(true), no = num_blocks(false);
-  const int n_upper = P.n_tiles * (P.n_tiles + 1) / 2;
-  const int per_chunk = P.n_tiles * nd + (n_upper - P.n_tiles) * no;
-  *kc = item / per_chunk;
-  int rest = item % per_chunk;
-  int r = 0, tile = 0;
-  for (;;) {
-    const int row_items = nd + (P.n_tiles - r - 1) * no;
-    if (rest < row_items) break;
-    rest -= row_items;
-    tile += P.n_tiles - r;
-    ++r;
+  const int n_off = P.n_tiles * (P.n_tiles - 1) / 2;
+  int rest = item, od = 0, oo = 0;
+  int c = 4;
+  for (; c >= 1; --c) {
+    const int per_kc = P.n_tiles * P.nd_c[c] + n_off * P.no_c[c];
+    if (rest < per_kc * P.n_kchunks) break;
+    rest -= per_kc * P.n_kchunks;
+    od += P.nd_c[c];
+    oo += P.no_c[c];
   }
-  *bi = r;
-  if (rest < nd) {
-    *bj = r;
-    *g = rest;
+  const int per_kc = P.n_tiles * P.nd_c[c] + n_off * P.no_c[c];
+  *kc = rest / per_kc;
+  rest %= per_kc;
+  if (rest < P.n_tiles * P.nd_c[c]) {
+    *bi = *bj = rest / P.nd_c[c];
+    *g = P.gd_order[od + rest % P.nd_c[c]];
   } else {
-    rest -= nd;
-    *bj = r + 1 + rest / no;
-    *g = rest % no;
+    rest -= P.n_tiles * P.nd_c[c];
+    int off = rest / P.no_c[c];
+    *g = P.go_order[oo + rest % P.no_c[c]];
+    int r = 0;
+    while (off >= P.n_tiles - r - 1) {
+      off -= P.n_tiles - r - 1;
+      ++r;
+    }
+    *bi = r;
+    *bj = r + 1 + off;
   }
-  *tile_out = tile + (*bj - r);
+  // upper tile pairs row-major (bi <= bj)
+  *tile_out = *bi * P.n_tiles - *bi * (*bi - 1) / 2 + (*bj - *bi);
 }
 
 // General product X^T Y: item -> (K chunk, tile pair (bi, bj) row-major over n_tiles x
@@ -324,8 +348,8 @@ gram_split_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_con
   const bool diag = SYM && bi == bj;
   GroupDesc gd;
   block_desc(diag, g, gd);
-  const int k_begin = kc * kKChunk;
-  const int k_end = min(P.K, k_begin + kKChunk);
+  const int k_begin = kc * P.kchunk;
+  const int k_end = min(P.K, k_begin + P.kchunk);
   const int nk = (k_end - k_begin + kBK - 1) / kBK;
 
   if (threadIdx.x == 0) {
@@ -357,6 +381,8 @@ gram_split_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_con
       tdig[i] = gd.digit[i] - 1;
     }
     const int ntiles = gd.ntiles;
+    int loaded = 0;  // tiles of existing digits (a digit past S is 0: not loaded, never read)
+    for (int i = 0; i < ntiles; ++i) loaded += gd.digit[i] != 0;
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % kStages;
       const uint32_t ph = (uint32_t)(kb / kStages) & 1u;
@@ -367,11 +393,11 @@ gram_split_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_con
       }
       if (*((volatile int*)&s_abort)) break;
       uint8_t* stage = tiles + (size_t)s * kStageBytes;
-      mbar_expect_tx(&full[s], (uint32_t)ntiles * kTileBytes);
+      mbar_expect_tx(&full[s], (uint32_t)loaded * kTileBytes);
       const int k = k_begin + kb * kBK;
 #pragma unroll
       for (int i = 0; i < kMaxTiles; ++i)
-        if (i < ntiles)
+        if (i < ntiles && gd.digit[i] != 0)
           tma_load_3d(stage + i * kTileBytes, SYM ? mapA : (gd.side[i] == 0 ? &tmap : &tmap2), &full[s], k,
                       trow[i], tdig[i]);
       ++issued;
@@ -459,11 +485,12 @@ gram_split_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_con
 }
 
 __device__ __forceinline__ int exponent_of_field(int m) {
-  // A normal value with exponent field f lies in [2^(f-1023), 2^(f-1022)).
-  return (m == 0 || m == 0x7FF) ? 0 : m - 1022;
+  // A normal value with exponent field f lies in [2^(f-1023), 2^(f-1022)): with e = f - 1021
+  // the column scaled by 2^-e lies in (-1/2, 1/2), which keeps the top digit within 32.
+  return (m == 0 || m == 0x7FF) ? 0 : m - 1021;
 }
 
-// Per-column exponent e_j with max_r |A(r,j)| < 2^e_j (0 for a zero column), read from the
+// Per-column exponent e_j with max_r |A(r,j)| < 2^(e_j - 1) (0 for a zero column), read from the
 // exponent fields of the FP64 bit patterns (integer work only).
 __global__ void column_exponent_kernel(int K, int n, const double* __restrict__ A, int64_t lda, int* __restrict__ exps) {
   const int j = blockIdx.x;
@@ -501,7 +528,8 @@ __device__ __forceinline__ long long split_value(long long bits, int ej, bool ne
   }
   if (f == 0) return 0;  // subnormals are below 2^-1022 and round to 0 at 50 bits
   const unsigned long long mant = (unsigned long long)(bits & 0xFFFFFFFFFFFFFll) | (1ull << 52);
-  // value = mant 2^(f - 1075); V = mant 2^(f - 1075 + kBeta*kSlices - e_j), rounded
+  // value = mant 2^(f - 1075); V = mant 2^(f - 1075 + kBeta*kSlices - e_j), rounded, with
+  // |V| <= 2^(kBeta*kSlices - 1) as |a| < 2^(e_j - 1)
   const int sh = 1075 - f - kBeta * kSlices + ej;
   if (sh >= 64) return 0;
   const unsigned long long half = (sh > 0) ? (1ull << (sh - 1)) : 0ull;
@@ -510,9 +538,9 @@ __device__ __forceinline__ long long split_value(long long bits, int ej, bool ne
 }
 
 // The digits of four consecutive rows r0 .. r0 + 3 of column j: one 8-byte store per slice.
-// Adding C = 16 (1 + 32 + ... + 32^(S-2)) turns the balanced digits d_t in [-16, 15] of
-// V into the plain base-32 digits d_t + 16 of W = V + C, and W >> 5 (S - 1) is the top
-// digit; so each digit is one 5-bit field of W.  A small integer u becomes its FP32 value
+// Adding C = 32 (1 + 64 + ... + 64^(S-2)) turns the balanced digits d_t in [-32, 31] of
+// V into the plain base-64 digits d_t + 32 of W = V + C, and W >> 6 (S - 1) is the top
+// digit; so each digit is one 6-bit field of W.  A small integer u becomes its FP32 value
 // by one integer and one FP32 addition (the bit pattern of 1.5 2^23 + u, minus 1.5 2^23),
 // and, having at most 7 significant bits, its BF16 pattern is the float's upper half.
 // This keeps the split off the conversion pipe (a quarter of the ALU rate).
@@ -522,8 +550,8 @@ __device__ __forceinline__ uint32_t small_int_bf16_bits(int u, float bias) {
 
 __device__ __forceinline__ void store_digits4(const long long (&V)[4], __nv_bfloat16* __restrict__ D, int64_t ldk,
                                               int n, int j, int64_t r0) {
-  constexpr long long kC = 16ll * ((1ll << (kBeta * (kSlices - 1))) - 1) / ((1ll << kBeta) - 1);
-  static_assert(kBeta == 5, "five-bit digit fields");
+  constexpr int kHalfBase = 1 << (kBeta - 1);  // 32: balanced digits lie in [-32, 31]
+  constexpr long long kC = kHalfBase * ((1ll << (kBeta * (kSlices - 1))) - 1) / ((1ll << kBeta) - 1);
   long long W[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) W[i] = V[i] + kC;
@@ -534,8 +562,8 @@ __device__ __forceinline__ void store_digits4(const long long (&V)[4], __nv_bflo
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       if (t < kSlices - 1) {
-        const int u = (int)((unsigned long long)W[i] >> (kBeta * t)) & 31;  // d_t + 16
-        h[i] = small_int_bf16_bits(u, 12582912.0f + 16.0f);
+        const int u = (int)((unsigned long long)W[i] >> (kBeta * t)) & ((1 << kBeta) - 1);  // d_t + 32
+        h[i] = small_int_bf16_bits(u, 12582912.0f + (float)kHalfBase);
       } else {
         const int top = (int)(W[i] >> (kBeta * t));  // |top| <= 32
         h[i] = small_int_bf16_bits(top + 64, 12582912.0f + 64.0f);
@@ -645,11 +673,11 @@ __global__ void __launch_bounds__(256) exponent_split_cluster_kernel(int K, int6
 constexpr int kScales = kSlices;  // t + u = 2 .. S + 1
 
 // Sum_g V[g] 2^(e - beta (g + 2)) for the exact integer group sums V[g] (g = t + u - 2).
-// Groups are joined four at a time by exact int64 Horner steps (each part stays below 2^53
-// for up to 1024 K chunks, so its conversion to FP64 is exact), then the parts by two
+// Groups are joined three at a time by exact int64 Horner steps (each part stays below 2^53
+// for up to 8192 K chunks, so its conversion to FP64 is exact), then the parts by two
 // FMAs and one ldexp: at most two roundings, and a handful of FP64 instructions instead of
 // one conversion, scaling and addition per group (the FP64 pipe is GB300's scarce unit).
-constexpr int kPartLen = 4;
+constexpr int kPartLen = 3;
 constexpr int kParts = (kScales + kPartLen - 1) / kPartLen;
 
 __device__ __forceinline__ double combine_groups(const long long (&V)[kScales], int e) {
@@ -755,12 +783,72 @@ size_t smem_bytes() { return 1024 + (size_t)kStages * kStageBytes + (2 * kStages
 
 }  // namespace
 
+namespace {
+
+// Heaviest-first tables of the Gram launches (group ids by MMA cost).
+void fill_item_order(SplitParams& P) {
+  for (int c = 0; c < 5; ++c) P.nd_c[c] = P.no_c[c] = 0;
+  int od = 0, oo = 0;
+  for (int c = 4; c >= 1; --c) {
+    for (int g = 0; g < num_blocks(true); ++g)
+      if (group_cost(true, g) == c) {
+        P.gd_order[od++] = (int8_t)g;
+        ++P.nd_c[c];
+      }
+    for (int g = 0; g < num_blocks(false); ++g)
+      if (group_cost(false, g) == c) {
+        P.go_order[oo++] = (int8_t)g;
+        ++P.no_c[c];
+      }
+  }
+}
+
+constexpr bool kGramBalanceChunks = false;  // measured: the extra chunks' fill and drain cost more than they save
+
+int device_sms() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      sms = 148;
+    }
+  }
+  return sms;
+}
+
+// K chunks of a Gram launch: at least ceil(K / 16384) (exact FP32 sums), and more where the
+// heaviest items (the groups of the largest MMA cost) would not cover the SMs: each chunk
+// then splits them, so the launch's length is set by items of about half the work, while
+// every chunk keeps at least 4096 rows (fill and drain of an item stay small beside it).
+// Returns the chunk count; *rows gets the rows per chunk (a multiple of 64).
+int gram_kchunks(int64_t K, int64_t n, int* rows) {
+  const int64_t nt = (n + kBM - 1) / kBM;
+  int heavy_d = 0, heavy_o = 0, top = 0;
+  for (int g = 0; g < num_blocks(true); ++g) top = std::max(top, group_cost(true, g));
+  for (int g = 0; g < num_blocks(false); ++g) top = std::max(top, group_cost(false, g));
+  for (int g = 0; g < num_blocks(true); ++g) heavy_d += group_cost(true, g) == top;
+  for (int g = 0; g < num_blocks(false); ++g) heavy_o += group_cost(false, g) == top;
+  const int64_t heavy = nt * heavy_d + nt * (nt - 1) / 2 * heavy_o;
+  const int64_t base = std::max<int64_t>(1, (K + kKChunk - 1) / kKChunk);
+  const int64_t want = kGramBalanceChunks ? (device_sms() + heavy - 1) / heavy : 1;
+  const int64_t kc = std::max<int64_t>(base, std::min<int64_t>(want, K / 4096));
+  int64_t r = (K + kc - 1) / kc;
+  r = (r + kBK - 1) / kBK * kBK;
+  if (r > kKChunk) r = kKChunk;
+  *rows = (int)r;
+  return (int)((K + r - 1) / r);
+}
+
+}  // namespace
+
 GramSplitWork gram_split_work(int64_t K, int64_t n) {
   GramSplitWork w;
   const int64_t ldk = ((K + 7) / 8) * 8;
   const int64_t n_tiles = (n + kBM - 1) / kBM;
   const int64_t n_upper = n_tiles * (n_tiles + 1) / 2;
-  const int64_t n_kchunks = std::max<int64_t>(1, (K + kKChunk - 1) / kKChunk);
+  int rows = 0;
+  const int64_t n_kchunks = K > 0 ? gram_kchunks(K, n, &rows) : 1;
   w.slice_elems = (size_t)kSlices * (size_t)n * (size_t)ldk;
   w.partial_elems = (size_t)n_upper * slots_per_tile() * n_kchunks * kBM * kBN;
   w.exps = (size_t)n;
@@ -825,41 +913,6 @@ cudaError_t slices_map(const void* slices, int64_t K, int64_t n, CUtensorMap* ma
 
 }  // namespace
 
-cudaError_t gram_split_tc(int64_t K, int64_t n, const double* A, int64_t lda, double* C, int64_t ldc, void* slices,
-                          double* partial, int* exps, int32_t* err, cudaStream_t s, cudaEvent_t mma_begin,
-                          cudaEvent_t mma_end, double* a_copy, int64_t ld_copy, cudaEvent_t copied) {
-  if (n <= 0) return cudaSuccess;
-  if (K <= 0) return cudaMemset2DAsync(C, sizeof(double) * ldc, 0, sizeof(double) * n, n, s);
-  if (K > (int64_t)1 << 30 || n > 65535) return cudaErrorInvalidValue;
-  cudaError_t e = split_into(K, n, A, lda, K, slices, exps, err, s, a_copy, ld_copy);
-  if (e != cudaSuccess) return e;
-  if (copied && (e = cudaEventRecord(copied, s)) != cudaSuccess) return e;
-  CUtensorMap map;
-  if ((e = slices_map(slices, K, n, &map)) != cudaSuccess) return e;
-  SplitParams P;
-  P.n = P.n2 = (int)n;
-  P.K = (int)K;
-  P.n_tiles = P.n_tiles2 = (int)((n + kBM - 1) / kBM);
-  P.n_kchunks = (int)std::max<int64_t>(1, (K + kKChunk - 1) / kKChunk);
-  P.exps = P.exps2 = exps;
-  P.partial = partial;
-  P.err = err;
-  const int n_upper = P.n_tiles * (P.n_tiles + 1) / 2;
-  const int items = (P.n_tiles * num_blocks(true) + (n_upper - P.n_tiles) * num_blocks(false)) * P.n_kchunks;
-  const size_t smem = smem_bytes();
-  e = cudaFuncSetAttribute(gram_split_mma_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  if (mma_begin && (e = cudaEventRecord(mma_begin, s)) != cudaSuccess) return e;
-  gram_split_mma_kernel<true><<<items, kThreads, smem, s>>>(map, map, P, P, items);
-  note_launch();
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if (mma_end && (e = cudaEventRecord(mma_end, s)) != cudaSuccess) return e;
-  split_reduce_kernel<<<(unsigned)std::min<int64_t>(((int64_t)n_upper * kBM * kBN + 255) / 256, 4096), 256, 0, s>>>(
-      P, C, ldc);
-  note_launch();
-  return cudaGetLastError();
-}
-
 namespace {
 
 SplitParams gram_params(int64_t K, int64_t n, int* exps, double* partial, int32_t* err) {
@@ -867,7 +920,8 @@ SplitParams gram_params(int64_t K, int64_t n, int* exps, double* partial, int32_
   P.n = P.n2 = (int)n;
   P.K = (int)K;
   P.n_tiles = P.n_tiles2 = (int)((n + kBM - 1) / kBM);
-  P.n_kchunks = (int)std::max<int64_t>(1, (K + kKChunk - 1) / kKChunk);
+  P.n_kchunks = gram_kchunks(K, n, &P.kchunk);
+  fill_item_order(P);
   P.exps = P.exps2 = exps;
   P.partial = partial;
   P.err = err;
@@ -888,6 +942,35 @@ cudaError_t gram_reduce(const SplitParams& P, double* C, int64_t ldc, cudaStream
 }
 
 }  // namespace
+
+cudaError_t gram_split_tc(int64_t K, int64_t n, const double* A, int64_t lda, double* C, int64_t ldc, void* slices,
+                          double* partial, int* exps, int32_t* err, cudaStream_t s, cudaEvent_t mma_begin,
+                          cudaEvent_t mma_end, double* a_copy, int64_t ld_copy, cudaEvent_t copied) {
+  if (n <= 0) return cudaSuccess;
+  if (K <= 0) return cudaMemset2DAsync(C, sizeof(double) * ldc, 0, sizeof(double) * n, n, s);
+  if (K > (int64_t)1 << 30 || n > 65535) return cudaErrorInvalidValue;
+  cudaError_t e = split_into(K, n, A, lda, K, slices, exps, err, s, a_copy, ld_copy);
+  if (e != cudaSuccess) return e;
+  if (copied && (e = cudaEventRecord(copied, s)) != cudaSuccess) return e;
+  CUtensorMap map;
+  if ((e = slices_map(slices, K, n, &map)) != cudaSuccess) return e;
+  const SplitParams P = gram_params(K, n, exps, partial, err);
+  const int n_upper = P.n_tiles * (P.n_tiles + 1) / 2;
+  const int items = gram_items(P);
+  const size_t smem = smem_bytes();
+  e = cudaFuncSetAttribute(gram_split_mma_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (mma_begin && (e = cudaEventRecord(mma_begin, s)) != cudaSuccess) return e;
+  gram_split_mma_kernel<true><<<items, kThreads, smem, s>>>(map, map, P, P, items);
+  note_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (mma_end && (e = cudaEventRecord(mma_end, s)) != cudaSuccess) return e;
+  split_reduce_kernel<<<(unsigned)std::min<int64_t>(((int64_t)n_upper * kBM * kBN + 255) / 256, 4096), 256, 0, s>>>(
+      P, C, ldc);
+  note_launch();
+  return cudaGetLastError();
+}
+
 
 cudaError_t gram_split_pair_tc(int64_t K1, int64_t K2, int64_t n, const double* A1, int64_t lda1, const double* A2,
                                int64_t lda2, double* C1, double* C2, int64_t ldc, void* slices1, void* slices2,
@@ -966,6 +1049,8 @@ cudaError_t gemm_split_tc(int64_t K, int64_t n1, int64_t n2, const void* slicesX
   P.n_tiles = (int)((n1 + kBM - 1) / kBM);
   P.n_tiles2 = (int)((n2 + kBN - 1) / kBN);
   P.n_kchunks = (int)std::max<int64_t>(1, (K + kKChunk - 1) / kKChunk);
+  P.kchunk = kKChunk;
+  fill_item_order(P);  // unused by the general product's items
   P.exps = expsX;
   P.exps2 = expsY;
   P.partial = partial;
