@@ -222,9 +222,11 @@ __global__ void __launch_bounds__(kLzThreads, 1) lanczos_cluster_kernel(LzArgs a
   float* rows2 = lsm;
   float* rows1 = rows2 + (SMEM ? (size_t)R * n : 0);
   float* tF = rows1 + (SMEM && args.prob[0].M1 != nullptr ? (size_t)R * n : 0);
-  float* uF = tF + n;
-  float* sF = uF + n;
-  float* yS = sF + n;  // this CTA's rows of M2 t
+  const int n4 = (n + 3) & ~3;
+  float* uF = tF + n4;
+  float* sF = uF + n4;
+  float* wF = sF + n4;  // the second copy of y (standard Lanczos)
+  float* yS = wF + n4;  // this CTA's rows of M2 t
   float* sS = yS + R;  // and of M1 u
   __shared__ LzSmem sm;
   if (SMEM) {
@@ -263,12 +265,70 @@ __global__ void __launch_bounds__(kLzThreads, 1) lanczos_cluster_kernel(LzArgs a
   const float inv0 = rsqrtf(nrm2);
   __syncthreads();
   for (int s2 = threadIdx.x; s2 < n; s2 += blockDim.x) tF[s2] *= inv0;
+  int m = 0;
+  if (!gen) {
+    // Standard Lanczos (M1 = I), one cluster barrier per step: every CTA pushes its rows of
+    // y = M2 v_j into every CTA's copy of y (two copies, alternating by step: a CTA one step
+    // ahead writes the other), and after the barrier each CTA forms alpha_j = y^T v_j,
+    // u = y - alpha_j v_j - beta_{j-1} v_{j-1}, beta_j = ||u|| and v_{j+1} = u / beta_j over
+    // the whole vector itself: the same vectors and the same order of sums in every CTA,
+    // so every CTA holds the same values.
+    float* vF = tF;                                   // v_j (full)
+    float* vpF = sF;                                  // v_{j-1}
+    float* yb[2] = {uF, wF};                          // y, two copies
+    __shared__ float red8[kLzWarps];
+    __shared__ float s_dot;
+    auto block_dot = [&](const float* a, const float* b) {
+      float v = 0.f;
+      for (int s2 = threadIdx.x; s2 < n; s2 += blockDim.x) v = fmaf(a[s2], b[s2], v);
+      v = lz_warp_sum(v);
+      if ((threadIdx.x & 31) == 0) red8[threadIdx.x >> 5] = v;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int w = 0; w < kLzWarps; ++w) t += red8[w];
+        s_dot = t;
+      }
+      __syncthreads();
+      const float r = s_dot;
+      __syncthreads();  // s_dot and red8 are reused by the next call
+      return r;
+    };
+    for (int s2 = threadIdx.x; s2 < n; s2 += blockDim.x) vpF[s2] = 0.f;
+    float beta_prev = 0.f;
+    __syncthreads();
+    for (int j = 0; j < steps; ++j) {
+      float* yF = yb[j & 1];
+      slice_matvec<SMEM>(n, r0, nr, rows2, P.M2, P.m2_f64, vF, yS);  // this CTA's rows of M2 v_j
+      __syncthreads();
+      for (int i = threadIdx.x; i < nr; i += blockDim.x)
+        for (int rk = 0; rk < cs; ++rk) st_remote(&yF[r0 + i], (uint32_t)rk, yS[i]);
+      cluster_sync();
+      const float alpha = block_dot(yF, vF);
+      for (int s2 = threadIdx.x; s2 < n; s2 += blockDim.x)
+        yF[s2] = fmaf(-beta_prev, vpF[s2], fmaf(-alpha, vF[s2], yF[s2]));  // u, in place
+      __syncthreads();
+      const float beta = sqrtf(fmaxf(block_dot(yF, yF), 0.f));
+      if (threadIdx.x == 0) {
+        sm.alpha[j] = (double)alpha;
+        sm.beta[j] = (double)beta;
+      }
+      m = j + 1;
+      if (!(beta > 1e-6f * fabsf(alpha)) || !isfinite(beta)) break;  // invariant subspace (same in every CTA)
+      const float ib = 1.0f / beta;
+      for (int s2 = threadIdx.x; s2 < n; s2 += blockDim.x) {
+        vpF[s2] = vF[s2];
+        vF[s2] = yF[s2] * ib;
+      }
+      beta_prev = beta;
+      __syncthreads();
+    }
+  }
   float vcur = 0.f, vprev = 0.f;  // thread i: v_j and v_{j-1} at entry r0 + i
   if (threadIdx.x < nr) vcur = uF[r0 + threadIdx.x] * inv0;
   __syncthreads();
   float beta_prev = 0.f;
-  int m = 0;
-  for (int j = 0; j < steps; ++j) {
+  for (int j = 0; gen && j < steps; ++j) {
     slice_matvec<SMEM>(n, r0, nr, rows2, P.M2, P.m2_f64, tF, yS);  // y = C v_j = M2 t_j
     __syncthreads();
     const int i = threadIdx.x;
@@ -327,7 +387,7 @@ __global__ void __launch_bounds__(kLzThreads, 1) lanczos_cluster_kernel(LzArgs a
 
 size_t lz_smem(int64_t n, int cs, bool rows, bool any_gen) {
   const int64_t R = (n + cs - 1) / cs;
-  return sizeof(float) * (size_t)((rows ? R * n * (any_gen ? 2 : 1) : 0) + 3 * n + 2 * R + 4);
+  return sizeof(float) * (size_t)((rows ? R * n * (any_gen ? 2 : 1) : 0) + 4 * ((n + 3) & ~3) + 2 * R + 4);
 }
 
 template <bool SMEM>
@@ -552,8 +612,12 @@ cudaError_t lanczos_extremes(int count, const LanczosProblem* probs, cudaStream_
   // A thread of each CTA owns one row of the CTA's slice, so a slice holds at most kLzThreads
   // rows: 8 CTAs up to n = 2048, 16 up to n = 4096.  The rows stay in shared memory where
   // they fit, else each step reads them from L2.
+  // Standard Lanczos takes 16 CTAs first: its step is one barrier after the product, so
+  // half the rows per CTA shorten the step (and half the shared memory lets the cluster
+  // share SMs with the setup's other kernels).
+  const int order[2] = {any_gen ? 8 : 16, any_gen ? 16 : 8};
   for (int pass = 0; pass < 2; ++pass) {  // rows in shared memory first, then rows from L2
-    for (int cs : {8, 16}) {
+    for (int cs : order) {
       if ((n + cs - 1) / cs > kLzThreads) continue;
       a.cs = cs;
       const size_t sm_rows = lz_smem(n, cs, true, any_gen);
