@@ -40,7 +40,7 @@ FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (FMA pipe) rate from the profiling
 FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
 # of each kernel as it stands, on the headline step; None once a kernel changes.
-MMA_TRAFFIC_BYTES = None  # the split Gram kernel changed (9 six-bit digits, chunked items): recaptured below
+MMA_TRAFFIC_BYTES = 144_444_416 + 9_991_936
 GJ_TRAFFIC_BYTES = 693_504 + 0
 
 
@@ -732,7 +732,7 @@ def main():
         "config": {
             "workload": WORKLOAD,
             "arithmetic": "Grams FP64-accurate from exact BF16 digit products (FP32 accumulation), P and "
-                          "sweeps FP32, A^T J b and residuals FP64",
+                          "sweeps FP32, A^T J b FP64, residuals double-FP32 on row-scaled H",
             "stop": "kappa_est * relres <= 1e-10 (Lanczos kappa_est; ILS_STOP_ERR_BOUND)",
             "relerr_vs_oracle": r4(mixed["relerr_timed"]),
             "err_bound": r4(mixed["info"]["err_bound"]), "kappa_est": r4(mixed["info"]["kappa_est"]),

@@ -666,8 +666,8 @@ __global__ void __launch_bounds__(256) exponent_split_cluster_kernel(int K, int6
 
 // C(i,j) for the upper tiles.  Every stored product is an exact integer held in FP32.
 // The products of equal t + u carry the same scale 2^{e_i + e_j - beta (t + u)}, so they
-// are added exactly in integers first (at most 10 terms below 2^24 each per K chunk), and
-// the 10 group sums are joined by combine_groups (below).  Then the tile is mirrored.  Every
+// are added exactly in integers first (at most 9 terms of magnitude at most 2^24 each per K chunk), and
+// the 9 group sums are joined by combine_groups (below).  Then the tile is mirrored.  Every
 // tile has all its ordered-pair slots (a diagonal tile's transposed slots were written by
 // the epilogue).  A thread takes one entry.
 constexpr int kScales = kSlices;  // t + u = 2 .. S + 1
@@ -741,7 +741,7 @@ __global__ void split_reduce_kernel(SplitParams P, double* __restrict__ C, int64
   }
 }
 
-// The general product X^T Y (n x n2 output, every tile pair with all 55 ordered digit pairs):
+// The general product X^T Y (n x n2 output, every tile pair with all 45 ordered digit pairs):
 // the same exact grouping by t + u.  With C0, C = C0 - X^T Y (the FP64 residual
 // bbar - H X of a refinement step); C and C0 may be the same array.
 __global__ void gemm_reduce_kernel(SplitParams P, double* __restrict__ C, int64_t ldc, const double* C0,
