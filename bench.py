@@ -175,9 +175,10 @@ class ClockSampler:
 
 
 def measure_stream(ils, torch, np, dev, reps=20):
-    """Time v = A_2^T (A_2 x) streamed from the FP64, FP32 and BF16 row-major copies of A_2 on
-    the tall bandwidth instance (A_2 262144 x 500: 1.05 GB in FP64, far above L2), and one
-    complete mixed-precision solve of that instance (matrix-free route, BF16 sweeps)."""
+    """Time v = A_2^T (A_2 x) streamed from the FP32, BF16, double-FP32 (a mixed handle's
+    FP64-accurate copy) and FP64 (an FP64 handle's) row-major copies of A_2 on the tall
+    bandwidth instance (A_2 262144 x 500: 1.05 GB in FP64, far above L2), and one complete
+    mixed-precision solve of that instance (matrix-free route, BF16 sweeps)."""
     import workloads
     inst = workloads.config2_roofline()
     q, n, p = inst.q, inst.n, inst.p
@@ -185,8 +186,8 @@ def measure_stream(ils, torch, np, dev, reps=20):
     x = torch.from_numpy(np.random.default_rng(0).standard_normal(n)).to(dev)
     v = torch.empty(n, dtype=torch.float64, device=dev)
     out = {}
-    for prec, name, elem in ((1, "fp32", 4), (2, "bf16", 2), (0, "fp64", 8)):
-        precision = {0: ils.ILS_BF16_REFINE, 1: ils.ILS_FP32_REFINE, 2: ils.ILS_BF16_REFINE}[prec]
+    for prec, name, elem, precision in ((1, "fp32", 4, ils.ILS_FP32_REFINE), (0, "df32", 8, ils.ILS_FP32_REFINE),
+                                        (0, "fp64", 8, ils.ILS_FP64), (2, "bf16", 2, ils.ILS_BF16_REFINE)):
         s = ils.Solver(At, p, ils.options(precision=precision, route=ils.ILS_ROUTE_MATRIX_FREE))
         for _ in range(3):
             s.aq_product(x, v, prec=prec)
@@ -582,14 +583,17 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     xs = _normal_solution(inst.A, inst.b, inst.p)
 
-    def measure(opts, steps, with_clocks):
-        """Warm up, gate accuracy, then time `steps` complete solves (per-step events)."""
-        solver = ils.Solver(At, p, opts, stream=stream)
+    def measure(kw, steps, with_clocks):
+        """Warm up, gate accuracy, then time `steps` complete solves (per-step events) with
+        options.timing off; the phase times come from as many further steps on a second
+        handle with options.timing on (its events and their reads stay out of the timed
+        region)."""
+        solver = ils.Solver(At, p, ils.options(**kw), stream=stream)
         route = "matrix_free" if ils.binding.route_model().get("matrix_free") == 1.0 else "explicit"
 
-        def step():
-            solver.refactor_async(At, stream=stream)
-            return solver.solve(b, x, tol=TOL_ERR, stream=stream)
+        def step(sv=solver):
+            sv.refactor_async(At, stream=stream)
+            return sv.solve(b, x, tol=TOL_ERR, stream=stream)
 
         # nvidia-smi starts before the warm-up so that its start-up does not overlap the
         # timed region; every sample it takes falls in the loaded warm-up or timed steps.
@@ -617,7 +621,6 @@ def main():
             ev[i][0].record(stream)
             info = step()
             ev[i][1].record(stream)
-            phases.append(solver.timings())
             infos.append(info.as_dict())
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
@@ -629,15 +632,24 @@ def main():
         barrier()
         clocks = sampler.stop() if sampler else None
         total_s = max_over_ranks(sum(a.elapsed_time(bb) for a, bb in ev) / 1e3, world, dev)
-        ph = {k: statistics.mean(d[k] for d in phases) for k in phases[0]}
+        timed = ils.Solver(At, p, ils.options(**kw, timing=1), stream=stream)
+        for _ in range(3):
+            step(timed)
+        for _ in range(steps):
+            flush.zero_()
+            step(timed)
+            phases.append(timed.timings())
+        timed.close()
+        torch.cuda.synchronize()
+        ph = {k: statistics.median(d[k] for d in phases) for k in phases[0]}
         return dict(solver=solver, total_s=total_s, wall=wall, launches=launches, clocks=clocks, relerr=relerr,
                     relerr_timed=relerr_timed, phases=ph, info=infos[-1], steps=steps, route=route)
 
-    certified = dict(stop_rule=ils.ILS_STOP_ERR_BOUND, timing=1)  # stop on kappa_est * relres <= 1e-10
-    mixed = measure(ils.options(precision=ils.ILS_FP32_REFINE, **certified), args.steps, True)
-    plain = measure(ils.options(**certified), max(3, min(args.steps, 10)), False)
+    certified = dict(stop_rule=ils.ILS_STOP_ERR_BOUND)  # stop on kappa_est * relres <= 1e-10
+    mixed = measure(dict(precision=ils.ILS_FP32_REFINE, **certified), args.steps, True)
+    plain = measure(dict(**certified), max(3, min(args.steps, 10)), False)
     # the mixed form with the factorization kept in FP64 (Cholesky of Abar1 and H)
-    mixed64 = measure(ils.options(precision=ils.ILS_FP32_REFINE, factor64=1, **certified), max(3, min(args.steps, 10)),
+    mixed64 = measure(dict(precision=ils.ILS_FP32_REFINE, factor64=1, **certified), max(3, min(args.steps, 10)),
                       False)
     solver = mixed["solver"]
     value = replica_rate(world, args.steps, mixed["total_s"])
@@ -754,7 +766,8 @@ def main():
                                  "frac_executed": r4(roof_mma["frac_executed"])},
                     "aq_stream_fp32": {"GBps": r4(stream["fp32"]["achieved_GBps"]), "frac": r4(stream["fp32"]["frac"])},
                     "aq_stream_bf16": {"GBps": r4(stream["bf16"]["achieved_GBps"]), "frac": r4(stream["bf16"]["frac"])},
-                    "aq_stream_fp64": {"GBps": r4(stream["fp64"]["achieved_GBps"]), "frac": r4(stream["fp64"]["frac"])}},
+                    "aq_stream_fp64": {"GBps": r4(stream["fp64"]["achieved_GBps"]), "frac": r4(stream["fp64"]["frac"])},
+                    "aq_stream_df32": {"GBps": r4(stream["df32"]["achieved_GBps"]), "frac": r4(stream["df32"]["frac"])}},
         "tall_ms_per_solve": r4((stream.get("tall_mixed_solve") or {}).get("ms_per_solve")),
         "other_configs": summary,
         "cpu_baseline": {

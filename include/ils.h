@@ -424,10 +424,12 @@ ils_status ils_gram_noalloc(int64_t K, int64_t n, const double* X, int64_t ldx, 
                             ils_stream_t stream);
 
 /* v = A_2^T (A_2 x) for one vector (length n in, length n out, FP64, device) by the
- * handle's one-pass stream over its row-major copy of A_2: prec 0 streams the FP64 copy,
- * 1 the FP32 copy, 2 the BF16 copy (FP32 accumulation); the copy must exist (matrix-free
- * route; the low-precision copy in the matching mixed precision).  For tests and
- * bandwidth measurements.  Errors: INVALID_ARG, CUDA. */
+ * handle's one-pass stream over its row-major copy of A_2: prec 0 streams the FP64-accurate
+ * copy (FP64 on an FP64 handle; on a mixed-precision handle the double-FP32 copy, each
+ * entry as its FP32 rounding plus the FP32 rounding of the rest, carried in double-FP32
+ * arithmetic), 1 the FP32 copy, 2 the BF16 copy (FP32 accumulation); the copy must exist
+ * (matrix-free route; the low-precision copy in the matching mixed precision).  For tests
+ * and bandwidth measurements.  Errors: INVALID_ARG, CUDA. */
 ils_status ils_aq_product(ils_handle h, const double* x, double* v, int prec, ils_stream_t stream);
 
 /* The last automatic route decision (options.route = auto) of this process, host only.  out

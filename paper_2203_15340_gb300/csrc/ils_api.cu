@@ -462,7 +462,8 @@ ils_status compute_setup_mf(ils_handle h) {
   ILS_CK(cudaMemcpyAsync(h->h_status, h->dstatus, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   if (h->opt.gram == ILS_GRAM_SPLIT)
     ILS_CK(cudaMemcpyAsync(h->h_status + 1, h->gs_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-  ILS_CK(aq_copy_rows(q, n, h->A + p, m, h->Aq64r, 0, s));
+  // the FP64-accurate copy: FP64 for FP64 SP, double-FP32 for the refinement's residuals
+  ILS_CK(aq_copy_rows(q, n, h->A + p, m, h->Aq64r, h->opt.precision == ILS_FP64 ? 0 : 3, s));
   if (h->opt.precision != ILS_FP64) {
     ILS_CK(aq_copy_rows(q, n, h->A + p, m, h->Aq_lo, h->opt.precision == ILS_FP32_REFINE ? 1 : 2, s));
     ILS_CK(mixed_setup(n, h->L, nullptr, h->opt.precision, h->L32, h->P32, nullptr, nullptr, nullptr,
@@ -951,7 +952,8 @@ ils_status pass_launch(ils_handle h, int64_t count) {
   for (int64_t i = 0; i < todo; ++i) {
     if (h->mf) {
       for (int c = 0; c < (int)h->pass_k; ++c)
-        ILS_CK(aq_product_iterate(h->q, h->n, h->Aq64r, 0, h->X0, h->X1, h->st, h->col_done, c, h->sp_part,
+        ILS_CK(aq_product_iterate(h->q, h->n, h->Aq64r, h->opt.precision == ILS_FP64 ? 0 : 3, h->X0, h->X1, h->st,
+                                  h->col_done, c, h->sp_part,
                                   h->vbuf + c * h->n, s));
     }
     ILS_CK(sp_iterate_f64(h->pa, s));
@@ -1462,7 +1464,8 @@ ils_status ils_aq_product(ils_handle h, const double* x, double* v, int prec, il
   const void* Ar = prec == 0 ? h->Aq64r : h->Aq_lo;
   if (prec != 0 && (h->opt.precision == ILS_FP64 || (prec == 1) != (h->opt.precision == ILS_FP32_REFINE)))
     return ILS_ERR_INVALID_ARG;
-  ILS_CK(aq_product(h->q, h->n, Ar, prec, x, h->sp_part, v, (cudaStream_t)stream));
+  const int kind = prec == 0 && h->opt.precision != ILS_FP64 ? 3 : prec;  // the mixed handles' double-FP32 copy
+  ILS_CK(aq_product(h->q, h->n, Ar, kind, x, h->sp_part, v, (cudaStream_t)stream));
   return ILS_OK;
 }
 

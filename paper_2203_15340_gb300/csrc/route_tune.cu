@@ -22,8 +22,8 @@ struct Rates {
   bool ready = false;
   double gram_split = 0.0;  // flop/s of the FP64-accurate Gram (split digits), in p n^2 units
   double gram_f64 = 0.0;    // the same for the FP64 FMA Gram
-  double bw[3] = {};        // bytes/s of the A_2 stream: FP64, FP32, BF16 copies
-  double lat[3] = {};       // fixed seconds per stream (launches and the reduction)
+  double bw[4] = {};        // bytes/s of the A_2 stream: FP64, FP32, BF16, double-FP32 copies
+  double lat[4] = {};       // fixed seconds per stream (launches and the reduction)
   double copy = 0.0;        // bytes/s of building the row-major copies
 };
 std::mutex g_rates_mu;
@@ -91,12 +91,12 @@ cudaError_t calibrate(Rates* r) {
     if ((e = cudaMemsetAsync(err, 0, 4, s)) != cudaSuccess) goto done;
     const double t_split = timed([&] { gram_split_tc(K, n_g, X, K, C, n_g, slices, partial, exps, err, s); }, 3);
     const double t_f64 = timed([&] { gemm_tn_f64(K, n_g, n_g, X, K, X, K, K, C, n_g, true, false, work, s); }, 1);
-    double t_copy = 0.0, t_bw[3] = {};
-    double t_small[3] = {};
+    double t_copy = 0.0, t_bw[4] = {};
+    double t_small[4] = {};
     const int64_t q_small = 16384;
-    for (int prec = 0; prec < 3; ++prec) {
+    for (int prec = 0; prec < 4; ++prec) {
       const double tc = timed([&] { aq_copy_rows(q, n, X, q, rows, prec, s); }, 1);
-      t_copy = std::max(t_copy, tc / (double)(q * n * (prec == 0 ? 16 : prec == 1 ? 12 : 10)));
+      t_copy = std::max(t_copy, tc / (double)(q * n * (prec == 0 || prec == 3 ? 16 : prec == 1 ? 12 : 10)));
       t_bw[prec] = timed([&] { aq_product(q, n, rows, prec, xv, part, v, s); }, 5);
       aq_copy_rows(q_small, n, X, q_small, rows, prec, s);
       t_small[prec] = timed([&] { aq_product(q_small, n, rows, prec, xv, part, v, s); }, 5);
@@ -108,8 +108,8 @@ cudaError_t calibrate(Rates* r) {
     }
     r->gram_split = (double)K * n_g * n_g / t_split;
     r->gram_f64 = (double)K * n_g * n_g / t_f64;
-    const double elem[3] = {8.0, 4.0, 2.0};
-    for (int prec = 0; prec < 3; ++prec) {  // t = lat + bytes / bw through the two sizes
+    const double elem[4] = {8.0, 4.0, 2.0, 8.0};
+    for (int prec = 0; prec < 4; ++prec) {  // t = lat + bytes / bw through the two sizes
       const double b1 = (double)q * n * elem[prec], b0 = (double)q_small * n * elem[prec];
       const double dt = t_bw[prec] - t_small[prec];
       r->bw[prec] = dt > 0.0 ? (b1 - b0) / dt : 1e12;
@@ -154,9 +154,10 @@ cudaError_t route_prefers_matrix_free(int64_t q, int64_t n, int precision, bool 
   // route's Lanczos works on n x n operators held on chip beside the setup).
   const int est_prec = precision == ILS_FP64 ? 0 : lo;
   const double est_bytes = precision == ILS_FP64 ? 8.0 : s_lo;
+  const int acc = precision == ILS_FP64 ? 0 : 3;  // the residuals' copy: FP64, or double-FP32
   const double mf_cost = qd * nd * (8.0 + s_lo) / r.copy +
                          (t_lo > 0.0 ? t_lo * (r.lat[lo] + qd * nd * s_lo / r.bw[lo]) : 0.0) +
-                         t_64 * (r.lat[0] + qd * nd * 8.0 / r.bw[0]) +
+                         t_64 * (r.lat[acc] + qd * nd * 8.0 / r.bw[acc]) +
                          estimate_steps * (r.lat[est_prec] + qd * nd * est_bytes / r.bw[est_prec]);
   *mf = n <= 512 && mf_cost < explicit_cost;
   if (model) {

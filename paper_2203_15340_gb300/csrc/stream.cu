@@ -8,6 +8,12 @@
 // same registers then accumulate v += u_r A_2(r,:).  Each element of A_2 is read from HBM
 // exactly once and the next row is loaded before the current one is reduced.  Per-CTA
 // partial v's are summed by a second small kernel in a fixed order (deterministic).
+//
+// The double-FP32 copy (prec 3) holds, for every padded row, the FP32 rounding of each entry
+// and then the FP32 rounding of what it leaves (about 48 bits of the entry, the FP64 copy's
+// 8 bytes): u_r and v are then carried in double-FP32 (each product split exactly by an
+// FMA, sums with their rounding errors kept), on the FP32 pipe at HBM speed, where the
+// FP64 stream is bound by GB300's narrow FP64 unit.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -246,6 +252,140 @@ __global__ void rowmajor_copy_kernel(int64_t q, int64_t n, const double* __restr
   }
 }
 
+// (sh, sl) += p + e with the rounding error of sh + p kept in sl.
+__device__ __forceinline__ void df_add(float& sh, float& sl, float p, float e) {
+  const float t = sh + p;
+  const float bp = t - sh;
+  sl += ((sh - (t - bp)) + (p - bp)) + e;
+  sh = t;
+}
+// (ah + al)(bh + bl) as p + e: p the FP32 product of the leading parts, e the rest.
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float& p, float& e) {
+  p = ah * bh;
+  e = fmaf(ah, bl, fmaf(al, bh, fmaf(ah, bh, -p)));
+}
+
+// Double-FP32 stream: rows of 2 * 128 NT floats (leading parts, then the rest); R rows in
+// flight per warp.  Partial v's (per CTA) are written in FP64.
+template <int NT, int R>
+__global__ void __launch_bounds__(32 * kStreamWarps)
+aq_stream_df_kernel(int64_t q, int64_t n, const float* __restrict__ Ar, XSrc src, double* __restrict__ part) {
+  constexpr int LDR = 128 * NT;
+  bool skip;
+  const double* __restrict__ x = resolve_x(src, n, &skip);
+  if (skip) return;
+  extern __shared__ __align__(16) unsigned char stream_smem[];
+  __shared__ float xsh[LDR], xsl[LDR];
+  __shared__ double red[LDR];
+  for (int64_t j = threadIdx.x; j < LDR; j += blockDim.x) {
+    const double xj = j < n ? x[j] : 0.0;
+    const float hi = __double2float_rn(xj);
+    xsh[j] = hi;
+    xsl[j] = __double2float_rn(xj - (double)hi);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float* ring = reinterpret_cast<float*>(stream_smem) + (size_t)w * R * (2 * LDR);
+  float xh[NT][4], xl[NT][4], vh[NT][4], vl[NT][4];
+#pragma unroll
+  for (int t = 0; t < NT; ++t)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      xh[t][e] = xsh[t * 128 + lane * 4 + e];
+      xl[t][e] = xsl[t * 128 + lane * 4 + e];
+      vh[t][e] = vl[t][e] = 0.f;
+    }
+  const int64_t gw = (int64_t)blockIdx.x * kStreamWarps + w, nw = (int64_t)gridDim.x * kStreamWarps;
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const int64_t r = gw + i * nw;
+    if (r < q) {
+      issue_row<float, NT>(ring + i * (2 * LDR), Ar + r * (2 * LDR), lane);
+      issue_row<float, NT>(ring + i * (2 * LDR) + LDR, Ar + r * (2 * LDR) + LDR, lane);
+    }
+    cp_async_commit();
+  }
+  int slot = 0;
+  for (int64_t r = gw; r < q; r += nw) {
+    cp_async_wait<R - 1>();
+    const float* srow = ring + slot * (2 * LDR);
+    float ah[NT][4], al[NT][4];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      load4<float, float>(srow + t * 128 + lane * 4, ah[t]);
+      load4<float, float>(srow + LDR + t * 128 + lane * 4, al[t]);
+    }
+    const int64_t rn = r + (int64_t)R * nw;
+    if (rn < q) {
+      issue_row<float, NT>(ring + slot * (2 * LDR), Ar + rn * (2 * LDR), lane);
+      issue_row<float, NT>(ring + slot * (2 * LDR) + LDR, Ar + rn * (2 * LDR) + LDR, lane);
+    }
+    cp_async_commit();
+    // u_r = A_2(r,:) x
+    float dh = 0.f, dl = 0.f;
+#pragma unroll
+    for (int t = 0; t < NT; ++t)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        float pp, ee;
+        df_mul(ah[t][e], al[t][e], xh[t][e], xl[t][e], pp, ee);
+        df_add(dh, dl, pp, ee);
+      }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float oh = __shfl_xor_sync(0xffffffffu, dh, o), ol = __shfl_xor_sync(0xffffffffu, dl, o);
+      df_add(dh, dl, oh, ol);
+    }
+    const float uh0 = __shfl_sync(0xffffffffu, dh, 0), ul0 = __shfl_sync(0xffffffffu, dl, 0);
+    const float uh = uh0 + ul0, ul = ul0 - (uh - uh0);  // renormalized
+    // v += u_r A_2(r,:)
+#pragma unroll
+    for (int t = 0; t < NT; ++t)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        float pp, ee;
+        df_mul(uh, ul, ah[t][e], al[t][e], pp, ee);
+        df_add(vh[t][e], vl[t][e], pp, ee);
+      }
+    slot = (slot + 1 == R) ? 0 : slot + 1;
+  }
+  cp_async_wait<0>();
+  for (int j = threadIdx.x; j < LDR; j += blockDim.x) red[j] = 0.0;
+  for (int ww = 0; ww < kStreamWarps; ++ww) {
+    __syncthreads();
+    if (w == ww) {
+#pragma unroll
+      for (int t = 0; t < NT; ++t)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) red[t * 128 + lane * 4 + e] += (double)vh[t][e] + (double)vl[t][e];
+    }
+  }
+  __syncthreads();
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) part[(int64_t)blockIdx.x * n + j] = red[j];
+}
+
+// Row-major double-FP32 copy: row r holds the FP32 roundings of A(r, :) (ldr of them, zero
+// past n) and then the FP32 roundings of what they leave.
+__global__ void rowmajor_copy_df_kernel(int64_t q, int64_t n, const double* __restrict__ Ac, int64_t lda,
+                                        float* __restrict__ Ar, int64_t ldr) {
+  __shared__ double tile[32][33];
+  const int64_t r0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t r = r0 + threadIdx.x, c = c0 + k;
+    tile[k][threadIdx.x] = (r < q && c < n) ? Ac[r + c * lda] : 0.0;
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t r = r0 + k, c = c0 + threadIdx.x;
+    if (r < q && c < ldr) {
+      const double a = tile[threadIdx.x][k];
+      const float hi = __double2float_rn(a);
+      Ar[r * 2 * ldr + c] = hi;
+      Ar[r * 2 * ldr + ldr + c] = __double2float_rn(a - (double)hi);
+    }
+  }
+}
+
 }  // namespace
 
 // Rows are padded to the chunk count of the kernel instantiation that streams them
@@ -279,6 +419,14 @@ static cudaError_t copy_rows(int64_t q, int64_t n, const double* Ac, int64_t lda
 }
 
 cudaError_t aq_copy_rows(int64_t q, int64_t n, const double* Ac, int64_t lda, void* Ar, int prec, cudaStream_t s) {
+  if (prec == 3) {
+    const int64_t ldr = aq_row_stride(n);
+    if (q <= 0) return cudaSuccess;
+    const dim3 grid((unsigned)((q + 31) / 32), (unsigned)((ldr + 31) / 32));
+    rowmajor_copy_df_kernel<<<grid, dim3(32, 8), 0, s>>>(q, n, Ac, lda, static_cast<float*>(Ar), ldr);
+    note_launch();
+    return cudaGetLastError();
+  }
   if (prec == 0) return copy_rows<double>(q, n, Ac, lda, static_cast<double*>(Ar), s);
   if (prec == 1) return copy_rows<float>(q, n, Ac, lda, static_cast<float*>(Ar), s);
   return copy_rows<__nv_bfloat16>(q, n, Ac, lda, static_cast<__nv_bfloat16*>(Ar), s);
@@ -323,16 +471,54 @@ static cudaError_t dispatch_stream(int64_t q, int64_t n, const T* Ar, XSrc x, vo
   return cudaErrorInvalidValue;  // wider rows: the explicit route handles them
 }
 
+template <int NT>
+static cudaError_t launch_stream_df(int64_t q, int64_t n, const float* Ar, XSrc x, void* part, double* v,
+                                   cudaStream_t s) {
+  constexpr int R = 2;  // rows in flight per warp (8 bytes per entry, as FP64)
+  const size_t smem = sizeof(float) * (size_t)kStreamWarps * R * 2 * 128 * NT;
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    if (cudaFuncSetAttribute(aq_stream_df_kernel<NT, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return cudaErrorInvalidValue;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, aq_stream_df_kernel<NT, R>, 32 * kStreamWarps, smem) !=
+            cudaSuccess ||
+        per_sm <= 0)
+      per_sm = 1;
+    per_sm = std::min(per_sm, 4);
+  }
+  const int blocks = (aq_stream_blocks() / 4) * per_sm;
+  aq_stream_df_kernel<NT, R><<<blocks, 32 * kStreamWarps, smem, s>>>(q, n, Ar, x, static_cast<double*>(part));
+  note_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  aq_reduce_kernel<double><<<(unsigned)((n + 31) / 32), 256, 0, s>>>(n, blocks, static_cast<const double*>(part), v, x);
+  note_launch();
+  return cudaGetLastError();
+}
+
+static cudaError_t dispatch_stream_df(int64_t q, int64_t n, const float* Ar, XSrc x, void* part, double* v,
+                                      cudaStream_t s) {
+  const int64_t nt = chunk_bucket(n);
+  if (q <= 0 && !x.st) return cudaMemsetAsync(v, 0, sizeof(double) * n, s);
+  if (q <= 0) return cudaErrorInvalidValue;
+  if (nt == 1) return launch_stream_df<1>(q, n, Ar, x, part, v, s);
+  if (nt == 2) return launch_stream_df<2>(q, n, Ar, x, part, v, s);
+  if (nt == 4) return launch_stream_df<4>(q, n, Ar, x, part, v, s);
+  return cudaErrorInvalidValue;  // wider rows: the explicit route handles them
+}
+
 template <typename... R>
 static cudaError_t by_prec(int prec, int64_t q, int64_t n, const void* Ar, XSrc x, void* part, double* v,
                            cudaStream_t s) {
+  if (prec == 3) return dispatch_stream_df(q, n, static_cast<const float*>(Ar), x, part, v, s);
   if (prec == 0) return dispatch_stream<double>(q, n, static_cast<const double*>(Ar), x, part, v, s);
   if (prec == 1) return dispatch_stream<float>(q, n, static_cast<const float*>(Ar), x, part, v, s);
   return dispatch_stream<__nv_bfloat16>(q, n, static_cast<const __nv_bfloat16*>(Ar), x, part, v, s);
 }
 
-// v = A_2^T (A_2 x) from the row-major copy Ar (prec 0 FP64, 1 FP32, 2 BF16).  part holds
-// aq_stream_blocks() * n accumulator values.
+// v = A_2^T (A_2 x) from the row-major copy Ar (prec 0 FP64, 1 FP32, 2 BF16, 3 double-FP32).
+// part holds aq_stream_blocks() * n accumulator values (doubles for prec 0 and 3).
 cudaError_t aq_product(int64_t q, int64_t n, const void* Ar, int prec, const double* x, void* part, double* v,
                        cudaStream_t s) {
   return by_prec(prec, q, n, Ar, XSrc{x, nullptr, nullptr, nullptr, 0}, part, v, s);

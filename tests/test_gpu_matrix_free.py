@@ -1,8 +1,9 @@
 """GPU parity of the matrix-free route: v = A_2^T (A_2 x) streamed in one pass over A_2,
 and SP driven by it (x_{k+1} = P (A_2^T A_2 x_k + bbar), Alg. 1 step 6 without Abar2).
 
-Bounds: the FP64 stream meets 4 q u |A_2|^T |A_2| |x| elementwise; the FP32 copy 1e-5 and the
-BF16 copy 2e-2 in relative 2-norm; every solve reaches ||x - x*|| / ||x*|| <= 1e-10.
+Bounds: the FP64-accurate stream (the FP64 copy of an FP64 handle, the double-FP32 copy of a
+mixed one) meets 4 q u |A_2|^T |A_2| |x| elementwise; the FP32 copy 1e-5 and the BF16 copy
+2e-2 in relative 2-norm; every solve reaches ||x - x*|| / ||x*|| <= 1e-10.
 """
 import numpy as np
 import pytest
