@@ -22,6 +22,8 @@ Parity status (what pins each function, see ``tests/test_oracle_*.py``):
   * sp_scd_solve: Theorem 4.1's exact energy decrease per step; alpha = n is the
     greedy (Motzkin) rule; the rank sampler has the same law as the literal
     alpha/subset sampler (exact enumeration for small n).
+  * theta_at (the inner-stop schedule): its closed form; gamma = 1 reproduces the
+    constant stop; each outer step within ||Abar1^{-1}|| theta_k ||r_k|| of the SP step.
   * philox4x32_10: the published known-answer vectors.
   * mlp_*: central finite differences.
   * sparse.*: hand-computed products of a literal 4 x 3 CSR matrix; the dense

@@ -53,6 +53,7 @@ __all__ = [
     "normal_matrix_condition",
     "error_certificate",
     "sp_rk_rgs_gram_solve",
+    "theta_at",
 ]
 
 
@@ -455,8 +456,18 @@ def scd_step(G1, beta, r, j):
     return beta, r - delta * G1[:, j]
 
 
+def theta_at(theta, k, theta_decay=1.0, theta_min=0.0):
+    """Inner-stop factor of outer iteration k under a schedule (not in the paper, which
+    leaves the inner stop open): theta_k = max(theta * theta_decay^k, theta_min).
+    theta_decay = 1 (or <= 0) keeps theta constant."""
+    if theta_decay <= 0.0 or theta_decay == 1.0:
+        return theta
+    return max(theta * theta_decay ** k, theta_min)
+
+
 def sp_rk_rgs_solve(A, b, p, x0=None, tol=1e-12, max_outer=20000, max_inner=None, theta=0.1,
-                    seed=0, chain=0, check_every=None, same_index=False, record=False, warm_inner=False):
+                    seed=0, chain=0, check_every=None, same_index=False, record=False, warm_inner=False,
+                    theta_decay=1.0, theta_min=0.0):
     """SP-RK-RGS method, Alg. 2.
 
     Outer: bhat = Abar2 x_k + bbar (step 5), z = w = 0 (step 6).  Inner step t:
@@ -475,6 +486,9 @@ def sp_rk_rgs_solve(A, b, p, x0=None, tol=1e-12, max_outer=20000, max_inner=None
     solve at z = x_k, w = A_1 x_k instead: w stays in range(A_1), the inner fixed point
     Abar1^{-1} bhat is unchanged, and the start's residual bhat - Abar1 x_k is the outer
     residual bbar - H x_k, which the inner stop measures against.
+
+    ``theta_decay`` / ``theta_min`` replace theta by ``theta_at(theta, k, ...)`` at outer
+    iteration k (a schedule, not in the paper).
     """
     A = np.asarray(A, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
@@ -499,7 +513,7 @@ def sp_rk_rgs_solve(A, b, p, x0=None, tol=1e-12, max_outer=20000, max_inner=None
         bhat = G2 @ x + bb
         w = A1 @ x if warm_inner else np.zeros(p)
         z = x.copy() if warm_inner else np.zeros(n)
-        target = theta * np.linalg.norm(r_out)
+        target = theta_at(theta, k, theta_decay, theta_min) * np.linalg.norm(r_out)
         t_done = max_inner
         for t in range(max_inner):
             u0, u1 = step_uniforms(seed, chain, k, t)
@@ -522,7 +536,8 @@ def sp_rk_rgs_solve(A, b, p, x0=None, tol=1e-12, max_outer=20000, max_inner=None
 
 
 def sp_rk_rgs_gram_solve(A, b, p, x0=None, tol=1e-12, max_outer=20000, max_inner=None, theta=0.1,
-                         seed=0, chain=0, check_every=None, same_index=False, warm_inner=False):
+                         seed=0, chain=0, check_every=None, same_index=False, warm_inner=False,
+                         theta_decay=1.0, theta_min=0.0):
     """SP-RK-RGS, Alg. 2, with the inner vectors carried in Gram space (not in the paper).
 
     From w = 0, every RK step adds a multiple of a column of A_1 to w, so w = A_1 y for a
@@ -557,7 +572,7 @@ def sp_rk_rgs_gram_solve(A, b, p, x0=None, tol=1e-12, max_outer=20000, max_inner
         z = x.copy() if warm_inner else np.zeros(n)
         g = G1 @ z  # w = A_1 z at a warm start (y = z), else w = 0
         h = g.copy()
-        target = theta * np.linalg.norm(r_out)
+        target = theta_at(theta, k, theta_decay, theta_min) * np.linalg.norm(r_out)
         t_done = max_inner
         for t in range(max_inner):
             u0, u1 = step_uniforms(seed, chain, k, t)
@@ -581,7 +596,8 @@ def sp_rk_rgs_gram_solve(A, b, p, x0=None, tol=1e-12, max_outer=20000, max_inner
 
 
 def sp_scd_solve(A, b, p, x0=None, tol=1e-12, max_outer=20000, max_inner=None, theta=0.1,
-                 sampler="rank", alpha=None, seed=0, chain=0, record=False, rng=None, warm_inner=False):
+                 sampler="rank", alpha=None, seed=0, chain=0, record=False, rng=None, warm_inner=False,
+                 theta_decay=1.0, theta_min=0.0):
     """SP-SCD method in the form the paper ran, Alg. 5.
 
     Outer: bhat = Abar2 x_k + bbar (step 4), beta = 0 and r = bhat (step 5).
@@ -601,7 +617,8 @@ def sp_scd_solve(A, b, p, x0=None, tol=1e-12, max_outer=20000, max_inner=None, t
         |r_s| with i = ``scd_fixed_rank_from_uniform(u0, n, alpha)``, u0 from Philox.
 
     ``warm_inner`` (not in the paper, which restarts at beta = 0 in step 5) starts the
-    inner solve at beta = x_k, r = bhat - Abar1 x_k (= bbar - H x_k).
+    inner solve at beta = x_k, r = bhat - Abar1 x_k (= bbar - H x_k).  ``theta_decay`` /
+    ``theta_min``: the schedule of ``theta_at``.
     """
     A = np.asarray(A, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
@@ -625,7 +642,7 @@ def sp_scd_solve(A, b, p, x0=None, tol=1e-12, max_outer=20000, max_inner=None, t
         bhat = G2 @ x + bb
         beta = x.copy() if warm_inner else np.zeros(n)
         r = bhat - G1 @ beta
-        target = theta * np.linalg.norm(r_out)
+        target = theta_at(theta, k, theta_decay, theta_min) * np.linalg.norm(r_out)
         t_done = max_inner
         for t in range(max_inner):
             if np.linalg.norm(r) <= target:

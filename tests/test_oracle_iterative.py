@@ -315,3 +315,45 @@ def test_warm_inner_start_keeps_the_sp_step(c1, solver):
     xw, warm = fn(inst.A, inst.b, inst.p, tol=1e-12, seed=3, warm_inner=True)
     assert warm.converged and np.linalg.norm(xw - xs) <= 1e-10 * np.linalg.norm(xs)
     assert sum(warm.inner_iters) < sum(cold.inner_iters)
+
+
+def test_theta_schedule_closed_form():
+    """theta_k = max(theta gamma^k, theta_min); gamma = 1 or <= 0 keeps theta."""
+    assert O.theta_at(0.1, 0, 0.5) == 0.1
+    assert abs(O.theta_at(0.1, 3, 0.5) - 0.0125) < 1e-18
+    assert O.theta_at(0.1, 10, 0.5, theta_min=1e-3) == 1e-3
+    assert O.theta_at(0.1, 7, 1.0) == 0.1 and O.theta_at(0.1, 7, 0.0) == 0.1
+
+
+@pytest.mark.parametrize("solver", ["rk_rgs", "scd"])
+def test_theta_schedule_constant_reproduces(c1, solver):
+    """A schedule with gamma = 1 is the constant inner stop: the same iterates and counts."""
+    inst, _ = c1
+    fn = O.sp_rk_rgs_solve if solver == "rk_rgs" else O.sp_scd_solve
+    x0, i0 = fn(inst.A, inst.b, inst.p, tol=1e-10, max_outer=60, seed=3)
+    x1, i1 = fn(inst.A, inst.b, inst.p, tol=1e-10, max_outer=60, seed=3, theta_decay=1.0, theta_min=0.5)
+    assert np.array_equal(x0, x1) and i0.inner_iters == i1.inner_iters
+
+
+def test_theta_schedule_bounds_each_outer_step(c1):
+    """Where an inner solve stopped on its test, z solves Abar1 z = bhat to theta_k ||r_k||,
+    so x_{k+1} lies within ||Abar1^{-1}|| theta_k ||r_k|| of the exact SP step
+    Abar1^{-1}(Abar2 x_k + bbar): the schedule's theta_k (not theta) is what bounds it."""
+    inst, _ = c1
+    G1, G2 = O.gram_blocks(inst.A, inst.p)
+    bb = O.rhs_bar(inst.A, inst.b, inst.p)
+    inv_norm = 1.0 / np.linalg.eigvalsh(G1)[0]
+    gamma, tmin = 0.3, 1e-6
+    x, info = O.sp_scd_solve(inst.A, inst.b, inst.p, tol=1e-11, max_outer=40, seed=5, record=True,
+                             theta_decay=gamma, theta_min=tmin)
+    it = info.iterates
+    checked = 0
+    for k in range(len(it) - 1):
+        if info.inner_iters[k] >= 200 * inst.n:
+            continue
+        r = O.residual(inst.A, inst.b, inst.p, it[k])
+        sp = np.linalg.solve(G1, G2 @ it[k] + bb)
+        bound = inv_norm * O.theta_at(0.1, k, gamma, tmin) * np.linalg.norm(r)
+        assert np.linalg.norm(it[k + 1] - sp) <= bound * (1 + 1e-9) + 1e-13
+        checked += 1
+    assert checked >= 3 and info.converged
