@@ -127,6 +127,11 @@ typedef struct {
   int32_t factor64;    /* mixed precision, single dense handle: != 0 forms P = Abar1^{-1} from the
                           FP64 Cholesky factor of Abar1 and tests H by FP64 Cholesky (the
                           factorization stays FP64), instead of the FP32 Gauss-Jordan inverse */
+  int32_t reserved0;
+  double theta_decay;  /* randomized methods: the inner stop of outer iteration k uses
+                          theta_k = max(theta * theta_decay^k, theta_min) (a schedule; not in the
+                          paper); 1 (the default) or 0 keeps theta; 0 <= theta_decay <= 1 */
+  double theta_min;    /* the schedule's floor (>= 0); default 0 */
 } ils_options;
 
 typedef enum {

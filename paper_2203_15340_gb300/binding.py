@@ -71,6 +71,9 @@ class ils_options(ctypes.Structure):
         ("wait_limit_ns", ctypes.c_int64),
         ("lanczos_steps", ctypes.c_int32),
         ("factor64", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32),
+        ("theta_decay", ctypes.c_double),
+        ("theta_min", ctypes.c_double),
     ]
 
 

@@ -819,7 +819,12 @@ __global__ void __launch_bounds__(32 * kIterWarps) sp_iter_kernel(SpIterArgs a) 
         else if (!conv) atomicCAS(&st->status, 0, ILS_ERR_NO_CONVERGENCE);
       } else {
         all = 0;
-        if (a.mode == 1 || a.mode == 2) a.col_target2[c] = a.theta2 * rr;
+        if (a.mode == 1 || a.mode == 2) {
+          double th2 = a.theta2;  // the schedule: theta_k^2 = max(theta^2 decay^(2k), theta_min^2)
+          if (a.theta_decay > 0.0 && a.theta_decay < 1.0)
+            th2 = fmax(a.theta2 * pow(a.theta_decay, 2.0 * (double)it), a.theta_min2);
+          a.col_target2[c] = th2 * rr;
+        }
       }
     }
     all_done = all;

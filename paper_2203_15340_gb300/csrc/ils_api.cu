@@ -335,6 +335,7 @@ ils_status validate_options(const ils_options* o) {
   if (o->max_outer < 0 || o->max_inner < 0 || o->check_every < 0) return ILS_ERR_INVALID_ARG;
   if (o->gram != ILS_GRAM_FP64 && o->gram != ILS_GRAM_SPLIT) return ILS_ERR_INVALID_ARG;
   if (!(o->theta > 0.0)) return ILS_ERR_INVALID_ARG;
+  if (!(o->theta_decay >= 0.0 && o->theta_decay <= 1.0) || !(o->theta_min >= 0.0)) return ILS_ERR_INVALID_ARG;
   if (o->stop_rule < ILS_STOP_RELRES || o->stop_rule > ILS_STOP_ERR_BOUND) return ILS_ERR_INVALID_ARG;
   if (o->alpha_mode < 0 || o->alpha_mode > 1 || o->sampler < 0 || o->sampler > 1) return ILS_ERR_INVALID_ARG;
   if (o->inner_form < 0 || o->inner_form > 1 || o->wait_limit_ns < 0) return ILS_ERR_INVALID_ARG;
@@ -847,6 +848,8 @@ ils_status pass_begin(ils_handle h, int64_t c0, int64_t kk, const double* B, int
   a.cvec = method == ILS_SP ? h->cvec : h->bbar;
   a.bhat_out = h->bhat;
   a.theta2 = h->opt.theta * h->opt.theta;
+  a.theta_decay = h->opt.theta_decay;
+  a.theta_min2 = h->opt.theta_min * h->opt.theta_min;
   a.col_target2 = h->col_target2;
   a.bbar = h->bbar;
   a.bnorm2 = h->bnorm2;
@@ -1378,6 +1381,8 @@ ils_status ils_options_default(ils_options* o) {
   o->max_outer = 20000;
   o->max_inner = 0;
   o->theta = 0.1;
+  o->theta_decay = 1.0;
+  o->theta_min = 0.0;
   o->check_every = 0;
   o->scd_sampler = 0;
   o->seed = 0;

@@ -153,7 +153,9 @@ struct SpIterArgs {
   const double* tol_scale;  // device scalar multiplying tol2 (1 / kappa_est^2 for the error-bound
                             // rule), or nullptr
   int64_t wait_ns;          // bound on the grid-barrier waits of the one-launch solve; 0 = 1 s
-  double theta2;       // theta^2 (mode 1): inner target = theta^2 ||r_k||^2
+  double theta2;       // theta^2 (mode 1): inner target = theta_k^2 ||r_k||^2 with
+  double theta_decay;  // theta_k = max(theta theta_decay^k, theta_min) (theta_decay 0 or 1: theta)
+  double theta_min2;
   double* col_target2; // k (mode 1)
   int32_t* col_done;   // k flags
   double* col_rr;      // k: ||r||^2 of each column's returned iterate

@@ -231,3 +231,22 @@ def test_alias_sampler_law_and_convergence(ils, c1):
     assert picks.min() >= 0 and stats.chisquare(counts, expected).pvalue > 1e-4
     x, info = run(ils, inst, ils.ILS_SP_RK_RGS, sampler=1, seed=4)
     assert info.status == ils.ILS_OK and relerr(x, xs) <= 1e-10
+
+
+@pytest.mark.parametrize("method", [1, 2])
+def test_theta_schedule_follows_oracle(ils, c1, method):
+    """theta_k = max(theta gamma^k, theta_min): four outer iterations follow the oracle's
+    schedule (the same inner counts, the same x to rounding; SCD by its greedy rule, RK-RGS by
+    the shared Philox draws), and a full solve with the schedule reaches x*."""
+    inst, xs = c1
+    sched = dict(theta_decay=0.5, theta_min=1e-6)
+    if method == 2:
+        xg, ig = run(ils, inst, method, tol=0.0, max_outer=4, scd_sampler=1, **sched)
+        xo, io = O.sp_scd_solve(inst.A, inst.b, inst.p, tol=0.0, max_outer=4, sampler="greedy", **sched)
+    else:
+        xg, ig = run(ils, inst, method, tol=0.0, max_outer=4, seed=4, check_every=25, **sched)
+        xo, io = O.sp_rk_rgs_solve(inst.A, inst.b, inst.p, tol=0.0, max_outer=4, seed=4, check_every=25, **sched)
+    assert ig.inner_iters == sum(io.inner_iters)
+    assert np.linalg.norm(xg - xo) <= 1e-10 * np.linalg.norm(xo)
+    x, info = run(ils, inst, method, seed=6, **sched)
+    assert info.status == ils.ILS_OK and relerr(x, xs) <= 1e-10

@@ -135,8 +135,10 @@ def test_new_options_are_validated_on_the_host(libpath):
     h = ctypes.c_void_p()
     o = binding.options()
     assert o.stop_rule == 0 and o.estimate == 0 and o.alpha_mode == 0 and o.sampler == 0 and o.factor64 == 0
+    assert o.theta_decay == 1.0 and o.theta_min == 0.0
     for field, bad in (("stop_rule", 3), ("alpha_mode", 2), ("sampler", 2), ("inner_form", 2),
-                       ("wait_limit_ns", -1), ("lanczos_steps", 300), ("estimate", 3)):
+                       ("wait_limit_ns", -1), ("lanczos_steps", 300), ("estimate", 3), ("theta_decay", 1.5),
+                       ("theta_decay", -0.1), ("theta_min", -1e-3)):
         o = binding.options(**{field: bad})
         assert lib.ils_setup(ctypes.byref(h), 30, 5, 20, 10, 1, 30, ctypes.byref(o), None) == \
             binding.ILS_ERR_INVALID_ARG, field
