@@ -109,6 +109,9 @@ struct ils_handle_s {
   bool l64_valid = true;  // L holds the FP64 factor of the current Abar1 (else formed on demand)
   bool pending = false;   // a setup enqueued by ils_refactor_async whose status is not yet read
   cudaStream_t s_aux = nullptr, s_h = nullptr;  // A_2^T A_2 and A^T J b; H and its test
+  cudaStream_t s_b = nullptr;                    // B = P Abar2 beside the one-cluster solve (FP32 refinement)
+  cudaEvent_t ev_b = nullptr;                    // B formed there
+  bool b_async = false;                          // the last setup formed B on s_b (wait for ev_b before use)
   cudaEvent_t ev_start = nullptr, ev_g2 = nullptr, ev_g1 = nullptr;
   cudaEvent_t ev_split2 = nullptr, ev_mma = nullptr;  // A_2's digits split; both Grams' products done
   cudaEvent_t ev_hs = nullptr;                        // H's double-FP32 split formed
@@ -608,6 +611,8 @@ ils_status compute_setup_overlap(ils_handle h, const double* src, int64_t lda_sr
   // (and its estimates on the fourth: H32, G2_32 and P32).
   ILS_CK(cudaStreamWaitEvent(s, h->ev_h, 0));
   if (h->ev_est) ILS_CK(cudaStreamWaitEvent(s, h->ev_est, 0));
+  if (h->b_async) ILS_CK(cudaStreamWaitEvent(s, h->ev_b, 0));  // the previous B still reads P32 and Abar2
+  h->b_async = false;
   ILS_CK(cudaMemsetAsync(h->est, 0, 16 * sizeof(double), s));
   ILS_CK(mark(h, 1));
   h->h_status[0] = 0;
@@ -688,7 +693,15 @@ ils_status compute_setup_overlap(ils_handle h, const double* src, int64_t lda_sr
   }
   ILS_CK(mark(h, 4));
   ILS_CK(cudaStreamWaitEvent(s, h->ev_g2, 0));
-  if (inverted)
+  if (inverted && h->Hh && h->opt.precision == ILS_FP32_REFINE) {
+    // The one-cluster FP32 refinement sweeps with P and Abar2 (B d + c = P (Abar2 d + r)):
+    // B is formed beside it, for the solve paths that read it (they wait for ev_b).
+    ILS_CK(cudaEventRecord(h->ev_b, s));  // P and Abar2 in FP32 are formed
+    ILS_CK(cudaStreamWaitEvent(h->s_b, h->ev_b, 0));
+    ILS_CK(mixed_setup_b(n, nullptr, h->opt.precision, h->P32, h->G2_32, h->Bt32, h->Bt16, h->s_b));
+    ILS_CK(cudaEventRecord(h->ev_b, h->s_b));
+    h->b_async = true;
+  } else if (inverted)
     ILS_CK(mixed_setup_b(n, nullptr, h->opt.precision, h->P32, h->G2_32, h->Bt32, h->Bt16, s));
   else
     ILS_CK(mixed_setup(n, nullptr, h->G2, h->opt.precision, h->L32, h->P32, h->G2_32, h->Bt32, h->Bt16,
@@ -744,6 +757,8 @@ ils_status setup_check(ils_handle h, bool* redone) {
     const ils_status fs = factor_f64_now(h);
     if (fs != ILS_OK) return fs;
     if (*h->h_status != 0) return (ils_status)*h->h_status;
+    if (h->b_async) ILS_CK(cudaStreamWaitEvent(h->stream, h->ev_b, 0));  // B from the FP32 inverse is done
+    h->b_async = false;  // P and B are formed again here, on the handle's stream
     ILS_CK(mixed_setup(h->n, h->L, h->G2, h->opt.precision, h->L32, h->P32, h->G2_32, h->Bt32, h->Bt16,
                        reinterpret_cast<float*>(h->Dinv), h->stream));
     if (redone) *redone = true;
@@ -774,6 +789,9 @@ ils_status setup_finish(ils_handle h) {
 // Autotune the sweep shapes for this handle's n once per process (mixed precision only).
 ils_status tune_handle(ils_handle h) {
   if (h->opt.precision == ILS_FP64 || h->opt.method != ILS_SP) return ILS_OK;
+  // the tuning times sweeps with B: only then does the handle's stream wait for it
+  if (h->b_async && (!h->tune_cache.empty() || !sweeps_tuned(h->n, h->opt.precision)))
+    ILS_CK(cudaStreamWaitEvent(h->stream, h->ev_b, 0));
   ILS_CK(tune_sweeps(h->n, h->opt.precision, h->P32, h->mf ? nullptr : h->Bt32, h->Bt16, h->r32, h->d32a, h->st,
                      h->stream, h->tune_cache.empty() ? nullptr : h->tune_cache.c_str()));
   return ILS_OK;
@@ -782,13 +800,13 @@ ils_status tune_handle(ils_handle h) {
 void free_handle(ils_handle h) {
   if (!h) return;
   if (h->block) cudaFreeAsync(h->block, h->stream);
-  for (cudaStream_t x : {h->s_aux, h->s_h, h->s_est})
+  for (cudaStream_t x : {h->s_aux, h->s_h, h->s_est, h->s_b})
     if (x) {
       cudaStreamSynchronize(x);
       cudaStreamDestroy(x);
     }
   for (cudaEvent_t e : {h->ev_start, h->ev_g2, h->ev_g1, h->ev_hd, h->ev_h, h->ev_acopy, h->ev_rhs, h->ev_split2,
-                        h->ev_mma, h->ev_hs, h->ev_p,
+                        h->ev_mma, h->ev_hs, h->ev_b, h->ev_p,
                         h->ev_estk, h->ev_est})
     if (e) cudaEventDestroy(e);
   if (h->h_st) cudaFreeHost(h->h_st);
@@ -918,6 +936,7 @@ ils_status pass_begin(ils_handle h, int64_t c0, int64_t kk, const double* B, int
   ma.Hh = h->Hh;
   ma.Hl = h->Hl;
   ma.He = h->He;
+  ma.A2_32 = h->b_async ? h->G2_32 : nullptr;  // sweeps from P and Abar2 where B is formed beside
   h->pa = a;
   h->pra = ra;
   h->pma = ma;
@@ -938,20 +957,23 @@ ils_status pass_launch(ils_handle h, int64_t count) {
     // the error-bound stop, a provisional launch runs beside the kappa estimate and a second
     // one, after it, applies the final rule (solve_fused.cu).
     const bool split = h->opt.stop_rule == ILS_STOP_ERR_BOUND && h->ev_estk;
-    const cudaError_t e = mixed_solve_fused(h->pa, h->pma, h->opt.precision, h->coop_sync, s, split ? 1 : 0);
+    cudaEvent_t b_wait = h->b_async ? h->ev_b : nullptr;
+    const cudaError_t e =
+        mixed_solve_fused(h->pa, h->pma, h->opt.precision, h->coop_sync, s, split ? 1 : 0, b_wait);
     if (e == cudaSuccess) {
       if (split) {
         ILS_CK(cudaStreamWaitEvent(s, h->ev_estk, 0));
-        ILS_CK(mixed_solve_fused(h->pa, h->pma, h->opt.precision, h->coop_sync, s, 2));
+        ILS_CK(mixed_solve_fused(h->pa, h->pma, h->opt.precision, h->coop_sync, s, 2, b_wait));
       }
       h->pass_launched = cap;
       return ILS_OK;
     }
     if (e != cudaErrorNotSupported) ILS_CK(e);
   }
-  // every other path reads kappa_est from its first step on
+  // every other path reads kappa_est from its first step on, and B
   if (h->pass_launched == 0 && h->opt.stop_rule == ILS_STOP_ERR_BOUND && h->ev_estk)
     ILS_CK(cudaStreamWaitEvent(s, h->ev_estk, 0));
+  if (h->pass_launched == 0 && h->b_async) ILS_CK(cudaStreamWaitEvent(s, h->ev_b, 0));
   for (int64_t i = 0; i < todo; ++i) {
     if (h->mf) {
       for (int c = 0; c < (int)h->pass_k; ++c)
@@ -1312,9 +1334,10 @@ ils_status create_handle(ils_handle* out, int64_t m, int64_t n, int64_t p, int64
     int lo_prio = 0, hi_prio = 0;
     bool ok = cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio) == cudaSuccess &&
               cudaStreamCreateWithFlags(&h->s_aux, cudaStreamNonBlocking) == cudaSuccess &&
-              cudaStreamCreateWithFlags(&h->s_h, cudaStreamNonBlocking) == cudaSuccess;
+              cudaStreamCreateWithFlags(&h->s_h, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&h->s_b, cudaStreamNonBlocking) == cudaSuccess;
     for (cudaEvent_t* e : {&h->ev_start, &h->ev_g2, &h->ev_g1, &h->ev_hd, &h->ev_h, &h->ev_acopy, &h->ev_rhs,
-                           &h->ev_split2, &h->ev_mma, &h->ev_hs})
+                           &h->ev_split2, &h->ev_mma, &h->ev_hs, &h->ev_b})
       ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
     if (h->opt.estimate) {
       ok = ok && cudaStreamCreateWithPriority(&h->s_est, cudaStreamNonBlocking, hi_prio) == cudaSuccess;
@@ -1580,6 +1603,7 @@ ils_status solve_many_now(ils_handle h, int64_t k, const double* B, int64_t ldb,
     wa.tol2 = tol2_of(h, tol);
     wa.tol_scale = tol_scale_of(h);
     WideMixedResult wr;
+    if (h->b_async) ILS_CK(cudaStreamWaitEvent(h->stream, h->ev_b, 0));
     ILS_CK(wide_mixed_solve(wa, k, B, ldb, X, ldx, x0_zero, &wr, h->h_status + 8, h->stream));
     agg.relres = wr.relres;
     agg.refinements = wr.refinements;

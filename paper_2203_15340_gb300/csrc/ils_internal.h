@@ -173,8 +173,10 @@ struct MixedArgs;
 // phase 0: the whole solve; 1: provisional, stopping on tol2 alone (col_done = 2 when that
 // is met: ||r||^2 and r of x are kept); 2: resume after a provisional launch with the final
 // rule (tol2 * tol_scale), refining on if the kept residual fails it.
+// b_ready (may be null): an event the launch makes the stream wait for before any kernel
+// that reads B (the one-cluster kernel with A2_32 does not).
 cudaError_t mixed_solve_fused(const SpIterArgs& sa, const MixedArgs& ma, int precision, uint32_t* sync,
-                              cudaStream_t s, int phase = 0);
+                              cudaStream_t s, int phase = 0, cudaEvent_t b_ready = nullptr);
 int sp_iterate_blocks(int64_t n);
 
 // Copy the final iterate buffer (chosen on the device) into the user's X.
@@ -279,6 +281,9 @@ struct MixedArgs {
   const float* Hh;
   const float* Hl;
   const int32_t* He;
+  // Abar2 in FP32 (symmetric): where set, the one-cluster solve sweeps d_{s+1} = P (Abar2 d_s + r)
+  // instead of B d_s + P r, and need not wait for B
+  const float* A2_32;
 };
 // H(i, j) = 2^He[i] (Hh + Hl)(i, j) with |Hh + Hl| < 1 and Hl the FP32 rounding of what Hh
 // leaves: about 48 bits of every entry, kept in FP32 so that H x can run on the FP32 pipe
@@ -295,6 +300,8 @@ SweepShape sweep_shape(int64_t n, int64_t k, bool bf16);
 // Time the candidate shapes for (n, k) on the handle's operators (P32 and Bt32 or Bt16) and
 // cache the fastest, once per process.  Synchronizes `s`; not for use inside a capture.
 // cache: a file keeping the choices between processes (read first, rewritten after new tuning), or null.
+// Whether the sweep shapes for (n, precision) are tuned in this process.
+bool sweeps_tuned(int64_t n, int precision);
 cudaError_t tune_sweeps(int64_t n, int precision, const float* P32, const float* Bt32, const void* Bt16,
                         float* scratch_in, float* scratch_out, SolveState* st, cudaStream_t s,
                         const char* cache = nullptr);

@@ -514,16 +514,17 @@ SweepShape sweep_shape(int64_t n, int64_t k, bool bf16) {
   return it != g_tune.end() ? it->second : default_shape(n);
 }
 
+bool sweeps_tuned(int64_t n, int precision) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  bool all = g_tune.count(tune_key(n, 1, false)) && g_tune.count(tune_key(n, 8, false));
+  if (precision == ILS_BF16_REFINE) all = all && g_tune.count(tune_key(n, 1, true)) && g_tune.count(tune_key(n, 8, true));
+  return all;
+}
+
 cudaError_t tune_sweeps(int64_t n, int precision, const float* P32, const float* Bt32, const void* Bt16,
                         float* scratch_in, float* scratch_out, SolveState* st, cudaStream_t s, const char* cache) {
   load_tune_cache(cache);
-  bool all = false;
-  {
-    std::lock_guard<std::mutex> lock(g_tune_mu);
-    all = g_tune.count(tune_key(n, 1, false)) && g_tune.count(tune_key(n, 8, false));
-    if (precision == ILS_BF16_REFINE)
-      all = all && g_tune.count(tune_key(n, 1, true)) && g_tune.count(tune_key(n, 8, true));
-  }
+  const bool all = sweeps_tuned(n, precision);
   if (all) {  // tuned earlier in this process: the file still receives every key
     save_tune_cache(cache);  // takes g_tune_mu itself
     return cudaSuccess;

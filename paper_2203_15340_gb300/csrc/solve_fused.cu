@@ -56,6 +56,7 @@ struct FusedArgs {
   const float* Hh;       // the row-scaled double-FP32 H (split_rows_df), for the cluster kernel
   const float* Hl;
   const int32_t* He;
+  const float* A2_32;    // Abar2 (FP32): sweeps as P (Abar2 d + r) instead of B d + P r (cluster kernel)
 };
 
 __device__ __forceinline__ uint32_t fs_ld_acquire(const uint32_t* p) {
@@ -509,9 +510,10 @@ __global__ void __launch_bounds__(kFsThreads, 1) mixed_solve_cluster_kernel(Fuse
 
   // this CTA's rows: P and B to shared memory (asynchronous), H (double-FP32) to registers
   cl_stage_rows<LD>(Ps, a.P32, n, row0);
-  if (!a.bf16) cl_stage_rows<LD>(Bs, a.Bt32, n, row0);
+  if (a.A2_32) cl_stage_rows<LD>(Bs, a.A2_32, n, row0);  // Bs holds Abar2's rows in this mode
+  else if (!a.bf16) cl_stage_rows<LD>(Bs, a.Bt32, n, row0);
   asm volatile("cp.async.commit_group;" ::: "memory");
-  if (a.bf16) {
+  if (a.bf16 && !a.A2_32) {
     for (int e = threadIdx.x; e < kClRows * LD; e += kFsThreads) {
       const int64_t j = e % LD, i = row0 + e / LD;
       Bs[e] = (i < n && j < n) ? __bfloat162float(a.Bt16[i * n + j]) : 0.f;
@@ -647,7 +649,20 @@ __global__ void __launch_bounds__(kFsThreads, 1) mixed_solve_cluster_kernel(Fuse
     const float* vin = vB;
     for (int sw = 0; sw < a.sweeps; ++sw) {
       float* vout = (vin == vB) ? vA : vB;  // vA (r) is free once P r is formed
-      if (sw > 0) cl_rows_f32<R>(Bs, vin, w, o);
+      if (sw > 0 && a.A2_32) {
+        // t = Abar2 d_s to every CTA's vA (free: P r is formed), then d_{s+1} = P t + c
+        cl_rows_f32<R>(Bs, vB, w, o);
+#pragma unroll
+        for (int q = 0; q < kClRowsPerWarp; ++q) {
+          const int64_t i = row0 + w * kClRowsPerWarp + q;
+          if (i < n) cl_broadcast(vA, i, o[q], cs);
+        }
+        cl_barrier();
+        cl_rows_f32<R>(Ps, vA, w, o);
+        vout = vB;  // d_{s+1} goes back to vB (its readers, the product above, are past the barrier)
+      } else if (sw > 0) {
+        cl_rows_f32<R>(Bs, vin, w, o);
+      }
       const bool last = sw + 1 == a.sweeps;
 #pragma unroll
       for (int q = 0; q < kClRowsPerWarp; ++q) {
@@ -771,7 +786,7 @@ cudaError_t launch_cluster_solve(const FusedArgs& a, cudaStream_t s) {
 }  // namespace
 
 cudaError_t mixed_solve_fused(const SpIterArgs& sa, const MixedArgs& ma, int precision, uint32_t* sync,
-                              cudaStream_t s, int phase) {
+                              cudaStream_t s, int phase, cudaEvent_t b_ready) {
   // the phase input vector is staged in shared memory: n doubles, at most 32 KB
   if (sa.k != 1 || ma.k != 1 || ma.sweeps < 1 || sa.n > 4096) return cudaErrorNotSupported;
   static int max_grid = 0;  // at most one CTA per SM: every CTA is resident with room to spare
@@ -825,9 +840,18 @@ cudaError_t mixed_solve_fused(const SpIterArgs& sa, const MixedArgs& ma, int pre
   a.Hh = ma.Hh;
   a.Hl = ma.Hl;
   a.He = ma.He;
+  a.A2_32 = precision == ILS_FP32_REFINE ? ma.A2_32 : nullptr;
   if (sa.n <= (int64_t)kClRows * kClMaxCtas && sa.wait_ns <= 0 && ma.Hh && ma.Hl && ma.He) {
+    if (!a.A2_32 && b_ready) {
+      const cudaError_t ew = cudaStreamWaitEvent(s, b_ready, 0);
+      if (ew != cudaSuccess) return ew;
+    }
     const cudaError_t ec = launch_cluster_solve(a, s);
     if (ec != cudaErrorNotSupported) return ec;
+  }
+  if (b_ready) {  // the grid kernel reads B
+    const cudaError_t ew = cudaStreamWaitEvent(s, b_ready, 0);
+    if (ew != cudaSuccess) return ew;
   }
   cudaError_t e = cudaMemsetAsync(sync, 0, 4 * sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
