@@ -325,7 +325,8 @@ class Solver:
         return info
 
     def aq_product(self, x, v, prec=0, stream=None):
-        """v = A_2^T (A_2 x) by the one-pass stream (prec 0 FP64, 1 FP32, 2 BF16 copy)."""
+        """v = A_2^T (A_2 x) by the one-pass stream (prec 0 the FP64-accurate copy: FP64, or
+        double-FP32 on a mixed-precision handle; 1 the FP32 copy, 2 the BF16 copy)."""
         return _check(lib().ils_aq_product(self.h, x.data_ptr(), v.data_ptr(), prec, _stream_ptr(stream)),
                       "ils_aq_product")
 

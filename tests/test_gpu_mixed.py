@@ -307,3 +307,32 @@ def test_tune_cache_file(ils, tmp_path):
     torch.cuda.synchronize()
     assert info.status == ils.ILS_OK and relerr(x.cpu().numpy(), O.qr_cholesky_solve(inst.A, inst.b, inst.p)) <= 1e-10
     s.close()
+
+
+def test_fp32_refinement_paths_agree(ils):
+    """The one-cluster FP32 refinement sweeps with P and Abar2 (B d + P r = P (Abar2 d + r)) while
+    B is formed beside it; a caller's wait limit selects the grid-barrier kernel, which reads B
+    and waits for it.  Both reach x*, and one correction of each contracts the residual alike."""
+    import torch
+    inst = W.config2()
+    xs = O.qr_cholesky_solve(inst.A, inst.b, inst.p)
+    At = colmajor(inst.A)  # read by the asynchronous setup: kept alive until its solve
+    s = ils.Solver(At, inst.p, ils.options(precision=ils.ILS_FP32_REFINE))
+    out = {}
+    for name, limit in (("cluster", 0), ("grid", 10 ** 9)):
+        s.set_wait_limit(limit)
+        s.refactor_async(At)  # B again beside the solve
+        x = vec(np.zeros(inst.n))
+        info = s.solve(vec(inst.b), x, tol=1e-12)
+        torch.cuda.synchronize()
+        assert info.status == ils.ILS_OK and relerr(x.cpu().numpy(), xs) <= 1e-10, name
+        one = ils.Solver(colmajor(inst.A), inst.p, ils.options(precision=ils.ILS_FP32_REFINE, max_outer=1))
+        one.set_wait_limit(limit)
+        x1 = vec(np.zeros(inst.n))
+        one.solve(vec(inst.b), x1, tol=0.0, allow=(ils.ILS_ERR_NO_CONVERGENCE,))
+        torch.cuda.synchronize()
+        out[name] = O.relres(inst.A, inst.b, inst.p, x1.cpu().numpy())
+        one.close()
+    s.close()
+    assert out["cluster"] <= 1e-3 and out["grid"] <= 1e-3
+    assert 0.2 <= out["cluster"] / out["grid"] <= 5.0
