@@ -43,6 +43,15 @@ __device__ __forceinline__ void st_remote(const float* local, uint32_t rank, flo
   asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(remote), "f"(v) : "memory");
 }
 
+// Store four consecutive floats (16-byte aligned) into the same location of CTA `rank`.
+__device__ __forceinline__ void st_remote4(const float* local, uint32_t rank, const float (&v)[4]) {
+  uint32_t remote;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(lz_smem_u32(local)), "r"(rank));
+  asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(remote), "f"(v[0]), "f"(v[1]), "f"(v[2]),
+               "f"(v[3])
+               : "memory");
+}
+
 // All threads of all CTAs of the cluster; release/acquire orders the DSMEM stores.
 __device__ __forceinline__ void cluster_sync() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
@@ -67,6 +76,7 @@ __device__ int sturm_count_scaled(const float* al, const float* be2, int m, floa
   bool neg = pm1 < 0.0f || (pm1 == 0.0f && !neg_prev);
   cnt += neg != neg_prev;
   neg_prev = neg;
+#pragma unroll 4
   for (int i = 1; i < m; ++i) {
     const float p = fmaf(al[i] - x, pm1, -be2[i - 1] * pm2);
     neg = p < 0.0f || (p == 0.0f && !neg_prev);
@@ -86,52 +96,76 @@ struct TridiagSmem {
   float al[kLzMaxSteps];
   float be2[kLzMaxSteps];
   float lo[2], hi[2];
-  int first[2];
-  double center, scale;
+  float wlo[32], whi[32];  // per-warp Gershgorin bounds
+  int wfirst[32];          // per-warp first point past the target count
 };
 
 // Smallest and largest eigenvalues of T_m by multisection with every thread of the block:
 // half the threads bracket the smallest, half the largest, each round evaluating one Sturm
 // count per thread at evenly spaced points and keeping the sub-interval where the count
 // first reaches 1 (smallest) or m (largest); four rounds of 128 points narrow [-1, 1] to
-// about 1e-8 of the spectrum's width.  Called by all threads; results in thread 0.
+// about 1e-8 of the spectrum's width.  The Gershgorin interval that is mapped to [-1, 1]
+// is formed in FP32 by all threads at once (a thread per row, then a block min / max) and
+// widened by 2^-16 of its half-width, which covers the roundings of the discs.  Called by
+// all threads; results in thread 0.
 __device__ void tridiag_extremes_block(const double* al, const double* be, int m, TridiagSmem& ts,
                                        double* lo_out, double* hi_out) {
   const int half = blockDim.x / 2;
   const int grp = threadIdx.x < half ? 0 : 1;
   const int t = threadIdx.x - grp * half;
-  if (threadIdx.x == 0) {
-    double glo = 1e300, ghi = -1e300;
-    for (int i = 0; i < m; ++i) {
-      const double rad = (i > 0 ? fabs(be[i - 1]) : 0.0) + (i + 1 < m ? fabs(be[i]) : 0.0);
-      glo = fmin(glo, al[i] - rad);
-      ghi = fmax(ghi, al[i] + rad);
-    }
-    ts.center = 0.5 * (glo + ghi);
-    ts.scale = fmax(0.5 * (ghi - glo), 1e-300);
-    for (int g = 0; g < 2; ++g) {
-      ts.lo[g] = -1.0f;
-      ts.hi[g] = 1.0f;
-    }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  float glo = INFINITY, ghi = -INFINITY;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const float a = (float)al[i];
+    const float b = (float)be[i];
+    const float rad = (i > 0 ? fabsf((float)be[i - 1]) : 0.f) + (i + 1 < m ? fabsf(b) : 0.f);
+    glo = fminf(glo, a - rad);
+    ghi = fmaxf(ghi, a + rad);
+    ts.al[i] = a;
+    ts.be2[i] = b;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    glo = fminf(glo, __shfl_xor_sync(0xffffffffu, glo, o));
+    ghi = fmaxf(ghi, __shfl_xor_sync(0xffffffffu, ghi, o));
+  }
+  if (lane == 0) {
+    ts.wlo[wid] = glo;
+    ts.whi[wid] = ghi;
+  }
+  if (threadIdx.x < 2) {
+    ts.lo[threadIdx.x] = -1.0f;
+    ts.hi[threadIdx.x] = 1.0f;
   }
   __syncthreads();
-  const double c = ts.center, inv = 1.0 / ts.scale;
+  glo = ts.wlo[0];
+  ghi = ts.whi[0];
+  for (int w = 1; w < nw; ++w) {
+    glo = fminf(glo, ts.wlo[w]);
+    ghi = fmaxf(ghi, ts.whi[w]);
+  }
+  const float c = 0.5f * (glo + ghi);
+  const float scale = fmaxf(0.5f * (ghi - glo) * (1.0f + 0x1p-16f), 0x1p-100f);
+  const float inv = 1.0f / scale;
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    ts.al[i] = (float)((al[i] - c) * inv);
-    const float b = (float)(be[i] * inv);
+    ts.al[i] = (ts.al[i] - c) * inv;
+    const float b = ts.be2[i] * inv;
     ts.be2[i] = b * b;
   }
   __syncthreads();
+  // A group is a whole number of warps (blockDim a multiple of 64): each warp posts its
+  // first point past the target (a ballot), and the group's first thread takes the least.
+  const int wpg = (half + 31) >> 5;
   for (int round = 0; round < 4; ++round) {
-    if (threadIdx.x < 2) ts.first[threadIdx.x] = half;
-    __syncthreads();
     const float a = ts.lo[grp], b = ts.hi[grp];
     const float x = a + (b - a) * (float)(t + 1) / (float)(half + 1);
     const int cnt = sturm_count_scaled(ts.al, ts.be2, m, x);
-    if (cnt >= (grp == 0 ? 1 : m)) atomicMin(&ts.first[grp], t);
+    const unsigned hit = __ballot_sync(0xffffffffu, cnt >= (grp == 0 ? 1 : m));
+    if (lane == 0) ts.wfirst[wid] = hit ? (t - lane) + __ffs((int)hit) - 1 : half;
     __syncthreads();
     if (t == 0) {
-      const int f = ts.first[grp];
+      int f = half;
+      for (int k = 0; k < wpg; ++k) f = min(f, ts.wfirst[grp * wpg + k]);
       const float w = (b - a) / (float)(half + 1);
       ts.lo[grp] = a + w * (float)f;
       ts.hi[grp] = f < half ? a + w * (float)(f + 1) : b;
@@ -139,8 +173,8 @@ __device__ void tridiag_extremes_block(const double* al, const double* be, int m
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    *lo_out = c + ts.scale * 0.5 * ((double)ts.lo[0] + (double)ts.hi[0]);
-    *hi_out = c + ts.scale * 0.5 * ((double)ts.lo[1] + (double)ts.hi[1]);
+    *lo_out = (double)c + (double)scale * 0.5 * ((double)ts.lo[0] + (double)ts.hi[0]);
+    *hi_out = (double)c + (double)scale * 0.5 * ((double)ts.lo[1] + (double)ts.hi[1]);
   }
 }
 
@@ -185,6 +219,38 @@ __device__ void slice_matvec(int n, int r0, int R, const float* srows, const voi
   }
 }
 
+// As slice_matvec, but each warp stores its rows of y straight into y's copy in every CTA
+// of the cluster (lane l < cs writes CTA l; four rows as one 16-byte store where aligned),
+// so the product needs no block barrier before the exchange.
+template <bool ROWS_IN_SMEM>
+__device__ void slice_matvec_push(int n, int r0, int R, const float* srows, const void* src, int f64, const float* x,
+                                  float* yfull, int cs) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int rr = 4 * w; rr < R; rr += 4 * kLzWarps) {
+    const int nrow = min(4, R - rr);
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+    for (int j = lane; j < n; j += 32) {
+      const float xv = x[j];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (q < nrow) acc[q] = fmaf(row_entry<ROWS_IN_SMEM>(srows, src, f64, n, r0, rr + q, j), xv, acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] = lz_warp_sum(acc[q]);  // every lane holds the sums
+    if (lane < cs) {
+      float* dst = yfull + r0 + rr;
+      if (nrow == 4 && (lz_smem_u32(dst) & 15u) == 0u) {
+        st_remote4(dst, (uint32_t)lane, acc);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (q < nrow) st_remote(dst + q, (uint32_t)lane, acc[q]);
+      }
+    }
+  }
+}
+
 // Warp w of CTA `rank` publishes its partial v into slot rank * kLzWarps + w of every CTA.
 __device__ __forceinline__ void publish_partial(float* slots, float v, int rank, int cs) {
   v = lz_warp_sum(v);
@@ -201,14 +267,107 @@ __device__ __forceinline__ float gather_partials(const float* slots, int cs) {
   return lz_warp_sum(v);
 }
 
+// dst[0 .. cnt) = FP32 copy of src[off .. off + cnt).  An FP32 source whose slice and
+// destination are 16-byte aligned moves as float4, eight loads in flight per thread (the
+// slice is read once per launch, so its latency is paid up front); otherwise entry by entry.
+__device__ void load_rows(float* dst, const void* src, int f64, size_t off, size_t cnt) {
+  const float* s32 = static_cast<const float*>(src) + off;
+  if (!f64 && ((reinterpret_cast<uintptr_t>(s32) | reinterpret_cast<uintptr_t>(dst)) & 15u) == 0) {
+    constexpr int kB = 8;
+    const size_t c4 = cnt / 4;
+    const float4* s4 = reinterpret_cast<const float4*>(s32);
+    float4* d4 = reinterpret_cast<float4*>(dst);
+    for (size_t base = threadIdx.x; base < c4; base += (size_t)kB * blockDim.x) {
+      float4 v[kB];
+#pragma unroll
+      for (int u = 0; u < kB; ++u) {
+        const size_t e = base + (size_t)u * blockDim.x;
+        if (e < c4) v[u] = __ldg(s4 + e);
+      }
+#pragma unroll
+      for (int u = 0; u < kB; ++u) {
+        const size_t e = base + (size_t)u * blockDim.x;
+        if (e < c4) d4[e] = v[u];
+      }
+    }
+    for (size_t e = 4 * c4 + threadIdx.x; e < cnt; e += blockDim.x) dst[e] = __ldg(s32 + e);
+    return;
+  }
+  for (size_t e = threadIdx.x; e < cnt; e += blockDim.x)
+    dst[e] = f64 ? (float)__ldg(static_cast<const double*>(src) + off + e) : __ldg(s32 + e);
+}
+
+// Rows held in registers (standard Lanczos, n <= 512, at most 32 rows a CTA): warp w keeps
+// rows 4w .. 4w + 3 of the slice and lane l their columns l + 32k (k < 16), zero past the
+// ends, so a step reads only x from shared memory.  The sums run in the same order as
+// slice_matvec's (k ascending, the zero padding adds nothing), so the products are the same.
+constexpr int kRegCols = 16;
+constexpr int kRegRowsPerCta = 4 * kLzWarps;
+
+__device__ __forceinline__ void load_rows_reg(float (&rv)[4][kRegCols], const void* src, int f64, int n, int r0,
+                                              int nr) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  // one branch on the source type, outside the loops, so all 64 loads issue before the
+  // first is used
+  if (f64) {
+    const double* s64 = static_cast<const double*>(src);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int k = 0; k < kRegCols; ++k) {
+        const int rr = 4 * w + q, j = lane + 32 * k;
+        rv[q][k] = rr < nr && j < n ? (float)__ldg(s64 + (size_t)(r0 + rr) * n + j) : 0.f;
+      }
+  } else {
+    const float* s32 = static_cast<const float*>(src);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int k = 0; k < kRegCols; ++k) {
+        const int rr = 4 * w + q, j = lane + 32 * k;
+        rv[q][k] = rr < nr && j < n ? __ldg(s32 + (size_t)(r0 + rr) * n + j) : 0.f;
+      }
+  }
+}
+
+__device__ __forceinline__ void matvec_push_reg(const float (&rv)[4][kRegCols], int n, int r0, int nr, const float* x,
+                                                float* yfull, int cs) {
+  const int lane = threadIdx.x & 31, rr = 4 * (threadIdx.x >> 5);
+  if (rr >= nr) return;  // warp-uniform
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int k = 0; k < kRegCols; ++k) {
+    const int j = lane + 32 * k;
+    const float xv = j < n ? x[j] : 0.f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] = fmaf(rv[q][k], xv, acc[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) acc[q] = lz_warp_sum(acc[q]);
+  if (lane < cs) {
+    const int nrow = min(4, nr - rr);
+    float* dst = yfull + r0 + rr;
+    if (nrow == 4 && (lz_smem_u32(dst) & 15u) == 0u) {
+      st_remote4(dst, (uint32_t)lane, acc);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (q < nrow) st_remote(dst + q, (uint32_t)lane, acc[q]);
+    }
+  }
+}
+
 struct LzArgs {
   LanczosProblem prob[4];
   int count;
   int cs;
 };
 
-template <bool SMEM>
+// ROWS: where a CTA's rows live for all steps: 0 read from L2 each step, 1 shared memory,
+// 2 registers (standard Lanczos only).
+template <int ROWS>
 __global__ void __launch_bounds__(kLzThreads, 1) lanczos_cluster_kernel(LzArgs args) {
+  constexpr bool SMEM = ROWS == 1;
   const int cs = args.cs;
   const LanczosProblem P = args.prob[blockIdx.x / cs];
   const int rank = (int)cluster_rank();
@@ -229,12 +388,11 @@ __global__ void __launch_bounds__(kLzThreads, 1) lanczos_cluster_kernel(LzArgs a
   float* yS = wF + n4;  // this CTA's rows of M2 t
   float* sS = yS + R;  // and of M1 u
   __shared__ LzSmem sm;
+  float rv[4][kRegCols];
+  if (ROWS == 2) load_rows_reg(rv, P.M2, P.m2_f64, n, r0, nr);
   if (SMEM) {
-    for (size_t e = threadIdx.x; e < (size_t)nr * n; e += blockDim.x) {
-      const size_t src = (size_t)r0 * n + e;
-      rows2[e] = P.m2_f64 ? (float)__ldg(static_cast<const double*>(P.M2) + src) : __ldg(static_cast<const float*>(P.M2) + src);
-      if (gen) rows1[e] = P.m1_f64 ? (float)__ldg(static_cast<const double*>(P.M1) + src) : __ldg(static_cast<const float*>(P.M1) + src);
-    }
+    load_rows(rows2, P.M2, P.m2_f64, (size_t)r0 * n, (size_t)nr * n);
+    if (gen) load_rows(rows1, P.M1, P.m1_f64, (size_t)r0 * n, (size_t)nr * n);
   }
   // Start vector: a fixed deterministic pattern with components along every eigenvector.
   for (int s = threadIdx.x; s < n; s += blockDim.x) uF[s] = 1.0f + 0.5f * __cosf(0.7f * (float)s + 0.3f);
@@ -267,48 +425,48 @@ __global__ void __launch_bounds__(kLzThreads, 1) lanczos_cluster_kernel(LzArgs a
   for (int s2 = threadIdx.x; s2 < n; s2 += blockDim.x) tF[s2] *= inv0;
   int m = 0;
   if (!gen) {
-    // Standard Lanczos (M1 = I), one cluster barrier per step: every CTA pushes its rows of
+    // Standard Lanczos (M1 = I), one cluster barrier per step: every warp pushes its rows of
     // y = M2 v_j into every CTA's copy of y (two copies, alternating by step: a CTA one step
     // ahead writes the other), and after the barrier each CTA forms alpha_j = y^T v_j,
     // u = y - alpha_j v_j - beta_{j-1} v_{j-1}, beta_j = ||u|| and v_{j+1} = u / beta_j over
     // the whole vector itself: the same vectors and the same order of sums in every CTA,
-    // so every CTA holds the same values.
+    // so every CTA holds the same values.  Each thread updates the entries it sums, so the
+    // two reductions take one block barrier each and the step three in all.
     float* vF = tF;                                   // v_j (full)
     float* vpF = sF;                                  // v_{j-1}
-    float* yb[2] = {uF, wF};                          // y, two copies
-    __shared__ float red8[kLzWarps];
-    __shared__ float s_dot;
-    auto block_dot = [&](const float* a, const float* b) {
-      float v = 0.f;
-      for (int s2 = threadIdx.x; s2 < n; s2 += blockDim.x) v = fmaf(a[s2], b[s2], v);
+    // y: two copies, wF at even steps (uF holds the start vector until every CTA has passed
+    // step 0's barrier), uF at odd steps
+    __shared__ float red2[2][kLzWarps];               // alternating: a call reuses its buffer two calls later
+    auto block_sum = [&](float v, int buf) {
       v = lz_warp_sum(v);
-      if ((threadIdx.x & 31) == 0) red8[threadIdx.x >> 5] = v;
+      if ((threadIdx.x & 31) == 0) red2[buf][threadIdx.x >> 5] = v;
       __syncthreads();
-      if (threadIdx.x == 0) {
-        float t = 0.f;
-        for (int w = 0; w < kLzWarps; ++w) t += red8[w];
-        s_dot = t;
-      }
-      __syncthreads();
-      const float r = s_dot;
-      __syncthreads();  // s_dot and red8 are reused by the next call
-      return r;
+      float t = 0.f;
+#pragma unroll
+      for (int w = 0; w < kLzWarps; ++w) t += red2[buf][w];
+      return t;
     };
     for (int s2 = threadIdx.x; s2 < n; s2 += blockDim.x) vpF[s2] = 0.f;
     float beta_prev = 0.f;
     __syncthreads();
     for (int j = 0; j < steps; ++j) {
-      float* yF = yb[j & 1];
-      slice_matvec<SMEM>(n, r0, nr, rows2, P.M2, P.m2_f64, vF, yS);  // this CTA's rows of M2 v_j
-      __syncthreads();
-      for (int i = threadIdx.x; i < nr; i += blockDim.x)
-        for (int rk = 0; rk < cs; ++rk) st_remote(&yF[r0 + i], (uint32_t)rk, yS[i]);
+      float* yF = (j & 1) ? uF : wF;
+      if (ROWS == 2) {
+        matvec_push_reg(rv, n, r0, nr, vF, yF, cs);  // this CTA's rows of M2 v_j
+      } else {
+        slice_matvec_push<SMEM>(n, r0, nr, rows2, P.M2, P.m2_f64, vF, yF, cs);
+      }
       cluster_sync();
-      const float alpha = block_dot(yF, vF);
-      for (int s2 = threadIdx.x; s2 < n; s2 += blockDim.x)
-        yF[s2] = fmaf(-beta_prev, vpF[s2], fmaf(-alpha, vF[s2], yF[s2]));  // u, in place
-      __syncthreads();
-      const float beta = sqrtf(fmaxf(block_dot(yF, yF), 0.f));
+      float pa = 0.f;
+      for (int s2 = threadIdx.x; s2 < n; s2 += blockDim.x) pa = fmaf(yF[s2], vF[s2], pa);
+      const float alpha = block_sum(pa, 0);
+      float pb = 0.f;
+      for (int s2 = threadIdx.x; s2 < n; s2 += blockDim.x) {
+        const float u = fmaf(-beta_prev, vpF[s2], fmaf(-alpha, vF[s2], yF[s2]));
+        yF[s2] = u;
+        pb = fmaf(u, u, pb);
+      }
+      const float beta = sqrtf(fmaxf(block_sum(pb, 1), 0.f));
       if (threadIdx.x == 0) {
         sm.alpha[j] = (double)alpha;
         sm.beta[j] = (double)beta;
@@ -390,9 +548,9 @@ size_t lz_smem(int64_t n, int cs, bool rows, bool any_gen) {
   return sizeof(float) * (size_t)((rows ? R * n * (any_gen ? 2 : 1) : 0) + 4 * ((n + 3) & ~3) + 2 * R + 4);
 }
 
-template <bool SMEM>
+template <int ROWS>
 cudaError_t lz_launch(const LzArgs& a, size_t smem, cudaStream_t s) {
-  auto kern = lanczos_cluster_kernel<SMEM>;
+  auto kern = lanczos_cluster_kernel<ROWS>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (a.cs > 8) {
@@ -616,17 +774,21 @@ cudaError_t lanczos_extremes(int count, const LanczosProblem* probs, cudaStream_
   // half the rows per CTA shorten the step (and half the shared memory lets the cluster
   // share SMs with the setup's other kernels).
   const int order[2] = {any_gen ? 8 : 16, any_gen ? 16 : 8};
-  for (int pass = 0; pass < 2; ++pass) {  // rows in shared memory first, then rows from L2
+  // Rows in registers first (standard Lanczos, n <= 512), then in shared memory, then from L2.
+  for (int pass = 0; pass < 3; ++pass) {
     for (int cs : order) {
       if ((n + cs - 1) / cs > kLzThreads) continue;
       a.cs = cs;
-      const size_t sm_rows = lz_smem(n, cs, true, any_gen);
       cudaError_t e;
       if (pass == 0) {
+        if (any_gen || n > 32 * kRegCols || (n + cs - 1) / cs > kRegRowsPerCta) continue;
+        e = lz_launch<2>(a, lz_smem(n, cs, false, false), s);
+      } else if (pass == 1) {
+        const size_t sm_rows = lz_smem(n, cs, true, any_gen);
         if (sm_rows > limit) continue;
-        e = lz_launch<true>(a, sm_rows, s);
+        e = lz_launch<1>(a, sm_rows, s);
       } else {
-        e = lz_launch<false>(a, lz_smem(n, cs, false, any_gen), s);
+        e = lz_launch<0>(a, lz_smem(n, cs, false, any_gen), s);
       }
       if (e == cudaSuccess) return e;
       cudaGetLastError();  // this cluster size is not available: try the next
