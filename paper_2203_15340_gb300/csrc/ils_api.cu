@@ -112,6 +112,8 @@ struct ils_handle_s {
   cudaStream_t s_b = nullptr;                    // B = P Abar2 beside the one-cluster solve (FP32 refinement)
   cudaEvent_t ev_b = nullptr;                    // B formed there
   bool b_async = false;                          // the last setup formed B on s_b (wait for ev_b before use)
+  bool b_deferred = false;                       // ... and left it to be enqueued (ensure_b)
+  cudaEvent_t ev_pb = nullptr;                   // P and Abar2 in FP32 formed (the inverse's status set)
   cudaEvent_t ev_start = nullptr, ev_g2 = nullptr, ev_g1 = nullptr;
   cudaEvent_t ev_split2 = nullptr, ev_mma = nullptr;  // A_2's digits split; both Grams' products done
   cudaEvent_t ev_hs = nullptr;                        // H's double-FP32 split formed
@@ -611,8 +613,10 @@ ils_status compute_setup_overlap(ils_handle h, const double* src, int64_t lda_sr
   // (and its estimates on the fourth: H32, G2_32 and P32).
   ILS_CK(cudaStreamWaitEvent(s, h->ev_h, 0));
   if (h->ev_est) ILS_CK(cudaStreamWaitEvent(s, h->ev_est, 0));
-  if (h->b_async) ILS_CK(cudaStreamWaitEvent(s, h->ev_b, 0));  // the previous B still reads P32 and Abar2
+  // the previous B still reads P32 and Abar2 (a deferred one was never enqueued: dropped)
+  if (h->b_async && !h->b_deferred) ILS_CK(cudaStreamWaitEvent(s, h->ev_b, 0));
   h->b_async = false;
+  h->b_deferred = false;
   ILS_CK(cudaMemsetAsync(h->est, 0, 16 * sizeof(double), s));
   ILS_CK(mark(h, 1));
   h->h_status[0] = 0;
@@ -693,14 +697,14 @@ ils_status compute_setup_overlap(ils_handle h, const double* src, int64_t lda_sr
   }
   ILS_CK(mark(h, 4));
   ILS_CK(cudaStreamWaitEvent(s, h->ev_g2, 0));
+  if (inverted) ILS_CK(cudaEventRecord(h->ev_pb, s));  // P and Abar2 in FP32 are formed
   if (inverted && h->Hh && h->opt.precision == ILS_FP32_REFINE) {
-    // The one-cluster FP32 refinement sweeps with P and Abar2 (B d + c = P (Abar2 d + r)):
-    // B is formed beside it, for the solve paths that read it (they wait for ev_b).
-    ILS_CK(cudaEventRecord(h->ev_b, s));  // P and Abar2 in FP32 are formed
-    ILS_CK(cudaStreamWaitEvent(h->s_b, h->ev_b, 0));
-    ILS_CK(mixed_setup_b(n, nullptr, h->opt.precision, h->P32, h->G2_32, h->Bt32, h->Bt16, h->s_b));
-    ILS_CK(cudaEventRecord(h->ev_b, h->s_b));
+    // The one-cluster FP32 refinement sweeps with P and Abar2 (B d + c = P (Abar2 d + r)) and
+    // never reads B: B is left to ensure_b, which the solve calls once its own kernels are
+    // enqueued (so that B's CTAs never hold the SMs the solve's cluster waits for), and every
+    // path that reads B before it.
     h->b_async = true;
+    h->b_deferred = true;
   } else if (inverted)
     ILS_CK(mixed_setup_b(n, nullptr, h->opt.precision, h->P32, h->G2_32, h->Bt32, h->Bt16, s));
   else
@@ -718,10 +722,36 @@ ils_status compute_setup_overlap(ils_handle h, const double* src, int64_t lda_sr
       ILS_CK(cudaEventRecord(h->ev_est, s));
     }
   }
-  ILS_CK(cudaMemcpyAsync(h->h_status + 6, h->dstatus, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-  ILS_CK(cudaMemcpyAsync(h->h_status + 1, h->gs_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  // The inverse's and the Grams' status words: read by setup_check, which synchronizes the
+  // stream of H's test first, so their copies ride there, off the solve's stream.
+  cudaStream_t st_copy = inverted ? h->s_h : s;
+  if (inverted) ILS_CK(cudaStreamWaitEvent(st_copy, h->ev_pb, 0));
+  ILS_CK(cudaMemcpyAsync(h->h_status + 6, h->dstatus, sizeof(int32_t), cudaMemcpyDeviceToHost, st_copy));
+  ILS_CK(cudaMemcpyAsync(h->h_status + 1, h->gs_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st_copy));
   ILS_CK(mark(h, 5));
   return ILS_OK;
+}
+
+// B = P Abar2 (FP32, and its BF16 copy) of a setup that deferred it: enqueued on s_b behind
+// everything now on the handle's stream (and behind P and Abar2), marked by ev_b.
+cudaError_t ensure_b(ils_handle h) {
+  if (!h->b_deferred) return cudaSuccess;
+  h->b_deferred = false;
+  cudaError_t e = cudaEventRecord(h->ev_b, h->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_b, h->ev_b, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_b, h->ev_pb, 0);
+  if (e == cudaSuccess)
+    e = mixed_setup_b(h->n, nullptr, h->opt.precision, h->P32, h->G2_32, h->Bt32, h->Bt16, h->s_b);
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev_b, h->s_b);
+  return e;
+}
+
+// BReady callback of the fused solve: B's event, its formation enqueued first if deferred.
+cudaError_t b_ready_event(void* ctx, cudaEvent_t* ev) {
+  ils_handle h = static_cast<ils_handle>(ctx);
+  const cudaError_t e = ensure_b(h);
+  *ev = h->b_async ? h->ev_b : nullptr;
+  return e;
 }
 
 // FP64 Cholesky of Abar1 into L (status in h_status[0]), for handles whose setup factored
@@ -757,8 +787,10 @@ ils_status setup_check(ils_handle h, bool* redone) {
     const ils_status fs = factor_f64_now(h);
     if (fs != ILS_OK) return fs;
     if (*h->h_status != 0) return (ils_status)*h->h_status;
-    if (h->b_async) ILS_CK(cudaStreamWaitEvent(h->stream, h->ev_b, 0));  // B from the FP32 inverse is done
+    // B from the FP32 inverse is done (a deferred one was never enqueued)
+    if (h->b_async && !h->b_deferred) ILS_CK(cudaStreamWaitEvent(h->stream, h->ev_b, 0));
     h->b_async = false;  // P and B are formed again here, on the handle's stream
+    h->b_deferred = false;
     ILS_CK(mixed_setup(h->n, h->L, h->G2, h->opt.precision, h->L32, h->P32, h->G2_32, h->Bt32, h->Bt16,
                        reinterpret_cast<float*>(h->Dinv), h->stream));
     if (redone) *redone = true;
@@ -790,8 +822,10 @@ ils_status setup_finish(ils_handle h) {
 ils_status tune_handle(ils_handle h) {
   if (h->opt.precision == ILS_FP64 || h->opt.method != ILS_SP) return ILS_OK;
   // the tuning times sweeps with B: only then does the handle's stream wait for it
-  if (h->b_async && (!h->tune_cache.empty() || !sweeps_tuned(h->n, h->opt.precision)))
+  if (h->b_async && (!h->tune_cache.empty() || !sweeps_tuned(h->n, h->opt.precision))) {
+    ILS_CK(ensure_b(h));
     ILS_CK(cudaStreamWaitEvent(h->stream, h->ev_b, 0));
+  }
   ILS_CK(tune_sweeps(h->n, h->opt.precision, h->P32, h->mf ? nullptr : h->Bt32, h->Bt16, h->r32, h->d32a, h->st,
                      h->stream, h->tune_cache.empty() ? nullptr : h->tune_cache.c_str()));
   return ILS_OK;
@@ -806,7 +840,7 @@ void free_handle(ils_handle h) {
       cudaStreamDestroy(x);
     }
   for (cudaEvent_t e : {h->ev_start, h->ev_g2, h->ev_g1, h->ev_hd, h->ev_h, h->ev_acopy, h->ev_rhs, h->ev_split2,
-                        h->ev_mma, h->ev_hs, h->ev_b, h->ev_p,
+                        h->ev_mma, h->ev_hs, h->ev_b, h->ev_pb, h->ev_p,
                         h->ev_estk, h->ev_est})
     if (e) cudaEventDestroy(e);
   if (h->h_st) cudaFreeHost(h->h_st);
@@ -957,7 +991,11 @@ ils_status pass_launch(ils_handle h, int64_t count) {
     // the error-bound stop, a provisional launch runs beside the kappa estimate and a second
     // one, after it, applies the final rule (solve_fused.cu).
     const bool split = h->opt.stop_rule == ILS_STOP_ERR_BOUND && h->ev_estk;
-    cudaEvent_t b_wait = h->b_async ? h->ev_b : nullptr;
+    BReady b_wait;
+    if (h->b_async) {
+      b_wait.fn = b_ready_event;
+      b_wait.ctx = h;
+    }
     const cudaError_t e =
         mixed_solve_fused(h->pa, h->pma, h->opt.precision, h->coop_sync, s, split ? 1 : 0, b_wait);
     if (e == cudaSuccess) {
@@ -965,6 +1003,7 @@ ils_status pass_launch(ils_handle h, int64_t count) {
         ILS_CK(cudaStreamWaitEvent(s, h->ev_estk, 0));
         ILS_CK(mixed_solve_fused(h->pa, h->pma, h->opt.precision, h->coop_sync, s, 2, b_wait));
       }
+      ILS_CK(ensure_b(h));  // B behind the solve's kernels, where it was deferred
       h->pass_launched = cap;
       return ILS_OK;
     }
@@ -973,7 +1012,10 @@ ils_status pass_launch(ils_handle h, int64_t count) {
   // every other path reads kappa_est from its first step on, and B
   if (h->pass_launched == 0 && h->opt.stop_rule == ILS_STOP_ERR_BOUND && h->ev_estk)
     ILS_CK(cudaStreamWaitEvent(s, h->ev_estk, 0));
-  if (h->pass_launched == 0 && h->b_async) ILS_CK(cudaStreamWaitEvent(s, h->ev_b, 0));
+  if (h->pass_launched == 0 && h->b_async) {
+    ILS_CK(ensure_b(h));
+    ILS_CK(cudaStreamWaitEvent(s, h->ev_b, 0));
+  }
   for (int64_t i = 0; i < todo; ++i) {
     if (h->mf) {
       for (int c = 0; c < (int)h->pass_k; ++c)
@@ -1337,7 +1379,7 @@ ils_status create_handle(ils_handle* out, int64_t m, int64_t n, int64_t p, int64
               cudaStreamCreateWithFlags(&h->s_h, cudaStreamNonBlocking) == cudaSuccess &&
               cudaStreamCreateWithFlags(&h->s_b, cudaStreamNonBlocking) == cudaSuccess;
     for (cudaEvent_t* e : {&h->ev_start, &h->ev_g2, &h->ev_g1, &h->ev_hd, &h->ev_h, &h->ev_acopy, &h->ev_rhs,
-                           &h->ev_split2, &h->ev_mma, &h->ev_hs, &h->ev_b})
+                           &h->ev_split2, &h->ev_mma, &h->ev_hs, &h->ev_b, &h->ev_pb})
       ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
     if (h->opt.estimate) {
       ok = ok && cudaStreamCreateWithPriority(&h->s_est, cudaStreamNonBlocking, hi_prio) == cudaSuccess;
@@ -1603,7 +1645,10 @@ ils_status solve_many_now(ils_handle h, int64_t k, const double* B, int64_t ldb,
     wa.tol2 = tol2_of(h, tol);
     wa.tol_scale = tol_scale_of(h);
     WideMixedResult wr;
-    if (h->b_async) ILS_CK(cudaStreamWaitEvent(h->stream, h->ev_b, 0));
+    if (h->b_async) {
+      ILS_CK(ensure_b(h));
+      ILS_CK(cudaStreamWaitEvent(h->stream, h->ev_b, 0));
+    }
     ILS_CK(wide_mixed_solve(wa, k, B, ldb, X, ldx, x0_zero, &wr, h->h_status + 8, h->stream));
     agg.relres = wr.relres;
     agg.refinements = wr.refinements;

@@ -173,10 +173,16 @@ struct MixedArgs;
 // phase 0: the whole solve; 1: provisional, stopping on tol2 alone (col_done = 2 when that
 // is met: ||r||^2 and r of x are kept); 2: resume after a provisional launch with the final
 // rule (tol2 * tol_scale), refining on if the kept residual fails it.
-// b_ready (may be null): an event the launch makes the stream wait for before any kernel
-// that reads B (the one-cluster kernel with A2_32 does not).
+// b_ready: where B = P Abar2 is formed off the stream, fn(ctx, &ev) yields the event that
+// orders it (enqueuing its formation first where the setup deferred it); the launch makes
+// the stream wait for it before any kernel that reads B (the one-cluster kernel with A2_32
+// does not, and never calls fn).  fn null: B is formed on the stream already.
+struct BReady {
+  cudaError_t (*fn)(void* ctx, cudaEvent_t* ev) = nullptr;
+  void* ctx = nullptr;
+};
 cudaError_t mixed_solve_fused(const SpIterArgs& sa, const MixedArgs& ma, int precision, uint32_t* sync,
-                              cudaStream_t s, int phase = 0, cudaEvent_t b_ready = nullptr);
+                              cudaStream_t s, int phase = 0, BReady b_ready = BReady());
 int sp_iterate_blocks(int64_t n);
 
 // Copy the final iterate buffer (chosen on the device) into the user's X.

@@ -552,6 +552,8 @@ template <int ROWS>
 cudaError_t lz_launch(const LzArgs& a, size_t smem, cudaStream_t s) {
   auto kern = lanczos_cluster_kernel<ROWS>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)  // placed beside the cooperative inverses: keep the SMs' carveout at its largest
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
   if (a.cs > 8) {
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);

@@ -786,7 +786,14 @@ cudaError_t launch_cluster_solve(const FusedArgs& a, cudaStream_t s) {
 }  // namespace
 
 cudaError_t mixed_solve_fused(const SpIterArgs& sa, const MixedArgs& ma, int precision, uint32_t* sync,
-                              cudaStream_t s, int phase, cudaEvent_t b_ready) {
+                              cudaStream_t s, int phase, BReady b_ready) {
+  auto wait_b = [&]() -> cudaError_t {
+    if (!b_ready.fn) return cudaSuccess;
+    cudaEvent_t ev = nullptr;
+    cudaError_t e = b_ready.fn(b_ready.ctx, &ev);
+    if (e == cudaSuccess && ev) e = cudaStreamWaitEvent(s, ev, 0);
+    return e;
+  };
   // the phase input vector is staged in shared memory: n doubles, at most 32 KB
   if (sa.k != 1 || ma.k != 1 || ma.sweeps < 1 || sa.n > 4096) return cudaErrorNotSupported;
   static int max_grid = 0;  // at most one CTA per SM: every CTA is resident with room to spare
@@ -842,15 +849,15 @@ cudaError_t mixed_solve_fused(const SpIterArgs& sa, const MixedArgs& ma, int pre
   a.He = ma.He;
   a.A2_32 = precision == ILS_FP32_REFINE ? ma.A2_32 : nullptr;
   if (sa.n <= (int64_t)kClRows * kClMaxCtas && sa.wait_ns <= 0 && ma.Hh && ma.Hl && ma.He) {
-    if (!a.A2_32 && b_ready) {
-      const cudaError_t ew = cudaStreamWaitEvent(s, b_ready, 0);
+    if (!a.A2_32) {
+      const cudaError_t ew = wait_b();
       if (ew != cudaSuccess) return ew;
     }
     const cudaError_t ec = launch_cluster_solve(a, s);
     if (ec != cudaErrorNotSupported) return ec;
   }
-  if (b_ready) {  // the grid kernel reads B
-    const cudaError_t ew = cudaStreamWaitEvent(s, b_ready, 0);
+  {  // the grid kernel reads B
+    const cudaError_t ew = wait_b();
     if (ew != cudaSuccess) return ew;
   }
   cudaError_t e = cudaMemsetAsync(sync, 0, 4 * sizeof(uint32_t), s);

@@ -232,20 +232,47 @@ __device__ void gj_sweep_pivot(float* T, float* prow, int32_t* status) {
 
 // acc[i][q] += sum_m L(r_i, m) R(m, c0 + q) for the thread's outputs: rows
 // r_i = G::kMR (tid / G::kColGroups) + i, columns c0 = 4 (tid % G::kColGroups), q < 4.
+// With 32-wide tiles (one output row per thread) the thread's row of L is read into
+// registers, a quarter of the row at a time by 16-byte loads, so each step of the product
+// reads only R's float4 from shared memory; the sums run in the same order.
 template <int TS>
 __device__ __forceinline__ void gj_mm(const float* L, const float* R, float (&acc)[GjShape<TS>::kMR][4]) {
   using G = GjShape<TS>;
   const int r0 = (threadIdx.x / G::kColGroups) * G::kMR, c0 = (threadIdx.x % G::kColGroups) * 4;
-#pragma unroll 8
-  for (int m = 0; m < TS; ++m) {
-    const float4 b = *reinterpret_cast<const float4*>(R + m * G::kPad + c0);
+  if constexpr (G::kMR == 1) {
 #pragma unroll
-    for (int i = 0; i < G::kMR; ++i) {
-      const float a = L[(r0 + i) * G::kPad + m];
-      acc[i][0] = fmaf(a, b.x, acc[i][0]);
-      acc[i][1] = fmaf(a, b.y, acc[i][1]);
-      acc[i][2] = fmaf(a, b.z, acc[i][2]);
-      acc[i][3] = fmaf(a, b.w, acc[i][3]);
+    for (int part = 0; part < 4; ++part) {  // 8 entries of the row at a time
+      float lr[TS / 4];
+#pragma unroll
+      for (int h = 0; h < TS / 16; ++h) {
+        const float4 v = reinterpret_cast<const float4*>(L + r0 * G::kPad + part * (TS / 4))[h];
+        lr[4 * h] = v.x;
+        lr[4 * h + 1] = v.y;
+        lr[4 * h + 2] = v.z;
+        lr[4 * h + 3] = v.w;
+      }
+#pragma unroll
+      for (int mm = 0; mm < TS / 4; ++mm) {
+        const int m = part * (TS / 4) + mm;
+        const float4 b = *reinterpret_cast<const float4*>(R + m * G::kPad + c0);
+        acc[0][0] = fmaf(lr[mm], b.x, acc[0][0]);
+        acc[0][1] = fmaf(lr[mm], b.y, acc[0][1]);
+        acc[0][2] = fmaf(lr[mm], b.z, acc[0][2]);
+        acc[0][3] = fmaf(lr[mm], b.w, acc[0][3]);
+      }
+    }
+  } else {
+#pragma unroll 8
+    for (int m = 0; m < TS; ++m) {
+      const float4 b = *reinterpret_cast<const float4*>(R + m * G::kPad + c0);
+#pragma unroll
+      for (int i = 0; i < G::kMR; ++i) {
+        const float a = L[(r0 + i) * G::kPad + m];
+        acc[i][0] = fmaf(a, b.x, acc[i][0]);
+        acc[i][1] = fmaf(a, b.y, acc[i][1]);
+        acc[i][2] = fmaf(a, b.z, acc[i][2]);
+        acc[i][3] = fmaf(a, b.w, acc[i][3]);
+      }
     }
   }
 }
@@ -436,6 +463,11 @@ cudaError_t gj_launch(int64_t n, int count, const float* const* A, float* const*
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
   if (e == cudaSuccess && G::smem_bytes() > 48 * 1024)
     e = cudaFuncSetAttribute(spd_gj_kernel<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_bytes());
+  // SMs running it keep the largest shared-memory carveout, so that the other cooperative
+  // inverse (the test of H) and the setup's cluster kernels can be placed beside its CTAs
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(spd_gj_kernel<TS>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
   if (e == cudaSuccess)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, spd_gj_kernel<TS>, kGjThreads, G::smem_bytes());
   if (e != cudaSuccess) return e;
