@@ -227,7 +227,9 @@ ils_status ils_refactor(ils_handle h, const double* A, int64_t lda, ils_stream_t
  * FP64 factorization has to settle a failed FP32 pivot test, that solve performs it and
  * solves again.  On a mixed-precision single handle with split Grams the solve's
  * A^T J b (Alg. 1 step 4) runs on a second stream beside the setup's last products, and
- * the FP32 test of H (condition (1.3)) on a third stream beside the solve.
+ * the FP32 test of H (condition (1.3)) on a third stream beside the solve; with FP32
+ * refinement, B = P Abar2 (which the one-cluster solve does not read) is formed on a
+ * fourth stream once the solve's own kernels are enqueued, or before any path that reads it.
  * Timings (ils_get_timings) are read at that solve.  Errors: INVALID_ARG, CUDA. */
 ils_status ils_refactor_async(ils_handle h, const double* A, int64_t lda, ils_stream_t stream);
 
