@@ -87,3 +87,34 @@ def test_async_fp32_pivot_failure_settled_in_fp64(ils):
     assert info.status == info_sync.status
     assert np.array_equal(x, x_sync)
     s.close()
+
+
+def test_deferred_b_reaches_the_paths_that_read_it(ils):
+    """With FP32 refinement the asynchronous setup leaves B = P Abar2 to be formed after the
+    one-cluster solve (which does not read it).  A multi-column solve reads B: after a setup
+    of a second matrix it must see that matrix's B, so its answers equal, bit for bit, those
+    of a handle set up on that matrix alone."""
+    import torch
+    inst = W.config2()
+    other = W.dense_gaussian(inst.p, inst.q, inst.n, 0.25, 78)
+    At, At2 = colmajor(inst.A), colmajor(other.A)
+    k = 4
+    Bm = np.stack([inst.b * (1.0 + 0.25 * c) for c in range(k)], axis=1)
+    opts = ils.options(precision=ils.ILS_FP32_REFINE)
+    s = ils.Solver(At2, inst.p, opts)
+    x0 = vec(np.zeros(inst.n))
+    s.solve(vec(other.b), x0, tol=1e-12)  # one column: the cluster solve, then B behind it
+    s.refactor_async(At)
+    X = colmajor(np.zeros((inst.n, k)))
+    info = s.solve_many(colmajor(Bm), X, tol=1e-12)
+    ref = ils.Solver(At, inst.p, opts)
+    Xr = colmajor(np.zeros((inst.n, k)))
+    info_r = ref.solve_many(colmajor(Bm), Xr, tol=1e-12)
+    torch.cuda.synchronize()
+    assert info.status == info_r.status == ils.ILS_OK
+    assert info.outer_iters == info_r.outer_iters
+    assert torch.equal(X, Xr)
+    xs = O.qr_cholesky_solve(inst.A, inst.b, inst.p)
+    assert relerr(X.cpu().numpy()[0], xs) <= 1e-10
+    s.close()
+    ref.close()
