@@ -230,6 +230,9 @@ ils_status ils_refactor(ils_handle h, const double* A, int64_t lda, ils_stream_t
  * the FP32 test of H (condition (1.3)) on a third stream beside the solve; with FP32
  * refinement, B = P Abar2 (which the one-cluster solve does not read) is formed on a
  * fourth stream once the solve's own kernels are enqueued, or before any path that reads it.
+ * Since that A^T J b may run before the setup ends, the right-hand sides of the next solve
+ * must be in place when ils_refactor_async is called (written by earlier work on `stream`
+ * or by the host), not by work enqueued between the two calls.
  * Timings (ils_get_timings) are read at that solve.  Errors: INVALID_ARG, CUDA. */
 ils_status ils_refactor_async(ils_handle h, const double* A, int64_t lda, ils_stream_t stream);
 
