@@ -299,7 +299,10 @@ class Solver:
         return _check(lib().ils_refactor(self.h, ptr, lda, _stream_ptr(stream)), "ils_refactor")
 
     def refactor_async(self, At, stream=None):
-        """Enqueue the setup for new values of A; the next solve reports its status."""
+        """Enqueue the setup for new values of A; the next solve reports its status.
+
+        That solve may form A^T J b before the setup ends, so its right-hand sides must be in
+        place when this is called (not written by work enqueued between the two calls)."""
         ptr, lda = _colmajor_ptr(At, self.m, self.n)
         return _check(lib().ils_refactor_async(self.h, ptr, lda, _stream_ptr(stream)), "ils_refactor_async")
 
