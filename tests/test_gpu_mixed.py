@@ -310,20 +310,22 @@ def test_tune_cache_file(ils, tmp_path):
 
 
 def test_fp32_refinement_paths_agree(ils):
-    """The one-cluster FP32 refinement sweeps with P and Abar2 (B d + P r = P (Abar2 d + r)) while
-    B is formed beside it; a caller's wait limit selects the grid-barrier kernel, which reads B
-    and waits for it.  Both reach x*, and one correction of each contracts the residual alike."""
+    """The one-cluster FP32 refinement sweeps with P and Abar2 (B d + P r = P (Abar2 d + r)) and
+    leaves B to be formed after its kernels; a caller's wait limit selects the grid-barrier
+    kernel, which reads B and has it formed first.  Both reach x*, and one correction of each
+    contracts the residual alike."""
     import torch
     inst = W.config2()
     xs = O.qr_cholesky_solve(inst.A, inst.b, inst.p)
     At = colmajor(inst.A)  # read by the asynchronous setup: kept alive until its solve
+    b = vec(inst.b)  # in place before each asynchronous setup, as the solve after it requires
     s = ils.Solver(At, inst.p, ils.options(precision=ils.ILS_FP32_REFINE))
     out = {}
     for name, limit in (("cluster", 0), ("grid", 10 ** 9)):
         s.set_wait_limit(limit)
-        s.refactor_async(At)  # B again beside the solve
+        s.refactor_async(At)  # B again after the solve's kernels (or before the grid kernel)
         x = vec(np.zeros(inst.n))
-        info = s.solve(vec(inst.b), x, tol=1e-12)
+        info = s.solve(b, x, tol=1e-12)
         torch.cuda.synchronize()
         assert info.status == ils.ILS_OK and relerr(x.cpu().numpy(), xs) <= 1e-10, name
         one = ils.Solver(colmajor(inst.A), inst.p, ils.options(precision=ils.ILS_FP32_REFINE, max_outer=1))

@@ -61,10 +61,11 @@ def test_async_reports_failed_setup_at_solve(ils, prec):
     bad = W.dense_gaussian(400, 300, 60, 2.0, 3)
     assert not O.is_spd(O.normal_matrix(bad.A, bad.p))
     s = ils.Solver(colmajor(good.A), good.p, ils.options(precision=prec))
-    s.refactor_async(colmajor(bad.A))
+    Abad, bbad = colmajor(bad.A), vec(bad.b)  # in place before the asynchronous setup
+    s.refactor_async(Abad)
     x = vec(np.zeros(good.n))
     with pytest.raises(ils.ILSError) as e:
-        s.solve(vec(bad.b), x, tol=1e-12)
+        s.solve(bbad, x, tol=1e-12)
     assert e.value.code == ils.ILS_ERR_NOT_SPD
     # the handle recovers with a valid matrix
     x2, info = _solve(ils, s, colmajor(good.A), vec(good.b), True)
@@ -104,9 +105,10 @@ def test_deferred_b_reaches_the_paths_that_read_it(ils):
     s = ils.Solver(At2, inst.p, opts)
     x0 = vec(np.zeros(inst.n))
     s.solve(vec(other.b), x0, tol=1e-12)  # one column: the cluster solve, then B behind it
+    Bdev = colmajor(Bm)  # in place before the asynchronous setup
     s.refactor_async(At)
     X = colmajor(np.zeros((inst.n, k)))
-    info = s.solve_many(colmajor(Bm), X, tol=1e-12)
+    info = s.solve_many(Bdev, X, tol=1e-12)
     ref = ils.Solver(At, inst.p, opts)
     Xr = colmajor(np.zeros((inst.n, k)))
     info_r = ref.solve_many(colmajor(Bm), Xr, tol=1e-12)
